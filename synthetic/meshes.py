@@ -1,0 +1,140 @@
+"""Seeded synthetic surface meshes shaped like the paper's test bodies.
+
+These generators produce geometry only (vertex coordinates and outward-wound
+triangles).  They contain none of the single-layer-potential arithmetic and
+are shared, as plain inputs, by the FP64 oracle and by the CUDA path.
+
+Shapes (Sec. 4 of the paper uses a cube, a sphere and a thin film):
+  * ``box``       axis-aligned cuboid, each face a structured grid of squares,
+                  every square split into two triangles;
+  * ``cube``      the unit cube as a ``box``;
+  * ``icosphere`` an icosahedron subdivided ``level`` times, vertices
+                  projected onto the sphere;
+  * ``torus``     a parametric torus with major radius R and minor radius r.
+
+All meshes are closed, 2-manifold and oriented with outward normals
+(counter-clockwise winding seen from outside).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def box(lx: float, ly: float, lz: float, nx: int, ny: int, nz: int,
+        center=(0.0, 0.0, 0.0)):
+    """Surface of the cuboid [-lx/2, lx/2] x [-ly/2, ly/2] x [-lz/2, lz/2].
+
+    Face grids have nx x ny squares on the two z faces, nx x nz on the two y
+    faces and ny x nz on the two x faces.  Returns (V[float64 n,3],
+    T[int32 m,3]) with 2*2*(nx*ny + ny*nz + nx*nz) triangles and
+    2*(nx*ny + ny*nz + nx*nz) + 2 vertices.
+    """
+    n = (nx, ny, nz)
+    ext = (lx, ly, lz)
+    idx = -np.ones((nx + 1, ny + 1, nz + 1), dtype=np.int64)
+    # mark lattice points on the boundary
+    I, J, K = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    onb = (I == 0) | (I == nx) | (J == 0) | (J == ny) | (K == 0) | (K == nz)
+    idx[onb] = np.arange(int(onb.sum()))
+    pts = np.stack([I[onb], J[onb], K[onb]], axis=1).astype(np.float64)
+    V = np.empty_like(pts)
+    for q in range(3):
+        V[:, q] = pts[:, q] / n[q] * ext[q] - 0.5 * ext[q] + center[q]
+
+    tris = []
+    # For each face: the two in-face axes (a, b) ordered so that a x b points outward.
+    for axis in range(3):
+        for side in (0, 1):
+            a, b = [(1, 2), (2, 0), (0, 1)][axis]
+            if side == 0:
+                a, b = b, a  # flip orientation on the low face
+            na, nb = n[a], n[b]
+            ia, ib = np.meshgrid(np.arange(na), np.arange(nb), indexing="ij")
+            ia = ia.ravel()
+            ib = ib.ravel()
+
+            def lat(da, db):
+                c = [None, None, None]
+                c[axis] = np.full(ia.shape, side * n[axis])
+                c[a] = ia + da
+                c[b] = ib + db
+                return idx[c[0], c[1], c[2]]
+
+            p00, p10, p11, p01 = lat(0, 0), lat(1, 0), lat(1, 1), lat(0, 1)
+            tris.append(np.stack([p00, p10, p11], axis=1))
+            tris.append(np.stack([p00, p11, p01], axis=1))
+    T = np.concatenate(tris, axis=0).astype(np.int32)
+    return V, T
+
+
+def cube(nper: int, side: float = 1.0):
+    """Cube of edge ``side`` centred at the origin, nper x nper squares per face."""
+    return box(side, side, side, nper, nper, nper)
+
+
+_ICO_FACES = np.array([
+    [0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11],
+    [1, 5, 9], [5, 11, 4], [11, 10, 2], [10, 7, 6], [7, 1, 8],
+    [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8], [3, 8, 9],
+    [4, 9, 5], [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], dtype=np.int64)
+
+
+def icosphere(level: int, radius: float = 1.0):
+    """Icosahedron refined ``level`` times by edge bisection, projected to the sphere.
+
+    Level L has 20*4**L triangles and 10*4**L + 2 vertices.
+    """
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    V = np.array([[-1, t, 0], [1, t, 0], [-1, -t, 0], [1, -t, 0],
+                  [0, -1, t], [0, 1, t], [0, -1, -t], [0, 1, -t],
+                  [t, 0, -1], [t, 0, 1], [-t, 0, -1], [-t, 0, 1]], dtype=np.float64)
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    F = _ICO_FACES.copy()
+    for _ in range(level):
+        nv = V.shape[0]
+        e = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]], axis=0)
+        e.sort(axis=1)
+        key = e[:, 0] * (nv + 1) + e[:, 1]
+        uniq, inv = np.unique(key, return_inverse=True)
+        a = uniq // (nv + 1)
+        b = uniq % (nv + 1)
+        mid = V[a] + V[b]
+        mid /= np.linalg.norm(mid, axis=1, keepdims=True)
+        V = np.concatenate([V, mid], axis=0)
+        m = F.shape[0]
+        ab = nv + inv[:m]
+        bc = nv + inv[m:2 * m]
+        ca = nv + inv[2 * m:]
+        F = np.concatenate([
+            np.stack([F[:, 0], ab, ca], 1),
+            np.stack([F[:, 1], bc, ab], 1),
+            np.stack([F[:, 2], ca, bc], 1),
+            np.stack([ab, bc, ca], 1)], axis=0)
+    return V * radius, F.astype(np.int32)
+
+
+def torus(R: float, r: float, nu: int, nv: int):
+    """Torus around the z axis: nu segments along the tube, nv around it."""
+    u = 2 * np.pi * np.arange(nu) / nu
+    v = 2 * np.pi * np.arange(nv) / nv
+    U, W = np.meshgrid(u, v, indexing="ij")
+    x = (R + r * np.cos(W)) * np.cos(U)
+    y = (R + r * np.cos(W)) * np.sin(U)
+    z = r * np.sin(W)
+    V = np.stack([x.ravel(), y.ravel(), z.ravel()], axis=1)
+    i, j = np.meshgrid(np.arange(nu), np.arange(nv), indexing="ij")
+    i = i.ravel()
+    j = j.ravel()
+    p00 = i * nv + j
+    p10 = ((i + 1) % nu) * nv + j
+    p11 = ((i + 1) % nu) * nv + (j + 1) % nv
+    p01 = i * nv + (j + 1) % nv
+    T = np.concatenate([np.stack([p00, p10, p11], 1), np.stack([p00, p11, p01], 1)], axis=0)
+    return V, T.astype(np.int32)
+
+
+def mesh_stats(V, T):
+    """Vertex/triangle counts and the outward signed volume (positive when outward)."""
+    P = V[T]
+    vol = np.einsum("ij,ij->i", P[:, 0], np.cross(P[:, 1], P[:, 2])).sum() / 6.0
+    return {"n_vertices": int(V.shape[0]), "n_triangles": int(T.shape[0]), "signed_volume": float(vol)}

@@ -1,0 +1,79 @@
+"""Named synthetic workloads shaped like the paper's test bodies (Sec. 4).
+
+Each workload bundles a mesh, a quadrature rule (points per triangle), a
+seeded nodal magnetisation, the oversampled FFT grid, the arithmetic
+precision and the relative L2 tolerance it is judged at.
+
+  cube     unit cube, 8x8 squares per face (768 triangles, 386 nodes), 3-point
+           rule, m = (1,0,0) + U[-0.1,0.1]^3 renormalised, grid 32^3, FP64,
+           tolerance 1e-10.  (Paper: cube runs, Sec. 4 / Table 4.)
+  sphere   icosphere level 5, R = 1 (20480 triangles, 10242 nodes), 7-point
+           rule, vortex m with N(0, 0.05^2) noise, grid 128^3, FP32,
+           tolerance 1e-5.  (Paper: uniformly magnetised sphere, Sec. 4.)
+  plate    2000 x 500 x 20 box, 5x5 squares (168000 triangles, 84002 nodes),
+           3-point rule, smooth random m, grid 512x128x16 requested, FP32,
+           tolerance 1e-5.  (Paper: thin film, Table 3.)
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import fields, meshes
+
+
+@dataclass
+class Workload:
+    name: str
+    V: np.ndarray
+    T: np.ndarray
+    quad: int
+    m_nodal: np.ndarray
+    grid: tuple
+    precision: int
+    tolerance: float
+    seed: int
+    info: dict = field(default_factory=dict)
+
+    @property
+    def n_targets(self) -> int:
+        return int(self.V.shape[0])
+
+    @property
+    def n_sources(self) -> int:
+        return int(self.T.shape[0]) * self.quad
+
+
+def cube(nper: int = 8, grid=(32, 32, 32), precision: int = 64, tolerance: float = 1e-10,
+         index: int = 0) -> Workload:
+    V, T = meshes.cube(nper)
+    seed = fields.workload_seed(index)
+    m = fields.perturbed_uniform(V, seed)
+    return Workload(f"cube{nper}", V, T, 3, m, tuple(grid), precision, tolerance, seed)
+
+
+def sphere(level: int = 5, grid=(128, 128, 128), precision: int = 32, tolerance: float = 1e-5,
+           quad: int = 7, index: int = 1) -> Workload:
+    V, T = meshes.icosphere(level, 1.0)
+    seed = fields.workload_seed(index)
+    m = fields.vortex(V, seed)
+    return Workload(f"sphere_L{level}", V, T, quad, m, tuple(grid), precision, tolerance, seed)
+
+
+def plate(dims=(2000.0, 500.0, 20.0), cell: float = 5.0, grid=(512, 128, 16), precision: int = 32,
+          tolerance: float = 1e-5, index: int = 2) -> Workload:
+    n = tuple(int(round(d / cell)) for d in dims)
+    V, T = meshes.box(*dims, *n)
+    seed = fields.workload_seed(index)
+    m = fields.smooth_random(V, seed)
+    return Workload(f"plate_{int(dims[0])}x{int(dims[1])}x{int(dims[2])}", V, T, 3, m, tuple(grid),
+                    precision, tolerance, seed)
+
+
+def torus(R=2.0, r=0.5, nu=64, nv=32, grid=(128, 128, 64), precision=32, tolerance=1e-5,
+          index: int = 4) -> Workload:
+    V, T = meshes.torus(R, r, nu, nv)
+    seed = fields.workload_seed(index)
+    m = fields.smooth_random(V, seed)
+    return Workload(f"torus_{nu}x{nv}", V, T, 3, m, tuple(grid), precision, tolerance, seed)
