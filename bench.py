@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the single-layer-potential evaluation (slp_eval) on GB300.
+
+Workload (default): sphere of radius 1, icosahedron refined 5 times (20480
+triangles, 10242 boundary nodes), 7-point rule (143360 sources), seeded
+vortex magnetisation at the nodes, oversampled grid 128^3, FP32, plan
+tolerance 1e-5.  One step = one slp_eval of one magnetisation state (the
+whole hot path: charges, spread, pruned FFT, kernel multiply, inverse FFT,
+gather, near field).  Eight seeded states are resident in HBM and cycled.
+
+Metric: boundary targets per second, counted only when the result of every
+checked state is within rel-L2 1e-5 of the FP64 direct-sum oracle.
+
+Timing: W warm-up steps, then K timed steps.  The working set (8 MB grid,
+~10 MB of plan data) fits in the 129 MB L2, so L2 is flushed before every
+step by writing a 512 MB buffer; each step is bracketed by CUDA events on
+the launch stream and the K event intervals are summed.  A barrier and
+torch.cuda.synchronize() bracket the timed loop; the max over ranks is
+reported.  N > 1 GPUs run independent replicas (the evaluation does not
+shard), so scaling is weak.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the FP64 oracle (plain C direct sum, OpenMP) on the
+host cores instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "SLP boundary targets/s at rel-L2 <=1e-5 vs FP64 oracle"
+UNIT = "targets/s"
+N_STATES = 8
+FLUSH_BYTES = 512 << 20
+NEAR_FLOPS_PER_PAIR = 30  # FP32 operations per (target, source) pair inside eps, erfc included
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(name):
+    from synthetic import workloads
+    if name == "sphere":
+        return workloads.sphere()
+    if name == "cube":
+        return workloads.cube()
+    if name == "plate":
+        return workloads.plate()
+    raise ValueError(name)
+
+
+def _states(w, n):
+    from synthetic import fields
+    if w.name.startswith("sphere"):
+        return [fields.vortex(w.V, w.seed + 1000 * i) for i in range(n)]
+    return [fields.smooth_random(w.V, w.seed + 1000 * i) for i in range(n)]
+
+
+def _algorithmic(info, stage, w, pairs_within):
+    """Algorithmic bytes (or FLOPs) of one launch of `stage` (FP32 model)."""
+    es = 4 if info["precision"] == 32 else 8
+    L = info["grid"]
+    n = info["modes"]
+    G = L[0] * L[1] * L[2]
+    Kx = n[0] // 2
+    N = info["n_targets"]
+    Q = info["n_sources"]
+    M = info["n_triangles"]
+    s1 = 2 * es * L[2] * L[1] * Kx  # complex [Lz][Ly][Kx]
+    s2 = 2 * es * L[2] * n[1] * Kx  # complex [Lz][ny][Kx]
+    table = {
+        "charges": ("hbm", 3 * es * N + 3 * es * Q + 4 * Q + 32 * M),
+        "spread": ("hbm", es * G + 5 * es * Q),
+        "fft_x": ("hbm", 2 * es * G + s1),       # read A, write zeros back, write S1
+        "fft_y": ("hbm", s1 + s2),
+        "fft_z_mul": ("hbm", 2 * s2 + es * n[2] * n[1] * Kx // 4),
+        "ifft_y": ("hbm", s2 + s1),
+        "ifft_x": ("hbm", s1 + es * G),
+        "gather": ("hbm", es * G + 4 * es * N + 4 * N + es * N),
+        "near": ("alu", NEAR_FLOPS_PER_PAIR * pairs_within),
+        "near_reduce": ("hbm", 0),
+    }
+    return table[stage]
+
+
+def run_ours(args):
+    import torch
+
+    import paper_1305_3162_gb300 as slp
+    from paper_1305_3162_gb300 import _build
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    else:
+        dist = None
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device"
+    _build.build()
+    dev = torch.cuda.current_device()
+    w = _workload(args.workload)
+    plan = slp.Plan(w.V, w.T, quadrature=w.quad, tolerance=w.tolerance, precision=w.precision, grid=w.grid,
+                    device=dev)
+    info = plan.info
+    dt = torch.float32 if w.precision == 32 else torch.float64
+    states = _states(w, N_STATES)
+    d_states = [torch.as_tensor(s, dtype=dt, device="cuda") for s in states]
+    d_phi = torch.empty(w.n_targets, dtype=dt, device="cuda")
+    stream = torch.cuda.current_stream()
+    kind = slp.SLP_INPUT_NODAL_MAG
+
+    # ---- parity gate (FP64 oracle on the host) for two of the states
+    import oracle
+    errs = []
+    for i in (0, N_STATES - 1):
+        plan.eval(kind, d_states[i], d_phi, stream)
+        torch.cuda.synchronize()
+        slp.slp_check(plan.handle)
+        phi = d_phi.double().cpu().numpy()
+        ref = oracle.slp_nodal(w.V, w.T, w.quad, states[i])
+        errs.append(float(np.linalg.norm(phi - ref) / np.linalg.norm(ref)))
+    rel_l2 = max(errs)
+    parity_ok = rel_l2 <= w.tolerance
+
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # ---- warm-up
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        plan.eval(kind, d_states[i % N_STATES], d_phi, stream)
+    torch.cuda.synchronize()
+
+    # ---- timed region
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(dev)
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev0[i].record(stream)
+        plan.eval(kind, d_states[i % N_STATES], d_phi, stream)
+        ev1[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = w.n_targets * args.steps * ws / total_s
+
+    # ---- per-kernel durations (CUDA events on the launch stream, after an L2 flush)
+    prof = {}
+    for r in range(max(5, min(args.steps, 20))):
+        flush.fill_(float(r))
+        d = slp.slp_debug_profile(plan.handle, kind, d_states[r % N_STATES], d_phi, stream)
+        for k, v in d.items():
+            prof.setdefault(k, []).append(v)
+    prof_ms = {k: statistics.median(v) for k, v in prof.items()}
+
+    # pairs inside eps (host, plan geometry; for the near-field work model)
+    from scipy.spatial import cKDTree
+    y = slp.slp_query_points(plan.handle, w.n_sources)
+    cnt = cKDTree(y).query_ball_point(w.V, info["eps_near"], return_length=True)
+    pairs_within = int(np.sum(cnt))
+
+    dom = max((k for k in prof_ms if prof_ms[k] > 0), key=lambda k: prof_ms[k])
+    peaks, peak_src = _peaks()
+    bound, work = _algorithmic(info, dom, w, pairs_within)
+    dom_s = prof_ms[dom] / 1e3
+    if bound == "hbm":
+        achieved = work / dom_s / 1e9
+        peak = float(peaks["hbm_gbs"])
+        unit = "GB/s"
+    else:
+        achieved = work / dom_s / 1e12
+        mhz = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+        unit = "TFLOP/s"
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        with open(tr_path) as f:
+            tr = json.load(f)
+        ent = tr.get(args.workload, {}).get(dom)
+        if ent and ent.get("source_hash") == _kernel_source_hash():
+            traffic = ent.get("bytes_per_launch")
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom, "kernel_ms": prof_ms[dom],
+                "peak_source": ("sm_max_mhz of " if bound == "alu" else "") + peak_src}
+    hbm_peak = float(peaks["hbm_gbs"])
+    per_kernel = {}
+    for k, v in prof_ms.items():
+        if v <= 0:
+            continue
+        b, wk = _algorithmic(info, k, w, pairs_within)
+        per_kernel[k] = {"ms": round(v, 5), "bound": b,
+                         ("gbs" if b == "hbm" else "tflops"): round(wk / (v / 1e3) / (1e9 if b == "hbm" else 1e12), 2)}
+        if b == "hbm":
+            per_kernel[k]["hbm_frac"] = round(wk / (v / 1e3) / 1e9 / hbm_peak, 4)
+
+    # ---- end to end through the host-buffer entry point (pinned memory)
+    h_in = [torch.as_tensor(s, dtype=dt).pin_memory() for s in states]
+    h_out = torch.empty(w.n_targets, dtype=dt).pin_memory()
+    for i in range(3):
+        slp.slp_eval_host(plan.handle, kind, h_in[i % N_STATES], h_out, stream)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    te0 = time.perf_counter()
+    for i in range(args.steps):
+        slp.slp_eval_host(plan.handle, kind, h_in[i % N_STATES], h_out, stream)
+    torch.cuda.synchronize()
+    te = time.perf_counter() - te0
+    if dist:
+        t = torch.tensor([te], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    es = 4 if w.precision == 32 else 8
+    e2e = {"value": w.n_targets * args.steps * ws / te, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * es * w.n_targets, "d2h_bytes_per_step": es * w.n_targets}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = _cpu_baseline(w, states[0], args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value if parity_ok else 0.0, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if w.precision == 32 else "f64", "data": "synthetic (seeded meshes and magnetisations)",
+            "config": {"workload": f"{w.name}_q{w.quad}_grid{'x'.join(map(str, w.grid))}_fp{w.precision}",
+                       "n_targets": w.n_targets, "n_sources": w.n_sources, "grid": info["grid"], "m": info["m"],
+                       "input": "nodal magnetisation", "states": N_STATES, "tolerance": w.tolerance,
+                       "l2_flush": f"{FLUSH_BYTES >> 20} MB write before every step",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "eps_near": info["eps_near"], "pairs_within_eps": pairs_within,
+                       "near_pairs_visited": info["near_pairs"]},
+            "rel_l2": rel_l2, "parity_ok": parity_ok,
+            "roofline": roofline, "per_kernel": per_kernel,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": info["launches_per_eval"] * args.steps,
+            "wall_s_timed_loop": wall,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def _kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1305_3162_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _cpu_baseline(w, m_nodal, seconds):
+    """The FP64 oracle (plain C, all host cores) on the full workload, repeated
+    until about `seconds` of CPU time have elapsed."""
+    import oracle
+    y, _, _ = oracle.sources(w.V, w.T, w.quad)
+    qk = oracle.charges(w.V, w.T, w.quad, oracle.KIND_NODAL_MAG, m_nodal)
+    reps = 0
+    t0 = time.perf_counter()
+    used = 0
+    while True:
+        _, used = oracle.direct(w.V, y, qk)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or reps >= 1000:
+            break
+    return {"value": w.n_targets * reps / el, "unit": UNIT, "cores": int(used), "kind": "oracle",
+            "sample": f"all {w.n_targets} targets x {w.n_sources} sources (direct sum), {reps} repetitions, "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return
+    w = _workload(args.workload)
+    from synthetic import fields  # noqa: F401
+    states = _states(w, N_STATES)
+    import oracle
+    y, _, _ = oracle.sources(w.V, w.T, w.quad)
+    qks = [oracle.charges(w.V, w.T, w.quad, oracle.KIND_NODAL_MAG, s) for s in states]
+    # each step: the direct sum on a bounded sample of targets (all of them when
+    # that fits the per-step budget), timed on the host cores
+    n_sel = w.n_targets
+    pairs = w.n_targets * w.n_sources
+    if pairs > 3e9:
+        n_sel = max(256, int(3e9 // w.n_sources))
+    rng = np.random.default_rng(w.seed)
+    sel = np.sort(rng.choice(w.n_targets, n_sel, replace=False)) if n_sel < w.n_targets else np.arange(w.n_targets)
+    used = 1
+    for i in range(args.warmup):
+        _, used = oracle.direct_subset(w.V, sel, y, qks[i % N_STATES])
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        _, used = oracle.direct_subset(w.V, sel, y, qks[i % N_STATES])
+    el = time.perf_counter() - t0
+    value = n_sel * args.steps / el
+    sample = f"{n_sel} of {w.n_targets} targets x {w.n_sources} sources per step (direct sum)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded meshes and magnetisations)",
+            "config": {"workload": f"{w.name}_q{w.quad}_grid{'x'.join(map(str, w.grid))}_fp{w.precision}",
+                       "n_targets": w.n_targets, "n_sources": w.n_sources},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": int(used), "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "cube", "plate"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * slp.h — C ABI of the GB300 single-layer-potential library.
+ *
+ * The library evaluates the single layer potential of a surface charge at
+ * the boundary nodes of a closed triangle mesh,
+ *
+ *     phi_i = sum_j sum_s w_s |S_j| sigma_{j,s} / (4 pi |x_i - y_{j,s}|),
+ *
+ * (Exl & Schrefl, "Non-uniform FFT for the finite element computation of the
+ * micromagnetic scalar potential": the discretised single layer potential of
+ * Sec. 2.2 with the triangle quadrature of the quadrature form in Sec. 3),
+ * by splitting the kernel into a smooth part applied through a non-uniform
+ * FFT (spread -> FFT -> multiply -> inverse FFT -> gather, the generalised
+ * convolution theorem of Sec. 2.2 and Sec. 5) and a short-range near-field
+ * correction (Sec. 3.4).
+ *
+ * Conventions shared by every entry point:
+ *   - every call returns an slp_status; nothing throws across the ABI;
+ *   - slp_last_error() returns a thread-local text for the last failure;
+ *   - "device" pointers live on the plan's CUDA device; "host" pointers are
+ *     ordinary (ideally page-locked) CPU memory;
+ *   - the arithmetic type of inputs and outputs is the plan's precision:
+ *     float for precision 32, double for precision 64;
+ *   - quadrature sources are numbered k = j * q + s (triangle j, rule point s,
+ *     the point order of slp_quadrature below); targets are the mesh vertices
+ *     in the caller's order.
+ */
+#ifndef SLP_H
+#define SLP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slp_plan_s *slp_plan_t;
+
+typedef enum {
+    SLP_OK = 0,
+    SLP_ERR_INVALID_ARG = 1,          /* null pointer, bad size, unknown enum value */
+    SLP_ERR_MESH = 2,                 /* index out of range, degenerate triangle, open or
+                                         inconsistently oriented surface, inward normals */
+    SLP_ERR_TOLERANCE_INFEASIBLE = 3, /* the forced grid cannot meet the tolerance */
+    SLP_ERR_OOM = 4,                  /* device allocation failed */
+    SLP_ERR_CUDA = 5,                 /* a CUDA runtime call failed */
+    SLP_ERR_TIMEOUT = 6,              /* a bounded device-side wait gave up */
+    SLP_ERR_NONFINITE = 7,            /* checked evaluation saw NaN/Inf */
+    SLP_ERR_NO_DEVICE = 8,            /* plan built host-only, or no CUDA device */
+    SLP_ERR_UNSUPPORTED = 9           /* option combination not implemented */
+} slp_status;
+
+/* Triangle rules (barycentric points, weights summing to 1):
+ *   SLP_QUAD_1: centroid;
+ *   SLP_QUAD_3: (2/3,1/6,1/6) and cyclic shifts, weights 1/3 (degree 2, interior);
+ *   SLP_QUAD_7: Radon's degree-5 rule: centroid 9/40; (a,a,1-2a),(a,1-2a,a),(1-2a,a,a)
+ *               for a = (6-sqrt15)/21 [weight (155-sqrt15)/1200], then the same three
+ *               for a = (6+sqrt15)/21 [weight (155+sqrt15)/1200]. */
+enum { SLP_QUAD_1 = 1, SLP_QUAD_3 = 3, SLP_QUAD_7 = 7 };
+
+/* Input kinds of slp_eval:
+ *   SIGMA:     sigma at the quadrature points, [Q] (Q = q * n_triangles);
+ *   MAG:       m at the quadrature points, [Q][3]; sigma = m . n_j;
+ *   NODAL_MAG: m at the mesh vertices, [N][3]; interpolated linearly on each
+ *              triangle (P1, Sec. 2.1) to the points; sigma = m(y) . n_j. */
+enum { SLP_INPUT_SIGMA = 0, SLP_INPUT_MAG = 1, SLP_INPUT_NODAL_MAG = 2 };
+
+/* Smooth-kernel choice (the splitting N = (N - N_s) + N_s of Sec. 2.2):
+ *   RADIAL:    N_s = (N truncated at radius R) convolved with an isotropic
+ *              Gaussian; near-field kernel erfc(r/(s sqrt2))/(4 pi r) inside eps;
+ *   SEPARABLE: N_s = a separable band-limited periodic kernel; every pair is
+ *              near and the near kernel is N - N_s evaluated exactly
+ *              (for grids too small to resolve RADIAL at the tolerance);
+ *   AUTO:      RADIAL when feasible on the grid, else SEPARABLE for small
+ *              meshes, else a raised grid (when allowed). */
+enum { SLP_KERNEL_AUTO = 0, SLP_KERNEL_RADIAL = 1, SLP_KERNEL_SEPARABLE = 2 };
+
+/* Near-field evaluation:
+ *   ON_THE_FLY:  kernel values computed per pair in every evaluation;
+ *   PRECOMPUTED: for NODAL_MAG input, the near-field operator is assembled
+ *                once at plan time as a sparse target-by-vertex matrix
+ *                (the precomputed near-field integrals of Sec. 3.4) and
+ *                applied as a sparse product; other inputs fall back to
+ *                ON_THE_FLY;
+ *   AUTO:        PRECOMPUTED when it fits the memory budget. */
+enum { SLP_NEAR_AUTO = 0, SLP_NEAR_ON_THE_FLY = 1, SLP_NEAR_PRECOMPUTED = 2 };
+
+typedef struct {
+    const double *vertices;   /* host, [n_vertices][3], read during slp_plan only */
+    int64_t n_vertices;
+    const int32_t *triangles; /* host, [n_triangles][3], outward (counter-clockwise) winding */
+    int64_t n_triangles;
+} slp_mesh;
+
+typedef struct {
+    int precision;        /* 32 (FP32 spread/FFT/gather/near field) or 64 */
+    int grid[3];          /* oversampled FFT grid per axis (power of two, 8..1024); 0 = auto */
+    int m;                /* Kaiser-Bessel half-width in grid cells; 0 = from the tolerance */
+    int kernel_mode;      /* SLP_KERNEL_* */
+    int near_mode;        /* SLP_NEAR_* */
+    int deterministic;    /* 1: fixed-order reductions, bitwise repeatable results */
+    int device;           /* CUDA device ordinal; -1 builds a host-only plan (slp_query works,
+                             slp_eval returns SLP_ERR_NO_DEVICE) */
+    int allow_grid_raise; /* 1: raise a grid that cannot meet the tolerance (else error) */
+    int check_mesh;       /* 1: require a closed, consistently and outward oriented surface */
+    int reserved[7];
+} slp_plan_opts;
+
+typedef struct {
+    int64_t n_targets;       /* N, mesh vertices */
+    int64_t n_sources;       /* Q = q * n_triangles */
+    int64_t n_triangles;
+    int quadrature;
+    int precision;
+    int grid[3];             /* oversampled grid used (alpha n, alpha = 2) */
+    int modes[3];            /* n per axis */
+    int m;                   /* window half-width */
+    int kernel_mode;         /* resolved SLP_KERNEL_* */
+    int near_mode;           /* resolved SLP_NEAR_* for NODAL_MAG input */
+    int grid_raised;         /* 1 if the requested grid was raised */
+    double center[3];        /* torus centre */
+    double period[3];        /* torus period per axis (physical units) */
+    double sigma_g;          /* Gaussian smoothing width (RADIAL) */
+    double trunc_radius;     /* truncation radius R (RADIAL) */
+    double eps_near;         /* near-field radius (infinite for SEPARABLE) */
+    double tolerance;
+    int64_t near_pairs;          /* (target, source) pairs visited per on-the-fly evaluation */
+    int64_t near_pairs_within;   /* of those, pairs closer than eps_near */
+    int64_t near_matrix_nnz;     /* (target, vertex) entries of the precomputed operator */
+    int64_t bytes_device;        /* device memory held by the plan */
+    int64_t n_spread_items;
+    int64_t n_gather_items;
+    int64_t n_near_items;
+    int launches_per_eval;       /* kernels launched by one slp_eval */
+} slp_info;
+
+/* Fill opts with defaults: precision 32, automatic grid/m/kernel/near mode,
+ * device 0, grid raise allowed, mesh checks on. */
+slp_status slp_default_opts(slp_plan_opts *opts);
+
+/* Build a plan (the setup phase of Alg. 1: geometry-only precomputation).
+ * mesh:       host arrays, only read during the call;
+ * quadrature: SLP_QUAD_1/3/7;
+ * tolerance:  target relative L2 error of phi against the exact quadrature sum
+ *             (drives m, the smoothing width and the near radius);
+ * opts:       may be NULL (defaults);
+ * out:        receives the plan; release with slp_destroy.
+ * Allocates all device memory the plan will use; evaluation allocates nothing.
+ * Errors: INVALID_ARG, MESH, TOLERANCE_INFEASIBLE, OOM, CUDA, NO_DEVICE. */
+slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance,
+                    const slp_plan_opts *opts, slp_plan_t *out);
+
+/* Evaluate phi at the mesh vertices (the computation phase of Alg. 1:
+ * spread, FFT, kernel multiply, inverse FFT, gather, near-field correction).
+ * d_in:   device, layout per input_kind (SLP_INPUT_*), plan precision;
+ * d_phi:  device, [n_targets], plan precision, overwritten;
+ * stream: cudaStream_t to enqueue on (NULL = legacy default stream).
+ * Stream-ordered: returns after enqueueing.  Calls on one plan must not
+ * overlap in time on different streams (they share the plan's scratch).
+ * Errors: INVALID_ARG, NO_DEVICE, CUDA. */
+slp_status slp_eval(slp_plan_t plan, int input_kind, const void *d_in, void *d_phi, void *stream);
+
+/* Same as slp_eval with host buffers: copies h_in to the plan's staging
+ * buffer, evaluates, copies phi back to h_phi and synchronises the stream.
+ * Page-locked host memory gives asynchronous copies. */
+slp_status slp_eval_host(slp_plan_t plan, int input_kind, const void *h_in, void *h_phi, void *stream);
+
+/* Plan parameters and sizes. */
+slp_status slp_query(slp_plan_t plan, slp_info *info);
+
+/* Quadrature point coordinates in the source order k = j*q + s: host [Q][3]. */
+slp_status slp_query_points(slp_plan_t plan, double *points);
+
+/* Synchronise the plan's device and report (and clear) the sticky device
+ * status word written by the kernels. */
+slp_status slp_check(slp_plan_t plan);
+
+/* Release the plan and all its device memory.  NULL is accepted. */
+slp_status slp_destroy(slp_plan_t plan);
+
+/* Static description of a status code; never NULL. */
+const char *slp_status_string(slp_status status);
+
+/* Thread-local detail of the last failing call on this thread ("" if none). */
+const char *slp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLP_H */

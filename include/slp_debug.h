@@ -1,0 +1,90 @@
+/*
+ * slp_debug.h — inspection entry points of the GB300 single-layer-potential
+ * library, for tests and profiling.  They expose intermediate buffers and
+ * plan-time host arrays; production callers need only slp.h.
+ *
+ * Same conventions as slp.h: every call returns an slp_status, host/device
+ * pointers as documented, the plan's precision for floating-point data.
+ */
+#ifndef SLP_DEBUG_H
+#define SLP_DEBUG_H
+
+#include <stdint.h>
+
+#include "slp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Pipeline stages of one evaluation, in launch order. */
+enum {
+    SLP_STAGE_CHARGES = 0, /* qbuf = w sigma, sorted sources */
+    SLP_STAGE_SPREAD = 1,  /* grid A: gridding tensor (Sec. 3.1, quadrature form) */
+    SLP_STAGE_FFT_X = 2,   /* S1: R2C along x, kx < n_x/2 (grid A is zeroed) */
+    SLP_STAGE_FFT_Y = 3,   /* S2: along y, pruned to I_n */
+    SLP_STAGE_FFT_Z = 4,   /* S2: along z, times D, inverse along z */
+    SLP_STAGE_IFFT_Y = 5,  /* S1: inverse along y, zero-padded */
+    SLP_STAGE_IFFT_X = 6,  /* grid B: C2R along x */
+    SLP_STAGE_GATHER = 7,  /* phi = smooth part (window interpolation) */
+    SLP_STAGE_NEAR = 8     /* phi += near-field correction: the full result */
+};
+
+/* Device buffers that slp_debug_copy can read back. */
+enum {
+    SLP_BUF_QBUF = 0,     /* [Q] */
+    SLP_BUF_GRID_A = 1,   /* [Lz][Ly][Lx] */
+    SLP_BUF_GRID_B = 2,   /* [Lz][Ly][Lx] */
+    SLP_BUF_S1 = 3,       /* complex [Lz][Ly][n_x/2] */
+    SLP_BUF_S2 = 4,       /* complex [Lz][n_y][n_x/2] */
+    SLP_BUF_DTAB = 5      /* [n_z/2][n_y/2][n_x/2] */
+};
+
+/* Plan-time host arrays that slp_debug_host_array can copy out. */
+enum {
+    SLP_HOST_SRC_PERM = 0,     /* int32 [Q]: sorted position -> source index k */
+    SLP_HOST_TGT_PERM = 1,     /* int32 [N]: sorted position -> vertex index */
+    SLP_HOST_SRC_GRID = 2,     /* double [Q][4]: frac x, y, z, packed cell (sorted) */
+    SLP_HOST_TGT_GRID = 3,     /* double [N][4] */
+    SLP_HOST_SPREAD_ITEMS = 4, /* int32 [n][8]: c0x, c0y, c0z, begin, end, 0, 0, 0 */
+    SLP_HOST_GATHER_ITEMS = 5, /* int32 [n][8] */
+    SLP_HOST_NEAR_ITEMS = 6,   /* int32 [n][4]: tbegin, tcount, rbegin, rend */
+    SLP_HOST_NEAR_RANGES = 7,  /* int32 [n][2]: begin, end (sorted sources) */
+    SLP_HOST_DTAB = 8,         /* double [n_z/2][n_y/2][n_x/2] */
+    SLP_HOST_SRC_POINTS = 9,   /* double [Q][3]: quadrature points, sorted order */
+    SLP_HOST_TGT_POINTS = 10   /* double [N][3]: targets, sorted order */
+};
+
+/* Run the pipeline of slp_eval up to and including stage last_stage, starting
+ * from a zeroed spread grid (a partial run leaves its grid behind). */
+slp_status slp_debug_run(slp_plan_t plan, int input_kind, const void *d_in, void *d_phi, void *stream,
+                         int last_stage);
+
+/* Copy a device buffer (SLP_BUF_*) to host memory (synchronises the device).
+ * bytes must equal the buffer size reported by slp_debug_buffer_bytes. */
+slp_status slp_debug_copy(slp_plan_t plan, int buffer, void *host, int64_t bytes);
+slp_status slp_debug_buffer_bytes(slp_plan_t plan, int buffer, int64_t *bytes);
+
+/* Element count of a host array (SLP_HOST_*) and a copy of it. */
+slp_status slp_debug_host_count(slp_plan_t plan, int which, int64_t *count);
+slp_status slp_debug_host_array(slp_plan_t plan, int which, void *out, int64_t count);
+
+/* Run one full evaluation and time each kernel with CUDA events recorded on
+ * `stream` between the launches; ms[i] receives kernel i's duration
+ * (n >= 10 entries; the kernels in launch order are named by
+ * slp_debug_stage_name).  Synchronises the stream. */
+slp_status slp_debug_profile(slp_plan_t plan, int input_kind, const void *d_in, void *d_phi, void *stream,
+                             float *ms, int n);
+const char *slp_debug_stage_name(int i);
+
+/* The normalised Kaiser-Bessel window psi(d) in grid units (Sec. 3.2,
+ * Eq. (KBfct) scaled to psi(0) = 1) and its continuous Fourier transform at
+ * frequency index l of an L-point grid, both in FP64 on the host. */
+double slp_debug_window(int m, double d);
+double slp_debug_window_hat(int m, int L, double l);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SLP_DEBUG_H */

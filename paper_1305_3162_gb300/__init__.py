@@ -1,0 +1,314 @@
+"""GB300 single-layer-potential library (NUFFT method of Exl & Schrefl).
+
+Thin Python binding of the C ABI in ``include/slp.h``: the functions below
+carry the same names as the C entry points and only marshal arguments
+(numpy arrays for host data, torch CUDA tensors or raw device pointers for
+device data, a CUDA stream handle).  Every step of an evaluation runs in the
+library's own CUDA kernels; there is no CPU or PyTorch fallback: if the
+compiled library is missing, loading raises.
+
+Build the library with ``paper_1305_3162_gb300._build.build()`` (or
+``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH
+
+# ------------------------------------------------------------------ constants
+SLP_OK = 0
+SLP_ERR_INVALID_ARG = 1
+SLP_ERR_MESH = 2
+SLP_ERR_TOLERANCE_INFEASIBLE = 3
+SLP_ERR_OOM = 4
+SLP_ERR_CUDA = 5
+SLP_ERR_TIMEOUT = 6
+SLP_ERR_NONFINITE = 7
+SLP_ERR_NO_DEVICE = 8
+SLP_ERR_UNSUPPORTED = 9
+
+SLP_QUAD_1, SLP_QUAD_3, SLP_QUAD_7 = 1, 3, 7
+SLP_INPUT_SIGMA, SLP_INPUT_MAG, SLP_INPUT_NODAL_MAG = 0, 1, 2
+SLP_KERNEL_AUTO, SLP_KERNEL_RADIAL, SLP_KERNEL_SEPARABLE = 0, 1, 2
+SLP_NEAR_AUTO, SLP_NEAR_ON_THE_FLY, SLP_NEAR_PRECOMPUTED = 0, 1, 2
+
+SLP_STAGE_CHARGES, SLP_STAGE_SPREAD, SLP_STAGE_FFT_X, SLP_STAGE_FFT_Y, SLP_STAGE_FFT_Z = 0, 1, 2, 3, 4
+SLP_STAGE_IFFT_Y, SLP_STAGE_IFFT_X, SLP_STAGE_GATHER, SLP_STAGE_NEAR = 5, 6, 7, 8
+SLP_BUF_QBUF, SLP_BUF_GRID_A, SLP_BUF_GRID_B, SLP_BUF_S1, SLP_BUF_S2, SLP_BUF_DTAB = 0, 1, 2, 3, 4, 5
+(SLP_HOST_SRC_PERM, SLP_HOST_TGT_PERM, SLP_HOST_SRC_GRID, SLP_HOST_TGT_GRID, SLP_HOST_SPREAD_ITEMS,
+ SLP_HOST_GATHER_ITEMS, SLP_HOST_NEAR_ITEMS, SLP_HOST_NEAR_RANGES, SLP_HOST_DTAB, SLP_HOST_SRC_POINTS,
+ SLP_HOST_TGT_POINTS) = range(11)
+
+
+class SlpError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status}: {detail}")
+        self.status = status
+
+
+# ------------------------------------------------------------------ structs
+class slp_mesh(ctypes.Structure):
+    _fields_ = [("vertices", ctypes.POINTER(ctypes.c_double)), ("n_vertices", ctypes.c_int64),
+                ("triangles", ctypes.POINTER(ctypes.c_int32)), ("n_triangles", ctypes.c_int64)]
+
+
+class slp_plan_opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("grid", ctypes.c_int * 3), ("m", ctypes.c_int),
+                ("kernel_mode", ctypes.c_int), ("near_mode", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("device", ctypes.c_int), ("allow_grid_raise", ctypes.c_int), ("check_mesh", ctypes.c_int),
+                ("reserved", ctypes.c_int * 7)]
+
+
+class slp_info(ctypes.Structure):
+    _fields_ = [("n_targets", ctypes.c_int64), ("n_sources", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
+                ("quadrature", ctypes.c_int), ("precision", ctypes.c_int), ("grid", ctypes.c_int * 3),
+                ("modes", ctypes.c_int * 3), ("m", ctypes.c_int), ("kernel_mode", ctypes.c_int),
+                ("near_mode", ctypes.c_int), ("grid_raised", ctypes.c_int), ("center", ctypes.c_double * 3),
+                ("period", ctypes.c_double * 3), ("sigma_g", ctypes.c_double), ("trunc_radius", ctypes.c_double),
+                ("eps_near", ctypes.c_double), ("tolerance", ctypes.c_double), ("near_pairs", ctypes.c_int64),
+                ("near_pairs_within", ctypes.c_int64), ("near_matrix_nnz", ctypes.c_int64),
+                ("bytes_device", ctypes.c_int64), ("n_spread_items", ctypes.c_int64),
+                ("n_gather_items", ctypes.c_int64), ("n_near_items", ctypes.c_int64),
+                ("launches_per_eval", ctypes.c_int)]
+
+    def to_dict(self):
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            if isinstance(v, ctypes.Array):
+                v = list(v)
+            out[name] = v
+        return out
+
+
+# ------------------------------------------------------------------ loading
+_lib = None
+
+#: C entry points the binding requires (the declarations of include/slp.h and include/slp_debug.h)
+EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_host", "slp_query", "slp_query_points",
+            "slp_check", "slp_destroy", "slp_status_string", "slp_last_error",
+            "slp_debug_run", "slp_debug_copy", "slp_debug_buffer_bytes", "slp_debug_host_count",
+            "slp_debug_host_array", "slp_debug_window", "slp_debug_window_hat", "slp_debug_profile",
+            "slp_debug_stage_name"]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"CUDA library not built: {_LIB_PATH} is missing "
+                          "(run paper_1305_3162_gb300._build.build())")
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp = ctypes.c_void_p
+    St = ctypes.c_int
+    I64 = ctypes.c_int64
+    sig = {
+        "slp_default_opts": ([ctypes.POINTER(slp_plan_opts)], St),
+        "slp_plan": ([ctypes.POINTER(slp_mesh), ctypes.c_int, ctypes.c_double, ctypes.POINTER(slp_plan_opts),
+                      ctypes.POINTER(vp)], St),
+        "slp_eval": ([vp, ctypes.c_int, vp, vp, vp], St),
+        "slp_eval_host": ([vp, ctypes.c_int, vp, vp, vp], St),
+        "slp_query": ([vp, ctypes.POINTER(slp_info)], St),
+        "slp_query_points": ([vp, ctypes.POINTER(ctypes.c_double)], St),
+        "slp_check": ([vp], St),
+        "slp_destroy": ([vp], St),
+        "slp_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "slp_last_error": ([], ctypes.c_char_p),
+        "slp_debug_run": ([vp, ctypes.c_int, vp, vp, vp, ctypes.c_int], St),
+        "slp_debug_copy": ([vp, ctypes.c_int, vp, I64], St),
+        "slp_debug_buffer_bytes": ([vp, ctypes.c_int, ctypes.POINTER(I64)], St),
+        "slp_debug_host_count": ([vp, ctypes.c_int, ctypes.POINTER(I64)], St),
+        "slp_debug_host_array": ([vp, ctypes.c_int, vp, I64], St),
+        "slp_debug_window": ([ctypes.c_int, ctypes.c_double], ctypes.c_double),
+        "slp_debug_window_hat": ([ctypes.c_int, ctypes.c_int, ctypes.c_double], ctypes.c_double),
+        "slp_debug_profile": ([vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int], St),
+        "slp_debug_stage_name": ([ctypes.c_int], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(st: int, where: str):
+    if st != SLP_OK:
+        detail = load().slp_last_error().decode(errors="replace")
+        raise SlpError(st, where, detail)
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor, numpy array or integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------ C entry points
+def slp_default_opts() -> slp_plan_opts:
+    o = slp_plan_opts()
+    _check(load().slp_default_opts(ctypes.byref(o)), "slp_default_opts")
+    return o
+
+
+def slp_plan(vertices, triangles, quadrature: int, tolerance: float, opts: slp_plan_opts | None = None):
+    """Build a plan; returns an opaque handle (release with slp_destroy)."""
+    lib = load()
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    T = np.ascontiguousarray(triangles, dtype=np.int32)
+    mesh = slp_mesh(V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), V.shape[0],
+                    T.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), T.shape[0])
+    out = ctypes.c_void_p()
+    o = opts if opts is not None else slp_default_opts()
+    _check(lib.slp_plan(ctypes.byref(mesh), int(quadrature), float(tolerance), ctypes.byref(o), ctypes.byref(out)),
+           "slp_plan")
+    return out
+
+
+def slp_eval(plan, input_kind: int, d_in, d_phi, stream=None):
+    _check(load().slp_eval(plan, int(input_kind), _ptr(d_in), _ptr(d_phi), _stream(stream)), "slp_eval")
+
+
+def slp_eval_host(plan, input_kind: int, h_in, h_phi, stream=None):
+    _check(load().slp_eval_host(plan, int(input_kind), _ptr(h_in), _ptr(h_phi), _stream(stream)), "slp_eval_host")
+
+
+def slp_query(plan) -> dict:
+    info = slp_info()
+    _check(load().slp_query(plan, ctypes.byref(info)), "slp_query")
+    return info.to_dict()
+
+
+def slp_query_points(plan, n_sources: int):
+    pts = np.zeros((n_sources, 3))
+    _check(load().slp_query_points(plan, pts.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "slp_query_points")
+    return pts
+
+
+def slp_check(plan):
+    _check(load().slp_check(plan), "slp_check")
+
+
+def slp_destroy(plan):
+    if plan is not None:
+        _check(load().slp_destroy(plan), "slp_destroy")
+
+
+def slp_status_string(status: int) -> str:
+    return load().slp_status_string(int(status)).decode()
+
+
+def slp_last_error() -> str:
+    return load().slp_last_error().decode(errors="replace")
+
+
+def slp_debug_run(plan, input_kind, d_in, d_phi, stream=None, last_stage=SLP_STAGE_NEAR):
+    _check(load().slp_debug_run(plan, int(input_kind), _ptr(d_in), _ptr(d_phi), _stream(stream), int(last_stage)),
+           "slp_debug_run")
+
+
+def slp_debug_copy(plan, buffer: int, dtype):
+    n = ctypes.c_int64()
+    _check(load().slp_debug_buffer_bytes(plan, int(buffer), ctypes.byref(n)), "slp_debug_buffer_bytes")
+    out = np.zeros(n.value // np.dtype(dtype).itemsize, dtype=dtype)
+    _check(load().slp_debug_copy(plan, int(buffer), _ptr(out), n.value), "slp_debug_copy")
+    return out
+
+
+_HOST_DTYPES = {SLP_HOST_SRC_PERM: np.int32, SLP_HOST_TGT_PERM: np.int32, SLP_HOST_SRC_GRID: np.float64,
+                SLP_HOST_TGT_GRID: np.float64, SLP_HOST_SPREAD_ITEMS: np.int32, SLP_HOST_GATHER_ITEMS: np.int32,
+                SLP_HOST_NEAR_ITEMS: np.int32, SLP_HOST_NEAR_RANGES: np.int32, SLP_HOST_DTAB: np.float64,
+                SLP_HOST_SRC_POINTS: np.float64, SLP_HOST_TGT_POINTS: np.float64}
+
+
+def slp_debug_host_array(plan, which: int):
+    n = ctypes.c_int64()
+    _check(load().slp_debug_host_count(plan, int(which), ctypes.byref(n)), "slp_debug_host_count")
+    out = np.zeros(n.value, dtype=_HOST_DTYPES[which])
+    _check(load().slp_debug_host_array(plan, int(which), _ptr(out), n.value), "slp_debug_host_array")
+    return out
+
+
+def slp_debug_profile(plan, input_kind, d_in, d_phi, stream=None) -> dict:
+    """Per-kernel durations (ms) of one evaluation, CUDA events on the launch stream."""
+    n = 10
+    ms = (ctypes.c_float * n)()
+    _check(load().slp_debug_profile(plan, int(input_kind), _ptr(d_in), _ptr(d_phi), _stream(stream), ms, n),
+           "slp_debug_profile")
+    return {load().slp_debug_stage_name(i).decode(): float(ms[i]) for i in range(n)}
+
+
+def slp_debug_window(m: int, d: float) -> float:
+    return load().slp_debug_window(int(m), float(d))
+
+
+def slp_debug_window_hat(m: int, L: int, l: float) -> float:
+    return load().slp_debug_window_hat(int(m), int(L), float(l))
+
+
+# ------------------------------------------------------------------ convenience
+class Plan:
+    """Owns an slp plan handle; ``eval`` enqueues on the given (or current) torch stream."""
+
+    def __init__(self, vertices, triangles, quadrature=7, tolerance=1e-5, precision=32, grid=None, m=0,
+                 kernel_mode=SLP_KERNEL_AUTO, near_mode=SLP_NEAR_AUTO, deterministic=False, device=0,
+                 allow_grid_raise=True, check_mesh=True):
+        o = slp_default_opts()
+        o.precision = int(precision)
+        if grid is not None:
+            for d in range(3):
+                o.grid[d] = int(grid[d])
+        o.m = int(m)
+        o.kernel_mode = int(kernel_mode)
+        o.near_mode = int(near_mode)
+        o.deterministic = int(bool(deterministic))
+        o.device = int(device)
+        o.allow_grid_raise = int(bool(allow_grid_raise))
+        o.check_mesh = int(bool(check_mesh))
+        self.handle = slp_plan(vertices, triangles, quadrature, tolerance, o)
+        self.info = slp_query(self.handle)
+        self.n_targets = self.info["n_targets"]
+        self.n_sources = self.info["n_sources"]
+        self.precision = self.info["precision"]
+
+    def eval(self, input_kind, d_in, d_phi, stream=None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream()
+        slp_eval(self.handle, input_kind, d_in, d_phi, stream)
+
+    def close(self):
+        if self.handle is not None:
+            slp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,87 @@
+// Device helpers shared by the CUDA kernels: vector types per precision,
+// complex arithmetic, packed cell coordinates and the Kaiser-Bessel window.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "slp_internal.h"
+
+namespace slp {
+
+template <typename T> struct VecT;
+template <> struct VecT<float> {
+    typedef float2 T2;
+    typedef float4 T4;
+};
+template <> struct VecT<double> {
+    typedef double2 T2;
+    typedef double4 T4;
+};
+
+// ---------------------------------------------------------------- complex
+__device__ __forceinline__ float2 cmk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 cmk(double a, double b) { return make_double2(a, b); }
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return cmk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return cmk(a.x, -a.y); }
+// multiply by -i (forward) or +i (inverse)
+template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return cmk(a.y, -a.x); }
+template <typename C> __device__ __forceinline__ C cmul_pi(C a) { return cmk(-a.y, a.x); }
+template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { return cmk(a.x * s, a.y * s); }
+
+// ---------------------------------------------------------------- cells
+// A grid coordinate u = c + f is stored as the fractional part f in [0, 1)
+// per axis (x, y, z components) and the integer cell c packed in w:
+// cx | cy << 10 | cz << 20 (each axis < 1024).
+__device__ __forceinline__ int packed_cell(float w) { return __float_as_int(w); }
+__device__ __forceinline__ int packed_cell(double w) { return (int)w; }
+__device__ __forceinline__ void unpack_cell(int c, int &cx, int &cy, int &cz) {
+    cx = c & 1023;
+    cy = (c >> 10) & 1023;
+    cz = (c >> 20) & 1023;
+}
+
+// ---------------------------------------------------------------- window
+// Kaiser-Bessel window of the paper's Sec. 3.2 in grid units, truncated to
+// |d| <= m and normalised to 1 at d = 0:
+//   psi(d) = sinh(beta s) / (s sinh beta),  s = sqrt(1 - (d/m)^2),  beta = b m,
+// with the limit beta / sinh(beta) at |d| = m.
+__device__ __forceinline__ float kb_window(float d, float inv_m, float beta, float inv_sinh_beta) {
+    const float t = d * inv_m;
+    const float s2 = 1.0f - t * t;
+    if (s2 < 0.0f) return 0.0f;
+    const float s = sqrtf(s2);
+    const float bs = beta * s;
+    const float r = (bs > 1e-3f) ? sinhf(bs) / s : beta * (1.0f + bs * bs * (1.0f / 6.0f));
+    return r * inv_sinh_beta;
+}
+__device__ __forceinline__ double kb_window(double d, double inv_m, double beta, double inv_sinh_beta) {
+    const double t = d * inv_m;
+    const double s2 = 1.0 - t * t;
+    if (s2 < 0.0) return 0.0;
+    const double s = sqrt(s2);
+    const double bs = beta * s;
+    const double r = (bs > 1e-6) ? sinh(bs) / s : beta * (1.0 + bs * bs * (1.0 / 6.0));
+    return r * inv_sinh_beta;
+}
+
+// warp sum
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// error codes written to the plan's status word
+enum { DEV_ERR_NONE = 0, DEV_ERR_BAD_ITEM = 1, DEV_ERR_BAD_INDEX = 2 };
+
+__device__ __forceinline__ void set_error(int *err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+}  // namespace slp

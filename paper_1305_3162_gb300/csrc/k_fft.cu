@@ -1,0 +1,403 @@
+// Pruned 3-D FFT passes of the smooth part (paper Sec. 2.2 / Sec. 5):
+//
+//   phi^s = NFFT( c(N_s) (.) FFT(A) / c(Upsilon) ),
+//
+// with the two window deconvolutions and c_l(N_s) folded into one real,
+// even table D.  Only l in I_n (|l_q| < n_q / 2; the Nyquist index is
+// dropped, which keeps the result real) survives the multiply, so each
+// pass transforms one axis and keeps or restores only the modes it needs:
+//
+//   FX  grid A[z][y][x] (real)  -> S1[z][y][kx],  kx < n_x/2   (R2C, two rows per complex FFT)
+//   FY  S1 -> S2[z][ky'][kx],  ky' over n_y signed modes       (column FFT, pruned output)
+//   FZ  S2 in place: FFT along z, multiply by D, inverse FFT    (fused pencil)
+//   IY  S2 -> S1, zero-padded inverse along y
+//   IX  S1 -> grid B (real), two rows per complex inverse FFT
+//
+// Each pass stages a batch of 1-D transforms in shared memory and runs a
+// mixed-radix (8/4/2) Stockham autosort FFT on them; consecutive threads
+// work on consecutive columns, so shared-memory accesses are conflict free
+// and global accesses coalesce along the contiguous axis.  FX also writes
+// zeros back to grid A so the next spread starts from a clean grid.
+#include "dev_common.cuh"
+
+namespace slp {
+
+// ---------------------------------------------------------------- small DFTs
+template <typename C> __device__ __forceinline__ void dft2(C &a, C &b) {
+    const C t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+template <typename C, bool INV> __device__ __forceinline__ void dft4(C &a, C &b, C &c, C &d) {
+    const C s0 = cadd(a, c), d0 = csub(a, c);
+    const C s1 = cadd(b, d), d1 = csub(b, d);
+    const C r1 = INV ? cmul_pi(d1) : cmul_mi(d1);
+    a = cadd(s0, s1);
+    c = csub(s0, s1);
+    b = cadd(d0, r1);
+    d = csub(d0, r1);
+}
+
+template <typename C, bool INV> __device__ __forceinline__ void dft8(C *v) {
+    typedef decltype(v[0].x) R;
+    const R h = R(0.70710678118654752440);
+    C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<C, INV>(e0, e1, e2, e3);
+    dft4<C, INV>(o0, o1, o2, o3);
+    // twiddles w8^k, w8 = exp(-+ 2 pi i / 8)
+    const C t1 = INV ? cmk(h * (o1.x - o1.y), h * (o1.x + o1.y)) : cmk(h * (o1.x + o1.y), h * (o1.y - o1.x));
+    const C t2 = INV ? cmul_pi(o2) : cmul_mi(o2);
+    const C t3 = INV ? cmk(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : cmk(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, t1);
+    v[5] = csub(e1, t1);
+    v[2] = cadd(e2, t2);
+    v[6] = csub(e2, t2);
+    v[3] = cadd(e3, t3);
+    v[7] = csub(e3, t3);
+}
+
+template <typename C, int R, bool INV> __device__ __forceinline__ void dftR(C *v) {
+    if constexpr (R == 2) dft2(v[0], v[1]);
+    if constexpr (R == 4) dft4<C, INV>(v[0], v[1], v[2], v[3]);
+    if constexpr (R == 8) dft8<C, INV>(v);
+}
+
+// One radix-R Stockham stage on B columns of length L.
+// Column b, element j lives at buf[j * ld + b].  tw[t] = exp(-2 pi i t / L).
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void stockham_stage(const C *__restrict__ src, C *__restrict__ dst, int L, int Ns,
+                                               int ld, int B, const C *__restrict__ tw) {
+    const int nj = L / R;
+    const int tstep = L / (Ns * R);
+    for (int w = threadIdx.x; w < nj * B; w += blockDim.x) {
+        const int b = w % B;
+        const int j = w / B;
+        const int k = j & (Ns - 1);
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = src[(j + r * nj) * ld + b];
+        if (Ns > 1) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C t = tw[(r * k * tstep) & (L - 1)];
+                if (INV) t.y = -t.y;
+                v[r] = cmul(v[r], t);
+            }
+        }
+        dftR<C, R, INV>(v);
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) dst[(base + r * Ns) * ld + b] = v[r];
+    }
+}
+
+// Full length-L transform of B columns; returns the buffer holding the result.
+// L = 2^p: p/3 radix-8 stages, then one radix-4 (p%3 == 2) or radix-2 (p%3 == 1).
+template <typename C, bool INV>
+__device__ C *fft_columns(C *b0, C *b1, int L, int ld, int B, const C *__restrict__ tw) {
+    const int lg = __ffs(L) - 1;
+    const int n8 = lg / 3, rem = lg - 3 * n8;
+    int Ns = 1;
+    C *src = b0, *dst = b1;
+    for (int st = 0; st < n8 + (rem ? 1 : 0); ++st) {
+        if (st < n8) {
+            stockham_stage<C, 8, INV>(src, dst, L, Ns, ld, B, tw);
+            Ns *= 8;
+        } else if (rem == 2) {
+            stockham_stage<C, 4, INV>(src, dst, L, Ns, ld, B, tw);
+            Ns *= 4;
+        } else {
+            stockham_stage<C, 2, INV>(src, dst, L, Ns, ld, B, tw);
+            Ns *= 2;
+        }
+        __syncthreads();
+        C *t = src;
+        src = dst;
+        dst = t;
+    }
+    return src;
+}
+
+// ---------------------------------------------------------------- FX
+// PB row pairs per CTA; pair pr covers rows y0 = 2*(pr % (Ly/2)) and y0+1 of plane z.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
+    typedef typename VecT<T>::T2 C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2], Kx = p.Kx;
+    const int ld = PB + 1;
+    C *b0 = (C *)smem_raw;
+    C *b1 = b0 + Lx * ld;
+    const int64_t npairs = (int64_t)Lz * (Ly / 2);
+    const int64_t pr0 = (int64_t)blockIdx.x * PB;
+    T *A = (T *)p.gridA;
+    for (int i = threadIdx.x; i < PB * Lx; i += blockDim.x) {
+        const int b = i / Lx, x = i - b * Lx;
+        const int64_t pr = pr0 + b;
+        C v = cmk(T(0), T(0));
+        if (pr < npairs) {
+            const int64_t z = pr / (Ly / 2);
+            const int y0 = 2 * (int)(pr - z * (Ly / 2));
+            const int64_t r0 = (z * Ly + y0) * Lx + x;
+            v = cmk(A[r0], A[r0 + Lx]);
+            A[r0] = T(0);
+            A[r0 + Lx] = T(0);
+        }
+        b0[x * ld + b] = v;
+    }
+    __syncthreads();
+    const C *res = fft_columns<C, false>(b0, b1, Lx, ld, PB, (const C *)p.tw[0]);
+    C *S1 = (C *)p.S1;
+    for (int i = threadIdx.x; i < PB * Kx; i += blockDim.x) {
+        const int b = i / Kx, k = i - b * Kx;
+        const int64_t pr = pr0 + b;
+        if (pr >= npairs) continue;
+        const int64_t z = pr / (Ly / 2);
+        const int y0 = 2 * (int)(pr - z * (Ly / 2));
+        const C Z = res[k * ld + b];
+        const C Zc = cconj(res[((Lx - k) & (Lx - 1)) * ld + b]);
+        const C xa = cscale(cadd(Z, Zc), T(0.5));
+        const C xb = cscale(cmul_mi(csub(Z, Zc)), T(0.5));  // (Z - Zc) / (2i)
+        const int64_t o = (z * Ly + y0) * Kx + k;
+        S1[o] = xa;
+        S1[o + Kx] = xb;
+    }
+}
+
+// ---------------------------------------------------------------- FY
+// CTA: plane z, columns kx0 .. kx0 + B.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
+    typedef typename VecT<T>::T2 C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
+    const int ld = B + 1;
+    C *b0 = (C *)smem_raw;
+    C *b1 = b0 + Ly * ld;
+    const int ntile = Kx / B;
+    const int z = blockIdx.x / ntile;
+    const int kx0 = (blockIdx.x - z * ntile) * B;
+    const C *S1 = (const C *)p.S1 + (int64_t)z * Ly * Kx + kx0;
+    for (int i = threadIdx.x; i < Ly * B; i += blockDim.x) {
+        const int y = i / B, b = i - y * B;
+        b0[y * ld + b] = S1[(int64_t)y * Kx + b];
+    }
+    __syncthreads();
+    const C *res = fft_columns<C, false>(b0, b1, Ly, ld, B, (const C *)p.tw[1]);
+    C *S2 = (C *)p.S2 + (int64_t)z * ny * Kx + kx0;
+    for (int i = threadIdx.x; i < ny * B; i += blockDim.x) {
+        const int kp = i / B, b = i - kp * B;
+        C v = cmk(T(0), T(0));
+        if (kp < ny / 2)
+            v = res[kp * ld + b];
+        else if (kp > ny / 2)
+            v = res[(Ly - ny + kp) * ld + b];
+        S2[(int64_t)kp * Kx + b] = v;
+    }
+}
+
+// ---------------------------------------------------------------- FZ * D * IZ
+// CTA: row ky', columns kx0 .. kx0 + B; the pencil along z stays in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
+    typedef typename VecT<T>::T2 C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Lz = p.L[2], Kx = p.Kx, ny = p.n[1], nz = p.n[2];
+    const int ld = B + 1;
+    C *b0 = (C *)smem_raw;
+    C *b1 = b0 + Lz * ld;
+    const int ntile = Kx / B;
+    const int kp = blockIdx.x / ntile;
+    const int kx0 = (blockIdx.x - kp * ntile) * B;
+    C *S2 = (C *)p.S2 + (int64_t)kp * Kx + kx0;
+    const int64_t zs = (int64_t)ny * Kx;
+    if (kp == ny / 2) {  // Nyquist row in y: dropped
+        for (int i = threadIdx.x; i < Lz * B; i += blockDim.x) {
+            const int z = i / B, b = i - z * B;
+            S2[z * zs + b] = cmk(T(0), T(0));
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < Lz * B; i += blockDim.x) {
+        const int z = i / B, b = i - z * B;
+        b0[z * ld + b] = S2[z * zs + b];
+    }
+    __syncthreads();
+    C *res = fft_columns<C, false>(b0, b1, Lz, ld, B, (const C *)p.tw[2]);
+    C *oth = (res == b0) ? b1 : b0;
+    const int aky = kp < ny / 2 ? kp : ny - kp;
+    const T *D = (const T *)p.Dtab;
+    for (int i = threadIdx.x; i < Lz * B; i += blockDim.x) {
+        const int kz = i / B, b = i - kz * B;
+        const int kzs = kz < Lz / 2 ? kz : kz - Lz;
+        const int akz = kzs < 0 ? -kzs : kzs;
+        C v = cmk(T(0), T(0));
+        if (akz < nz / 2) {
+            const T d = D[((int64_t)akz * (ny / 2) + aky) * Kx + kx0 + b];
+            v = cscale(res[kz * ld + b], d);
+        }
+        res[kz * ld + b] = v;
+    }
+    __syncthreads();
+    const C *out = fft_columns<C, true>(res, oth, Lz, ld, B, (const C *)p.tw[2]);
+    for (int i = threadIdx.x; i < Lz * B; i += blockDim.x) {
+        const int z = i / B, b = i - z * B;
+        S2[z * zs + b] = out[z * ld + b];
+    }
+}
+
+// ---------------------------------------------------------------- IY
+template <typename T>
+__global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
+    typedef typename VecT<T>::T2 C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
+    const int ld = B + 1;
+    C *b0 = (C *)smem_raw;
+    C *b1 = b0 + Ly * ld;
+    const int ntile = Kx / B;
+    const int z = blockIdx.x / ntile;
+    const int kx0 = (blockIdx.x - z * ntile) * B;
+    const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx + kx0;
+    for (int i = threadIdx.x; i < Ly * B; i += blockDim.x) {
+        const int y = i / B, b = i - y * B;
+        // position y holds mode y (y < ny/2), or mode y - Ly (y > Ly - ny/2), else zero
+        C v = cmk(T(0), T(0));
+        if (y < ny / 2)
+            v = S2[(int64_t)y * Kx + b];
+        else if (y > Ly - ny / 2)
+            v = S2[(int64_t)(y - Ly + ny) * Kx + b];
+        b0[y * ld + b] = v;
+    }
+    __syncthreads();
+    const C *res = fft_columns<C, true>(b0, b1, Ly, ld, B, (const C *)p.tw[1]);
+    C *S1 = (C *)p.S1 + (int64_t)z * Ly * Kx + kx0;
+    for (int i = threadIdx.x; i < Ly * B; i += blockDim.x) {
+        const int y = i / B, b = i - y * B;
+        S1[(int64_t)y * Kx + b] = res[y * ld + b];
+    }
+}
+
+// ---------------------------------------------------------------- IX
+template <typename T>
+__global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
+    typedef typename VecT<T>::T2 C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2], Kx = p.Kx;
+    const int ld = PB + 1;
+    C *b0 = (C *)smem_raw;
+    C *b1 = b0 + Lx * ld;
+    const int64_t npairs = (int64_t)Lz * (Ly / 2);
+    const int64_t pr0 = (int64_t)blockIdx.x * PB;
+    for (int i = threadIdx.x; i < PB * Lx; i += blockDim.x) b0[(i % Lx) * ld + i / Lx] = cmk(T(0), T(0));
+    __syncthreads();
+    const C *S1 = (const C *)p.S1;
+    for (int i = threadIdx.x; i < PB * Kx; i += blockDim.x) {
+        const int b = i / Kx, k = i - b * Kx;
+        const int64_t pr = pr0 + b;
+        if (pr >= npairs) continue;
+        const int64_t z = pr / (Ly / 2);
+        const int y0 = 2 * (int)(pr - z * (Ly / 2));
+        const int64_t o = (z * Ly + y0) * Kx + k;
+        const C xa = S1[o], xb = S1[o + Kx];
+        if (k == 0) {
+            b0[b] = cmk(xa.x, xb.x);
+        } else {
+            b0[k * ld + b] = cmk(xa.x - xb.y, xa.y + xb.x);             // xa + i xb
+            b0[(Lx - k) * ld + b] = cmk(xa.x + xb.y, xb.x - xa.y);      // conj(xa) + i conj(xb)
+        }
+    }
+    __syncthreads();
+    const C *res = fft_columns<C, true>(b0, b1, Lx, ld, PB, (const C *)p.tw[0]);
+    T *G = (T *)p.gridB;
+    for (int i = threadIdx.x; i < PB * Lx; i += blockDim.x) {
+        const int b = i / Lx, x = i - b * Lx;
+        const int64_t pr = pr0 + b;
+        if (pr >= npairs) continue;
+        const int64_t z = pr / (Ly / 2);
+        const int y0 = 2 * (int)(pr - z * (Ly / 2));
+        const int64_t r0 = (z * Ly + y0) * Lx + x;
+        const C v = res[x * ld + b];
+        G[r0] = v.x;
+        G[r0 + Lx] = v.y;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+// Batch sizes: keep two buffers of (L x (B+1)) complex within ~64 KB.
+static int row_batch(int L, size_t celem) {
+    int pb = 16;
+    while (pb > 1 && 2 * (size_t)L * (pb + 1) * celem > 64 * 1024) pb >>= 1;
+    return pb;
+}
+static int col_batch(int L, int Kx, size_t celem) {
+    int b = 16;
+    if (b > Kx) b = Kx;
+    while (b > 1 && 2 * (size_t)L * (b + 1) * celem > 64 * 1024) b >>= 1;
+    return b;
+}
+
+template <typename K> static cudaError_t prep(K kern, size_t sm) {
+    if (sm > 48 * 1024) return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    return cudaSuccess;
+}
+
+template <typename T> static cudaError_t fx_t(const DevPlan &p, cudaStream_t s) {
+    const size_t ce = 2 * sizeof(T);
+    const int PB = row_batch(p.L[0], ce);
+    const size_t sm = 2 * (size_t)p.L[0] * (PB + 1) * ce;
+    cudaError_t e = prep(k_fx<T>, sm);
+    if (e != cudaSuccess) return e;
+    const int64_t npairs = (int64_t)p.L[2] * (p.L[1] / 2);
+    k_fx<T><<<(int)((npairs + PB - 1) / PB), 256, sm, s>>>(p, PB);
+    return cudaGetLastError();
+}
+template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) {
+    const size_t ce = 2 * sizeof(T);
+    const int PB = row_batch(p.L[0], ce);
+    const size_t sm = 2 * (size_t)p.L[0] * (PB + 1) * ce;
+    cudaError_t e = prep(k_ix<T>, sm);
+    if (e != cudaSuccess) return e;
+    const int64_t npairs = (int64_t)p.L[2] * (p.L[1] / 2);
+    k_ix<T><<<(int)((npairs + PB - 1) / PB), 256, sm, s>>>(p, PB);
+    return cudaGetLastError();
+}
+template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) {
+    const size_t ce = 2 * sizeof(T);
+    const int B = col_batch(p.L[1], p.Kx, ce);
+    const size_t sm = 2 * (size_t)p.L[1] * (B + 1) * ce;
+    cudaError_t e = prep(k_fy<T>, sm);
+    if (e != cudaSuccess) return e;
+    k_fy<T><<<p.L[2] * (p.Kx / B), 256, sm, s>>>(p, B);
+    return cudaGetLastError();
+}
+template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) {
+    const size_t ce = 2 * sizeof(T);
+    const int B = col_batch(p.L[1], p.Kx, ce);
+    const size_t sm = 2 * (size_t)p.L[1] * (B + 1) * ce;
+    cudaError_t e = prep(k_iy<T>, sm);
+    if (e != cudaSuccess) return e;
+    k_iy<T><<<p.L[2] * (p.Kx / B), 256, sm, s>>>(p, B);
+    return cudaGetLastError();
+}
+template <typename T> static cudaError_t fz_t(const DevPlan &p, cudaStream_t s) {
+    const size_t ce = 2 * sizeof(T);
+    const int B = col_batch(p.L[2], p.Kx, ce);
+    const size_t sm = 2 * (size_t)p.L[2] * (B + 1) * ce;
+    cudaError_t e = prep(k_fz<T>, sm);
+    if (e != cudaSuccess) return e;
+    k_fz<T><<<p.n[1] * (p.Kx / B), 256, sm, s>>>(p, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fft_forward_x(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? fx_t<double>(p, s) : fx_t<float>(p, s); }
+cudaError_t launch_fft_forward_y(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? fy_t<double>(p, s) : fy_t<float>(p, s); }
+cudaError_t launch_fft_z_multiply(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? fz_t<double>(p, s) : fz_t<float>(p, s); }
+cudaError_t launch_fft_inverse_y(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? iy_t<double>(p, s) : iy_t<float>(p, s); }
+cudaError_t launch_fft_inverse_x(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? ix_t<double>(p, s) : ix_t<float>(p, s); }
+
+}  // namespace slp

@@ -1,0 +1,99 @@
+// Internal declarations shared by the host plan code and the CUDA kernels.
+// Not part of the public ABI (see include/slp.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace slp {
+
+// Work item of the tiled spread (type-1 gridding) and gather (type-2
+// interpolation) kernels: a tile of TS^3 grid cells with base cell c0, and a
+// contiguous range [begin, end) of sources (spread) or targets (gather)
+// whose cells lie inside the tile, in the plan's sorted order.
+struct TileItem {
+    int c0x, c0y, c0z;
+    int begin, end;
+    int pad0, pad1, pad2;
+};
+
+// Work item of the near-field kernel: up to 32 sorted targets
+// [tbegin, tbegin + tcount) and a slice [rbegin, rend) of the range list,
+// each range a contiguous run of sorted sources.
+struct NearItem {
+    int tbegin, tcount;
+    int rbegin, rend;
+};
+
+// Device-side view of a plan.  Plain data, passed by value to launchers.
+struct DevPlan {
+    int prec;           // 32 or 64
+    int q;              // points per triangle
+    int64_t N, Q, M, NV;
+    int L[3];           // oversampled grid (x, y, z)
+    int n[3];           // modes per axis, L = 2 n
+    int Kx;             // stored x frequencies: n_x / 2
+    int m;              // window half-width
+    int TS, TE;         // tile cells per axis; tile extent with halo TS + 2m - 1
+    double h[3];        // physical grid spacing P_q / L_q
+    double beta;        // Kaiser-Bessel shape b * m, b = pi (2 - 1/alpha)
+    double inv_sinh_beta;
+    double eps2;        // squared near radius (physical)
+    double inv_s_sqrt2; // 1 / (sigma_g sqrt 2)
+    int kernel_mode;    // SLP_KERNEL_RADIAL or SLP_KERNEL_SEPARABLE
+    int deterministic;
+
+    // sources, sorted (k_sorted); grid coordinates: frac (x,y,z) and packed cell
+    const void *src_grid;   // T4 [Q]
+    const int *src_perm;    // [Q] sorted -> user index k = j*q + s
+    const void *src_w;      // T [Q] w_s |S_j| in sorted order
+    const void *tri_nrm;    // T4 [M] outward unit normals (user triangle order)
+    const int4 *tri_vtx;    // [M] vertex ids
+    const void *lam;        // T [q*3] barycentric points of the rule
+    // targets, sorted
+    const void *tgt_grid;   // T4 [N]
+    const int *tgt_perm;    // [N] sorted -> user vertex index
+
+    // scratch (written during evaluation)
+    void *qbuf;    // T [Q] weighted charges, sorted order
+    void *gridA;   // T [Lz][Ly][Lx] spread grid (kept zero between evaluations)
+    void *gridB;   // T [Lz][Ly][Lx] interpolation grid
+    void *S1;      // T2 [Lz][Ly][Kx]
+    void *S2;      // T2 [Lz][n_y][Kx]
+    void *phi_near; // T [N] near-field partials (deterministic mode), sorted order
+    const void *Dtab;   // T [n_z/2][n_y/2][Kx] kernel multiplier by |l_z|, |l_y|, l_x
+    const void *tw[3];  // T2 [L_q] forward twiddles exp(-2 pi i t / L_q)
+
+    const TileItem *spread_items; int n_spread;
+    const TileItem *gather_items; int n_gather;
+    const NearItem *near_items;   int n_near;
+    const int2 *near_ranges;
+    int near_chunk;               // deterministic mode: item slot per target block
+
+    // separable kernel: K_n(d) = A prod_q f_q(d_q / L_q), f_q(t) = sum_l hq[l] cos(2 pi l t)
+    const void *sep_h[3]; int sep_nh[3];  // hq[0..nh-1], term l uses weight (l==0 ? 1 : 2) * hq[l]
+    double sep_A;
+
+    // precomputed near-field operator (NODAL_MAG): CSR over sorted targets
+    const int64_t *nm_rowptr;  // [N + 1]
+    const int *nm_col;         // [nnz] vertex ids
+    const void *nm_val;        // T4 [nnz] (wx, wy, wz, unused)
+    int64_t nm_nnz;
+
+    int *err;  // device status word (sticky)
+};
+
+// Kernel launchers (return the launch error, if any).
+cudaError_t launch_charges(const DevPlan &p, int kind, const void *d_in, cudaStream_t s);
+cudaError_t launch_spread(const DevPlan &p, cudaStream_t s);
+cudaError_t launch_fft_forward_x(const DevPlan &p, cudaStream_t s);
+cudaError_t launch_fft_forward_y(const DevPlan &p, cudaStream_t s);
+cudaError_t launch_fft_z_multiply(const DevPlan &p, cudaStream_t s);
+cudaError_t launch_fft_inverse_y(const DevPlan &p, cudaStream_t s);
+cudaError_t launch_fft_inverse_x(const DevPlan &p, cudaStream_t s);
+cudaError_t launch_gather(const DevPlan &p, void *d_phi, cudaStream_t s);
+cudaError_t launch_near(const DevPlan &p, void *d_phi, cudaStream_t s);
+cudaError_t launch_near_reduce(const DevPlan &p, const int *blk_first, int nblk, void *d_phi, cudaStream_t s);
+cudaError_t launch_zero(void *ptr, size_t bytes, cudaStream_t s);
+
+}  // namespace slp

@@ -1,0 +1,1273 @@
+// Host side of the library: the C ABI, plan construction (the setup phase of
+// the paper's Alg. 1) and the launch sequence of one evaluation (its
+// computation phase).
+//
+// Plan construction, all in FP64 on the host:
+//   1. validate the mesh (indices, degenerate triangles, closed and
+//      consistently outward oriented surface);
+//   2. quadrature sources y_{j,s} = sum_a lambda_{s,a} v_{j,a}, weights
+//      w_s |S_j|, outward normals (Sec. 2.2 discretisation, quadrature form of
+//      Sec. 3);
+//   3. parameters: window half-width m from the NFFT error bound C(2, m)
+//      (Sec. 3.2, Eq. (error_bound_nufft)), the torus (centre, period), the
+//      smooth kernel and the near-field radius (see choose_radial);
+//   4. grid coordinates, tile sort of sources and targets, work lists of the
+//      spread, gather and near-field kernels;
+//   5. the kernel multiplier table D (Sec. 3, Eq. (deconv) and Sec. 5, Eq.
+//      (BEM_NFFT_compact2): kernel Fourier coefficients divided by the squared
+//      window coefficients of Eq. (cFB)) and the FFT twiddles;
+//   6. device allocation and upload.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/slp.h"
+#include "../../include/slp_debug.h"
+#include "slp_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+slp_status fail(slp_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+const double PI = 3.14159265358979323846;
+
+// ---------------------------------------------------------------- rules
+// Barycentric points and weights (see slp.h for the point order).
+bool quad_rule(int q, std::vector<double> &lam, std::vector<double> &w) {
+    lam.assign(3 * q, 0.0);
+    w.assign(q, 0.0);
+    if (q == 1) {
+        lam = {1.0 / 3, 1.0 / 3, 1.0 / 3};
+        w = {1.0};
+        return true;
+    }
+    if (q == 3) {
+        for (int s = 0; s < 3; ++s) {
+            for (int a = 0; a < 3; ++a) lam[3 * s + a] = (a == s) ? 2.0 / 3.0 : 1.0 / 6.0;
+            w[s] = 1.0 / 3.0;
+        }
+        return true;
+    }
+    if (q == 7) {
+        const double r = std::sqrt(15.0);
+        lam[0] = lam[1] = lam[2] = 1.0 / 3.0;
+        w[0] = 9.0 / 40.0;
+        const double av[2] = {(6.0 - r) / 21.0, (6.0 + r) / 21.0};
+        const double wv[2] = {(155.0 - r) / 1200.0, (155.0 + r) / 1200.0};
+        int s = 1;
+        for (int g = 0; g < 2; ++g) {
+            const double a = av[g], o = 1.0 - 2.0 * a;
+            const double pts[3][3] = {{a, a, o}, {a, o, a}, {o, a, a}};
+            for (int p = 0; p < 3; ++p, ++s) {
+                for (int c = 0; c < 3; ++c) lam[3 * s + c] = pts[p][c];
+                w[s] = wv[g];
+            }
+        }
+        return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------- window
+const double KB_B = PI * (2.0 - 1.0 / 2.0);  // b = pi (2 - 1/alpha), alpha = 2
+
+double kb_window_host(int m, double d) {
+    const double beta = KB_B * m;
+    const double t = d / m;
+    const double s2 = 1.0 - t * t;
+    if (s2 < 0.0) return 0.0;
+    const double s = std::sqrt(s2);
+    const double r = (beta * s > 1e-8) ? std::sinh(beta * s) / s : beta;
+    return r / std::sinh(beta);
+}
+
+// Continuous Fourier transform of the normalised window at the frequency of
+// index l on an L-point grid: (pi m / sinh beta) I0(m sqrt(b^2 - (2 pi l / L)^2))
+// (Eq. (cFB) times L, times the normalisation pi m / sinh beta).
+double kb_hat_host(int m, int L, double l) {
+    const double beta = KB_B * m;
+    const double om = 2.0 * PI * l / L;
+    const double a2 = KB_B * KB_B - om * om;
+    if (a2 <= 0.0) return 0.0;
+    return PI * m / std::sinh(beta) * std::cyl_bessel_i(0.0, m * std::sqrt(a2));
+}
+
+// NFFT error bound C(alpha, m) of Eq. (error_bound_nufft), alpha = 2.
+double nfft_bound(int m) {
+    const double a = 2.0;
+    return 4.0 * PI * (std::sqrt((double)m) + m) * std::pow(1.0 - 1.0 / a, 0.25) *
+           std::exp(-2.0 * PI * m * std::sqrt(1.0 - 1.0 / a));
+}
+
+// inverse of erfc on (0, 1] by bisection (monotone), FP64
+double erfc_inv(double y) {
+    double lo = 0.0, hi = 30.0;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (std::erfc(mid) > y)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// Morton code of a cell inside its tile (3 bits per axis level)
+uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+    uint32_t c = 0;
+    for (int b = 0; b < 10; ++b) {
+        c |= ((x >> b) & 1u) << (3 * b);
+        c |= ((y >> b) & 1u) << (3 * b + 1);
+        c |= ((z >> b) & 1u) << (3 * b + 2);
+    }
+    return c;
+}
+
+// error-budget factors of the RADIAL split (relative to the tolerance):
+// band-limit tail of the Gaussian and the erfc tail left outside eps.
+const double KFAC = 30.0;
+const double NFAC = 2.0;
+
+}  // namespace
+
+// ======================================================================= plan
+struct slp_plan_s {
+    // configuration
+    slp_plan_opts opts;
+    int q = 0;
+    int prec = 32;
+    double tol = 0;
+    int64_t N = 0, M = 0, Q = 0;
+    int device = 0;
+
+    // geometry (host, FP64)
+    std::vector<double> V;       // [N][3]
+    std::vector<int32_t> T;      // [M][3]
+    std::vector<double> lam, wq; // rule
+    std::vector<double> y;       // [Q][3] user order
+    std::vector<double> wk;      // [Q]
+    std::vector<double> nrm;     // [M][3]
+
+    // parameters
+    int L[3] = {0, 0, 0}, n[3] = {0, 0, 0}, m = 0, TS = 8, TE = 0;
+    int kernel_mode = SLP_KERNEL_RADIAL, near_mode = SLP_NEAR_ON_THE_FLY;
+    int grid_raised = 0;
+    double ctr[3] = {0, 0, 0}, P[3] = {0, 0, 0}, D[3] = {0, 0, 0};
+    double diam = 0, sigma_g = 0, R = 0, eps = 0, c_band = 0;
+    double sep_A = 0;
+    std::vector<double> sep_h[3];
+
+    // sorted data (host)
+    std::vector<int32_t> src_perm, tgt_perm;
+    std::vector<double> src_grid, tgt_grid;  // [.][4]
+    std::vector<slp::TileItem> spread_items, gather_items;
+    std::vector<slp::NearItem> near_items;
+    std::vector<int2> near_ranges;
+    std::vector<int> near_blk_first;  // CSR of items per target block
+    std::vector<double> Dtab;
+    int64_t near_pairs = 0;
+
+    // device
+    slp::DevPlan dp;
+    std::vector<void *> allocs;
+    int64_t bytes_device = 0;
+    void *d_stage_in = nullptr, *d_stage_phi = nullptr;
+    int *d_blk_first = nullptr;
+    int launches_per_eval = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- mesh
+slp_status validate_mesh(slp_plan_s &p) {
+    const int64_t N = p.N, M = p.M;
+    for (int64_t j = 0; j < M; ++j) {
+        const int32_t *t = &p.T[3 * j];
+        for (int a = 0; a < 3; ++a)
+            if (t[a] < 0 || t[a] >= N) return fail(SLP_ERR_MESH, "triangle %lld has vertex index %d out of range", (long long)j, t[a]);
+        if (t[0] == t[1] || t[1] == t[2] || t[0] == t[2])
+            return fail(SLP_ERR_MESH, "triangle %lld repeats a vertex", (long long)j);
+    }
+    if (!p.opts.check_mesh) return SLP_OK;
+    // closed and consistently oriented: every directed edge once, and its reverse once
+    std::vector<uint64_t> e, r;
+    e.reserve(3 * M);
+    r.reserve(3 * M);
+    for (int64_t j = 0; j < M; ++j) {
+        for (int a = 0; a < 3; ++a) {
+            const uint64_t u = (uint32_t)p.T[3 * j + a], v = (uint32_t)p.T[3 * j + (a + 1) % 3];
+            e.push_back((u << 32) | v);
+            r.push_back((v << 32) | u);
+        }
+    }
+    std::sort(e.begin(), e.end());
+    std::sort(r.begin(), r.end());
+    if (std::adjacent_find(e.begin(), e.end()) != e.end())
+        return fail(SLP_ERR_MESH, "a directed edge is used twice: the surface is non-manifold or inconsistently oriented");
+    if (e != r) return fail(SLP_ERR_MESH, "the surface is not closed (an edge has no opposite half-edge)");
+    // outward orientation: signed volume > 0
+    double vol = 0.0;
+    for (int64_t j = 0; j < M; ++j) {
+        const double *a = &p.V[3 * p.T[3 * j]], *b = &p.V[3 * p.T[3 * j + 1]], *c = &p.V[3 * p.T[3 * j + 2]];
+        vol += a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+    }
+    if (!(vol > 0.0)) return fail(SLP_ERR_MESH, "the enclosed signed volume is not positive: normals point inward");
+    return SLP_OK;
+}
+
+slp_status build_sources(slp_plan_s &p) {
+    if (!quad_rule(p.q, p.lam, p.wq)) return fail(SLP_ERR_INVALID_ARG, "unsupported quadrature %d (use 1, 3 or 7)", p.q);
+    p.Q = p.M * p.q;
+    p.y.assign(3 * p.Q, 0.0);
+    p.wk.assign(p.Q, 0.0);
+    p.nrm.assign(3 * p.M, 0.0);
+    for (int64_t j = 0; j < p.M; ++j) {
+        const double *v0 = &p.V[3 * p.T[3 * j]], *v1 = &p.V[3 * p.T[3 * j + 1]], *v2 = &p.V[3 * p.T[3 * j + 2]];
+        const double e1[3] = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]};
+        const double e2[3] = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
+        const double c[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        const double a2 = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        double scale = 0;
+        for (int d = 0; d < 3; ++d) scale = std::max(scale, std::fabs(e1[d]) + std::fabs(e2[d]));
+        if (!(a2 > 1e-14 * scale * scale)) return fail(SLP_ERR_MESH, "triangle %lld is degenerate (zero area)", (long long)j);
+        for (int d = 0; d < 3; ++d) p.nrm[3 * j + d] = c[d] / a2;
+        for (int s = 0; s < p.q; ++s) {
+            const int64_t k = j * p.q + s;
+            for (int d = 0; d < 3; ++d)
+                p.y[3 * k + d] = p.lam[3 * s] * v0[d] + p.lam[3 * s + 1] * v1[d] + p.lam[3 * s + 2] * v2[d];
+            p.wk[k] = p.wq[s] * 0.5 * a2;
+        }
+    }
+    return SLP_OK;
+}
+
+// ---------------------------------------------------------------- parameters
+// RADIAL smooth kernel (the reading of Sec. 3.3 this library uses):
+//   N_s = (N 1_{|x| <= R}) * g_s, g_s an isotropic Gaussian of width s.
+// Its Fourier transform is closed form, Khat(k) = 2 sin^2(k R / 2) / k^2 exp(-s^2 k^2 / 2),
+// and for |x| <= R - c s, N_s(x) = erf(|x| / (s sqrt 2)) / (4 pi |x|), so the near-field
+// kernel N - N_s = erfc(r / (s sqrt 2)) / (4 pi r) decays like a Gaussian.
+// Conditions (c = sqrt(2 ln(1/tau_k))):
+//   band limit  s >= c P_q / (pi n_q)           (Gaussian below tau_k at |l_q| = n_q/2)
+//   isolation   P_q >= D_q + R + c s,  R = diam + c s  (no periodic image overlaps)
+//   near radius erfc(eps / (s sqrt 2)) = tau_nf
+// which give s = max_q c (D_q + diam) / (pi n_q - 2 c^2), feasible iff pi n_q > 2 c^2.
+bool radial_feasible(const slp_plan_s &p, const int n[3], double c) {
+    for (int d = 0; d < 3; ++d)
+        if (!(PI * n[d] > 2.0 * c * c * 1.05)) return false;
+    return true;
+}
+
+void radial_params(slp_plan_s &p, double c) {
+    double s = 0.0;
+    for (int d = 0; d < 3; ++d) s = std::max(s, c * (p.D[d] + p.diam) / (PI * p.n[d] - 2.0 * c * c));
+    p.sigma_g = s;
+    for (int d = 0; d < 3; ++d) p.P[d] = p.D[d] + p.diam + 2.0 * c * s;
+    p.R = p.diam + c * s;
+    const double tnf = std::min(0.5, p.tol * NFAC);
+    p.eps = s * std::sqrt(2.0) * erfc_inv(tnf);
+}
+
+slp_status choose_parameters(slp_plan_s &p) {
+    // bounding box and enclosing-ball diameter of targets (sources are convex
+    // combinations of targets, so they lie inside both)
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = 0; i < p.N; ++i)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], p.V[3 * i + d]);
+            hi[d] = std::max(hi[d], p.V[3 * i + d]);
+        }
+    double rad2 = 0;
+    for (int d = 0; d < 3; ++d) {
+        p.ctr[d] = 0.5 * (lo[d] + hi[d]);
+        p.D[d] = hi[d] - lo[d];
+    }
+    for (int64_t i = 0; i < p.N; ++i) {
+        double r2 = 0;
+        for (int d = 0; d < 3; ++d) r2 += (p.V[3 * i + d] - p.ctr[d]) * (p.V[3 * i + d] - p.ctr[d]);
+        rad2 = std::max(rad2, r2);
+    }
+    p.diam = 2.0 * std::sqrt(rad2) * (1.0 + 1e-12);
+    if (!(p.diam > 0)) return fail(SLP_ERR_MESH, "mesh has zero extent");
+
+    // window half-width from the NFFT bound
+    int m = p.opts.m;
+    if (m == 0) {
+        m = 2;
+        while (nfft_bound(m) > p.tol / 4.0 && m < 8) ++m;
+        if (p.prec == 32) m = std::min(m, 6);
+    }
+    if (m < 2 || m > 8) return fail(SLP_ERR_INVALID_ARG, "window half-width m = %d outside [2, 8]", m);
+    p.m = m;
+
+    // requested grid
+    int L[3];
+    for (int d = 0; d < 3; ++d) {
+        L[d] = p.opts.grid[d];
+        if (L[d] == 0) L[d] = -1;
+        if (L[d] > 0 && (!is_pow2(L[d]) || L[d] < 8 || L[d] > 1024))
+            return fail(SLP_ERR_INVALID_ARG, "grid[%d] = %d must be a power of two in [8, 1024]", d, L[d]);
+    }
+    const double tk = std::min(0.1, p.tol * KFAC);
+    const double c = std::sqrt(2.0 * std::log(1.0 / tk));
+    p.c_band = c;
+    if (L[0] < 0 || L[1] < 0 || L[2] < 0) {
+        // automatic: equal spacing at about (Q + N)^(1/2) cells across the body
+        const double target_cells = std::max(16.0, 2.0 * std::sqrt((double)(p.Q + p.N)));
+        const double dmax = std::max(p.D[0], std::max(p.D[1], p.D[2]));
+        for (int d = 0; d < 3; ++d) {
+            if (L[d] > 0) continue;
+            // cells of the oversampled grid across the period ~ 2.3x the body
+            double want = target_cells * (p.D[d] + p.diam) / (dmax + p.diam) * 1.0;
+            int v = 16;
+            while (v < want && v < 1024) v <<= 1;
+            L[d] = v;
+        }
+    }
+    int nreq[3] = {L[0] / 2, L[1] / 2, L[2] / 2};
+
+    int mode = p.opts.kernel_mode;
+    if (mode == SLP_KERNEL_AUTO) {
+        if (radial_feasible(p, nreq, c))
+            mode = SLP_KERNEL_RADIAL;
+        else if ((double)p.Q * (double)p.N <= (double)(1 << 24))
+            mode = SLP_KERNEL_SEPARABLE;
+        else if (p.opts.allow_grid_raise)
+            mode = -SLP_KERNEL_RADIAL;  // radial after raising the grid
+        else
+            return fail(SLP_ERR_TOLERANCE_INFEASIBLE,
+                        "grid %dx%dx%d cannot resolve the smooth kernel at tolerance %g (needs pi n > %.1f per axis)",
+                        L[0], L[1], L[2], p.tol, 2 * c * c * 1.05);
+    }
+    if (mode == SLP_KERNEL_RADIAL && !radial_feasible(p, nreq, c)) {
+        if (!p.opts.allow_grid_raise)
+            return fail(SLP_ERR_TOLERANCE_INFEASIBLE,
+                        "grid %dx%dx%d cannot resolve the smooth kernel at tolerance %g (needs pi n > %.1f per axis)",
+                        L[0], L[1], L[2], p.tol, 2 * c * c * 1.05);
+        mode = -SLP_KERNEL_RADIAL;
+    }
+    if (mode == -SLP_KERNEL_RADIAL) {
+        // raise: take the best-resolved feasible axis' smoothing width, and give
+        // every axis the grid that resolves it (nearest power of two, never below
+        // the request and at least the feasibility limit)
+        double sbest = 1e300;
+        for (int d = 0; d < 3; ++d)
+            if (PI * nreq[d] > 2.0 * c * c * 1.05) sbest = std::min(sbest, c * (p.D[d] + p.diam) / (PI * nreq[d] - 2.0 * c * c));
+        int nmin = 8;
+        while (!(PI * nmin > 2.0 * c * c * 1.05)) nmin <<= 1;
+        for (int d = 0; d < 3; ++d) {
+            int nn = nreq[d];
+            if (sbest < 1e299) {
+                const double need = c * (p.D[d] + p.diam + 2 * c * sbest) / (PI * sbest);
+                int v = 4;
+                while (v < need) v <<= 1;
+                if (v / 2 >= 4 && need / (v / 2) < (double)v / need) v /= 2;  // nearest in log scale
+                nn = std::max(nn, v);
+            }
+            nn = std::max(nn, nmin);
+            if (nn > 512) return fail(SLP_ERR_TOLERANCE_INFEASIBLE, "raised grid exceeds 1024 cells per axis");
+            if (nn != nreq[d]) p.grid_raised = 1;
+            nreq[d] = nn;
+        }
+        mode = SLP_KERNEL_RADIAL;
+    }
+    for (int d = 0; d < 3; ++d) {
+        p.n[d] = nreq[d];
+        p.L[d] = 2 * nreq[d];
+    }
+    p.kernel_mode = mode;
+
+    if (mode == SLP_KERNEL_RADIAL) {
+        if (!radial_feasible(p, p.n, c))
+            return fail(SLP_ERR_TOLERANCE_INFEASIBLE, "grid %dx%dx%d cannot resolve the smooth kernel at tolerance %g",
+                        p.L[0], p.L[1], p.L[2], p.tol);
+        radial_params(p, c);
+    } else if (mode == SLP_KERNEL_SEPARABLE) {
+        // every pair is near; the far kernel is any band-limited periodic
+        // function that the near kernel can subtract exactly
+        const double dmax = std::max(p.D[0], std::max(p.D[1], p.D[2]));
+        for (int d = 0; d < 3; ++d) {
+            p.P[d] = 1.5 * std::max(p.D[d], 0.25 * dmax) + 1e-9 * dmax;
+            const int nh = p.n[d] / 2;  // modes 0 .. n/2 - 1 (Nyquist dropped)
+            p.sep_h[d].assign(nh, 0.0);
+            for (int l = 0; l < nh; ++l) {
+                const double t = (double)l / (0.5 * p.n[d]);
+                p.sep_h[d][l] = std::exp(-2.0 * t * t);
+            }
+        }
+        // scale: K_n(0) = 1 / (4 pi diam / 2)
+        double k0 = 1.0;
+        for (int d = 0; d < 3; ++d) {
+            double f = p.sep_h[d][0];
+            for (size_t l = 1; l < p.sep_h[d].size(); ++l) f += 2.0 * p.sep_h[d][l];
+            k0 *= f;
+        }
+        p.sep_A = 1.0 / (4.0 * PI * 0.5 * p.diam) / k0;
+        p.eps = INFINITY;
+        p.sigma_g = 0;
+        p.R = 0;
+    } else {
+        return fail(SLP_ERR_INVALID_ARG, "unknown kernel_mode %d", p.opts.kernel_mode);
+    }
+    // grid spacing must put the whole body strictly inside the period
+    for (int d = 0; d < 3; ++d)
+        if (!(p.P[d] > p.D[d])) return fail(SLP_ERR_INVALID_ARG, "period does not contain the mesh");
+
+    // tile size: keep the halo tile within 96 KB of shared memory
+    const size_t esz = p.prec == 64 ? 8 : 4;
+    p.TS = 8;
+    while (p.TS > 2 && std::pow((double)(p.TS + 2 * p.m - 1), 3) * esz > 96 * 1024) p.TS /= 2;
+    p.TE = p.TS + 2 * p.m - 1;
+    return SLP_OK;
+}
+
+// ---------------------------------------------------------------- sorting / items
+void grid_coords(const slp_plan_s &p, const double *x, double *g, int &cx, int &cy, int &cz) {
+    int c[3];
+    for (int d = 0; d < 3; ++d) {
+        const double u = (x[d] - p.ctr[d]) / p.P[d] * p.L[d] + 0.5 * p.L[d];
+        double f = std::floor(u);
+        int ci = (int)f;
+        double fr = u - f;
+        if (fr >= 1.0) {  // rounding guard
+            fr = 0.0;
+            ci += 1;
+        }
+        ci = ((ci % p.L[d]) + p.L[d]) % p.L[d];
+        c[d] = ci;
+        g[d] = fr;
+    }
+    cx = c[0];
+    cy = c[1];
+    cz = c[2];
+    const uint32_t packed = (uint32_t)cx | ((uint32_t)cy << 10) | ((uint32_t)cz << 20);
+    g[3] = (double)packed;
+}
+
+// sort points by (tile, Morton order inside the tile); fills perm and grid[.][4]
+void sort_points(const slp_plan_s &p, const double *pts, int64_t n, std::vector<int32_t> &perm,
+                 std::vector<double> &grid, std::vector<uint64_t> &keys_sorted) {
+    std::vector<double> g(4 * n);
+    std::vector<uint64_t> key(n);
+    const int ntx = (p.L[0] + p.TS - 1) / p.TS, nty = (p.L[1] + p.TS - 1) / p.TS;
+    for (int64_t i = 0; i < n; ++i) {
+        int cx, cy, cz;
+        grid_coords(p, pts + 3 * i, &g[4 * i], cx, cy, cz);
+        const uint64_t tile = ((uint64_t)(cz / p.TS) * nty + (cy / p.TS)) * ntx + (cx / p.TS);
+        const uint32_t mort = morton3(cx % p.TS, cy % p.TS, cz % p.TS);
+        key[i] = (tile << 32) | mort;
+    }
+    perm.resize(n);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    grid.resize(4 * n);
+    keys_sorted.resize(n);
+    for (int64_t i = 0; i < n; ++i) {
+        for (int d = 0; d < 4; ++d) grid[4 * i + d] = g[4 * perm[i] + d];
+        keys_sorted[i] = key[perm[i]];
+    }
+}
+
+void tile_items(const slp_plan_s &p, const std::vector<double> &grid, const std::vector<uint64_t> &keys, int64_t n,
+                int chunk, std::vector<slp::TileItem> &items) {
+    items.clear();
+    int64_t i = 0;
+    while (i < n) {
+        int64_t j = i;
+        const uint64_t tile = keys[i] >> 32;
+        while (j < n && (keys[j] >> 32) == tile) ++j;
+        const uint32_t packed = (uint32_t)grid[4 * i + 3];
+        const int cx = packed & 1023, cy = (packed >> 10) & 1023, cz = (packed >> 20) & 1023;
+        for (int64_t b = i; b < j; b += chunk) {
+            slp::TileItem it;
+            it.c0x = cx / p.TS * p.TS;
+            it.c0y = cy / p.TS * p.TS;
+            it.c0z = cz / p.TS * p.TS;
+            it.begin = (int)b;
+            it.end = (int)std::min<int64_t>(j, b + chunk);
+            it.pad0 = it.pad1 = it.pad2 = 0;
+            items.push_back(it);
+        }
+        i = j;
+    }
+}
+
+// physical position (relative to the torus centre) of a sorted grid entry
+inline void phys(const slp_plan_s &p, const double *g, double *x) {
+    const uint32_t packed = (uint32_t)g[3];
+    const int c[3] = {(int)(packed & 1023), (int)((packed >> 10) & 1023), (int)((packed >> 20) & 1023)};
+    for (int d = 0; d < 3; ++d) x[d] = ((c[d] + g[d]) - 0.5 * p.L[d]) * (p.P[d] / p.L[d]);
+}
+
+// near-field work list: target blocks of <= 32 sorted targets in one tile,
+// candidate source bins (aligned 2x2x2 cell blocks, contiguous in the sort)
+// whose bounding box lies within eps of the block's bounding box.
+void near_items(slp_plan_s &p, const std::vector<uint64_t> &skeys, const std::vector<uint64_t> &tkeys) {
+    p.near_items.clear();
+    p.near_ranges.clear();
+    p.near_blk_first.clear();
+    p.near_pairs = 0;
+    const int64_t NCH = 2048;  // sources per item
+    // target blocks
+    std::vector<std::pair<int, int>> blocks;
+    for (int64_t i = 0; i < p.N;) {
+        int64_t j = i;
+        const uint64_t tile = tkeys[i] >> 32;
+        while (j < p.N && (tkeys[j] >> 32) == tile && j - i < 32) ++j;
+        blocks.push_back({(int)i, (int)(j - i)});
+        i = j;
+    }
+    const bool all_pairs = p.kernel_mode == SLP_KERNEL_SEPARABLE || !(p.eps < p.diam);
+    // source bins: key = (tile, morton >> 3)
+    struct Bin {
+        int b, e;
+        double lo[3], hi[3];
+    };
+    std::vector<Bin> bins;
+    std::unordered_map<uint64_t, int> bin_of;  // cell-block coordinate -> bin
+    if (!all_pairs) {
+        for (int64_t i = 0; i < p.Q;) {
+            int64_t j = i;
+            const uint64_t bk = skeys[i] >> 3;
+            while (j < p.Q && (skeys[j] >> 3) == bk) ++j;
+            Bin bn;
+            bn.b = (int)i;
+            bn.e = (int)j;
+            for (int d = 0; d < 3; ++d) {
+                bn.lo[d] = 1e300;
+                bn.hi[d] = -1e300;
+            }
+            for (int64_t k = i; k < j; ++k) {
+                double x[3];
+                phys(p, &p.src_grid[4 * k], x);
+                for (int d = 0; d < 3; ++d) {
+                    bn.lo[d] = std::min(bn.lo[d], x[d]);
+                    bn.hi[d] = std::max(bn.hi[d], x[d]);
+                }
+            }
+            const uint32_t packed = (uint32_t)p.src_grid[4 * i + 3];
+            const uint64_t bx = (packed & 1023) / 2, by = ((packed >> 10) & 1023) / 2, bz = ((packed >> 20) & 1023) / 2;
+            bin_of[(bz << 40) | (by << 20) | bx] = (int)bins.size();
+            bins.push_back(bn);
+            i = j;
+        }
+    }
+    const double eps = p.eps;
+    std::vector<int> found;
+    for (const auto &blk : blocks) {
+        std::vector<int2> rng;
+        if (all_pairs) {
+            rng.push_back(make_int2(0, (int)p.Q));
+        } else {
+            double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+            for (int t = blk.first; t < blk.first + blk.second; ++t) {
+                double x[3];
+                phys(p, &p.tgt_grid[4 * t], x);
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = std::min(lo[d], x[d]);
+                    hi[d] = std::max(hi[d], x[d]);
+                }
+            }
+            int b0[3], b1[3];
+            for (int d = 0; d < 3; ++d) {
+                const double h = p.P[d] / p.L[d];
+                const double u0 = (lo[d] - eps) / h + 0.5 * p.L[d], u1 = (hi[d] + eps) / h + 0.5 * p.L[d];
+                b0[d] = std::max(0, (int)std::floor(u0) - 1) / 2;
+                b1[d] = std::min(p.L[d] - 1, (int)std::floor(u1) + 1) / 2;
+            }
+            found.clear();
+            for (int bz = b0[2]; bz <= b1[2]; ++bz)
+                for (int by = b0[1]; by <= b1[1]; ++by)
+                    for (int bx = b0[0]; bx <= b1[0]; ++bx) {
+                        auto itb = bin_of.find(((uint64_t)bz << 40) | ((uint64_t)by << 20) | (uint64_t)bx);
+                        if (itb == bin_of.end()) continue;
+                        const Bin &bn = bins[itb->second];
+                        double d2 = 0;
+                        for (int d = 0; d < 3; ++d) {
+                            const double g = std::max(0.0, std::max(bn.lo[d] - hi[d], lo[d] - bn.hi[d]));
+                            d2 += g * g;
+                        }
+                        if (d2 <= eps * eps * (1.0 + 1e-9)) found.push_back(itb->second);
+                    }
+            std::sort(found.begin(), found.end(), [&](int a, int b) { return bins[a].b < bins[b].b; });
+            for (int f : found) {
+                if (!rng.empty() && rng.back().y == bins[f].b)
+                    rng.back().y = bins[f].e;
+                else
+                    rng.push_back(make_int2(bins[f].b, bins[f].e));
+            }
+        }
+        // chunk into items of <= NCH sources
+        p.near_blk_first.push_back((int)p.near_items.size());
+        int64_t acc = 0;
+        slp::NearItem it;
+        it.tbegin = blk.first;
+        it.tcount = blk.second;
+        it.rbegin = (int)p.near_ranges.size();
+        for (int2 r : rng) {
+            int b = r.x;
+            while (b < r.y) {
+                const int take = (int)std::min<int64_t>(r.y - b, NCH - acc);
+                p.near_ranges.push_back(make_int2(b, b + take));
+                acc += take;
+                b += take;
+                p.near_pairs += (int64_t)take * blk.second;
+                if (acc == NCH) {
+                    it.rend = (int)p.near_ranges.size();
+                    p.near_items.push_back(it);
+                    it.rbegin = it.rend;
+                    acc = 0;
+                }
+            }
+        }
+        if (acc > 0) {
+            it.rend = (int)p.near_ranges.size();
+            p.near_items.push_back(it);
+        }
+        if ((int)p.near_items.size() == p.near_blk_first.back()) {
+            // no candidate sources: keep an empty item so the block is represented
+            it.rbegin = it.rend = (int)p.near_ranges.size();
+            p.near_items.push_back(it);
+        }
+    }
+    p.near_blk_first.push_back((int)p.near_items.size());
+}
+
+// kernel multiplier table D[|kz|][|ky|][kx] (l in I_n, Nyquist dropped)
+void build_dtab(slp_plan_s &p) {
+    const int Kx = p.n[0] / 2, hy = p.n[1] / 2, hz = p.n[2] / 2;
+    p.Dtab.assign((size_t)hz * hy * Kx, 0.0);
+    std::vector<double> W[3];
+    const int hn[3] = {Kx, hy, hz};
+    for (int d = 0; d < 3; ++d) {
+        W[d].resize(hn[d]);
+        for (int l = 0; l < hn[d]; ++l) W[d][l] = kb_hat_host(p.m, p.L[d], (double)l);
+    }
+    const double V = p.P[0] * p.P[1] * p.P[2];
+    for (int kz = 0; kz < hz; ++kz)
+        for (int ky = 0; ky < hy; ++ky)
+            for (int kx = 0; kx < Kx; ++kx) {
+                double cl;
+                if (p.kernel_mode == SLP_KERNEL_RADIAL) {
+                    const double ax = 2 * PI * kx / p.P[0], ay = 2 * PI * ky / p.P[1], az = 2 * PI * kz / p.P[2];
+                    const double k2 = ax * ax + ay * ay + az * az;
+                    const double k = std::sqrt(k2);
+                    double kh;
+                    if (k * p.R < 1e-6)
+                        kh = 0.5 * p.R * p.R;
+                    else {
+                        const double sn = std::sin(0.5 * k * p.R);
+                        kh = 2.0 * sn * sn / k2;
+                    }
+                    kh *= std::exp(-0.5 * p.sigma_g * p.sigma_g * k2);
+                    cl = kh / V;
+                } else {
+                    cl = p.sep_A * p.sep_h[0][kx] * p.sep_h[1][ky] * p.sep_h[2][kz];
+                }
+                const double w = W[0][kx] * W[1][ky] * W[2][kz];
+                p.Dtab[((size_t)kz * hy + ky) * Kx + kx] = cl / (w * w);
+            }
+}
+
+// ---------------------------------------------------------------- device upload
+template <typename T> struct V4;
+template <> struct V4<float> { typedef float4 t; typedef float2 t2; };
+template <> struct V4<double> { typedef double4 t; typedef double2 t2; };
+
+slp_status dalloc(slp_plan_s &p, void **ptr, size_t bytes) {
+    bytes = (size_t)round_up((int64_t)std::max<size_t>(bytes, 16), 256);
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SLP_ERR_OOM : SLP_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    p.allocs.push_back(*ptr);
+    p.bytes_device += (int64_t)bytes;
+    return SLP_OK;
+}
+
+template <typename S> slp_status upload(slp_plan_s &p, void **ptr, const S *src, size_t count) {
+    slp_status st = dalloc(p, ptr, count * sizeof(S));
+    if (st != SLP_OK) return st;
+    if (count == 0) return SLP_OK;
+    cudaError_t e = cudaMemcpy(*ptr, src, count * sizeof(S), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(SLP_ERR_CUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    return SLP_OK;
+}
+
+#define TRY(x)                          \
+    do {                                \
+        slp_status _s = (x);            \
+        if (_s != SLP_OK) return _s;    \
+    } while (0)
+
+template <typename T> slp_status upload_all(slp_plan_s &p) {
+    typedef typename V4<T>::t T4;
+    typedef typename V4<T>::t2 T2;
+    slp::DevPlan &d = p.dp;
+    memset(&d, 0, sizeof d);
+    d.prec = p.prec;
+    d.q = p.q;
+    d.N = p.N;
+    d.Q = p.Q;
+    d.M = p.M;
+    d.NV = p.N;
+    for (int a = 0; a < 3; ++a) {
+        d.L[a] = p.L[a];
+        d.n[a] = p.n[a];
+        d.h[a] = p.P[a] / p.L[a];
+    }
+    d.Kx = p.n[0] / 2;
+    d.m = p.m;
+    d.TS = p.TS;
+    d.TE = p.TE;
+    d.beta = KB_B * p.m;
+    d.inv_sinh_beta = 1.0 / std::sinh(d.beta);
+    d.eps2 = std::isfinite(p.eps) ? p.eps * p.eps : 1e300;
+    d.inv_s_sqrt2 = p.sigma_g > 0 ? 1.0 / (p.sigma_g * std::sqrt(2.0)) : 0.0;
+    d.kernel_mode = p.kernel_mode;
+    d.deterministic = p.opts.deterministic;
+
+    // sources / targets in sorted order
+    std::vector<T4> sg(p.Q), tg(p.N);
+    for (int64_t i = 0; i < p.Q; ++i) {
+        const double *g = &p.src_grid[4 * i];
+        T w;
+        if (sizeof(T) == 4) {
+            const uint32_t pk = (uint32_t)g[3];
+            float f;
+            memcpy(&f, &pk, 4);
+            w = (T)f;
+        } else {
+            w = (T)g[3];
+        }
+        sg[i].x = (T)g[0];
+        sg[i].y = (T)g[1];
+        sg[i].z = (T)g[2];
+        sg[i].w = w;
+        // guard: a fraction that rounds up to 1 in FP32 stays below 1
+        if (sg[i].x >= T(1)) sg[i].x = std::nextafter(T(1), T(0));
+        if (sg[i].y >= T(1)) sg[i].y = std::nextafter(T(1), T(0));
+        if (sg[i].z >= T(1)) sg[i].z = std::nextafter(T(1), T(0));
+    }
+    for (int64_t i = 0; i < p.N; ++i) {
+        const double *g = &p.tgt_grid[4 * i];
+        T w;
+        if (sizeof(T) == 4) {
+            const uint32_t pk = (uint32_t)g[3];
+            float f;
+            memcpy(&f, &pk, 4);
+            w = (T)f;
+        } else {
+            w = (T)g[3];
+        }
+        tg[i].x = (T)g[0];
+        tg[i].y = (T)g[1];
+        tg[i].z = (T)g[2];
+        tg[i].w = w;
+        if (tg[i].x >= T(1)) tg[i].x = std::nextafter(T(1), T(0));
+        if (tg[i].y >= T(1)) tg[i].y = std::nextafter(T(1), T(0));
+        if (tg[i].z >= T(1)) tg[i].z = std::nextafter(T(1), T(0));
+    }
+    std::vector<T> sw(p.Q);
+    for (int64_t i = 0; i < p.Q; ++i) sw[i] = (T)p.wk[p.src_perm[i]];
+    std::vector<T4> tn(p.M);
+    std::vector<int4> tv(p.M);
+    for (int64_t j = 0; j < p.M; ++j) {
+        tn[j].x = (T)p.nrm[3 * j];
+        tn[j].y = (T)p.nrm[3 * j + 1];
+        tn[j].z = (T)p.nrm[3 * j + 2];
+        tn[j].w = T(0);
+        tv[j] = make_int4(p.T[3 * j], p.T[3 * j + 1], p.T[3 * j + 2], 0);
+    }
+    std::vector<T> lamT(p.lam.begin(), p.lam.end());
+    void *ptr;
+    TRY(upload(p, &ptr, sg.data(), sg.size()));
+    d.src_grid = ptr;
+    TRY(upload(p, &ptr, p.src_perm.data(), p.src_perm.size()));
+    d.src_perm = (const int *)ptr;
+    TRY(upload(p, &ptr, sw.data(), sw.size()));
+    d.src_w = ptr;
+    TRY(upload(p, &ptr, tn.data(), tn.size()));
+    d.tri_nrm = ptr;
+    TRY(upload(p, &ptr, tv.data(), tv.size()));
+    d.tri_vtx = (const int4 *)ptr;
+    TRY(upload(p, &ptr, lamT.data(), lamT.size()));
+    d.lam = ptr;
+    TRY(upload(p, &ptr, tg.data(), tg.size()));
+    d.tgt_grid = ptr;
+    TRY(upload(p, &ptr, p.tgt_perm.data(), p.tgt_perm.size()));
+    d.tgt_perm = (const int *)ptr;
+
+    // scratch
+    const int64_t G = (int64_t)p.L[0] * p.L[1] * p.L[2];
+    const int Kx = p.n[0] / 2;
+    TRY(dalloc(p, &d.qbuf, sizeof(T) * p.Q));
+    TRY(dalloc(p, &d.gridA, sizeof(T) * G));
+    TRY(dalloc(p, &d.gridB, sizeof(T) * G));
+    TRY(dalloc(p, &d.S1, sizeof(T2) * (size_t)p.L[2] * p.L[1] * Kx));
+    TRY(dalloc(p, &d.S2, sizeof(T2) * (size_t)p.L[2] * p.n[1] * Kx));
+    if (cudaMemset(d.gridA, 0, sizeof(T) * G) != cudaSuccess) return fail(SLP_ERR_CUDA, "cudaMemset failed");
+
+    std::vector<T> Dt(p.Dtab.begin(), p.Dtab.end());
+    TRY(upload(p, &ptr, Dt.data(), Dt.size()));
+    d.Dtab = ptr;
+    for (int a = 0; a < 3; ++a) {
+        std::vector<T2> tw(p.L[a]);
+        for (int t = 0; t < p.L[a]; ++t) {
+            const double ang = 2.0 * PI * t / p.L[a];
+            tw[t].x = (T)std::cos(ang);
+            tw[t].y = (T)(-std::sin(ang));
+        }
+        TRY(upload(p, &ptr, tw.data(), tw.size()));
+        d.tw[a] = ptr;
+    }
+    TRY(upload(p, &ptr, p.spread_items.data(), p.spread_items.size()));
+    d.spread_items = (const slp::TileItem *)ptr;
+    d.n_spread = (int)p.spread_items.size();
+    TRY(upload(p, &ptr, p.gather_items.data(), p.gather_items.size()));
+    d.gather_items = (const slp::TileItem *)ptr;
+    d.n_gather = (int)p.gather_items.size();
+    TRY(upload(p, &ptr, p.near_items.data(), p.near_items.size()));
+    d.near_items = (const slp::NearItem *)ptr;
+    d.n_near = (int)p.near_items.size();
+    TRY(upload(p, &ptr, p.near_ranges.data(), p.near_ranges.size()));
+    d.near_ranges = (const int2 *)ptr;
+    TRY(upload(p, &ptr, p.near_blk_first.data(), p.near_blk_first.size()));
+    p.d_blk_first = (int *)ptr;
+    if (p.opts.deterministic) TRY(dalloc(p, &d.phi_near, sizeof(T) * 32 * std::max<size_t>(1, p.near_items.size())));
+    if (p.kernel_mode == SLP_KERNEL_SEPARABLE) {
+        for (int a = 0; a < 3; ++a) {
+            std::vector<T> h(p.sep_h[a].begin(), p.sep_h[a].end());
+            TRY(upload(p, &ptr, h.data(), h.size()));
+            d.sep_h[a] = ptr;
+            d.sep_nh[a] = (int)h.size();
+        }
+        d.sep_A = 4.0 * PI * p.sep_A;
+    }
+    void *errp;
+    TRY(dalloc(p, &errp, sizeof(int)));
+    if (cudaMemset(errp, 0, sizeof(int)) != cudaSuccess) return fail(SLP_ERR_CUDA, "cudaMemset failed");
+    d.err = (int *)errp;
+    // staging buffers for slp_eval_host
+    TRY(dalloc(p, &p.d_stage_in, sizeof(T) * 3 * std::max(p.Q, p.N)));
+    TRY(dalloc(p, &p.d_stage_phi, sizeof(T) * p.N));
+    p.launches_per_eval = 9 + (p.opts.deterministic ? 1 : 0);
+    return SLP_OK;
+}
+
+void free_device(slp_plan_s &p) {
+    if (p.device < 0) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(p.device);
+    for (void *a : p.allocs) cudaFree(a);
+    p.allocs.clear();
+    cudaSetDevice(prev);
+}
+
+slp_status cuda_status(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return SLP_OK;
+    return fail(SLP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Kernels of one evaluation, in launch order (names reported by the profiler entry point).
+const char *const STAGE_NAMES[] = {"charges", "spread", "fft_x", "fft_y", "fft_z_mul", "ifft_y", "ifft_x",
+                                   "gather", "near", "near_reduce"};
+const int N_STAGE_NAMES = 10;
+
+// Enqueue the evaluation up to stage `last`.  With ev != NULL, ev[i] is
+// recorded before kernel i and ev[i + 1] after it (ev has N_STAGE_NAMES + 1 entries).
+slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, cudaStream_t s, int last,
+                        cudaEvent_t *ev = nullptr) {
+    const slp::DevPlan &d = p.dp;
+    int k = 0;
+    auto rec = [&]() {
+        if (ev) cudaEventRecord(ev[k], s);
+        ++k;
+    };
+    rec();
+    TRY(cuda_status(slp::launch_charges(d, kind, d_in, s), "charges"));
+    rec();
+    if (last <= SLP_STAGE_CHARGES) return SLP_OK;
+    TRY(cuda_status(slp::launch_spread(d, s), "spread"));
+    rec();
+    if (last <= SLP_STAGE_SPREAD) return SLP_OK;
+    TRY(cuda_status(slp::launch_fft_forward_x(d, s), "fft x"));
+    rec();
+    if (last <= SLP_STAGE_FFT_X) return SLP_OK;
+    TRY(cuda_status(slp::launch_fft_forward_y(d, s), "fft y"));
+    rec();
+    if (last <= SLP_STAGE_FFT_Y) return SLP_OK;
+    TRY(cuda_status(slp::launch_fft_z_multiply(d, s), "fft z"));
+    rec();
+    if (last <= SLP_STAGE_FFT_Z) return SLP_OK;
+    TRY(cuda_status(slp::launch_fft_inverse_y(d, s), "ifft y"));
+    rec();
+    if (last <= SLP_STAGE_IFFT_Y) return SLP_OK;
+    TRY(cuda_status(slp::launch_fft_inverse_x(d, s), "ifft x"));
+    rec();
+    if (last <= SLP_STAGE_IFFT_X) return SLP_OK;
+    TRY(cuda_status(slp::launch_gather(d, d_phi, s), "gather"));
+    rec();
+    if (last <= SLP_STAGE_GATHER) return SLP_OK;
+    TRY(cuda_status(slp::launch_near(d, d_phi, s), "near field"));
+    rec();
+    if (p.opts.deterministic)
+        TRY(cuda_status(slp::launch_near_reduce(d, p.d_blk_first, (int)p.near_blk_first.size() - 1, d_phi, s),
+                        "near reduce"));
+    rec();
+    return SLP_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+slp_status slp_default_opts(slp_plan_opts *o) {
+    if (!o) return fail(SLP_ERR_INVALID_ARG, "opts is NULL");
+    memset(o, 0, sizeof *o);
+    o->precision = 32;
+    o->kernel_mode = SLP_KERNEL_AUTO;
+    o->near_mode = SLP_NEAR_AUTO;
+    o->device = 0;
+    o->allow_grid_raise = 1;
+    o->check_mesh = 1;
+    return SLP_OK;
+}
+
+slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, const slp_plan_opts *opts,
+                    slp_plan_t *out) {
+    g_last_error.clear();
+    if (!out) return fail(SLP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!mesh || !mesh->vertices || !mesh->triangles) return fail(SLP_ERR_INVALID_ARG, "mesh or its arrays are NULL");
+    if (mesh->n_vertices < 3 || mesh->n_triangles < 1) return fail(SLP_ERR_INVALID_ARG, "mesh is empty");
+    if (mesh->n_vertices > (1LL << 30) || mesh->n_triangles * 7 > (1LL << 30))
+        return fail(SLP_ERR_INVALID_ARG, "mesh too large for 32-bit indices");
+    if (!(tolerance > 0.0 && tolerance < 1.0)) return fail(SLP_ERR_INVALID_ARG, "tolerance must be in (0, 1)");
+    slp_plan_opts o;
+    if (opts)
+        o = *opts;
+    else
+        slp_default_opts(&o);
+    if (o.precision != 32 && o.precision != 64) return fail(SLP_ERR_INVALID_ARG, "precision must be 32 or 64");
+
+    slp_plan_s *p = new slp_plan_s();
+    p->opts = o;
+    p->q = quadrature;
+    p->prec = o.precision;
+    p->tol = tolerance;
+    p->N = mesh->n_vertices;
+    p->M = mesh->n_triangles;
+    p->device = o.device;
+    p->V.assign(mesh->vertices, mesh->vertices + 3 * p->N);
+    p->T.assign(mesh->triangles, mesh->triangles + 3 * p->M);
+    for (double v : p->V)
+        if (!std::isfinite(v)) {
+            delete p;
+            return fail(SLP_ERR_MESH, "vertex coordinates must be finite");
+        }
+    slp_status st = validate_mesh(*p);
+    if (st == SLP_OK) st = build_sources(*p);
+    if (st == SLP_OK) st = choose_parameters(*p);
+    if (st != SLP_OK) {
+        delete p;
+        return st;
+    }
+    std::vector<uint64_t> skeys, tkeys;
+    sort_points(*p, p->y.data(), p->Q, p->src_perm, p->src_grid, skeys);
+    sort_points(*p, p->V.data(), p->N, p->tgt_perm, p->tgt_grid, tkeys);
+    tile_items(*p, p->src_grid, skeys, p->Q, 1024, p->spread_items);
+    tile_items(*p, p->tgt_grid, tkeys, p->N, 256, p->gather_items);
+    near_items(*p, skeys, tkeys);
+    build_dtab(*p);
+    p->near_mode = SLP_NEAR_ON_THE_FLY;
+
+    if (p->device >= 0) {
+        int ndev = 0;
+        if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= p->device) {
+            cudaGetLastError();
+            delete p;
+            return fail(SLP_ERR_NO_DEVICE, "CUDA device %d is not available", o.device);
+        }
+        DeviceGuard g(p->device);
+        st = p->prec == 64 ? upload_all<double>(*p) : upload_all<float>(*p);
+        if (st != SLP_OK) {
+            free_device(*p);
+            delete p;
+            return st;
+        }
+    }
+    *out = p;
+    return SLP_OK;
+}
+
+slp_status slp_eval(slp_plan_t p, int kind, const void *d_in, void *d_phi, void *stream) {
+    if (!p) return fail(SLP_ERR_INVALID_ARG, "plan is NULL");
+    if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan cannot evaluate");
+    if (kind < 0 || kind > 2) return fail(SLP_ERR_INVALID_ARG, "unknown input kind %d", kind);
+    if (!d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "input or output pointer is NULL");
+    DeviceGuard g(p->device);
+    return run_pipeline(*p, kind, d_in, d_phi, (cudaStream_t)stream, SLP_STAGE_NEAR);
+}
+
+slp_status slp_eval_host(slp_plan_t p, int kind, const void *h_in, void *h_phi, void *stream) {
+    if (!p) return fail(SLP_ERR_INVALID_ARG, "plan is NULL");
+    if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan cannot evaluate");
+    if (kind < 0 || kind > 2) return fail(SLP_ERR_INVALID_ARG, "unknown input kind %d", kind);
+    if (!h_in || !h_phi) return fail(SLP_ERR_INVALID_ARG, "input or output pointer is NULL");
+    DeviceGuard g(p->device);
+    const size_t es = p->prec == 64 ? 8 : 4;
+    const size_t nin = kind == SLP_INPUT_SIGMA ? (size_t)p->Q : (kind == SLP_INPUT_MAG ? 3 * (size_t)p->Q : 3 * (size_t)p->N);
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(cuda_status(cudaMemcpyAsync(p->d_stage_in, h_in, nin * es, cudaMemcpyHostToDevice, s), "copy in"));
+    TRY(run_pipeline(*p, kind, p->d_stage_in, p->d_stage_phi, s, SLP_STAGE_NEAR));
+    TRY(cuda_status(cudaMemcpyAsync(h_phi, p->d_stage_phi, (size_t)p->N * es, cudaMemcpyDeviceToHost, s), "copy out"));
+    TRY(cuda_status(cudaStreamSynchronize(s), "synchronize"));
+    return SLP_OK;
+}
+
+slp_status slp_query(slp_plan_t p, slp_info *info) {
+    if (!p || !info) return fail(SLP_ERR_INVALID_ARG, "NULL argument");
+    memset(info, 0, sizeof *info);
+    info->n_targets = p->N;
+    info->n_sources = p->Q;
+    info->n_triangles = p->M;
+    info->quadrature = p->q;
+    info->precision = p->prec;
+    for (int d = 0; d < 3; ++d) {
+        info->grid[d] = p->L[d];
+        info->modes[d] = p->n[d];
+        info->center[d] = p->ctr[d];
+        info->period[d] = p->P[d];
+    }
+    info->m = p->m;
+    info->kernel_mode = p->kernel_mode;
+    info->near_mode = p->near_mode;
+    info->grid_raised = p->grid_raised;
+    info->sigma_g = p->sigma_g;
+    info->trunc_radius = p->R;
+    info->eps_near = p->eps;
+    info->tolerance = p->tol;
+    info->near_pairs = p->near_pairs;
+    info->near_pairs_within = -1;
+    info->near_matrix_nnz = 0;
+    info->bytes_device = p->bytes_device;
+    info->n_spread_items = (int64_t)p->spread_items.size();
+    info->n_gather_items = (int64_t)p->gather_items.size();
+    info->n_near_items = (int64_t)p->near_items.size();
+    info->launches_per_eval = p->launches_per_eval;
+    return SLP_OK;
+}
+
+slp_status slp_query_points(slp_plan_t p, double *points) {
+    if (!p || !points) return fail(SLP_ERR_INVALID_ARG, "NULL argument");
+    memcpy(points, p->y.data(), sizeof(double) * 3 * p->Q);
+    return SLP_OK;
+}
+
+slp_status slp_check(slp_plan_t p) {
+    if (!p) return fail(SLP_ERR_INVALID_ARG, "plan is NULL");
+    if (p->device < 0) return SLP_OK;
+    DeviceGuard g(p->device);
+    TRY(cuda_status(cudaDeviceSynchronize(), "synchronize"));
+    int code = 0;
+    TRY(cuda_status(cudaMemcpy(&code, p->dp.err, sizeof(int), cudaMemcpyDeviceToHost), "read status"));
+    if (code != 0) {
+        cudaMemset(p->dp.err, 0, sizeof(int));
+        return fail(SLP_ERR_CUDA, "device status word %d (a kernel saw an inconsistent work item)", code);
+    }
+    return SLP_OK;
+}
+
+slp_status slp_destroy(slp_plan_t p) {
+    if (!p) return SLP_OK;
+    free_device(*p);
+    delete p;
+    return SLP_OK;
+}
+
+const char *slp_status_string(slp_status s) {
+    switch (s) {
+        case SLP_OK: return "ok";
+        case SLP_ERR_INVALID_ARG: return "invalid argument";
+        case SLP_ERR_MESH: return "invalid mesh";
+        case SLP_ERR_TOLERANCE_INFEASIBLE: return "tolerance infeasible on this grid";
+        case SLP_ERR_OOM: return "out of device memory";
+        case SLP_ERR_CUDA: return "CUDA error";
+        case SLP_ERR_TIMEOUT: return "device wait timed out";
+        case SLP_ERR_NONFINITE: return "non-finite value";
+        case SLP_ERR_NO_DEVICE: return "no CUDA device";
+        case SLP_ERR_UNSUPPORTED: return "unsupported option";
+    }
+    return "unknown status";
+}
+
+const char *slp_last_error(void) { return g_last_error.c_str(); }
+
+// ---------------------------------------------------------------- debug ABI
+slp_status slp_debug_run(slp_plan_t p, int kind, const void *d_in, void *d_phi, void *stream, int last) {
+    if (!p) return fail(SLP_ERR_INVALID_ARG, "plan is NULL");
+    if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan");
+    if (kind < 0 || kind > 2 || !d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "bad input");
+    DeviceGuard g(p->device);
+    // a partial run may have left a spread grid behind: start from zero
+    const size_t es = p->prec == 64 ? 8 : 4;
+    TRY(cuda_status(slp::launch_zero(p->dp.gridA, es * (size_t)p->L[0] * p->L[1] * p->L[2], (cudaStream_t)stream),
+                    "zero grid"));
+    return run_pipeline(*p, kind, d_in, d_phi, (cudaStream_t)stream, last);
+}
+
+slp_status slp_debug_buffer_bytes(slp_plan_t p, int buf, int64_t *bytes) {
+    if (!p || !bytes) return fail(SLP_ERR_INVALID_ARG, "NULL argument");
+    const int64_t es = p->prec == 64 ? 8 : 4;
+    const int64_t G = (int64_t)p->L[0] * p->L[1] * p->L[2];
+    const int64_t Kx = p->n[0] / 2;
+    switch (buf) {
+        case SLP_BUF_QBUF: *bytes = es * p->Q; break;
+        case SLP_BUF_GRID_A:
+        case SLP_BUF_GRID_B: *bytes = es * G; break;
+        case SLP_BUF_S1: *bytes = 2 * es * p->L[2] * p->L[1] * Kx; break;
+        case SLP_BUF_S2: *bytes = 2 * es * p->L[2] * p->n[1] * Kx; break;
+        case SLP_BUF_DTAB: *bytes = es * (int64_t)p->Dtab.size(); break;
+        default: return fail(SLP_ERR_INVALID_ARG, "unknown buffer %d", buf);
+    }
+    return SLP_OK;
+}
+
+slp_status slp_debug_copy(slp_plan_t p, int buf, void *host, int64_t bytes) {
+    if (!p || !host) return fail(SLP_ERR_INVALID_ARG, "NULL argument");
+    if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan");
+    int64_t need = 0;
+    TRY(slp_debug_buffer_bytes(p, buf, &need));
+    if (bytes != need) return fail(SLP_ERR_INVALID_ARG, "buffer %d holds %lld bytes", buf, (long long)need);
+    const void *src = nullptr;
+    switch (buf) {
+        case SLP_BUF_QBUF: src = p->dp.qbuf; break;
+        case SLP_BUF_GRID_A: src = p->dp.gridA; break;
+        case SLP_BUF_GRID_B: src = p->dp.gridB; break;
+        case SLP_BUF_S1: src = p->dp.S1; break;
+        case SLP_BUF_S2: src = p->dp.S2; break;
+        case SLP_BUF_DTAB: src = p->dp.Dtab; break;
+    }
+    DeviceGuard g(p->device);
+    TRY(cuda_status(cudaDeviceSynchronize(), "synchronize"));
+    TRY(cuda_status(cudaMemcpy(host, src, (size_t)bytes, cudaMemcpyDeviceToHost), "copy"));
+    return SLP_OK;
+}
+
+slp_status slp_debug_host_count(slp_plan_t p, int which, int64_t *count) {
+    if (!p || !count) return fail(SLP_ERR_INVALID_ARG, "NULL argument");
+    switch (which) {
+        case SLP_HOST_SRC_PERM: *count = p->Q; break;
+        case SLP_HOST_TGT_PERM: *count = p->N; break;
+        case SLP_HOST_SRC_GRID: *count = 4 * p->Q; break;
+        case SLP_HOST_TGT_GRID: *count = 4 * p->N; break;
+        case SLP_HOST_SPREAD_ITEMS: *count = 8 * (int64_t)p->spread_items.size(); break;
+        case SLP_HOST_GATHER_ITEMS: *count = 8 * (int64_t)p->gather_items.size(); break;
+        case SLP_HOST_NEAR_ITEMS: *count = 4 * (int64_t)p->near_items.size(); break;
+        case SLP_HOST_NEAR_RANGES: *count = 2 * (int64_t)p->near_ranges.size(); break;
+        case SLP_HOST_DTAB: *count = (int64_t)p->Dtab.size(); break;
+        case SLP_HOST_SRC_POINTS: *count = 3 * p->Q; break;
+        case SLP_HOST_TGT_POINTS: *count = 3 * p->N; break;
+        default: return fail(SLP_ERR_INVALID_ARG, "unknown host array %d", which);
+    }
+    return SLP_OK;
+}
+
+slp_status slp_debug_host_array(slp_plan_t p, int which, void *out, int64_t count) {
+    int64_t need = 0;
+    TRY(slp_debug_host_count(p, which, &need));
+    if (!out || count != need) return fail(SLP_ERR_INVALID_ARG, "array %d has %lld elements", which, (long long)need);
+    switch (which) {
+        case SLP_HOST_SRC_PERM: memcpy(out, p->src_perm.data(), 4 * count); break;
+        case SLP_HOST_TGT_PERM: memcpy(out, p->tgt_perm.data(), 4 * count); break;
+        case SLP_HOST_SRC_GRID: memcpy(out, p->src_grid.data(), 8 * count); break;
+        case SLP_HOST_TGT_GRID: memcpy(out, p->tgt_grid.data(), 8 * count); break;
+        case SLP_HOST_SPREAD_ITEMS: memcpy(out, p->spread_items.data(), 4 * count); break;
+        case SLP_HOST_GATHER_ITEMS: memcpy(out, p->gather_items.data(), 4 * count); break;
+        case SLP_HOST_NEAR_ITEMS: memcpy(out, p->near_items.data(), 4 * count); break;
+        case SLP_HOST_NEAR_RANGES: memcpy(out, p->near_ranges.data(), 4 * count); break;
+        case SLP_HOST_DTAB: memcpy(out, p->Dtab.data(), 8 * count); break;
+        case SLP_HOST_SRC_POINTS: {
+            double *o = (double *)out;
+            for (int64_t i = 0; i < p->Q; ++i)
+                for (int d = 0; d < 3; ++d) o[3 * i + d] = p->y[3 * (int64_t)p->src_perm[i] + d];
+            break;
+        }
+        case SLP_HOST_TGT_POINTS: {
+            double *o = (double *)out;
+            for (int64_t i = 0; i < p->N; ++i)
+                for (int d = 0; d < 3; ++d) o[3 * i + d] = p->V[3 * (int64_t)p->tgt_perm[i] + d];
+            break;
+        }
+    }
+    return SLP_OK;
+}
+
+slp_status slp_debug_profile(slp_plan_t p, int kind, const void *d_in, void *d_phi, void *stream, float *ms,
+                             int n) {
+    if (!p || !ms) return fail(SLP_ERR_INVALID_ARG, "NULL argument");
+    if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan");
+    if (n < N_STAGE_NAMES) return fail(SLP_ERR_INVALID_ARG, "need room for %d timings", N_STAGE_NAMES);
+    if (kind < 0 || kind > 2 || !d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "bad input");
+    DeviceGuard g(p->device);
+    cudaEvent_t ev[N_STAGE_NAMES + 1];
+    for (int i = 0; i <= N_STAGE_NAMES; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) return fail(SLP_ERR_CUDA, "cudaEventCreate");
+    slp_status st = run_pipeline(*p, kind, d_in, d_phi, (cudaStream_t)stream, SLP_STAGE_NEAR, ev);
+    if (st == SLP_OK) st = cuda_status(cudaEventSynchronize(ev[N_STAGE_NAMES]), "event sync");
+    for (int i = 0; i < N_STAGE_NAMES && st == SLP_OK; ++i) {
+        float t = 0.f;
+        st = cuda_status(cudaEventElapsedTime(&t, ev[i], ev[i + 1]), "elapsed");
+        ms[i] = t;
+    }
+    for (int i = 0; i <= N_STAGE_NAMES; ++i) cudaEventDestroy(ev[i]);
+    return st;
+}
+
+const char *slp_debug_stage_name(int i) { return (i >= 0 && i < N_STAGE_NAMES) ? STAGE_NAMES[i] : ""; }
+
+double slp_debug_window(int m, double d) { return kb_window_host(m, d); }
+double slp_debug_window_hat(int m, int L, double l) { return kb_hat_host(m, L, l); }
+
+}  // extern "C"

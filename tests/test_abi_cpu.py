@@ -1,0 +1,217 @@
+"""CPU checks of the C ABI: the library loads and exports every declared
+symbol, host-only plans validate meshes and choose consistent parameters,
+and the plan-time sort and work lists are complete.  No GPU needed."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from synthetic import meshes, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def slp():
+    import paper_1305_3162_gb300 as m
+    from paper_1305_3162_gb300 import _build
+    _build.build()
+    m.load()
+    return m
+
+
+def _declared_functions():
+    names = set()
+    for h in ("slp.h", "slp_debug.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for mt in re.finditer(r"\b(?:slp_status|double|const char \*|void)\s*\*?\s*(slp_\w+)\s*\(", src):
+            names.add(mt.group(1))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(slp):
+    names = _declared_functions()
+    assert len(names) >= 15
+    lib = ctypes.CDLL(slp.library_path())
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(slp.EXPORTED)
+
+
+def _host_plan(slp, V, T, q=3, tol=1e-5, prec=32, grid=(0, 0, 0), **kw):
+    o = slp.slp_default_opts()
+    o.precision = prec
+    o.device = -1
+    for d in range(3):
+        o.grid[d] = grid[d]
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return slp.slp_plan(V, T, q, tol, o)
+
+
+def test_status_strings_and_errors(slp):
+    assert slp.slp_status_string(0) == "ok"
+    V, T = meshes.cube(2)
+    with pytest.raises(slp.SlpError) as e:
+        _host_plan(slp, V, T[:, ::-1].copy())  # inward normals
+    assert e.value.status == slp.SLP_ERR_MESH
+    with pytest.raises(slp.SlpError) as e:
+        _host_plan(slp, V, T[:-1])  # open surface
+    assert e.value.status == slp.SLP_ERR_MESH
+    bad = T.copy()
+    bad[0, 0] = V.shape[0]
+    with pytest.raises(slp.SlpError) as e:
+        _host_plan(slp, V, bad)
+    assert e.value.status == slp.SLP_ERR_MESH
+    with pytest.raises(slp.SlpError) as e:
+        _host_plan(slp, V, T, q=5)
+    assert e.value.status == slp.SLP_ERR_INVALID_ARG
+    with pytest.raises(slp.SlpError) as e:
+        _host_plan(slp, V, T, grid=(48, 32, 32))
+    assert e.value.status == slp.SLP_ERR_INVALID_ARG
+    # a degenerate (zero-area) triangle
+    Vd = V.copy()
+    t0 = T[0]
+    Vd[t0[2]] = 0.5 * (Vd[t0[0]] + Vd[t0[1]])
+    with pytest.raises(slp.SlpError):
+        _host_plan(slp, Vd, T, check_mesh=0)
+    # host-only plan cannot evaluate
+    p = _host_plan(slp, V, T)
+    with pytest.raises(slp.SlpError) as e:
+        slp.slp_eval(p, 0, 1, 1, None)
+    assert e.value.status == slp.SLP_ERR_NO_DEVICE
+    slp.slp_destroy(p)
+
+
+def test_infeasible_forced_grid(slp):
+    w = workloads.plate(dims=(200.0, 50.0, 2.0), cell=1.0)
+    with pytest.raises(slp.SlpError) as e:
+        _host_plan(slp, w.V, w.T, grid=(256, 64, 16), kernel_mode=slp.SLP_KERNEL_RADIAL, allow_grid_raise=0)
+    assert e.value.status == slp.SLP_ERR_TOLERANCE_INFEASIBLE
+    p = _host_plan(slp, w.V, w.T, grid=(256, 64, 16))
+    info = slp.slp_query(p)
+    assert info["grid_raised"] == 1 and info["kernel_mode"] == slp.SLP_KERNEL_RADIAL
+    assert all(math.pi * n > 2 * 4.0 ** 2 for n in info["modes"])
+    slp.slp_destroy(p)
+
+
+def test_radial_parameters_satisfy_their_constraints(slp):
+    w = workloads.sphere(level=4)
+    p = _host_plan(slp, w.V, w.T, q=7, grid=(128, 128, 128))
+    info = slp.slp_query(p)
+    assert info["kernel_mode"] == slp.SLP_KERNEL_RADIAL
+    s, R, eps = info["sigma_g"], info["trunc_radius"], info["eps_near"]
+    diam = 2.0  # unit sphere
+    for d in range(3):
+        P = info["period"][d]
+        # no periodic image of the truncated, smoothed kernel reaches a difference vector
+        assert P >= 2.0 + R - 1e-9
+        # grid resolves the Gaussian: exp(-(s k_max)^2 / 2) small at the band edge
+        kmax = math.pi * info["modes"][d] / P
+        assert math.exp(-0.5 * (s * kmax) ** 2) < 1e-3
+    assert R >= diam
+    assert math.erfc(eps / (s * math.sqrt(2))) <= 2 * 1e-5 * 1.0001
+    slp.slp_destroy(p)
+
+
+def test_sort_permutation_and_grid_coordinates(slp):
+    V, T = meshes.icosphere(3)
+    p = _host_plan(slp, V, T, q=7, grid=(64, 64, 64))
+    info = slp.slp_query(p)
+    L = np.array(info["grid"])
+    P = np.array(info["period"])
+    c = np.array(info["center"])
+    Q = info["n_sources"]
+    perm = slp.slp_debug_host_array(p, slp.SLP_HOST_SRC_PERM)
+    assert np.array_equal(np.sort(perm), np.arange(Q))
+    g = slp.slp_debug_host_array(p, slp.SLP_HOST_SRC_GRID).reshape(-1, 4)
+    packed = g[:, 3].astype(np.int64)
+    cell = np.stack([packed & 1023, (packed >> 10) & 1023, (packed >> 20) & 1023], 1)
+    assert np.all((g[:, :3] >= 0) & (g[:, :3] < 1))
+    pts = slp.slp_query_points(p, Q)
+    x = (cell + g[:, :3] - L / 2) * (P / L) + c
+    assert np.abs(x - pts[perm]).max() < 1e-12
+    # spread items cover every source once, each inside its tile
+    it = slp.slp_debug_host_array(p, slp.SLP_HOST_SPREAD_ITEMS).reshape(-1, 8)
+    cover = np.zeros(Q, int)
+    for c0x, c0y, c0z, b, e, *_ in it:
+        cover[b:e] += 1
+        cc = cell[b:e] - np.array([c0x, c0y, c0z])
+        assert np.all((cc >= 0) & (cc < 8))
+    assert np.all(cover == 1)
+    slp.slp_destroy(p)
+
+
+def test_near_work_list_covers_every_close_pair(slp):
+    """Every (target, source) pair closer than eps is visited by exactly one
+    near-field work item (brute force over all pairs)."""
+    V, T = meshes.icosphere(3)
+    p = _host_plan(slp, V, T, q=7, grid=(128, 128, 128))
+    info = slp.slp_query(p)
+    eps = info["eps_near"]
+    assert eps < 1.0  # a real near field, not all pairs
+    sp = slp.slp_debug_host_array(p, slp.SLP_HOST_SRC_POINTS).reshape(-1, 3)
+    tp = slp.slp_debug_host_array(p, slp.SLP_HOST_TGT_POINTS).reshape(-1, 3)
+    items = slp.slp_debug_host_array(p, slp.SLP_HOST_NEAR_ITEMS).reshape(-1, 4)
+    ranges = slp.slp_debug_host_array(p, slp.SLP_HOST_NEAR_RANGES).reshape(-1, 2)
+    N, Q = tp.shape[0], sp.shape[0]
+    visits = np.zeros((N, Q), np.int16)
+    for tb, tc, rb, re_ in items:
+        for r in range(rb, re_):
+            visits[tb:tb + tc, ranges[r, 0]:ranges[r, 1]] += 1
+    d = np.linalg.norm(tp[:, None, :] - sp[None, :, :], axis=2)
+    close = d < eps
+    assert np.all(visits[close] == 1)
+    assert visits.max() == 1
+    # the work list is not the all-pairs list
+    assert visits.sum() < 0.5 * N * Q
+    assert info["near_pairs"] == int(visits.sum())
+    slp.slp_destroy(p)
+
+
+@pytest.mark.parametrize("m", [4, 6])
+def test_window_transform_matches_numerical_integral(slp, m):
+    """Fourier transform of the normalised Kaiser-Bessel window (I0 closed
+    form of Sec. 3.2, Eq. (cFB)) against a numerical integral of the window."""
+    from scipy.integrate import quad
+    L = 64
+    for l in (0, 3, 11, 16):
+        w = 2 * np.pi * l / L
+        num, _ = quad(lambda d: slp.slp_debug_window(m, d) * np.cos(w * d), -m, m, limit=200, epsabs=1e-13)
+        # the truncated window differs from the untruncated one by the
+        # NFFT error; the untruncated tail beyond m is below C(2, m)
+        assert abs(num - slp.slp_debug_window_hat(m, L, l)) < 10 * (4 * np.pi * (m ** 0.5 + m) * 0.5 ** 0.25 *
+                                                                  np.exp(-2 * np.pi * m * 0.5 ** 0.5))
+    assert abs(slp.slp_debug_window(m, 0.0) - 1.0) < 1e-15
+
+
+def test_dtab_radial_matches_quadrature_of_the_kernel_transform(slp):
+    """D = c_l(N_s) / W^2: recover c_l and compare with an independent FP64
+    quadrature of the radial transform of the truncated kernel,
+    (1/k) int_0^R sin(k r) dr, times the Gaussian factor."""
+    from scipy.integrate import quad
+    V, T = meshes.icosphere(2)
+    p = _host_plan(slp, V, T, q=3, grid=(32, 32, 32))
+    info = slp.slp_query(p)
+    n = info["modes"]
+    L = info["grid"]
+    P = info["period"]
+    m = info["m"]
+    R = info["trunc_radius"]
+    s = info["sigma_g"]
+    D = slp.slp_debug_host_array(p, slp.SLP_HOST_DTAB).reshape(n[2] // 2, n[1] // 2, n[0] // 2)
+    for (kz, ky, kx) in [(0, 0, 0), (1, 2, 3), (3, 1, 0), (7, 7, 7), (5, 0, 2)]:
+        k = 2 * np.pi * np.sqrt((kx / P[0]) ** 2 + (ky / P[1]) ** 2 + (kz / P[2]) ** 2)
+        if k == 0:
+            ft = R * R / 2
+        else:
+            ft, _ = quad(lambda r: np.sin(k * r) / k, 0, R, limit=400, epsabs=1e-14)
+        cl = ft * np.exp(-0.5 * s * s * k * k) / (P[0] * P[1] * P[2])
+        W = (slp.slp_debug_window_hat(m, L[0], kx) * slp.slp_debug_window_hat(m, L[1], ky) *
+             slp.slp_debug_window_hat(m, L[2], kz))
+        assert abs(D[kz, ky, kx] * W * W - cl) <= 1e-10 * abs(cl) + 1e-16
+    slp.slp_destroy(p)
