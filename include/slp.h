@@ -165,6 +165,31 @@ slp_status slp_eval(slp_plan_t plan, int input_kind, const void *d_in, void *d_p
  * Page-locked host memory gives asynchronous copies. */
 slp_status slp_eval_host(slp_plan_t plan, int input_kind, const void *h_in, void *h_phi, void *stream);
 
+/* Allocation-free evaluation for callers that cannot call cudaMalloc (code
+ * running while a stream is captured into a CUDA graph, hosts inside another
+ * framework's memory pool, loops that must not touch the allocator after
+ * start-up).  The paper has no counterpart: this evaluates the same
+ * quantity as slp_eval, phi at the mesh vertices, by direct summation over
+ * all (vertex, quadrature point) pairs, without a plan.
+ * d_vertices:  device, [n_vertices][3] double;  d_triangles: device, [n_triangles][3]
+ *              int32, outward winding (indices are bounds-checked: a triangle with
+ *              an index out of range carries no charge);
+ * quadrature:  SLP_QUAD_1/3/7;  precision: 32 or 64 (type of d_in and d_phi);
+ * input_kind:  SLP_INPUT_* with the layouts of slp_eval;
+ * d_phi:       device, [n_vertices], overwritten;  stream: cudaStream_t or NULL.
+ * Scratch: one 32 MiB static device array inside the library (held by every
+ * GPU that loads it, until exit): at most 2,097,152 sources (q * n_triangles)
+ * at precision 32, 1,048,576 at precision 64; larger meshes return
+ * SLP_ERR_INVALID_ARG with the sizes in slp_last_error().  Nothing in the
+ * array needs to start at zero.  All calls share the array, so calls that
+ * overlap on the GPU (other streams, other host threads) race: order them.
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Costs O(N Q): meant for small meshes. */
+slp_status slp_eval_direct_static(const double *d_vertices, int64_t n_vertices, const int32_t *d_triangles,
+                                  int64_t n_triangles, int quadrature, int precision, int input_kind,
+                                  const void *d_in, void *d_phi, void *stream);
+
 /* Plan parameters and sizes. */
 slp_status slp_query(slp_plan_t plan, slp_info *info);
 

@@ -93,7 +93,7 @@ EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_host", "slp_qu
             "slp_check", "slp_destroy", "slp_status_string", "slp_last_error",
             "slp_debug_run", "slp_debug_copy", "slp_debug_buffer_bytes", "slp_debug_host_count",
             "slp_debug_host_array", "slp_debug_window", "slp_debug_window_hat", "slp_debug_profile",
-            "slp_debug_stage_name"]
+            "slp_debug_stage_name", "slp_eval_direct_static"]
 
 
 def library_path() -> str:
@@ -133,6 +133,7 @@ def load():
         "slp_debug_window_hat": ([ctypes.c_int, ctypes.c_int, ctypes.c_double], ctypes.c_double),
         "slp_debug_profile": ([vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int], St),
         "slp_debug_stage_name": ([ctypes.c_int], ctypes.c_char_p),
+        "slp_eval_direct_static": ([vp, I64, vp, I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp], St),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -196,6 +197,14 @@ def slp_eval(plan, input_kind: int, d_in, d_phi, stream=None):
 
 def slp_eval_host(plan, input_kind: int, h_in, h_phi, stream=None):
     _check(load().slp_eval_host(plan, int(input_kind), _ptr(h_in), _ptr(h_phi), _stream(stream)), "slp_eval_host")
+
+
+def slp_eval_direct_static(d_vertices, n_vertices, d_triangles, n_triangles, quadrature, precision, input_kind,
+                           d_in, d_phi, stream=None):
+    """Allocation-free direct evaluation (see include/slp.h): device mesh, input and output."""
+    _check(load().slp_eval_direct_static(_ptr(d_vertices), int(n_vertices), _ptr(d_triangles), int(n_triangles),
+                                         int(quadrature), int(precision), int(input_kind), _ptr(d_in), _ptr(d_phi),
+                                         _stream(stream)), "slp_eval_direct_static")
 
 
 def slp_query(plan) -> dict:

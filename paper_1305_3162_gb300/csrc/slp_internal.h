@@ -96,4 +96,7 @@ cudaError_t launch_near(const DevPlan &p, void *d_phi, cudaStream_t s);
 cudaError_t launch_near_reduce(const DevPlan &p, const int *blk_first, int nblk, void *d_phi, cudaStream_t s);
 cudaError_t launch_zero(void *ptr, size_t bytes, cudaStream_t s);
 
+// Set the thread-local text returned by slp_last_error().
+void set_last_error(const char *msg);
+
 }  // namespace slp

@@ -959,6 +959,8 @@ struct DeviceGuard {
 
 }  // namespace
 
+void slp::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
 // ======================================================================= C ABI
 extern "C" {
 
