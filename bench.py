@@ -159,7 +159,8 @@ def _algorithmic(info, stage, w, pairs_within):
         "ifft_y": ("hbm", s2 + s1),
         "ifft_x": ("hbm", s1 + es * G),
         "gather": ("hbm", es * G + 4 * es * N + 4 * N + es * N),
-        "near": ("alu", NEAR_FLOPS_PER_PAIR * pairs_within),
+        "near": (("hbm", info["near_matrix_nnz"] * 4 * es + 8 * (N + 1) + 3 * es * N + 2 * es * N + 4 * N)
+                 if info["near_mode"] == 2 else ("alu", NEAR_FLOPS_PER_PAIR * pairs_within)),
         "near_reduce": ("hbm", 0),
     }
     return table[stage]
@@ -328,7 +329,8 @@ def run_ours(args):
                        "l2_flush": f"{FLUSH_BYTES >> 20} MB write before every step",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "eps_near": info["eps_near"], "pairs_within_eps": pairs_within,
-                       "near_pairs_visited": info["near_pairs"]},
+                       "near_pairs_visited": info["near_pairs"], "near_mode": ["auto", "on_the_fly", "precomputed"][info["near_mode"]],
+                       "near_matrix_nnz": info["near_matrix_nnz"]},
             "rel_l2": rel_l2, "parity_ok": parity_ok,
             "roofline": roofline, "per_kernel": per_kernel,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

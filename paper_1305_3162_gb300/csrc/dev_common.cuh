@@ -40,6 +40,9 @@ template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) 
 // cx | cy << 10 | cz << 20 (each axis < 1024).
 __device__ __forceinline__ int packed_cell(float w) { return __float_as_int(w); }
 __device__ __forceinline__ int packed_cell(double w) { return (int)w; }
+// an integer carried in a floating-point slot: bit pattern (FP32) or exact value (FP64)
+__device__ __forceinline__ float pack_id(float, int v) { return __int_as_float(v); }
+__device__ __forceinline__ double pack_id(double, int v) { return (double)v; }
 __device__ __forceinline__ void unpack_cell(int c, int &cx, int &cy, int &cz) {
     cx = c & 1023;
     cy = (c >> 10) & 1023;

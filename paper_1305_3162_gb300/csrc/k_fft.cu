@@ -22,6 +22,23 @@
 
 namespace slp {
 
+// 16-byte vector access to real rows: 4 floats or 2 doubles
+template <typename T> struct VecW;
+template <> struct VecW<float> {
+    typedef float4 V;
+    static constexpr int W = 4;
+    __device__ static void split(const V &v, float *r) { r[0] = v.x; r[1] = v.y; r[2] = v.z; r[3] = v.w; }
+    __device__ static V join(const float *r) { return make_float4(r[0], r[1], r[2], r[3]); }
+    __device__ static V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <> struct VecW<double> {
+    typedef double2 V;
+    static constexpr int W = 2;
+    __device__ static void split(const V &v, double *r) { r[0] = v.x; r[1] = v.y; }
+    __device__ static V join(const double *r) { return make_double2(r[0], r[1]); }
+    __device__ static V zero() { return make_double2(0.0, 0.0); }
+};
+
 // ---------------------------------------------------------------- small DFTs
 template <typename C> __device__ __forceinline__ void dft2(C &a, C &b) {
     const C t = a;
@@ -135,21 +152,41 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     const int64_t npairs = (int64_t)Lz * (Ly / 2);
     const int64_t pr0 = (int64_t)blockIdx.x * PB;
     T *A = (T *)p.gridA;
-    for (int i = threadIdx.x; i < PB * Lx; i += blockDim.x) {
-        const int b = i / Lx, x = i - b * Lx;
+    // rows y0 and y0+1 of each pair, VW elements per vector load; all loads are
+    // issued before the zeroing stores so they overlap
+    typedef typename VecW<T>::V V;
+    constexpr int VW = VecW<T>::W;
+    const int nv = Lx / VW;
+    for (int i = threadIdx.x; i < PB * nv; i += blockDim.x) {
+        const int b = i / nv, xv = i - b * nv;
         const int64_t pr = pr0 + b;
-        C v = cmk(T(0), T(0));
+        T ra[VW], rb[VW];
         if (pr < npairs) {
             const int64_t z = pr / (Ly / 2);
             const int y0 = 2 * (int)(pr - z * (Ly / 2));
-            const int64_t r0 = (z * Ly + y0) * Lx + x;
-            v = cmk(A[r0], A[r0 + Lx]);
-            A[r0] = T(0);
-            A[r0 + Lx] = T(0);
+            const int64_t r0 = (z * Ly + y0) * Lx;
+            const V va = ((const V *)(A + r0))[xv];
+            const V vb = ((const V *)(A + r0 + Lx))[xv];
+            VecW<T>::split(va, ra);
+            VecW<T>::split(vb, rb);
+        } else {
+#pragma unroll
+            for (int e = 0; e < VW; ++e) ra[e] = rb[e] = T(0);
         }
-        b0[x * ld + b] = v;
+#pragma unroll
+        for (int e = 0; e < VW; ++e) b0[(xv * VW + e) * ld + b] = cmk(ra[e], rb[e]);
     }
     __syncthreads();
+    for (int i = threadIdx.x; i < PB * nv; i += blockDim.x) {
+        const int b = i / nv, xv = i - b * nv;
+        const int64_t pr = pr0 + b;
+        if (pr >= npairs) continue;
+        const int64_t z = pr / (Ly / 2);
+        const int y0 = 2 * (int)(pr - z * (Ly / 2));
+        const int64_t r0 = (z * Ly + y0) * Lx;
+        ((V *)(A + r0))[xv] = VecW<T>::zero();
+        ((V *)(A + r0 + Lx))[xv] = VecW<T>::zero();
+    }
     const C *res = fft_columns<C, false>(b0, b1, Lx, ld, PB, (const C *)p.tw[0]);
     C *S1 = (C *)p.S1;
     for (int i = threadIdx.x; i < PB * Kx; i += blockDim.x) {
@@ -314,16 +351,25 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
     __syncthreads();
     const C *res = fft_columns<C, true>(b0, b1, Lx, ld, PB, (const C *)p.tw[0]);
     T *G = (T *)p.gridB;
-    for (int i = threadIdx.x; i < PB * Lx; i += blockDim.x) {
-        const int b = i / Lx, x = i - b * Lx;
+    typedef typename VecW<T>::V V;
+    constexpr int VW = VecW<T>::W;
+    const int nv = Lx / VW;
+    for (int i = threadIdx.x; i < PB * nv; i += blockDim.x) {
+        const int b = i / nv, xv = i - b * nv;
         const int64_t pr = pr0 + b;
         if (pr >= npairs) continue;
         const int64_t z = pr / (Ly / 2);
         const int y0 = 2 * (int)(pr - z * (Ly / 2));
-        const int64_t r0 = (z * Ly + y0) * Lx + x;
-        const C v = res[x * ld + b];
-        G[r0] = v.x;
-        G[r0 + Lx] = v.y;
+        const int64_t r0 = (z * Ly + y0) * Lx;
+        T ra[VW], rb[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            const C v = res[(xv * VW + e) * ld + b];
+            ra[e] = v.x;
+            rb[e] = v.y;
+        }
+        ((V *)(G + r0))[xv] = VecW<T>::join(ra);
+        ((V *)(G + r0 + Lx))[xv] = VecW<T>::join(rb);
     }
 }
 

@@ -52,6 +52,11 @@ __global__ void __launch_bounds__(256) k_charges(DevPlan p, int kind, const T *_
 }
 
 // ---------------------------------------------------------------- spread
+// Each warp accumulates into its own copy of the halo tile, so the updates
+// are plain read-modify-writes: within one warp instruction every lane owns a
+// different (y, z) row of the source's window box, and consecutive sources of
+// a warp are ordered by __syncwarp.  The warp copies are summed in a fixed
+// order before the tile is added to the global grid.
 template <typename T, int M>
 __global__ void __launch_bounds__(256) k_spread(DevPlan p) {
     typedef typename VecT<T>::T4 T4;
@@ -60,13 +65,14 @@ __global__ void __launch_bounds__(256) k_spread(DevPlan p) {
     const int TE = p.TE;
     const int TE2 = TE * TE;
     const int TE3 = TE2 * TE;
-    T *tile = (T *)smem_raw;
-    T *wall = tile + ((TE3 + 3) & ~3);
+    const int TEP = (TE3 + 31) & ~31;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    T *wv = wall + warp * (3 * W);
+    T *tiles = (T *)smem_raw;
+    T *wv = tiles + (size_t)nwarps * TEP + warp * (3 * W);
+    T *my = tiles + (size_t)warp * TEP;
 
     const TileItem it = p.spread_items[blockIdx.x];
-    for (int i = threadIdx.x; i < TE3; i += blockDim.x) tile[i] = T(0);
+    for (int i = threadIdx.x; i < nwarps * TEP; i += blockDim.x) tiles[i] = T(0);
     __syncthreads();
 
     const T4 *src = (const T4 *)p.src_grid;
@@ -90,23 +96,31 @@ __global__ void __launch_bounds__(256) k_spread(DevPlan p) {
             wv[j] = kb_window(f + T(M - 1 - i), inv_m, beta, isb);
         }
         __syncwarp();
+        T wx[W];
+#pragma unroll
+        for (int ix = 0; ix < W; ++ix) wx[ix] = wv[ix];
         for (int pi = lane; pi < W * W; pi += 32) {
             const int iy = pi % W, iz = pi / W;
             const T wyz = qk * wv[2 * W + iz] * wv[W + iy];
-            T *row = tile + (lz + iz) * TE2 + (ly + iy) * TE + lx;
+            T *row = my + (lz + iz) * TE2 + (ly + iy) * TE + lx;
+            T r[W];
 #pragma unroll
-            for (int ix = 0; ix < W; ++ix) atomicAdd(row + ix, wyz * wv[ix]);
+            for (int ix = 0; ix < W; ++ix) r[ix] = row[ix];
+#pragma unroll
+            for (int ix = 0; ix < W; ++ix) row[ix] = r[ix] + wyz * wx[ix];
         }
         __syncwarp();
     }
     __syncthreads();
 
-    // add the tile (with wrap-around of the periodic grid) to the global grid
+    // sum the warp copies in order, then add the tile (with the periodic
+    // wrap-around) to the global grid
     const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
     const int gx0 = it.c0x - M + 1, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
     T *grid = (T *)p.gridA;
     for (int i = threadIdx.x; i < TE3; i += blockDim.x) {
-        const T v = tile[i];
+        T v = T(0);
+        for (int w = 0; w < nwarps; ++w) v += tiles[(size_t)w * TEP + i];
         if (v == T(0)) continue;
         const int iz = i / TE2;
         const int r = i - iz * TE2;
@@ -194,13 +208,24 @@ static size_t tile_smem_bytes(const DevPlan &p, size_t elem) {
     return (((TE3 + 3) & ~(size_t)3) + 8 * 3 * 2 * (size_t)p.m) * elem;
 }
 
+// warps per spread block: as many private tiles as fit in ~110 KB (two blocks per SM)
+static int spread_warps(const DevPlan &p, size_t elem) {
+    const size_t TE3 = (size_t)p.TE * p.TE * p.TE;
+    const size_t TEP = (TE3 + 31) & ~(size_t)31;
+    int nw = 8;
+    while (nw > 1 && nw * (TEP + 3 * 2 * (size_t)p.m) * elem > 110 * 1024) nw >>= 1;
+    return nw;
+}
+
 template <typename T, int M> static cudaError_t spread_t(const DevPlan &p, cudaStream_t s) {
-    const size_t sm = tile_smem_bytes(p, sizeof(T));
+    const int nw = spread_warps(p, sizeof(T));
+    const size_t TE3 = (size_t)p.TE * p.TE * p.TE;
+    const size_t sm = (nw * ((TE3 + 31) & ~(size_t)31) + nw * 3 * 2 * (size_t)M) * sizeof(T);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_spread<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    if (p.n_spread > 0) k_spread<T, M><<<p.n_spread, 256, sm, s>>>(p);
+    if (p.n_spread > 0) k_spread<T, M><<<p.n_spread, 32 * nw, sm, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -149,3 +149,130 @@ cudaError_t launch_near_reduce(const DevPlan &p, const int *blk_first, int nblk,
 }
 
 }  // namespace slp
+
+// =====================================================================
+// Precomputed near-field operator for nodal magnetisation input.
+//
+// With sigma_k = m(y_k) . n_j and m interpolated linearly from the vertices
+// (P1, Sec. 2.1), the near-field correction is linear in the nodal m:
+//   phi_i += sum_v W_iv . m_v,
+//   W_iv = sum_{k near x_i, v a vertex of tri(k)} w_k (N - N_s)(x_i - y_k) lambda_{s(k), a(v)} n_{j(k)}.
+// The paper precomputes the near-field integrals in the set-up phase and
+// applies them as a sparse matrix (Sec. 3.4); here W is assembled once per
+// plan on the GPU in FP64 (two passes: count, fill) and stored as one
+// 4-vector (W_x, W_y, W_z, vertex id) per non-zero, rows in sorted target
+// order.  Each evaluation is then a sparse product streamed from HBM.
+namespace slp {
+
+__device__ __forceinline__ double nm_kernel(const NMBuild &b, double dx, double dy, double dz, double r2) {
+    const double ri = rsqrt(r2);
+    if (b.kernel_mode == 2) {
+        const double kn = sep_factor(b.sep_h[0], b.sep_nh[0], dx / b.P[0]) *
+                          sep_factor(b.sep_h[1], b.sep_nh[1], dy / b.P[1]) *
+                          sep_factor(b.sep_h[2], b.sep_nh[2], dz / b.P[2]);
+        return (ri - b.sep_A4pi * kn) * 0.079577471545947667884;
+    }
+    return erfc(r2 * ri * b.inv_s_sqrt2) * ri * 0.079577471545947667884;
+}
+
+// pass 0: count non-zeros per row (and near pairs); pass 1: fill.
+template <typename T4>
+__global__ void __launch_bounds__(256) k_nm_build(NMBuild b, int pass, int64_t *__restrict__ counts,
+                                                  int64_t *__restrict__ pairs, const int64_t *__restrict__ rowptr,
+                                                  T4 *__restrict__ val) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 8 + warp;
+    if (t >= b.N) return;
+    const double4 xt = b.tgt[t];
+    const int blk = b.tgt_block[t];
+    int64_t out = pass == 1 ? rowptr[t] : 0;
+    int64_t cnt = 0, npairs = 0;
+    for (int r = b.blk_r0[blk]; r < b.blk_r0[blk + 1]; ++r) {
+        const int2 rg = b.ranges[r];
+        for (int u0 = rg.x; u0 < rg.y; u0 += 32) {
+            const int u = u0 + lane;
+            double wx = 0.0, wy = 0.0, wz = 0.0;
+            int v = -1;
+            if (u < rg.y) {
+                v = b.tgt_perm[u];
+                for (int e = b.vt_ptr[v]; e < b.vt_ptr[v + 1]; ++e) {
+                    const int ent = b.vt_ent[e];
+                    const int j = ent >> 2, a = ent & 3;
+                    const double4 n = b.nrm[j];
+                    double acc = 0.0;
+                    for (int s = 0; s < b.q; ++s) {
+                        const double4 y = b.src[(int64_t)j * b.q + s];
+                        const double dx = xt.x - y.x, dy = xt.y - y.y, dz = xt.z - y.z;
+                        const double r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < b.eps2 && r2 > 0.0) {
+                            acc += y.w * nm_kernel(b, dx, dy, dz, r2) * b.lam[3 * s + a];
+                            if (a == 0) ++npairs;
+                        }
+                    }
+                    wx += acc * n.x;
+                    wy += acc * n.y;
+                    wz += acc * n.z;
+                }
+            }
+            const bool nz = (v >= 0) && (wx != 0.0 || wy != 0.0 || wz != 0.0);
+            const unsigned bal = __ballot_sync(0xffffffffu, nz);
+            if (pass == 1 && nz) {
+                const int pos = __popc(bal & ((1u << lane) - 1u));
+                T4 o;
+                o.x = wx;
+                o.y = wy;
+                o.z = wz;
+                o.w = pack_id(o.w, v);  // vertex id in the fourth component
+                val[out + cnt + pos] = o;
+            }
+            cnt += __popc(bal);
+        }
+    }
+    npairs = warp_sum((long long)npairs);
+    if (pass == 0 && lane == 0) {
+        counts[t] = cnt;
+        pairs[t] = npairs;
+    }
+}
+
+cudaError_t launch_nm_build(const NMBuild &b, int pass, int prec, int64_t *counts, int64_t *pairs,
+                            const int64_t *rowptr, void *val, cudaStream_t s) {
+    const unsigned nb = (unsigned)((b.N + 7) / 8);
+    if (prec == 64)
+        k_nm_build<double4><<<nb, 256, 0, s>>>(b, pass, counts, pairs, rowptr, (double4 *)val);
+    else
+        k_nm_build<float4><<<nb, 256, 0, s>>>(b, pass, counts, pairs, rowptr, (float4 *)val);
+    return cudaGetLastError();
+}
+
+// phi[perm[t]] += sum_e W_e . m[col_e] over row t (sorted target order); one
+// warp per row, rows read front to back, lanes combined in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_near_matrix(DevPlan p, const T *__restrict__ m, T *__restrict__ phi) {
+    typedef typename VecT<T>::T4 T4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 8 + warp;
+    if (t >= p.N) return;
+    const T4 *val = (const T4 *)p.nm_val;
+    const int64_t e0 = p.nm_rowptr[t], e1 = p.nm_rowptr[t + 1];
+    T acc = T(0);
+    for (int64_t e = e0 + lane; e < e1; e += 32) {
+        const T4 w = val[e];
+        const int64_t v = (int64_t)packed_cell(w.w);
+        acc += w.x * m[3 * v] + w.y * m[3 * v + 1] + w.z * m[3 * v + 2];
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) phi[p.tgt_perm[t]] += acc;
+}
+
+cudaError_t launch_near_matrix(const DevPlan &p, const void *d_m, void *d_phi, cudaStream_t s) {
+    if (p.N == 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((p.N + 7) / 8);
+    if (p.prec == 64)
+        k_near_matrix<double><<<nb, 256, 0, s>>>(p, (const double *)d_m, (double *)d_phi);
+    else
+        k_near_matrix<float><<<nb, 256, 0, s>>>(p, (const float *)d_m, (float *)d_phi);
+    return cudaGetLastError();
+}
+
+}  // namespace slp

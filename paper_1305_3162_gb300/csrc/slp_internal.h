@@ -96,6 +96,33 @@ cudaError_t launch_near(const DevPlan &p, void *d_phi, cudaStream_t s);
 cudaError_t launch_near_reduce(const DevPlan &p, const int *blk_first, int nblk, void *d_phi, cudaStream_t s);
 cudaError_t launch_zero(void *ptr, size_t bytes, cudaStream_t s);
 
+// Precomputed near-field operator (k_near.cu): inputs of the plan-time
+// assembly of W (FP64, temporary device arrays).
+struct NMBuild {
+    const double4 *tgt;      // [N] sorted targets, physical coordinates relative to the torus centre
+    const int *tgt_perm;     // [N] sorted -> user vertex
+    const int *tgt_block;    // [N] target block of each sorted target
+    const int *blk_r0;       // [nblk + 1] range list of each block
+    const int2 *ranges;      // candidate vertex ranges (sorted target order)
+    const int *vt_ptr;       // [NV + 1] vertex -> adjacency entries
+    const int *vt_ent;       // triangle * 4 + local vertex index
+    const double4 *src;      // [Q] user-order quadrature points (x, y, z relative to the centre, w_k)
+    const double4 *nrm;      // [M] outward unit normals
+    const double *lam;       // [q * 3]
+    int q;
+    int64_t N;
+    double eps2;
+    double inv_s_sqrt2;
+    int kernel_mode;
+    const double *sep_h[3];
+    int sep_nh[3];
+    double sep_A4pi;         // 4 pi A
+    double P[3];
+};
+cudaError_t launch_nm_build(const NMBuild &b, int pass, int prec, int64_t *counts, int64_t *pairs,
+                            const int64_t *rowptr, void *val, cudaStream_t s);
+cudaError_t launch_near_matrix(const DevPlan &p, const void *d_m, void *d_phi, cudaStream_t s);
+
 // Set the thread-local text returned by slp_last_error().
 void set_last_error(const char *msg);
 

@@ -196,6 +196,8 @@ struct slp_plan_s {
     void *d_stage_in = nullptr, *d_stage_phi = nullptr;
     int *d_blk_first = nullptr;
     int launches_per_eval = 0;
+    int64_t near_pairs_within = -1;
+    int64_t nm_nnz = 0;
 };
 
 namespace {
@@ -435,10 +437,11 @@ slp_status choose_parameters(slp_plan_s &p) {
     for (int d = 0; d < 3; ++d)
         if (!(p.P[d] > p.D[d])) return fail(SLP_ERR_INVALID_ARG, "period does not contain the mesh");
 
-    // tile size: keep the halo tile within 96 KB of shared memory
+    // tile size: a halo tile of at most 28 KB, so the spread can give several
+    // warps a private copy each
     const size_t esz = p.prec == 64 ? 8 : 4;
     p.TS = 8;
-    while (p.TS > 2 && std::pow((double)(p.TS + 2 * p.m - 1), 3) * esz > 96 * 1024) p.TS /= 2;
+    while (p.TS > 2 && std::pow((double)(p.TS + 2 * p.m - 1), 3) * esz > 28 * 1024) p.TS /= 2;
     p.TE = p.TS + 2 * p.m - 1;
     return SLP_OK;
 }
@@ -890,6 +893,223 @@ void free_device(slp_plan_s &p) {
     cudaSetDevice(prev);
 }
 
+slp_status cuda_status(cudaError_t e, const char *what);
+
+// Temporary device buffer released at scope exit (plan-time only).
+struct TmpBuf {
+    void *p = nullptr;
+    ~TmpBuf() {
+        if (p) cudaFree(p);
+    }
+};
+
+template <typename S> slp_status tmp_upload(TmpBuf &b, const S *src, size_t n) {
+    const size_t bytes = std::max<size_t>(16, n * sizeof(S));
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? SLP_ERR_OOM : SLP_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    if (n && cudaMemcpy(b.p, src, n * sizeof(S), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(SLP_ERR_CUDA, "cudaMemcpy failed");
+    return SLP_OK;
+}
+
+// Assemble the vertex-based near-field operator W (see k_near.cu) on the
+// device.  Candidate vertices of each target block: aligned 2x2x2-cell bins
+// of the sorted targets whose bounding box lies within eps + r_adj of the
+// block, r_adj being the largest distance from a vertex to a quadrature point
+// of an adjacent triangle.  Returns SLP_OK without building when the matrix
+// would exceed the memory budget (near_mode stays ON_THE_FLY).
+slp_status build_near_matrix(slp_plan_s &p, const std::vector<uint64_t> &tkeys) {
+    const int64_t N = p.N, M = p.M, q = p.q;
+    // vertex -> adjacent (triangle, local vertex)
+    std::vector<int> vt_ptr(N + 1, 0), vt_ent(3 * M);
+    for (int64_t j = 0; j < M; ++j)
+        for (int a = 0; a < 3; ++a) vt_ptr[p.T[3 * j + a] + 1]++;
+    for (int64_t i = 0; i < N; ++i) vt_ptr[i + 1] += vt_ptr[i];
+    {
+        std::vector<int> fillc(vt_ptr.begin(), vt_ptr.end() - 1);
+        for (int64_t j = 0; j < M; ++j)
+            for (int a = 0; a < 3; ++a) vt_ent[fillc[p.T[3 * j + a]]++] = (int)(j * 4 + a);
+    }
+    double r_adj = 0.0;
+    for (int64_t j = 0; j < M; ++j)
+        for (int a = 0; a < 3; ++a) {
+            const double *v = &p.V[3 * p.T[3 * j + a]];
+            for (int s2 = 0; s2 < q; ++s2) {
+                const double *y = &p.y[3 * (j * q + s2)];
+                const double d = std::sqrt((v[0] - y[0]) * (v[0] - y[0]) + (v[1] - y[1]) * (v[1] - y[1]) +
+                                           (v[2] - y[2]) * (v[2] - y[2]));
+                r_adj = std::max(r_adj, d);
+            }
+        }
+    const bool all_pairs = p.kernel_mode == SLP_KERNEL_SEPARABLE || !(p.eps < p.diam);
+    const double rad = all_pairs ? INFINITY : p.eps + r_adj * (1.0 + 1e-9) + 1e-12 * p.diam;
+
+    // target physical positions (sorted, relative to the centre)
+    std::vector<double4> tgt(N);
+    for (int64_t i = 0; i < N; ++i) {
+        const double *v = &p.V[3 * (int64_t)p.tgt_perm[i]];
+        tgt[i] = make_double4(v[0] - p.ctr[0], v[1] - p.ctr[1], v[2] - p.ctr[2], 0.0);
+    }
+    // target blocks (as in the near-field work list)
+    const int nblk = (int)p.near_blk_first.size() - 1;
+    std::vector<int> tgt_block(N, 0), blk_r0(nblk + 1, 0);
+    std::vector<int2> ranges;
+    struct Bin {
+        int b, e;
+        double lo[3], hi[3];
+    };
+    std::vector<Bin> bins;
+    std::unordered_map<uint64_t, int> bin_of;
+    if (!all_pairs) {
+        for (int64_t i = 0; i < N;) {
+            int64_t j = i;
+            const uint64_t bk = tkeys[i] >> 3;
+            while (j < N && (tkeys[j] >> 3) == bk) ++j;
+            Bin bn;
+            bn.b = (int)i;
+            bn.e = (int)j;
+            for (int d = 0; d < 3; ++d) {
+                bn.lo[d] = 1e300;
+                bn.hi[d] = -1e300;
+            }
+            for (int64_t k = i; k < j; ++k) {
+                const double x[3] = {tgt[k].x, tgt[k].y, tgt[k].z};
+                for (int d = 0; d < 3; ++d) {
+                    bn.lo[d] = std::min(bn.lo[d], x[d]);
+                    bn.hi[d] = std::max(bn.hi[d], x[d]);
+                }
+            }
+            const uint32_t packed = (uint32_t)p.tgt_grid[4 * i + 3];
+            const uint64_t bx = (packed & 1023) / 2, by = ((packed >> 10) & 1023) / 2, bz = ((packed >> 20) & 1023) / 2;
+            bin_of[(bz << 40) | (by << 20) | bx] = (int)bins.size();
+            bins.push_back(bn);
+            i = j;
+        }
+    }
+    std::vector<int> found;
+    for (int b = 0; b < nblk; ++b) {
+        const slp::NearItem &it = p.near_items[p.near_blk_first[b]];
+        for (int t = it.tbegin; t < it.tbegin + it.tcount; ++t) tgt_block[t] = b;
+        blk_r0[b] = (int)ranges.size();
+        if (all_pairs) {
+            ranges.push_back(make_int2(0, (int)N));
+            continue;
+        }
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int t = it.tbegin; t < it.tbegin + it.tcount; ++t) {
+            const double x[3] = {tgt[t].x, tgt[t].y, tgt[t].z};
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], x[d]);
+                hi[d] = std::max(hi[d], x[d]);
+            }
+        }
+        int b0[3], b1[3];
+        for (int d = 0; d < 3; ++d) {
+            const double h = p.P[d] / p.L[d];
+            const double u0 = (lo[d] - rad) / h + 0.5 * p.L[d], u1 = (hi[d] + rad) / h + 0.5 * p.L[d];
+            b0[d] = std::max(0, (int)std::floor(u0) - 1) / 2;
+            b1[d] = std::min(p.L[d] - 1, (int)std::floor(u1) + 1) / 2;
+        }
+        found.clear();
+        for (int bz = b0[2]; bz <= b1[2]; ++bz)
+            for (int by = b0[1]; by <= b1[1]; ++by)
+                for (int bx = b0[0]; bx <= b1[0]; ++bx) {
+                    auto itb = bin_of.find(((uint64_t)bz << 40) | ((uint64_t)by << 20) | (uint64_t)bx);
+                    if (itb == bin_of.end()) continue;
+                    const Bin &bn = bins[itb->second];
+                    double d2 = 0;
+                    for (int d = 0; d < 3; ++d) {
+                        const double g = std::max(0.0, std::max(bn.lo[d] - hi[d], lo[d] - bn.hi[d]));
+                        d2 += g * g;
+                    }
+                    if (d2 <= rad * rad) found.push_back(itb->second);
+                }
+        std::sort(found.begin(), found.end(), [&](int a2, int b2) { return bins[a2].b < bins[b2].b; });
+        for (int f : found) {
+            if ((int)ranges.size() > blk_r0[b] && ranges.back().y == bins[f].b)
+                ranges.back().y = bins[f].e;
+            else
+                ranges.push_back(make_int2(bins[f].b, bins[f].e));
+        }
+    }
+    blk_r0[nblk] = (int)ranges.size();
+
+    // device inputs
+    std::vector<double4> src(p.Q), nrm(M);
+    for (int64_t k = 0; k < p.Q; ++k)
+        src[k] = make_double4(p.y[3 * k] - p.ctr[0], p.y[3 * k + 1] - p.ctr[1], p.y[3 * k + 2] - p.ctr[2], p.wk[k]);
+    for (int64_t j = 0; j < M; ++j) nrm[j] = make_double4(p.nrm[3 * j], p.nrm[3 * j + 1], p.nrm[3 * j + 2], 0.0);
+    TmpBuf b_tgt, b_blk, b_r0, b_rng, b_vtp, b_vte, b_src, b_nrm, b_lam, b_h[3], b_cnt, b_pairs;
+    TRY(tmp_upload(b_tgt, tgt.data(), tgt.size()));
+    TRY(tmp_upload(b_blk, tgt_block.data(), tgt_block.size()));
+    TRY(tmp_upload(b_r0, blk_r0.data(), blk_r0.size()));
+    TRY(tmp_upload(b_rng, ranges.data(), ranges.size()));
+    TRY(tmp_upload(b_vtp, vt_ptr.data(), vt_ptr.size()));
+    TRY(tmp_upload(b_vte, vt_ent.data(), vt_ent.size()));
+    TRY(tmp_upload(b_src, src.data(), src.size()));
+    TRY(tmp_upload(b_nrm, nrm.data(), nrm.size()));
+    TRY(tmp_upload(b_lam, p.lam.data(), p.lam.size()));
+    std::vector<int64_t> zeros(N + 1, 0);
+    TRY(tmp_upload(b_cnt, zeros.data(), zeros.size()));
+    TRY(tmp_upload(b_pairs, zeros.data(), zeros.size()));
+    slp::NMBuild nb;
+    memset(&nb, 0, sizeof nb);
+    nb.tgt = (const double4 *)b_tgt.p;
+    nb.tgt_perm = p.dp.tgt_perm;
+    nb.tgt_block = (const int *)b_blk.p;
+    nb.blk_r0 = (const int *)b_r0.p;
+    nb.ranges = (const int2 *)b_rng.p;
+    nb.vt_ptr = (const int *)b_vtp.p;
+    nb.vt_ent = (const int *)b_vte.p;
+    nb.src = (const double4 *)b_src.p;
+    nb.nrm = (const double4 *)b_nrm.p;
+    nb.lam = (const double *)b_lam.p;
+    nb.q = p.q;
+    nb.N = N;
+    nb.eps2 = std::isfinite(p.eps) ? p.eps * p.eps : 1e300;
+    nb.inv_s_sqrt2 = p.sigma_g > 0 ? 1.0 / (p.sigma_g * std::sqrt(2.0)) : 0.0;
+    nb.kernel_mode = p.kernel_mode;
+    if (p.kernel_mode == SLP_KERNEL_SEPARABLE) {
+        for (int a = 0; a < 3; ++a) {
+            TRY(tmp_upload(b_h[a], p.sep_h[a].data(), p.sep_h[a].size()));
+            nb.sep_h[a] = (const double *)b_h[a].p;
+            nb.sep_nh[a] = (int)p.sep_h[a].size();
+        }
+        nb.sep_A4pi = 4.0 * PI * p.sep_A;
+    }
+    for (int a = 0; a < 3; ++a) nb.P[a] = p.P[a];
+    TRY(cuda_status(slp::launch_nm_build(nb, 0, p.prec, (int64_t *)b_cnt.p, (int64_t *)b_pairs.p, nullptr, nullptr, 0),
+                    "near matrix count"));
+    std::vector<int64_t> cnt(N), prs(N);
+    TRY(cuda_status(cudaMemcpy(cnt.data(), b_cnt.p, sizeof(int64_t) * N, cudaMemcpyDeviceToHost), "count copy"));
+    TRY(cuda_status(cudaMemcpy(prs.data(), b_pairs.p, sizeof(int64_t) * N, cudaMemcpyDeviceToHost), "pairs copy"));
+    std::vector<int64_t> rowptr(N + 1, 0);
+    for (int64_t i = 0; i < N; ++i) rowptr[i + 1] = rowptr[i] + cnt[i];
+    const int64_t nnz = rowptr[N];
+    p.near_pairs_within = 0;
+    for (int64_t i = 0; i < N; ++i) p.near_pairs_within += prs[i];
+    const size_t vbytes = (size_t)nnz * (p.prec == 64 ? 32 : 16);
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    if (vbytes > ((size_t)8 << 30) || vbytes > freeb / 2) return SLP_OK;  // budget: keep the on-the-fly near field
+    void *ptr = nullptr;
+    TRY(upload(p, &ptr, rowptr.data(), rowptr.size()));
+    p.dp.nm_rowptr = (const int64_t *)ptr;
+    TRY(dalloc(p, &ptr, vbytes));
+    p.dp.nm_val = ptr;
+    TRY(cuda_status(slp::launch_nm_build(nb, 1, p.prec, nullptr, nullptr, p.dp.nm_rowptr, ptr, 0), "near matrix fill"));
+    TRY(cuda_status(cudaDeviceSynchronize(), "near matrix build"));
+    p.dp.nm_nnz = nnz;
+    p.nm_nnz = nnz;
+    p.near_mode = SLP_NEAR_PRECOMPUTED;
+    return SLP_OK;
+}
+
 slp_status cuda_status(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return SLP_OK;
     return fail(SLP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -935,6 +1155,13 @@ slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, 
     TRY(cuda_status(slp::launch_gather(d, d_phi, s), "gather"));
     rec();
     if (last <= SLP_STAGE_GATHER) return SLP_OK;
+    const bool use_matrix = kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
+    if (use_matrix) {
+        TRY(cuda_status(slp::launch_near_matrix(d, d_in, d_phi, s), "near-field matrix"));
+        rec();
+        rec();
+        return SLP_OK;
+    }
     TRY(cuda_status(slp::launch_near(d, d_phi, s), "near field"));
     rec();
     if (p.opts.deterministic)
@@ -1018,7 +1245,12 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
     std::vector<uint64_t> skeys, tkeys;
     sort_points(*p, p->y.data(), p->Q, p->src_perm, p->src_grid, skeys);
     sort_points(*p, p->V.data(), p->N, p->tgt_perm, p->tgt_grid, tkeys);
-    tile_items(*p, p->src_grid, skeys, p->Q, 1024, p->spread_items);
+    {
+        // spread chunk: about four items per SM, 128..1024 sources, a multiple of 32
+        int64_t ch = (p->Q + 152 * 4 - 1) / (152 * 4);
+        ch = std::max<int64_t>(128, std::min<int64_t>(1024, (ch + 31) / 32 * 32));
+        tile_items(*p, p->src_grid, skeys, p->Q, (int)ch, p->spread_items);
+    }
     tile_items(*p, p->tgt_grid, tkeys, p->N, 256, p->gather_items);
     near_items(*p, skeys, tkeys);
     build_dtab(*p);
@@ -1033,6 +1265,7 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
         }
         DeviceGuard g(p->device);
         st = p->prec == 64 ? upload_all<double>(*p) : upload_all<float>(*p);
+        if (st == SLP_OK && o.near_mode != SLP_NEAR_ON_THE_FLY) st = build_near_matrix(*p, tkeys);
         if (st != SLP_OK) {
             free_device(*p);
             delete p;
@@ -1091,8 +1324,8 @@ slp_status slp_query(slp_plan_t p, slp_info *info) {
     info->eps_near = p->eps;
     info->tolerance = p->tol;
     info->near_pairs = p->near_pairs;
-    info->near_pairs_within = -1;
-    info->near_matrix_nnz = 0;
+    info->near_pairs_within = p->near_pairs_within;
+    info->near_matrix_nnz = p->nm_nnz;
     info->bytes_device = p->bytes_device;
     info->n_spread_items = (int64_t)p->spread_items.size();
     info->n_gather_items = (int64_t)p->gather_items.size();

@@ -143,3 +143,42 @@ def test_plate_workload_sampled():
         assert rel_l2(phi[sel], ref) <= 1e-5
     finally:
         slp.slp_destroy(plan)
+
+
+@pytest.mark.parametrize("prec,tol", [(32, 1e-5), (64, 1e-10)])
+def test_near_field_modes_agree(prec, tol):
+    """Nodal input: the precomputed vertex-based near-field operator and the
+    per-evaluation near field give the same potential, both within the
+    tolerance of the oracle."""
+    slp = lib()
+    V, T = meshes.icosphere(4)
+    m = fields.vortex(V, 31)
+    ref = oracle.slp_nodal(V, T, 7, m)
+    out = {}
+    for mode in (slp.SLP_NEAR_PRECOMPUTED, slp.SLP_NEAR_ON_THE_FLY):
+        plan = _plan(slp, V, T, 7, tol, prec, (64, 64, 64), near_mode=mode)
+        try:
+            info = slp.slp_query(plan)
+            assert info["near_mode"] == mode
+            if mode == slp.SLP_NEAR_PRECOMPUTED:
+                assert info["near_matrix_nnz"] > 0
+                assert 0 < info["near_pairs_within"] <= info["near_pairs"]
+            out[mode] = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, m, prec)
+            assert rel_l2(out[mode], ref) <= tol
+        finally:
+            slp.slp_destroy(plan)
+    assert rel_l2(out[slp.SLP_NEAR_PRECOMPUTED], out[slp.SLP_NEAR_ON_THE_FLY]) <= tol
+
+
+def test_separable_mode_precomputed_near_field():
+    """All-pairs separable kernel with the precomputed operator (cube, FP64)."""
+    slp = lib()
+    w = workloads.cube()
+    plan = _plan(slp, w.V, w.T, w.quad, w.tolerance, 64, w.grid, near_mode=slp.SLP_NEAR_PRECOMPUTED)
+    try:
+        info = slp.slp_query(plan)
+        assert info["kernel_mode"] == slp.SLP_KERNEL_SEPARABLE and info["near_mode"] == slp.SLP_NEAR_PRECOMPUTED
+        phi = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, w.m_nodal, 64)
+        assert rel_l2(phi, oracle.slp_nodal(w.V, w.T, w.quad, w.m_nodal)) <= 1e-10
+    finally:
+        slp.slp_destroy(plan)
