@@ -62,7 +62,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         o = os.path.join(OBJ, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+            cmd = [nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-diag-suppress", "1444",
                    "-I", INCLUDE, "-c", s, "-o", o]
             jobs.append(cmd)
     for src in CPP_SOURCES:

@@ -73,6 +73,25 @@ __device__ __forceinline__ double kb_window(double d, double inv_m, double beta,
     return r * inv_sinh_beta;
 }
 
+// Block-wide copy of `total` elements with up to 8 independent loads in
+// flight per thread: ld(i) reads element i, st(i, v) stores it.
+template <typename V, typename LoadF, typename StoreF>
+__device__ __forceinline__ void pipelined_copy(int total, LoadF ld, StoreF st) {
+    for (int base = threadIdx.x; base < total; base += 8 * blockDim.x) {
+        V tmp[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int i = base + r * blockDim.x;
+            if (i < total) tmp[r] = ld(i);
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int i = base + r * blockDim.x;
+            if (i < total) st(i, tmp[r]);
+        }
+    }
+}
+
 // warp sum
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll

@@ -83,32 +83,37 @@ template <typename C, int R, bool INV> __device__ __forceinline__ void dftR(C *v
     if constexpr (R == 8) dft8<C, INV>(v);
 }
 
-// One radix-R Stockham stage on B columns of length L.
+// One radix-R Stockham stage on B columns of length L (all powers of two,
+// passed as log2 so the index arithmetic is shifts and masks).
 // Column b, element j lives at buf[j * ld + b].  tw[t] = exp(-2 pi i t / L).
 template <typename C, int R, bool INV>
-__device__ __forceinline__ void stockham_stage(const C *__restrict__ src, C *__restrict__ dst, int L, int Ns,
-                                               int ld, int B, const C *__restrict__ tw) {
-    const int nj = L / R;
-    const int tstep = L / (Ns * R);
-    for (int w = threadIdx.x; w < nj * B; w += blockDim.x) {
-        const int b = w % B;
-        const int j = w / B;
-        const int k = j & (Ns - 1);
+__device__ __forceinline__ void stockham_stage(const C *__restrict__ src, C *__restrict__ dst, int lgL, int lgNs,
+                                               int ld, int lgB, const C *__restrict__ tw) {
+    constexpr int LGR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+    const int L = 1 << lgL;
+    const int nj = L >> LGR;
+    const int lgt = lgL - lgNs - LGR;  // log2 of the twiddle stride L / (Ns R)
+    const int Bm = (1 << lgB) - 1, Nm = (1 << lgNs) - 1;
+    const int total = nj << lgB;
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int b = w & Bm;
+        const int j = w >> lgB;
+        const int k = j & Nm;
         C v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = src[(j + r * nj) * ld + b];
-        if (Ns > 1) {
+        if (lgNs > 0) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C t = tw[(r * k * tstep) & (L - 1)];
+                C t = tw[((r * k) << lgt) & (L - 1)];
                 if (INV) t.y = -t.y;
                 v[r] = cmul(v[r], t);
             }
         }
         dftR<C, R, INV>(v);
-        const int base = (j - k) * R + k;
+        const int base = ((j - k) << LGR) + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[(base + r * Ns) * ld + b] = v[r];
+        for (int r = 0; r < R; ++r) dst[(base + (r << lgNs)) * ld + b] = v[r];
     }
 }
 
@@ -117,19 +122,20 @@ __device__ __forceinline__ void stockham_stage(const C *__restrict__ src, C *__r
 template <typename C, bool INV>
 __device__ C *fft_columns(C *b0, C *b1, int L, int ld, int B, const C *__restrict__ tw) {
     const int lg = __ffs(L) - 1;
+    const int lgB = __ffs(B) - 1;
     const int n8 = lg / 3, rem = lg - 3 * n8;
-    int Ns = 1;
+    int lgNs = 0;
     C *src = b0, *dst = b1;
     for (int st = 0; st < n8 + (rem ? 1 : 0); ++st) {
         if (st < n8) {
-            stockham_stage<C, 8, INV>(src, dst, L, Ns, ld, B, tw);
-            Ns *= 8;
+            stockham_stage<C, 8, INV>(src, dst, lg, lgNs, ld, lgB, tw);
+            lgNs += 3;
         } else if (rem == 2) {
-            stockham_stage<C, 4, INV>(src, dst, L, Ns, ld, B, tw);
-            Ns *= 4;
+            stockham_stage<C, 4, INV>(src, dst, lg, lgNs, ld, lgB, tw);
+            lgNs += 2;
         } else {
-            stockham_stage<C, 2, INV>(src, dst, L, Ns, ld, B, tw);
-            Ns *= 2;
+            stockham_stage<C, 2, INV>(src, dst, lg, lgNs, ld, lgB, tw);
+            lgNs += 1;
         }
         __syncthreads();
         C *t = src;
@@ -147,6 +153,7 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2], Kx = p.Kx;
     const int ld = PB + 1;
+    const int lgLx = __ffs(Lx) - 1, lgKx = __ffs(Kx) - 1, lgHy = __ffs(Ly) - 2;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Lx * ld;
     const int64_t npairs = (int64_t)Lz * (Ly / 2);
@@ -156,14 +163,15 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     // issued before the zeroing stores so they overlap
     typedef typename VecW<T>::V V;
     constexpr int VW = VecW<T>::W;
+    constexpr int lgVW = VW == 4 ? 2 : 1;
     const int nv = Lx / VW;
     for (int i = threadIdx.x; i < PB * nv; i += blockDim.x) {
-        const int b = i / nv, xv = i - b * nv;
+        const int b = i >> (lgLx - lgVW), xv = i & (nv - 1);
         const int64_t pr = pr0 + b;
         T ra[VW], rb[VW];
         if (pr < npairs) {
-            const int64_t z = pr / (Ly / 2);
-            const int y0 = 2 * (int)(pr - z * (Ly / 2));
+            const int64_t z = pr >> lgHy;
+            const int y0 = 2 * (int)(pr & ((Ly >> 1) - 1));
             const int64_t r0 = (z * Ly + y0) * Lx;
             const V va = ((const V *)(A + r0))[xv];
             const V vb = ((const V *)(A + r0 + Lx))[xv];
@@ -178,11 +186,11 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     }
     __syncthreads();
     for (int i = threadIdx.x; i < PB * nv; i += blockDim.x) {
-        const int b = i / nv, xv = i - b * nv;
+        const int b = i >> (lgLx - lgVW), xv = i & (nv - 1);
         const int64_t pr = pr0 + b;
         if (pr >= npairs) continue;
-        const int64_t z = pr / (Ly / 2);
-        const int y0 = 2 * (int)(pr - z * (Ly / 2));
+        const int64_t z = pr >> lgHy;
+        const int y0 = 2 * (int)(pr & ((Ly >> 1) - 1));
         const int64_t r0 = (z * Ly + y0) * Lx;
         ((V *)(A + r0))[xv] = VecW<T>::zero();
         ((V *)(A + r0 + Lx))[xv] = VecW<T>::zero();
@@ -190,11 +198,11 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     const C *res = fft_columns<C, false>(b0, b1, Lx, ld, PB, (const C *)p.tw[0]);
     C *S1 = (C *)p.S1;
     for (int i = threadIdx.x; i < PB * Kx; i += blockDim.x) {
-        const int b = i / Kx, k = i - b * Kx;
+        const int b = i >> lgKx, k = i & (Kx - 1);
         const int64_t pr = pr0 + b;
         if (pr >= npairs) continue;
-        const int64_t z = pr / (Ly / 2);
-        const int y0 = 2 * (int)(pr - z * (Ly / 2));
+        const int64_t z = pr >> lgHy;
+        const int y0 = 2 * (int)(pr & ((Ly >> 1) - 1));
         const C Z = res[k * ld + b];
         const C Zc = cconj(res[((Lx - k) & (Lx - 1)) * ld + b]);
         const C xa = cscale(cadd(Z, Zc), T(0.5));
@@ -213,21 +221,21 @@ __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
     const int ld = B + 1;
+    const int lgB = __ffs(B) - 1;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Ly * ld;
     const int ntile = Kx / B;
     const int z = blockIdx.x / ntile;
     const int kx0 = (blockIdx.x - z * ntile) * B;
     const C *S1 = (const C *)p.S1 + (int64_t)z * Ly * Kx + kx0;
-    for (int i = threadIdx.x; i < Ly * B; i += blockDim.x) {
-        const int y = i / B, b = i - y * B;
-        b0[y * ld + b] = S1[(int64_t)y * Kx + b];
-    }
+    pipelined_copy<C>(
+        Ly * B, [&](int i) { return S1[(int64_t)(i >> lgB) * Kx + (i & (B - 1))]; },
+        [&](int i, C v) { b0[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
     const C *res = fft_columns<C, false>(b0, b1, Ly, ld, B, (const C *)p.tw[1]);
     C *S2 = (C *)p.S2 + (int64_t)z * ny * Kx + kx0;
     for (int i = threadIdx.x; i < ny * B; i += blockDim.x) {
-        const int kp = i / B, b = i - kp * B;
+        const int kp = i >> lgB, b = i & (B - 1);
         C v = cmk(T(0), T(0));
         if (kp < ny / 2)
             v = res[kp * ld + b];
@@ -245,6 +253,7 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lz = p.L[2], Kx = p.Kx, ny = p.n[1], nz = p.n[2];
     const int ld = B + 1;
+    const int lgB = __ffs(B) - 1;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Lz * ld;
     const int ntile = Kx / B;
@@ -254,22 +263,21 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
     const int64_t zs = (int64_t)ny * Kx;
     if (kp == ny / 2) {  // Nyquist row in y: dropped
         for (int i = threadIdx.x; i < Lz * B; i += blockDim.x) {
-            const int z = i / B, b = i - z * B;
+            const int z = i >> lgB, b = i & (B - 1);
             S2[z * zs + b] = cmk(T(0), T(0));
         }
         return;
     }
-    for (int i = threadIdx.x; i < Lz * B; i += blockDim.x) {
-        const int z = i / B, b = i - z * B;
-        b0[z * ld + b] = S2[z * zs + b];
-    }
+    pipelined_copy<C>(
+        Lz * B, [&](int i) { return S2[(i >> lgB) * zs + (i & (B - 1))]; },
+        [&](int i, C v) { b0[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
     C *res = fft_columns<C, false>(b0, b1, Lz, ld, B, (const C *)p.tw[2]);
     C *oth = (res == b0) ? b1 : b0;
     const int aky = kp < ny / 2 ? kp : ny - kp;
     const T *D = (const T *)p.Dtab;
     for (int i = threadIdx.x; i < Lz * B; i += blockDim.x) {
-        const int kz = i / B, b = i - kz * B;
+        const int kz = i >> lgB, b = i & (B - 1);
         const int kzs = kz < Lz / 2 ? kz : kz - Lz;
         const int akz = kzs < 0 ? -kzs : kzs;
         C v = cmk(T(0), T(0));
@@ -282,7 +290,7 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
     __syncthreads();
     const C *out = fft_columns<C, true>(res, oth, Lz, ld, B, (const C *)p.tw[2]);
     for (int i = threadIdx.x; i < Lz * B; i += blockDim.x) {
-        const int z = i / B, b = i - z * B;
+        const int z = i >> lgB, b = i & (B - 1);
         S2[z * zs + b] = out[z * ld + b];
     }
 }
@@ -294,27 +302,31 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
     const int ld = B + 1;
+    const int lgB = __ffs(B) - 1;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Ly * ld;
     const int ntile = Kx / B;
     const int z = blockIdx.x / ntile;
     const int kx0 = (blockIdx.x - z * ntile) * B;
     const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx + kx0;
-    for (int i = threadIdx.x; i < Ly * B; i += blockDim.x) {
-        const int y = i / B, b = i - y * B;
-        // position y holds mode y (y < ny/2), or mode y - Ly (y > Ly - ny/2), else zero
-        C v = cmk(T(0), T(0));
-        if (y < ny / 2)
-            v = S2[(int64_t)y * Kx + b];
-        else if (y > Ly - ny / 2)
-            v = S2[(int64_t)(y - Ly + ny) * Kx + b];
-        b0[y * ld + b] = v;
-    }
+    // position y holds mode y (y < ny/2), or mode y - Ly (y > Ly - ny/2), else zero
+    pipelined_copy<C>(
+        Ly * B,
+        [&](int i) {
+            const int y = i >> lgB, b = i & (B - 1);
+            C v = cmk(T(0), T(0));
+            if (y < ny / 2)
+                v = S2[(int64_t)y * Kx + b];
+            else if (y > Ly - ny / 2)
+                v = S2[(int64_t)(y - Ly + ny) * Kx + b];
+            return v;
+        },
+        [&](int i, C v) { b0[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
     const C *res = fft_columns<C, true>(b0, b1, Ly, ld, B, (const C *)p.tw[1]);
     C *S1 = (C *)p.S1 + (int64_t)z * Ly * Kx + kx0;
     for (int i = threadIdx.x; i < Ly * B; i += blockDim.x) {
-        const int y = i / B, b = i - y * B;
+        const int y = i >> lgB, b = i & (B - 1);
         S1[(int64_t)y * Kx + b] = res[y * ld + b];
     }
 }
@@ -326,40 +338,57 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2], Kx = p.Kx;
     const int ld = PB + 1;
+    const int lgLx = __ffs(Lx) - 1, lgKx = __ffs(Kx) - 1, lgHy = __ffs(Ly) - 2;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Lx * ld;
     const int64_t npairs = (int64_t)Lz * (Ly / 2);
     const int64_t pr0 = (int64_t)blockIdx.x * PB;
-    for (int i = threadIdx.x; i < PB * Lx; i += blockDim.x) b0[(i % Lx) * ld + i / Lx] = cmk(T(0), T(0));
+    for (int i = threadIdx.x; i < PB * Lx; i += blockDim.x) b0[(i & (Lx - 1)) * ld + (i >> lgLx)] = cmk(T(0), T(0));
     __syncthreads();
     const C *S1 = (const C *)p.S1;
-    for (int i = threadIdx.x; i < PB * Kx; i += blockDim.x) {
-        const int b = i / Kx, k = i - b * Kx;
-        const int64_t pr = pr0 + b;
-        if (pr >= npairs) continue;
-        const int64_t z = pr / (Ly / 2);
-        const int y0 = 2 * (int)(pr - z * (Ly / 2));
-        const int64_t o = (z * Ly + y0) * Kx + k;
-        const C xa = S1[o], xb = S1[o + Kx];
-        if (k == 0) {
-            b0[b] = cmk(xa.x, xb.x);
-        } else {
-            b0[k * ld + b] = cmk(xa.x - xb.y, xa.y + xb.x);             // xa + i xb
-            b0[(Lx - k) * ld + b] = cmk(xa.x + xb.y, xb.x - xa.y);      // conj(xa) + i conj(xb)
-        }
-    }
+    typedef typename VecT<T>::T4 T4;  // (xa, xb) of one mode, loaded together
+    pipelined_copy<T4>(
+        PB * Kx,
+        [&](int i) {
+            const int b = i >> lgKx, k = i & (Kx - 1);
+            const int64_t pr = pr0 + b;
+            T4 v;
+            v.x = v.y = v.z = v.w = T(0);
+            if (pr < npairs) {
+                const int64_t z = pr >> lgHy;
+                const int y0 = 2 * (int)(pr & ((Ly >> 1) - 1));
+                const int64_t o = (z * Ly + y0) * Kx + k;
+                const C xa = S1[o], xb = S1[o + Kx];
+                v.x = xa.x;
+                v.y = xa.y;
+                v.z = xb.x;
+                v.w = xb.y;
+            }
+            return v;
+        },
+        [&](int i, T4 v) {
+            const int b = i >> lgKx, k = i & (Kx - 1);
+            if (pr0 + b >= npairs) return;
+            if (k == 0) {
+                b0[b] = cmk(v.x, v.z);
+            } else {
+                b0[k * ld + b] = cmk(v.x - v.w, v.y + v.z);          // xa + i xb
+                b0[(Lx - k) * ld + b] = cmk(v.x + v.w, v.z - v.y);   // conj(xa) + i conj(xb)
+            }
+        });
     __syncthreads();
     const C *res = fft_columns<C, true>(b0, b1, Lx, ld, PB, (const C *)p.tw[0]);
     T *G = (T *)p.gridB;
     typedef typename VecW<T>::V V;
     constexpr int VW = VecW<T>::W;
+    constexpr int lgVW = VW == 4 ? 2 : 1;
     const int nv = Lx / VW;
     for (int i = threadIdx.x; i < PB * nv; i += blockDim.x) {
-        const int b = i / nv, xv = i - b * nv;
+        const int b = i >> (lgLx - lgVW), xv = i & (nv - 1);
         const int64_t pr = pr0 + b;
         if (pr >= npairs) continue;
-        const int64_t z = pr / (Ly / 2);
-        const int y0 = 2 * (int)(pr - z * (Ly / 2));
+        const int64_t z = pr >> lgHy;
+        const int y0 = 2 * (int)(pr & ((Ly >> 1) - 1));
         const int64_t r0 = (z * Ly + y0) * Lx;
         T ra[VW], rb[VW];
 #pragma unroll

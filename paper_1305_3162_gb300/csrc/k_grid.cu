@@ -17,38 +17,107 @@
 namespace slp {
 
 // ---------------------------------------------------------------- charges
-// qbuf[k] = w_k * sigma_k in sorted source order, for the three input kinds.
+// Nodal magnetisation in sorted target order, one 4-vector per vertex, so the
+// charge assembly and the near-field product read it coalesced.
 template <typename T>
-__global__ void __launch_bounds__(256) k_charges(DevPlan p, int kind, const T *__restrict__ in) {
+__global__ void __launch_bounds__(256) k_nodal_prep(DevPlan p, const T *__restrict__ in) {
     typedef typename VecT<T>::T4 T4;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= p.Q) return;
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= p.N) return;
+    const int64_t v = p.tgt_perm[u];
+    T4 o;
+    o.x = in[3 * v];
+    o.y = in[3 * v + 1];
+    o.z = in[3 * v + 2];
+    o.w = T(0);
+    ((T4 *)p.m4)[u] = o;
+}
+
+// w_k * sigma_k of sorted source k for the three input kinds (NODAL_MAG
+// reads the sorted 4-vectors written by k_nodal_prep).
+template <typename T>
+__device__ __forceinline__ T source_charge(const DevPlan &p, int64_t k, int kind, const T *__restrict__ in) {
+    typedef typename VecT<T>::T4 T4;
     const int u = p.src_perm[k];
     const T w = ((const T *)p.src_w)[k];
-    T sigma;
-    if (kind == 0) {
-        sigma = in[u];
+    if (kind == 0) return w * in[u];
+    const int j = u / p.q;
+    const int s = u - j * p.q;
+    const T4 nrm = ((const T4 *)p.tri_nrm)[j];
+    T mx, my, mz;
+    if (kind == 1) {
+        mx = in[3 * (int64_t)u];
+        my = in[3 * (int64_t)u + 1];
+        mz = in[3 * (int64_t)u + 2];
     } else {
-        const int j = u / p.q;
-        const int s = u - j * p.q;
-        const T4 nrm = ((const T4 *)p.tri_nrm)[j];
-        T mx, my, mz;
-        if (kind == 1) {
-            mx = in[3 * (int64_t)u];
-            my = in[3 * (int64_t)u + 1];
-            mz = in[3 * (int64_t)u + 2];
-        } else {
-            const int4 v = p.tri_vtx[j];
-            const T *lam = (const T *)p.lam + 3 * s;
-            const T l0 = lam[0], l1 = lam[1], l2 = lam[2];
-            const int64_t a = 3 * (int64_t)v.x, b = 3 * (int64_t)v.y, c = 3 * (int64_t)v.z;
-            mx = l0 * in[a] + l1 * in[b] + l2 * in[c];
-            my = l0 * in[a + 1] + l1 * in[b + 1] + l2 * in[c + 1];
-            mz = l0 * in[a + 2] + l1 * in[b + 2] + l2 * in[c + 2];
-        }
-        sigma = mx * nrm.x + my * nrm.y + mz * nrm.z;
+        const int4 v = p.tri_vtx[j];
+        const T *lam = (const T *)p.lam + 3 * s;
+        const T l0 = lam[0], l1 = lam[1], l2 = lam[2];
+        const T4 *m4 = (const T4 *)p.m4;
+        const T4 a = m4[v.x], b = m4[v.y], c = m4[v.z];
+        mx = l0 * a.x + l1 * b.x + l2 * c.x;
+        my = l0 * a.y + l1 * b.y + l2 * c.y;
+        mz = l0 * a.z + l1 * b.z + l2 * c.z;
     }
-    ((T *)p.qbuf)[k] = w * sigma;
+    return w * (mx * nrm.x + my * nrm.y + mz * nrm.z);
+}
+
+// qbuf[k] = w_k * sigma_k in sorted source order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_charges(DevPlan p, int kind, const T *__restrict__ in) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= p.Q) return;
+    ((T *)p.qbuf)[k] = source_charge<T>(p, k, kind, in);
+}
+
+// ---------------------------------------------------------------- tile geometry
+// A tile covers TS^3 cells; with the window's halo it spans TE = TS + 2M - 1
+// grid points per axis.  In shared memory a tile is stored with x extent XE
+// (TE widened so that the first x point is 16-byte aligned in the global
+// grid), row stride RS and plane stride PS chosen so that the 32 lanes of a
+// warp, one per (y, z) row of a window box (8 x 4 rows for M = 4), fall on 32
+// different banks.
+template <int M, int TS> struct TileGeom {
+    static constexpr int W = 2 * M;
+    static constexpr int TE = TS + W - 1;
+    static constexpr int XO = (4 - ((M - 1) % 4)) % 4;  // x offset of the halo start inside the aligned row
+    static constexpr int XE = ((XO + TE + 3) / 4) * 4;
+    static constexpr int RS = (XE % 8 == 4) ? XE : XE + 4;
+    static constexpr int PS = ((TE * RS + 31) / 32) * 32 + 1;
+    static constexpr int SIZE = TE * PS;                  // elements of one tile copy
+};
+
+// Window values w[axis][i] = psi(f_axis + M - 1 - i) for the 3 x 2M window
+// points of one source or target, computed by the lanes of one warp.
+// FP32: per-interval polynomial in the fraction f (coefficients fitted on the
+// host, max error ~1e-10 of psi(0)); FP64: the closed form.
+constexpr int WDEG = 9;  // degree of the FP32 window polynomials (set by the plan)
+
+template <int M>
+__device__ __forceinline__ void window_values(float *wv, float fx, float fy, float fz, const float *__restrict__ coef,
+                                              int, float, float, float) {
+    constexpr int W = 2 * M;
+    const int lane = threadIdx.x & 31;
+    for (int j = lane; j < 3 * W; j += 32) {
+        const int ax = j / W, i = j - ax * W;
+        const float f = ax == 0 ? fx : (ax == 1 ? fy : fz);
+        const float *c = coef + i * (WDEG + 1);
+        float v = c[WDEG];
+#pragma unroll
+        for (int k = WDEG - 1; k >= 0; --k) v = fmaf(v, f, c[k]);
+        wv[j] = v;
+    }
+}
+template <int M>
+__device__ __forceinline__ void window_values(double *wv, double fx, double fy, double fz, const double *, int,
+                                              double inv_m, double beta, double isb) {
+    constexpr int W = 2 * M;
+    const int lane = threadIdx.x & 31;
+    for (int j = lane; j < 3 * W; j += 32) {
+        const int ax = j / W, i = j - ax * W;
+        const double f = ax == 0 ? fx : (ax == 1 ? fy : fz);
+        wv[j] = kb_window(f + double(M - 1 - i), inv_m, beta, isb);
+    }
 }
 
 // ---------------------------------------------------------------- spread
@@ -56,111 +125,315 @@ __global__ void __launch_bounds__(256) k_charges(DevPlan p, int kind, const T *_
 // are plain read-modify-writes: within one warp instruction every lane owns a
 // different (y, z) row of the source's window box, and consecutive sources of
 // a warp are ordered by __syncwarp.  The warp copies are summed in a fixed
-// order before the tile is added to the global grid.
-template <typename T, int M>
-__global__ void __launch_bounds__(256) k_spread(DevPlan p) {
+// order and the tile is added to the global grid, 16 bytes per atomic where
+// the row does not wrap around the periodic grid.
+template <typename T, int M, int TS>
+__global__ void __launch_bounds__(256) k_spread(DevPlan p, int fused_kind, const T *__restrict__ in) {
     typedef typename VecT<T>::T4 T4;
-    constexpr int W = 2 * M;  // window points per axis
+    typedef TileGeom<M, TS> G;
+    constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO, XE = G::XE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TE = p.TE;
-    const int TE2 = TE * TE;
-    const int TE3 = TE2 * TE;
-    const int TEP = (TE3 + 31) & ~31;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     T *tiles = (T *)smem_raw;
-    T *wv = tiles + (size_t)nwarps * TEP + warp * (3 * W);
-    T *my = tiles + (size_t)warp * TEP;
+    T *coef = tiles + nwarps * G::SIZE;
+    const int ncoef = W * (p.wdeg + 1);
+    T *wv = coef + ((ncoef + 3) & ~3) + warp * (3 * W);
+    T *my = tiles + warp * G::SIZE;
+
+    // the item's sources (positions and charges), staged once per block
+    const size_t head = ((size_t)nwarps * G::SIZE + ((ncoef + 3) & ~3) + (size_t)nwarps * 3 * W + 3) & ~(size_t)3;
+    T4 *sg = (T4 *)(tiles + head);
+    T *sq = (T *)(sg + p.spread_chunk);
 
     const TileItem it = p.spread_items[blockIdx.x];
-    for (int i = threadIdx.x; i < nwarps * TEP; i += blockDim.x) tiles[i] = T(0);
+    const int nsrc = it.end - it.begin;
+    {
+        // charges either from the charge kernel (qbuf) or computed here from
+        // the input (fused_kind >= 0)
+        const T4 *src = (const T4 *)p.src_grid + it.begin;
+        const T *qb = (const T *)p.qbuf + it.begin;
+        for (int i = threadIdx.x; i < nsrc; i += blockDim.x) {
+            sg[i] = src[i];
+            sq[i] = fused_kind >= 0 ? source_charge<T>(p, it.begin + i, fused_kind, in) : qb[i];
+        }
+    }
+    for (int i = threadIdx.x; i < nwarps * G::SIZE; i += blockDim.x) tiles[i] = T(0);
+    if (sizeof(T) == 4)
+        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) coef[i] = ((const T *)p.wcoef)[i];
     __syncthreads();
 
-    const T4 *src = (const T4 *)p.src_grid;
-    const T *qb = (const T *)p.qbuf;
     const T inv_m = T(1) / T(M);
     const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
-    for (int k = it.begin + warp; k < it.end; k += nwarps) {
-        const T4 g = src[k];
-        const T qk = qb[k];
+    for (int k = warp; k < nsrc; k += nwarps) {
+        const T4 g = sg[k];
+        const T qk = sq[k];
         int cx, cy, cz;
         unpack_cell(packed_cell(g.w), cx, cy, cz);
         const int lx = cx - it.c0x, ly = cy - it.c0y, lz = cz - it.c0z;
-        if ((unsigned)lx >= (unsigned)p.TS || (unsigned)ly >= (unsigned)p.TS || (unsigned)lz >= (unsigned)p.TS) {
+        if ((unsigned)lx >= (unsigned)TS || (unsigned)ly >= (unsigned)TS || (unsigned)lz >= (unsigned)TS) {
             set_error(p.err, DEV_ERR_BAD_ITEM);
             continue;
         }
-        // window values: wv[axis * W + i] = psi(f + M - 1 - i)
-        for (int j = lane; j < 3 * W; j += 32) {
-            const int ax = j / W, i = j - ax * W;
-            const T f = ax == 0 ? g.x : (ax == 1 ? g.y : g.z);
-            wv[j] = kb_window(f + T(M - 1 - i), inv_m, beta, isb);
-        }
+        window_values<M>(wv, g.x, g.y, g.z, coef, p.wdeg, inv_m, beta, isb);
         __syncwarp();
         T wx[W];
 #pragma unroll
         for (int ix = 0; ix < W; ++ix) wx[ix] = wv[ix];
-        for (int pi = lane; pi < W * W; pi += 32) {
-            const int iy = pi % W, iz = pi / W;
-            const T wyz = qk * wv[2 * W + iz] * wv[W + iy];
-            T *row = my + (lz + iz) * TE2 + (ly + iy) * TE + lx;
-            T r[W];
+        T *base = my + lz * PS + ly * RS + lx + XO;
 #pragma unroll
-            for (int ix = 0; ix < W; ++ix) r[ix] = row[ix];
+        for (int rep = 0; rep < (W * W + 31) / 32; ++rep) {
+            const int pi = lane + 32 * rep;
+            if (pi < W * W) {
+                const int iy = pi % W, iz = pi / W;
+                const T wyz = qk * wv[2 * W + iz] * wv[W + iy];
+                T *row = base + iz * PS + iy * RS;
+                T r[W];
 #pragma unroll
-            for (int ix = 0; ix < W; ++ix) row[ix] = r[ix] + wyz * wx[ix];
+                for (int ix = 0; ix < W; ++ix) r[ix] = row[ix];
+#pragma unroll
+                for (int ix = 0; ix < W; ++ix) row[ix] = r[ix] + wyz * wx[ix];
+            }
         }
         __syncwarp();
     }
     __syncthreads();
 
-    // sum the warp copies in order, then add the tile (with the periodic
-    // wrap-around) to the global grid
     const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
-    const int gx0 = it.c0x - M + 1, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
+    const int gxs = it.c0x - M + 1 - XO, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
     T *grid = (T *)p.gridA;
-    for (int i = threadIdx.x; i < TE3; i += blockDim.x) {
-        T v = T(0);
-        for (int w = 0; w < nwarps; ++w) v += tiles[(size_t)w * TEP + i];
-        if (v == T(0)) continue;
-        const int iz = i / TE2;
-        const int r = i - iz * TE2;
-        const int iy = r / TE;
-        const int ix = r - iy * TE;
-        const int gx = (gx0 + ix) & (Lx - 1);
-        const int gy = (gy0 + iy) & (Ly - 1);
-        const int gz = (gz0 + iz) & (Lz - 1);
-        atomicAdd(grid + ((int64_t)gz * Ly + gy) * Lx + gx, v);
+    // 16-byte vector atomics need an aligned row start inside the grid (TS a
+    // multiple of 4 makes gxs a multiple of 4 by construction of XO)
+    const bool xin = gxs >= 0 && gxs + XE <= Lx && (gxs & 3) == 0;
+    if (sizeof(T) == 4 && TS % 4 == 0 && xin) {
+        // 4-wide: rows of XE/4 aligned vectors
+        constexpr int NV = XE / 4;
+        for (int i = threadIdx.x; i < TE * TE * NV; i += blockDim.x) {
+            const int v = i % NV, r = i / NV;
+            const int iy = r % TE, iz = r / TE;
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int w = 0; w < nwarps; ++w) {
+                const T *t = tiles + w * G::SIZE + iz * PS + iy * RS + 4 * v;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) a[e] += (float)t[e];
+            }
+            if (a[0] == 0.f && a[1] == 0.f && a[2] == 0.f && a[3] == 0.f) continue;
+            const int gy = (gy0 + iy) & (Ly - 1), gz = (gz0 + iz) & (Lz - 1);
+            float4 *dst = (float4 *)((float *)grid + ((int64_t)gz * Ly + gy) * Lx + gxs) + v;
+            atomicAdd(dst, make_float4(a[0], a[1], a[2], a[3]));
+        }
+    } else {
+        for (int i = threadIdx.x; i < TE * TE * XE; i += blockDim.x) {
+            const int x = i % XE, r = i / XE;
+            const int iy = r % TE, iz = r / TE;
+            T v = T(0);
+            for (int w = 0; w < nwarps; ++w) v += tiles[w * G::SIZE + iz * PS + iy * RS + x];
+            if (v == T(0)) continue;
+            const int gx = (gxs + x) & (Lx - 1);
+            const int gy = (gy0 + iy) & (Ly - 1), gz = (gz0 + iz) & (Lz - 1);
+            atomicAdd(grid + ((int64_t)gz * Ly + gy) * Lx + gx, v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- spread, cell groups
+// Variant for 2M <= 10: runs of consecutive sources that share a grid cell
+// (the Morton sort makes them contiguous) have the same window box, so a warp
+// sums a whole run in registers and updates its private tile once per run.
+// Lanes map to (x offset ix, z offset izs); a lane holds the box column
+// (ix, iz = izs + ZL h, all iy) as H x W accumulators.  The plane stride is
+// congruent to W modulo 32, so the 8 x 4 lanes of a row update hit 32
+// different banks.
+template <int M, int TS> struct TileGeomG {
+    static constexpr int W = 2 * M;
+    static constexpr int TE = TS + W - 1;
+    static constexpr int XO = (4 - ((M - 1) % 4)) % 4;
+    static constexpr int XE = ((XO + TE + 3) / 4) * 4;
+    static constexpr int RS = XE;
+    static constexpr int PS = ((TE * RS - W + 31) / 32) * 32 + W;  // >= TE RS, == W mod 32
+    static constexpr int SIZE = TE * PS;
+    static constexpr int ZL = 32 / W;                   // z offsets per lane group
+    static constexpr int H = (W + ZL - 1) / ZL;         // z offsets per lane
+};
+
+constexpr int SPREAD_GMAX = 16;  // sources per cell group
+
+template <typename T, int M, int TS>
+__global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind, const T *__restrict__ in) {
+    typedef typename VecT<T>::T4 T4;
+    typedef TileGeomG<M, TS> G;
+    constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO, XE = G::XE, ZL = G::ZL, H = G::H;
+    constexpr int GW = 3 * W;  // window values per source
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    T *tiles = (T *)smem_raw;
+    T *coef = tiles + nwarps * G::SIZE;
+    const int ncoef = W * (WDEG + 1);
+    T *wvall = coef + ((ncoef + 3) & ~3);
+    T *wv = wvall + warp * (SPREAD_GMAX * GW);
+    const size_t head = ((size_t)nwarps * G::SIZE + ((ncoef + 3) & ~3) + (size_t)nwarps * SPREAD_GMAX * GW + 3) & ~(size_t)3;
+    T4 *sg = (T4 *)(tiles + head);
+    T *sq = (T *)(sg + p.spread_chunk);
+    T *my = tiles + warp * G::SIZE;
+
+    const TileItem it = p.spread_items[blockIdx.x];
+    const int nsrc = it.end - it.begin;
+    {
+        const T4 *src = (const T4 *)p.src_grid + it.begin;
+        const T *qb = (const T *)p.qbuf + it.begin;
+        for (int i = threadIdx.x; i < nsrc; i += blockDim.x) {
+            sg[i] = src[i];
+            sq[i] = fused_kind >= 0 ? source_charge<T>(p, it.begin + i, fused_kind, in) : qb[i];
+        }
+    }
+    for (int i = threadIdx.x; i < nwarps * G::SIZE; i += blockDim.x) tiles[i] = T(0);
+    if (sizeof(T) == 4)
+        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) coef[i] = ((const T *)p.wcoef)[i];
+    __syncthreads();
+
+    const T inv_m = T(1) / T(M);
+    const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
+    const int ix = lane % W, izs = lane / W;
+    const bool lane_on = lane < W * ZL;
+    const int c0 = (nsrc * warp) / nwarps, c1 = (nsrc * (warp + 1)) / nwarps;
+    for (int g0 = c0; g0 < c1;) {
+        const int cell = packed_cell(sg[g0].w);
+        int ge = g0 + 1;
+        while (ge < c1 && ge - g0 < SPREAD_GMAX && packed_cell(sg[ge].w) == cell) ++ge;
+        const int ng = ge - g0;
+        int cx, cy, cz;
+        unpack_cell(cell, cx, cy, cz);
+        const int lx = cx - it.c0x, ly = cy - it.c0y, lz = cz - it.c0z;
+        if ((unsigned)lx >= (unsigned)TS || (unsigned)ly >= (unsigned)TS || (unsigned)lz >= (unsigned)TS) {
+            set_error(p.err, DEV_ERR_BAD_ITEM);
+            g0 = ge;
+            continue;
+        }
+        // window values of the group: wv[g * GW + axis * W + i]
+        for (int j = lane; j < ng * GW; j += 32) {
+            const int g = j / GW, r = j - g * GW;
+            const T4 sgg = sg[g0 + g];
+            const int ax = r / W, i = r - ax * W;
+            const T f = ax == 0 ? sgg.x : (ax == 1 ? sgg.y : sgg.z);
+            if (sizeof(T) == 4) {
+                const T *c = coef + i * (WDEG + 1);
+                T v = c[WDEG];
+#pragma unroll
+                for (int k = WDEG - 1; k >= 0; --k) v = v * f + c[k];
+                wv[j] = v;
+            } else {
+                wv[j] = kb_window(f + T(M - 1 - i), inv_m, beta, isb);
+            }
+        }
+        __syncwarp();
+        if (lane_on) {
+            T acc[H][W];
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+#pragma unroll
+                for (int iy = 0; iy < W; ++iy) acc[h][iy] = T(0);
+            for (int g = 0; g < ng; ++g) {
+                const T *w = wv + g * GW;
+                const T a = sq[g0 + g] * w[ix];
+                T b[H];
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const int iz = izs + ZL * h;
+                    b[h] = iz < W ? a * w[2 * W + iz] : T(0);
+                }
+#pragma unroll
+                for (int iy = 0; iy < W; ++iy) {
+                    const T wy = w[W + iy];
+#pragma unroll
+                    for (int h = 0; h < H; ++h) acc[h][iy] += b[h] * wy;
+                }
+            }
+            T *base = my + lz * PS + ly * RS + lx + XO + ix;
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                const int iz = izs + ZL * h;
+                if (iz < W) {
+#pragma unroll
+                    for (int iy = 0; iy < W; ++iy) {
+                        T *a = base + iz * PS + iy * RS;
+                        *a = *a + acc[h][iy];
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        g0 = ge;
+    }
+    __syncthreads();
+
+    const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
+    const int gxs = it.c0x - M + 1 - XO, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
+    T *grid = (T *)p.gridA;
+    const bool xin = gxs >= 0 && gxs + XE <= Lx && (gxs & 3) == 0;
+    if (sizeof(T) == 4 && TS % 4 == 0 && xin) {
+        constexpr int NV = XE / 4;
+        for (int i = threadIdx.x; i < TE * TE * NV; i += blockDim.x) {
+            const int v = i % NV, r = i / NV;
+            const int iy = r % TE, iz = r / TE;
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int w = 0; w < nwarps; ++w) {
+                const T *t = tiles + w * G::SIZE + iz * PS + iy * RS + 4 * v;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) a[e] += (float)t[e];
+            }
+            if (a[0] == 0.f && a[1] == 0.f && a[2] == 0.f && a[3] == 0.f) continue;
+            const int gy = (gy0 + iy) & (Ly - 1), gz = (gz0 + iz) & (Lz - 1);
+            float4 *dst = (float4 *)((float *)grid + ((int64_t)gz * Ly + gy) * Lx + gxs) + v;
+            atomicAdd(dst, make_float4(a[0], a[1], a[2], a[3]));
+        }
+    } else {
+        for (int i = threadIdx.x; i < TE * TE * XE; i += blockDim.x) {
+            const int x = i % XE, r = i / XE;
+            const int iy = r % TE, iz = r / TE;
+            T v = T(0);
+            for (int w = 0; w < nwarps; ++w) v += tiles[w * G::SIZE + iz * PS + iy * RS + x];
+            if (v == T(0)) continue;
+            const int gx = (gxs + x) & (Lx - 1);
+            const int gy = (gy0 + iy) & (Ly - 1), gz = (gz0 + iz) & (Lz - 1);
+            atomicAdd(grid + ((int64_t)gz * Ly + gy) * Lx + gx, v);
+        }
     }
 }
 
 // ---------------------------------------------------------------- gather
-template <typename T, int M>
-__global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) {
+// One block per work item (a tile and up to 32 of its targets): the tile plus
+// halo of grid B is staged in shared memory (same padded layout as the
+// spread), then one warp per target sums its (2M)^3 window box.
+template <typename T, int M, int TS>
+__global__ void __launch_bounds__(128) k_gather(DevPlan p, T *__restrict__ phi) {
     typedef typename VecT<T>::T4 T4;
-    constexpr int W = 2 * M;
+    typedef TileGeom<M, TS> G;
+    constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TE = p.TE;
-    const int TE2 = TE * TE;
-    const int TE3 = TE2 * TE;
-    T *tile = (T *)smem_raw;
-    T *wall = tile + ((TE3 + 3) & ~3);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    T *wv = wall + warp * (3 * W);
+    T *tile = (T *)smem_raw;
+    T *coef = tile + G::SIZE;
+    const int ncoef = W * (p.wdeg + 1);
+    T *wv = coef + ((ncoef + 3) & ~3) + warp * (3 * W);
 
     const TileItem it = p.gather_items[blockIdx.x];
     const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
     const int gx0 = it.c0x - M + 1, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
     const T *grid = (const T *)p.gridB;
-    for (int i = threadIdx.x; i < TE3; i += blockDim.x) {
-        const int iz = i / TE2;
-        const int r = i - iz * TE2;
-        const int iy = r / TE;
-        const int ix = r - iy * TE;
-        const int gx = (gx0 + ix) & (Lx - 1);
-        const int gy = (gy0 + iy) & (Ly - 1);
-        const int gz = (gz0 + iz) & (Lz - 1);
-        tile[i] = grid[((int64_t)gz * Ly + gy) * Lx + gx];
-    }
+    pipelined_copy<T>(
+        TE * TE * TE,
+        [&](int i) {
+            const int x = i % TE, r = i / TE;
+            const int gx = (gx0 + x) & (Lx - 1);
+            const int gy = (gy0 + r % TE) & (Ly - 1);
+            const int gz = (gz0 + r / TE) & (Lz - 1);
+            return grid[((int64_t)gz * Ly + gy) * Lx + gx];
+        },
+        [&](int i, T v) {
+            const int x = i % TE, r = i / TE;
+            tile[(r / TE) * PS + (r % TE) * RS + x + XO] = v;
+        });
+    if (sizeof(T) == 4)
+        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) coef[i] = ((const T *)p.wcoef)[i];
     __syncthreads();
 
     const T4 *tg = (const T4 *)p.tgt_grid;
@@ -171,24 +444,25 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
         int cx, cy, cz;
         unpack_cell(packed_cell(g.w), cx, cy, cz);
         const int lx = cx - it.c0x, ly = cy - it.c0y, lz = cz - it.c0z;
-        if ((unsigned)lx >= (unsigned)p.TS || (unsigned)ly >= (unsigned)p.TS || (unsigned)lz >= (unsigned)p.TS) {
+        if ((unsigned)lx >= (unsigned)TS || (unsigned)ly >= (unsigned)TS || (unsigned)lz >= (unsigned)TS) {
             set_error(p.err, DEV_ERR_BAD_ITEM);
             continue;
         }
-        for (int j = lane; j < 3 * W; j += 32) {
-            const int ax = j / W, i = j - ax * W;
-            const T f = ax == 0 ? g.x : (ax == 1 ? g.y : g.z);
-            wv[j] = kb_window(f + T(M - 1 - i), inv_m, beta, isb);
-        }
+        window_values<M>(wv, g.x, g.y, g.z, coef, p.wdeg, inv_m, beta, isb);
         __syncwarp();
+        const T *base = tile + lz * PS + ly * RS + lx + XO;
         T acc = T(0);
-        for (int pi = lane; pi < W * W; pi += 32) {
-            const int iy = pi % W, iz = pi / W;
-            const T *row = tile + (lz + iz) * TE2 + (ly + iy) * TE + lx;
-            T s = T(0);
 #pragma unroll
-            for (int ix = 0; ix < W; ++ix) s += row[ix] * wv[ix];
-            acc += s * wv[2 * W + iz] * wv[W + iy];
+        for (int rep = 0; rep < (W * W + 31) / 32; ++rep) {
+            const int pi = lane + 32 * rep;
+            if (pi < W * W) {
+                const int iy = pi % W, iz = pi / W;
+                const T *row = base + iz * PS + iy * RS;
+                T s = T(0);
+#pragma unroll
+                for (int ix = 0; ix < W; ++ix) s += row[ix] * wv[ix];
+                acc += s * wv[2 * W + iz] * wv[W + iy];
+            }
         }
         acc = warp_sum(acc);
         if (lane == 0) phi[p.tgt_perm[t]] = acc;
@@ -203,40 +477,75 @@ __global__ void k_zero4(float4 *p, int64_t n4) {
 }
 
 // ---------------------------------------------------------------- launchers
-static size_t tile_smem_bytes(const DevPlan &p, size_t elem) {
-    const size_t TE3 = (size_t)p.TE * p.TE * p.TE;
-    return (((TE3 + 3) & ~(size_t)3) + 8 * 3 * 2 * (size_t)p.m) * elem;
+template <typename T, int M, int TS> static size_t spread_smem(int nwarps, int wdeg, int chunk) {
+    typedef TileGeom<M, TS> G;
+    const int ncoef = 2 * M * (wdeg + 1);
+    const size_t head = (((size_t)nwarps * G::SIZE + ((ncoef + 3) & ~3) + (size_t)nwarps * 3 * 2 * M) + 3) & ~(size_t)3;
+    return head * sizeof(T) + (size_t)chunk * (4 * sizeof(T) + sizeof(T));
 }
 
-// warps per spread block: as many private tiles as fit in ~110 KB (two blocks per SM)
-static int spread_warps(const DevPlan &p, size_t elem) {
-    const size_t TE3 = (size_t)p.TE * p.TE * p.TE;
-    const size_t TEP = (TE3 + 31) & ~(size_t)31;
+template <typename T, int M, int TS> static size_t spread_groups_smem(int nwarps, int chunk) {
+    typedef TileGeomG<M, TS> G;
+    const int ncoef = 2 * M * (WDEG + 1);
+    const size_t head =
+        (((size_t)nwarps * G::SIZE + ((ncoef + 3) & ~3) + (size_t)nwarps * SPREAD_GMAX * 3 * 2 * M) + 3) & ~(size_t)3;
+    return head * sizeof(T) + (size_t)chunk * (4 * sizeof(T) + sizeof(T));
+}
+
+template <typename T, int M, int TS>
+static cudaError_t spread_mt(const DevPlan &p, int fused_kind, const void *in, cudaStream_t s) {
+    if constexpr (M <= 5) {
+        int nw = 8;
+        while (nw > 1 && spread_groups_smem<T, M, TS>(nw, p.spread_chunk) > 100 * 1024) nw >>= 1;
+        const size_t sm = spread_groups_smem<T, M, TS>(nw, p.spread_chunk);
+        if (sm > 48 * 1024) {
+            cudaError_t e =
+                cudaFuncSetAttribute(k_spread_groups<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+        }
+        if (p.n_spread > 0)
+            k_spread_groups<T, M, TS><<<p.n_spread, 32 * nw, sm, s>>>(p, fused_kind, (const T *)in);
+        return cudaGetLastError();
+    }
     int nw = 8;
-    while (nw > 1 && nw * (TEP + 3 * 2 * (size_t)p.m) * elem > 110 * 1024) nw >>= 1;
-    return nw;
-}
-
-template <typename T, int M> static cudaError_t spread_t(const DevPlan &p, cudaStream_t s) {
-    const int nw = spread_warps(p, sizeof(T));
-    const size_t TE3 = (size_t)p.TE * p.TE * p.TE;
-    const size_t sm = (nw * ((TE3 + 31) & ~(size_t)31) + nw * 3 * 2 * (size_t)M) * sizeof(T);
+    while (nw > 1 && spread_smem<T, M, TS>(nw, p.wdeg, p.spread_chunk) > 100 * 1024) nw >>= 1;
+    const size_t sm = spread_smem<T, M, TS>(nw, p.wdeg, p.spread_chunk);
     if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_spread<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = cudaFuncSetAttribute(k_spread<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    if (p.n_spread > 0) k_spread<T, M><<<p.n_spread, 32 * nw, sm, s>>>(p);
+    if (p.n_spread > 0) k_spread<T, M, TS><<<p.n_spread, 32 * nw, sm, s>>>(p, fused_kind, (const T *)in);
     return cudaGetLastError();
 }
 
+template <typename T, int M, int TS> static cudaError_t gather_mt(const DevPlan &p, void *phi, cudaStream_t s) {
+    typedef TileGeom<M, TS> G;
+    const int ncoef = 2 * M * (p.wdeg + 1);
+    const size_t sm = ((size_t)G::SIZE + ((ncoef + 3) & ~3) + 4 * 3 * 2 * M) * sizeof(T);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_gather<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    if (p.n_gather > 0) k_gather<T, M, TS><<<p.n_gather, 128, sm, s>>>(p, (T *)phi);
+    return cudaGetLastError();
+}
+
+template <typename T, int M>
+static cudaError_t spread_t(const DevPlan &p, int fused_kind, const void *in, cudaStream_t s) {
+    switch (p.TS) {
+        case 2: return spread_mt<T, M, 2>(p, fused_kind, in, s);
+        case 4: return spread_mt<T, M, 4>(p, fused_kind, in, s);
+        case 8: return spread_mt<T, M, 8>(p, fused_kind, in, s);
+    }
+    return cudaErrorInvalidValue;
+}
 template <typename T, int M> static cudaError_t gather_t(const DevPlan &p, void *phi, cudaStream_t s) {
-    const size_t sm = tile_smem_bytes(p, sizeof(T));
-    if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_gather<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
+    switch (p.TS) {
+        case 2: return gather_mt<T, M, 2>(p, phi, s);
+        case 4: return gather_mt<T, M, 4>(p, phi, s);
+        case 8: return gather_mt<T, M, 8>(p, phi, s);
     }
-    if (p.n_gather > 0) k_gather<T, M><<<p.n_gather, 256, sm, s>>>(p, (T *)phi);
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 #define SLP_DISPATCH_M(FN, T, ...)                                  \
@@ -251,14 +560,24 @@ template <typename T, int M> static cudaError_t gather_t(const DevPlan &p, void 
         default: return cudaErrorInvalidValue;                      \
     }
 
-cudaError_t launch_spread(const DevPlan &p, cudaStream_t s) {
-    if (p.prec == 64) { SLP_DISPATCH_M(spread_t, double, p, s) }
-    SLP_DISPATCH_M(spread_t, float, p, s)
+cudaError_t launch_spread(const DevPlan &p, int fused_kind, const void *in, cudaStream_t s) {
+    if (p.prec == 64) { SLP_DISPATCH_M(spread_t, double, p, fused_kind, in, s) }
+    SLP_DISPATCH_M(spread_t, float, p, fused_kind, in, s)
 }
 
 cudaError_t launch_gather(const DevPlan &p, void *phi, cudaStream_t s) {
     if (p.prec == 64) { SLP_DISPATCH_M(gather_t, double, p, phi, s) }
     SLP_DISPATCH_M(gather_t, float, p, phi, s)
+}
+
+cudaError_t launch_nodal_prep(const DevPlan &p, const void *d_in, cudaStream_t s) {
+    if (p.N == 0) return cudaSuccess;
+    const int nb = (int)((p.N + 255) / 256);
+    if (p.prec == 64)
+        k_nodal_prep<double><<<nb, 256, 0, s>>>(p, (const double *)d_in);
+    else
+        k_nodal_prep<float><<<nb, 256, 0, s>>>(p, (const float *)d_in);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_charges(const DevPlan &p, int kind, const void *d_in, cudaStream_t s) {

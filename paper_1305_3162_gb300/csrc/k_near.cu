@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(256) k_nm_build(NMBuild b, int pass, int64_t *
                 o.x = wx;
                 o.y = wy;
                 o.z = wz;
-                o.w = pack_id(o.w, v);  // vertex id in the fourth component
+                o.w = pack_id(o.w, u);  // vertex (sorted target position) in the fourth component
                 val[out + cnt + pos] = o;
             }
             cnt += __popc(bal);
@@ -247,19 +247,43 @@ cudaError_t launch_nm_build(const NMBuild &b, int pass, int prec, int64_t *count
 
 // phi[perm[t]] += sum_e W_e . m[col_e] over row t (sorted target order); one
 // warp per row, rows read front to back, lanes combined in a fixed order.
+// streaming (evict-first) 16/32-byte load of one matrix entry
+__device__ __forceinline__ float4 ld_stream(const float4 *p) { return __ldcs(p); }
+__device__ __forceinline__ double4 ld_stream(const double4 *p) {
+    const double2 a = __ldcs((const double2 *)p), b = __ldcs((const double2 *)p + 1);
+    return make_double4(a.x, a.y, b.x, b.y);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_near_matrix(DevPlan p, const T *__restrict__ m, T *__restrict__ phi) {
+__global__ void __launch_bounds__(128) k_near_matrix(DevPlan p, const T *__restrict__ m, T *__restrict__ phi) {
     typedef typename VecT<T>::T4 T4;
+    constexpr int U = 8;  // independent 16-byte loads in flight per lane
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t t = (int64_t)blockIdx.x * 8 + warp;
+    const int64_t t = (int64_t)blockIdx.x * 4 + warp;
     if (t >= p.N) return;
     const T4 *val = (const T4 *)p.nm_val;
+    const T4 *m4 = (const T4 *)p.m4;  // sorted nodal m (k_nodal_prep)
     const int64_t e0 = p.nm_rowptr[t], e1 = p.nm_rowptr[t + 1];
     T acc = T(0);
-    for (int64_t e = e0 + lane; e < e1; e += 32) {
-        const T4 w = val[e];
-        const int64_t v = (int64_t)packed_cell(w.w);
-        acc += w.x * m[3 * v] + w.y * m[3 * v + 1] + w.z * m[3 * v + 2];
+    // batches of 32 U entries, predicated, so a row of ~500 entries takes two
+    // batches with U loads in flight per lane
+    for (int64_t e = e0 + lane; e < e1; e += 32 * U) {
+        T4 w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = e + 32 * u;
+            if (i < e1) {
+                w[u] = ld_stream(val + i);  // streamed once per evaluation
+            } else {
+                w[u].x = w[u].y = w[u].z = T(0);
+                w[u].w = pack_id(w[u].w, 0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const T4 mv = m4[packed_cell(w[u].w)];
+            acc += w[u].x * mv.x + w[u].y * mv.y + w[u].z * mv.z;
+        }
     }
     acc = warp_sum(acc);
     if (lane == 0) phi[p.tgt_perm[t]] += acc;
@@ -267,11 +291,11 @@ __global__ void __launch_bounds__(256) k_near_matrix(DevPlan p, const T *__restr
 
 cudaError_t launch_near_matrix(const DevPlan &p, const void *d_m, void *d_phi, cudaStream_t s) {
     if (p.N == 0) return cudaSuccess;
-    const unsigned nb = (unsigned)((p.N + 7) / 8);
+    const unsigned nb = (unsigned)((p.N + 3) / 4);
     if (p.prec == 64)
-        k_near_matrix<double><<<nb, 256, 0, s>>>(p, (const double *)d_m, (double *)d_phi);
+        k_near_matrix<double><<<nb, 128, 0, s>>>(p, (const double *)d_m, (double *)d_phi);
     else
-        k_near_matrix<float><<<nb, 256, 0, s>>>(p, (const float *)d_m, (float *)d_phi);
+        k_near_matrix<float><<<nb, 128, 0, s>>>(p, (const float *)d_m, (float *)d_phi);
     return cudaGetLastError();
 }
 

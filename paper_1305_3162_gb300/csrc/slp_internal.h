@@ -37,6 +37,8 @@ struct DevPlan {
     int TS, TE;         // tile cells per axis; tile extent with halo TS + 2m - 1
     double h[3];        // physical grid spacing P_q / L_q
     double beta;        // Kaiser-Bessel shape b * m, b = pi (2 - 1/alpha)
+    const void *wcoef;  // FP32 window polynomials: [2m][wdeg + 1], coefficient k of f^k for point i
+    int wdeg;
     double inv_sinh_beta;
     double eps2;        // squared near radius (physical)
     double inv_s_sqrt2; // 1 / (sigma_g sqrt 2)
@@ -48,7 +50,7 @@ struct DevPlan {
     const int *src_perm;    // [Q] sorted -> user index k = j*q + s
     const void *src_w;      // T [Q] w_s |S_j| in sorted order
     const void *tri_nrm;    // T4 [M] outward unit normals (user triangle order)
-    const int4 *tri_vtx;    // [M] vertex ids
+    const int4 *tri_vtx;    // [M] vertex ids as sorted target positions
     const void *lam;        // T [q*3] barycentric points of the rule
     // targets, sorted
     const void *tgt_grid;   // T4 [N]
@@ -56,6 +58,7 @@ struct DevPlan {
 
     // scratch (written during evaluation)
     void *qbuf;    // T [Q] weighted charges, sorted order
+    void *m4;      // T4 [N] nodal magnetisation in sorted target order (NODAL_MAG input)
     void *gridA;   // T [Lz][Ly][Lx] spread grid (kept zero between evaluations)
     void *gridB;   // T [Lz][Ly][Lx] interpolation grid
     void *S1;      // T2 [Lz][Ly][Kx]
@@ -65,6 +68,7 @@ struct DevPlan {
     const void *tw[3];  // T2 [L_q] forward twiddles exp(-2 pi i t / L_q)
 
     const TileItem *spread_items; int n_spread;
+    int spread_chunk;             // most sources in one spread item
     const TileItem *gather_items; int n_gather;
     const NearItem *near_items;   int n_near;
     const int2 *near_ranges;
@@ -84,8 +88,10 @@ struct DevPlan {
 };
 
 // Kernel launchers (return the launch error, if any).
+cudaError_t launch_nodal_prep(const DevPlan &p, const void *d_in, cudaStream_t s);
 cudaError_t launch_charges(const DevPlan &p, int kind, const void *d_in, cudaStream_t s);
-cudaError_t launch_spread(const DevPlan &p, cudaStream_t s);
+// fused_kind >= 0: compute the charges of that input kind inside the spread (no qbuf)
+cudaError_t launch_spread(const DevPlan &p, int fused_kind, const void *d_in, cudaStream_t s);
 cudaError_t launch_fft_forward_x(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_forward_y(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_z_multiply(const DevPlan &p, cudaStream_t s);

@@ -130,6 +130,50 @@ double erfc_inv(double y) {
     return 0.5 * (lo + hi);
 }
 
+// Per-interval polynomial of the window for the FP32 kernels:
+// p_i(f) = sum_k c[i][k] f^k interpolates psi(f + m - 1 - i) at deg + 1
+// Chebyshev nodes of f in [0, 1] (psi = sinh(beta s)/s is entire in the
+// offset, so the interpolant converges geometrically: degree 9 is within
+// 1e-10 of psi(0) for m <= 6).
+std::vector<double> window_polynomials(int m, int deg) {
+    const int n = deg + 1;
+    std::vector<double> out((size_t)2 * m * n, 0.0);
+    std::vector<double> x(n);
+    for (int k = 0; k < n; ++k) x[k] = 0.5 - 0.5 * std::cos(PI * (k + 0.5) / n);
+    for (int i = 0; i < 2 * m; ++i) {
+        // Vandermonde system A c = y, Gaussian elimination with partial pivoting
+        std::vector<double> A((size_t)n * n), y(n);
+        for (int r = 0; r < n; ++r) {
+            double pw = 1.0;
+            for (int c = 0; c < n; ++c) {
+                A[(size_t)r * n + c] = pw;
+                pw *= x[r];
+            }
+            y[r] = kb_window_host(m, x[r] + m - 1 - i);
+        }
+        for (int c = 0; c < n; ++c) {
+            int piv = c;
+            for (int r = c + 1; r < n; ++r)
+                if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = r;
+            if (piv != c) {
+                for (int cc = 0; cc < n; ++cc) std::swap(A[(size_t)c * n + cc], A[(size_t)piv * n + cc]);
+                std::swap(y[c], y[piv]);
+            }
+            for (int r = c + 1; r < n; ++r) {
+                const double f = A[(size_t)r * n + c] / A[(size_t)c * n + c];
+                for (int cc = c; cc < n; ++cc) A[(size_t)r * n + cc] -= f * A[(size_t)c * n + cc];
+                y[r] -= f * y[c];
+            }
+        }
+        for (int r = n - 1; r >= 0; --r) {
+            double v = y[r];
+            for (int cc = r + 1; cc < n; ++cc) v -= A[(size_t)r * n + cc] * out[(size_t)i * n + cc];
+            out[(size_t)i * n + r] = v / A[(size_t)r * n + r];
+        }
+    }
+    return out;
+}
+
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
 
 int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
@@ -437,11 +481,11 @@ slp_status choose_parameters(slp_plan_s &p) {
     for (int d = 0; d < 3; ++d)
         if (!(p.P[d] > p.D[d])) return fail(SLP_ERR_INVALID_ARG, "period does not contain the mesh");
 
-    // tile size: a halo tile of at most 28 KB, so the spread can give several
-    // warps a private copy each
+    // tile size: 4^3 cells, halved while a halo tile (padded layout of the
+    // spread/gather kernels) exceeds 40 KB, so several warps get a private copy
     const size_t esz = p.prec == 64 ? 8 : 4;
-    p.TS = 8;
-    while (p.TS > 2 && std::pow((double)(p.TS + 2 * p.m - 1), 3) * esz > 28 * 1024) p.TS /= 2;
+    p.TS = 4;
+    while (p.TS > 2 && std::pow((double)(p.TS + 2 * p.m + 3), 3) * esz > 40 * 1024) p.TS /= 2;
     p.TE = p.TS + 2 * p.m - 1;
     return SLP_OK;
 }
@@ -749,6 +793,15 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     d.TS = p.TS;
     d.TE = p.TE;
     d.beta = KB_B * p.m;
+    {
+        const int deg = 9;
+        const std::vector<double> wc = window_polynomials(p.m, deg);
+        std::vector<float> wcf(wc.begin(), wc.end());
+        void *wp;
+        TRY(upload(p, &wp, wcf.data(), wcf.size()));
+        d.wcoef = wp;
+        d.wdeg = deg;
+    }
     d.inv_sinh_beta = 1.0 / std::sinh(d.beta);
     d.eps2 = std::isfinite(p.eps) ? p.eps * p.eps : 1e300;
     d.inv_s_sqrt2 = p.sigma_g > 0 ? 1.0 / (p.sigma_g * std::sqrt(2.0)) : 0.0;
@@ -800,12 +853,14 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     for (int64_t i = 0; i < p.Q; ++i) sw[i] = (T)p.wk[p.src_perm[i]];
     std::vector<T4> tn(p.M);
     std::vector<int4> tv(p.M);
+    std::vector<int> inv_tperm(p.N);
+    for (int64_t i = 0; i < p.N; ++i) inv_tperm[p.tgt_perm[i]] = (int)i;
     for (int64_t j = 0; j < p.M; ++j) {
         tn[j].x = (T)p.nrm[3 * j];
         tn[j].y = (T)p.nrm[3 * j + 1];
         tn[j].z = (T)p.nrm[3 * j + 2];
         tn[j].w = T(0);
-        tv[j] = make_int4(p.T[3 * j], p.T[3 * j + 1], p.T[3 * j + 2], 0);
+        tv[j] = make_int4(inv_tperm[p.T[3 * j]], inv_tperm[p.T[3 * j + 1]], inv_tperm[p.T[3 * j + 2]], 0);
     }
     std::vector<T> lamT(p.lam.begin(), p.lam.end());
     void *ptr;
@@ -830,6 +885,7 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     const int64_t G = (int64_t)p.L[0] * p.L[1] * p.L[2];
     const int Kx = p.n[0] / 2;
     TRY(dalloc(p, &d.qbuf, sizeof(T) * p.Q));
+    TRY(dalloc(p, &d.m4, 4 * sizeof(T) * p.N));
     TRY(dalloc(p, &d.gridA, sizeof(T) * G));
     TRY(dalloc(p, &d.gridB, sizeof(T) * G));
     TRY(dalloc(p, &d.S1, sizeof(T2) * (size_t)p.L[2] * p.L[1] * Kx));
@@ -852,6 +908,8 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     TRY(upload(p, &ptr, p.spread_items.data(), p.spread_items.size()));
     d.spread_items = (const slp::TileItem *)ptr;
     d.n_spread = (int)p.spread_items.size();
+    d.spread_chunk = 1;
+    for (const auto &it : p.spread_items) d.spread_chunk = std::max(d.spread_chunk, it.end - it.begin);
     TRY(upload(p, &ptr, p.gather_items.data(), p.gather_items.size()));
     d.gather_items = (const slp::TileItem *)ptr;
     d.n_gather = (int)p.gather_items.size();
@@ -879,7 +937,8 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     // staging buffers for slp_eval_host
     TRY(dalloc(p, &p.d_stage_in, sizeof(T) * 3 * std::max(p.Q, p.N)));
     TRY(dalloc(p, &p.d_stage_phi, sizeof(T) * p.N));
-    p.launches_per_eval = 9 + (p.opts.deterministic ? 1 : 0);
+    // for NODAL_MAG input: prep, charges, spread, 5 FFT passes, gather, near field (+ ordered reduction)
+    p.launches_per_eval = 10 + (p.opts.deterministic ? 1 : 0);
     return SLP_OK;
 }
 
@@ -1107,6 +1166,7 @@ slp_status build_near_matrix(slp_plan_s &p, const std::vector<uint64_t> &tkeys) 
     p.dp.nm_nnz = nnz;
     p.nm_nnz = nnz;
     p.near_mode = SLP_NEAR_PRECOMPUTED;
+    p.launches_per_eval = 9;  // prep, spread (charges fused), 5 FFT passes, gather, near-field product
     return SLP_OK;
 }
 
@@ -1130,11 +1190,16 @@ slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, 
         if (ev) cudaEventRecord(ev[k], s);
         ++k;
     };
+    // nodal input with the precomputed near field: the charges are only needed
+    // by the spread, which computes them itself
+    const bool use_matrix = kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
+    const bool fuse = use_matrix && last > SLP_STAGE_CHARGES;
     rec();
-    TRY(cuda_status(slp::launch_charges(d, kind, d_in, s), "charges"));
+    if (kind == SLP_INPUT_NODAL_MAG) TRY(cuda_status(slp::launch_nodal_prep(d, d_in, s), "nodal prep"));
+    if (!fuse) TRY(cuda_status(slp::launch_charges(d, kind, d_in, s), "charges"));
     rec();
     if (last <= SLP_STAGE_CHARGES) return SLP_OK;
-    TRY(cuda_status(slp::launch_spread(d, s), "spread"));
+    TRY(cuda_status(slp::launch_spread(d, fuse ? kind : -1, d_in, s), "spread"));
     rec();
     if (last <= SLP_STAGE_SPREAD) return SLP_OK;
     TRY(cuda_status(slp::launch_fft_forward_x(d, s), "fft x"));
@@ -1155,7 +1220,6 @@ slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, 
     TRY(cuda_status(slp::launch_gather(d, d_phi, s), "gather"));
     rec();
     if (last <= SLP_STAGE_GATHER) return SLP_OK;
-    const bool use_matrix = kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
     if (use_matrix) {
         TRY(cuda_status(slp::launch_near_matrix(d, d_in, d_phi, s), "near-field matrix"));
         rec();
@@ -1251,7 +1315,7 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
         ch = std::max<int64_t>(128, std::min<int64_t>(1024, (ch + 31) / 32 * 32));
         tile_items(*p, p->src_grid, skeys, p->Q, (int)ch, p->spread_items);
     }
-    tile_items(*p, p->tgt_grid, tkeys, p->N, 256, p->gather_items);
+    tile_items(*p, p->tgt_grid, tkeys, p->N, 32, p->gather_items);
     near_items(*p, skeys, tkeys);
     build_dtab(*p);
     p->near_mode = SLP_NEAR_ON_THE_FLY;
