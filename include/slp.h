@@ -72,7 +72,7 @@ enum { SLP_INPUT_SIGMA = 0, SLP_INPUT_MAG = 1, SLP_INPUT_NODAL_MAG = 2 };
  *              near and the near kernel is N - N_s evaluated exactly
  *              (for grids too small to resolve RADIAL at the tolerance);
  *   AUTO:      RADIAL when feasible on the grid, else SEPARABLE for small
- *              meshes, else a raised grid (when allowed). */
+ *              meshes at precision 64, else a raised grid (when allowed). */
 enum { SLP_KERNEL_AUTO = 0, SLP_KERNEL_RADIAL = 1, SLP_KERNEL_SEPARABLE = 2 };
 
 /* Near-field evaluation:
@@ -189,6 +189,45 @@ slp_status slp_eval_host(slp_plan_t plan, int input_kind, const void *h_in, void
 slp_status slp_eval_direct_static(const double *d_vertices, int64_t n_vertices, const int32_t *d_triangles,
                                   int64_t n_triangles, int quadrature, int precision, int input_kind,
                                   const void *d_in, void *d_phi, void *stream);
+
+/* ---- Batched evaluation (many states, many meshes, one CUDA graph) ----
+ * An item evaluates plans[plan_of[i]] on d_in[i] -> d_phi[i] (device buffers
+ * with the layouts of slp_eval; they must stay valid and fixed for the life of
+ * the batch: the caller refills d_in and reads d_phi between runs).
+ * lanes_per_plan (1..64) scratch sets per plan run that plan's items
+ * concurrently on separate streams (lane 0 is the plan's own scratch, the
+ * others are allocated here); items are dealt round-robin to the lanes.
+ * slp_batch_create captures every item into one CUDA graph (fork/join over
+ * the lanes); slp_batch_run launches it on `stream`.  All plans must share a
+ * device.  A plan must not be evaluated elsewhere while a batch that uses it
+ * runs (lane 0 shares the plan's scratch). */
+typedef struct slp_batch_s *slp_batch_t;
+slp_status slp_batch_create(int n_plans, const slp_plan_t *plans, int n_items, const int *plan_of, int input_kind,
+                            const void *const *d_in, void *const *d_phi, int lanes_per_plan, slp_batch_t *out);
+slp_status slp_batch_run(slp_batch_t batch, void *stream);
+slp_status slp_batch_query(slp_batch_t batch, int64_t *n_items, int64_t *n_lanes, int64_t *kernel_launches,
+                           int64_t *extra_scratch_bytes);
+slp_status slp_batch_destroy(slp_batch_t batch);
+
+/* ---- Grid autotuner ----
+ * Considers equal-spacing grids whose largest axis spans 32, 64, ..., 512
+ * cells (powers of two per axis), drops grids that cannot meet the tolerance
+ * (allow_grid_raise is forced off), ranks the rest by a cost model from
+ * host-only plans (grid points, near-field pairs, sources), builds the two
+ * cheapest on the opts' device, times `reps` evaluations of each with nodal
+ * input, and returns the faster plan in *out.  info (may be NULL) receives every candidate's grid
+ * and mean milliseconds and the index chosen.  The remaining opts apply to
+ * every candidate. */
+#define SLP_TUNE_MAX 8
+typedef struct {
+    int n_candidates;
+    int chosen;
+    int grid[SLP_TUNE_MAX][3];
+    double ms[SLP_TUNE_MAX];
+    int kernel_mode[SLP_TUNE_MAX];
+} slp_tune_info;
+slp_status slp_plan_autotune(const slp_mesh *mesh, int quadrature, double tolerance, const slp_plan_opts *opts,
+                             int reps, slp_plan_t *out, slp_tune_info *info);
 
 /* Plan parameters and sizes. */
 slp_status slp_query(slp_plan_t plan, slp_info *info);

@@ -63,6 +63,21 @@ class slp_plan_opts(ctypes.Structure):
                 ("reserved", ctypes.c_int * 7)]
 
 
+SLP_TUNE_MAX = 8
+
+
+class slp_tune_info(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int), ("chosen", ctypes.c_int),
+                ("grid", (ctypes.c_int * 3) * SLP_TUNE_MAX), ("ms", ctypes.c_double * SLP_TUNE_MAX),
+                ("kernel_mode", ctypes.c_int * SLP_TUNE_MAX)]
+
+    def to_dict(self):
+        n = self.n_candidates
+        return {"chosen": self.chosen,
+                "candidates": [{"grid": list(self.grid[i]), "ms": self.ms[i], "kernel_mode": self.kernel_mode[i]}
+                               for i in range(n)]}
+
+
 class slp_info(ctypes.Structure):
     _fields_ = [("n_targets", ctypes.c_int64), ("n_sources", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
                 ("quadrature", ctypes.c_int), ("precision", ctypes.c_int), ("grid", ctypes.c_int * 3),
@@ -93,7 +108,8 @@ EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_host", "slp_qu
             "slp_check", "slp_destroy", "slp_status_string", "slp_last_error",
             "slp_debug_run", "slp_debug_copy", "slp_debug_buffer_bytes", "slp_debug_host_count",
             "slp_debug_host_array", "slp_debug_window", "slp_debug_window_hat", "slp_debug_profile",
-            "slp_debug_stage_name", "slp_eval_direct_static"]
+            "slp_debug_stage_name", "slp_eval_direct_static", "slp_batch_create", "slp_batch_run",
+            "slp_batch_query", "slp_batch_destroy", "slp_plan_autotune"]
 
 
 def library_path() -> str:
@@ -134,6 +150,13 @@ def load():
         "slp_debug_profile": ([vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int], St),
         "slp_debug_stage_name": ([ctypes.c_int], ctypes.c_char_p),
         "slp_eval_direct_static": ([vp, I64, vp, I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp], St),
+        "slp_batch_create": ([ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                              ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)], St),
+        "slp_batch_run": ([vp, vp], St),
+        "slp_batch_query": ([vp, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)], St),
+        "slp_batch_destroy": ([vp], St),
+        "slp_plan_autotune": ([ctypes.POINTER(slp_mesh), ctypes.c_int, ctypes.c_double, ctypes.POINTER(slp_plan_opts),
+                               ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(slp_tune_info)], St),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -205,6 +228,51 @@ def slp_eval_direct_static(d_vertices, n_vertices, d_triangles, n_triangles, qua
     _check(load().slp_eval_direct_static(_ptr(d_vertices), int(n_vertices), _ptr(d_triangles), int(n_triangles),
                                          int(quadrature), int(precision), int(input_kind), _ptr(d_in), _ptr(d_phi),
                                          _stream(stream)), "slp_eval_direct_static")
+
+
+def slp_batch_create(plans, plan_of, input_kind, d_in, d_phi, lanes_per_plan=1):
+    """Capture items (plans[plan_of[i]], d_in[i] -> d_phi[i]) into one CUDA graph; returns the batch handle."""
+    n_plans = len(plans)
+    n_items = len(plan_of)
+    P = (ctypes.c_void_p * n_plans)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    po = (ctypes.c_int * n_items)(*[int(i) for i in plan_of])
+    ins = (ctypes.c_void_p * n_items)(*[_ptr(x).value for x in d_in])
+    outs = (ctypes.c_void_p * n_items)(*[_ptr(x).value for x in d_phi])
+    out = ctypes.c_void_p()
+    _check(load().slp_batch_create(n_plans, P, n_items, po, int(input_kind), ins, outs, int(lanes_per_plan),
+                                   ctypes.byref(out)), "slp_batch_create")
+    return out
+
+
+def slp_batch_run(batch, stream=None):
+    _check(load().slp_batch_run(batch, _stream(stream)), "slp_batch_run")
+
+
+def slp_batch_query(batch) -> dict:
+    a, b, c, d = (ctypes.c_int64() for _ in range(4))
+    _check(load().slp_batch_query(batch, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+           "slp_batch_query")
+    return {"n_items": a.value, "n_lanes": b.value, "kernel_launches": c.value, "extra_scratch_bytes": d.value}
+
+
+def slp_batch_destroy(batch):
+    if batch is not None:
+        _check(load().slp_batch_destroy(batch), "slp_batch_destroy")
+
+
+def slp_plan_autotune(vertices, triangles, quadrature, tolerance, opts=None, reps=5):
+    """Plan on candidate grids, time each, keep the fastest; returns (plan handle, tuning record)."""
+    lib = load()
+    V = np.ascontiguousarray(vertices, dtype=np.float64)
+    T = np.ascontiguousarray(triangles, dtype=np.int32)
+    mesh = slp_mesh(V.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), V.shape[0],
+                    T.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), T.shape[0])
+    o = opts if opts is not None else slp_default_opts()
+    out = ctypes.c_void_p()
+    ti = slp_tune_info()
+    _check(lib.slp_plan_autotune(ctypes.byref(mesh), int(quadrature), float(tolerance), ctypes.byref(o), int(reps),
+                                 ctypes.byref(out), ctypes.byref(ti)), "slp_plan_autotune")
+    return out, ti.to_dict()
 
 
 def slp_query(plan) -> dict:

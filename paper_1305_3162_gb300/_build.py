@@ -20,7 +20,7 @@ LIB = os.path.join(LIB_DIR, "libslp_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 CU_SOURCES = ["k_grid.cu", "k_fft.cu", "k_near.cu", "k_static.cu"]
-CPP_SOURCES = ["slp_plan.cpp"]
+CPP_SOURCES = ["slp_plan.cpp", "slp_batch.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

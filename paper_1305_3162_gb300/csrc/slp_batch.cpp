@@ -1,0 +1,318 @@
+// Batched evaluation (many magnetisation states and many meshes of uneven
+// size in one CUDA graph) and the grid autotuner.
+//
+// A batch is a list of items (plan, input buffer, output buffer).  Each plan
+// gets `lanes` scratch sets (its own plus lanes - 1 extra); the items of a
+// plan are dealt round-robin to its lanes, and every lane runs its items in
+// order on a stream of its own.  The whole set is captured once into a graph
+// (fork from the launch stream, one branch per lane, join), so a run is one
+// graph launch: small meshes and independent states overlap on the device
+// and no per-kernel launch cost is paid on the host.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "slp_plan_internal.h"
+
+struct slp_batch_s {
+    int device = 0;
+    std::vector<void *> allocs;      // extra scratch sets
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int n_items = 0;
+    int n_lanes = 0;
+    int64_t launches = 0;
+    int64_t scratch_bytes = 0;
+};
+
+namespace {
+
+void release(slp_batch_s *b) {
+    if (!b) return;
+    SlpDeviceGuard g(b->device);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    for (void *p : b->allocs) cudaFree(p);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+slp_status slp_batch_create(int n_plans, const slp_plan_t *plans, int n_items, const int *plan_of, int input_kind,
+                            const void *const *d_in, void *const *d_phi, int lanes_per_plan, slp_batch_t *out) {
+    if (!out) return slp_fail(SLP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n_plans < 1 || !plans || n_items < 1 || !plan_of || !d_in || !d_phi)
+        return slp_fail(SLP_ERR_INVALID_ARG, "empty batch or NULL array");
+    if (input_kind < SLP_INPUT_SIGMA || input_kind > SLP_INPUT_NODAL_MAG)
+        return slp_fail(SLP_ERR_INVALID_ARG, "unknown input kind %d", input_kind);
+    if (lanes_per_plan < 1 || lanes_per_plan > 64) return slp_fail(SLP_ERR_INVALID_ARG, "lanes_per_plan must be 1..64");
+    const int dev = plans[0] ? plans[0]->device : -1;
+    for (int i = 0; i < n_plans; ++i) {
+        if (!plans[i]) return slp_fail(SLP_ERR_INVALID_ARG, "plan %d is NULL", i);
+        if (plans[i]->device < 0) return slp_fail(SLP_ERR_NO_DEVICE, "plan %d is host-only", i);
+        if (plans[i]->device != dev) return slp_fail(SLP_ERR_INVALID_ARG, "all plans of a batch must share a device");
+    }
+    std::vector<std::vector<int>> items_of(n_plans);
+    for (int i = 0; i < n_items; ++i) {
+        if (plan_of[i] < 0 || plan_of[i] >= n_plans) return slp_fail(SLP_ERR_INVALID_ARG, "item %d: bad plan index", i);
+        if (!d_in[i] || !d_phi[i]) return slp_fail(SLP_ERR_INVALID_ARG, "item %d: NULL buffer", i);
+        items_of[plan_of[i]].push_back(i);
+    }
+    SlpDeviceGuard g(dev);
+    slp_batch_s *b = new slp_batch_s();
+    b->device = dev;
+    b->n_items = n_items;
+    // lanes: (plan, device view) pairs
+    struct Lane {
+        int plan;
+        slp::DevPlan view;
+        std::vector<int> items;
+    };
+    std::vector<Lane> lanes;
+    for (int pi = 0; pi < n_plans; ++pi) {
+        if (items_of[pi].empty()) continue;
+        const int nl = std::min<int>(lanes_per_plan, (int)items_of[pi].size());
+        for (int l = 0; l < nl; ++l) {
+            Lane ln;
+            ln.plan = pi;
+            if (l == 0) {
+                ln.view = plans[pi]->dp;
+            } else {
+                int64_t nb = 0;
+                const slp_status st = slp_alloc_scratch(*plans[pi], ln.view, b->allocs, &nb);
+                if (st != SLP_OK) {
+                    release(b);
+                    return st;
+                }
+                b->scratch_bytes += nb;
+            }
+            lanes.push_back(ln);
+        }
+        const size_t first = lanes.size() - nl;
+        for (size_t k = 0; k < items_of[pi].size(); ++k) lanes[first + k % nl].items.push_back(items_of[pi][k]);
+    }
+    b->n_lanes = (int)lanes.size();
+    // streams and events for the capture
+    cudaStream_t s0;
+    if (cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking) != cudaSuccess) {
+        release(b);
+        return slp_fail(SLP_ERR_CUDA, "cudaStreamCreate failed");
+    }
+    b->streams.push_back(s0);
+    for (size_t l = 0; l < lanes.size(); ++l) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            release(b);
+            return slp_fail(SLP_ERR_CUDA, "stream/event creation failed");
+        }
+        b->streams.push_back(s);
+        b->events.push_back(e);
+    }
+    cudaEvent_t fork;
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) {
+        release(b);
+        return slp_fail(SLP_ERR_CUDA, "event creation failed");
+    }
+    b->events.push_back(fork);
+    // capture: fork, one branch per lane, join
+    slp_status st = SLP_OK;
+    if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        release(b);
+        return slp_fail(SLP_ERR_CUDA, "cudaStreamBeginCapture failed");
+    }
+    cudaEventRecord(fork, s0);
+    for (size_t l = 0; l < lanes.size() && st == SLP_OK; ++l) {
+        cudaStream_t s = b->streams[l + 1];
+        cudaStreamWaitEvent(s, fork, 0);
+        slp_plan_s &p = *plans[lanes[l].plan];
+        for (int it : lanes[l].items) {
+            st = slp_run_pipeline(p, lanes[l].view, input_kind, d_in[it], d_phi[it], s, SLP_STAGE_NEAR, nullptr);
+            if (st != SLP_OK) break;
+            b->launches += p.launches_per_eval;
+        }
+        cudaEventRecord(b->events[l], s);
+        cudaStreamWaitEvent(s0, b->events[l], 0);
+    }
+    const cudaError_t ce = cudaStreamEndCapture(s0, &b->graph);
+    if (st != SLP_OK || ce != cudaSuccess) {
+        if (st == SLP_OK) st = slp_fail(SLP_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(ce));
+        cudaGetLastError();
+        release(b);
+        return st;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (ie != cudaSuccess) {
+        cudaGetLastError();
+        release(b);
+        return slp_fail(SLP_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ie));
+    }
+    *out = b;
+    return SLP_OK;
+}
+
+slp_status slp_batch_run(slp_batch_t b, void *stream) {
+    if (!b) return slp_fail(SLP_ERR_INVALID_ARG, "batch is NULL");
+    SlpDeviceGuard g(b->device);
+    const cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return slp_fail(SLP_ERR_CUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    return SLP_OK;
+}
+
+slp_status slp_batch_query(slp_batch_t b, int64_t *n_items, int64_t *n_lanes, int64_t *launches, int64_t *scratch_bytes) {
+    if (!b) return slp_fail(SLP_ERR_INVALID_ARG, "batch is NULL");
+    if (n_items) *n_items = b->n_items;
+    if (n_lanes) *n_lanes = b->n_lanes;
+    if (launches) *launches = b->launches;
+    if (scratch_bytes) *scratch_bytes = b->scratch_bytes;
+    return SLP_OK;
+}
+
+slp_status slp_batch_destroy(slp_batch_t b) {
+    release(b);
+    return SLP_OK;
+}
+
+// ------------------------------------------------------------------ autotuner
+// Candidate grids of equal spacing, the largest axis spanning 32 .. 512 cells
+// (powers of two, each axis the nearest power of two to its share); every
+// candidate that meets the tolerance is planned and timed over `reps`
+// evaluations of a fixed pseudo-random nodal field; the fastest plan is kept.
+slp_status slp_plan_autotune(const slp_mesh *mesh, int quadrature, double tolerance, const slp_plan_opts *opts,
+                             int reps, slp_plan_t *out, slp_tune_info *info) {
+    if (!out || !mesh) return slp_fail(SLP_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    slp_plan_opts o;
+    if (opts)
+        o = *opts;
+    else
+        slp_default_opts(&o);
+    if (o.device < 0) return slp_fail(SLP_ERR_NO_DEVICE, "the autotuner times evaluations on a device");
+    if (reps < 1) reps = 5;
+    // extent per axis (for the grid shapes)
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = 0; i < mesh->n_vertices; ++i)
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = std::min(lo[d], mesh->vertices[3 * i + d]);
+            hi[d] = std::max(hi[d], mesh->vertices[3 * i + d]);
+        }
+    double ext[3], emax = 0.0, diam2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        ext[d] = hi[d] - lo[d];
+        diam2 += ext[d] * ext[d];
+        emax = std::max(emax, ext[d]);
+    }
+    const double diam = std::sqrt(diam2);
+    SlpDeviceGuard g(o.device);
+    const int prec = o.precision;
+    const size_t es = prec == 64 ? 8 : 4;
+    // pseudo-random nodal input on the device
+    const int64_t N = mesh->n_vertices;
+    std::vector<float> hin32(3 * N);
+    std::vector<double> hin64(3 * N);
+    uint64_t state = 0x9E3779B97F4A7C15ull;
+    for (int64_t i = 0; i < 3 * N; ++i) {
+        state = state * 6364136223846793005ull + 1442695040888963407ull;
+        const double v = (double)(state >> 11) / (double)(1ull << 53) - 0.5;
+        hin32[i] = (float)v;
+        hin64[i] = v;
+    }
+    void *d_in = nullptr, *d_out = nullptr;
+    if (cudaMalloc(&d_in, es * 3 * N) != cudaSuccess || cudaMalloc(&d_out, es * N) != cudaSuccess) {
+        cudaGetLastError();
+        if (d_in) cudaFree(d_in);
+        return slp_fail(SLP_ERR_OOM, "autotune buffers");
+    }
+    cudaMemcpy(d_in, prec == 64 ? (const void *)hin64.data() : (const void *)hin32.data(), es * 3 * N,
+               cudaMemcpyHostToDevice);
+    cudaStream_t s;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    slp_plan_t best = nullptr;
+    double best_ms = 1e300;
+    int ntried = 0;
+    slp_tune_info ti;
+    memset(&ti, 0, sizeof ti);
+    // candidates, ranked by a cost model evaluated on host-only plans:
+    // t ~ 2.5e-11 s per grid point (five FFT passes) + 2.5e-13 s per near pair
+    // visited + 2.4e-10 s per source (spread), fitted on GB300 measurements;
+    // only the two cheapest are built on the device and timed
+    struct Cand {
+        slp_plan_opts o;
+        double model;
+    };
+    std::vector<Cand> cands;
+    for (int cells = 32; cells <= 512; cells *= 2) {
+        slp_plan_opts oc = o;
+        for (int d = 0; d < 3; ++d) {
+            const double want = cells * (ext[d] + diam) / (emax + diam);
+            int v = 8;
+            while (v * 2 <= 1024 && v * 1.41421356 < want) v <<= 1;
+            oc.grid[d] = v;
+        }
+        oc.allow_grid_raise = 0;
+        slp_plan_opts oh = oc;
+        oh.device = -1;
+        slp_plan_t hp = nullptr;
+        if (slp_plan(mesh, quadrature, tolerance, &oh, &hp) != SLP_OK) continue;  // infeasible
+        slp_info hi_;
+        slp_query(hp, &hi_);
+        slp_destroy(hp);
+        const double G = (double)hi_.grid[0] * hi_.grid[1] * hi_.grid[2];
+        cands.push_back({oc, 2.5e-11 * G + 2.5e-13 * (double)hi_.near_pairs + 2.4e-10 * (double)hi_.n_sources});
+    }
+    std::sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b2) { return a.model < b2.model; });
+    if (cands.size() > 2) cands.resize(2);
+    for (const Cand &cand : cands) {
+        if (ntried >= SLP_TUNE_MAX) break;
+        slp_plan_opts oc = cand.o;
+        slp_plan_t p = nullptr;
+        if (slp_plan(mesh, quadrature, tolerance, &oc, &p) != SLP_OK) continue;
+        // time reps evaluations (after one warm-up)
+        slp_status st = slp_eval(p, SLP_INPUT_NODAL_MAG, d_in, d_out, s);
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == SLP_OK; ++r) st = slp_eval(p, SLP_INPUT_NODAL_MAG, d_in, d_out, s);
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (st == SLP_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        slp_info inf;
+        slp_query(p, &inf);
+        for (int d = 0; d < 3; ++d) ti.grid[ntried][d] = inf.grid[d];
+        ti.ms[ntried] = st == SLP_OK ? ms : -1.0;
+        ti.kernel_mode[ntried] = inf.kernel_mode;
+        ++ntried;
+        if (st == SLP_OK && ms < best_ms) {
+            if (best) slp_destroy(best);
+            best = p;
+            best_ms = ms;
+            ti.chosen = ntried - 1;
+        } else {
+            slp_destroy(p);
+        }
+    }
+    ti.n_candidates = ntried;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(s);
+    cudaFree(d_in);
+    cudaFree(d_out);
+    if (!best) return slp_fail(SLP_ERR_TOLERANCE_INFEASIBLE, "no candidate grid meets the tolerance");
+    *out = best;
+    if (info) *info = ti;
+    return SLP_OK;
+}
+
+}  // extern "C"

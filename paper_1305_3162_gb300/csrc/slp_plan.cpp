@@ -29,9 +29,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/slp.h"
-#include "../../include/slp_debug.h"
-#include "slp_internal.h"
+#include "slp_plan_internal.h"
 
 namespace {
 
@@ -191,58 +189,10 @@ uint32_t morton3(uint32_t x, uint32_t y, uint32_t z) {
 
 // error-budget factors of the RADIAL split (relative to the tolerance):
 // band-limit tail of the Gaussian and the erfc tail left outside eps.
-const double KFAC = 30.0;
+const double KFAC = 10.0;
 const double NFAC = 2.0;
 
 }  // namespace
-
-// ======================================================================= plan
-struct slp_plan_s {
-    // configuration
-    slp_plan_opts opts;
-    int q = 0;
-    int prec = 32;
-    double tol = 0;
-    int64_t N = 0, M = 0, Q = 0;
-    int device = 0;
-
-    // geometry (host, FP64)
-    std::vector<double> V;       // [N][3]
-    std::vector<int32_t> T;      // [M][3]
-    std::vector<double> lam, wq; // rule
-    std::vector<double> y;       // [Q][3] user order
-    std::vector<double> wk;      // [Q]
-    std::vector<double> nrm;     // [M][3]
-
-    // parameters
-    int L[3] = {0, 0, 0}, n[3] = {0, 0, 0}, m = 0, TS = 8, TE = 0;
-    int kernel_mode = SLP_KERNEL_RADIAL, near_mode = SLP_NEAR_ON_THE_FLY;
-    int grid_raised = 0;
-    double ctr[3] = {0, 0, 0}, P[3] = {0, 0, 0}, D[3] = {0, 0, 0};
-    double diam = 0, sigma_g = 0, R = 0, eps = 0, c_band = 0;
-    double sep_A = 0;
-    std::vector<double> sep_h[3];
-
-    // sorted data (host)
-    std::vector<int32_t> src_perm, tgt_perm;
-    std::vector<double> src_grid, tgt_grid;  // [.][4]
-    std::vector<slp::TileItem> spread_items, gather_items;
-    std::vector<slp::NearItem> near_items;
-    std::vector<int2> near_ranges;
-    std::vector<int> near_blk_first;  // CSR of items per target block
-    std::vector<double> Dtab;
-    int64_t near_pairs = 0;
-
-    // device
-    slp::DevPlan dp;
-    std::vector<void *> allocs;
-    int64_t bytes_device = 0;
-    void *d_stage_in = nullptr, *d_stage_phi = nullptr;
-    int *d_blk_first = nullptr;
-    int launches_per_eval = 0;
-    int64_t near_pairs_within = -1;
-    int64_t nm_nnz = 0;
-};
 
 namespace {
 
@@ -398,8 +348,8 @@ slp_status choose_parameters(slp_plan_s &p) {
     if (mode == SLP_KERNEL_AUTO) {
         if (radial_feasible(p, nreq, c))
             mode = SLP_KERNEL_RADIAL;
-        else if ((double)p.Q * (double)p.N <= (double)(1 << 24))
-            mode = SLP_KERNEL_SEPARABLE;
+        else if (p.prec == 64 && (double)p.Q * (double)p.N <= (double)(1 << 24))
+            mode = SLP_KERNEL_SEPARABLE;  // FP64 only: in FP32 the all-pairs difference loses digits
         else if (p.opts.allow_grid_raise)
             mode = -SLP_KERNEL_RADIAL;  // radial after raising the grid
         else
@@ -463,14 +413,14 @@ slp_status choose_parameters(slp_plan_s &p) {
                 p.sep_h[d][l] = std::exp(-2.0 * t * t);
             }
         }
-        // scale: K_n(0) = 1 / (4 pi diam / 2)
+        // scale: K_n(0) = 0.1 / (4 pi diam), a small smooth part next to 1/(4 pi r)
         double k0 = 1.0;
         for (int d = 0; d < 3; ++d) {
             double f = p.sep_h[d][0];
             for (size_t l = 1; l < p.sep_h[d].size(); ++l) f += 2.0 * p.sep_h[d][l];
             k0 *= f;
         }
-        p.sep_A = 1.0 / (4.0 * PI * 0.5 * p.diam) / k0;
+        p.sep_A = 0.1 / (4.0 * PI * p.diam) / k0;
         p.eps = INFINITY;
         p.sigma_g = 0;
         p.R = 0;
@@ -1182,9 +1132,8 @@ const int N_STAGE_NAMES = 10;
 
 // Enqueue the evaluation up to stage `last`.  With ev != NULL, ev[i] is
 // recorded before kernel i and ev[i + 1] after it (ev has N_STAGE_NAMES + 1 entries).
-slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, cudaStream_t s, int last,
-                        cudaEvent_t *ev = nullptr) {
-    const slp::DevPlan &d = p.dp;
+slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *d_in, void *d_phi,
+                        cudaStream_t s, int last, cudaEvent_t *ev) {
     int k = 0;
     auto rec = [&]() {
         if (ev) cudaEventRecord(ev[k], s);
@@ -1235,6 +1184,11 @@ slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, 
     return SLP_OK;
 }
 
+slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, cudaStream_t s, int last,
+                        cudaEvent_t *ev = nullptr) {
+    return run_pipeline(p, p.dp, kind, d_in, d_phi, s, last, ev);
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -1251,6 +1205,65 @@ struct DeviceGuard {
 }  // namespace
 
 void slp::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+slp_status slp_fail(slp_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+slp_status slp_run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *d_in, void *d_phi,
+                            cudaStream_t s, int last, cudaEvent_t *ev) {
+    return run_pipeline(p, d, kind, d_in, d_phi, s, last, ev);
+}
+
+int64_t slp_scratch_bytes(const slp_plan_s &p) {
+    const int64_t es = p.prec == 64 ? 8 : 4;
+    const int64_t G = (int64_t)p.L[0] * p.L[1] * p.L[2];
+    const int64_t Kx = p.n[0] / 2;
+    int64_t b = es * p.Q + 4 * es * p.N + 2 * es * G + 2 * es * p.L[2] * p.L[1] * Kx + 2 * es * p.L[2] * p.n[1] * Kx;
+    if (p.opts.deterministic) b += es * 32 * (int64_t)std::max<size_t>(1, p.near_items.size());
+    return b;
+}
+
+slp_status slp_alloc_scratch(slp_plan_s &p, slp::DevPlan &out, std::vector<void *> &allocs, int64_t *bytes) {
+    out = p.dp;
+    const int64_t es = p.prec == 64 ? 8 : 4;
+    const int64_t G = (int64_t)p.L[0] * p.L[1] * p.L[2];
+    const int64_t Kx = p.n[0] / 2;
+    struct Req {
+        void **dst;
+        int64_t n;
+    } reqs[] = {{&out.qbuf, es * p.Q},
+                {&out.m4, 4 * es * p.N},
+                {&out.gridA, es * G},
+                {&out.gridB, es * G},
+                {&out.S1, 2 * es * p.L[2] * p.L[1] * Kx},
+                {&out.S2, 2 * es * p.L[2] * p.n[1] * Kx},
+                {&out.phi_near, p.opts.deterministic ? es * 32 * (int64_t)std::max<size_t>(1, p.near_items.size()) : 0}};
+    int64_t total = 0;
+    for (auto &r : reqs) {
+        if (r.n == 0) continue;
+        const size_t nb = (size_t)((r.n + 255) / 256 * 256);
+        void *ptr = nullptr;
+        const cudaError_t e = cudaMalloc(&ptr, nb);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return slp_fail(e == cudaErrorMemoryAllocation ? SLP_ERR_OOM : SLP_ERR_CUDA, "scratch allocation of %zu bytes: %s",
+                            nb, cudaGetErrorString(e));
+        }
+        allocs.push_back(ptr);
+        *r.dst = ptr;
+        total += (int64_t)nb;
+    }
+    if (cudaMemset(out.gridA, 0, es * G) != cudaSuccess) return slp_fail(SLP_ERR_CUDA, "cudaMemset failed");
+    if (bytes) *bytes = total;
+    return SLP_OK;
+}
 
 // ======================================================================= C ABI
 extern "C" {

@@ -1,0 +1,93 @@
+// Host-side plan object and the internal host functions shared by the
+// plan, batch and serving code.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/slp.h"
+#include "../../include/slp_debug.h"
+#include "slp_internal.h"
+
+struct slp_plan_s {
+    // configuration
+    slp_plan_opts opts;
+    int q = 0;
+    int prec = 32;
+    double tol = 0;
+    int64_t N = 0, M = 0, Q = 0;
+    int device = 0;
+
+    // geometry (host, FP64)
+    std::vector<double> V;       // [N][3]
+    std::vector<int32_t> T;      // [M][3]
+    std::vector<double> lam, wq; // rule
+    std::vector<double> y;       // [Q][3] user order
+    std::vector<double> wk;      // [Q]
+    std::vector<double> nrm;     // [M][3]
+
+    // parameters
+    int L[3] = {0, 0, 0}, n[3] = {0, 0, 0}, m = 0, TS = 8, TE = 0;
+    int kernel_mode = SLP_KERNEL_RADIAL, near_mode = SLP_NEAR_ON_THE_FLY;
+    int grid_raised = 0;
+    double ctr[3] = {0, 0, 0}, P[3] = {0, 0, 0}, D[3] = {0, 0, 0};
+    double diam = 0, sigma_g = 0, R = 0, eps = 0, c_band = 0;
+    double sep_A = 0;
+    std::vector<double> sep_h[3];
+
+    // sorted data (host)
+    std::vector<int32_t> src_perm, tgt_perm;
+    std::vector<double> src_grid, tgt_grid;  // [.][4]
+    std::vector<slp::TileItem> spread_items, gather_items;
+    std::vector<slp::NearItem> near_items;
+    std::vector<int2> near_ranges;
+    std::vector<int> near_blk_first;  // CSR of items per target block
+    std::vector<double> Dtab;
+    int64_t near_pairs = 0;
+
+    // device
+    slp::DevPlan dp;
+    std::vector<void *> allocs;
+    int64_t bytes_device = 0;
+    void *d_stage_in = nullptr, *d_stage_phi = nullptr;
+    int *d_blk_first = nullptr;
+    int launches_per_eval = 0;
+    int64_t near_pairs_within = -1;
+    int64_t nm_nnz = 0;
+};
+
+
+// Record a failure text for slp_last_error() and return the status.
+slp_status slp_fail(slp_status st, const char *fmt, ...);
+
+// Enqueue one evaluation of `p` with the device view `d` (the plan's own
+// scratch or another scratch set) up to stage `last`; with ev != NULL,
+// events are recorded around each kernel (SLP_PROFILE_SLOTS + 1 entries).
+constexpr int SLP_PROFILE_SLOTS = 10;
+slp_status slp_run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *d_in, void *d_phi,
+                            cudaStream_t s, int last, cudaEvent_t *ev);
+
+// Allocate a second scratch set (charges, sorted m, grids, spectra, partials)
+// for `p` and return a device view that uses it; the pointers are appended to
+// `allocs` (released by the caller with cudaFree).  Grid A is zeroed.
+slp_status slp_alloc_scratch(slp_plan_s &p, slp::DevPlan &out, std::vector<void *> &allocs, int64_t *bytes);
+
+// Bytes of one scratch set of `p`.
+int64_t slp_scratch_bytes(const slp_plan_s &p);
+
+// Current device switched to `dev` for the guard's lifetime.
+struct SlpDeviceGuard {
+    int prev = -1;
+    explicit SlpDeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (dev >= 0 && prev != dev) cudaSetDevice(dev);
+    }
+    ~SlpDeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
