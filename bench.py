@@ -530,6 +530,113 @@ def run_batched(args):
         slp.slp_destroy(p)
 
 
+def _served_pool():
+    """Eight resident meshes (cube, sphere, plate, torus), ~2k to 1.92M triangles."""
+    from synthetic import meshes
+    return [("cube13", meshes.cube(13), 3, (64, 64, 64)),
+            ("sphere_L5", meshes.icosphere(5), 7, (128, 128, 128)),
+            ("plate_2000x500x20_c10", meshes.box(2000.0, 500.0, 20.0, 200, 50, 2), 3, (512, 128, 128)),
+            ("torus_400x100", meshes.torus(2.0, 0.5, 400, 100), 3, (256, 256, 128)),
+            ("sphere_L6", meshes.icosphere(6), 3, (256, 256, 256)),
+            ("plate_2000x500x20_c5", meshes.box(2000.0, 500.0, 20.0, 400, 100, 4), 3, (512, 256, 256)),
+            ("torus_800x200", meshes.torus(2.0, 0.5, 800, 200), 3, (512, 512, 256)),
+            ("cube400", meshes.cube(400), 3, (1024, 1024, 1024))]
+
+
+def run_served(args):
+    """Served form: seeded Poisson arrivals (mean 2000 requests/s) over the eight
+    resident meshes, 1..32 states per request, admission by an HBM budget."""
+    import torch
+
+    import oracle
+    import paper_1305_3162_gb300 as slp
+    from paper_1305_3162_gb300 import _build
+    from synthetic import fields
+    _build.build()
+    pool = _served_pool()
+    plans, info = [], []
+    t0 = time.perf_counter()
+    for name, (V, T), q, grid in pool:
+        o = slp.slp_default_opts()
+        o.precision = 32
+        for d in range(3):
+            o.grid[d] = grid[d]
+        h = slp.slp_plan(V, T, q, 1e-5, o)
+        plans.append(h)
+        inf = slp.slp_query(h)
+        info.append({"mesh": name, "triangles": int(T.shape[0]), "targets": int(V.shape[0]), "grid": inf["grid"],
+                     "near": ["auto", "on_the_fly", "precomputed"][inf["near_mode"]],
+                     "plan_gb": round(inf["bytes_device"] / 2 ** 30, 2)})
+    t_plan = time.perf_counter() - t0
+    # a pool of 32 seeded states per mesh, page-locked; a request takes a slice
+    states = []
+    for k, (name, (V, T), q, grid) in enumerate(pool):
+        st = np.stack([fields.smooth_random(V, 9000 + 100 * k + j) for j in range(32)]).astype(np.float32)
+        states.append(torch.from_numpy(st.reshape(32, -1)).pin_memory())
+    rng = np.random.default_rng(fields.workload_seed(4))
+    n_req = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, size=n_req))
+    which = rng.integers(0, len(pool), size=n_req)
+    nst = rng.integers(1, 33, size=n_req)
+    start = np.array([rng.integers(0, 33 - n) for n in nst])
+    # outputs: a ring of 8 buffers of 32 states per mesh (the bench reads only the probes)
+    rings = [[torch.empty(32 * V.shape[0], dtype=torch.float32).pin_memory() for _ in range(8)]
+             for name, (V, T), q, grid in pool]
+    so = slp.slp_server_default_opts()
+    so.slots_per_plan = 2
+    so.hbm_budget_bytes = int(args.budget_gb * 2 ** 30)
+    server = slp.slp_server_create(plans, slp.SLP_INPUT_NODAL_MAG, so)
+    # probes: one private request per mesh, before the stream, for parity
+    probe_out = []
+    for k, (name, (V, T), q, grid) in enumerate(pool):
+        ho = torch.empty(V.shape[0], dtype=torch.float32).pin_memory()
+        rid = slp.slp_server_submit(server, k, 1, states[k][0], ho)
+        probe_out.append((rid, ho))
+    for rid, _ in probe_out:
+        slp.slp_server_wait(server, rid, 600.0)
+    # the timed stream: submit each request at its arrival time (open loop)
+    ids = []
+    ring_pos = [0] * len(pool)
+    tstart = time.perf_counter()
+    for i in range(n_req):
+        k = int(which[i])
+        now = time.perf_counter() - tstart
+        if arrivals[i] > now:
+            time.sleep(arrivals[i] - now)
+        ho = rings[k][ring_pos[k] % 8]
+        ring_pos[k] += 1
+        src = states[k][int(start[i])]
+        ids.append(slp.slp_server_submit(server, k, int(nst[i]), src, ho))
+    for rid in ids:
+        slp.slp_server_wait(server, rid, 3600.0)
+    wall = time.perf_counter() - tstart
+    stats = slp.slp_server_stats(server)
+    slp.slp_server_destroy(server)
+    # parity of the probes (oracle at up to 256 sampled nodes)
+    errs = {}
+    for k, (name, (V, T), q, grid) in enumerate(pool):
+        sel = np.sort(np.random.default_rng(k).choice(V.shape[0], min(256, V.shape[0]), replace=False))
+        y, _, _ = oracle.sources(V, T, q)
+        m = states[k][0].numpy().reshape(-1, 3).astype(np.float64)
+        qk = oracle.charges(V, T, q, oracle.KIND_NODAL_MAG, m)
+        ref, _ = oracle.direct_subset(V, sel, y, qk)
+        got = probe_out[k][1].numpy().astype(np.float64)[sel]
+        errs[name] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+    targets = int(sum(int(nst[i]) * pool[int(which[i])][1][0].shape[0] for i in range(n_req)))
+    line = {"metric": METRIC + " (served form)", "value": targets / wall, "unit": UNIT, "mode": "served",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded meshes and magnetisations)",
+            "config": {"workload": "Poisson arrivals over 8 resident meshes", "rate_req_per_s": args.rate,
+                       "requests": n_req, "states_per_request": "uniform 1..32", "slots_per_plan": 2,
+                       "hbm_budget_gb": args.budget_gb, "plans_s": round(t_plan, 1), "meshes": info},
+            "latency_p50_ms": stats["latency_p50_ms"], "latency_p99_ms": stats["latency_p99_ms"],
+            "queue_wait_p50_ms": stats["queue_wait_p50_ms"], "queue_wait_p99_ms": stats["queue_wait_p99_ms"],
+            "wall_s": wall, "server": stats, "probe_rel_l2_sampled": errs,
+            "parity_ok": max(errs.values()) <= 1e-5}
+    print(json.dumps(line), flush=True)
+    for p in plans:
+        slp.slp_destroy(p)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -542,6 +649,9 @@ def main():
     ap.add_argument("--mode", choices=["plain", "batched", "served"], default="plain",
                     help="plain: the headline single evaluation; batched/served: the other forms")
     ap.add_argument("--lanes", type=int, default=4, help="batched form: concurrent scratch sets per plan")
+    ap.add_argument("--rate", type=float, default=2000.0, help="served form: mean arrivals per second")
+    ap.add_argument("--requests", type=int, default=400, help="served form: requests in the arrival stream")
+    ap.add_argument("--budget-gb", type=float, default=48.0, help="served form: HBM budget of the server")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -549,6 +659,8 @@ def main():
         run_reference(args)
     elif args.mode == "batched":
         run_batched(args)
+    elif args.mode == "served":
+        run_served(args)
     else:
         run_ours(args)
 

@@ -82,7 +82,8 @@ enum { SLP_KERNEL_AUTO = 0, SLP_KERNEL_RADIAL = 1, SLP_KERNEL_SEPARABLE = 2 };
  *                (the precomputed near-field integrals of Sec. 3.4) and
  *                applied as a sparse product; other inputs fall back to
  *                ON_THE_FLY;
- *   AUTO:        PRECOMPUTED when it fits the memory budget. */
+ *   AUTO:        PRECOMPUTED when the operator needs at most 24 GiB and at
+ *                most half of the free device memory. */
 enum { SLP_NEAR_AUTO = 0, SLP_NEAR_ON_THE_FLY = 1, SLP_NEAR_PRECOMPUTED = 2 };
 
 typedef struct {
@@ -228,6 +229,55 @@ typedef struct {
 } slp_tune_info;
 slp_status slp_plan_autotune(const slp_mesh *mesh, int quadrature, double tolerance, const slp_plan_opts *opts,
                              int reps, slp_plan_t *out, slp_tune_info *info);
+
+/* ---- Serving: continuous batching of requests on resident plans ----
+ * A server keeps the given plans resident, gives each plan slots_per_plan
+ * execution slots (a CUDA stream and a scratch set each; slot 0 uses the
+ * plan's own scratch) and allocates one device arena for request buffers:
+ * hbm_budget_bytes minus the extra slot scratch.  slp_server_submit queues a
+ * request of n_states inputs for one plan (host buffers: n_states
+ * consecutive inputs with the slp_eval layout of input_kind, and n_states
+ * consecutive outputs of n_targets values; page-locked memory keeps the
+ * copies asynchronous; both must stay valid until the request finishes).  A
+ * scheduler thread admits queued requests in arrival order as soon as a slot
+ * of their plan is free and their device buffers fit the arena, letting
+ * later requests pass one that cannot start yet, and runs each admitted
+ * request on its slot's stream (copy in, one evaluation per state, copy
+ * out), so the work of several requests overlaps on the device.  A request
+ * that can never fit the arena is REJECTED at once (SLP_ERR_OOM).  Requests
+ * remain queryable until the server is destroyed; destroying it cancels the
+ * queued requests and waits for the running ones.  The plans must not be
+ * evaluated elsewhere while the server exists. */
+typedef struct slp_server_s *slp_server_t;
+enum { SLP_REQ_QUEUED = 1, SLP_REQ_RUNNING = 2, SLP_REQ_DONE = 3, SLP_REQ_REJECTED = 4, SLP_REQ_CANCELLED = 5,
+       SLP_REQ_FAILED = 6 };
+typedef struct {
+    int slots_per_plan;         /* 1..16, default 2 */
+    int64_t hbm_budget_bytes;   /* default 8 GiB */
+    int reserved[6];
+} slp_server_opts;
+typedef struct {
+    int64_t completed, rejected, cancelled, queued;
+    int64_t targets_done;                    /* sum over completed requests of n_states * n_targets */
+    double latency_p50_ms, latency_p99_ms, latency_max_ms;  /* submit -> completion observed */
+    double queue_wait_p50_ms, queue_wait_p99_ms;            /* submit -> admission */
+    double makespan_s;                       /* first submission -> last completion */
+    int64_t arena_bytes, arena_peak_bytes, slot_scratch_bytes, n_slots, max_inflight;
+} slp_server_statistics;
+slp_status slp_server_default_opts(slp_server_opts *opts);
+slp_status slp_server_create(int n_plans, const slp_plan_t *plans, int input_kind, const slp_server_opts *opts,
+                             slp_server_t *out);
+slp_status slp_server_submit(slp_server_t server, int plan_index, int n_states, const void *h_in, void *h_out,
+                             int64_t *request_id);
+/* state: SLP_REQ_*; result: the request's status once finished */
+slp_status slp_server_status(slp_server_t server, int64_t request_id, int *state, slp_status *result);
+/* Blocks until the request leaves QUEUED/RUNNING or timeout_s passes
+ * (SLP_ERR_TIMEOUT); returns the request's own status. */
+slp_status slp_server_wait(slp_server_t server, int64_t request_id, double timeout_s, int *state);
+/* Cancels a request that is still queued. */
+slp_status slp_server_cancel(slp_server_t server, int64_t request_id);
+slp_status slp_server_stats(slp_server_t server, slp_server_statistics *stats);
+slp_status slp_server_destroy(slp_server_t server);
 
 /* Plan parameters and sizes. */
 slp_status slp_query(slp_plan_t plan, slp_info *info);

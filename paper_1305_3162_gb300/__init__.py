@@ -78,6 +78,25 @@ class slp_tune_info(ctypes.Structure):
                                for i in range(n)]}
 
 
+SLP_REQ_QUEUED, SLP_REQ_RUNNING, SLP_REQ_DONE, SLP_REQ_REJECTED, SLP_REQ_CANCELLED, SLP_REQ_FAILED = 1, 2, 3, 4, 5, 6
+
+
+class slp_server_opts(ctypes.Structure):
+    _fields_ = [("slots_per_plan", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64), ("reserved", ctypes.c_int * 6)]
+
+
+class slp_server_statistics(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_int64), ("rejected", ctypes.c_int64), ("cancelled", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("targets_done", ctypes.c_int64), ("latency_p50_ms", ctypes.c_double),
+                ("latency_p99_ms", ctypes.c_double), ("latency_max_ms", ctypes.c_double),
+                ("queue_wait_p50_ms", ctypes.c_double), ("queue_wait_p99_ms", ctypes.c_double),
+                ("makespan_s", ctypes.c_double), ("arena_bytes", ctypes.c_int64), ("arena_peak_bytes", ctypes.c_int64),
+                ("slot_scratch_bytes", ctypes.c_int64), ("n_slots", ctypes.c_int64), ("max_inflight", ctypes.c_int64)]
+
+    def to_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class slp_info(ctypes.Structure):
     _fields_ = [("n_targets", ctypes.c_int64), ("n_sources", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
                 ("quadrature", ctypes.c_int), ("precision", ctypes.c_int), ("grid", ctypes.c_int * 3),
@@ -109,7 +128,9 @@ EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_host", "slp_qu
             "slp_debug_run", "slp_debug_copy", "slp_debug_buffer_bytes", "slp_debug_host_count",
             "slp_debug_host_array", "slp_debug_window", "slp_debug_window_hat", "slp_debug_profile",
             "slp_debug_stage_name", "slp_eval_direct_static", "slp_batch_create", "slp_batch_run",
-            "slp_batch_query", "slp_batch_destroy", "slp_plan_autotune"]
+            "slp_batch_query", "slp_batch_destroy", "slp_plan_autotune", "slp_server_default_opts",
+            "slp_server_create", "slp_server_submit", "slp_server_status", "slp_server_wait", "slp_server_cancel",
+            "slp_server_stats", "slp_server_destroy"]
 
 
 def library_path() -> str:
@@ -157,6 +178,15 @@ def load():
         "slp_batch_destroy": ([vp], St),
         "slp_plan_autotune": ([ctypes.POINTER(slp_mesh), ctypes.c_int, ctypes.c_double, ctypes.POINTER(slp_plan_opts),
                                ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(slp_tune_info)], St),
+        "slp_server_default_opts": ([ctypes.POINTER(slp_server_opts)], St),
+        "slp_server_create": ([ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(slp_server_opts),
+                               ctypes.POINTER(vp)], St),
+        "slp_server_submit": ([vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.POINTER(I64)], St),
+        "slp_server_status": ([vp, I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)], St),
+        "slp_server_wait": ([vp, I64, ctypes.c_double, ctypes.POINTER(ctypes.c_int)], St),
+        "slp_server_cancel": ([vp, I64], St),
+        "slp_server_stats": ([vp, ctypes.POINTER(slp_server_statistics)], St),
+        "slp_server_destroy": ([vp], St),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -273,6 +303,58 @@ def slp_plan_autotune(vertices, triangles, quadrature, tolerance, opts=None, rep
     _check(lib.slp_plan_autotune(ctypes.byref(mesh), int(quadrature), float(tolerance), ctypes.byref(o), int(reps),
                                  ctypes.byref(out), ctypes.byref(ti)), "slp_plan_autotune")
     return out, ti.to_dict()
+
+
+def slp_server_default_opts() -> slp_server_opts:
+    o = slp_server_opts()
+    _check(load().slp_server_default_opts(ctypes.byref(o)), "slp_server_default_opts")
+    return o
+
+
+def slp_server_create(plans, input_kind, opts=None):
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    o = opts if opts is not None else slp_server_default_opts()
+    out = ctypes.c_void_p()
+    _check(load().slp_server_create(n, P, int(input_kind), ctypes.byref(o), ctypes.byref(out)), "slp_server_create")
+    return out
+
+
+def slp_server_submit(server, plan_index, n_states, h_in, h_out) -> int:
+    rid = ctypes.c_int64()
+    _check(load().slp_server_submit(server, int(plan_index), int(n_states), _ptr(h_in), _ptr(h_out), ctypes.byref(rid)),
+           "slp_server_submit")
+    return rid.value
+
+
+def slp_server_status(server, request_id):
+    """(state, result status) of a request."""
+    st = ctypes.c_int()
+    res = ctypes.c_int()
+    _check(load().slp_server_status(server, int(request_id), ctypes.byref(st), ctypes.byref(res)), "slp_server_status")
+    return st.value, res.value
+
+
+def slp_server_wait(server, request_id, timeout_s=60.0):
+    """Wait for a request; raises SlpError on timeout or if the request failed or was rejected."""
+    st = ctypes.c_int()
+    _check(load().slp_server_wait(server, int(request_id), float(timeout_s), ctypes.byref(st)), "slp_server_wait")
+    return st.value
+
+
+def slp_server_cancel(server, request_id):
+    _check(load().slp_server_cancel(server, int(request_id)), "slp_server_cancel")
+
+
+def slp_server_stats(server) -> dict:
+    st = slp_server_statistics()
+    _check(load().slp_server_stats(server, ctypes.byref(st)), "slp_server_stats")
+    return st.to_dict()
+
+
+def slp_server_destroy(server):
+    if server is not None:
+        _check(load().slp_server_destroy(server), "slp_server_destroy")
 
 
 def slp_query(plan) -> dict:

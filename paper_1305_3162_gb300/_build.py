@@ -20,7 +20,7 @@ LIB = os.path.join(LIB_DIR, "libslp_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 CU_SOURCES = ["k_grid.cu", "k_fft.cu", "k_near.cu", "k_static.cu"]
-CPP_SOURCES = ["slp_plan.cpp", "slp_batch.cpp"]
+CPP_SOURCES = ["slp_plan.cpp", "slp_batch.cpp", "slp_serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -70,7 +70,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
         o = os.path.join(OBJ, src.replace(".cpp", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
-            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-I", os.path.join(cuda, "include"), "-I", INCLUDE,
+            cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-Wno-deprecated-declarations", "-I", os.path.join(cuda, "include"),
+                   "-I", INCLUDE,
                    "-c", s, "-o", o]
             jobs.append(cmd)
     procs = [(cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)) for cmd in jobs]
@@ -85,7 +86,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         raise RuntimeError(f"compilation failed: {failed}")
     if force or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"]
+        cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart", "-lpthread"]
         r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
         if r.returncode != 0:
             sys.stderr.write(" ".join(cmd) + "\n" + r.stdout.decode(errors="replace"))

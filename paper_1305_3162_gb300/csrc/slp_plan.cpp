@@ -1105,7 +1105,7 @@ slp_status build_near_matrix(slp_plan_s &p, const std::vector<uint64_t> &tkeys) 
     const size_t vbytes = (size_t)nnz * (p.prec == 64 ? 32 : 16);
     size_t freeb = 0, totb = 0;
     cudaMemGetInfo(&freeb, &totb);
-    if (vbytes > ((size_t)8 << 30) || vbytes > freeb / 2) return SLP_OK;  // budget: keep the on-the-fly near field
+    if (vbytes > ((size_t)24 << 30) || vbytes > freeb / 2) return SLP_OK;  // budget: keep the on-the-fly near field
     void *ptr = nullptr;
     TRY(upload(p, &ptr, rowptr.data(), rowptr.size()));
     p.dp.nm_rowptr = (const int64_t *)ptr;

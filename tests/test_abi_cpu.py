@@ -215,3 +215,20 @@ def test_dtab_radial_matches_quadrature_of_the_kernel_transform(slp):
              slp.slp_debug_window_hat(m, L[2], kz))
         assert abs(D[kz, ky, kx] * W * W - cl) <= 1e-10 * abs(cl) + 1e-16
     slp.slp_destroy(p)
+
+
+def test_batch_and_server_refuse_host_only_plans(slp):
+    V, T = meshes.cube(3)
+    p = _host_plan(slp, V, T)
+    try:
+        with pytest.raises(slp.SlpError) as e:
+            slp.slp_server_create([p], slp.SLP_INPUT_NODAL_MAG)
+        assert e.value.status == slp.SLP_ERR_NO_DEVICE
+        with pytest.raises(slp.SlpError) as e:
+            slp.slp_batch_create([p], [0], slp.SLP_INPUT_NODAL_MAG, [1], [1])
+        assert e.value.status == slp.SLP_ERR_NO_DEVICE
+        with pytest.raises(slp.SlpError) as e:
+            slp.slp_batch_create([p], [0], 7, [1], [1])  # unknown input kind
+        assert e.value.status == slp.SLP_ERR_INVALID_ARG
+    finally:
+        slp.slp_destroy(p)
