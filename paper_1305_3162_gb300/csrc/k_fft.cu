@@ -403,14 +403,16 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
 }
 
 // ---------------------------------------------------------------- launchers
-// Batch sizes: keep two buffers of (L x (B+1)) complex within ~64 KB.
+// Batch sizes: at most 8 transforms per block (more blocks for the small
+// grids, where the passes are latency-bound), two buffers of (L x (B+1))
+// complex within ~64 KB.
 static int row_batch(int L, size_t celem) {
-    int pb = 16;
+    int pb = 8;
     while (pb > 1 && 2 * (size_t)L * (pb + 1) * celem > 64 * 1024) pb >>= 1;
     return pb;
 }
 static int col_batch(int L, int Kx, size_t celem) {
-    int b = 16;
+    int b = 8;
     if (b > Kx) b = Kx;
     while (b > 1 && 2 * (size_t)L * (b + 1) * celem > 64 * 1024) b >>= 1;
     return b;

@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(128) k_gather(DevPlan p, T *__restrict__ phi) 
             }
         }
         acc = warp_sum(acc);
-        if (lane == 0) phi[p.tgt_perm[t]] = acc;
+        if (lane == 0) phi[p.tgt_perm[t]] = acc + ((const T *)p.phi_part)[t];
         __syncwarp();
     }
 }

@@ -39,7 +39,7 @@ template <typename T> __device__ __forceinline__ T sep_factor(const T *__restric
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(NEAR_WARPS * 32) k_near(DevPlan p, T *__restrict__ phi) {
+__global__ void __launch_bounds__(NEAR_WARPS * 32) k_near(DevPlan p) {
     typedef typename VecT<T>::T4 T4;
     __shared__ T4 sg[NEAR_WARPS][32];
     __shared__ T sq[NEAR_WARPS][32];
@@ -105,14 +105,14 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) k_near(DevPlan p, T *__restri
         if (p.deterministic)
             ((T *)p.phi_near)[(int64_t)item * 32 + lane] = v;
         else
-            atomicAdd(phi + p.tgt_perm[it.tbegin + lane], v);
+            atomicAdd((T *)p.phi_part + it.tbegin + lane, v);
     }
 }
 
 // Deterministic mode: items of one target block are consecutive; add their
 // partials in item order.  blk_items[b] = first item of block b (CSR).
 template <typename T>
-__global__ void k_near_reduce(DevPlan p, const int *__restrict__ blk_first, int nblk, T *__restrict__ phi) {
+__global__ void k_near_reduce(DevPlan p, const int *__restrict__ blk_first, int nblk) {
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= nblk) return;
@@ -121,30 +121,30 @@ __global__ void k_near_reduce(DevPlan p, const int *__restrict__ blk_first, int 
     if (lane >= it0.tcount) return;
     T s = T(0);
     for (int i = i0; i < i1; ++i) s += ((const T *)p.phi_near)[(int64_t)i * 32 + lane];
-    phi[p.tgt_perm[it0.tbegin + lane]] += s;
+    ((T *)p.phi_part)[it0.tbegin + lane] = s;
 }
 
-template <typename T> static cudaError_t near_t(const DevPlan &p, void *phi, cudaStream_t s) {
+template <typename T> static cudaError_t near_t(const DevPlan &p, cudaStream_t s) {
     if (p.n_near == 0) return cudaSuccess;
     const int nb = (p.n_near + NEAR_WARPS - 1) / NEAR_WARPS;
     if (p.kernel_mode == 2)
-        k_near<T, 2><<<nb, NEAR_WARPS * 32, 0, s>>>(p, (T *)phi);
+        k_near<T, 2><<<nb, NEAR_WARPS * 32, 0, s>>>(p);
     else
-        k_near<T, 1><<<nb, NEAR_WARPS * 32, 0, s>>>(p, (T *)phi);
+        k_near<T, 1><<<nb, NEAR_WARPS * 32, 0, s>>>(p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_near(const DevPlan &p, void *phi, cudaStream_t s) {
-    return p.prec == 64 ? near_t<double>(p, phi, s) : near_t<float>(p, phi, s);
+cudaError_t launch_near(const DevPlan &p, cudaStream_t s) {
+    return p.prec == 64 ? near_t<double>(p, s) : near_t<float>(p, s);
 }
 
-cudaError_t launch_near_reduce(const DevPlan &p, const int *blk_first, int nblk, void *phi, cudaStream_t s) {
+cudaError_t launch_near_reduce(const DevPlan &p, const int *blk_first, int nblk, cudaStream_t s) {
     if (nblk == 0) return cudaSuccess;
     const int nb = (nblk + 7) / 8;
     if (p.prec == 64)
-        k_near_reduce<double><<<nb, 256, 0, s>>>(p, blk_first, nblk, (double *)phi);
+        k_near_reduce<double><<<nb, 256, 0, s>>>(p, blk_first, nblk);
     else
-        k_near_reduce<float><<<nb, 256, 0, s>>>(p, blk_first, nblk, (float *)phi);
+        k_near_reduce<float><<<nb, 256, 0, s>>>(p, blk_first, nblk);
     return cudaGetLastError();
 }
 
@@ -255,7 +255,7 @@ __device__ __forceinline__ double4 ld_stream(const double4 *p) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_near_matrix(DevPlan p, const T *__restrict__ m, T *__restrict__ phi) {
+__global__ void __launch_bounds__(128) k_near_matrix(DevPlan p) {
     typedef typename VecT<T>::T4 T4;
     constexpr int U = 8;  // independent 16-byte loads in flight per lane
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -286,16 +286,16 @@ __global__ void __launch_bounds__(128) k_near_matrix(DevPlan p, const T *__restr
         }
     }
     acc = warp_sum(acc);
-    if (lane == 0) phi[p.tgt_perm[t]] += acc;
+    if (lane == 0) ((T *)p.phi_part)[t] = acc;
 }
 
-cudaError_t launch_near_matrix(const DevPlan &p, const void *d_m, void *d_phi, cudaStream_t s) {
+cudaError_t launch_near_matrix(const DevPlan &p, const void *, cudaStream_t s) {
     if (p.N == 0) return cudaSuccess;
     const unsigned nb = (unsigned)((p.N + 3) / 4);
     if (p.prec == 64)
-        k_near_matrix<double><<<nb, 128, 0, s>>>(p, (const double *)d_m, (double *)d_phi);
+        k_near_matrix<double><<<nb, 128, 0, s>>>(p);
     else
-        k_near_matrix<float><<<nb, 128, 0, s>>>(p, (const float *)d_m, (float *)d_phi);
+        k_near_matrix<float><<<nb, 128, 0, s>>>(p);
     return cudaGetLastError();
 }
 

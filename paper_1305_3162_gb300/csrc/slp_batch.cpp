@@ -21,6 +21,7 @@ struct slp_batch_s {
     std::vector<void *> allocs;      // extra scratch sets
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
+    std::vector<SlpExec> execs;  // near-field branch of each lane
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int n_items = 0;
@@ -37,6 +38,7 @@ void release(slp_batch_s *b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     for (cudaEvent_t e : b->events) cudaEventDestroy(e);
+    for (SlpExec &e : b->execs) slp_exec_destroy(e);
     for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
     for (void *p : b->allocs) cudaFree(p);
     delete b;
@@ -118,6 +120,13 @@ slp_status slp_batch_create(int n_plans, const slp_plan_t *plans, int n_items, c
         }
         b->streams.push_back(s);
         b->events.push_back(e);
+        SlpExec ex;
+        if (slp_exec_create(ex) != cudaSuccess) {
+            slp_exec_destroy(ex);
+            release(b);
+            return slp_fail(SLP_ERR_CUDA, "stream/event creation failed");
+        }
+        b->execs.push_back(ex);
     }
     cudaEvent_t fork;
     if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) {
@@ -137,7 +146,8 @@ slp_status slp_batch_create(int n_plans, const slp_plan_t *plans, int n_items, c
         cudaStreamWaitEvent(s, fork, 0);
         slp_plan_s &p = *plans[lanes[l].plan];
         for (int it : lanes[l].items) {
-            st = slp_run_pipeline(p, lanes[l].view, input_kind, d_in[it], d_phi[it], s, SLP_STAGE_NEAR, nullptr);
+            st = slp_run_pipeline(p, lanes[l].view, input_kind, d_in[it], d_phi[it], s, SLP_STAGE_NEAR, nullptr,
+                                  &b->execs[l]);
             if (st != SLP_OK) break;
             b->launches += p.launches_per_eval;
         }

@@ -63,7 +63,8 @@ struct DevPlan {
     void *gridB;   // T [Lz][Ly][Lx] interpolation grid
     void *S1;      // T2 [Lz][Ly][Kx]
     void *S2;      // T2 [Lz][n_y][Kx]
-    void *phi_near; // T [N] near-field partials (deterministic mode), sorted order
+    void *phi_near; // T [32 * n_near] near-field partials per work item (deterministic mode)
+    void *phi_part; // T [N] near-field correction per sorted target, added by the gather
     const void *Dtab;   // T [n_z/2][n_y/2][Kx] kernel multiplier by |l_z|, |l_y|, l_x
     const void *tw[3];  // T2 [L_q] forward twiddles exp(-2 pi i t / L_q)
 
@@ -97,9 +98,12 @@ cudaError_t launch_fft_forward_y(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_z_multiply(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_inverse_y(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_inverse_x(const DevPlan &p, cudaStream_t s);
+// phi[perm[t]] = far field at t + phi_part[t]
 cudaError_t launch_gather(const DevPlan &p, void *d_phi, cudaStream_t s);
-cudaError_t launch_near(const DevPlan &p, void *d_phi, cudaStream_t s);
-cudaError_t launch_near_reduce(const DevPlan &p, const int *blk_first, int nblk, void *d_phi, cudaStream_t s);
+// near field into phi_part (atomics: phi_part must be zero; deterministic: per-item partials, then the reduction
+// overwrites phi_part)
+cudaError_t launch_near(const DevPlan &p, cudaStream_t s);
+cudaError_t launch_near_reduce(const DevPlan &p, const int *blk_first, int nblk, cudaStream_t s);
 cudaError_t launch_zero(void *ptr, size_t bytes, cudaStream_t s);
 
 // Precomputed near-field operator (k_near.cu): inputs of the plan-time
@@ -127,7 +131,8 @@ struct NMBuild {
 };
 cudaError_t launch_nm_build(const NMBuild &b, int pass, int prec, int64_t *counts, int64_t *pairs,
                             const int64_t *rowptr, void *val, cudaStream_t s);
-cudaError_t launch_near_matrix(const DevPlan &p, const void *d_m, void *d_phi, cudaStream_t s);
+// phi_part = W m (overwrites)
+cudaError_t launch_near_matrix(const DevPlan &p, const void *d_m, cudaStream_t s);
 
 // Set the thread-local text returned by slp_last_error().
 void set_last_error(const char *msg);

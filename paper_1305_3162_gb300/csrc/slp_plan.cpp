@@ -836,6 +836,7 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     const int Kx = p.n[0] / 2;
     TRY(dalloc(p, &d.qbuf, sizeof(T) * p.Q));
     TRY(dalloc(p, &d.m4, 4 * sizeof(T) * p.N));
+    TRY(dalloc(p, &d.phi_part, sizeof(T) * p.N));
     TRY(dalloc(p, &d.gridA, sizeof(T) * G));
     TRY(dalloc(p, &d.gridB, sizeof(T) * G));
     TRY(dalloc(p, &d.S1, sizeof(T2) * (size_t)p.L[2] * p.L[1] * Kx));
@@ -897,6 +898,7 @@ void free_device(slp_plan_s &p) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(p.device);
+    slp_exec_destroy(p.exec);
     for (void *a : p.allocs) cudaFree(a);
     p.allocs.clear();
     cudaSetDevice(prev);
@@ -1125,15 +1127,20 @@ slp_status cuda_status(cudaError_t e, const char *what) {
     return fail(SLP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// Kernels of one evaluation, in launch order (names reported by the profiler entry point).
+// Kernels of one evaluation in serial order (names reported by the profiler entry point).
 const char *const STAGE_NAMES[] = {"charges", "spread", "fft_x", "fft_y", "fft_z_mul", "ifft_y", "ifft_x",
-                                   "gather", "near", "near_reduce"};
+                                   "near", "near_reduce", "gather"};
 const int N_STAGE_NAMES = 10;
 
-// Enqueue the evaluation up to stage `last`.  With ev != NULL, ev[i] is
-// recorded before kernel i and ev[i + 1] after it (ev has N_STAGE_NAMES + 1 entries).
+// Enqueue the evaluation up to stage `last`.
+//   serial (ev != NULL, or ex == NULL): charges, spread, 5 FFT passes, near
+//     field into phi_part, gather (far field + phi_part) on s; with ev,
+//     ev[i] is recorded before kernel slot i and ev[i + 1] after it;
+//   concurrent (ex != NULL, no ev): after the charges the near field runs on
+//     ex->aux while the spread and FFT passes run on s; s waits for it
+//     before the gather.
 slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *d_in, void *d_phi,
-                        cudaStream_t s, int last, cudaEvent_t *ev) {
+                        cudaStream_t s, int last, cudaEvent_t *ev, SlpExec *ex) {
     int k = 0;
     auto rec = [&]() {
         if (ev) cudaEventRecord(ev[k], s);
@@ -1143,11 +1150,37 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
     // by the spread, which computes them itself
     const bool use_matrix = kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
     const bool fuse = use_matrix && last > SLP_STAGE_CHARGES;
+    const bool concurrent = ex != nullptr && ev == nullptr && last >= SLP_STAGE_NEAR;
+    const size_t es = p.prec == 64 ? 8 : 4;
+    // near-field branch on stream t
+    auto near_branch = [&](cudaStream_t t) -> slp_status {
+        if (use_matrix) {
+            TRY(cuda_status(slp::launch_near_matrix(d, d_in, t), "near-field matrix"));
+            rec();
+            rec();
+            return SLP_OK;
+        }
+        if (!p.opts.deterministic)
+            TRY(cuda_status(slp::launch_zero(d.phi_part, (es * (size_t)p.N + 15) / 16 * 16, t), "zero near field"));
+        TRY(cuda_status(slp::launch_near(d, t), "near field"));
+        rec();
+        if (p.opts.deterministic)
+            TRY(cuda_status(slp::launch_near_reduce(d, p.d_blk_first, (int)p.near_blk_first.size() - 1, t),
+                            "near reduce"));
+        rec();
+        return SLP_OK;
+    };
     rec();
     if (kind == SLP_INPUT_NODAL_MAG) TRY(cuda_status(slp::launch_nodal_prep(d, d_in, s), "nodal prep"));
     if (!fuse) TRY(cuda_status(slp::launch_charges(d, kind, d_in, s), "charges"));
     rec();
     if (last <= SLP_STAGE_CHARGES) return SLP_OK;
+    if (concurrent) {
+        TRY(cuda_status(cudaEventRecord(ex->fork, s), "fork"));
+        TRY(cuda_status(cudaStreamWaitEvent(ex->aux, ex->fork, 0), "fork wait"));
+        TRY(near_branch(ex->aux));
+        TRY(cuda_status(cudaEventRecord(ex->join, ex->aux), "join"));
+    }
     TRY(cuda_status(slp::launch_spread(d, fuse ? kind : -1, d_in, s), "spread"));
     rec();
     if (last <= SLP_STAGE_SPREAD) return SLP_OK;
@@ -1166,27 +1199,24 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
     TRY(cuda_status(slp::launch_fft_inverse_x(d, s), "ifft x"));
     rec();
     if (last <= SLP_STAGE_IFFT_X) return SLP_OK;
-    TRY(cuda_status(slp::launch_gather(d, d_phi, s), "gather"));
-    rec();
-    if (last <= SLP_STAGE_GATHER) return SLP_OK;
-    if (use_matrix) {
-        TRY(cuda_status(slp::launch_near_matrix(d, d_in, d_phi, s), "near-field matrix"));
+    if (concurrent) {
+        TRY(cuda_status(cudaStreamWaitEvent(s, ex->join, 0), "join wait"));
+    } else if (last >= SLP_STAGE_NEAR) {
+        TRY(near_branch(s));
+    } else {
+        // far field only
+        TRY(cuda_status(slp::launch_zero(d.phi_part, (es * (size_t)p.N + 15) / 16 * 16, s), "zero near field"));
         rec();
         rec();
-        return SLP_OK;
     }
-    TRY(cuda_status(slp::launch_near(d, d_phi, s), "near field"));
-    rec();
-    if (p.opts.deterministic)
-        TRY(cuda_status(slp::launch_near_reduce(d, p.d_blk_first, (int)p.near_blk_first.size() - 1, d_phi, s),
-                        "near reduce"));
+    TRY(cuda_status(slp::launch_gather(d, d_phi, s), "gather"));
     rec();
     return SLP_OK;
 }
 
 slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, cudaStream_t s, int last,
                         cudaEvent_t *ev = nullptr) {
-    return run_pipeline(p, p.dp, kind, d_in, d_phi, s, last, ev);
+    return run_pipeline(p, p.dp, kind, d_in, d_phi, s, last, ev, ev ? nullptr : &p.exec);
 }
 
 struct DeviceGuard {
@@ -1217,15 +1247,29 @@ slp_status slp_fail(slp_status st, const char *fmt, ...) {
 }
 
 slp_status slp_run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *d_in, void *d_phi,
-                            cudaStream_t s, int last, cudaEvent_t *ev) {
-    return run_pipeline(p, d, kind, d_in, d_phi, s, last, ev);
+                            cudaStream_t s, int last, cudaEvent_t *ev, SlpExec *ex) {
+    return run_pipeline(p, d, kind, d_in, d_phi, s, last, ev, ex);
+}
+
+cudaError_t slp_exec_create(SlpExec &e) {
+    cudaError_t r = cudaStreamCreateWithFlags(&e.aux, cudaStreamNonBlocking);
+    if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming);
+    if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e.join, cudaEventDisableTiming);
+    return r;
+}
+
+void slp_exec_destroy(SlpExec &e) {
+    if (e.join) cudaEventDestroy(e.join);
+    if (e.fork) cudaEventDestroy(e.fork);
+    if (e.aux) cudaStreamDestroy(e.aux);
+    e = SlpExec();
 }
 
 int64_t slp_scratch_bytes(const slp_plan_s &p) {
     const int64_t es = p.prec == 64 ? 8 : 4;
     const int64_t G = (int64_t)p.L[0] * p.L[1] * p.L[2];
     const int64_t Kx = p.n[0] / 2;
-    int64_t b = es * p.Q + 4 * es * p.N + 2 * es * G + 2 * es * p.L[2] * p.L[1] * Kx + 2 * es * p.L[2] * p.n[1] * Kx;
+    int64_t b = es * p.Q + 5 * es * p.N + 2 * es * G + 2 * es * p.L[2] * p.L[1] * Kx + 2 * es * p.L[2] * p.n[1] * Kx;
     if (p.opts.deterministic) b += es * 32 * (int64_t)std::max<size_t>(1, p.near_items.size());
     return b;
 }
@@ -1240,6 +1284,7 @@ slp_status slp_alloc_scratch(slp_plan_s &p, slp::DevPlan &out, std::vector<void 
         int64_t n;
     } reqs[] = {{&out.qbuf, es * p.Q},
                 {&out.m4, 4 * es * p.N},
+                {&out.phi_part, es * p.N},
                 {&out.gridA, es * G},
                 {&out.gridB, es * G},
                 {&out.S1, 2 * es * p.L[2] * p.L[1] * Kx},
@@ -1343,6 +1388,7 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
         DeviceGuard g(p->device);
         st = p->prec == 64 ? upload_all<double>(*p) : upload_all<float>(*p);
         if (st == SLP_OK && o.near_mode != SLP_NEAR_ON_THE_FLY) st = build_near_matrix(*p, tkeys);
+        if (st == SLP_OK && slp_exec_create(p->exec) != cudaSuccess) st = fail(SLP_ERR_CUDA, "stream creation failed");
         if (st != SLP_OK) {
             free_device(*p);
             delete p;

@@ -12,6 +12,16 @@
 #include "../../include/slp_debug.h"
 #include "slp_internal.h"
 
+// Auxiliary stream and fork/join events of one execution context: the
+// near-field branch runs on `aux` while the far-field chain runs on the
+// caller's stream.
+struct SlpExec {
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+cudaError_t slp_exec_create(SlpExec &e);
+void slp_exec_destroy(SlpExec &e);
+
 struct slp_plan_s {
     // configuration
     slp_plan_opts opts;
@@ -57,6 +67,7 @@ struct slp_plan_s {
     int launches_per_eval = 0;
     int64_t near_pairs_within = -1;
     int64_t nm_nnz = 0;
+    SlpExec exec;  // for evaluations on the plan's own scratch
 };
 
 
@@ -64,11 +75,13 @@ struct slp_plan_s {
 slp_status slp_fail(slp_status st, const char *fmt, ...);
 
 // Enqueue one evaluation of `p` with the device view `d` (the plan's own
-// scratch or another scratch set) up to stage `last`; with ev != NULL,
-// events are recorded around each kernel (SLP_PROFILE_SLOTS + 1 entries).
+// scratch or another scratch set) up to stage `last`.  With ex != NULL (and
+// no profiling events) the near-field branch runs concurrently on ex->aux;
+// with ev != NULL everything runs in order on s and events are recorded
+// around each kernel (SLP_PROFILE_SLOTS + 1 entries).
 constexpr int SLP_PROFILE_SLOTS = 10;
 slp_status slp_run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *d_in, void *d_phi,
-                            cudaStream_t s, int last, cudaEvent_t *ev);
+                            cudaStream_t s, int last, cudaEvent_t *ev, SlpExec *ex);
 
 // Allocate a second scratch set (charges, sorted m, grids, spectra, partials)
 // for `p` and return a device view that uses it; the pointers are appended to

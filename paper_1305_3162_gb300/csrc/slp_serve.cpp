@@ -108,6 +108,7 @@ struct Request {
 struct Slot {
     int plan = 0;
     slp::DevPlan view;
+    SlpExec exec;  // near-field branch
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     int64_t request = -1;
@@ -171,7 +172,7 @@ slp_status launch_request(slp_server_s &S, Request &r, Slot &sl) {
     if (e != cudaSuccess) return slp_fail(SLP_ERR_CUDA, "request %lld: copy in: %s", (long long)r.id, cudaGetErrorString(e));
     for (int k = 0; k < r.n_states; ++k) {
         const slp_status st = slp_run_pipeline(p, sl.view, S.kind, din + k * ib, dout + k * ob, sl.stream,
-                                               SLP_STAGE_NEAR, nullptr);
+                                               SLP_STAGE_NEAR, nullptr, &sl.exec);
         if (st != SLP_OK) return st;
     }
     e = cudaMemcpy2DAsync(r.h_out, (size_t)ohb, dout, (size_t)ob, (size_t)ohb, (size_t)r.n_states,
@@ -334,6 +335,7 @@ slp_status slp_server_create(int n_plans, const slp_plan_t *plans, int input_kin
         for (Slot &sl : S->slots) {
             if (sl.stream) cudaStreamDestroy(sl.stream);
             if (sl.done) cudaEventDestroy(sl.done);
+            slp_exec_destroy(sl.exec);
         }
         for (void *p : S->allocs) cudaFree(p);
         delete S;
@@ -360,7 +362,8 @@ slp_status slp_server_create(int n_plans, const slp_plan_t *plans, int input_kin
                 S->scratch_bytes += nb;
             }
             if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
+                cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
+                slp_exec_create(sl.exec) != cudaSuccess) {
                 S->slots.push_back(sl);
                 return cleanup(slp_fail(SLP_ERR_CUDA, "stream/event creation failed"));
             }
@@ -509,6 +512,7 @@ slp_status slp_server_destroy(slp_server_t S) {
     for (Slot &sl : S->slots) {
         if (sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
+        slp_exec_destroy(sl.exec);
     }
     for (void *p : S->allocs) cudaFree(p);
     delete S;
