@@ -133,6 +133,8 @@ typedef struct {
     int64_t n_gather_items;
     int64_t n_near_items;
     int launches_per_eval;       /* kernels launched by one slp_eval */
+    int64_t active_rows;         /* grid rows (z, y) the FFT passes transform along x: those within
+                                    the window of some source or target, widened to row pairs */
 } slp_info;
 
 /* Fill opts with defaults: precision 32, automatic grid/m/kernel/near mode,

@@ -52,7 +52,10 @@ enum {
     SLP_HOST_NEAR_RANGES = 7,  /* int32 [n][2]: begin, end (sorted sources) */
     SLP_HOST_DTAB = 8,         /* double [n_z/2][n_y/2][n_x/2] */
     SLP_HOST_SRC_POINTS = 9,   /* double [Q][3]: quadrature points, sorted order */
-    SLP_HOST_TGT_POINTS = 10   /* double [N][3]: targets, sorted order */
+    SLP_HOST_TGT_POINTS = 10,  /* double [N][3]: targets, sorted order */
+    SLP_HOST_PLANE_ROWS = 11,  /* int32 [Lz][2]: first active row y0 and active row count of each
+                                  plane (rows y0 .. y0 + count - 1 modulo Ly; pair aligned) */
+    SLP_HOST_ACTIVE_Z = 12     /* int32 [2]: first active plane z0 and active plane count (mod Lz) */
 };
 
 /* Run the pipeline of slp_eval up to and including stage last_stage, starting

@@ -18,6 +18,13 @@
 // work on consecutive columns, so shared-memory accesses are conflict free
 // and global accesses coalesce along the contiguous axis.  FX also writes
 // zeros back to grid A so the next spread starts from a clean grid.
+//
+// All passes are restricted to the plan's active region: the row pairs of
+// grid A the spread can reach (FX), and the rows of grid B the gather reads
+// (IX); FY / IY run on the active z planes only and read / write only the
+// plane's active y interval, FZ reads and writes only active z.  Rows outside
+// stay zero in every buffer, which is what the full transforms would compute
+// for grid A's zero rows; grid B's inactive rows are never read.
 #include "dev_common.cuh"
 
 namespace slp {
@@ -151,13 +158,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2], Kx = p.Kx;
+    const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx;
     const int ld = PB + 1;
     const int lgLx = __ffs(Lx) - 1, lgKx = __ffs(Kx) - 1, lgHy = __ffs(Ly) - 2;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Lx * ld;
-    const int64_t npairs = (int64_t)Lz * (Ly / 2);
-    const int64_t pr0 = (int64_t)blockIdx.x * PB;
+    const int npairs = p.n_row_pairs;
+    const int pr0 = blockIdx.x * PB;
     T *A = (T *)p.gridA;
     // rows y0 and y0+1 of each pair, VW elements per vector load; all loads are
     // issued before the zeroing stores so they overlap
@@ -167,11 +174,11 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     const int nv = Lx / VW;
     for (int i = threadIdx.x; i < PB * nv; i += blockDim.x) {
         const int b = i >> (lgLx - lgVW), xv = i & (nv - 1);
-        const int64_t pr = pr0 + b;
         T ra[VW], rb[VW];
-        if (pr < npairs) {
+        if (pr0 + b < npairs) {
+            const int pr = p.row_pairs[pr0 + b];
             const int64_t z = pr >> lgHy;
-            const int y0 = 2 * (int)(pr & ((Ly >> 1) - 1));
+            const int y0 = 2 * (pr & ((Ly >> 1) - 1));
             const int64_t r0 = (z * Ly + y0) * Lx;
             const V va = ((const V *)(A + r0))[xv];
             const V vb = ((const V *)(A + r0 + Lx))[xv];
@@ -187,10 +194,10 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     __syncthreads();
     for (int i = threadIdx.x; i < PB * nv; i += blockDim.x) {
         const int b = i >> (lgLx - lgVW), xv = i & (nv - 1);
-        const int64_t pr = pr0 + b;
-        if (pr >= npairs) continue;
+        if (pr0 + b >= npairs) continue;
+        const int pr = p.row_pairs[pr0 + b];
         const int64_t z = pr >> lgHy;
-        const int y0 = 2 * (int)(pr & ((Ly >> 1) - 1));
+        const int y0 = 2 * (pr & ((Ly >> 1) - 1));
         const int64_t r0 = (z * Ly + y0) * Lx;
         ((V *)(A + r0))[xv] = VecW<T>::zero();
         ((V *)(A + r0 + Lx))[xv] = VecW<T>::zero();
@@ -199,10 +206,10 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     C *S1 = (C *)p.S1;
     for (int i = threadIdx.x; i < PB * Kx; i += blockDim.x) {
         const int b = i >> lgKx, k = i & (Kx - 1);
-        const int64_t pr = pr0 + b;
-        if (pr >= npairs) continue;
+        if (pr0 + b >= npairs) continue;
+        const int pr = p.row_pairs[pr0 + b];
         const int64_t z = pr >> lgHy;
-        const int y0 = 2 * (int)(pr & ((Ly >> 1) - 1));
+        const int y0 = 2 * (pr & ((Ly >> 1) - 1));
         const C Z = res[k * ld + b];
         const C Zc = cconj(res[((Lx - k) & (Lx - 1)) * ld + b]);
         const C xa = cscale(cadd(Z, Zc), T(0.5));
@@ -225,11 +232,19 @@ __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Ly * ld;
     const int ntile = Kx / B;
-    const int z = blockIdx.x / ntile;
-    const int kx0 = (blockIdx.x - z * ntile) * B;
+    const int zi = blockIdx.x / ntile;
+    const int z = (p.z0 + zi) & (p.L[2] - 1);
+    const int kx0 = (blockIdx.x - zi * ntile) * B;
+    const int2 iv = p.plane_iv[z];  // active rows y0 .. y0 + rows - 1 (mod Ly)
     const C *S1 = (const C *)p.S1 + (int64_t)z * Ly * Kx + kx0;
     pipelined_copy<C>(
-        Ly * B, [&](int i) { return S1[(int64_t)(i >> lgB) * Kx + (i & (B - 1))]; },
+        Ly * B,
+        [&](int i) {
+            const int y = i >> lgB;
+            C v = cmk(T(0), T(0));
+            if (((y - iv.x) & (Ly - 1)) < iv.y) v = S1[(int64_t)y * Kx + (i & (B - 1))];
+            return v;
+        },
         [&](int i, C v) { b0[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
     const C *res = fft_columns<C, false>(b0, b1, Ly, ld, B, (const C *)p.tw[1]);
@@ -261,15 +276,22 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
     const int kx0 = (blockIdx.x - kp * ntile) * B;
     C *S2 = (C *)p.S2 + (int64_t)kp * Kx + kx0;
     const int64_t zs = (int64_t)ny * Kx;
+    const int z0 = p.z0, nza = p.nz_act;
     if (kp == ny / 2) {  // Nyquist row in y: dropped
         for (int i = threadIdx.x; i < Lz * B; i += blockDim.x) {
             const int z = i >> lgB, b = i & (B - 1);
-            S2[z * zs + b] = cmk(T(0), T(0));
+            if (((z - z0) & (Lz - 1)) < nza) S2[z * zs + b] = cmk(T(0), T(0));
         }
         return;
     }
     pipelined_copy<C>(
-        Lz * B, [&](int i) { return S2[(i >> lgB) * zs + (i & (B - 1))]; },
+        Lz * B,
+        [&](int i) {
+            const int z = i >> lgB;
+            C v = cmk(T(0), T(0));
+            if (((z - z0) & (Lz - 1)) < nza) v = S2[z * zs + (i & (B - 1))];
+            return v;
+        },
         [&](int i, C v) { b0[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
     C *res = fft_columns<C, false>(b0, b1, Lz, ld, B, (const C *)p.tw[2]);
@@ -289,8 +311,8 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
     }
     __syncthreads();
     const C *out = fft_columns<C, true>(res, oth, Lz, ld, B, (const C *)p.tw[2]);
-    for (int i = threadIdx.x; i < Lz * B; i += blockDim.x) {
-        const int z = i >> lgB, b = i & (B - 1);
+    for (int i = threadIdx.x; i < nza * B; i += blockDim.x) {
+        const int z = (z0 + (i >> lgB)) & (Lz - 1), b = i & (B - 1);
         S2[z * zs + b] = out[z * ld + b];
     }
 }
@@ -306,8 +328,10 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Ly * ld;
     const int ntile = Kx / B;
-    const int z = blockIdx.x / ntile;
-    const int kx0 = (blockIdx.x - z * ntile) * B;
+    const int zi = blockIdx.x / ntile;
+    const int z = (p.z0 + zi) & (p.L[2] - 1);
+    const int kx0 = (blockIdx.x - zi * ntile) * B;
+    const int2 iv = p.plane_iv[z];
     const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx + kx0;
     // position y holds mode y (y < ny/2), or mode y - Ly (y > Ly - ny/2), else zero
     pipelined_copy<C>(
@@ -325,8 +349,8 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
     __syncthreads();
     const C *res = fft_columns<C, true>(b0, b1, Ly, ld, B, (const C *)p.tw[1]);
     C *S1 = (C *)p.S1 + (int64_t)z * Ly * Kx + kx0;
-    for (int i = threadIdx.x; i < Ly * B; i += blockDim.x) {
-        const int y = i >> lgB, b = i & (B - 1);
+    for (int i = threadIdx.x; i < iv.y * B; i += blockDim.x) {
+        const int y = (iv.x + (i >> lgB)) & (Ly - 1), b = i & (B - 1);
         S1[(int64_t)y * Kx + b] = res[y * ld + b];
     }
 }
@@ -336,13 +360,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2], Kx = p.Kx;
+    const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx;
     const int ld = PB + 1;
     const int lgLx = __ffs(Lx) - 1, lgKx = __ffs(Kx) - 1, lgHy = __ffs(Ly) - 2;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Lx * ld;
-    const int64_t npairs = (int64_t)Lz * (Ly / 2);
-    const int64_t pr0 = (int64_t)blockIdx.x * PB;
+    const int npairs = p.n_row_pairs;
+    const int pr0 = blockIdx.x * PB;
     for (int i = threadIdx.x; i < PB * Lx; i += blockDim.x) b0[(i & (Lx - 1)) * ld + (i >> lgLx)] = cmk(T(0), T(0));
     __syncthreads();
     const C *S1 = (const C *)p.S1;
@@ -351,12 +375,12 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
         PB * Kx,
         [&](int i) {
             const int b = i >> lgKx, k = i & (Kx - 1);
-            const int64_t pr = pr0 + b;
             T4 v;
             v.x = v.y = v.z = v.w = T(0);
-            if (pr < npairs) {
+            if (pr0 + b < npairs) {
+                const int pr = p.row_pairs[pr0 + b];
                 const int64_t z = pr >> lgHy;
-                const int y0 = 2 * (int)(pr & ((Ly >> 1) - 1));
+                const int y0 = 2 * (pr & ((Ly >> 1) - 1));
                 const int64_t o = (z * Ly + y0) * Kx + k;
                 const C xa = S1[o], xb = S1[o + Kx];
                 v.x = xa.x;
@@ -385,10 +409,10 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
     const int nv = Lx / VW;
     for (int i = threadIdx.x; i < PB * nv; i += blockDim.x) {
         const int b = i >> (lgLx - lgVW), xv = i & (nv - 1);
-        const int64_t pr = pr0 + b;
-        if (pr >= npairs) continue;
+        if (pr0 + b >= npairs) continue;
+        const int pr = p.row_pairs[pr0 + b];
         const int64_t z = pr >> lgHy;
-        const int y0 = 2 * (int)(pr & ((Ly >> 1) - 1));
+        const int y0 = 2 * (pr & ((Ly >> 1) - 1));
         const int64_t r0 = (z * Ly + y0) * Lx;
         T ra[VW], rb[VW];
 #pragma unroll
@@ -429,8 +453,8 @@ template <typename T> static cudaError_t fx_t(const DevPlan &p, cudaStream_t s) 
     const size_t sm = 2 * (size_t)p.L[0] * (PB + 1) * ce;
     cudaError_t e = prep(k_fx<T>, sm);
     if (e != cudaSuccess) return e;
-    const int64_t npairs = (int64_t)p.L[2] * (p.L[1] / 2);
-    k_fx<T><<<(int)((npairs + PB - 1) / PB), 256, sm, s>>>(p, PB);
+    if (p.n_row_pairs == 0) return cudaSuccess;
+    k_fx<T><<<(p.n_row_pairs + PB - 1) / PB, 256, sm, s>>>(p, PB);
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) {
@@ -439,8 +463,8 @@ template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) 
     const size_t sm = 2 * (size_t)p.L[0] * (PB + 1) * ce;
     cudaError_t e = prep(k_ix<T>, sm);
     if (e != cudaSuccess) return e;
-    const int64_t npairs = (int64_t)p.L[2] * (p.L[1] / 2);
-    k_ix<T><<<(int)((npairs + PB - 1) / PB), 256, sm, s>>>(p, PB);
+    if (p.n_row_pairs == 0) return cudaSuccess;
+    k_ix<T><<<(p.n_row_pairs + PB - 1) / PB, 256, sm, s>>>(p, PB);
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) {
@@ -449,7 +473,8 @@ template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) 
     const size_t sm = 2 * (size_t)p.L[1] * (B + 1) * ce;
     cudaError_t e = prep(k_fy<T>, sm);
     if (e != cudaSuccess) return e;
-    k_fy<T><<<p.L[2] * (p.Kx / B), 256, sm, s>>>(p, B);
+    if (p.nz_act == 0) return cudaSuccess;
+    k_fy<T><<<p.nz_act * (p.Kx / B), 256, sm, s>>>(p, B);
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) {
@@ -458,7 +483,8 @@ template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) 
     const size_t sm = 2 * (size_t)p.L[1] * (B + 1) * ce;
     cudaError_t e = prep(k_iy<T>, sm);
     if (e != cudaSuccess) return e;
-    k_iy<T><<<p.L[2] * (p.Kx / B), 256, sm, s>>>(p, B);
+    if (p.nz_act == 0) return cudaSuccess;
+    k_iy<T><<<p.nz_act * (p.Kx / B), 256, sm, s>>>(p, B);
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t fz_t(const DevPlan &p, cudaStream_t s) {
@@ -467,6 +493,7 @@ template <typename T> static cudaError_t fz_t(const DevPlan &p, cudaStream_t s) 
     const size_t sm = 2 * (size_t)p.L[2] * (B + 1) * ce;
     cudaError_t e = prep(k_fz<T>, sm);
     if (e != cudaSuccess) return e;
+    if (p.nz_act == 0) return cudaSuccess;
     k_fz<T><<<p.n[1] * (p.Kx / B), 256, sm, s>>>(p, B);
     return cudaGetLastError();
 }

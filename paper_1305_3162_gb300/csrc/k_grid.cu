@@ -18,7 +18,7 @@ namespace slp {
 
 // ---------------------------------------------------------------- charges
 // Nodal magnetisation in sorted target order, one 4-vector per vertex, so the
-// charge assembly and the near-field product read it coalesced.
+// precomputed near-field product reads it coalesced.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nodal_prep(DevPlan p, const T *__restrict__ in) {
     typedef typename VecT<T>::T4 T4;
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) k_nodal_prep(DevPlan p, const T *__restri
 }
 
 // w_k * sigma_k of sorted source k for the three input kinds (NODAL_MAG
-// reads the sorted 4-vectors written by k_nodal_prep).
+// interpolates the user-order nodal values of the triangle's vertices).
 template <typename T>
 __device__ __forceinline__ T source_charge(const DevPlan &p, int64_t k, int kind, const T *__restrict__ in) {
     typedef typename VecT<T>::T4 T4;
@@ -53,11 +53,10 @@ __device__ __forceinline__ T source_charge(const DevPlan &p, int64_t k, int kind
         const int4 v = p.tri_vtx[j];
         const T *lam = (const T *)p.lam + 3 * s;
         const T l0 = lam[0], l1 = lam[1], l2 = lam[2];
-        const T4 *m4 = (const T4 *)p.m4;
-        const T4 a = m4[v.x], b = m4[v.y], c = m4[v.z];
-        mx = l0 * a.x + l1 * b.x + l2 * c.x;
-        my = l0 * a.y + l1 * b.y + l2 * c.y;
-        mz = l0 * a.z + l1 * b.z + l2 * c.z;
+        const T *a = in + 3 * (int64_t)v.x, *b = in + 3 * (int64_t)v.y, *c = in + 3 * (int64_t)v.z;
+        mx = l0 * a[0] + l1 * b[0] + l2 * c[0];
+        my = l0 * a[1] + l1 * b[1] + l2 * c[1];
+        mz = l0 * a[2] + l1 * b[2] + l2 * c[2];
     }
     return w * (mx * nrm.x + my * nrm.y + mz * nrm.z);
 }
@@ -239,10 +238,16 @@ __global__ void __launch_bounds__(256) k_spread(DevPlan p, int fused_kind, const
 // Variant for 2M <= 10: runs of consecutive sources that share a grid cell
 // (the Morton sort makes them contiguous) have the same window box, so a warp
 // sums a whole run in registers and updates its private tile once per run.
-// Lanes map to (x offset ix, z offset izs); a lane holds the box column
-// (ix, iz = izs + ZL h, all iy) as H x W accumulators.  The plane stride is
-// congruent to W modulo 32, so the 8 x 4 lanes of a row update hit 32
-// different banks.
+//   * run length: one ballot over the next SPREAD_GMAX sources;
+//   * window values: lane (axis, i) evaluates psi(f_axis + M - 1 - i) for
+//     every source of the run (FP32: the per-interval polynomial, its
+//     coefficients held in registers), the charge folded into the x values;
+//     rows of WP (W rounded up to 4) values, so the y row is read as 16-byte
+//     vectors;
+//   * accumulation: lanes map to (x offset ix, z offset izs); a lane holds
+//     the box column (ix, iz = izs + ZL h, all iy) as H x W accumulators.  The
+//     plane stride is congruent to W modulo 32, so the 8 x 4 lanes of a row
+//     update hit 32 different banks.
 template <int M, int TS> struct TileGeomG {
     static constexpr int W = 2 * M;
     static constexpr int TE = TS + W - 1;
@@ -253,25 +258,52 @@ template <int M, int TS> struct TileGeomG {
     static constexpr int SIZE = TE * PS;
     static constexpr int ZL = 32 / W;                   // z offsets per lane group
     static constexpr int H = (W + ZL - 1) / ZL;         // z offsets per lane
+    static constexpr int WP = (W + 3) & ~3;             // padded row of window values
 };
 
 constexpr int SPREAD_GMAX = 16;  // sources per cell group
+
+// row of WP window values from shared memory, 16 bytes per load
+template <int WP> __device__ __forceinline__ void load_row(const float *src, float *dst) {
+#pragma unroll
+    for (int j = 0; j < WP / 4; ++j) {
+        const float4 v = ((const float4 *)src)[j];
+        dst[4 * j] = v.x;
+        dst[4 * j + 1] = v.y;
+        dst[4 * j + 2] = v.z;
+        dst[4 * j + 3] = v.w;
+    }
+}
+template <int WP> __device__ __forceinline__ void load_row(const double *src, double *dst) {
+#pragma unroll
+    for (int j = 0; j < WP / 2; ++j) {
+        const double2 v = ((const double2 *)src)[j];
+        dst[2 * j] = v.x;
+        dst[2 * j + 1] = v.y;
+    }
+}
+
+template <typename T, int M, int TS> struct SpreadSmem {
+    typedef TileGeomG<M, TS> G;
+    static constexpr int AX = SPREAD_GMAX * G::WP;  // window values of one axis of one warp
+    // offsets in elements of T: tiles, window values (16-byte aligned), sources
+    __host__ __device__ static size_t wv(int nwarps) { return ((size_t)nwarps * G::SIZE + 3) & ~(size_t)3; }
+    __host__ __device__ static size_t head(int nwarps) { return (wv(nwarps) + (size_t)nwarps * 3 * AX + 3) & ~(size_t)3; }
+    __host__ __device__ static size_t bytes(int nwarps, int chunk) { return head(nwarps) * sizeof(T) + (size_t)chunk * 5 * sizeof(T); }
+};
 
 template <typename T, int M, int TS>
 __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind, const T *__restrict__ in) {
     typedef typename VecT<T>::T4 T4;
     typedef TileGeomG<M, TS> G;
-    constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO, XE = G::XE, ZL = G::ZL, H = G::H;
-    constexpr int GW = 3 * W;  // window values per source
+    typedef SpreadSmem<T, M, TS> SM;
+    constexpr int W = G::W, TS_ = TS, RS = G::RS, PS = G::PS, XO = G::XO, ZL = G::ZL, H = G::H, WP = G::WP;
+    constexpr int AX = SM::AX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     T *tiles = (T *)smem_raw;
-    T *coef = tiles + nwarps * G::SIZE;
-    const int ncoef = W * (WDEG + 1);
-    T *wvall = coef + ((ncoef + 3) & ~3);
-    T *wv = wvall + warp * (SPREAD_GMAX * GW);
-    const size_t head = ((size_t)nwarps * G::SIZE + ((ncoef + 3) & ~3) + (size_t)nwarps * SPREAD_GMAX * GW + 3) & ~(size_t)3;
-    T4 *sg = (T4 *)(tiles + head);
+    T *wv = tiles + SM::wv(nwarps) + (size_t)warp * 3 * AX;
+    T4 *sg = (T4 *)(tiles + SM::head(nwarps));
     T *sq = (T *)(sg + p.spread_chunk);
     T *my = tiles + warp * G::SIZE;
 
@@ -286,42 +318,51 @@ __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind
         }
     }
     for (int i = threadIdx.x; i < nwarps * G::SIZE; i += blockDim.x) tiles[i] = T(0);
-    if (sizeof(T) == 4)
-        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) coef[i] = ((const T *)p.wcoef)[i];
-    __syncthreads();
 
+    // lane (wax, wi) evaluates window point wi along axis wax
+    const int wax = lane / W, wi = lane - wax * W;
+    const bool wlane = lane < 3 * W;
+    T cf[WDEG + 1];
+#pragma unroll
+    for (int k = 0; k <= WDEG; ++k) cf[k] = T(0);
+    if (sizeof(T) == 4 && wlane) {
+#pragma unroll
+        for (int k = 0; k <= WDEG; ++k) cf[k] = ((const T *)p.wcoef)[wi * (WDEG + 1) + k];
+    }
     const T inv_m = T(1) / T(M);
     const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
+    __syncthreads();
+
     const int ix = lane % W, izs = lane / W;
     const bool lane_on = lane < W * ZL;
     const int c0 = (nsrc * warp) / nwarps, c1 = (nsrc * (warp + 1)) / nwarps;
     for (int g0 = c0; g0 < c1;) {
         const int cell = packed_cell(sg[g0].w);
-        int ge = g0 + 1;
-        while (ge < c1 && ge - g0 < SPREAD_GMAX && packed_cell(sg[ge].w) == cell) ++ge;
-        const int ng = ge - g0;
+        const int idx = g0 + lane;
+        const bool same = lane < SPREAD_GMAX && idx < c1 && packed_cell(sg[idx].w) == cell;
+        const int ng = __ffs(~__ballot_sync(0xffffffffu, same)) - 1;  // >= 1: lane 0 always matches
         int cx, cy, cz;
         unpack_cell(cell, cx, cy, cz);
         const int lx = cx - it.c0x, ly = cy - it.c0y, lz = cz - it.c0z;
-        if ((unsigned)lx >= (unsigned)TS || (unsigned)ly >= (unsigned)TS || (unsigned)lz >= (unsigned)TS) {
+        if ((unsigned)lx >= (unsigned)TS_ || (unsigned)ly >= (unsigned)TS_ || (unsigned)lz >= (unsigned)TS_) {
             set_error(p.err, DEV_ERR_BAD_ITEM);
-            g0 = ge;
+            g0 += ng;
             continue;
         }
-        // window values of the group: wv[g * GW + axis * W + i]
-        for (int j = lane; j < ng * GW; j += 32) {
-            const int g = j / GW, r = j - g * GW;
-            const T4 sgg = sg[g0 + g];
-            const int ax = r / W, i = r - ax * W;
-            const T f = ax == 0 ? sgg.x : (ax == 1 ? sgg.y : sgg.z);
-            if (sizeof(T) == 4) {
-                const T *c = coef + i * (WDEG + 1);
-                T v = c[WDEG];
+        if (wlane) {
+            T *dst = wv + wax * AX + wi;
+            for (int g = 0; g < ng; ++g) {
+                const T f = ((const T *)(sg + g0 + g))[wax];
+                T v;
+                if (sizeof(T) == 4) {
+                    v = cf[WDEG];
 #pragma unroll
-                for (int k = WDEG - 1; k >= 0; --k) v = v * f + c[k];
-                wv[j] = v;
-            } else {
-                wv[j] = kb_window(f + T(M - 1 - i), inv_m, beta, isb);
+                    for (int k = WDEG - 1; k >= 0; --k) v = v * f + cf[k];
+                } else {
+                    v = kb_window(f + T(M - 1 - wi), inv_m, beta, isb);
+                }
+                if (wax == 0) v *= sq[g0 + g];
+                dst[g * WP] = v;
             }
         }
         __syncwarp();
@@ -332,20 +373,20 @@ __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind
 #pragma unroll
                 for (int iy = 0; iy < W; ++iy) acc[h][iy] = T(0);
             for (int g = 0; g < ng; ++g) {
-                const T *w = wv + g * GW;
-                const T a = sq[g0 + g] * w[ix];
+                const T a = wv[g * WP + ix];
+                const T *wz = wv + 2 * AX + g * WP;
                 T b[H];
 #pragma unroll
                 for (int h = 0; h < H; ++h) {
                     const int iz = izs + ZL * h;
-                    b[h] = iz < W ? a * w[2 * W + iz] : T(0);
+                    b[h] = iz < W ? a * wz[iz] : T(0);
                 }
+                T wy[WP];
+                load_row<WP>(wv + AX + g * WP, wy);
 #pragma unroll
-                for (int iy = 0; iy < W; ++iy) {
-                    const T wy = w[W + iy];
+                for (int iy = 0; iy < W; ++iy)
 #pragma unroll
-                    for (int h = 0; h < H; ++h) acc[h][iy] += b[h] * wy;
-                }
+                    for (int h = 0; h < H; ++h) acc[h][iy] += b[h] * wy[iy];
             }
             T *base = my + lz * PS + ly * RS + lx + XO + ix;
 #pragma unroll
@@ -361,10 +402,11 @@ __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind
             }
         }
         __syncwarp();
-        g0 = ge;
+        g0 += ng;
     }
     __syncthreads();
 
+    constexpr int TE = G::TE, XE = G::XE;
     const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
     const int gxs = it.c0x - M + 1 - XO, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
     T *grid = (T *)p.gridA;
@@ -400,25 +442,50 @@ __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind
 }
 
 // ---------------------------------------------------------------- gather
-// One block per work item (a tile and up to 32 of its targets): the tile plus
-// halo of grid B is staged in shared memory (same padded layout as the
-// spread), then one warp per target sums its (2M)^3 window box.
+// One block per work item (a tile and up to GATHER_CHUNK of its targets): the
+// tile plus halo of grid B is staged in shared memory (same padded layout as
+// the spread), together with the item's target coordinates, permutation,
+// near-field parts and window values; then one warp per target sums its
+// (2M)^3 window box, lanes over the (y, z) rows of the box.
+constexpr int GATHER_CHUNK = 32;  // targets per gather item (set by the plan)
+
 template <typename T, int M, int TS>
-__global__ void __launch_bounds__(128) k_gather(DevPlan p, T *__restrict__ phi) {
+__global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) {
     typedef typename VecT<T>::T4 T4;
     typedef TileGeom<M, TS> G;
     constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO;
+    constexpr int GW = 3 * W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     T *tile = (T *)smem_raw;
     T *coef = tile + G::SIZE;
-    const int ncoef = W * (p.wdeg + 1);
-    T *wv = coef + ((ncoef + 3) & ~3) + warp * (3 * W);
+    const int ncoef = W * (WDEG + 1);
+    T *wv = coef + ((ncoef + 3) & ~3);  // [GATHER_CHUNK][3W]
+    T *sf = wv + GATHER_CHUNK * GW;     // [3][GATHER_CHUNK] fractions
+    T *sphi = sf + 3 * GATHER_CHUNK;    // [GATHER_CHUNK] near-field parts
+    int *sidx = (int *)(sphi + GATHER_CHUNK);  // [2][GATHER_CHUNK] packed cell, output index
 
     const TileItem it = p.gather_items[blockIdx.x];
+    const int nt = it.end - it.begin;
+    if (nt > GATHER_CHUNK) {
+        if (threadIdx.x == 0) set_error(p.err, DEV_ERR_BAD_ITEM);
+        return;
+    }
     const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
     const int gx0 = it.c0x - M + 1, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
     const T *grid = (const T *)p.gridB;
+    if (threadIdx.x < nt) {
+        const int t = it.begin + threadIdx.x;
+        const T4 g = ((const T4 *)p.tgt_grid)[t];
+        sf[threadIdx.x] = g.x;
+        sf[GATHER_CHUNK + threadIdx.x] = g.y;
+        sf[2 * GATHER_CHUNK + threadIdx.x] = g.z;
+        sidx[threadIdx.x] = packed_cell(g.w);
+        sidx[GATHER_CHUNK + threadIdx.x] = p.tgt_perm[t];
+        sphi[threadIdx.x] = ((const T *)p.phi_part)[t];
+    }
+    if (sizeof(T) == 4)
+        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) coef[i] = ((const T *)p.wcoef)[i];
     pipelined_copy<T>(
         TE * TE * TE,
         [&](int i) {
@@ -432,24 +499,36 @@ __global__ void __launch_bounds__(128) k_gather(DevPlan p, T *__restrict__ phi) 
             const int x = i % TE, r = i / TE;
             tile[(r / TE) * PS + (r % TE) * RS + x + XO] = v;
         });
-    if (sizeof(T) == 4)
-        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) coef[i] = ((const T *)p.wcoef)[i];
     __syncthreads();
 
-    const T4 *tg = (const T4 *)p.tgt_grid;
+    // window values of every target of the item: wv[t * 3W + axis * W + i]
     const T inv_m = T(1) / T(M);
     const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
-    for (int t = it.begin + warp; t < it.end; t += nwarps) {
-        const T4 g = tg[t];
+    for (int j = threadIdx.x; j < nt * GW; j += blockDim.x) {
+        const int t = j / GW, r = j - t * GW;
+        const int ax = r / W, i = r - ax * W;
+        const T f = sf[ax * GATHER_CHUNK + t];
+        if (sizeof(T) == 4) {
+            const T *c = coef + i * (WDEG + 1);
+            T v = c[WDEG];
+#pragma unroll
+            for (int k = WDEG - 1; k >= 0; --k) v = v * f + c[k];
+            wv[j] = v;
+        } else {
+            wv[j] = kb_window(f + T(M - 1 - i), inv_m, beta, isb);
+        }
+    }
+    __syncthreads();
+
+    for (int t = warp; t < nt; t += nwarps) {
         int cx, cy, cz;
-        unpack_cell(packed_cell(g.w), cx, cy, cz);
+        unpack_cell(sidx[t], cx, cy, cz);
         const int lx = cx - it.c0x, ly = cy - it.c0y, lz = cz - it.c0z;
         if ((unsigned)lx >= (unsigned)TS || (unsigned)ly >= (unsigned)TS || (unsigned)lz >= (unsigned)TS) {
             set_error(p.err, DEV_ERR_BAD_ITEM);
             continue;
         }
-        window_values<M>(wv, g.x, g.y, g.z, coef, p.wdeg, inv_m, beta, isb);
-        __syncwarp();
+        const T *w = wv + t * GW;
         const T *base = tile + lz * PS + ly * RS + lx + XO;
         T acc = T(0);
 #pragma unroll
@@ -460,13 +539,12 @@ __global__ void __launch_bounds__(128) k_gather(DevPlan p, T *__restrict__ phi) 
                 const T *row = base + iz * PS + iy * RS;
                 T s = T(0);
 #pragma unroll
-                for (int ix = 0; ix < W; ++ix) s += row[ix] * wv[ix];
-                acc += s * wv[2 * W + iz] * wv[W + iy];
+                for (int ix = 0; ix < W; ++ix) s += row[ix] * w[ix];
+                acc += s * w[2 * W + iz] * w[W + iy];
             }
         }
         acc = warp_sum(acc);
-        if (lane == 0) phi[p.tgt_perm[t]] = acc + ((const T *)p.phi_part)[t];
-        __syncwarp();
+        if (lane == 0) phi[sidx[GATHER_CHUNK + t]] = acc + sphi[t];
     }
 }
 
@@ -484,20 +562,12 @@ template <typename T, int M, int TS> static size_t spread_smem(int nwarps, int w
     return head * sizeof(T) + (size_t)chunk * (4 * sizeof(T) + sizeof(T));
 }
 
-template <typename T, int M, int TS> static size_t spread_groups_smem(int nwarps, int chunk) {
-    typedef TileGeomG<M, TS> G;
-    const int ncoef = 2 * M * (WDEG + 1);
-    const size_t head =
-        (((size_t)nwarps * G::SIZE + ((ncoef + 3) & ~3) + (size_t)nwarps * SPREAD_GMAX * 3 * 2 * M) + 3) & ~(size_t)3;
-    return head * sizeof(T) + (size_t)chunk * (4 * sizeof(T) + sizeof(T));
-}
-
 template <typename T, int M, int TS>
 static cudaError_t spread_mt(const DevPlan &p, int fused_kind, const void *in, cudaStream_t s) {
     if constexpr (M <= 5) {
         int nw = 8;
-        while (nw > 1 && spread_groups_smem<T, M, TS>(nw, p.spread_chunk) > 100 * 1024) nw >>= 1;
-        const size_t sm = spread_groups_smem<T, M, TS>(nw, p.spread_chunk);
+        while (nw > 1 && SpreadSmem<T, M, TS>::bytes(nw, p.spread_chunk) > 100 * 1024) nw >>= 1;
+        const size_t sm = SpreadSmem<T, M, TS>::bytes(nw, p.spread_chunk);
         if (sm > 48 * 1024) {
             cudaError_t e =
                 cudaFuncSetAttribute(k_spread_groups<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -520,13 +590,14 @@ static cudaError_t spread_mt(const DevPlan &p, int fused_kind, const void *in, c
 
 template <typename T, int M, int TS> static cudaError_t gather_mt(const DevPlan &p, void *phi, cudaStream_t s) {
     typedef TileGeom<M, TS> G;
-    const int ncoef = 2 * M * (p.wdeg + 1);
-    const size_t sm = ((size_t)G::SIZE + ((ncoef + 3) & ~3) + 4 * 3 * 2 * M) * sizeof(T);
+    const int ncoef = 2 * M * (WDEG + 1);
+    const size_t sm = ((size_t)G::SIZE + ((ncoef + 3) & ~3) + GATHER_CHUNK * (3 * 2 * M + 4)) * sizeof(T) +
+                      2 * GATHER_CHUNK * sizeof(int);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_gather<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    if (p.n_gather > 0) k_gather<T, M, TS><<<p.n_gather, 128, sm, s>>>(p, (T *)phi);
+    if (p.n_gather > 0) k_gather<T, M, TS><<<p.n_gather, 256, sm, s>>>(p, (T *)phi);
     return cudaGetLastError();
 }
 

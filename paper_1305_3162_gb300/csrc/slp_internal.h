@@ -50,7 +50,7 @@ struct DevPlan {
     const int *src_perm;    // [Q] sorted -> user index k = j*q + s
     const void *src_w;      // T [Q] w_s |S_j| in sorted order
     const void *tri_nrm;    // T4 [M] outward unit normals (user triangle order)
-    const int4 *tri_vtx;    // [M] vertex ids as sorted target positions
+    const int4 *tri_vtx;    // [M] vertex ids (user order)
     const void *lam;        // T [q*3] barycentric points of the rule
     // targets, sorted
     const void *tgt_grid;   // T4 [N]
@@ -67,6 +67,14 @@ struct DevPlan {
     void *phi_part; // T [N] near-field correction per sorted target, added by the gather
     const void *Dtab;   // T [n_z/2][n_y/2][Kx] kernel multiplier by |l_z|, |l_y|, l_x
     const void *tw[3];  // T2 [L_q] forward twiddles exp(-2 pi i t / L_q)
+
+    // active rows (spread support of the sources and gather support of the
+    // targets): planes z0 .. z0 + nz_act - 1 (mod Lz); in plane z the rows
+    // plane_iv[z].x .. plane_iv[z].x + plane_iv[z].y - 1 (mod Ly), pair aligned
+    int z0, nz_act;
+    const int2 *plane_iv;
+    const int *row_pairs;  // [n_row_pairs] z * (Ly / 2) + y / 2
+    int n_row_pairs;
 
     const TileItem *spread_items; int n_spread;
     int spread_chunk;             // most sources in one spread item

@@ -688,6 +688,81 @@ void build_dtab(slp_plan_s &p) {
             }
 }
 
+// ---------------------------------------------------------------- active rows
+// Shortest cyclic interval of Z_L holding every set entry s[i * stride]:
+// the complement of the longest cyclic run of unset entries.
+void cyclic_cover(const uint8_t *s, int L, size_t stride, int &start, int &len) {
+    int best = 0, best_end = -1, run = 0;
+    for (int i = 0; i < 2 * L; ++i) {
+        if (!s[(size_t)(i % L) * stride]) {
+            if (++run > best) {
+                best = run;
+                best_end = i;
+            }
+        } else {
+            run = 0;
+        }
+    }
+    if (best >= L) {  // nothing set
+        start = 0;
+        len = 0;
+    } else if (best == 0) {
+        start = 0;
+        len = L;
+    } else {
+        start = (best_end + 1) % L;
+        len = L - best;
+    }
+}
+
+// Grid A is nonzero only on rows (z, y) within the window of some source,
+// and the gather reads grid B only on rows within the window of some target
+// (offsets -m+1 .. m of the point's cell on each axis).  The FFT passes work
+// on the cyclic z interval covering those rows and, per plane, on the cyclic
+// y interval covering them, widened to whole row pairs; every other row of
+// grid A, S1 and grid B is zero or never read (Sec. 5: the transforms only
+// need the data the spread can produce and the gather consumes).
+void active_region(slp_plan_s &p) {
+    const int Ly = p.L[1], Lz = p.L[2], m = p.m;
+    std::vector<uint8_t> col((size_t)Lz * Ly, 0), dy((size_t)Lz * Ly, 0), dz((size_t)Lz * Ly, 0);
+    auto mark = [&](const std::vector<double> &grid, int64_t n) {
+        for (int64_t i = 0; i < n; ++i) {
+            const uint32_t pk = (uint32_t)grid[4 * i + 3];
+            col[(size_t)((pk >> 20) & 1023) * Ly + ((pk >> 10) & 1023)] = 1;
+        }
+    };
+    mark(p.src_grid, p.Q);
+    mark(p.tgt_grid, p.N);
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < Ly; ++y)
+            if (col[(size_t)z * Ly + y])
+                for (int o = -m + 1; o <= m; ++o) dy[(size_t)z * Ly + (((y + o) % Ly) + Ly) % Ly] = 1;
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < Ly; ++y)
+            if (dy[(size_t)z * Ly + y])
+                for (int o = -m + 1; o <= m; ++o) dz[(size_t)((((z + o) % Lz) + Lz) % Lz) * Ly + y] = 1;
+    std::vector<uint8_t> zany(Lz, 0);
+    for (int z = 0; z < Lz; ++z)
+        for (int y = 0; y < Ly; ++y) zany[z] |= dz[(size_t)z * Ly + y];
+    cyclic_cover(zany.data(), Lz, 1, p.z0, p.nz_act);
+    p.plane_iv.assign(Lz, make_int2(0, 0));
+    p.row_pairs.clear();
+    for (int i = 0; i < p.nz_act; ++i) {
+        const int z = (p.z0 + i) % Lz;
+        int y0, ny;
+        cyclic_cover(&dz[(size_t)z * Ly], Ly, 1, y0, ny);
+        if (ny > 0) {
+            int ye = y0 + ny;
+            y0 &= ~1;
+            ye = (ye + 1) & ~1;
+            ny = std::min(ye - y0, Ly);
+            if (ny == Ly) y0 = 0;
+        }
+        p.plane_iv[z] = make_int2(y0, ny);
+        for (int j = 0; j < ny / 2; ++j) p.row_pairs.push_back(z * (Ly / 2) + ((y0 + 2 * j) % Ly) / 2);
+    }
+}
+
 // ---------------------------------------------------------------- device upload
 template <typename T> struct V4;
 template <> struct V4<float> { typedef float4 t; typedef float2 t2; };
@@ -803,14 +878,12 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     for (int64_t i = 0; i < p.Q; ++i) sw[i] = (T)p.wk[p.src_perm[i]];
     std::vector<T4> tn(p.M);
     std::vector<int4> tv(p.M);
-    std::vector<int> inv_tperm(p.N);
-    for (int64_t i = 0; i < p.N; ++i) inv_tperm[p.tgt_perm[i]] = (int)i;
     for (int64_t j = 0; j < p.M; ++j) {
         tn[j].x = (T)p.nrm[3 * j];
         tn[j].y = (T)p.nrm[3 * j + 1];
         tn[j].z = (T)p.nrm[3 * j + 2];
         tn[j].w = T(0);
-        tv[j] = make_int4(inv_tperm[p.T[3 * j]], inv_tperm[p.T[3 * j + 1]], inv_tperm[p.T[3 * j + 2]], 0);
+        tv[j] = make_int4(p.T[3 * j], p.T[3 * j + 1], p.T[3 * j + 2], 0);
     }
     std::vector<T> lamT(p.lam.begin(), p.lam.end());
     void *ptr;
@@ -841,7 +914,12 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     TRY(dalloc(p, &d.gridB, sizeof(T) * G));
     TRY(dalloc(p, &d.S1, sizeof(T2) * (size_t)p.L[2] * p.L[1] * Kx));
     TRY(dalloc(p, &d.S2, sizeof(T2) * (size_t)p.L[2] * p.n[1] * Kx));
-    if (cudaMemset(d.gridA, 0, sizeof(T) * G) != cudaSuccess) return fail(SLP_ERR_CUDA, "cudaMemset failed");
+    // grid A starts zero; rows outside the active region of S1, S2 and grid B
+    // are never written, so they are cleared once here
+    if (cudaMemset(d.gridA, 0, sizeof(T) * G) != cudaSuccess || cudaMemset(d.gridB, 0, sizeof(T) * G) != cudaSuccess ||
+        cudaMemset(d.S1, 0, sizeof(T2) * (size_t)p.L[2] * p.L[1] * Kx) != cudaSuccess ||
+        cudaMemset(d.S2, 0, sizeof(T2) * (size_t)p.L[2] * p.n[1] * Kx) != cudaSuccess)
+        return fail(SLP_ERR_CUDA, "cudaMemset failed");
 
     std::vector<T> Dt(p.Dtab.begin(), p.Dtab.end());
     TRY(upload(p, &ptr, Dt.data(), Dt.size()));
@@ -856,6 +934,13 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
         TRY(upload(p, &ptr, tw.data(), tw.size()));
         d.tw[a] = ptr;
     }
+    d.z0 = p.z0;
+    d.nz_act = p.nz_act;
+    TRY(upload(p, &ptr, p.plane_iv.data(), p.plane_iv.size()));
+    d.plane_iv = (const int2 *)ptr;
+    TRY(upload(p, &ptr, p.row_pairs.data(), p.row_pairs.size()));
+    d.row_pairs = (const int *)ptr;
+    d.n_row_pairs = (int)p.row_pairs.size();
     TRY(upload(p, &ptr, p.spread_items.data(), p.spread_items.size()));
     d.spread_items = (const slp::TileItem *)ptr;
     d.n_spread = (int)p.spread_items.size();
@@ -888,8 +973,9 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     // staging buffers for slp_eval_host
     TRY(dalloc(p, &p.d_stage_in, sizeof(T) * 3 * std::max(p.Q, p.N)));
     TRY(dalloc(p, &p.d_stage_phi, sizeof(T) * p.N));
-    // for NODAL_MAG input: prep, charges, spread, 5 FFT passes, gather, near field (+ ordered reduction)
-    p.launches_per_eval = 10 + (p.opts.deterministic ? 1 : 0);
+    // on-the-fly near field: charges, spread, 5 FFT passes, gather, and either
+    // zeroing + atomic near field or near field + ordered reduction
+    p.launches_per_eval = 10;
     return SLP_OK;
 }
 
@@ -1155,6 +1241,7 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
     // near-field branch on stream t
     auto near_branch = [&](cudaStream_t t) -> slp_status {
         if (use_matrix) {
+            TRY(cuda_status(slp::launch_nodal_prep(d, d_in, t), "nodal prep"));
             TRY(cuda_status(slp::launch_near_matrix(d, d_in, t), "near-field matrix"));
             rec();
             rec();
@@ -1171,7 +1258,6 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
         return SLP_OK;
     };
     rec();
-    if (kind == SLP_INPUT_NODAL_MAG) TRY(cuda_status(slp::launch_nodal_prep(d, d_in, s), "nodal prep"));
     if (!fuse) TRY(cuda_status(slp::launch_charges(d, kind, d_in, s), "charges"));
     rec();
     if (last <= SLP_STAGE_CHARGES) return SLP_OK;
@@ -1305,7 +1391,10 @@ slp_status slp_alloc_scratch(slp_plan_s &p, slp::DevPlan &out, std::vector<void 
         *r.dst = ptr;
         total += (int64_t)nb;
     }
-    if (cudaMemset(out.gridA, 0, es * G) != cudaSuccess) return slp_fail(SLP_ERR_CUDA, "cudaMemset failed");
+    if (cudaMemset(out.gridA, 0, es * G) != cudaSuccess || cudaMemset(out.gridB, 0, es * G) != cudaSuccess ||
+        cudaMemset(out.S1, 0, 2 * es * p.L[2] * p.L[1] * Kx) != cudaSuccess ||
+        cudaMemset(out.S2, 0, 2 * es * p.L[2] * p.n[1] * Kx) != cudaSuccess)
+        return slp_fail(SLP_ERR_CUDA, "cudaMemset failed");
     if (bytes) *bytes = total;
     return SLP_OK;
 }
@@ -1376,6 +1465,7 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
     tile_items(*p, p->tgt_grid, tkeys, p->N, 32, p->gather_items);
     near_items(*p, skeys, tkeys);
     build_dtab(*p);
+    active_region(*p);
     p->near_mode = SLP_NEAR_ON_THE_FLY;
 
     if (p->device >= 0) {
@@ -1454,6 +1544,7 @@ slp_status slp_query(slp_plan_t p, slp_info *info) {
     info->n_gather_items = (int64_t)p->gather_items.size();
     info->n_near_items = (int64_t)p->near_items.size();
     info->launches_per_eval = p->launches_per_eval;
+    info->active_rows = 2 * (int64_t)p->row_pairs.size();
     return SLP_OK;
 }
 
@@ -1567,6 +1658,8 @@ slp_status slp_debug_host_count(slp_plan_t p, int which, int64_t *count) {
         case SLP_HOST_DTAB: *count = (int64_t)p->Dtab.size(); break;
         case SLP_HOST_SRC_POINTS: *count = 3 * p->Q; break;
         case SLP_HOST_TGT_POINTS: *count = 3 * p->N; break;
+        case SLP_HOST_PLANE_ROWS: *count = 2 * (int64_t)p->plane_iv.size(); break;
+        case SLP_HOST_ACTIVE_Z: *count = 2; break;
         default: return fail(SLP_ERR_INVALID_ARG, "unknown host array %d", which);
     }
     return SLP_OK;
@@ -1596,6 +1689,13 @@ slp_status slp_debug_host_array(slp_plan_t p, int which, void *out, int64_t coun
             double *o = (double *)out;
             for (int64_t i = 0; i < p->N; ++i)
                 for (int d = 0; d < 3; ++d) o[3 * i + d] = p->V[3 * (int64_t)p->tgt_perm[i] + d];
+            break;
+        }
+        case SLP_HOST_PLANE_ROWS: memcpy(out, p->plane_iv.data(), 4 * count); break;
+        case SLP_HOST_ACTIVE_Z: {
+            int32_t *o = (int32_t *)out;
+            o[0] = p->z0;
+            o[1] = p->nz_act;
             break;
         }
     }

@@ -57,6 +57,11 @@ struct slp_plan_s {
     std::vector<int> near_blk_first;  // CSR of items per target block
     std::vector<double> Dtab;
     int64_t near_pairs = 0;
+    // rows of the grid the FFT passes work on: the cyclic z interval
+    // [z0, z0 + nz_act) and, per plane, a pair-aligned cyclic y interval
+    std::vector<int2> plane_iv;       // [Lz] (y0, rows)
+    std::vector<int32_t> row_pairs;   // z * (Ly / 2) + y / 2 of each active row pair
+    int z0 = 0, nz_act = 0;
 
     // device
     slp::DevPlan dp;
@@ -85,7 +90,8 @@ slp_status slp_run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, cons
 
 // Allocate a second scratch set (charges, sorted m, grids, spectra, partials)
 // for `p` and return a device view that uses it; the pointers are appended to
-// `allocs` (released by the caller with cudaFree).  Grid A is zeroed.
+// `allocs` (released by the caller with cudaFree).  Grids and spectra are
+// zeroed (rows outside the active region are never written afterwards).
 slp_status slp_alloc_scratch(slp_plan_s &p, slp::DevPlan &out, std::vector<void *> &allocs, int64_t *bytes);
 
 // Bytes of one scratch set of `p`.

@@ -232,3 +232,53 @@ def test_batch_and_server_refuse_host_only_plans(slp):
         assert e.value.status == slp.SLP_ERR_INVALID_ARG
     finally:
         slp.slp_destroy(p)
+
+
+def _in_cyclic(v, start, count, L):
+    return ((v - start) % L) < count
+
+
+@pytest.mark.parametrize("shape", ["sphere", "torus", "plate"])
+def test_active_region_covers_every_window_row(slp, shape):
+    """The FFT passes only transform the active rows: every (z, y) row inside
+    the window of a source (where grid A can be nonzero) or of a target
+    (where the gather reads grid B) must be active, with pair-aligned
+    intervals; and for a surface in its padded torus most rows are not."""
+    if shape == "sphere":
+        w = workloads.sphere(level=4)
+        p = _host_plan(slp, w.V, w.T, q=7, grid=(128, 128, 128))
+    elif shape == "torus":
+        V, T = meshes.torus(2.0, 0.5, 48, 16)
+        p = _host_plan(slp, V, T, q=3, grid=(64, 64, 32))
+    else:
+        w = workloads.plate(dims=(200.0, 50.0, 2.0), cell=1.0)
+        p = _host_plan(slp, w.V, w.T, q=3, grid=(512, 128, 16))
+    try:
+        info = slp.slp_query(p)
+        Lx, Ly, Lz = info["grid"]
+        m = info["m"]
+        iv = slp.slp_debug_host_array(p, slp.SLP_HOST_PLANE_ROWS).reshape(Lz, 2)
+        z0, nz = slp.slp_debug_host_array(p, slp.SLP_HOST_ACTIVE_Z)
+        assert np.all(iv[:, 0] % 2 == 0) and np.all(iv[:, 1] % 2 == 0)
+        assert np.all((iv[:, 1] >= 0) & (iv[:, 1] <= Ly))
+        active = np.zeros((Lz, Ly), bool)
+        for z in range(Lz):
+            if _in_cyclic(z, z0, nz, Lz):
+                y = np.arange(Ly)
+                active[z] = _in_cyclic(y, iv[z, 0], iv[z, 1], Ly)
+            else:
+                assert iv[z, 1] == 0
+        assert info["active_rows"] == active.sum()
+        need = np.zeros((Lz, Ly), bool)
+        for which in (slp.SLP_HOST_SRC_GRID, slp.SLP_HOST_TGT_GRID):
+            g = slp.slp_debug_host_array(p, which).reshape(-1, 4)
+            pk = g[:, 3].astype(np.int64)
+            cy, cz = (pk >> 10) & 1023, (pk >> 20) & 1023
+            cells = np.unique(cz * Ly + cy)
+            for oz in range(-m + 1, m + 1):
+                for oy in range(-m + 1, m + 1):
+                    need[((cells // Ly) + oz) % Lz, ((cells % Ly) + oy) % Ly] = True
+        assert np.all(active[need]), "an active window row is pruned"
+        assert active.sum() < 0.5 * Lz * Ly
+    finally:
+        slp.slp_destroy(p)
