@@ -104,7 +104,10 @@ typedef struct {
                              slp_eval returns SLP_ERR_NO_DEVICE) */
     int allow_grid_raise; /* 1: raise a grid that cannot meet the tolerance (else error) */
     int check_mesh;       /* 1: require a closed, consistently and outward oriented surface */
-    int reserved[7];
+    int fuse_plane_passes; /* x and y FFT passes fused per z plane (one block per plane, the plane
+                              spectrum in shared memory): 0 off, 1 on where the plane fits,
+                              -1 automatic (on when there are at least two active planes per SM) */
+    int reserved[6];
 } slp_plan_opts;
 
 typedef struct {
@@ -135,6 +138,8 @@ typedef struct {
     int launches_per_eval;       /* kernels launched by one slp_eval */
     int64_t active_rows;         /* grid rows (z, y) the FFT passes transform along x: those within
                                     the window of some source or target, widened to row pairs */
+    int active_planes;           /* z planes the FFT passes along y work on */
+    int fused_plane_passes;      /* 1: the x and y passes run fused, one block per active plane */
 } slp_info;
 
 /* Fill opts with defaults: precision 32, automatic grid/m/kernel/near mode,

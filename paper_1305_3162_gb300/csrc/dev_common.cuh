@@ -99,6 +99,32 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Programmatic dependent launch (sm_90 and later).  Every evaluation kernel
+// calls pdl_trigger() first, so the next kernel of the stream may be
+// scheduled while this one runs, and pdl_wait() before it reads or writes
+// any global memory other than plan constants: the wait returns once the
+// previous kernel of the stream has completed and its writes are visible
+// (immediately when the kernel was launched without the attribute).
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch with programmatic stream serialization allowed (see pdl_wait).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                            Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // error codes written to the plan's status word
 enum { DEV_ERR_NONE = 0, DEV_ERR_BAD_ITEM = 1, DEV_ERR_BAD_INDEX = 2 };
 

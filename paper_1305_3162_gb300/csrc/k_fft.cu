@@ -156,6 +156,8 @@ __device__ C *fft_columns(C *b0, C *b1, int L, int ld, int B, const C *__restric
 // PB row pairs per CTA; pair pr covers rows y0 = 2*(pr % (Ly/2)) and y0+1 of plane z.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
+    pdl_trigger();
+    pdl_wait();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx;
@@ -224,6 +226,8 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
 // CTA: plane z, columns kx0 .. kx0 + B.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
+    pdl_trigger();
+    pdl_wait();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
@@ -264,6 +268,8 @@ __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
 // CTA: row ky', columns kx0 .. kx0 + B; the pencil along z stays in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
+    pdl_trigger();
+    pdl_wait();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lz = p.L[2], Kx = p.Kx, ny = p.n[1], nz = p.n[2];
@@ -320,6 +326,8 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
 // ---------------------------------------------------------------- IY
 template <typename T>
 __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
+    pdl_trigger();
+    pdl_wait();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
@@ -358,6 +366,8 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
 // ---------------------------------------------------------------- IX
 template <typename T>
 __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
+    pdl_trigger();
+    pdl_wait();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx;
@@ -426,6 +436,173 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
     }
 }
 
+// ---------------------------------------------------------------- fused plane passes
+// For planes that fit in shared memory, FX + FY and IY + IX run as one block
+// per active z plane: the plane's active row pairs are transformed along x
+// into the plane spectrum P[y][kx] in shared memory, which is then
+// transformed along y (and the reverse for the inverse).  This removes the
+// S1 round trip and two launches.
+//   x buffers X0, X1: [Lx][PB + 1] (PB >= the plane's active pairs)
+//   plane buffer P: [Ly][Kx + 1]; its ping-pong buffer Y1 aliases the x
+//   buffers where they are large enough (FXY), and the inverse x transform's
+//   ping-pong buffer aliases whichever plane buffer is free (IYX).
+struct FusedLayout {
+    int xb, pb;           // complex elements of one x buffer and of one plane buffer
+    int fxy_y1, fxy_total;  // FXY: offset of Y1, total elements
+    int iyx_x0, iyx_x1, iyx_total;  // IYX: offsets of X0 and X1 (-1: alias the free plane buffer)
+};
+static FusedLayout fused_layout(const DevPlan &p, int PB) {
+    FusedLayout f;
+    f.xb = p.L[0] * (PB + 1);
+    f.pb = p.L[1] * (p.Kx + 1);
+    // FXY: X0 | X1 | P [| Y1]
+    f.fxy_y1 = 2 * f.xb >= f.pb ? 0 : 2 * f.xb + f.pb;
+    f.fxy_total = 2 * f.xb + f.pb + (2 * f.xb >= f.pb ? 0 : f.pb);
+    // IYX: P | Y1 | X0 [| X1]
+    f.iyx_x0 = 2 * f.pb;
+    f.iyx_x1 = f.pb >= f.xb ? -1 : 2 * f.pb + f.xb;
+    f.iyx_total = 2 * f.pb + f.xb + (f.pb >= f.xb ? 0 : f.xb);
+    return f;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_fxy(DevPlan p, int PB, int y1_off) {
+    pdl_trigger();
+    pdl_wait();
+    typedef typename VecT<T>::T2 C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
+    const int ldx = PB + 1, ldp = Kx + 1;
+    const int lgKx = __ffs(Kx) - 1, lgPB = __ffs(PB) - 1;
+    C *X0 = (C *)smem_raw;
+    C *X1 = X0 + Lx * ldx;
+    C *P = X1 + Lx * ldx;
+    C *Y1 = (C *)smem_raw + y1_off;
+    const int z = (p.z0 + (int)blockIdx.x) & (p.L[2] - 1);
+    const int2 iv = p.plane_iv[z];
+    const int npr = iv.y >> 1;
+    T *A = (T *)p.gridA + (int64_t)z * Ly * Lx;
+    typedef typename VecW<T>::V V;
+    constexpr int VW = VecW<T>::W;
+    const int nv = Lx / VW, lgnv = __ffs(nv) - 1;
+    for (int i = threadIdx.x; i < Ly * ldp; i += blockDim.x) P[i] = cmk(T(0), T(0));
+    // pair j: rows ya, ya + 1 -> column j of X0 (real and imaginary parts)
+    for (int i = threadIdx.x; i < (PB << lgnv); i += blockDim.x) {
+        const int j = i >> lgnv, xv = i & (nv - 1);
+        T ra[VW], rb[VW];
+        if (j < npr) {
+            const int ya = (iv.x + 2 * j) & (Ly - 1);
+            VecW<T>::split(((const V *)(A + (int64_t)ya * Lx))[xv], ra);
+            VecW<T>::split(((const V *)(A + (int64_t)(ya + 1) * Lx))[xv], rb);
+        } else {
+#pragma unroll
+            for (int e = 0; e < VW; ++e) ra[e] = rb[e] = T(0);
+        }
+#pragma unroll
+        for (int e = 0; e < VW; ++e) X0[(xv * VW + e) * ldx + j] = cmk(ra[e], rb[e]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (npr << lgnv); i += blockDim.x) {
+        const int j = i >> lgnv, xv = i & (nv - 1);
+        const int ya = (iv.x + 2 * j) & (Ly - 1);
+        ((V *)(A + (int64_t)ya * Lx))[xv] = VecW<T>::zero();
+        ((V *)(A + (int64_t)(ya + 1) * Lx))[xv] = VecW<T>::zero();
+    }
+    const C *res = fft_columns<C, false>(X0, X1, Lx, ldx, PB, (const C *)p.tw[0]);
+    for (int i = threadIdx.x; i < (npr << lgKx); i += blockDim.x) {
+        const int j = i >> lgKx, k = i & (Kx - 1);
+        const int ya = (iv.x + 2 * j) & (Ly - 1);
+        const C Z = res[k * ldx + j];
+        const C Zc = cconj(res[((Lx - k) & (Lx - 1)) * ldx + j]);
+        P[ya * ldp + k] = cscale(cadd(Z, Zc), T(0.5));
+        P[(ya + 1) * ldp + k] = cscale(cmul_mi(csub(Z, Zc)), T(0.5));
+    }
+    __syncthreads();
+    const C *r2 = fft_columns<C, false>(P, Y1, Ly, ldp, Kx, (const C *)p.tw[1]);
+    C *S2 = (C *)p.S2 + (int64_t)z * ny * Kx;
+    for (int i = threadIdx.x; i < ny * Kx; i += blockDim.x) {
+        const int kp = i >> lgKx, k = i & (Kx - 1);
+        C v = cmk(T(0), T(0));
+        if (kp < ny / 2)
+            v = r2[kp * ldp + k];
+        else if (kp > ny / 2)
+            v = r2[(Ly - ny + kp) * ldp + k];
+        S2[(int64_t)kp * Kx + k] = v;
+    }
+    (void)lgPB;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_iyx(DevPlan p, int PB, int x0_off, int x1_off) {
+    pdl_trigger();
+    pdl_wait();
+    typedef typename VecT<T>::T2 C;
+    typedef typename VecT<T>::T4 T4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
+    const int ldx = PB + 1, ldp = Kx + 1;
+    const int lgKx = __ffs(Kx) - 1, lgLx = __ffs(Lx) - 1;
+    C *P = (C *)smem_raw;
+    C *Y1 = P + Ly * ldp;
+    C *X0 = (C *)smem_raw + x0_off;
+    const int z = (p.z0 + (int)blockIdx.x) & (p.L[2] - 1);
+    const int2 iv = p.plane_iv[z];
+    const int npr = iv.y >> 1;
+    if (npr == 0) return;
+    // plane spectrum, zero padded along y: position y holds mode y (y < ny/2)
+    // or mode y - Ly (y > Ly - ny/2)
+    const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx;
+    pipelined_copy<C>(
+        Ly * Kx,
+        [&](int i) {
+            const int y = i >> lgKx, k = i & (Kx - 1);
+            C v = cmk(T(0), T(0));
+            if (y < ny / 2)
+                v = S2[(int64_t)y * Kx + k];
+            else if (y > Ly - ny / 2)
+                v = S2[(int64_t)(y - Ly + ny) * Kx + k];
+            return v;
+        },
+        [&](int i, C v) { P[(i >> lgKx) * ldp + (i & (Kx - 1))] = v; });
+    for (int i = threadIdx.x; i < Lx * ldx; i += blockDim.x) X0[i] = cmk(T(0), T(0));
+    __syncthreads();
+    const C *R = fft_columns<C, true>(P, Y1, Ly, ldp, Kx, (const C *)p.tw[1]);
+    C *X1 = x1_off >= 0 ? (C *)smem_raw + x1_off : (R == P ? Y1 : P);
+    // pair j: rows ya (real part) and ya + 1 (imaginary part) of one inverse x transform
+    for (int i = threadIdx.x; i < (npr << lgKx); i += blockDim.x) {
+        const int j = i >> lgKx, k = i & (Kx - 1);
+        const int ya = (iv.x + 2 * j) & (Ly - 1);
+        const C xa = R[ya * ldp + k], xb = R[(ya + 1) * ldp + k];
+        if (k == 0) {
+            X0[j] = cmk(xa.x, xb.x);
+        } else {
+            X0[k * ldx + j] = cmk(xa.x - xb.y, xa.y + xb.x);          // xa + i xb
+            X0[(Lx - k) * ldx + j] = cmk(xa.x + xb.y, xb.x - xa.y);   // conj(xa) + i conj(xb)
+        }
+    }
+    __syncthreads();
+    const C *res = fft_columns<C, true>(X0, X1, Lx, ldx, PB, (const C *)p.tw[0]);
+    T *G = (T *)p.gridB + (int64_t)z * Ly * Lx;
+    typedef typename VecW<T>::V V;
+    constexpr int VW = VecW<T>::W;
+    const int nv = Lx / VW, lgnv = __ffs(nv) - 1;
+    for (int i = threadIdx.x; i < (npr << lgnv); i += blockDim.x) {
+        const int j = i >> lgnv, xv = i & (nv - 1);
+        const int ya = (iv.x + 2 * j) & (Ly - 1);
+        T ra[VW], rb[VW];
+#pragma unroll
+        for (int e = 0; e < VW; ++e) {
+            const C v = res[(xv * VW + e) * ldx + j];
+            ra[e] = v.x;
+            rb[e] = v.y;
+        }
+        ((V *)(G + (int64_t)ya * Lx))[xv] = VecW<T>::join(ra);
+        ((V *)(G + (int64_t)(ya + 1) * Lx))[xv] = VecW<T>::join(rb);
+    }
+    (void)lgLx;
+    (void)sizeof(T4);
+}
+
 // ---------------------------------------------------------------- launchers
 // Batch sizes: at most 8 transforms per block (more blocks for the small
 // grids, where the passes are latency-bound), two buffers of (L x (B+1))
@@ -454,7 +631,7 @@ template <typename T> static cudaError_t fx_t(const DevPlan &p, cudaStream_t s) 
     cudaError_t e = prep(k_fx<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.n_row_pairs == 0) return cudaSuccess;
-    k_fx<T><<<(p.n_row_pairs + PB - 1) / PB, 256, sm, s>>>(p, PB);
+    { const cudaError_t le = launch_k(k_fx<T>, (p.n_row_pairs + PB - 1) / PB, 256, sm, s, p, PB); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) {
@@ -464,7 +641,7 @@ template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) 
     cudaError_t e = prep(k_ix<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.n_row_pairs == 0) return cudaSuccess;
-    k_ix<T><<<(p.n_row_pairs + PB - 1) / PB, 256, sm, s>>>(p, PB);
+    { const cudaError_t le = launch_k(k_ix<T>, (p.n_row_pairs + PB - 1) / PB, 256, sm, s, p, PB); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) {
@@ -474,7 +651,7 @@ template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) 
     cudaError_t e = prep(k_fy<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
-    k_fy<T><<<p.nz_act * (p.Kx / B), 256, sm, s>>>(p, B);
+    { const cudaError_t le = launch_k(k_fy<T>, p.nz_act * (p.Kx / B), 256, sm, s, p, B); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) {
@@ -484,7 +661,7 @@ template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) 
     cudaError_t e = prep(k_iy<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
-    k_iy<T><<<p.nz_act * (p.Kx / B), 256, sm, s>>>(p, B);
+    { const cudaError_t le = launch_k(k_iy<T>, p.nz_act * (p.Kx / B), 256, sm, s, p, B); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t fz_t(const DevPlan &p, cudaStream_t s) {
@@ -494,9 +671,36 @@ template <typename T> static cudaError_t fz_t(const DevPlan &p, cudaStream_t s) 
     cudaError_t e = prep(k_fz<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
-    k_fz<T><<<p.n[1] * (p.Kx / B), 256, sm, s>>>(p, B);
+    { const cudaError_t le = launch_k(k_fz<T>, p.n[1] * (p.Kx / B), 256, sm, s, p, B); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
+
+template <typename T> static cudaError_t fxy_t(const DevPlan &p, cudaStream_t s) {
+    const FusedLayout f = fused_layout(p, p.fuse_pb);
+    const size_t sm = (size_t)f.fxy_total * 2 * sizeof(T);
+    cudaError_t e = prep(k_fxy<T>, sm);
+    if (e != cudaSuccess) return e;
+    if (p.nz_act == 0) return cudaSuccess;
+    { const cudaError_t le = launch_k(k_fxy<T>, p.nz_act, 512, sm, s, p, p.fuse_pb, f.fxy_y1); if (le != cudaSuccess) return le; }
+    return cudaGetLastError();
+}
+template <typename T> static cudaError_t iyx_t(const DevPlan &p, cudaStream_t s) {
+    const FusedLayout f = fused_layout(p, p.fuse_pb);
+    const size_t sm = (size_t)f.iyx_total * 2 * sizeof(T);
+    cudaError_t e = prep(k_iyx<T>, sm);
+    if (e != cudaSuccess) return e;
+    if (p.nz_act == 0) return cudaSuccess;
+    { const cudaError_t le = launch_k(k_iyx<T>, p.nz_act, 512, sm, s, p, p.fuse_pb, f.iyx_x0, f.iyx_x1); if (le != cudaSuccess) return le; }
+    return cudaGetLastError();
+}
+
+size_t fused_plane_smem(const DevPlan &p, int PB) {
+    const FusedLayout f = fused_layout(p, PB);
+    const size_t ce = 2 * (p.prec == 64 ? sizeof(double) : sizeof(float));
+    return (size_t)(f.fxy_total > f.iyx_total ? f.fxy_total : f.iyx_total) * ce;
+}
+cudaError_t launch_fft_forward_xy(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? fxy_t<double>(p, s) : fxy_t<float>(p, s); }
+cudaError_t launch_fft_inverse_yx(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? iyx_t<double>(p, s) : iyx_t<float>(p, s); }
 
 cudaError_t launch_fft_forward_x(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? fx_t<double>(p, s) : fx_t<float>(p, s); }
 cudaError_t launch_fft_forward_y(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? fy_t<double>(p, s) : fy_t<float>(p, s); }

@@ -21,6 +21,8 @@ namespace slp {
 // precomputed near-field product reads it coalesced.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nodal_prep(DevPlan p, const T *__restrict__ in) {
+    pdl_trigger();
+    pdl_wait();
     typedef typename VecT<T>::T4 T4;
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= p.N) return;
@@ -64,6 +66,8 @@ __device__ __forceinline__ T source_charge(const DevPlan &p, int64_t k, int kind
 // qbuf[k] = w_k * sigma_k in sorted source order.
 template <typename T>
 __global__ void __launch_bounds__(256) k_charges(DevPlan p, int kind, const T *__restrict__ in) {
+    pdl_trigger();
+    pdl_wait();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.Q) return;
     ((T *)p.qbuf)[k] = source_charge<T>(p, k, kind, in);
@@ -128,6 +132,8 @@ __device__ __forceinline__ void window_values(double *wv, double fx, double fy, 
 // the row does not wrap around the periodic grid.
 template <typename T, int M, int TS>
 __global__ void __launch_bounds__(256) k_spread(DevPlan p, int fused_kind, const T *__restrict__ in) {
+    pdl_trigger();
+    pdl_wait();
     typedef typename VecT<T>::T4 T4;
     typedef TileGeom<M, TS> G;
     constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO, XE = G::XE;
@@ -247,7 +253,11 @@ __global__ void __launch_bounds__(256) k_spread(DevPlan p, int fused_kind, const
 //   * accumulation: lanes map to (x offset ix, z offset izs); a lane holds
 //     the box column (ix, iz = izs + ZL h, all iy) as H x W accumulators.  The
 //     plane stride is congruent to W modulo 32, so the 8 x 4 lanes of a row
-//     update hit 32 different banks.
+//     update hit 32 different banks;
+//   * the tile: FP32 keeps one tile per block, updated with shared-memory
+//     atomic adds (the order of the adds, like that of the global adds below,
+//     is not fixed); FP64 keeps one private tile per warp (plain
+//     read-modify-writes, warp copies summed in a fixed order).
 template <int M, int TS> struct TileGeomG {
     static constexpr int W = 2 * M;
     static constexpr int TE = TS + W - 1;
@@ -285,39 +295,41 @@ template <int WP> __device__ __forceinline__ void load_row(const double *src, do
 
 template <typename T, int M, int TS> struct SpreadSmem {
     typedef TileGeomG<M, TS> G;
+    static constexpr bool SHARED_ATOMIC = sizeof(T) == 4;
     static constexpr int AX = SPREAD_GMAX * G::WP;  // window values of one axis of one warp
+    __host__ __device__ static int copies(int nwarps) { return SHARED_ATOMIC ? 1 : nwarps; }
     // offsets in elements of T: tiles, window values (16-byte aligned), sources
-    __host__ __device__ static size_t wv(int nwarps) { return ((size_t)nwarps * G::SIZE + 3) & ~(size_t)3; }
+    __host__ __device__ static size_t wv(int nwarps) { return ((size_t)copies(nwarps) * G::SIZE + 3) & ~(size_t)3; }
     __host__ __device__ static size_t head(int nwarps) { return (wv(nwarps) + (size_t)nwarps * 3 * AX + 3) & ~(size_t)3; }
     __host__ __device__ static size_t bytes(int nwarps, int chunk) { return head(nwarps) * sizeof(T) + (size_t)chunk * 5 * sizeof(T); }
 };
 
 template <typename T, int M, int TS>
 __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind, const T *__restrict__ in) {
+    pdl_trigger();
     typedef typename VecT<T>::T4 T4;
     typedef TileGeomG<M, TS> G;
     typedef SpreadSmem<T, M, TS> SM;
     constexpr int W = G::W, TS_ = TS, RS = G::RS, PS = G::PS, XO = G::XO, ZL = G::ZL, H = G::H, WP = G::WP;
     constexpr int AX = SM::AX;
+    static_assert(3 * W <= 32, "one lane per window point and axis");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     T *tiles = (T *)smem_raw;
     T *wv = tiles + SM::wv(nwarps) + (size_t)warp * 3 * AX;
     T4 *sg = (T4 *)(tiles + SM::head(nwarps));
     T *sq = (T *)(sg + p.spread_chunk);
-    T *my = tiles + warp * G::SIZE;
+    constexpr bool SA = SM::SHARED_ATOMIC;
+    const int ncopies = SM::copies(nwarps);
+    T *my = tiles + (SA ? 0 : warp * G::SIZE);
 
     const TileItem it = p.spread_items[blockIdx.x];
     const int nsrc = it.end - it.begin;
     {
-        const T4 *src = (const T4 *)p.src_grid + it.begin;
-        const T *qb = (const T *)p.qbuf + it.begin;
-        for (int i = threadIdx.x; i < nsrc; i += blockDim.x) {
-            sg[i] = src[i];
-            sq[i] = fused_kind >= 0 ? source_charge<T>(p, it.begin + i, fused_kind, in) : qb[i];
-        }
+        // the tile copies (and the padding up to the window values), 16 bytes per store
+        const int n4 = (int)(SM::wv(nwarps) * sizeof(T) / 16);
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) ((float4 *)tiles)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    for (int i = threadIdx.x; i < nwarps * G::SIZE; i += blockDim.x) tiles[i] = T(0);
 
     // lane (wax, wi) evaluates window point wi along axis wax
     const int wax = lane / W, wi = lane - wax * W;
@@ -331,6 +343,16 @@ __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind
     }
     const T inv_m = T(1) / T(M);
     const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
+    // charges and grid A may be the previous kernel's output
+    pdl_wait();
+    {
+        const T4 *src = (const T4 *)p.src_grid + it.begin;
+        const T *qb = (const T *)p.qbuf + it.begin;
+        for (int i = threadIdx.x; i < nsrc; i += blockDim.x) {
+            sg[i] = src[i];
+            sq[i] = fused_kind >= 0 ? source_charge<T>(p, it.begin + i, fused_kind, in) : qb[i];
+        }
+    }
     __syncthreads();
 
     const int ix = lane % W, izs = lane / W;
@@ -396,7 +418,10 @@ __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind
 #pragma unroll
                     for (int iy = 0; iy < W; ++iy) {
                         T *a = base + iz * PS + iy * RS;
-                        *a = *a + acc[h][iy];
+                        if constexpr (SA)
+                            atomicAdd(a, acc[h][iy]);
+                        else
+                            *a = *a + acc[h][iy];
                     }
                 }
             }
@@ -417,10 +442,24 @@ __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind
             const int v = i % NV, r = i / NV;
             const int iy = r % TE, iz = r / TE;
             float a[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int w = 0; w < nwarps; ++w) {
-                const T *t = tiles + w * G::SIZE + iz * PS + iy * RS + 4 * v;
+            for (int w = 0; w < ncopies; ++w) {
+                const float *t = (const float *)tiles + w * G::SIZE + iz * PS + iy * RS + 4 * v;
+                if constexpr (PS % 4 == 0 && G::SIZE % 4 == 0) {
+                    const float4 f = *(const float4 *)t;
+                    a[0] += f.x;
+                    a[1] += f.y;
+                    a[2] += f.z;
+                    a[3] += f.w;
+                } else if constexpr (PS % 2 == 0 && G::SIZE % 2 == 0) {
+                    const float2 f0 = *(const float2 *)t, f1 = *(const float2 *)(t + 2);
+                    a[0] += f0.x;
+                    a[1] += f0.y;
+                    a[2] += f1.x;
+                    a[3] += f1.y;
+                } else {
 #pragma unroll
-                for (int e = 0; e < 4; ++e) a[e] += (float)t[e];
+                    for (int e = 0; e < 4; ++e) a[e] += t[e];
+                }
             }
             if (a[0] == 0.f && a[1] == 0.f && a[2] == 0.f && a[3] == 0.f) continue;
             const int gy = (gy0 + iy) & (Ly - 1), gz = (gz0 + iz) & (Lz - 1);
@@ -432,7 +471,7 @@ __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind
             const int x = i % XE, r = i / XE;
             const int iy = r % TE, iz = r / TE;
             T v = T(0);
-            for (int w = 0; w < nwarps; ++w) v += tiles[w * G::SIZE + iz * PS + iy * RS + x];
+            for (int w = 0; w < ncopies; ++w) v += tiles[w * G::SIZE + iz * PS + iy * RS + x];
             if (v == T(0)) continue;
             const int gx = (gxs + x) & (Lx - 1);
             const int gy = (gy0 + iy) & (Ly - 1), gz = (gz0 + iz) & (Lz - 1);
@@ -451,6 +490,8 @@ constexpr int GATHER_CHUNK = 32;  // targets per gather item (set by the plan)
 
 template <typename T, int M, int TS>
 __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) {
+    pdl_trigger();
+    pdl_wait();
     typedef typename VecT<T>::T4 T4;
     typedef TileGeom<M, TS> G;
     constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO;
@@ -458,9 +499,7 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
     T *tile = (T *)smem_raw;
-    T *coef = tile + G::SIZE;
-    const int ncoef = W * (WDEG + 1);
-    T *wv = coef + ((ncoef + 3) & ~3);  // [GATHER_CHUNK][3W]
+    T *wv = tile + ((G::SIZE + 3) & ~3);  // [GATHER_CHUNK][3W]
     T *sf = wv + GATHER_CHUNK * GW;     // [3][GATHER_CHUNK] fractions
     T *sphi = sf + 3 * GATHER_CHUNK;    // [GATHER_CHUNK] near-field parts
     int *sidx = (int *)(sphi + GATHER_CHUNK);  // [2][GATHER_CHUNK] packed cell, output index
@@ -484,41 +523,74 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
         sidx[GATHER_CHUNK + threadIdx.x] = p.tgt_perm[t];
         sphi[threadIdx.x] = ((const T *)p.phi_part)[t];
     }
-    if (sizeof(T) == 4)
-        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) coef[i] = ((const T *)p.wcoef)[i];
-    pipelined_copy<T>(
-        TE * TE * TE,
-        [&](int i) {
-            const int x = i % TE, r = i / TE;
-            const int gx = (gx0 + x) & (Lx - 1);
-            const int gy = (gy0 + r % TE) & (Ly - 1);
-            const int gz = (gz0 + r / TE) & (Lz - 1);
-            return grid[((int64_t)gz * Ly + gy) * Lx + gx];
-        },
-        [&](int i, T v) {
-            const int x = i % TE, r = i / TE;
-            tile[(r / TE) * PS + (r % TE) * RS + x + XO] = v;
-        });
-    __syncthreads();
-
-    // window values of every target of the item: wv[t * 3W + axis * W + i]
-    const T inv_m = T(1) / T(M);
-    const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
-    for (int j = threadIdx.x; j < nt * GW; j += blockDim.x) {
-        const int t = j / GW, r = j - t * GW;
-        const int ax = r / W, i = r - ax * W;
-        const T f = sf[ax * GATHER_CHUNK + t];
-        if (sizeof(T) == 4) {
-            const T *c = coef + i * (WDEG + 1);
-            T v = c[WDEG];
-#pragma unroll
-            for (int k = WDEG - 1; k >= 0; --k) v = v * f + c[k];
-            wv[j] = v;
-        } else {
-            wv[j] = kb_window(f + T(M - 1 - i), inv_m, beta, isb);
-        }
+    constexpr int XE = G::XE;
+    const int gxs = gx0 - XO;  // a multiple of 4 when TS is
+    if (sizeof(T) == 4 && TS % 4 == 0 && gxs >= 0 && gxs + XE <= Lx) {
+        // rows of XE/4 aligned 16-byte vectors (the tile's x extent widened to XE)
+        constexpr int NV = XE / 4;
+        pipelined_copy<float4>(
+            TE * TE * NV,
+            [&](int i) {
+                const int v = i % NV, r = i / NV;
+                const int gy = (gy0 + r % TE) & (Ly - 1);
+                const int gz = (gz0 + r / TE) & (Lz - 1);
+                return ((const float4 *)((const float *)grid + ((int64_t)gz * Ly + gy) * Lx + gxs))[v];
+            },
+            [&](int i, float4 v) {
+                const int vv = i % NV, r = i / NV;
+                float *d = (float *)tile + (r / TE) * PS + (r % TE) * RS + 4 * vv;
+                d[0] = v.x;
+                d[1] = v.y;
+                d[2] = v.z;
+                d[3] = v.w;
+            });
+    } else {
+        pipelined_copy<T>(
+            TE * TE * TE,
+            [&](int i) {
+                const int x = i % TE, r = i / TE;
+                const int gx = (gx0 + x) & (Lx - 1);
+                const int gy = (gy0 + r % TE) & (Ly - 1);
+                const int gz = (gz0 + r / TE) & (Lz - 1);
+                return grid[((int64_t)gz * Ly + gy) * Lx + gx];
+            },
+            [&](int i, T v) {
+                const int x = i % TE, r = i / TE;
+                tile[(r / TE) * PS + (r % TE) * RS + x + XO] = v;
+            });
     }
     __syncthreads();
+
+    // window values of the warp's targets, wv[t * 3W + axis * W + i]: lane
+    // j = (wax, wi) evaluates point wi along axis wax (FP32: the interval
+    // polynomial, coefficients in registers), and point j + 32 where 3W > 32
+    const T inv_m = T(1) / T(M);
+    const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
+#pragma unroll
+    for (int j0 = 0; j0 < GW; j0 += 32) {
+        const int j = j0 + lane;
+        if (j < GW) {
+            const int wax = j / W, wi = j - wax * W;
+            T cf[WDEG + 1];
+            if (sizeof(T) == 4) {
+#pragma unroll
+                for (int k = 0; k <= WDEG; ++k) cf[k] = ((const T *)p.wcoef)[wi * (WDEG + 1) + k];
+            }
+            for (int t = warp; t < nt; t += nwarps) {
+                const T f = sf[wax * GATHER_CHUNK + t];
+                T v;
+                if (sizeof(T) == 4) {
+                    v = cf[WDEG];
+#pragma unroll
+                    for (int k = WDEG - 1; k >= 0; --k) v = v * f + cf[k];
+                } else {
+                    v = kb_window(f + T(M - 1 - wi), inv_m, beta, isb);
+                }
+                wv[t * GW + j] = v;
+            }
+        }
+    }
+    __syncwarp();
 
     for (int t = warp; t < nt; t += nwarps) {
         int cx, cy, cz;
@@ -550,6 +622,8 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
 
 // ---------------------------------------------------------------- zero
 __global__ void k_zero4(float4 *p, int64_t n4) {
+    pdl_trigger();
+    pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
@@ -574,7 +648,7 @@ static cudaError_t spread_mt(const DevPlan &p, int fused_kind, const void *in, c
             if (e != cudaSuccess) return e;
         }
         if (p.n_spread > 0)
-            k_spread_groups<T, M, TS><<<p.n_spread, 32 * nw, sm, s>>>(p, fused_kind, (const T *)in);
+            { const cudaError_t le = launch_k(k_spread_groups<T, M, TS>, p.n_spread, 32 * nw, sm, s, p, fused_kind, (const T *)in); if (le != cudaSuccess) return le; }
         return cudaGetLastError();
     }
     int nw = 8;
@@ -584,20 +658,19 @@ static cudaError_t spread_mt(const DevPlan &p, int fused_kind, const void *in, c
         cudaError_t e = cudaFuncSetAttribute(k_spread<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    if (p.n_spread > 0) k_spread<T, M, TS><<<p.n_spread, 32 * nw, sm, s>>>(p, fused_kind, (const T *)in);
+    if (p.n_spread > 0) { const cudaError_t le = launch_k(k_spread<T, M, TS>, p.n_spread, 32 * nw, sm, s, p, fused_kind, (const T *)in); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
 template <typename T, int M, int TS> static cudaError_t gather_mt(const DevPlan &p, void *phi, cudaStream_t s) {
     typedef TileGeom<M, TS> G;
-    const int ncoef = 2 * M * (WDEG + 1);
-    const size_t sm = ((size_t)G::SIZE + ((ncoef + 3) & ~3) + GATHER_CHUNK * (3 * 2 * M + 4)) * sizeof(T) +
+    const size_t sm = ((size_t)((G::SIZE + 3) & ~3) + GATHER_CHUNK * (3 * 2 * M + 4)) * sizeof(T) +
                       2 * GATHER_CHUNK * sizeof(int);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_gather<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    if (p.n_gather > 0) k_gather<T, M, TS><<<p.n_gather, 256, sm, s>>>(p, (T *)phi);
+    if (p.n_gather > 0) { const cudaError_t le = launch_k(k_gather<T, M, TS>, p.n_gather, 256, sm, s, p, (T *)phi); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -645,9 +718,9 @@ cudaError_t launch_nodal_prep(const DevPlan &p, const void *d_in, cudaStream_t s
     if (p.N == 0) return cudaSuccess;
     const int nb = (int)((p.N + 255) / 256);
     if (p.prec == 64)
-        k_nodal_prep<double><<<nb, 256, 0, s>>>(p, (const double *)d_in);
+        { const cudaError_t le = launch_k(k_nodal_prep<double>, nb, 256, 0, s, p, (const double *)d_in); if (le != cudaSuccess) return le; }
     else
-        k_nodal_prep<float><<<nb, 256, 0, s>>>(p, (const float *)d_in);
+        { const cudaError_t le = launch_k(k_nodal_prep<float>, nb, 256, 0, s, p, (const float *)d_in); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -655,9 +728,9 @@ cudaError_t launch_charges(const DevPlan &p, int kind, const void *d_in, cudaStr
     if (p.Q == 0) return cudaSuccess;
     const int nb = (int)((p.Q + 255) / 256);
     if (p.prec == 64)
-        k_charges<double><<<nb, 256, 0, s>>>(p, kind, (const double *)d_in);
+        { const cudaError_t le = launch_k(k_charges<double>, nb, 256, 0, s, p, kind, (const double *)d_in); if (le != cudaSuccess) return le; }
     else
-        k_charges<float><<<nb, 256, 0, s>>>(p, kind, (const float *)d_in);
+        { const cudaError_t le = launch_k(k_charges<float>, nb, 256, 0, s, p, kind, (const float *)d_in); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -667,7 +740,7 @@ cudaError_t launch_zero(void *ptr, size_t bytes, cudaStream_t s) {
     if (n4 == 0) return cudaSuccess;
     int nb = (int)((n4 + 255) / 256);
     if (nb > 152 * 16) nb = 152 * 16;
-    k_zero4<<<nb, 256, 0, s>>>((float4 *)ptr, n4);
+    { const cudaError_t le = launch_k(k_zero4, nb, 256, 0, s, (float4 *)ptr, n4); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 

@@ -40,6 +40,8 @@ template <typename T> __device__ __forceinline__ T sep_factor(const T *__restric
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(NEAR_WARPS * 32) k_near(DevPlan p) {
+    pdl_trigger();
+    pdl_wait();
     typedef typename VecT<T>::T4 T4;
     __shared__ T4 sg[NEAR_WARPS][32];
     __shared__ T sq[NEAR_WARPS][32];
@@ -113,6 +115,8 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) k_near(DevPlan p) {
 // partials in item order.  blk_items[b] = first item of block b (CSR).
 template <typename T>
 __global__ void k_near_reduce(DevPlan p, const int *__restrict__ blk_first, int nblk) {
+    pdl_trigger();
+    pdl_wait();
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= nblk) return;
@@ -128,9 +132,9 @@ template <typename T> static cudaError_t near_t(const DevPlan &p, cudaStream_t s
     if (p.n_near == 0) return cudaSuccess;
     const int nb = (p.n_near + NEAR_WARPS - 1) / NEAR_WARPS;
     if (p.kernel_mode == 2)
-        k_near<T, 2><<<nb, NEAR_WARPS * 32, 0, s>>>(p);
+        { const cudaError_t le = launch_k(k_near<T, 2>, nb, NEAR_WARPS * 32, 0, s, p); if (le != cudaSuccess) return le; }
     else
-        k_near<T, 1><<<nb, NEAR_WARPS * 32, 0, s>>>(p);
+        { const cudaError_t le = launch_k(k_near<T, 1>, nb, NEAR_WARPS * 32, 0, s, p); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -142,9 +146,9 @@ cudaError_t launch_near_reduce(const DevPlan &p, const int *blk_first, int nblk,
     if (nblk == 0) return cudaSuccess;
     const int nb = (nblk + 7) / 8;
     if (p.prec == 64)
-        k_near_reduce<double><<<nb, 256, 0, s>>>(p, blk_first, nblk);
+        { const cudaError_t le = launch_k(k_near_reduce<double>, nb, 256, 0, s, p, blk_first, nblk); if (le != cudaSuccess) return le; }
     else
-        k_near_reduce<float><<<nb, 256, 0, s>>>(p, blk_first, nblk);
+        { const cudaError_t le = launch_k(k_near_reduce<float>, nb, 256, 0, s, p, blk_first, nblk); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -256,6 +260,8 @@ __device__ __forceinline__ double4 ld_stream(const double4 *p) {
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_near_matrix(DevPlan p) {
+    pdl_trigger();
+    pdl_wait();
     typedef typename VecT<T>::T4 T4;
     constexpr int U = 8;  // independent 16-byte loads in flight per lane
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -293,9 +299,9 @@ cudaError_t launch_near_matrix(const DevPlan &p, const void *, cudaStream_t s) {
     if (p.N == 0) return cudaSuccess;
     const unsigned nb = (unsigned)((p.N + 3) / 4);
     if (p.prec == 64)
-        k_near_matrix<double><<<nb, 128, 0, s>>>(p);
+        { const cudaError_t le = launch_k(k_near_matrix<double>, nb, 128, 0, s, p); if (le != cudaSuccess) return le; }
     else
-        k_near_matrix<float><<<nb, 128, 0, s>>>(p);
+        { const cudaError_t le = launch_k(k_near_matrix<float>, nb, 128, 0, s, p); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 

@@ -75,6 +75,7 @@ struct DevPlan {
     const int2 *plane_iv;
     const int *row_pairs;  // [n_row_pairs] z * (Ly / 2) + y / 2
     int n_row_pairs;
+    int fuse_pb;           // > 0: fused plane passes with this many row pairs per plane (a power of two)
 
     const TileItem *spread_items; int n_spread;
     int spread_chunk;             // most sources in one spread item
@@ -106,6 +107,11 @@ cudaError_t launch_fft_forward_y(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_z_multiply(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_inverse_y(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_inverse_x(const DevPlan &p, cudaStream_t s);
+// fused plane passes (FX + FY, IY + IX; one block per active plane, fuse_pb > 0)
+cudaError_t launch_fft_forward_xy(const DevPlan &p, cudaStream_t s);
+cudaError_t launch_fft_inverse_yx(const DevPlan &p, cudaStream_t s);
+// shared memory of the fused plane passes with PB row pairs per plane
+size_t fused_plane_smem(const DevPlan &p, int PB);
 // phi[perm[t]] = far field at t + phi_part[t]
 cudaError_t launch_gather(const DevPlan &p, void *d_phi, cudaStream_t s);
 // near field into phi_part (atomics: phi_part must be zero; deterministic: per-item partials, then the reduction

@@ -941,6 +941,21 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     TRY(upload(p, &ptr, p.row_pairs.data(), p.row_pairs.size()));
     d.row_pairs = (const int *)ptr;
     d.n_row_pairs = (int)p.row_pairs.size();
+    {
+        // fused plane passes when both fit in shared memory
+        int maxp = 0;
+        for (const int2 &v : p.plane_iv) maxp = std::max(maxp, v.y / 2);
+        int PB = 1;
+        while (PB < maxp) PB <<= 1;
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p.device);
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, p.device);
+        const size_t sm = slp::fused_plane_smem(d, PB);
+        const bool fits = maxp > 0 && sm <= std::min<size_t>((size_t)optin, 200 * 1024);
+        const int want = p.opts.fuse_plane_passes;
+        d.fuse_pb = (fits && (want == 1 || (want < 0 && p.nz_act >= 2 * nsm))) ? PB : 0;
+    }
     TRY(upload(p, &ptr, p.spread_items.data(), p.spread_items.size()));
     d.spread_items = (const slp::TileItem *)ptr;
     d.n_spread = (int)p.spread_items.size();
@@ -973,9 +988,10 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     // staging buffers for slp_eval_host
     TRY(dalloc(p, &p.d_stage_in, sizeof(T) * 3 * std::max(p.Q, p.N)));
     TRY(dalloc(p, &p.d_stage_phi, sizeof(T) * p.N));
-    // on-the-fly near field: charges, spread, 5 FFT passes, gather, and either
-    // zeroing + atomic near field or near field + ordered reduction
-    p.launches_per_eval = 10;
+    // on-the-fly near field: charges, spread, 5 FFT passes (3 when the plane
+    // passes are fused), gather, and either zeroing + atomic near field or
+    // near field + ordered reduction
+    p.launches_per_eval = d.fuse_pb > 0 ? 8 : 10;
     return SLP_OK;
 }
 
@@ -1204,7 +1220,8 @@ slp_status build_near_matrix(slp_plan_s &p, const std::vector<uint64_t> &tkeys) 
     p.dp.nm_nnz = nnz;
     p.nm_nnz = nnz;
     p.near_mode = SLP_NEAR_PRECOMPUTED;
-    p.launches_per_eval = 9;  // prep, spread (charges fused), 5 FFT passes, gather, near-field product
+    // prep, spread (charges fused), 5 (fused: 3) FFT passes, gather, near-field product
+    p.launches_per_eval = p.dp.fuse_pb > 0 ? 7 : 9;
     return SLP_OK;
 }
 
@@ -1270,20 +1287,34 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
     TRY(cuda_status(slp::launch_spread(d, fuse ? kind : -1, d_in, s), "spread"));
     rec();
     if (last <= SLP_STAGE_SPREAD) return SLP_OK;
-    TRY(cuda_status(slp::launch_fft_forward_x(d, s), "fft x"));
-    rec();
-    if (last <= SLP_STAGE_FFT_X) return SLP_OK;
-    TRY(cuda_status(slp::launch_fft_forward_y(d, s), "fft y"));
-    rec();
+    // fused plane passes (FX + FY, IY + IX) unless the run stops between them
+    const bool fused = d.fuse_pb > 0;
+    if (fused && last >= SLP_STAGE_FFT_Y) {
+        TRY(cuda_status(slp::launch_fft_forward_xy(d, s), "fft xy"));
+        rec();
+        rec();
+    } else {
+        TRY(cuda_status(slp::launch_fft_forward_x(d, s), "fft x"));
+        rec();
+        if (last <= SLP_STAGE_FFT_X) return SLP_OK;
+        TRY(cuda_status(slp::launch_fft_forward_y(d, s), "fft y"));
+        rec();
+    }
     if (last <= SLP_STAGE_FFT_Y) return SLP_OK;
     TRY(cuda_status(slp::launch_fft_z_multiply(d, s), "fft z"));
     rec();
     if (last <= SLP_STAGE_FFT_Z) return SLP_OK;
-    TRY(cuda_status(slp::launch_fft_inverse_y(d, s), "ifft y"));
-    rec();
-    if (last <= SLP_STAGE_IFFT_Y) return SLP_OK;
-    TRY(cuda_status(slp::launch_fft_inverse_x(d, s), "ifft x"));
-    rec();
+    if (fused && last >= SLP_STAGE_IFFT_X) {
+        TRY(cuda_status(slp::launch_fft_inverse_yx(d, s), "ifft yx"));
+        rec();
+        rec();
+    } else {
+        TRY(cuda_status(slp::launch_fft_inverse_y(d, s), "ifft y"));
+        rec();
+        if (last <= SLP_STAGE_IFFT_Y) return SLP_OK;
+        TRY(cuda_status(slp::launch_fft_inverse_x(d, s), "ifft x"));
+        rec();
+    }
     if (last <= SLP_STAGE_IFFT_X) return SLP_OK;
     if (concurrent) {
         TRY(cuda_status(cudaStreamWaitEvent(s, ex->join, 0), "join wait"));
@@ -1411,6 +1442,7 @@ slp_status slp_default_opts(slp_plan_opts *o) {
     o->device = 0;
     o->allow_grid_raise = 1;
     o->check_mesh = 1;
+    o->fuse_plane_passes = -1;
     return SLP_OK;
 }
 
@@ -1545,6 +1577,8 @@ slp_status slp_query(slp_plan_t p, slp_info *info) {
     info->n_near_items = (int64_t)p->near_items.size();
     info->launches_per_eval = p->launches_per_eval;
     info->active_rows = 2 * (int64_t)p->row_pairs.size();
+    info->active_planes = p->nz_act;
+    info->fused_plane_passes = p->device >= 0 && p->dp.fuse_pb > 0 ? 1 : 0;
     return SLP_OK;
 }
 

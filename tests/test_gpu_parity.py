@@ -57,14 +57,17 @@ def test_input_kinds_sphere_L3(kind, prec, tol):
         slp.slp_destroy(plan)
 
 
-def test_sphere_L5_workload():
-    """Sphere level 5 (20480 triangles), 7-point rule, grid 128^3, FP32, 1e-5."""
+@pytest.mark.parametrize("fuse", [0, 1], ids=["separate", "fused"])
+def test_sphere_L5_workload(fuse):
+    """Sphere level 5 (20480 triangles), 7-point rule, grid 128^3, FP32, 1e-5,
+    with the x and y FFT passes separate and fused per plane."""
     slp = lib()
     w = workloads.sphere()
-    plan = _plan(slp, w.V, w.T, w.quad, w.tolerance, w.precision, w.grid)
+    plan = _plan(slp, w.V, w.T, w.quad, w.tolerance, w.precision, w.grid, fuse_plane_passes=fuse)
     try:
         info = slp.slp_query(plan)
         assert info["grid"] == [128, 128, 128] and not info["grid_raised"]
+        assert info["fused_plane_passes"] == fuse
         phi = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, w.m_nodal, 32)
         ref = oracle.slp_nodal(w.V, w.T, w.quad, w.m_nodal)
         err = rel_l2(phi, ref)

@@ -10,12 +10,13 @@ from tests.gpu_util import lib, rel_l2, run
 pytestmark = pytest.mark.gpu
 
 
-def _plan(slp, V, T, q, tol, prec, grid, kernel_mode=0):
+def _plan(slp, V, T, q, tol, prec, grid, kernel_mode=0, fuse=-1):
     o = slp.slp_default_opts()
     o.precision = prec
     for d in range(3):
         o.grid[d] = grid[d]
     o.kernel_mode = kernel_mode
+    o.fuse_plane_passes = fuse
     return slp.slp_plan(V, T, q, tol, o)
 
 
@@ -28,14 +29,20 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("fuse", [0, 1], ids=["separate", "fused"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
-def test_stages(case):
+def test_stages(case, fuse):
+    """With fused plane passes, the FFT_Y stage runs FX + FY as one kernel
+    (checked against the y transform of the separate FX output) and the
+    IFFT_X stage runs IY + IX as one kernel (checked against the x transform
+    of the separate IY output)."""
     name, mk, q, tol, prec, grid, kmode, rtol = case
     slp = lib()
     V, T = mk()
-    plan = _plan(slp, V, T, q, tol, prec, grid, kmode)
+    plan = _plan(slp, V, T, q, tol, prec, grid, kmode, fuse)
     try:
         info = slp.slp_query(plan)
+        assert info["fused_plane_passes"] == fuse
         L = info["grid"]
         n = info["modes"]
         m = info["m"]
