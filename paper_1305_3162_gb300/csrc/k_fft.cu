@@ -157,7 +157,6 @@ __device__ C *fft_columns(C *b0, C *b1, int L, int ld, int B, const C *__restric
 template <typename T>
 __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     pdl_trigger();
-    pdl_wait();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx;
@@ -165,6 +164,10 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     const int lgLx = __ffs(Lx) - 1, lgKx = __ffs(Kx) - 1, lgHy = __ffs(Ly) - 2;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Lx * ld;
+    // twiddles of this axis in shared memory (plan constants: loaded before the wait)
+    C *stw = b1 + Lx * ld;
+    for (int i = threadIdx.x; i < Lx; i += blockDim.x) stw[i] = ((const C *)p.tw[0])[i];
+    pdl_wait();
     const int npairs = p.n_row_pairs;
     const int pr0 = blockIdx.x * PB;
     T *A = (T *)p.gridA;
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
         ((V *)(A + r0))[xv] = VecW<T>::zero();
         ((V *)(A + r0 + Lx))[xv] = VecW<T>::zero();
     }
-    const C *res = fft_columns<C, false>(b0, b1, Lx, ld, PB, (const C *)p.tw[0]);
+    const C *res = fft_columns<C, false>(b0, b1, Lx, ld, PB, stw);
     C *S1 = (C *)p.S1;
     for (int i = threadIdx.x; i < PB * Kx; i += blockDim.x) {
         const int b = i >> lgKx, k = i & (Kx - 1);
@@ -227,7 +230,6 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
     pdl_trigger();
-    pdl_wait();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
@@ -235,6 +237,10 @@ __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
     const int lgB = __ffs(B) - 1;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Ly * ld;
+    // twiddles of this axis in shared memory (plan constants: loaded before the wait)
+    C *stw = b1 + Ly * ld;
+    for (int i = threadIdx.x; i < Ly; i += blockDim.x) stw[i] = ((const C *)p.tw[1])[i];
+    pdl_wait();
     const int ntile = Kx / B;
     const int zi = blockIdx.x / ntile;
     const int z = (p.z0 + zi) & (p.L[2] - 1);
@@ -251,7 +257,7 @@ __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
         },
         [&](int i, C v) { b0[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
-    const C *res = fft_columns<C, false>(b0, b1, Ly, ld, B, (const C *)p.tw[1]);
+    const C *res = fft_columns<C, false>(b0, b1, Ly, ld, B, stw);
     C *S2 = (C *)p.S2 + (int64_t)z * ny * Kx + kx0;
     for (int i = threadIdx.x; i < ny * B; i += blockDim.x) {
         const int kp = i >> lgB, b = i & (B - 1);
@@ -269,7 +275,6 @@ __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
     pdl_trigger();
-    pdl_wait();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lz = p.L[2], Kx = p.Kx, ny = p.n[1], nz = p.n[2];
@@ -277,6 +282,10 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
     const int lgB = __ffs(B) - 1;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Lz * ld;
+    // twiddles of this axis in shared memory (plan constants: loaded before the wait)
+    C *stw = b1 + Lz * ld;
+    for (int i = threadIdx.x; i < Lz; i += blockDim.x) stw[i] = ((const C *)p.tw[2])[i];
+    pdl_wait();
     const int ntile = Kx / B;
     const int kp = blockIdx.x / ntile;
     const int kx0 = (blockIdx.x - kp * ntile) * B;
@@ -300,7 +309,7 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
         },
         [&](int i, C v) { b0[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
-    C *res = fft_columns<C, false>(b0, b1, Lz, ld, B, (const C *)p.tw[2]);
+    C *res = fft_columns<C, false>(b0, b1, Lz, ld, B, stw);
     C *oth = (res == b0) ? b1 : b0;
     const int aky = kp < ny / 2 ? kp : ny - kp;
     const T *D = (const T *)p.Dtab;
@@ -316,7 +325,7 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
         res[kz * ld + b] = v;
     }
     __syncthreads();
-    const C *out = fft_columns<C, true>(res, oth, Lz, ld, B, (const C *)p.tw[2]);
+    const C *out = fft_columns<C, true>(res, oth, Lz, ld, B, stw);
     for (int i = threadIdx.x; i < nza * B; i += blockDim.x) {
         const int z = (z0 + (i >> lgB)) & (Lz - 1), b = i & (B - 1);
         S2[z * zs + b] = out[z * ld + b];
@@ -327,7 +336,6 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
     pdl_trigger();
-    pdl_wait();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
@@ -335,6 +343,10 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
     const int lgB = __ffs(B) - 1;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Ly * ld;
+    // twiddles of this axis in shared memory (plan constants: loaded before the wait)
+    C *stw = b1 + Ly * ld;
+    for (int i = threadIdx.x; i < Ly; i += blockDim.x) stw[i] = ((const C *)p.tw[1])[i];
+    pdl_wait();
     const int ntile = Kx / B;
     const int zi = blockIdx.x / ntile;
     const int z = (p.z0 + zi) & (p.L[2] - 1);
@@ -355,7 +367,7 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
         },
         [&](int i, C v) { b0[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
-    const C *res = fft_columns<C, true>(b0, b1, Ly, ld, B, (const C *)p.tw[1]);
+    const C *res = fft_columns<C, true>(b0, b1, Ly, ld, B, stw);
     C *S1 = (C *)p.S1 + (int64_t)z * Ly * Kx + kx0;
     for (int i = threadIdx.x; i < iv.y * B; i += blockDim.x) {
         const int y = (iv.x + (i >> lgB)) & (Ly - 1), b = i & (B - 1);
@@ -367,7 +379,6 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
     pdl_trigger();
-    pdl_wait();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx;
@@ -375,9 +386,13 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
     const int lgLx = __ffs(Lx) - 1, lgKx = __ffs(Kx) - 1, lgHy = __ffs(Ly) - 2;
     C *b0 = (C *)smem_raw;
     C *b1 = b0 + Lx * ld;
+    // twiddles of this axis in shared memory (plan constants: loaded before the wait)
+    C *stw = b1 + Lx * ld;
+    for (int i = threadIdx.x; i < Lx; i += blockDim.x) stw[i] = ((const C *)p.tw[0])[i];
     const int npairs = p.n_row_pairs;
     const int pr0 = blockIdx.x * PB;
     for (int i = threadIdx.x; i < PB * Lx; i += blockDim.x) b0[(i & (Lx - 1)) * ld + (i >> lgLx)] = cmk(T(0), T(0));
+    pdl_wait();
     __syncthreads();
     const C *S1 = (const C *)p.S1;
     typedef typename VecT<T>::T4 T4;  // (xa, xb) of one mode, loaded together
@@ -411,7 +426,7 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
             }
         });
     __syncthreads();
-    const C *res = fft_columns<C, true>(b0, b1, Lx, ld, PB, (const C *)p.tw[0]);
+    const C *res = fft_columns<C, true>(b0, b1, Lx, ld, PB, stw);
     T *G = (T *)p.gridB;
     typedef typename VecW<T>::V V;
     constexpr int VW = VecW<T>::W;
@@ -609,13 +624,13 @@ __global__ void __launch_bounds__(512) k_iyx(DevPlan p, int PB, int x0_off, int 
 // complex within ~64 KB.
 static int row_batch(int L, size_t celem) {
     int pb = 8;
-    while (pb > 1 && 2 * (size_t)L * (pb + 1) * celem > 64 * 1024) pb >>= 1;
+    while (pb > 1 && (2 * (size_t)L * (pb + 1) + L) * celem > 64 * 1024) pb >>= 1;
     return pb;
 }
 static int col_batch(int L, int Kx, size_t celem) {
     int b = 8;
     if (b > Kx) b = Kx;
-    while (b > 1 && 2 * (size_t)L * (b + 1) * celem > 64 * 1024) b >>= 1;
+    while (b > 1 && (2 * (size_t)L * (b + 1) + L) * celem > 64 * 1024) b >>= 1;
     return b;
 }
 
@@ -627,7 +642,7 @@ template <typename K> static cudaError_t prep(K kern, size_t sm) {
 template <typename T> static cudaError_t fx_t(const DevPlan &p, cudaStream_t s) {
     const size_t ce = 2 * sizeof(T);
     const int PB = row_batch(p.L[0], ce);
-    const size_t sm = 2 * (size_t)p.L[0] * (PB + 1) * ce;
+    const size_t sm = (2 * (size_t)p.L[0] * (PB + 1) + p.L[0]) * ce;
     cudaError_t e = prep(k_fx<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.n_row_pairs == 0) return cudaSuccess;
@@ -637,7 +652,7 @@ template <typename T> static cudaError_t fx_t(const DevPlan &p, cudaStream_t s) 
 template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) {
     const size_t ce = 2 * sizeof(T);
     const int PB = row_batch(p.L[0], ce);
-    const size_t sm = 2 * (size_t)p.L[0] * (PB + 1) * ce;
+    const size_t sm = (2 * (size_t)p.L[0] * (PB + 1) + p.L[0]) * ce;
     cudaError_t e = prep(k_ix<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.n_row_pairs == 0) return cudaSuccess;
@@ -647,7 +662,7 @@ template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) 
 template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) {
     const size_t ce = 2 * sizeof(T);
     const int B = col_batch(p.L[1], p.Kx, ce);
-    const size_t sm = 2 * (size_t)p.L[1] * (B + 1) * ce;
+    const size_t sm = (2 * (size_t)p.L[1] * (B + 1) + p.L[1]) * ce;
     cudaError_t e = prep(k_fy<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
@@ -657,7 +672,7 @@ template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) 
 template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) {
     const size_t ce = 2 * sizeof(T);
     const int B = col_batch(p.L[1], p.Kx, ce);
-    const size_t sm = 2 * (size_t)p.L[1] * (B + 1) * ce;
+    const size_t sm = (2 * (size_t)p.L[1] * (B + 1) + p.L[1]) * ce;
     cudaError_t e = prep(k_iy<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
@@ -667,7 +682,7 @@ template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) 
 template <typename T> static cudaError_t fz_t(const DevPlan &p, cudaStream_t s) {
     const size_t ce = 2 * sizeof(T);
     const int B = col_batch(p.L[2], p.Kx, ce);
-    const size_t sm = 2 * (size_t)p.L[2] * (B + 1) * ce;
+    const size_t sm = (2 * (size_t)p.L[2] * (B + 1) + p.L[2]) * ce;
     cudaError_t e = prep(k_fz<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;

@@ -40,19 +40,17 @@ __global__ void __launch_bounds__(256) k_nodal_prep(DevPlan p, const T *__restri
 template <typename T>
 __device__ __forceinline__ T source_charge(const DevPlan &p, int64_t k, int kind, const T *__restrict__ in) {
     typedef typename VecT<T>::T4 T4;
-    const int u = p.src_perm[k];
-    const T w = ((const T *)p.src_w)[k];
-    if (kind == 0) return w * in[u];
-    const int j = u / p.q;
-    const int s = u - j * p.q;
-    const T4 nrm = ((const T4 *)p.tri_nrm)[j];
+    const int4 v = p.src_tri[k];
+    const T4 wn = ((const T4 *)p.src_wn)[k];
+    const int u = v.w;
+    if (kind == 0) return wn.w * in[u];
     T mx, my, mz;
     if (kind == 1) {
         mx = in[3 * (int64_t)u];
         my = in[3 * (int64_t)u + 1];
         mz = in[3 * (int64_t)u + 2];
     } else {
-        const int4 v = p.tri_vtx[j];
+        const int s = u - (u / p.q) * p.q;
         const T *lam = (const T *)p.lam + 3 * s;
         const T l0 = lam[0], l1 = lam[1], l2 = lam[2];
         const T *a = in + 3 * (int64_t)v.x, *b = in + 3 * (int64_t)v.y, *c = in + 3 * (int64_t)v.z;
@@ -60,7 +58,7 @@ __device__ __forceinline__ T source_charge(const DevPlan &p, int64_t k, int kind
         my = l0 * a[1] + l1 * b[1] + l2 * c[1];
         mz = l0 * a[2] + l1 * b[2] + l2 * c[2];
     }
-    return w * (mx * nrm.x + my * nrm.y + mz * nrm.z);
+    return mx * wn.x + my * wn.y + mz * wn.z;
 }
 
 // qbuf[k] = w_k * sigma_k in sorted source order.
@@ -305,7 +303,7 @@ template <typename T, int M, int TS> struct SpreadSmem {
 };
 
 template <typename T, int M, int TS>
-__global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind, const T *__restrict__ in) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spread_groups(DevPlan p, int fused_kind, const T *__restrict__ in) {
     pdl_trigger();
     typedef typename VecT<T>::T4 T4;
     typedef TileGeomG<M, TS> G;
@@ -373,27 +371,40 @@ __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind
         }
         if (wlane) {
             T *dst = wv + wax * AX + wi;
-            for (int g = 0; g < ng; ++g) {
-                const T f = ((const T *)(sg + g0 + g))[wax];
-                T v;
-                if (sizeof(T) == 4) {
-                    v = cf[WDEG];
+            if constexpr (sizeof(T) == 4) {
+                // two sources per step, paired FP32 multiply-adds
+                for (int g = 0; g < ng; g += 2) {
+                    const int g1 = g + 1 < ng ? g + 1 : g;
+                    const float2 f2 = make_float2(((const float *)(sg + g0 + g))[wax], ((const float *)(sg + g0 + g1))[wax]);
+                    float2 v = make_float2(cf[WDEG], cf[WDEG]);
 #pragma unroll
-                    for (int k = WDEG - 1; k >= 0; --k) v = v * f + cf[k];
-                } else {
-                    v = kb_window(f + T(M - 1 - wi), inv_m, beta, isb);
+                    for (int k = WDEG - 1; k >= 0; --k) v = __ffma2_rn(v, f2, make_float2(cf[k], cf[k]));
+                    if (wax == 0) {
+                        v.x *= sq[g0 + g];
+                        v.y *= sq[g0 + g1];
+                    }
+                    dst[g * WP] = v.x;
+                    if (g + 1 < ng) dst[(g + 1) * WP] = v.y;
                 }
-                if (wax == 0) v *= sq[g0 + g];
-                dst[g * WP] = v;
+            } else {
+                for (int g = 0; g < ng; ++g) {
+                    const T f = ((const T *)(sg + g0 + g))[wax];
+                    T v = kb_window(f + T(M - 1 - wi), inv_m, beta, isb);
+                    if (wax == 0) v *= sq[g0 + g];
+                    dst[g * WP] = v;
+                }
             }
         }
         __syncwarp();
         if (lane_on) {
-            T acc[H][W];
+            // acc[h][iy] of box point (ix, iy, izs + ZL h); FP32 pairs (iy, iy + 1)
+            constexpr int W2 = (W + 1) / 2;
+            typedef typename VecT<T>::T2 P2;
+            P2 acc[H][W2];
 #pragma unroll
             for (int h = 0; h < H; ++h)
 #pragma unroll
-                for (int iy = 0; iy < W; ++iy) acc[h][iy] = T(0);
+                for (int j = 0; j < W2; ++j) acc[h][j].x = acc[h][j].y = T(0);
             for (int g = 0; g < ng; ++g) {
                 const T a = wv[g * WP + ix];
                 const T *wz = wv + 2 * AX + g * WP;
@@ -406,9 +417,16 @@ __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind
                 T wy[WP];
                 load_row<WP>(wv + AX + g * WP, wy);
 #pragma unroll
-                for (int iy = 0; iy < W; ++iy)
+                for (int j = 0; j < W2; ++j)
 #pragma unroll
-                    for (int h = 0; h < H; ++h) acc[h][iy] += b[h] * wy[iy];
+                    for (int h = 0; h < H; ++h) {
+                        if constexpr (sizeof(T) == 4) {
+                            acc[h][j] = __ffma2_rn(make_float2(b[h], b[h]), make_float2(wy[2 * j], wy[2 * j + 1]), acc[h][j]);
+                        } else {
+                            acc[h][j].x += b[h] * wy[2 * j];
+                            acc[h][j].y += b[h] * wy[2 * j + 1];
+                        }
+                    }
             }
             T *base = my + lz * PS + ly * RS + lx + XO + ix;
 #pragma unroll
@@ -418,10 +436,11 @@ __global__ void __launch_bounds__(256) k_spread_groups(DevPlan p, int fused_kind
 #pragma unroll
                     for (int iy = 0; iy < W; ++iy) {
                         T *a = base + iz * PS + iy * RS;
+                        const T v = (iy & 1) ? acc[h][iy >> 1].y : acc[h][iy >> 1].x;
                         if constexpr (SA)
-                            atomicAdd(a, acc[h][iy]);
+                            atomicAdd(a, v);
                         else
-                            *a = *a + acc[h][iy];
+                            *a = *a + v;
                     }
                 }
             }

@@ -48,9 +48,8 @@ struct DevPlan {
     // sources, sorted (k_sorted); grid coordinates: frac (x,y,z) and packed cell
     const void *src_grid;   // T4 [Q]
     const int *src_perm;    // [Q] sorted -> user index k = j*q + s
-    const void *src_w;      // T [Q] w_s |S_j| in sorted order
-    const void *tri_nrm;    // T4 [M] outward unit normals (user triangle order)
-    const int4 *tri_vtx;    // [M] vertex ids (user order)
+    const void *src_wn;     // T4 [Q] sorted: w_k n_j (outward unit normal times the weight w_s |S_j|), w_k
+    const int4 *src_tri;    // [Q] sorted: user vertex ids of triangle j, user index k
     const void *lam;        // T [q*3] barycentric points of the rule
     // targets, sorted
     const void *tgt_grid;   // T4 [N]

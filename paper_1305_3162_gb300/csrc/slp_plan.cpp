@@ -874,16 +874,17 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
         if (tg[i].y >= T(1)) tg[i].y = std::nextafter(T(1), T(0));
         if (tg[i].z >= T(1)) tg[i].z = std::nextafter(T(1), T(0));
     }
-    std::vector<T> sw(p.Q);
-    for (int64_t i = 0; i < p.Q; ++i) sw[i] = (T)p.wk[p.src_perm[i]];
-    std::vector<T4> tn(p.M);
-    std::vector<int4> tv(p.M);
-    for (int64_t j = 0; j < p.M; ++j) {
-        tn[j].x = (T)p.nrm[3 * j];
-        tn[j].y = (T)p.nrm[3 * j + 1];
-        tn[j].z = (T)p.nrm[3 * j + 2];
-        tn[j].w = T(0);
-        tv[j] = make_int4(p.T[3 * j], p.T[3 * j + 1], p.T[3 * j + 2], 0);
+    // per sorted source: w_k n_j (and w_k), and the triangle's vertices with the user index k
+    std::vector<T4> swn(p.Q);
+    std::vector<int4> stri(p.Q);
+    for (int64_t i = 0; i < p.Q; ++i) {
+        const int64_t k = p.src_perm[i], j = k / p.q;
+        const double w = p.wk[k];
+        swn[i].x = (T)(w * p.nrm[3 * j]);
+        swn[i].y = (T)(w * p.nrm[3 * j + 1]);
+        swn[i].z = (T)(w * p.nrm[3 * j + 2]);
+        swn[i].w = (T)w;
+        stri[i] = make_int4(p.T[3 * j], p.T[3 * j + 1], p.T[3 * j + 2], (int)k);
     }
     std::vector<T> lamT(p.lam.begin(), p.lam.end());
     void *ptr;
@@ -891,12 +892,10 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     d.src_grid = ptr;
     TRY(upload(p, &ptr, p.src_perm.data(), p.src_perm.size()));
     d.src_perm = (const int *)ptr;
-    TRY(upload(p, &ptr, sw.data(), sw.size()));
-    d.src_w = ptr;
-    TRY(upload(p, &ptr, tn.data(), tn.size()));
-    d.tri_nrm = ptr;
-    TRY(upload(p, &ptr, tv.data(), tv.size()));
-    d.tri_vtx = (const int4 *)ptr;
+    TRY(upload(p, &ptr, swn.data(), swn.size()));
+    d.src_wn = ptr;
+    TRY(upload(p, &ptr, stri.data(), stri.size()));
+    d.src_tri = (const int4 *)ptr;
     TRY(upload(p, &ptr, lamT.data(), lamT.size()));
     d.lam = ptr;
     TRY(upload(p, &ptr, tg.data(), tg.size()));
@@ -1495,6 +1494,11 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
         tile_items(*p, p->src_grid, skeys, p->Q, (int)ch, p->spread_items);
     }
     tile_items(*p, p->tgt_grid, tkeys, p->N, 32, p->gather_items);
+    // largest items first: blocks are dispatched in index order, so this
+    // schedules the long items early and the short ones fill the tail
+    auto by_size = [](const slp::TileItem &a, const slp::TileItem &b) { return a.end - a.begin > b.end - b.begin; };
+    std::stable_sort(p->spread_items.begin(), p->spread_items.end(), by_size);
+    std::stable_sort(p->gather_items.begin(), p->gather_items.end(), by_size);
     near_items(*p, skeys, tkeys);
     build_dtab(*p);
     active_region(*p);
