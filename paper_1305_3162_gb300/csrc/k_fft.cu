@@ -152,6 +152,98 @@ __device__ C *fft_columns(C *b0, C *b1, int L, int ld, int B, const C *__restric
     return src;
 }
 
+// ---------------------------------------------------------------- in-place column FFT
+// In-place mixed-radix transform of B columns of length L = 2^p (column b,
+// element j at buf[j * ld + b]), used by the column passes so that a block
+// needs one buffer instead of two and can hold more columns.
+//   forward: decimation in frequency, stages s = 0 .. S-1 with radices
+//     R_s (8, ..., then 4 or 2); stage s splits each block of length
+//     N_s = L / (R_0 ... R_{s-1}) into R_s interleaved sub-sequences: DFT of
+//     {x[k0 + j + r N_s / R_s]}_r, then twiddle W_{N_s}^{j r}, written back in
+//     place.  Output: frequency k at position pos(k) (digit reversal below).
+//   inverse: the same stages in reverse order, each undone (conjugate
+//     twiddle first, then the DFT with the opposite sign): input at pos(k),
+//     output in natural order, unnormalised.
+// Radices: n8 = lgL / 3 stages of 8, then one stage of 2^rem (rem = lgL % 3)
+// when rem > 0; stage s has N_s = 2^(lgL - 3 s).
+struct RadixPlan {
+    int n8, rem, S;
+};
+__device__ __forceinline__ RadixPlan radix_plan(int lgL) {
+    RadixPlan r;
+    r.n8 = lgL / 3;
+    r.rem = lgL - 3 * r.n8;
+    r.S = r.n8 + (r.rem ? 1 : 0);
+    return r;
+}
+// position of frequency k after the forward transform: the stage-s digit of
+// k (3 bits, or rem bits for the last stage, least significant first) sits at
+// bit lgL - 3 (s + 1) of the position (bit 0 for the last digit)
+__device__ __forceinline__ int fft_pos(const RadixPlan &rp, int lgL, int k) {
+    int pos = 0;
+    for (int s = 0; s < rp.n8; ++s) pos |= ((k >> (3 * s)) & 7) << (lgL - 3 * (s + 1));
+    if (rp.rem) pos |= k >> (3 * rp.n8);
+    return pos;
+}
+// frequency held at position p after the forward transform (inverse of fft_pos)
+__device__ __forceinline__ int fft_freq(const RadixPlan &rp, int lgL, int p) {
+    int k = 0;
+    for (int s = 0; s < rp.n8; ++s) k |= ((p >> (lgL - 3 * (s + 1))) & 7) << (3 * s);
+    if (rp.rem) k |= (p & ((1 << rp.rem) - 1)) << (3 * rp.n8);
+    return k;
+}
+
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void inplace_stage(C *__restrict__ buf, int lgL, int lgNs, int ld, int lgB,
+                                              const C *__restrict__ tw) {
+    constexpr int LGR = R == 8 ? 3 : (R == 4 ? 2 : 1);
+    const int lgQ = lgNs - LGR;  // log2 of N_s / R
+    const int Qm = (1 << lgQ) - 1, Bm = (1 << lgB) - 1;
+    const int total = 1 << (lgL - LGR + lgB);
+    const int lgt = lgL - lgNs;  // twiddle stride L / N_s
+    for (int w = threadIdx.x; w < total; w += blockDim.x) {
+        const int b = w & Bm;
+        const int t = w >> lgB;
+        const int j = t & Qm;
+        const int k0 = (t >> lgQ) << lgNs;
+        C v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = buf[(k0 + j + (r << lgQ)) * ld + b];
+        if (INV && j != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C t2 = tw[((r * j) << lgt) & ((1 << lgL) - 1)];
+                t2.y = -t2.y;
+                v[r] = cmul(v[r], t2);
+            }
+        }
+        dftR<C, R, INV>(v);
+        if (!INV && j != 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[((r * j) << lgt) & ((1 << lgL) - 1)]);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[(k0 + j + (r << lgQ)) * ld + b] = v[r];
+    }
+}
+
+// All stages; ends with __syncthreads().
+template <typename C, bool INV>
+__device__ void fft_columns_inplace(C *buf, int lgL, int ld, int lgB, const C *__restrict__ tw) {
+    const RadixPlan rp = radix_plan(lgL);
+    for (int i = 0; i < rp.S; ++i) {
+        const int s = INV ? rp.S - 1 - i : i;
+        const int lgNs = lgL - 3 * s;
+        if (s < rp.n8)
+            inplace_stage<C, 8, INV>(buf, lgL, lgNs, ld, lgB, tw);
+        else if (rp.rem == 2)
+            inplace_stage<C, 4, INV>(buf, lgL, lgNs, ld, lgB, tw);
+        else
+            inplace_stage<C, 2, INV>(buf, lgL, lgNs, ld, lgB, tw);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- FX
 // PB row pairs per CTA; pair pr covers rows y0 = 2*(pr % (Ly/2)) and y0+1 of plane z.
 template <typename T>
@@ -226,19 +318,18 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
 }
 
 // ---------------------------------------------------------------- FY
-// CTA: plane z, columns kx0 .. kx0 + B.
+// CTA: plane z, columns kx0 .. kx0 + B; one in-place buffer [Ly][B + 1].
 template <typename T>
 __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
-    pdl_trigger();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
     const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
     const int ld = B + 1;
-    const int lgB = __ffs(B) - 1;
-    C *b0 = (C *)smem_raw;
-    C *b1 = b0 + Ly * ld;
+    const int lgB = __ffs(B) - 1, lgLy = __ffs(Ly) - 1;
+    C *buf = (C *)smem_raw;
     // twiddles of this axis in shared memory (plan constants: loaded before the wait)
-    C *stw = b1 + Ly * ld;
+    C *stw = buf + Ly * ld;
     for (int i = threadIdx.x; i < Ly; i += blockDim.x) stw[i] = ((const C *)p.tw[1])[i];
     pdl_wait();
     const int ntile = Kx / B;
@@ -255,35 +346,37 @@ __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
             if (((y - iv.x) & (Ly - 1)) < iv.y) v = S1[(int64_t)y * Kx + (i & (B - 1))];
             return v;
         },
-        [&](int i, C v) { b0[(i >> lgB) * ld + (i & (B - 1))] = v; });
+        [&](int i, C v) { buf[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
-    const C *res = fft_columns<C, false>(b0, b1, Ly, ld, B, stw);
+    fft_columns_inplace<C, false>(buf, lgLy, ld, lgB, stw);
+    const RadixPlan rp = radix_plan(lgLy);
     C *S2 = (C *)p.S2 + (int64_t)z * ny * Kx + kx0;
     for (int i = threadIdx.x; i < ny * B; i += blockDim.x) {
         const int kp = i >> lgB, b = i & (B - 1);
         C v = cmk(T(0), T(0));
-        if (kp < ny / 2)
-            v = res[kp * ld + b];
-        else if (kp > ny / 2)
-            v = res[(Ly - ny + kp) * ld + b];
+        if (kp != ny / 2) {
+            const int k = kp < ny / 2 ? kp : Ly - ny + kp;
+            v = buf[fft_pos(rp, lgLy, k) * ld + b];
+        }
         S2[(int64_t)kp * Kx + b] = v;
     }
 }
 
 // ---------------------------------------------------------------- FZ * D * IZ
-// CTA: row ky', columns kx0 .. kx0 + B; the pencil along z stays in shared memory.
+// CTA: row ky', columns kx0 .. kx0 + B; the pencil along z stays in shared
+// memory: forward transform in place (frequencies at digit-reversed
+// positions), multiply by D there, inverse transform in place (natural order).
 template <typename T>
 __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
-    pdl_trigger();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
     const int Lz = p.L[2], Kx = p.Kx, ny = p.n[1], nz = p.n[2];
     const int ld = B + 1;
-    const int lgB = __ffs(B) - 1;
-    C *b0 = (C *)smem_raw;
-    C *b1 = b0 + Lz * ld;
+    const int lgB = __ffs(B) - 1, lgLz = __ffs(Lz) - 1;
+    C *buf = (C *)smem_raw;
     // twiddles of this axis in shared memory (plan constants: loaded before the wait)
-    C *stw = b1 + Lz * ld;
+    C *stw = buf + Lz * ld;
     for (int i = threadIdx.x; i < Lz; i += blockDim.x) stw[i] = ((const C *)p.tw[2])[i];
     pdl_wait();
     const int ntile = Kx / B;
@@ -307,44 +400,43 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
             if (((z - z0) & (Lz - 1)) < nza) v = S2[z * zs + (i & (B - 1))];
             return v;
         },
-        [&](int i, C v) { b0[(i >> lgB) * ld + (i & (B - 1))] = v; });
+        [&](int i, C v) { buf[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
-    C *res = fft_columns<C, false>(b0, b1, Lz, ld, B, stw);
-    C *oth = (res == b0) ? b1 : b0;
+    fft_columns_inplace<C, false>(buf, lgLz, ld, lgB, stw);
+    const RadixPlan rp = radix_plan(lgLz);
     const int aky = kp < ny / 2 ? kp : ny - kp;
     const T *D = (const T *)p.Dtab;
     for (int i = threadIdx.x; i < Lz * B; i += blockDim.x) {
-        const int kz = i >> lgB, b = i & (B - 1);
-        const int kzs = kz < Lz / 2 ? kz : kz - Lz;
-        const int akz = kzs < 0 ? -kzs : kzs;
+        const int pz = i >> lgB, b = i & (B - 1);
+        const int kz = fft_freq(rp, lgLz, pz);
+        const int akz = kz < Lz / 2 ? kz : Lz - kz;
         C v = cmk(T(0), T(0));
         if (akz < nz / 2) {
             const T d = D[((int64_t)akz * (ny / 2) + aky) * Kx + kx0 + b];
-            v = cscale(res[kz * ld + b], d);
+            v = cscale(buf[pz * ld + b], d);
         }
-        res[kz * ld + b] = v;
+        buf[pz * ld + b] = v;
     }
     __syncthreads();
-    const C *out = fft_columns<C, true>(res, oth, Lz, ld, B, stw);
+    fft_columns_inplace<C, true>(buf, lgLz, ld, lgB, stw);
     for (int i = threadIdx.x; i < nza * B; i += blockDim.x) {
         const int z = (z0 + (i >> lgB)) & (Lz - 1), b = i & (B - 1);
-        S2[z * zs + b] = out[z * ld + b];
+        S2[z * zs + b] = buf[z * ld + b];
     }
 }
 
 // ---------------------------------------------------------------- IY
 template <typename T>
 __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
-    pdl_trigger();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
     const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
     const int ld = B + 1;
-    const int lgB = __ffs(B) - 1;
-    C *b0 = (C *)smem_raw;
-    C *b1 = b0 + Ly * ld;
+    const int lgB = __ffs(B) - 1, lgLy = __ffs(Ly) - 1;
+    C *buf = (C *)smem_raw;
     // twiddles of this axis in shared memory (plan constants: loaded before the wait)
-    C *stw = b1 + Ly * ld;
+    C *stw = buf + Ly * ld;
     for (int i = threadIdx.x; i < Ly; i += blockDim.x) stw[i] = ((const C *)p.tw[1])[i];
     pdl_wait();
     const int ntile = Kx / B;
@@ -353,25 +445,27 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
     const int kx0 = (blockIdx.x - zi * ntile) * B;
     const int2 iv = p.plane_iv[z];
     const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx + kx0;
-    // position y holds mode y (y < ny/2), or mode y - Ly (y > Ly - ny/2), else zero
+    // position q holds frequency k = fft_freq(q): mode k (k < ny/2) or mode
+    // k - Ly (k > Ly - ny/2), zero elsewhere
+    const RadixPlan rp = radix_plan(lgLy);
     pipelined_copy<C>(
         Ly * B,
         [&](int i) {
-            const int y = i >> lgB, b = i & (B - 1);
+            const int k = fft_freq(rp, lgLy, i >> lgB), b = i & (B - 1);
             C v = cmk(T(0), T(0));
-            if (y < ny / 2)
-                v = S2[(int64_t)y * Kx + b];
-            else if (y > Ly - ny / 2)
-                v = S2[(int64_t)(y - Ly + ny) * Kx + b];
+            if (k < ny / 2)
+                v = S2[(int64_t)k * Kx + b];
+            else if (k > Ly - ny / 2)
+                v = S2[(int64_t)(k - Ly + ny) * Kx + b];
             return v;
         },
-        [&](int i, C v) { b0[(i >> lgB) * ld + (i & (B - 1))] = v; });
+        [&](int i, C v) { buf[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
-    const C *res = fft_columns<C, true>(b0, b1, Ly, ld, B, stw);
+    fft_columns_inplace<C, true>(buf, lgLy, ld, lgB, stw);
     C *S1 = (C *)p.S1 + (int64_t)z * Ly * Kx + kx0;
     for (int i = threadIdx.x; i < iv.y * B; i += blockDim.x) {
         const int y = (iv.x + (i >> lgB)) & (Ly - 1), b = i & (B - 1);
-        S1[(int64_t)y * Kx + b] = res[y * ld + b];
+        S1[(int64_t)y * Kx + b] = buf[y * ld + b];
     }
 }
 
@@ -627,10 +721,14 @@ static int row_batch(int L, size_t celem) {
     while (pb > 1 && (2 * (size_t)L * (pb + 1) + L) * celem > 64 * 1024) pb >>= 1;
     return pb;
 }
-static int col_batch(int L, int Kx, size_t celem) {
-    int b = 8;
+// Column passes: one in-place buffer (L x (B+1)) plus the twiddles; up to 16
+// columns per block (128-byte row segments) within ~100 KB of shared memory,
+// but no fewer than two blocks per SM while halving B keeps it at >= 8.
+static int col_batch(int L, int Kx, size_t celem, int64_t rows_of_blocks) {
+    int b = 16;
     if (b > Kx) b = Kx;
-    while (b > 1 && (2 * (size_t)L * (b + 1) + L) * celem > 64 * 1024) b >>= 1;
+    while (b > 1 && ((size_t)L * (b + 1) + L) * celem > 100 * 1024) b >>= 1;
+    while (b > 8 && rows_of_blocks * (Kx / b) < 2 * 152) b >>= 1;
     return b;
 }
 
@@ -661,8 +759,8 @@ template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) 
 }
 template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) {
     const size_t ce = 2 * sizeof(T);
-    const int B = col_batch(p.L[1], p.Kx, ce);
-    const size_t sm = (2 * (size_t)p.L[1] * (B + 1) + p.L[1]) * ce;
+    const int B = col_batch(p.L[1], p.Kx, ce, p.nz_act);
+    const size_t sm = ((size_t)p.L[1] * (B + 1) + p.L[1]) * ce;
     cudaError_t e = prep(k_fy<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
@@ -671,8 +769,8 @@ template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) 
 }
 template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) {
     const size_t ce = 2 * sizeof(T);
-    const int B = col_batch(p.L[1], p.Kx, ce);
-    const size_t sm = (2 * (size_t)p.L[1] * (B + 1) + p.L[1]) * ce;
+    const int B = col_batch(p.L[1], p.Kx, ce, p.nz_act);
+    const size_t sm = ((size_t)p.L[1] * (B + 1) + p.L[1]) * ce;
     cudaError_t e = prep(k_iy<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
@@ -681,8 +779,8 @@ template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) 
 }
 template <typename T> static cudaError_t fz_t(const DevPlan &p, cudaStream_t s) {
     const size_t ce = 2 * sizeof(T);
-    const int B = col_batch(p.L[2], p.Kx, ce);
-    const size_t sm = (2 * (size_t)p.L[2] * (B + 1) + p.L[2]) * ce;
+    const int B = col_batch(p.L[2], p.Kx, ce, p.n[1]);
+    const size_t sm = ((size_t)p.L[2] * (B + 1) + p.L[2]) * ce;
     cudaError_t e = prep(k_fz<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;

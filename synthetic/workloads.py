@@ -53,6 +53,16 @@ def cube(nper: int = 8, grid=(32, 32, 32), precision: int = 64, tolerance: float
     return Workload(f"cube{nper}", V, T, 3, m, tuple(grid), precision, tolerance, seed)
 
 
+def cube_large(nper: int = 400, grid=(1024, 1024, 1024), precision: int = 32, tolerance: float = 1e-5,
+               index: int = 5) -> Workload:
+    """Largest serving mesh: unit cube, nper x nper squares per face (1.92M
+    triangles at 400), 3-point rule, smooth random field."""
+    V, T = meshes.cube(nper)
+    seed = fields.workload_seed(index)
+    m = fields.smooth_random(V, seed)
+    return Workload(f"cube{nper}", V, T, 3, m, tuple(grid), precision, tolerance, seed)
+
+
 def sphere(level: int = 5, grid=(128, 128, 128), precision: int = 32, tolerance: float = 1e-5,
            quad: int = 7, index: int = 1) -> Workload:
     V, T = meshes.icosphere(level, 1.0)
