@@ -122,6 +122,21 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(dist, seconds, device="cuda"):
+    """Largest of the ranks' timed regions (the whole-job time of N replicas)."""
+    if not dist:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _throughput(n_targets, steps, world_size, seconds):
+    """Whole-job targets/s: every rank evaluates `steps` states of n_targets."""
+    return n_targets * steps * world_size / seconds
+
+
 def _workload(name):
     from synthetic import workloads
     if name == "sphere":
@@ -257,12 +272,8 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = w.n_targets * args.steps * ws / total_s
+    total_s = _max_over_ranks(dist, sum(step_ms) / 1e3)
+    value = _throughput(w.n_targets, args.steps, ws, total_s)
 
     # ---- per-kernel durations (CUDA events on the launch stream, after an L2 flush)
     prof = {}
@@ -330,13 +341,9 @@ def run_ours(args):
     for i in range(args.steps):
         slp.slp_eval_host(plan.handle, kind, h_in[i % N_STATES], h_out, stream)
     torch.cuda.synchronize()
-    te = time.perf_counter() - te0
-    if dist:
-        t = torch.tensor([te], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te = float(t.item())
+    te = _max_over_ranks(dist, time.perf_counter() - te0)
     es = 4 if w.precision == 32 else 8
-    e2e = {"value": w.n_targets * args.steps * ws / te, "unit": UNIT,
+    e2e = {"value": _throughput(w.n_targets, args.steps, ws, te), "unit": UNIT,
            "h2d_bytes_per_step": 3 * es * w.n_targets, "d2h_bytes_per_step": es * w.n_targets}
 
     cpu = None
@@ -637,6 +644,19 @@ def run_served(args):
     wall = time.perf_counter() - tstart
     stats = slp.slp_server_stats(server)
     slp.slp_server_destroy(server)
+    # the same requests one state at a time through the plain host-buffer entry
+    # point (copy in, evaluate, copy out, synchronise), back to back
+    stream = torch.cuda.current_stream()
+    t1 = time.perf_counter()
+    for i in range(n_req):
+        k = int(which[i])
+        nV = pool[k][1][0].shape[0]
+        ho = rings[k][0]
+        for j in range(int(nst[i])):
+            src = states[k][int(start[i]) + j]
+            slp.slp_eval_host(plans[k], slp.SLP_INPUT_NODAL_MAG, src, ho[j * nV:(j + 1) * nV], stream)
+    torch.cuda.synchronize()
+    wall_single = time.perf_counter() - t1
     # parity of the probes (oracle at up to 256 sampled nodes)
     errs = {}
     for k, (name, (V, T), q, grid) in enumerate(pool):
@@ -656,7 +676,10 @@ def run_served(args):
             "latency_p50_ms": stats["latency_p50_ms"], "latency_p99_ms": stats["latency_p99_ms"],
             "queue_wait_p50_ms": stats["queue_wait_p50_ms"], "queue_wait_p99_ms": stats["queue_wait_p99_ms"],
             "wall_s": wall, "server": stats, "probe_rel_l2_sampled": errs,
-            "parity_ok": max(errs.values()) <= 1e-5}
+            "parity_ok": max(errs.values()) <= 1e-5,
+            "one_at_a_time": {"value": targets / wall_single, "wall_s": wall_single,
+                              "path": "slp_eval_host per state, same requests, back to back"},
+            "speedup_vs_one_at_a_time": wall_single / wall}
     print(json.dumps(line), flush=True)
     for p in plans:
         slp.slp_destroy(p)

@@ -99,7 +99,8 @@ typedef struct {
     int m;                /* Kaiser-Bessel half-width in grid cells; 0 = from the tolerance */
     int kernel_mode;      /* SLP_KERNEL_* */
     int near_mode;        /* SLP_NEAR_* */
-    int deterministic;    /* 1: fixed-order reductions, bitwise repeatable results */
+    int deterministic;    /* 1: near-field sums in a fixed order (the spread still adds tiles with
+                             atomics, so results repeat to rounding level, not bitwise) */
     int device;           /* CUDA device ordinal; -1 builds a host-only plan (slp_query works,
                              slp_eval returns SLP_ERR_NO_DEVICE) */
     int allow_grid_raise; /* 1: raise a grid that cannot meet the tolerance (else error) */
