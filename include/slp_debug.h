@@ -72,6 +72,14 @@ slp_status slp_debug_buffer_bytes(slp_plan_t plan, int buffer, int64_t *bytes);
 slp_status slp_debug_host_count(slp_plan_t plan, int which, int64_t *count);
 slp_status slp_debug_host_array(slp_plan_t plan, int which, void *out, int64_t count);
 
+/* Run one full evaluation as slp_eval does (near-field branch concurrent on
+ * the plan's auxiliary stream) with events recorded at its milestones; ms[0..3]
+ * receive the times from the start to: the end of the spread, the end of the
+ * FFT passes, the end of the near-field branch and the end of the gather.
+ * Synchronises the stream. */
+slp_status slp_debug_timeline(slp_plan_t plan, int input_kind, const void *d_in, void *d_phi, void *stream,
+                              float *ms);
+
 /* Run one full evaluation and time each kernel with CUDA events recorded on
  * `stream` between the launches; ms[i] receives kernel i's duration
  * (n >= 10 entries; the kernels in launch order are named by

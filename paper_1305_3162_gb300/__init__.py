@@ -128,6 +128,7 @@ EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_host", "slp_qu
             "slp_check", "slp_destroy", "slp_status_string", "slp_last_error",
             "slp_debug_run", "slp_debug_copy", "slp_debug_buffer_bytes", "slp_debug_host_count",
             "slp_debug_host_array", "slp_debug_window", "slp_debug_window_hat", "slp_debug_profile",
+            "slp_debug_timeline",
             "slp_debug_stage_name", "slp_eval_direct_static", "slp_batch_create", "slp_batch_run",
             "slp_batch_query", "slp_batch_destroy", "slp_plan_autotune", "slp_server_default_opts",
             "slp_server_create", "slp_server_submit", "slp_server_status", "slp_server_wait", "slp_server_cancel",
@@ -170,6 +171,7 @@ def load():
         "slp_debug_window": ([ctypes.c_int, ctypes.c_double], ctypes.c_double),
         "slp_debug_window_hat": ([ctypes.c_int, ctypes.c_int, ctypes.c_double], ctypes.c_double),
         "slp_debug_profile": ([vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int], St),
+        "slp_debug_timeline": ([vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_float)], St),
         "slp_debug_stage_name": ([ctypes.c_int], ctypes.c_char_p),
         "slp_eval_direct_static": ([vp, I64, vp, I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp], St),
         "slp_batch_create": ([ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -413,6 +415,15 @@ def slp_debug_host_array(plan, which: int):
     out = np.zeros(n.value, dtype=_HOST_DTYPES[which])
     _check(load().slp_debug_host_array(plan, int(which), _ptr(out), n.value), "slp_debug_host_array")
     return out
+
+
+def slp_debug_timeline(plan, input_kind, d_in, d_phi, stream=None):
+    """Milestones (ms from the start) of one concurrent evaluation: spread,
+    fft, near branch, gather."""
+    ms = (ctypes.c_float * 4)()
+    _check(load().slp_debug_timeline(plan, int(input_kind), _ptr(d_in), _ptr(d_phi), _stream(stream), ms),
+           "slp_debug_timeline")
+    return {"spread": ms[0], "fft": ms[1], "near": ms[2], "gather": ms[3]}
 
 
 def slp_debug_profile(plan, input_kind, d_in, d_phi, stream=None) -> dict:

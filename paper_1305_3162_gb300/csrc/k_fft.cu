@@ -25,6 +25,8 @@
 // plane's active y interval, FZ reads and writes only active z.  Rows outside
 // stay zero in every buffer, which is what the full transforms would compute
 // for grid A's zero rows; grid B's inactive rows are never read.
+#include <cooperative_groups.h>
+
 #include "dev_common.cuh"
 
 namespace slp {
@@ -546,61 +548,53 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
 }
 
 // ---------------------------------------------------------------- fused plane passes
-// For planes that fit in shared memory, FX + FY and IY + IX run as one block
-// per active z plane: the plane's active row pairs are transformed along x
-// into the plane spectrum P[y][kx] in shared memory, which is then
-// transformed along y (and the reverse for the inverse).  This removes the
-// S1 round trip and two launches.
-//   x buffers X0, X1: [Lx][PB + 1] (PB >= the plane's active pairs)
-//   plane buffer P: [Ly][Kx + 1]; its ping-pong buffer Y1 aliases the x
-//   buffers where they are large enough (FXY), and the inverse x transform's
-//   ping-pong buffer aliases whichever plane buffer is free (IYX).
-struct FusedLayout {
-    int xb, pb;           // complex elements of one x buffer and of one plane buffer
-    int fxy_y1, fxy_total;  // FXY: offset of Y1, total elements
-    int iyx_x0, iyx_x1, iyx_total;  // IYX: offsets of X0 and X1 (-1: alias the free plane buffer)
-};
-static FusedLayout fused_layout(const DevPlan &p, int PB) {
-    FusedLayout f;
-    f.xb = p.L[0] * (PB + 1);
-    f.pb = p.L[1] * (p.Kx + 1);
-    // FXY: X0 | X1 | P [| Y1]
-    f.fxy_y1 = 2 * f.xb >= f.pb ? 0 : 2 * f.xb + f.pb;
-    f.fxy_total = 2 * f.xb + f.pb + (2 * f.xb >= f.pb ? 0 : f.pb);
-    // IYX: P | Y1 | X0 [| X1]
-    f.iyx_x0 = 2 * f.pb;
-    f.iyx_x1 = f.pb >= f.xb ? -1 : 2 * f.pb + f.xb;
-    f.iyx_total = 2 * f.pb + f.xb + (f.pb >= f.xb ? 0 : f.xb);
-    return f;
-}
+// FX + FY and IY + IX of one active z plane run in a thread-block cluster of
+// FUSE_CL CTAs that exchange the plane spectrum through distributed shared
+// memory, so S1 never goes to global memory and two launches disappear.
+// CTA c of a cluster owns row pairs [c PB/CL, (c+1) PB/CL) of the plane for
+// the x transforms and spectrum columns [c Kx/CL, (c+1) Kx/CL) for the y
+// transforms.  Per CTA: X0, X1 [Lx][PB/CL + 1] (x transforms), P [Ly][Kx/CL + 1]
+// (its columns of the plane spectrum), twiddles of x and y.  Every CTA passes
+// both cluster barriers (no early exit), so each remote store lands in live
+// shared memory before the barrier that orders it.
+constexpr int FUSE_CL = 4;
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_fxy(DevPlan p, int PB, int y1_off) {
-    pdl_trigger();
-    pdl_wait();
+__global__ void __launch_bounds__(256) k_fxy(DevPlan p, int PB) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
     const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
-    const int ldx = PB + 1, ldp = Kx + 1;
-    const int lgKx = __ffs(Kx) - 1, lgPB = __ffs(PB) - 1;
+    const int c = (int)cluster.block_rank();
+    const int PBc = PB / FUSE_CL, KC = Kx / FUSE_CL;
+    const int ldx = PBc + 1, ldp = KC + 1;
+    const int lgKx = __ffs(Kx) - 1, lgKC = __ffs(KC) - 1, lgLy = __ffs(Ly) - 1;
     C *X0 = (C *)smem_raw;
     C *X1 = X0 + Lx * ldx;
     C *P = X1 + Lx * ldx;
-    C *Y1 = (C *)smem_raw + y1_off;
-    const int z = (p.z0 + (int)blockIdx.x) & (p.L[2] - 1);
+    C *twx = P + Ly * ldp;
+    C *twy = twx + Lx;
+    for (int i = threadIdx.x; i < Lx; i += blockDim.x) twx[i] = ((const C *)p.tw[0])[i];
+    for (int i = threadIdx.x; i < Ly; i += blockDim.x) twy[i] = ((const C *)p.tw[1])[i];
+    for (int i = threadIdx.x; i < Ly * ldp; i += blockDim.x) P[i] = cmk(T(0), T(0));
+    const int z = (p.z0 + (int)blockIdx.x / FUSE_CL) & (p.L[2] - 1);
+    pdl_wait();
     const int2 iv = p.plane_iv[z];
     const int npr = iv.y >> 1;
+    const int j0 = c * PBc;
+    const int nj = npr - j0 < 0 ? 0 : (npr - j0 > PBc ? PBc : npr - j0);
     T *A = (T *)p.gridA + (int64_t)z * Ly * Lx;
     typedef typename VecW<T>::V V;
     constexpr int VW = VecW<T>::W;
     const int nv = Lx / VW, lgnv = __ffs(nv) - 1;
-    for (int i = threadIdx.x; i < Ly * ldp; i += blockDim.x) P[i] = cmk(T(0), T(0));
-    // pair j: rows ya, ya + 1 -> column j of X0 (real and imaginary parts)
-    for (int i = threadIdx.x; i < (PB << lgnv); i += blockDim.x) {
+    // own pairs: rows ya, ya + 1 -> column j of X0
+    for (int i = threadIdx.x; i < (PBc << lgnv); i += blockDim.x) {
         const int j = i >> lgnv, xv = i & (nv - 1);
         T ra[VW], rb[VW];
-        if (j < npr) {
-            const int ya = (iv.x + 2 * j) & (Ly - 1);
+        if (j < nj) {
+            const int ya = (iv.x + 2 * (j0 + j)) & (Ly - 1);
             VecW<T>::split(((const V *)(A + (int64_t)ya * Lx))[xv], ra);
             VecW<T>::split(((const V *)(A + (int64_t)(ya + 1) * Lx))[xv], rb);
         } else {
@@ -610,94 +604,113 @@ __global__ void __launch_bounds__(512) k_fxy(DevPlan p, int PB, int y1_off) {
 #pragma unroll
         for (int e = 0; e < VW; ++e) X0[(xv * VW + e) * ldx + j] = cmk(ra[e], rb[e]);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < (npr << lgnv); i += blockDim.x) {
+    // every CTA's P is clear before any remote store; X0 is complete
+    cluster.sync();
+    for (int i = threadIdx.x; i < (nj << lgnv); i += blockDim.x) {
         const int j = i >> lgnv, xv = i & (nv - 1);
-        const int ya = (iv.x + 2 * j) & (Ly - 1);
+        const int ya = (iv.x + 2 * (j0 + j)) & (Ly - 1);
         ((V *)(A + (int64_t)ya * Lx))[xv] = VecW<T>::zero();
         ((V *)(A + (int64_t)(ya + 1) * Lx))[xv] = VecW<T>::zero();
     }
-    const C *res = fft_columns<C, false>(X0, X1, Lx, ldx, PB, (const C *)p.tw[0]);
-    for (int i = threadIdx.x; i < (npr << lgKx); i += blockDim.x) {
+    const C *res = fft_columns<C, false>(X0, X1, Lx, ldx, PBc, twx);
+    // pair j, frequency k -> rows ya, ya + 1, column k & (KC - 1) of CTA k / KC
+    for (int i = threadIdx.x; i < (nj << lgKx); i += blockDim.x) {
         const int j = i >> lgKx, k = i & (Kx - 1);
-        const int ya = (iv.x + 2 * j) & (Ly - 1);
+        const int ya = (iv.x + 2 * (j0 + j)) & (Ly - 1);
         const C Z = res[k * ldx + j];
         const C Zc = cconj(res[((Lx - k) & (Lx - 1)) * ldx + j]);
-        P[ya * ldp + k] = cscale(cadd(Z, Zc), T(0.5));
-        P[(ya + 1) * ldp + k] = cscale(cmul_mi(csub(Z, Zc)), T(0.5));
+        C *dst = cluster.map_shared_rank(P, k >> lgKC);
+        dst[ya * ldp + (k & (KC - 1))] = cscale(cadd(Z, Zc), T(0.5));
+        dst[(ya + 1) * ldp + (k & (KC - 1))] = cscale(cmul_mi(csub(Z, Zc)), T(0.5));
     }
-    __syncthreads();
-    const C *r2 = fft_columns<C, false>(P, Y1, Ly, ldp, Kx, (const C *)p.tw[1]);
-    C *S2 = (C *)p.S2 + (int64_t)z * ny * Kx;
-    for (int i = threadIdx.x; i < ny * Kx; i += blockDim.x) {
-        const int kp = i >> lgKx, k = i & (Kx - 1);
+    // all rows of this CTA's columns have arrived
+    cluster.sync();
+    fft_columns_inplace<C, false>(P, lgLy, ldp, lgKC, twy);
+    const RadixPlan rp = radix_plan(lgLy);
+    C *S2 = (C *)p.S2 + (int64_t)z * ny * Kx + c * KC;
+    for (int i = threadIdx.x; i < ny * KC; i += blockDim.x) {
+        const int kp = i >> lgKC, b = i & (KC - 1);
         C v = cmk(T(0), T(0));
-        if (kp < ny / 2)
-            v = r2[kp * ldp + k];
-        else if (kp > ny / 2)
-            v = r2[(Ly - ny + kp) * ldp + k];
-        S2[(int64_t)kp * Kx + k] = v;
+        if (kp != ny / 2) {
+            const int k = kp < ny / 2 ? kp : Ly - ny + kp;
+            v = P[fft_pos(rp, lgLy, k) * ldp + b];
+        }
+        S2[(int64_t)kp * Kx + b] = v;
     }
-    (void)lgPB;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) k_iyx(DevPlan p, int PB, int x0_off, int x1_off) {
-    pdl_trigger();
-    pdl_wait();
+__global__ void __launch_bounds__(256) k_iyx(DevPlan p, int PB) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
     typedef typename VecT<T>::T2 C;
-    typedef typename VecT<T>::T4 T4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
     const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
-    const int ldx = PB + 1, ldp = Kx + 1;
-    const int lgKx = __ffs(Kx) - 1, lgLx = __ffs(Lx) - 1;
-    C *P = (C *)smem_raw;
-    C *Y1 = P + Ly * ldp;
-    C *X0 = (C *)smem_raw + x0_off;
-    const int z = (p.z0 + (int)blockIdx.x) & (p.L[2] - 1);
+    const int c = (int)cluster.block_rank();
+    const int PBc = PB / FUSE_CL, KC = Kx / FUSE_CL;
+    const int ldx = PBc + 1, ldp = KC + 1;
+    const int lgKC = __ffs(KC) - 1, lgPBc = __ffs(PBc) - 1, lgLy = __ffs(Ly) - 1;
+    C *X0 = (C *)smem_raw;
+    C *X1 = X0 + Lx * ldx;
+    C *P = X1 + Lx * ldx;
+    C *twx = P + Ly * ldp;
+    C *twy = twx + Lx;
+    for (int i = threadIdx.x; i < Lx; i += blockDim.x) twx[i] = ((const C *)p.tw[0])[i];
+    for (int i = threadIdx.x; i < Ly; i += blockDim.x) twy[i] = ((const C *)p.tw[1])[i];
+    for (int i = threadIdx.x; i < Lx * ldx; i += blockDim.x) X0[i] = cmk(T(0), T(0));
+    const int z = (p.z0 + (int)blockIdx.x / FUSE_CL) & (p.L[2] - 1);
+    pdl_wait();
     const int2 iv = p.plane_iv[z];
     const int npr = iv.y >> 1;
-    if (npr == 0) return;
-    // plane spectrum, zero padded along y: position y holds mode y (y < ny/2)
-    // or mode y - Ly (y > Ly - ny/2)
-    const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx;
+    const int j0 = c * PBc;
+    const int nj = npr - j0 < 0 ? 0 : (npr - j0 > PBc ? PBc : npr - j0);
+    // this CTA's columns of the plane spectrum at the positions of the
+    // in-place inverse: position q holds mode k = fft_freq(q) (k < ny/2), or
+    // k - Ly (k > Ly - ny/2), zero elsewhere
+    const RadixPlan rp = radix_plan(lgLy);
+    const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx + c * KC;
     pipelined_copy<C>(
-        Ly * Kx,
+        Ly * KC,
         [&](int i) {
-            const int y = i >> lgKx, k = i & (Kx - 1);
+            const int k = fft_freq(rp, lgLy, i >> lgKC), b = i & (KC - 1);
             C v = cmk(T(0), T(0));
-            if (y < ny / 2)
-                v = S2[(int64_t)y * Kx + k];
-            else if (y > Ly - ny / 2)
-                v = S2[(int64_t)(y - Ly + ny) * Kx + k];
+            if (k < ny / 2)
+                v = S2[(int64_t)k * Kx + b];
+            else if (k > Ly - ny / 2)
+                v = S2[(int64_t)(k - Ly + ny) * Kx + b];
             return v;
         },
-        [&](int i, C v) { P[(i >> lgKx) * ldp + (i & (Kx - 1))] = v; });
-    for (int i = threadIdx.x; i < Lx * ldx; i += blockDim.x) X0[i] = cmk(T(0), T(0));
-    __syncthreads();
-    const C *R = fft_columns<C, true>(P, Y1, Ly, ldp, Kx, (const C *)p.tw[1]);
-    C *X1 = x1_off >= 0 ? (C *)smem_raw + x1_off : (R == P ? Y1 : P);
-    // pair j: rows ya (real part) and ya + 1 (imaginary part) of one inverse x transform
-    for (int i = threadIdx.x; i < (npr << lgKx); i += blockDim.x) {
-        const int j = i >> lgKx, k = i & (Kx - 1);
-        const int ya = (iv.x + 2 * j) & (Ly - 1);
-        const C xa = R[ya * ldp + k], xb = R[(ya + 1) * ldp + k];
+        [&](int i, C v) { P[(i >> lgKC) * ldp + (i & (KC - 1))] = v; });
+    // every CTA's X0 is clear before any remote store; P is complete
+    cluster.sync();
+    fft_columns_inplace<C, true>(P, lgLy, ldp, lgKC, twy);
+    // pair jj of the plane, frequency k of this CTA -> column jj % PBc of CTA jj / PBc:
+    // one complex inverse transform carries row ya (real part) and ya + 1 (imaginary part)
+    for (int i = threadIdx.x; i < (npr << lgKC); i += blockDim.x) {
+        const int jj = i >> lgKC, kl = i & (KC - 1);
+        const int k = c * KC + kl;
+        const int ya = (iv.x + 2 * jj) & (Ly - 1);
+        const C xa = P[ya * ldp + kl], xb = P[(ya + 1) * ldp + kl];
+        C *dst = cluster.map_shared_rank(X0, jj >> lgPBc);
+        const int jl = jj & (PBc - 1);
         if (k == 0) {
-            X0[j] = cmk(xa.x, xb.x);
+            dst[jl] = cmk(xa.x, xb.x);
         } else {
-            X0[k * ldx + j] = cmk(xa.x - xb.y, xa.y + xb.x);          // xa + i xb
-            X0[(Lx - k) * ldx + j] = cmk(xa.x + xb.y, xb.x - xa.y);   // conj(xa) + i conj(xb)
+            dst[k * ldx + jl] = cmk(xa.x - xb.y, xa.y + xb.x);          // xa + i xb
+            dst[(Lx - k) * ldx + jl] = cmk(xa.x + xb.y, xb.x - xa.y);   // conj(xa) + i conj(xb)
         }
     }
-    __syncthreads();
-    const C *res = fft_columns<C, true>(X0, X1, Lx, ldx, PB, (const C *)p.tw[0]);
+    // all frequencies of this CTA's pairs have arrived
+    cluster.sync();
+    const C *res = fft_columns<C, true>(X0, X1, Lx, ldx, PBc, twx);
     T *G = (T *)p.gridB + (int64_t)z * Ly * Lx;
     typedef typename VecW<T>::V V;
     constexpr int VW = VecW<T>::W;
     const int nv = Lx / VW, lgnv = __ffs(nv) - 1;
-    for (int i = threadIdx.x; i < (npr << lgnv); i += blockDim.x) {
+    for (int i = threadIdx.x; i < (nj << lgnv); i += blockDim.x) {
         const int j = i >> lgnv, xv = i & (nv - 1);
-        const int ya = (iv.x + 2 * j) & (Ly - 1);
+        const int ya = (iv.x + 2 * (j0 + j)) & (Ly - 1);
         T ra[VW], rb[VW];
 #pragma unroll
         for (int e = 0; e < VW; ++e) {
@@ -708,8 +721,6 @@ __global__ void __launch_bounds__(512) k_iyx(DevPlan p, int PB, int x0_off, int 
         ((V *)(G + (int64_t)ya * Lx))[xv] = VecW<T>::join(ra);
         ((V *)(G + (int64_t)(ya + 1) * Lx))[xv] = VecW<T>::join(rb);
     }
-    (void)lgLx;
-    (void)sizeof(T4);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -788,29 +799,42 @@ template <typename T> static cudaError_t fz_t(const DevPlan &p, cudaStream_t s) 
     return cudaGetLastError();
 }
 
-template <typename T> static cudaError_t fxy_t(const DevPlan &p, cudaStream_t s) {
-    const FusedLayout f = fused_layout(p, p.fuse_pb);
-    const size_t sm = (size_t)f.fxy_total * 2 * sizeof(T);
-    cudaError_t e = prep(k_fxy<T>, sm);
+// shared memory of one CTA of the fused plane passes
+static size_t fused_cta_smem(const DevPlan &p, int PB, size_t ce) {
+    const size_t xb = (size_t)p.L[0] * (PB / FUSE_CL + 1), pb = (size_t)p.L[1] * (p.Kx / FUSE_CL + 1);
+    return (2 * xb + pb + p.L[0] + p.L[1]) * ce;
+}
+
+template <typename K> static cudaError_t launch_cluster(K kern, const DevPlan &p, size_t sm, cudaStream_t s) {
+    cudaError_t e = prep(kern, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
-    { const cudaError_t le = launch_k(k_fxy<T>, p.nz_act, 512, sm, s, p, p.fuse_pb, f.fxy_y1); if (le != cudaSuccess) return le; }
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p.nz_act * FUSE_CL);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = FUSE_CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, kern, p, p.fuse_pb);
+}
+template <typename T> static cudaError_t fxy_t(const DevPlan &p, cudaStream_t s) {
+    return launch_cluster(k_fxy<T>, p, fused_cta_smem(p, p.fuse_pb, 2 * sizeof(T)), s);
 }
 template <typename T> static cudaError_t iyx_t(const DevPlan &p, cudaStream_t s) {
-    const FusedLayout f = fused_layout(p, p.fuse_pb);
-    const size_t sm = (size_t)f.iyx_total * 2 * sizeof(T);
-    cudaError_t e = prep(k_iyx<T>, sm);
-    if (e != cudaSuccess) return e;
-    if (p.nz_act == 0) return cudaSuccess;
-    { const cudaError_t le = launch_k(k_iyx<T>, p.nz_act, 512, sm, s, p, p.fuse_pb, f.iyx_x0, f.iyx_x1); if (le != cudaSuccess) return le; }
-    return cudaGetLastError();
+    return launch_cluster(k_iyx<T>, p, fused_cta_smem(p, p.fuse_pb, 2 * sizeof(T)), s);
 }
 
 size_t fused_plane_smem(const DevPlan &p, int PB) {
-    const FusedLayout f = fused_layout(p, PB);
-    const size_t ce = 2 * (p.prec == 64 ? sizeof(double) : sizeof(float));
-    return (size_t)(f.fxy_total > f.iyx_total ? f.fxy_total : f.iyx_total) * ce;
+    if (PB < FUSE_CL || p.Kx < FUSE_CL) return (size_t)-1;  // not applicable
+    return fused_cta_smem(p, PB, 2 * (p.prec == 64 ? sizeof(double) : sizeof(float)));
 }
 cudaError_t launch_fft_forward_xy(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? fxy_t<double>(p, s) : fxy_t<float>(p, s); }
 cudaError_t launch_fft_inverse_yx(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? iyx_t<double>(p, s) : iyx_t<float>(p, s); }

@@ -944,7 +944,7 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
         // fused plane passes when both fit in shared memory
         int maxp = 0;
         for (const int2 &v : p.plane_iv) maxp = std::max(maxp, v.y / 2);
-        int PB = 1;
+        int PB = 4;  // at least one pair per CTA of the four-CTA cluster
         while (PB < maxp) PB <<= 1;
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p.device);
@@ -1273,6 +1273,8 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
         rec();
         return SLP_OK;
     };
+    cudaEvent_t *tl = concurrent ? ex->timeline : nullptr;
+    if (tl) TRY(cuda_status(cudaEventRecord(tl[0], s), "timeline"));
     rec();
     if (!fuse) TRY(cuda_status(slp::launch_charges(d, kind, d_in, s), "charges"));
     rec();
@@ -1281,9 +1283,11 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
         TRY(cuda_status(cudaEventRecord(ex->fork, s), "fork"));
         TRY(cuda_status(cudaStreamWaitEvent(ex->aux, ex->fork, 0), "fork wait"));
         TRY(near_branch(ex->aux));
+        if (tl) TRY(cuda_status(cudaEventRecord(tl[3], ex->aux), "timeline"));
         TRY(cuda_status(cudaEventRecord(ex->join, ex->aux), "join"));
     }
     TRY(cuda_status(slp::launch_spread(d, fuse ? kind : -1, d_in, s), "spread"));
+    if (tl) TRY(cuda_status(cudaEventRecord(tl[1], s), "timeline"));
     rec();
     if (last <= SLP_STAGE_SPREAD) return SLP_OK;
     // fused plane passes (FX + FY, IY + IX) unless the run stops between them
@@ -1315,6 +1319,7 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
         rec();
     }
     if (last <= SLP_STAGE_IFFT_X) return SLP_OK;
+    if (tl) TRY(cuda_status(cudaEventRecord(tl[2], s), "timeline"));
     if (concurrent) {
         TRY(cuda_status(cudaStreamWaitEvent(s, ex->join, 0), "join wait"));
     } else if (last >= SLP_STAGE_NEAR) {
@@ -1326,6 +1331,7 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
         rec();
     }
     TRY(cuda_status(slp::launch_gather(d, d_phi, s), "gather"));
+    if (tl) TRY(cuda_status(cudaEventRecord(tl[4], s), "timeline"));
     rec();
     return SLP_OK;
 }
@@ -1758,6 +1764,23 @@ slp_status slp_debug_profile(slp_plan_t p, int kind, const void *d_in, void *d_p
         ms[i] = t;
     }
     for (int i = 0; i <= N_STAGE_NAMES; ++i) cudaEventDestroy(ev[i]);
+    return st;
+}
+
+slp_status slp_debug_timeline(slp_plan_t p, int kind, const void *d_in, void *d_phi, void *stream, float *ms) {
+    if (!p || !ms) return fail(SLP_ERR_INVALID_ARG, "NULL argument");
+    if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan");
+    if (kind < 0 || kind > 2 || !d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "bad input");
+    DeviceGuard g(p->device);
+    cudaEvent_t tl[5];
+    for (int i = 0; i < 5; ++i)
+        if (cudaEventCreate(&tl[i]) != cudaSuccess) return fail(SLP_ERR_CUDA, "cudaEventCreate");
+    p->exec.timeline = tl;
+    slp_status st = run_pipeline(*p, kind, d_in, d_phi, (cudaStream_t)stream, SLP_STAGE_NEAR);
+    p->exec.timeline = nullptr;
+    if (st == SLP_OK) st = cuda_status(cudaEventSynchronize(tl[4]), "event sync");
+    for (int i = 1; i < 5 && st == SLP_OK; ++i) st = cuda_status(cudaEventElapsedTime(&ms[i - 1], tl[0], tl[i]), "elapsed");
+    for (int i = 0; i < 5; ++i) cudaEventDestroy(tl[i]);
     return st;
 }
 

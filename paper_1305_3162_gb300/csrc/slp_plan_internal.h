@@ -18,6 +18,9 @@
 struct SlpExec {
     cudaStream_t aux = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
+    // optional timeline (5 events): start, spread done, FFT passes done (on
+    // the caller's stream), near branch done (auxiliary stream), gather done
+    cudaEvent_t *timeline = nullptr;
 };
 cudaError_t slp_exec_create(SlpExec &e);
 void slp_exec_destroy(SlpExec &e);
