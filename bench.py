@@ -147,6 +147,8 @@ def _workload(name):
         return workloads.plate()
     if name == "cube400":
         return workloads.cube_large()
+    if name == "cube100":  # a 512^3 grid: the large-grid kernels at a size ncu can capture
+        return workloads.cube_large(nper=100, grid=(512, 512, 512))
     raise ValueError(name)
 
 
@@ -691,7 +693,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="sphere", choices=["sphere", "cube", "plate", "cube400"])
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "cube", "plate", "cube400", "cube100"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", choices=["plain", "batched", "served"], default="plain",

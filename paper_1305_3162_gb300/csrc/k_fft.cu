@@ -547,6 +547,243 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
     }
 }
 
+// ---------------------------------------------------------------- column engine
+// Column passes with the transform length L = 2^LG fixed at compile time (so
+// all index arithmetic folds) and the stages kept in registers: a block of
+// 8 L/8 threads transforms CB = 8 columns; thread (t, b) (b the column) owns
+// eight elements of column b in every stage, the in-place decimation-in-
+// frequency stages of fft_columns_inplace (radix 8, then 4 or 2 for the
+// remaining bits).  Stage 0 reads its elements from global memory and the
+// last stage writes them back; between stages the elements are exchanged
+// through one shared buffer [L][CB + 1] with one barrier per exchange.  A
+// thread writes back exactly the positions it read, so a stage needs no
+// barrier between its read and its write.
+constexpr int CB = 8;
+
+template <int LG> struct ColShape {
+    static constexpr int L = 1 << LG, S8 = LG / 3, REM = LG - 3 * S8, NS = S8 + (REM ? 1 : 0);
+};
+
+// position of element r of task t in stage S
+template <int LG, int S> __device__ __forceinline__ int col_idx(int t, int r) {
+    typedef ColShape<LG> Sh;
+    if constexpr (S < Sh::S8) {
+        constexpr int lgNs = LG - 3 * S, lgQ = lgNs - 3;
+        const int j = t & ((1 << lgQ) - 1), k0 = (t >> lgQ) << lgNs;
+        return k0 + j + (r << lgQ);
+    } else {
+        return (t << 3) + r;  // the last stage, radix 2^REM: 8 / 2^REM butterflies of consecutive elements
+    }
+}
+
+// frequency at position p after the forward stages
+template <int LG> __device__ __forceinline__ int col_freq(int p) {
+    typedef ColShape<LG> Sh;
+    int k = 0;
+#pragma unroll
+    for (int s = 0; s < Sh::S8; ++s) k |= ((p >> (LG - 3 * (s + 1))) & 7) << (3 * s);
+    if constexpr (Sh::REM > 0) k |= (p & ((1 << Sh::REM) - 1)) << (3 * Sh::S8);
+    return k;
+}
+
+// stage S on the eight elements of task t (forward: DFT then twiddle;
+// inverse: conjugate twiddle then DFT)
+template <typename C, int LG, int S, bool INV> __device__ __forceinline__ void col_stage(C (&v)[8], int t, const C *tw) {
+    typedef ColShape<LG> Sh;
+    if constexpr (S < Sh::S8) {
+        constexpr int lgQ = LG - 3 * S - 3;
+        const int j = t & ((1 << lgQ) - 1);
+        if (INV && j != 0) {
+#pragma unroll
+            for (int r = 1; r < 8; ++r) {
+                C w = tw[((r * j) << (3 * S)) & (Sh::L - 1)];
+                w.y = -w.y;
+                v[r] = cmul(v[r], w);
+            }
+        }
+        dft8<C, INV>(v);
+        if (!INV && j != 0) {
+#pragma unroll
+            for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw[((r * j) << (3 * S)) & (Sh::L - 1)]);
+        }
+    } else if constexpr (Sh::REM == 2) {
+        dft4<C, INV>(v[0], v[1], v[2], v[3]);
+        dft4<C, INV>(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dft2(v[2 * u], v[2 * u + 1]);
+    }
+}
+
+template <typename C, int LG, int S> __device__ __forceinline__ void col_put(C *buf, const C (&v)[8], int t, int b) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) buf[col_idx<LG, S>(t, r) * (CB + 1) + b] = v[r];
+}
+template <typename C, int LG, int S> __device__ __forceinline__ void col_get(const C *buf, C (&v)[8], int t, int b) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = buf[col_idx<LG, S>(t, r) * (CB + 1) + b];
+}
+
+// forward stages S .. NS-1 (the elements of stage S - 1 are in v and are
+// exchanged first); on return v holds the last stage's elements
+template <typename C, int LG, int S> __device__ __forceinline__ void col_forward_from(C *buf, C (&v)[8], int t, int b,
+                                                                                   const C *tw) {
+    if constexpr (S < ColShape<LG>::NS) {
+        col_put<C, LG, S - 1>(buf, v, t, b);
+        __syncthreads();
+        col_get<C, LG, S>(buf, v, t, b);
+        col_stage<C, LG, S, false>(v, t, tw);
+        col_forward_from<C, LG, S + 1>(buf, v, t, b, tw);
+    }
+}
+// inverse stages S .. 0 (v holds the elements of stage S + 1 after its inverse)
+template <typename C, int LG, int S> __device__ __forceinline__ void col_inverse_from(C *buf, C (&v)[8], int t, int b,
+                                                                                   const C *tw) {
+    if constexpr (S >= 0) {
+        col_put<C, LG, S + 1>(buf, v, t, b);
+        __syncthreads();
+        col_get<C, LG, S>(buf, v, t, b);
+        col_stage<C, LG, S, true>(v, t, tw);
+        col_inverse_from<C, LG, S - 1>(buf, v, t, b, tw);
+    }
+}
+
+// FY: plane z, columns kx0 .. kx0 + 8; active rows in, the n_y kept modes out
+template <typename T, int LG>
+__global__ void __launch_bounds__(1 << LG) k_fy_c(DevPlan p) {
+    typedef typename VecT<T>::T2 C;
+    typedef ColShape<LG> Sh;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
+    C *buf = (C *)smem_raw;
+    C *tw = buf + Sh::L * (CB + 1);
+    for (int i = threadIdx.x; i < Sh::L; i += blockDim.x) tw[i] = ((const C *)p.tw[1])[i];
+    const int b = threadIdx.x & (CB - 1), t = threadIdx.x >> 3;
+    const int Kx = p.Kx, ny = p.n[1];
+    const int ntile = Kx / CB;
+    const int zi = blockIdx.x / ntile;
+    const int z = (p.z0 + zi) & (p.L[2] - 1);
+    const int kx0 = (blockIdx.x - zi * ntile) * CB;
+    pdl_wait();
+    const int2 iv = p.plane_iv[z];
+    const C *S1 = (const C *)p.S1 + (int64_t)z * Sh::L * Kx + kx0 + b;
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int y = col_idx<LG, 0>(t, r);
+        v[r] = ((y - iv.x) & (Sh::L - 1)) < iv.y ? S1[(int64_t)y * Kx] : cmk(T(0), T(0));
+    }
+    __syncthreads();  // twiddles
+    col_stage<C, LG, 0, false>(v, t, tw);
+    col_forward_from<C, LG, 1>(buf, v, t, b, tw);
+    C *S2 = (C *)p.S2 + (int64_t)z * ny * Kx + kx0 + b;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int k = col_freq<LG>(col_idx<LG, Sh::NS - 1>(t, r));
+        if (k < ny / 2)
+            S2[(int64_t)k * Kx] = v[r];
+        else if (k > Sh::L - ny / 2)
+            S2[(int64_t)(k - Sh::L + ny) * Kx] = v[r];
+    }
+}
+
+// FZ * D * IZ: row ky', columns kx0 .. kx0 + 8; the last forward stage, the
+// multiply and the first inverse stage share the same registers
+template <typename T, int LG>
+__global__ void __launch_bounds__(1 << LG) k_fz_c(DevPlan p) {
+    typedef typename VecT<T>::T2 C;
+    typedef ColShape<LG> Sh;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
+    C *buf = (C *)smem_raw;
+    C *tw = buf + Sh::L * (CB + 1);
+    for (int i = threadIdx.x; i < Sh::L; i += blockDim.x) tw[i] = ((const C *)p.tw[2])[i];
+    const int b = threadIdx.x & (CB - 1), t = threadIdx.x >> 3;
+    const int Kx = p.Kx, ny = p.n[1], nz = p.n[2];
+    const int ntile = Kx / CB;
+    const int kp = blockIdx.x / ntile;
+    const int kx0 = (blockIdx.x - kp * ntile) * CB;
+    const int z0 = p.z0, nza = p.nz_act;
+    const int64_t zs = (int64_t)ny * Kx;
+    pdl_wait();
+    C *S2 = (C *)p.S2 + (int64_t)kp * Kx + kx0 + b;
+    if (kp == ny / 2) {  // Nyquist row in y: dropped
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int z = col_idx<LG, 0>(t, r);
+            if (((z - z0) & (Sh::L - 1)) < nza) S2[z * zs] = cmk(T(0), T(0));
+        }
+        return;
+    }
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int z = col_idx<LG, 0>(t, r);
+        v[r] = ((z - z0) & (Sh::L - 1)) < nza ? S2[z * zs] : cmk(T(0), T(0));
+    }
+    __syncthreads();  // twiddles
+    col_stage<C, LG, 0, false>(v, t, tw);
+    col_forward_from<C, LG, 1>(buf, v, t, b, tw);
+    const int aky = kp < ny / 2 ? kp : ny - kp;
+    const T *D = (const T *)p.Dtab + (int64_t)aky * Kx + kx0 + b;
+    const int64_t dz = (int64_t)(ny / 2) * Kx;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int kz = col_freq<LG>(col_idx<LG, Sh::NS - 1>(t, r));
+        const int akz = kz < Sh::L / 2 ? kz : Sh::L - kz;
+        v[r] = akz < nz / 2 ? cscale(v[r], D[akz * dz]) : cmk(T(0), T(0));
+    }
+    col_stage<C, LG, Sh::NS - 1, true>(v, t, tw);
+    col_inverse_from<C, LG, Sh::NS - 2>(buf, v, t, b, tw);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int z = col_idx<LG, 0>(t, r);
+        if (((z - z0) & (Sh::L - 1)) < nza) S2[z * zs] = v[r];
+    }
+}
+
+// IY: plane z, columns kx0 .. kx0 + 8; the kept modes in (zero padded),
+// active rows out
+template <typename T, int LG>
+__global__ void __launch_bounds__(1 << LG) k_iy_c(DevPlan p) {
+    typedef typename VecT<T>::T2 C;
+    typedef ColShape<LG> Sh;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    pdl_trigger();
+    C *buf = (C *)smem_raw;
+    C *tw = buf + Sh::L * (CB + 1);
+    for (int i = threadIdx.x; i < Sh::L; i += blockDim.x) tw[i] = ((const C *)p.tw[1])[i];
+    const int b = threadIdx.x & (CB - 1), t = threadIdx.x >> 3;
+    const int Kx = p.Kx, ny = p.n[1];
+    const int ntile = Kx / CB;
+    const int zi = blockIdx.x / ntile;
+    const int z = (p.z0 + zi) & (p.L[2] - 1);
+    const int kx0 = (blockIdx.x - zi * ntile) * CB;
+    pdl_wait();
+    const int2 iv = p.plane_iv[z];
+    const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx + kx0 + b;
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int k = col_freq<LG>(col_idx<LG, Sh::NS - 1>(t, r));
+        C x = cmk(T(0), T(0));
+        if (k < ny / 2)
+            x = S2[(int64_t)k * Kx];
+        else if (k > Sh::L - ny / 2)
+            x = S2[(int64_t)(k - Sh::L + ny) * Kx];
+        v[r] = x;
+    }
+    __syncthreads();  // twiddles
+    col_stage<C, LG, Sh::NS - 1, true>(v, t, tw);
+    col_inverse_from<C, LG, Sh::NS - 2>(buf, v, t, b, tw);
+    C *S1 = (C *)p.S1 + (int64_t)z * Sh::L * Kx + kx0 + b;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int y = col_idx<LG, 0>(t, r);
+        if (((y - iv.x) & (Sh::L - 1)) < iv.y) S1[(int64_t)y * Kx] = v[r];
+    }
+}
+
 // ---------------------------------------------------------------- fused plane passes
 // FX + FY and IY + IX of one active z plane run in a thread-block cluster of
 // FUSE_CL CTAs that exchange the plane spectrum through distributed shared
@@ -768,7 +1005,32 @@ template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) 
     { const cudaError_t le = launch_k(k_ix<T>, (p.n_row_pairs + PB - 1) / PB, 256, sm, s, p, PB); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
+// column engine launch: L = 2^lg threads, 8 columns per block
+#define SLP_COL_DISPATCH(KERN, T, LGV, NBLK, SM, S)                                                      \
+    switch (LGV) {                                                                                       \
+        case 5: { cudaError_t e_ = prep(KERN<T, 5>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 5>, NBLK, 32, SM, S, p); }                                     \
+        case 6: { cudaError_t e_ = prep(KERN<T, 6>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 6>, NBLK, 64, SM, S, p); }                                     \
+        case 7: { cudaError_t e_ = prep(KERN<T, 7>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 7>, NBLK, 128, SM, S, p); }                                    \
+        case 8: { cudaError_t e_ = prep(KERN<T, 8>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 8>, NBLK, 256, SM, S, p); }                                    \
+        case 9: { cudaError_t e_ = prep(KERN<T, 9>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 9>, NBLK, 512, SM, S, p); }                                    \
+        case 10: { cudaError_t e_ = prep(KERN<T, 10>, SM); if (e_ != cudaSuccess) return e_;             \
+                   return launch_k(KERN<T, 10>, NBLK, 1024, SM, S, p); }                                 \
+    }
+// the engine applies for 32 <= L <= 1024 and at least 8 stored x frequencies
+static bool col_engine_ok(const DevPlan &p, int L) { return L >= 32 && L <= 1024 && p.Kx >= CB; }
+
 template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) {
+    if (col_engine_ok(p, p.L[1])) {
+        if (p.nz_act == 0) return cudaSuccess;
+        const size_t sm = ((size_t)p.L[1] * (CB + 1) + p.L[1]) * 2 * sizeof(T);
+        const unsigned nb = (unsigned)(p.nz_act * (p.Kx / CB));
+        SLP_COL_DISPATCH(k_fy_c, T, __builtin_ctz(p.L[1]), nb, sm, s)
+    }
     const size_t ce = 2 * sizeof(T);
     const int B = col_batch(p.L[1], p.Kx, ce, p.nz_act);
     const size_t sm = ((size_t)p.L[1] * (B + 1) + p.L[1]) * ce;
@@ -779,6 +1041,12 @@ template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) 
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) {
+    if (col_engine_ok(p, p.L[1])) {
+        if (p.nz_act == 0) return cudaSuccess;
+        const size_t sm = ((size_t)p.L[1] * (CB + 1) + p.L[1]) * 2 * sizeof(T);
+        const unsigned nb = (unsigned)(p.nz_act * (p.Kx / CB));
+        SLP_COL_DISPATCH(k_iy_c, T, __builtin_ctz(p.L[1]), nb, sm, s)
+    }
     const size_t ce = 2 * sizeof(T);
     const int B = col_batch(p.L[1], p.Kx, ce, p.nz_act);
     const size_t sm = ((size_t)p.L[1] * (B + 1) + p.L[1]) * ce;
@@ -789,6 +1057,12 @@ template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) 
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t fz_t(const DevPlan &p, cudaStream_t s) {
+    if (col_engine_ok(p, p.L[2])) {
+        if (p.nz_act == 0) return cudaSuccess;
+        const size_t sm = ((size_t)p.L[2] * (CB + 1) + p.L[2]) * 2 * sizeof(T);
+        const unsigned nb = (unsigned)(p.n[1] * (p.Kx / CB));
+        SLP_COL_DISPATCH(k_fz_c, T, __builtin_ctz(p.L[2]), nb, sm, s)
+    }
     const size_t ce = 2 * sizeof(T);
     const int B = col_batch(p.L[2], p.Kx, ce, p.n[1]);
     const size_t sm = ((size_t)p.L[2] * (B + 1) + p.L[2]) * ce;

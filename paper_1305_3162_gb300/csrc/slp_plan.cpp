@@ -1238,9 +1238,11 @@ const int N_STAGE_NAMES = 10;
 //   serial (ev != NULL, or ex == NULL): charges, spread, 5 FFT passes, near
 //     field into phi_part, gather (far field + phi_part) on s; with ev,
 //     ev[i] is recorded before kernel slot i and ev[i + 1] after it;
-//   concurrent (ex != NULL, no ev): after the charges the near field runs on
-//     ex->aux while the spread and FFT passes run on s; s waits for it
-//     before the gather.
+//   concurrent (ex != NULL, no ev): the near field runs on ex->aux (lowest
+//     priority) while the spread, FFT passes and gather run on ex->main
+//     (highest priority, so the latency-bound FFT blocks are dispatched ahead
+//     of pending near-field blocks); both fork from s, the gather waits for
+//     the near field, and s waits for the gather.
 slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *d_in, void *d_phi,
                         cudaStream_t s, int last, cudaEvent_t *ev, SlpExec *ex) {
     int k = 0;
@@ -1279,9 +1281,12 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
     if (!fuse) TRY(cuda_status(slp::launch_charges(d, kind, d_in, s), "charges"));
     rec();
     if (last <= SLP_STAGE_CHARGES) return SLP_OK;
+    cudaStream_t caller = s;
     if (concurrent) {
         TRY(cuda_status(cudaEventRecord(ex->fork, s), "fork"));
         TRY(cuda_status(cudaStreamWaitEvent(ex->aux, ex->fork, 0), "fork wait"));
+        TRY(cuda_status(cudaStreamWaitEvent(ex->main, ex->fork, 0), "fork wait"));
+        s = ex->main;
         TRY(near_branch(ex->aux));
         if (tl) TRY(cuda_status(cudaEventRecord(tl[3], ex->aux), "timeline"));
         TRY(cuda_status(cudaEventRecord(ex->join, ex->aux), "join"));
@@ -1333,6 +1338,10 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
     TRY(cuda_status(slp::launch_gather(d, d_phi, s), "gather"));
     if (tl) TRY(cuda_status(cudaEventRecord(tl[4], s), "timeline"));
     rec();
+    if (concurrent) {
+        TRY(cuda_status(cudaEventRecord(ex->done, s), "done"));
+        TRY(cuda_status(cudaStreamWaitEvent(caller, ex->done, 0), "done wait"));
+    }
     return SLP_OK;
 }
 
@@ -1374,15 +1383,21 @@ slp_status slp_run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, cons
 }
 
 cudaError_t slp_exec_create(SlpExec &e) {
-    cudaError_t r = cudaStreamCreateWithFlags(&e.aux, cudaStreamNonBlocking);
+    int least = 0, greatest = 0;
+    cudaError_t r = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (r == cudaSuccess) r = cudaStreamCreateWithPriority(&e.aux, cudaStreamNonBlocking, least);
+    if (r == cudaSuccess) r = cudaStreamCreateWithPriority(&e.main, cudaStreamNonBlocking, greatest);
     if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e.fork, cudaEventDisableTiming);
     if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e.join, cudaEventDisableTiming);
+    if (r == cudaSuccess) r = cudaEventCreateWithFlags(&e.done, cudaEventDisableTiming);
     return r;
 }
 
 void slp_exec_destroy(SlpExec &e) {
+    if (e.done) cudaEventDestroy(e.done);
     if (e.join) cudaEventDestroy(e.join);
     if (e.fork) cudaEventDestroy(e.fork);
+    if (e.main) cudaStreamDestroy(e.main);
     if (e.aux) cudaStreamDestroy(e.aux);
     e = SlpExec();
 }

@@ -17,7 +17,11 @@
 // caller's stream.
 struct SlpExec {
     cudaStream_t aux = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
+    // the spread / FFT / gather chain runs on `main` (highest priority), so
+    // its blocks are dispatched ahead of the near-field branch's when both
+    // are pending; `done` returns the chain to the caller's stream
+    cudaStream_t main = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, done = nullptr;
     // optional timeline (5 events): start, spread done, FFT passes done (on
     // the caller's stream), near branch done (auxiliary stream), gather done
     cudaEvent_t *timeline = nullptr;
