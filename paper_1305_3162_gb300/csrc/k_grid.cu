@@ -505,7 +505,6 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spr
 // the spread), together with the item's target coordinates, permutation,
 // near-field parts and window values; then one warp per target sums its
 // (2M)^3 window box, lanes over the (y, z) rows of the box.
-constexpr int GATHER_CHUNK = 32;  // targets per gather item (set by the plan)
 
 template <typename T, int M, int TS>
 __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) {
@@ -703,7 +702,7 @@ static cudaError_t spread_t(const DevPlan &p, int fused_kind, const void *in, cu
     return cudaErrorInvalidValue;
 }
 template <typename T, int M> static cudaError_t gather_t(const DevPlan &p, void *phi, cudaStream_t s) {
-    switch (p.TS) {
+    switch (p.TSg) {
         case 2: return gather_mt<T, M, 2>(p, phi, s);
         case 4: return gather_mt<T, M, 4>(p, phi, s);
         case 8: return gather_mt<T, M, 8>(p, phi, s);

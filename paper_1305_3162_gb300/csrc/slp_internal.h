@@ -17,6 +17,10 @@ struct TileItem {
     int pad0, pad1, pad2;
 };
 
+// Targets per gather item (the plan splits target tiles into items of at
+// most this many; the gather kernel stages one item per block).
+constexpr int GATHER_CHUNK = 64;
+
 // Work item of the near-field kernel: up to 32 sorted targets
 // [tbegin, tbegin + tcount) and a slice [rbegin, rend) of the range list,
 // each range a contiguous run of sorted sources.
@@ -34,7 +38,8 @@ struct DevPlan {
     int n[3];           // modes per axis, L = 2 n
     int Kx;             // stored x frequencies: n_x / 2
     int m;              // window half-width
-    int TS, TE;         // tile cells per axis; tile extent with halo TS + 2m - 1
+    int TS, TE;         // source tile cells per axis; tile extent with halo TS + 2m - 1
+    int TSg;            // target (gather) tile cells per axis
     double h[3];        // physical grid spacing P_q / L_q
     double beta;        // Kaiser-Bessel shape b * m, b = pi (2 - 1/alpha)
     const void *wcoef;  // FP32 window polynomials: [2m][wdeg + 1], coefficient k of f^k for point i

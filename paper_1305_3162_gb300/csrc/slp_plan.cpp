@@ -436,6 +436,9 @@ slp_status choose_parameters(slp_plan_s &p) {
     const size_t esz = p.prec == 64 ? 8 : 4;
     p.TS = 4;
     while (p.TS > 2 && std::pow((double)(p.TS + 2 * p.m + 3), 3) * esz > 40 * 1024) p.TS /= 2;
+    // targets: larger tiles (fewer gather items, each tile load shared by more targets)
+    p.TSg = 8;
+    while (p.TSg > 2 && std::pow((double)(p.TSg + 2 * p.m + 3), 3) * esz > 40 * 1024) p.TSg /= 2;
     p.TE = p.TS + 2 * p.m - 1;
     return SLP_OK;
 }
@@ -464,16 +467,16 @@ void grid_coords(const slp_plan_s &p, const double *x, double *g, int &cx, int &
 }
 
 // sort points by (tile, Morton order inside the tile); fills perm and grid[.][4]
-void sort_points(const slp_plan_s &p, const double *pts, int64_t n, std::vector<int32_t> &perm,
+void sort_points(const slp_plan_s &p, const double *pts, int64_t n, int ts, std::vector<int32_t> &perm,
                  std::vector<double> &grid, std::vector<uint64_t> &keys_sorted) {
     std::vector<double> g(4 * n);
     std::vector<uint64_t> key(n);
-    const int ntx = (p.L[0] + p.TS - 1) / p.TS, nty = (p.L[1] + p.TS - 1) / p.TS;
+    const int ntx = (p.L[0] + ts - 1) / ts, nty = (p.L[1] + ts - 1) / ts;
     for (int64_t i = 0; i < n; ++i) {
         int cx, cy, cz;
         grid_coords(p, pts + 3 * i, &g[4 * i], cx, cy, cz);
-        const uint64_t tile = ((uint64_t)(cz / p.TS) * nty + (cy / p.TS)) * ntx + (cx / p.TS);
-        const uint32_t mort = morton3(cx % p.TS, cy % p.TS, cz % p.TS);
+        const uint64_t tile = ((uint64_t)(cz / ts) * nty + (cy / ts)) * ntx + (cx / ts);
+        const uint32_t mort = morton3(cx % ts, cy % ts, cz % ts);
         key[i] = (tile << 32) | mort;
     }
     perm.resize(n);
@@ -487,8 +490,8 @@ void sort_points(const slp_plan_s &p, const double *pts, int64_t n, std::vector<
     }
 }
 
-void tile_items(const slp_plan_s &p, const std::vector<double> &grid, const std::vector<uint64_t> &keys, int64_t n,
-                int chunk, std::vector<slp::TileItem> &items) {
+void tile_items(const std::vector<double> &grid, const std::vector<uint64_t> &keys, int64_t n, int ts, int chunk,
+                std::vector<slp::TileItem> &items) {
     items.clear();
     int64_t i = 0;
     while (i < n) {
@@ -499,9 +502,9 @@ void tile_items(const slp_plan_s &p, const std::vector<double> &grid, const std:
         const int cx = packed & 1023, cy = (packed >> 10) & 1023, cz = (packed >> 20) & 1023;
         for (int64_t b = i; b < j; b += chunk) {
             slp::TileItem it;
-            it.c0x = cx / p.TS * p.TS;
-            it.c0y = cy / p.TS * p.TS;
-            it.c0z = cz / p.TS * p.TS;
+            it.c0x = cx / ts * ts;
+            it.c0y = cy / ts * ts;
+            it.c0z = cz / ts * ts;
             it.begin = (int)b;
             it.end = (int)std::min<int64_t>(j, b + chunk);
             it.pad0 = it.pad1 = it.pad2 = 0;
@@ -816,6 +819,7 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     d.Kx = p.n[0] / 2;
     d.m = p.m;
     d.TS = p.TS;
+    d.TSg = p.TSg;
     d.TE = p.TE;
     d.beta = KB_B * p.m;
     {
@@ -1506,15 +1510,15 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
         return st;
     }
     std::vector<uint64_t> skeys, tkeys;
-    sort_points(*p, p->y.data(), p->Q, p->src_perm, p->src_grid, skeys);
-    sort_points(*p, p->V.data(), p->N, p->tgt_perm, p->tgt_grid, tkeys);
+    sort_points(*p, p->y.data(), p->Q, p->TS, p->src_perm, p->src_grid, skeys);
+    sort_points(*p, p->V.data(), p->N, p->TSg, p->tgt_perm, p->tgt_grid, tkeys);
     {
         // spread chunk: about four items per SM, 128..1024 sources, a multiple of 32
         int64_t ch = (p->Q + 152 * 4 - 1) / (152 * 4);
         ch = std::max<int64_t>(128, std::min<int64_t>(1024, (ch + 31) / 32 * 32));
-        tile_items(*p, p->src_grid, skeys, p->Q, (int)ch, p->spread_items);
+        tile_items(p->src_grid, skeys, p->Q, p->TS, (int)ch, p->spread_items);
     }
-    tile_items(*p, p->tgt_grid, tkeys, p->N, 32, p->gather_items);
+    tile_items(p->tgt_grid, tkeys, p->N, p->TSg, slp::GATHER_CHUNK, p->gather_items);
     // largest items first: blocks are dispatched in index order, so this
     // schedules the long items early and the short ones fill the tail
     auto by_size = [](const slp::TileItem &a, const slp::TileItem &b) { return a.end - a.begin > b.end - b.begin; };
