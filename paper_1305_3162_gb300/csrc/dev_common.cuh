@@ -100,11 +100,14 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 }
 
 // Programmatic dependent launch (sm_90 and later).  Every evaluation kernel
-// calls pdl_trigger() first, so the next kernel of the stream may be
-// scheduled while this one runs, and pdl_wait() before it reads or writes
-// any global memory other than plan constants: the wait returns once the
-// previous kernel of the stream has completed and its writes are visible
-// (immediately when the kernel was launched without the attribute).
+// calls pdl_wait() before it reads or writes any global memory other than
+// plan constants (the wait returns once the previous kernel of the stream has
+// completed and its writes are visible; at once when the kernel was launched
+// without the attribute), and pdl_trigger() right after it, so the next
+// kernel of the stream may be scheduled and run its prologue while this one
+// works.  Triggering only after the wait keeps at most one waiting kernel
+// resident: triggering before it would let the whole chain's blocks occupy
+// the SMs while they wait, starving concurrent work.
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 

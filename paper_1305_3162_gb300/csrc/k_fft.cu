@@ -250,7 +250,6 @@ __device__ void fft_columns_inplace(C *buf, int lgL, int ld, int lgB, const C *_
 // PB row pairs per CTA; pair pr covers rows y0 = 2*(pr % (Ly/2)) and y0+1 of plane z.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
-    pdl_trigger();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx;
@@ -262,6 +261,7 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     C *stw = b1 + Lx * ld;
     for (int i = threadIdx.x; i < Lx; i += blockDim.x) stw[i] = ((const C *)p.tw[0])[i];
     pdl_wait();
+    pdl_trigger();
     const int npairs = p.n_row_pairs;
     const int pr0 = blockIdx.x * PB;
     T *A = (T *)p.gridA;
@@ -325,7 +325,6 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_trigger();
     const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
     const int ld = B + 1;
     const int lgB = __ffs(B) - 1, lgLy = __ffs(Ly) - 1;
@@ -334,6 +333,7 @@ __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
     C *stw = buf + Ly * ld;
     for (int i = threadIdx.x; i < Ly; i += blockDim.x) stw[i] = ((const C *)p.tw[1])[i];
     pdl_wait();
+    pdl_trigger();
     const int ntile = Kx / B;
     const int zi = blockIdx.x / ntile;
     const int z = (p.z0 + zi) & (p.L[2] - 1);
@@ -372,7 +372,6 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_trigger();
     const int Lz = p.L[2], Kx = p.Kx, ny = p.n[1], nz = p.n[2];
     const int ld = B + 1;
     const int lgB = __ffs(B) - 1, lgLz = __ffs(Lz) - 1;
@@ -381,6 +380,7 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
     C *stw = buf + Lz * ld;
     for (int i = threadIdx.x; i < Lz; i += blockDim.x) stw[i] = ((const C *)p.tw[2])[i];
     pdl_wait();
+    pdl_trigger();
     const int ntile = Kx / B;
     const int kp = blockIdx.x / ntile;
     const int kx0 = (blockIdx.x - kp * ntile) * B;
@@ -432,7 +432,6 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_trigger();
     const int Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
     const int ld = B + 1;
     const int lgB = __ffs(B) - 1, lgLy = __ffs(Ly) - 1;
@@ -441,6 +440,7 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
     C *stw = buf + Ly * ld;
     for (int i = threadIdx.x; i < Ly; i += blockDim.x) stw[i] = ((const C *)p.tw[1])[i];
     pdl_wait();
+    pdl_trigger();
     const int ntile = Kx / B;
     const int zi = blockIdx.x / ntile;
     const int z = (p.z0 + zi) & (p.L[2] - 1);
@@ -474,7 +474,6 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
 // ---------------------------------------------------------------- IX
 template <typename T>
 __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
-    pdl_trigger();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx;
@@ -489,6 +488,7 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
     const int pr0 = blockIdx.x * PB;
     for (int i = threadIdx.x; i < PB * Lx; i += blockDim.x) b0[(i & (Lx - 1)) * ld + (i >> lgLx)] = cmk(T(0), T(0));
     pdl_wait();
+    pdl_trigger();
     __syncthreads();
     const C *S1 = (const C *)p.S1;
     typedef typename VecT<T>::T4 T4;  // (xa, xb) of one mode, loaded together
@@ -654,7 +654,6 @@ __global__ void __launch_bounds__(1 << LG) k_fy_c(DevPlan p) {
     typedef typename VecT<T>::T2 C;
     typedef ColShape<LG> Sh;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_trigger();
     C *buf = (C *)smem_raw;
     C *tw = buf + Sh::L * (CB + 1);
     for (int i = threadIdx.x; i < Sh::L; i += blockDim.x) tw[i] = ((const C *)p.tw[1])[i];
@@ -665,6 +664,7 @@ __global__ void __launch_bounds__(1 << LG) k_fy_c(DevPlan p) {
     const int z = (p.z0 + zi) & (p.L[2] - 1);
     const int kx0 = (blockIdx.x - zi * ntile) * CB;
     pdl_wait();
+    pdl_trigger();
     const int2 iv = p.plane_iv[z];
     const C *S1 = (const C *)p.S1 + (int64_t)z * Sh::L * Kx + kx0 + b;
     C v[8];
@@ -694,7 +694,6 @@ __global__ void __launch_bounds__(1 << LG) k_fz_c(DevPlan p) {
     typedef typename VecT<T>::T2 C;
     typedef ColShape<LG> Sh;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_trigger();
     C *buf = (C *)smem_raw;
     C *tw = buf + Sh::L * (CB + 1);
     for (int i = threadIdx.x; i < Sh::L; i += blockDim.x) tw[i] = ((const C *)p.tw[2])[i];
@@ -706,6 +705,7 @@ __global__ void __launch_bounds__(1 << LG) k_fz_c(DevPlan p) {
     const int z0 = p.z0, nza = p.nz_act;
     const int64_t zs = (int64_t)ny * Kx;
     pdl_wait();
+    pdl_trigger();
     C *S2 = (C *)p.S2 + (int64_t)kp * Kx + kx0 + b;
     if (kp == ny / 2) {  // Nyquist row in y: dropped
 #pragma unroll
@@ -749,7 +749,6 @@ __global__ void __launch_bounds__(1 << LG) k_iy_c(DevPlan p) {
     typedef typename VecT<T>::T2 C;
     typedef ColShape<LG> Sh;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_trigger();
     C *buf = (C *)smem_raw;
     C *tw = buf + Sh::L * (CB + 1);
     for (int i = threadIdx.x; i < Sh::L; i += blockDim.x) tw[i] = ((const C *)p.tw[1])[i];
@@ -760,6 +759,7 @@ __global__ void __launch_bounds__(1 << LG) k_iy_c(DevPlan p) {
     const int z = (p.z0 + zi) & (p.L[2] - 1);
     const int kx0 = (blockIdx.x - zi * ntile) * CB;
     pdl_wait();
+    pdl_trigger();
     const int2 iv = p.plane_iv[z];
     const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx + kx0 + b;
     C v[8];
@@ -802,7 +802,6 @@ __global__ void __launch_bounds__(256) k_fxy(DevPlan p, int PB) {
     cg::cluster_group cluster = cg::this_cluster();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_trigger();
     const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
     const int c = (int)cluster.block_rank();
     const int PBc = PB / FUSE_CL, KC = Kx / FUSE_CL;
@@ -818,6 +817,7 @@ __global__ void __launch_bounds__(256) k_fxy(DevPlan p, int PB) {
     for (int i = threadIdx.x; i < Ly * ldp; i += blockDim.x) P[i] = cmk(T(0), T(0));
     const int z = (p.z0 + (int)blockIdx.x / FUSE_CL) & (p.L[2] - 1);
     pdl_wait();
+    pdl_trigger();
     const int2 iv = p.plane_iv[z];
     const int npr = iv.y >> 1;
     const int j0 = c * PBc;
@@ -882,7 +882,6 @@ __global__ void __launch_bounds__(256) k_iyx(DevPlan p, int PB) {
     cg::cluster_group cluster = cg::this_cluster();
     typedef typename VecT<T>::T2 C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    pdl_trigger();
     const int Lx = p.L[0], Ly = p.L[1], Kx = p.Kx, ny = p.n[1];
     const int c = (int)cluster.block_rank();
     const int PBc = PB / FUSE_CL, KC = Kx / FUSE_CL;
@@ -898,6 +897,7 @@ __global__ void __launch_bounds__(256) k_iyx(DevPlan p, int PB) {
     for (int i = threadIdx.x; i < Lx * ldx; i += blockDim.x) X0[i] = cmk(T(0), T(0));
     const int z = (p.z0 + (int)blockIdx.x / FUSE_CL) & (p.L[2] - 1);
     pdl_wait();
+    pdl_trigger();
     const int2 iv = p.plane_iv[z];
     const int npr = iv.y >> 1;
     const int j0 = c * PBc;
@@ -985,6 +985,25 @@ template <typename K> static cudaError_t prep(K kern, size_t sm) {
     return cudaSuccess;
 }
 
+// column engine launch: L = 2^lg threads, 8 columns per block
+#define SLP_COL_DISPATCH(KERN, T, LGV, NBLK, SM, S)                                                      \
+    switch (LGV) {                                                                                       \
+        case 5: { cudaError_t e_ = prep(KERN<T, 5>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 5>, NBLK, 32, SM, S, p); }                                     \
+        case 6: { cudaError_t e_ = prep(KERN<T, 6>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 6>, NBLK, 64, SM, S, p); }                                     \
+        case 7: { cudaError_t e_ = prep(KERN<T, 7>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 7>, NBLK, 128, SM, S, p); }                                    \
+        case 8: { cudaError_t e_ = prep(KERN<T, 8>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 8>, NBLK, 256, SM, S, p); }                                    \
+        case 9: { cudaError_t e_ = prep(KERN<T, 9>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 9>, NBLK, 512, SM, S, p); }                                    \
+        case 10: { cudaError_t e_ = prep(KERN<T, 10>, SM); if (e_ != cudaSuccess) return e_;             \
+                   return launch_k(KERN<T, 10>, NBLK, 1024, SM, S, p); }                                 \
+    }
+// the engine applies for 32 <= L <= 1024 and at least 8 stored x frequencies
+static bool col_engine_ok(const DevPlan &p, int L) { return L >= 32 && L <= 1024 && p.Kx >= CB; }
+
 template <typename T> static cudaError_t fx_t(const DevPlan &p, cudaStream_t s) {
     const size_t ce = 2 * sizeof(T);
     const int PB = row_batch(p.L[0], ce);
@@ -1005,25 +1024,6 @@ template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) 
     { const cudaError_t le = launch_k(k_ix<T>, (p.n_row_pairs + PB - 1) / PB, 256, sm, s, p, PB); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
-// column engine launch: L = 2^lg threads, 8 columns per block
-#define SLP_COL_DISPATCH(KERN, T, LGV, NBLK, SM, S)                                                      \
-    switch (LGV) {                                                                                       \
-        case 5: { cudaError_t e_ = prep(KERN<T, 5>, SM); if (e_ != cudaSuccess) return e_;               \
-                  return launch_k(KERN<T, 5>, NBLK, 32, SM, S, p); }                                     \
-        case 6: { cudaError_t e_ = prep(KERN<T, 6>, SM); if (e_ != cudaSuccess) return e_;               \
-                  return launch_k(KERN<T, 6>, NBLK, 64, SM, S, p); }                                     \
-        case 7: { cudaError_t e_ = prep(KERN<T, 7>, SM); if (e_ != cudaSuccess) return e_;               \
-                  return launch_k(KERN<T, 7>, NBLK, 128, SM, S, p); }                                    \
-        case 8: { cudaError_t e_ = prep(KERN<T, 8>, SM); if (e_ != cudaSuccess) return e_;               \
-                  return launch_k(KERN<T, 8>, NBLK, 256, SM, S, p); }                                    \
-        case 9: { cudaError_t e_ = prep(KERN<T, 9>, SM); if (e_ != cudaSuccess) return e_;               \
-                  return launch_k(KERN<T, 9>, NBLK, 512, SM, S, p); }                                    \
-        case 10: { cudaError_t e_ = prep(KERN<T, 10>, SM); if (e_ != cudaSuccess) return e_;             \
-                   return launch_k(KERN<T, 10>, NBLK, 1024, SM, S, p); }                                 \
-    }
-// the engine applies for 32 <= L <= 1024 and at least 8 stored x frequencies
-static bool col_engine_ok(const DevPlan &p, int L) { return L >= 32 && L <= 1024 && p.Kx >= CB; }
-
 template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) {
     if (col_engine_ok(p, p.L[1])) {
         if (p.nz_act == 0) return cudaSuccess;

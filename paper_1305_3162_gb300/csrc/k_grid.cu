@@ -21,8 +21,8 @@ namespace slp {
 // precomputed near-field product reads it coalesced.
 template <typename T>
 __global__ void __launch_bounds__(256) k_nodal_prep(DevPlan p, const T *__restrict__ in) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     typedef typename VecT<T>::T4 T4;
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= p.N) return;
@@ -64,8 +64,8 @@ __device__ __forceinline__ T source_charge(const DevPlan &p, int64_t k, int kind
 // qbuf[k] = w_k * sigma_k in sorted source order.
 template <typename T>
 __global__ void __launch_bounds__(256) k_charges(DevPlan p, int kind, const T *__restrict__ in) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.Q) return;
     ((T *)p.qbuf)[k] = source_charge<T>(p, k, kind, in);
@@ -130,8 +130,8 @@ __device__ __forceinline__ void window_values(double *wv, double fx, double fy, 
 // the row does not wrap around the periodic grid.
 template <typename T, int M, int TS>
 __global__ void __launch_bounds__(256) k_spread(DevPlan p, int fused_kind, const T *__restrict__ in) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     typedef typename VecT<T>::T4 T4;
     typedef TileGeom<M, TS> G;
     constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO, XE = G::XE;
@@ -304,7 +304,6 @@ template <typename T, int M, int TS> struct SpreadSmem {
 
 template <typename T, int M, int TS>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spread_groups(DevPlan p, int fused_kind, const T *__restrict__ in) {
-    pdl_trigger();
     typedef typename VecT<T>::T4 T4;
     typedef TileGeomG<M, TS> G;
     typedef SpreadSmem<T, M, TS> SM;
@@ -343,6 +342,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spr
     const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
     // charges and grid A may be the previous kernel's output
     pdl_wait();
+    pdl_trigger();
     {
         const T4 *src = (const T4 *)p.src_grid + it.begin;
         const T *qb = (const T *)p.qbuf + it.begin;
@@ -508,8 +508,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spr
 
 template <typename T, int M, int TS>
 __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     typedef typename VecT<T>::T4 T4;
     typedef TileGeom<M, TS> G;
     constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO;
@@ -640,8 +640,8 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
 
 // ---------------------------------------------------------------- zero
 __global__ void k_zero4(float4 *p, int64_t n4) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }

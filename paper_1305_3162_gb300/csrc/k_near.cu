@@ -40,8 +40,8 @@ template <typename T> __device__ __forceinline__ T sep_factor(const T *__restric
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(NEAR_WARPS * 32) k_near(DevPlan p) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     typedef typename VecT<T>::T4 T4;
     __shared__ T4 sg[NEAR_WARPS][32];
     __shared__ T sq[NEAR_WARPS][32];
@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) k_near(DevPlan p) {
 // partials in item order.  blk_items[b] = first item of block b (CSR).
 template <typename T>
 __global__ void k_near_reduce(DevPlan p, const int *__restrict__ blk_first, int nblk) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (b >= nblk) return;
@@ -260,8 +260,8 @@ __device__ __forceinline__ double4 ld_stream(const double4 *p) {
 
 template <typename T>
 __global__ void __launch_bounds__(128) k_near_matrix(DevPlan p) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     typedef typename VecT<T>::T4 T4;
     constexpr int U = 8;  // independent 16-byte loads in flight per lane
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
