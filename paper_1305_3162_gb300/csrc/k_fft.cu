@@ -559,6 +559,10 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
 // thread writes back exactly the positions it read, so a stage needs no
 // barrier between its read and its write.
 constexpr int CB = 8;
+// Register budget: blocks of L threads are asked to fit 1024 / L per SM (at
+// most 64 registers a thread) for L <= 256, and for the z pass at every L;
+// the y passes at L >= 512 keep their natural (smaller) count.  Chosen by
+// measurement on the 128^3 sphere and the 1024^3 cube.
 
 template <int LG> struct ColShape {
     static constexpr int L = 1 << LG, S8 = LG / 3, REM = LG - 3 * S8, NS = S8 + (REM ? 1 : 0);
@@ -650,7 +654,7 @@ template <typename C, int LG, int S> __device__ __forceinline__ void col_inverse
 
 // FY: plane z, columns kx0 .. kx0 + 8; active rows in, the n_y kept modes out
 template <typename T, int LG>
-__global__ void __launch_bounds__(1 << LG) k_fy_c(DevPlan p) {
+__global__ void __launch_bounds__(1 << LG, (LG <= 8 ? (1024 >> LG) : 1)) k_fy_c(DevPlan p) {
     typedef typename VecT<T>::T2 C;
     typedef ColShape<LG> Sh;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -690,7 +694,7 @@ __global__ void __launch_bounds__(1 << LG) k_fy_c(DevPlan p) {
 // FZ * D * IZ: row ky', columns kx0 .. kx0 + 8; the last forward stage, the
 // multiply and the first inverse stage share the same registers
 template <typename T, int LG>
-__global__ void __launch_bounds__(1 << LG) k_fz_c(DevPlan p) {
+__global__ void __launch_bounds__(1 << LG, (1024 >> LG) > 0 ? (1024 >> LG) : 1) k_fz_c(DevPlan p) {
     typedef typename VecT<T>::T2 C;
     typedef ColShape<LG> Sh;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -745,7 +749,7 @@ __global__ void __launch_bounds__(1 << LG) k_fz_c(DevPlan p) {
 // IY: plane z, columns kx0 .. kx0 + 8; the kept modes in (zero padded),
 // active rows out
 template <typename T, int LG>
-__global__ void __launch_bounds__(1 << LG) k_iy_c(DevPlan p) {
+__global__ void __launch_bounds__(1 << LG, (LG <= 8 ? (1024 >> LG) : 1)) k_iy_c(DevPlan p) {
     typedef typename VecT<T>::T2 C;
     typedef ColShape<LG> Sh;
     extern __shared__ __align__(16) unsigned char smem_raw[];
