@@ -561,8 +561,8 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
 constexpr int CB = 8;
 // Register budget: blocks of L threads are asked to fit 1024 / L per SM (at
 // most 64 registers a thread) for L <= 256, and for the z pass at every L;
-// the y passes at L >= 512 keep their natural (smaller) count.  Chosen by
-// measurement on the 128^3 sphere and the 1024^3 cube.
+// the y passes at L >= 512 use the variants without a minimum (`_long`).
+// Chosen by measurement on the 128^3 sphere and the 1024^3 cube.
 
 template <int LG> struct ColShape {
     static constexpr int L = 1 << LG, S8 = LG / 3, REM = LG - 3 * S8, NS = S8 + (REM ? 1 : 0);
@@ -654,7 +654,7 @@ template <typename C, int LG, int S> __device__ __forceinline__ void col_inverse
 
 // FY: plane z, columns kx0 .. kx0 + 8; active rows in, the n_y kept modes out
 template <typename T, int LG>
-__global__ void __launch_bounds__(1 << LG, (LG <= 8 ? (1024 >> LG) : 1)) k_fy_c(DevPlan p) {
+__device__ __forceinline__ void k_fy_c_body(const DevPlan &p) {
     typedef typename VecT<T>::T2 C;
     typedef ColShape<LG> Sh;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -690,6 +690,12 @@ __global__ void __launch_bounds__(1 << LG, (LG <= 8 ? (1024 >> LG) : 1)) k_fy_c(
             S2[(int64_t)(k - Sh::L + ny) * Kx] = v[r];
     }
 }
+// at L <= 256 a block asks for 1024 / L blocks per SM (at most 64 registers);
+// longer transforms keep the compiler's own choice
+template <typename T, int LG>
+__global__ void __launch_bounds__(1 << LG, (1024 >> LG)) k_fy_c(DevPlan p) { k_fy_c_body<T, LG>(p); }
+template <typename T, int LG>
+__global__ void __launch_bounds__(1 << LG) k_fy_c_long(DevPlan p) { k_fy_c_body<T, LG>(p); }
 
 // FZ * D * IZ: row ky', columns kx0 .. kx0 + 8; the last forward stage, the
 // multiply and the first inverse stage share the same registers
@@ -749,7 +755,7 @@ __global__ void __launch_bounds__(1 << LG, (1024 >> LG) > 0 ? (1024 >> LG) : 1) 
 // IY: plane z, columns kx0 .. kx0 + 8; the kept modes in (zero padded),
 // active rows out
 template <typename T, int LG>
-__global__ void __launch_bounds__(1 << LG, (LG <= 8 ? (1024 >> LG) : 1)) k_iy_c(DevPlan p) {
+__device__ __forceinline__ void k_iy_c_body(const DevPlan &p) {
     typedef typename VecT<T>::T2 C;
     typedef ColShape<LG> Sh;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -785,6 +791,126 @@ __global__ void __launch_bounds__(1 << LG, (LG <= 8 ? (1024 >> LG) : 1)) k_iy_c(
     for (int r = 0; r < 8; ++r) {
         const int y = col_idx<LG, 0>(t, r);
         if (((y - iv.x) & (Sh::L - 1)) < iv.y) S1[(int64_t)y * Kx] = v[r];
+    }
+}
+// at L <= 256 a block asks for 1024 / L blocks per SM (at most 64 registers);
+// longer transforms keep the compiler's own choice
+template <typename T, int LG>
+__global__ void __launch_bounds__(1 << LG, (1024 >> LG)) k_iy_c(DevPlan p) { k_iy_c_body<T, LG>(p); }
+template <typename T, int LG>
+__global__ void __launch_bounds__(1 << LG) k_iy_c_long(DevPlan p) { k_iy_c_body<T, LG>(p); }
+
+// ---------------------------------------------------------------- x inverse, compile-time length
+// The inverse row pass with Lx = 2^LG fixed at compile time: CB row pairs per block,
+// L / 8 threads per pair (t fastest, so a warp touches consecutive x), one
+// radix-8 butterfly per thread per stage (radix 8 stages, then 4 or 2).
+// Stockham stages keep the output in natural order, so the R2C split reads
+// Z(k) and Z(L - k) without bank conflicts.  One shared buffer: a stage reads
+// its eight inputs, waits, writes its eight outputs, waits.
+template <typename C, int LG, int S, bool INV>
+__device__ __forceinline__ void stk_compute_store(C *buf, C (&v)[8], int t, int b, const C *tw) {
+    typedef ColShape<LG> Sh;
+    constexpr int LGR = S < Sh::S8 ? 3 : Sh::REM;
+    constexpr int R = 1 << LGR, NB = 8 / R, lgNs = 3 * S;
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+        const int j = t + u * (Sh::L / 8);
+        const int k = j & ((1 << lgNs) - 1);
+        C *w = v + u * R;
+        if constexpr (lgNs > 0) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C tt = tw[((r * k) << (LG - lgNs - LGR)) & (Sh::L - 1)];
+                if (INV) tt.y = -tt.y;
+                w[r] = cmul(w[r], tt);
+            }
+        }
+        if constexpr (R == 8) dft8<C, INV>(w);
+        if constexpr (R == 4) dft4<C, INV>(w[0], w[1], w[2], w[3]);
+        if constexpr (R == 2) dft2(w[0], w[1]);
+        const int base = ((j - k) << LGR) + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[(base + (r << lgNs)) * (CB + 1) + b] = w[r];
+    }
+}
+// inputs of stage S for thread t: elements j + r L / R, j = t + u L / 8
+template <typename C, int LG, int S>
+__device__ __forceinline__ void stk_load(const C *buf, C (&v)[8], int t, int b) {
+    typedef ColShape<LG> Sh;
+    constexpr int LGR = S < Sh::S8 ? 3 : Sh::REM;
+    constexpr int R = 1 << LGR, NB = 8 / R;
+#pragma unroll
+    for (int u = 0; u < NB; ++u)
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[u * R + r] = buf[(t + u * (Sh::L / 8) + r * (Sh::L >> LGR)) * (CB + 1) + b];
+}
+// stages S .. NS-1 (stage S - 1 already stored); ends with a barrier
+template <typename C, int LG, int S, bool INV>
+__device__ __forceinline__ void stk_from(C *buf, int t, int b, const C *tw) {
+    if constexpr (S < ColShape<LG>::NS) {
+        C v[8];
+        stk_load<C, LG, S>(buf, v, t, b);
+        __syncthreads();
+        stk_compute_store<C, LG, S, INV>(buf, v, t, b, tw);
+        __syncthreads();
+        stk_from<C, LG, S + 1, INV>(buf, t, b, tw);
+    }
+}
+
+template <typename T, int LG>
+__global__ void __launch_bounds__(1 << LG) k_ix_s(DevPlan p) {
+    typedef typename VecT<T>::T2 C;
+    typedef ColShape<LG> Sh;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *buf = (C *)smem_raw;
+    C *tw = buf + Sh::L * (CB + 1);
+    for (int i = threadIdx.x; i < Sh::L; i += blockDim.x) tw[i] = ((const C *)p.tw[0])[i];
+    constexpr int TPB = Sh::L / 8;
+    const int b = threadIdx.x / TPB, t = threadIdx.x - b * TPB;
+    const int Ly = p.L[1], Kx = p.Kx;
+    const int lgHy = __ffs(Ly) - 2;
+    const int pr = blockIdx.x * CB + b;
+    const bool on = pr < p.n_row_pairs;
+    pdl_wait();
+    pdl_trigger();
+    int64_t r0 = 0;
+    if (on) {
+        const int rp = p.row_pairs[pr];
+        r0 = ((int64_t)(rp >> lgHy) * Ly + 2 * (rp & ((Ly >> 1) - 1))) * Sh::L;
+    }
+    // stage 0 reads frequencies t + r L / 8 of the pair's complex spectrum
+    // Y(k) = xa(k) + i xb(k), Y(L - k) = conj(xa(k)) + i conj(xb(k))
+    const C *S1 = (const C *)p.S1 + r0 / Sh::L * Kx;
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int k = t + r * TPB;
+        C y = cmk(T(0), T(0));
+        if (on) {
+            if (k == 0) {
+                y = cmk(S1[0].x, S1[Kx].x);
+            } else if (k < Kx) {
+                const C xa = S1[k], xb = S1[Kx + k];
+                y = cmk(xa.x - xb.y, xa.y + xb.x);
+            } else if (k > Sh::L - Kx) {
+                const C xa = S1[Sh::L - k], xb = S1[Kx + Sh::L - k];
+                y = cmk(xa.x + xb.y, xb.x - xa.y);
+            }
+        }
+        v[r] = y;
+    }
+    __syncthreads();  // twiddles
+    stk_compute_store<C, LG, 0, true>(buf, v, t, b, tw);
+    __syncthreads();
+    stk_from<C, LG, 1, true>(buf, t, b, tw);
+    if (!on) return;
+    T *G = (T *)p.gridB + r0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int x = t + r * TPB;
+        const C y = buf[x * (CB + 1) + b];
+        G[x] = y.x;
+        G[Sh::L + x] = y.y;
     }
 }
 
@@ -1005,6 +1131,21 @@ template <typename K> static cudaError_t prep(K kern, size_t sm) {
         case 10: { cudaError_t e_ = prep(KERN<T, 10>, SM); if (e_ != cudaSuccess) return e_;             \
                    return launch_k(KERN<T, 10>, NBLK, 1024, SM, S, p); }                                 \
     }
+#define SLP_COL_DISPATCH2(KERN, KERNL, T, LGV, NBLK, SM, S)                                                      \
+    switch (LGV) {                                                                                       \
+        case 5: { cudaError_t e_ = prep(KERN<T, 5>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 5>, NBLK, 32, SM, S, p); }                                     \
+        case 6: { cudaError_t e_ = prep(KERN<T, 6>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 6>, NBLK, 64, SM, S, p); }                                     \
+        case 7: { cudaError_t e_ = prep(KERN<T, 7>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 7>, NBLK, 128, SM, S, p); }                                    \
+        case 8: { cudaError_t e_ = prep(KERN<T, 8>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERN<T, 8>, NBLK, 256, SM, S, p); }                                    \
+        case 9: { cudaError_t e_ = prep(KERNL<T, 9>, SM); if (e_ != cudaSuccess) return e_;               \
+                  return launch_k(KERNL<T, 9>, NBLK, 512, SM, S, p); }                                    \
+        case 10: { cudaError_t e_ = prep(KERNL<T, 10>, SM); if (e_ != cudaSuccess) return e_;             \
+                   return launch_k(KERNL<T, 10>, NBLK, 1024, SM, S, p); }                                 \
+    }
 // the engine applies for 32 <= L <= 1024 and at least 8 stored x frequencies
 static bool col_engine_ok(const DevPlan &p, int L) { return L >= 32 && L <= 1024 && p.Kx >= CB; }
 
@@ -1019,6 +1160,14 @@ template <typename T> static cudaError_t fx_t(const DevPlan &p, cudaStream_t s) 
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) {
+    // the compile-time inverse pays off for long rows (measured at 1024);
+    // short, latency-bound rows keep the runtime kernel
+    if (col_engine_ok(p, p.L[0]) && p.L[0] >= 512) {
+        if (p.n_row_pairs == 0) return cudaSuccess;
+        const size_t sm = ((size_t)p.L[0] * (CB + 1) + p.L[0]) * 2 * sizeof(T);
+        const unsigned nb = (unsigned)((p.n_row_pairs + CB - 1) / CB);
+        SLP_COL_DISPATCH(k_ix_s, T, __builtin_ctz(p.L[0]), nb, sm, s)
+    }
     const size_t ce = 2 * sizeof(T);
     const int PB = row_batch(p.L[0], ce);
     const size_t sm = (2 * (size_t)p.L[0] * (PB + 1) + p.L[0]) * ce;
@@ -1033,7 +1182,7 @@ template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) 
         if (p.nz_act == 0) return cudaSuccess;
         const size_t sm = ((size_t)p.L[1] * (CB + 1) + p.L[1]) * 2 * sizeof(T);
         const unsigned nb = (unsigned)(p.nz_act * (p.Kx / CB));
-        SLP_COL_DISPATCH(k_fy_c, T, __builtin_ctz(p.L[1]), nb, sm, s)
+        SLP_COL_DISPATCH2(k_fy_c, k_fy_c_long, T, __builtin_ctz(p.L[1]), nb, sm, s)
     }
     const size_t ce = 2 * sizeof(T);
     const int B = col_batch(p.L[1], p.Kx, ce, p.nz_act);
@@ -1049,7 +1198,7 @@ template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) 
         if (p.nz_act == 0) return cudaSuccess;
         const size_t sm = ((size_t)p.L[1] * (CB + 1) + p.L[1]) * 2 * sizeof(T);
         const unsigned nb = (unsigned)(p.nz_act * (p.Kx / CB));
-        SLP_COL_DISPATCH(k_iy_c, T, __builtin_ctz(p.L[1]), nb, sm, s)
+        SLP_COL_DISPATCH2(k_iy_c, k_iy_c_long, T, __builtin_ctz(p.L[1]), nb, sm, s)
     }
     const size_t ce = 2 * sizeof(T);
     const int B = col_batch(p.L[1], p.Kx, ce, p.nz_act);
