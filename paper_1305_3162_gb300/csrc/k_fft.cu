@@ -804,9 +804,10 @@ __global__ void __launch_bounds__(1 << LG) k_iy_c_long(DevPlan p) { k_iy_c_body<
 // The inverse row pass with Lx = 2^LG fixed at compile time: CB row pairs per block,
 // L / 8 threads per pair (t fastest, so a warp touches consecutive x), one
 // radix-8 butterfly per thread per stage (radix 8 stages, then 4 or 2).
-// Stockham stages keep the output in natural order, so the R2C split reads
-// Z(k) and Z(L - k) without bank conflicts.  One shared buffer: a stage reads
-// its eight inputs, waits, writes its eight outputs, waits.
+// Stockham stages take natural-order input (the first stage reads the
+// spectrum straight from S1) and leave natural-order output, which is read
+// back by consecutive x.  One shared buffer: a stage reads its eight inputs,
+// waits, writes its eight outputs, waits.
 template <typename C, int LG, int S, bool INV>
 __device__ __forceinline__ void stk_compute_store(C *buf, C (&v)[8], int t, int b, const C *tw) {
     typedef ColShape<LG> Sh;
