@@ -185,3 +185,46 @@ def test_separable_mode_precomputed_near_field():
         assert rel_l2(phi, oracle.slp_nodal(w.V, w.T, w.quad, w.m_nodal)) <= 1e-10
     finally:
         slp.slp_destroy(plan)
+
+
+@pytest.mark.parametrize("grid", [(1024, 1024, 64), (64, 64, 1024), (512, 512, 512)],
+                         ids=["xy1024", "z1024", "512cube"])
+def test_long_transforms(grid):
+    """Transform lengths 512 and 1024 (the compile-time column engine at its
+    largest lengths, the compile-time inverse x pass, the z pass with its
+    register budget): a small slab elongated along the long axes, FP32, 1e-5."""
+    slp = lib()
+    dims = [4.0 if g >= 512 else 0.5 for g in grid]
+    nseg = [16 if g >= 512 else 2 for g in grid]
+    V, T = meshes.box(*dims, *nseg)
+    m = fields.smooth_random(V, 31)
+    plan = _plan(slp, V, T, 3, 1e-5, 32, grid, allow_grid_raise=0)
+    try:
+        info = slp.slp_query(plan)
+        assert info["grid"] == list(grid)
+        phi = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, m, 32)
+        ref = oracle.slp_nodal(V, T, 3, m)
+        assert rel_l2(phi, ref) <= 1e-5
+    finally:
+        slp.slp_destroy(plan)
+
+
+def test_timeline_milestones_are_ordered():
+    """slp_debug_timeline runs the concurrent evaluation: the spread ends
+    before the FFT passes, and the gather ends last (it waits for the near
+    branch); the result is the same evaluation."""
+    slp = lib()
+    torch = pytest.importorskip("torch")
+    V, T = meshes.icosphere(3)
+    m = fields.vortex(V, 41)
+    plan = _plan(slp, V, T, 7, 1e-5, 32, (64, 64, 64))
+    try:
+        d_in = torch.as_tensor(m, dtype=torch.float32, device="cuda")
+        d_phi = torch.empty(V.shape[0], dtype=torch.float32, device="cuda")
+        tl = slp.slp_debug_timeline(plan, slp.SLP_INPUT_NODAL_MAG, d_in, d_phi)
+        assert 0 < tl["spread"] <= tl["fft"] <= tl["gather"]
+        assert 0 < tl["near"] <= tl["gather"]
+        ref = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, m, 32)
+        assert rel_l2(d_phi.double().cpu().numpy(), ref) < 1e-6
+    finally:
+        slp.slp_destroy(plan)
