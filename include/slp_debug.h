@@ -55,7 +55,10 @@ enum {
     SLP_HOST_TGT_POINTS = 10,  /* double [N][3]: targets, sorted order */
     SLP_HOST_PLANE_ROWS = 11,  /* int32 [Lz][2]: first active row y0 and active row count of each
                                   plane (rows y0 .. y0 + count - 1 modulo Ly; pair aligned) */
-    SLP_HOST_ACTIVE_Z = 12     /* int32 [2]: first active plane z0 and active plane count (mod Lz) */
+    SLP_HOST_ACTIVE_Z = 12,    /* int32 [2]: first active plane z0 and active plane count (mod Lz) */
+    SLP_HOST_SPREAD_GROUPS = 13,    /* int32 [n]: spread cell groups, first source within the item
+                                       | source count << 16 */
+    SLP_HOST_SPREAD_GROUP_OFF = 14  /* int32 [spread items][9]: bounds of the 8 group lists of each item */
 };
 
 /* Run the pipeline of slp_eval up to and including stage last_stage, starting

@@ -41,7 +41,8 @@ SLP_STAGE_IFFT_Y, SLP_STAGE_IFFT_X, SLP_STAGE_GATHER, SLP_STAGE_NEAR = 5, 6, 7, 
 SLP_BUF_QBUF, SLP_BUF_GRID_A, SLP_BUF_GRID_B, SLP_BUF_S1, SLP_BUF_S2, SLP_BUF_DTAB = 0, 1, 2, 3, 4, 5
 (SLP_HOST_SRC_PERM, SLP_HOST_TGT_PERM, SLP_HOST_SRC_GRID, SLP_HOST_TGT_GRID, SLP_HOST_SPREAD_ITEMS,
  SLP_HOST_GATHER_ITEMS, SLP_HOST_NEAR_ITEMS, SLP_HOST_NEAR_RANGES, SLP_HOST_DTAB, SLP_HOST_SRC_POINTS,
- SLP_HOST_TGT_POINTS, SLP_HOST_PLANE_ROWS, SLP_HOST_ACTIVE_Z) = range(13)
+ SLP_HOST_TGT_POINTS, SLP_HOST_PLANE_ROWS, SLP_HOST_ACTIVE_Z, SLP_HOST_SPREAD_GROUPS,
+ SLP_HOST_SPREAD_GROUP_OFF) = range(15)
 
 
 class SlpError(RuntimeError):
@@ -406,7 +407,7 @@ _HOST_DTYPES = {SLP_HOST_SRC_PERM: np.int32, SLP_HOST_TGT_PERM: np.int32, SLP_HO
                 SLP_HOST_TGT_GRID: np.float64, SLP_HOST_SPREAD_ITEMS: np.int32, SLP_HOST_GATHER_ITEMS: np.int32,
                 SLP_HOST_NEAR_ITEMS: np.int32, SLP_HOST_NEAR_RANGES: np.int32, SLP_HOST_DTAB: np.float64,
                 SLP_HOST_SRC_POINTS: np.float64, SLP_HOST_TGT_POINTS: np.float64, SLP_HOST_PLANE_ROWS: np.int32,
-                SLP_HOST_ACTIVE_Z: np.int32}
+                SLP_HOST_ACTIVE_Z: np.int32, SLP_HOST_SPREAD_GROUPS: np.int32, SLP_HOST_SPREAD_GROUP_OFF: np.int32}
 
 
 def slp_debug_host_array(plan, which: int):

@@ -242,7 +242,9 @@ __global__ void __launch_bounds__(256) k_spread(DevPlan p, int fused_kind, const
 // Variant for 2M <= 10: runs of consecutive sources that share a grid cell
 // (the Morton sort makes them contiguous) have the same window box, so a warp
 // sums a whole run in registers and updates its private tile once per run.
-//   * run length: one ballot over the next SPREAD_GMAX sources;
+//   * groups: the plan lists, per item, runs of one cell (at most
+//     SPREAD_GMAX sources), dealt largest first to SPREAD_WARPS lists of
+//     about equal work, so the warps of a block finish together;
 //   * window values: lane (axis, i) evaluates psi(f_axis + M - 1 - i) for
 //     every source of the run (FP32: the per-interval polynomial, its
 //     coefficients held in registers), the charge folded into the x values;
@@ -269,7 +271,8 @@ template <int M, int TS> struct TileGeomG {
     static constexpr int WP = (W + 3) & ~3;             // padded row of window values
 };
 
-constexpr int SPREAD_GMAX = 16;  // sources per cell group
+// SPREAD_GMAX (sources per cell group) and SPREAD_WARPS (group lists per
+// item) are set with the plan's group lists (slp_internal.h)
 
 // row of WP window values from shared memory, 16 bytes per load
 template <int WP> __device__ __forceinline__ void load_row(const float *src, float *dst) {
@@ -355,18 +358,23 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spr
 
     const int ix = lane % W, izs = lane / W;
     const bool lane_on = lane < W * ZL;
-    const int c0 = (nsrc * warp) / nwarps, c1 = (nsrc * (warp + 1)) / nwarps;
-    for (int g0 = c0; g0 < c1;) {
+    // the plan's cell groups of this item, dealt to SPREAD_WARPS lists; a
+    // block with fewer warps takes lists w, w + nwarps, ...
+    const int *goff = p.sgroup_off + (int64_t)blockIdx.x * (SPREAD_WARPS + 1);
+    for (int wl = warp; wl < SPREAD_WARPS; wl += nwarps)
+    for (int gi = goff[wl]; gi < goff[wl + 1]; ++gi) {
+        const int gd = p.sgroups[gi];
+        const int g0 = gd & 0xffff, ng = gd >> 16;
+        if (g0 + ng > nsrc || ng < 1 || ng > SPREAD_GMAX) {
+            set_error(p.err, DEV_ERR_BAD_ITEM);
+            continue;
+        }
         const int cell = packed_cell(sg[g0].w);
-        const int idx = g0 + lane;
-        const bool same = lane < SPREAD_GMAX && idx < c1 && packed_cell(sg[idx].w) == cell;
-        const int ng = __ffs(~__ballot_sync(0xffffffffu, same)) - 1;  // >= 1: lane 0 always matches
         int cx, cy, cz;
         unpack_cell(cell, cx, cy, cz);
         const int lx = cx - it.c0x, ly = cy - it.c0y, lz = cz - it.c0z;
         if ((unsigned)lx >= (unsigned)TS_ || (unsigned)ly >= (unsigned)TS_ || (unsigned)lz >= (unsigned)TS_) {
             set_error(p.err, DEV_ERR_BAD_ITEM);
-            g0 += ng;
             continue;
         }
         if (wlane) {
@@ -446,7 +454,6 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spr
             }
         }
         __syncwarp();
-        g0 += ng;
     }
     __syncthreads();
 

@@ -17,6 +17,11 @@ struct TileItem {
     int pad0, pad1, pad2;
 };
 
+// Cell groups of the spread: at most SPREAD_GMAX consecutive sources of one
+// cell; each item's groups are dealt to SPREAD_WARPS lists.
+constexpr int SPREAD_GMAX = 16;
+constexpr int SPREAD_WARPS = 8;
+
 // Targets per gather item (the plan splits target tiles into items of at
 // most this many; the gather kernel stages one item per block).
 constexpr int GATHER_CHUNK = 64;
@@ -83,6 +88,8 @@ struct DevPlan {
 
     const TileItem *spread_items; int n_spread;
     int spread_chunk;             // most sources in one spread item
+    const int *sgroups;           // cell groups: first source (within the item) | count << 16
+    const int *sgroup_off;        // [n_spread][SPREAD_WARPS + 1] group list bounds of each item
     const TileItem *gather_items; int n_gather;
     const NearItem *near_items;   int n_near;
     const int2 *near_ranges;

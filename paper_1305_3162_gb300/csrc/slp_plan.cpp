@@ -514,6 +514,44 @@ void tile_items(const std::vector<double> &grid, const std::vector<uint64_t> &ke
     }
 }
 
+// Cell groups of each spread item (runs of one cell, at most SPREAD_GMAX
+// sources; the sort makes a cell's sources contiguous), dealt largest first to
+// SPREAD_WARPS lists, each group to the list with the least work so far (work
+// of a group ~ a fixed part for its tile update plus one part per source).
+void spread_groups(slp_plan_s &p) {
+    p.sgroups.clear();
+    p.sgroup_off.assign(p.spread_items.size() * (slp::SPREAD_WARPS + 1), 0);
+    std::vector<std::pair<int, int>> g;  // (count, first)
+    std::vector<std::vector<int>> lists(slp::SPREAD_WARPS);
+    for (size_t k = 0; k < p.spread_items.size(); ++k) {
+        const slp::TileItem &it = p.spread_items[k];
+        g.clear();
+        for (int i = it.begin; i < it.end;) {
+            const uint32_t cell = (uint32_t)p.src_grid[4 * (int64_t)i + 3];
+            int j = i + 1;
+            while (j < it.end && j - i < slp::SPREAD_GMAX && (uint32_t)p.src_grid[4 * (int64_t)j + 3] == cell) ++j;
+            g.push_back({j - i, i - it.begin});
+            i = j;
+        }
+        std::stable_sort(g.begin(), g.end(), [](const std::pair<int, int> &a, const std::pair<int, int> &b) {
+            return a.first > b.first;
+        });
+        std::vector<int> load(slp::SPREAD_WARPS, 0);
+        for (auto &l : lists) l.clear();
+        for (const auto &gr : g) {
+            const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            load[w] += 4 + gr.first;
+            lists[w].push_back(gr.second | (gr.first << 16));
+        }
+        int32_t *off = &p.sgroup_off[k * (slp::SPREAD_WARPS + 1)];
+        for (int w = 0; w < slp::SPREAD_WARPS; ++w) {
+            off[w] = (int32_t)p.sgroups.size();
+            p.sgroups.insert(p.sgroups.end(), lists[w].begin(), lists[w].end());
+        }
+        off[slp::SPREAD_WARPS] = (int32_t)p.sgroups.size();
+    }
+}
+
 // physical position (relative to the torus centre) of a sorted grid entry
 inline void phys(const slp_plan_s &p, const double *g, double *x) {
     const uint32_t packed = (uint32_t)g[3];
@@ -964,6 +1002,10 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     d.n_spread = (int)p.spread_items.size();
     d.spread_chunk = 1;
     for (const auto &it : p.spread_items) d.spread_chunk = std::max(d.spread_chunk, it.end - it.begin);
+    TRY(upload(p, &ptr, p.sgroups.data(), p.sgroups.size()));
+    d.sgroups = (const int *)ptr;
+    TRY(upload(p, &ptr, p.sgroup_off.data(), p.sgroup_off.size()));
+    d.sgroup_off = (const int *)ptr;
     TRY(upload(p, &ptr, p.gather_items.data(), p.gather_items.size()));
     d.gather_items = (const slp::TileItem *)ptr;
     d.n_gather = (int)p.gather_items.size();
@@ -1524,6 +1566,7 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
     auto by_size = [](const slp::TileItem &a, const slp::TileItem &b) { return a.end - a.begin > b.end - b.begin; };
     std::stable_sort(p->spread_items.begin(), p->spread_items.end(), by_size);
     std::stable_sort(p->gather_items.begin(), p->gather_items.end(), by_size);
+    spread_groups(*p);
     near_items(*p, skeys, tkeys);
     build_dtab(*p);
     active_region(*p);
@@ -1723,6 +1766,8 @@ slp_status slp_debug_host_count(slp_plan_t p, int which, int64_t *count) {
         case SLP_HOST_TGT_POINTS: *count = 3 * p->N; break;
         case SLP_HOST_PLANE_ROWS: *count = 2 * (int64_t)p->plane_iv.size(); break;
         case SLP_HOST_ACTIVE_Z: *count = 2; break;
+        case SLP_HOST_SPREAD_GROUPS: *count = (int64_t)p->sgroups.size(); break;
+        case SLP_HOST_SPREAD_GROUP_OFF: *count = (int64_t)p->sgroup_off.size(); break;
         default: return fail(SLP_ERR_INVALID_ARG, "unknown host array %d", which);
     }
     return SLP_OK;
@@ -1755,6 +1800,8 @@ slp_status slp_debug_host_array(slp_plan_t p, int which, void *out, int64_t coun
             break;
         }
         case SLP_HOST_PLANE_ROWS: memcpy(out, p->plane_iv.data(), 4 * count); break;
+        case SLP_HOST_SPREAD_GROUPS: memcpy(out, p->sgroups.data(), 4 * count); break;
+        case SLP_HOST_SPREAD_GROUP_OFF: memcpy(out, p->sgroup_off.data(), 4 * count); break;
         case SLP_HOST_ACTIVE_Z: {
             int32_t *o = (int32_t *)out;
             o[0] = p->z0;

@@ -282,3 +282,35 @@ def test_active_region_covers_every_window_row(slp, shape):
         assert active.sum() < 0.5 * Lz * Ly
     finally:
         slp.slp_destroy(p)
+
+
+def test_spread_cell_groups_cover_each_item(slp):
+    """The plan's spread groups: each item's sources covered exactly once,
+    each group one cell and at most 16 sources, dealt to 8 lists whose work
+    (4 per group + 1 per source) differs by at most one group's share."""
+    w = workloads.sphere(level=4)
+    p = _host_plan(slp, w.V, w.T, q=7, grid=(64, 64, 64))
+    try:
+        g = slp.slp_debug_host_array(p, slp.SLP_HOST_SRC_GRID).reshape(-1, 4)
+        cells = g[:, 3].astype(np.int64)
+        items = slp.slp_debug_host_array(p, slp.SLP_HOST_SPREAD_ITEMS).reshape(-1, 8)
+        groups = slp.slp_debug_host_array(p, slp.SLP_HOST_SPREAD_GROUPS)
+        off = slp.slp_debug_host_array(p, slp.SLP_HOST_SPREAD_GROUP_OFF).reshape(-1, 9)
+        assert off.shape[0] == items.shape[0]
+        for k, (c0x, c0y, c0z, b, e, *_) in enumerate(items):
+            cover = np.zeros(e - b, int)
+            loads = []
+            for wl in range(8):
+                load = 0
+                for gd in groups[off[k, wl]:off[k, wl + 1]]:
+                    first, n = gd & 0xFFFF, gd >> 16
+                    assert 1 <= n <= 16
+                    cover[first:first + n] += 1
+                    assert np.all(cells[b + first:b + first + n] == cells[b + first])
+                    load += 4 + n
+                loads.append(load)
+            assert np.all(cover == 1)
+            assert max(loads) - min(loads) <= 4 + 16
+        assert off[-1, 8] == groups.size
+    finally:
+        slp.slp_destroy(p)
