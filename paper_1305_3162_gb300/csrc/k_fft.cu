@@ -731,18 +731,23 @@ __global__ void __launch_bounds__(1 << LG, (1024 >> LG) > 0 ? (1024 >> LG) : 1) 
         const int z = col_idx<LG, 0>(t, r);
         v[r] = ((z - z0) & (Sh::L - 1)) < nza ? S2[z * zs] : cmk(T(0), T(0));
     }
-    __syncthreads();  // twiddles
-    col_stage<C, LG, 0, false>(v, t, tw);
-    col_forward_from<C, LG, 1>(buf, v, t, b, tw);
+    // the multipliers of the elements this thread holds after the forward
+    // stages depend on its positions only: load them now, beside the pencil
     const int aky = kp < ny / 2 ? kp : ny - kp;
     const T *D = (const T *)p.Dtab + (int64_t)aky * Kx + kx0 + b;
     const int64_t dz = (int64_t)(ny / 2) * Kx;
+    T dv[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int kz = col_freq<LG>(col_idx<LG, Sh::NS - 1>(t, r));
         const int akz = kz < Sh::L / 2 ? kz : Sh::L - kz;
-        v[r] = akz < nz / 2 ? cscale(v[r], D[akz * dz]) : cmk(T(0), T(0));
+        dv[r] = akz < nz / 2 ? D[akz * dz] : T(0);
     }
+    __syncthreads();  // twiddles
+    col_stage<C, LG, 0, false>(v, t, tw);
+    col_forward_from<C, LG, 1>(buf, v, t, b, tw);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = cscale(v[r], dv[r]);
     col_stage<C, LG, Sh::NS - 1, true>(v, t, tw);
     col_inverse_from<C, LG, Sh::NS - 2>(buf, v, t, b, tw);
 #pragma unroll
