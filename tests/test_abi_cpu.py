@@ -314,3 +314,17 @@ def test_spread_cell_groups_cover_each_item(slp):
         assert off[-1, 8] == groups.size
     finally:
         slp.slp_destroy(p)
+
+
+def test_empty_and_minimal_meshes(slp):
+    """No triangles -> SLP_ERR_INVALID_ARG; the smallest closed surface (a
+    tetrahedron, 4 vertices) plans with automatic parameters."""
+    with pytest.raises(slp.SlpError) as e:
+        _host_plan(slp, np.zeros((0, 3)), np.zeros((0, 3), np.int32))
+    assert e.value.status == slp.SLP_ERR_INVALID_ARG
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    T = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]], np.int32)
+    p = _host_plan(slp, V, T, q=7)
+    info = slp.slp_query(p)
+    assert info["n_targets"] == 4 and info["n_sources"] == 28
+    slp.slp_destroy(p)

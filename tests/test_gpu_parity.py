@@ -228,3 +228,43 @@ def test_timeline_milestones_are_ordered():
         assert rel_l2(d_phi.double().cpu().numpy(), ref) < 1e-6
     finally:
         slp.slp_destroy(plan)
+
+
+def _tetrahedron():
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], float)
+    T = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]], np.int32)
+    return V, T
+
+
+@pytest.mark.parametrize("prec,tol", [(32, 1e-5), (64, 1e-10)])
+def test_tetrahedron(prec, tol):
+    """The smallest closed surface: 4 targets, 4 triangles, automatic grid."""
+    slp = lib()
+    V, T = _tetrahedron()
+    m = np.array([[1.0, 0.2, -0.3], [0.0, 1.0, 0.5], [0.3, -0.4, 1.0], [-1.0, 0.5, 0.2]])
+    plan = _plan(slp, V, T, 7, tol, prec)
+    try:
+        phi = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, m, prec)
+        ref = oracle.slp_nodal(V, T, 7, m)
+        assert rel_l2(phi, ref) <= tol
+    finally:
+        slp.slp_destroy(plan)
+
+
+def test_far_from_origin_and_zero_input():
+    """A sphere centred at (1000, -2000, 500): FP32 keeps its accuracy because
+    positions are stored as integer cells plus fractions relative to the
+    torus; and a zero magnetisation gives exactly zero."""
+    slp = lib()
+    V, T = meshes.icosphere(3)
+    V = V + np.array([1000.0, -2000.0, 500.0])
+    m = fields.vortex(V - V.mean(0), 51)
+    plan = _plan(slp, V, T, 7, 1e-5, 32, (64, 64, 64))
+    try:
+        phi = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, m, 32)
+        ref = oracle.slp_nodal(V, T, 7, m)
+        assert rel_l2(phi, ref) <= 1e-5
+        zero = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, np.zeros_like(m), 32)
+        assert np.all(zero == 0.0)
+    finally:
+        slp.slp_destroy(plan)
