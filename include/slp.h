@@ -169,6 +169,16 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance,
  * Errors: INVALID_ARG, NO_DEVICE, CUDA. */
 slp_status slp_eval(slp_plan_t plan, int input_kind, const void *d_in, void *d_phi, void *stream);
 
+/* Evaluate n_states inputs of one plan in one call: d_in holds the states
+ * back to back (each in the layout of input_kind), d_phi receives
+ * [n_states][n_targets].  For nodal input with the precomputed near field,
+ * up to 8 states share one pass over the near-field operator (the operator is
+ * read once per 8 states instead of once per state); each result equals that
+ * of slp_eval on the same state.  Stream-ordered; same rules as slp_eval.
+ * Errors: INVALID_ARG, NO_DEVICE, CUDA. */
+slp_status slp_eval_states(slp_plan_t plan, int input_kind, int n_states, const void *d_in, void *d_phi,
+                           void *stream);
+
 /* Same as slp_eval with host buffers: copies h_in to the plan's staging
  * buffer, evaluates, copies phi back to h_phi and synchronises the stream.
  * Page-locked host memory gives asynchronous copies. */

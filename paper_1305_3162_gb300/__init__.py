@@ -125,7 +125,7 @@ class slp_info(ctypes.Structure):
 _lib = None
 
 #: C entry points the binding requires (the declarations of include/slp.h and include/slp_debug.h)
-EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_host", "slp_query", "slp_query_points",
+EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_states", "slp_eval_host", "slp_query", "slp_query_points",
             "slp_check", "slp_destroy", "slp_status_string", "slp_last_error",
             "slp_debug_run", "slp_debug_copy", "slp_debug_buffer_bytes", "slp_debug_host_count",
             "slp_debug_host_array", "slp_debug_window", "slp_debug_window_hat", "slp_debug_profile",
@@ -158,6 +158,7 @@ def load():
                       ctypes.POINTER(vp)], St),
         "slp_eval": ([vp, ctypes.c_int, vp, vp, vp], St),
         "slp_eval_host": ([vp, ctypes.c_int, vp, vp, vp], St),
+        "slp_eval_states": ([vp, ctypes.c_int, ctypes.c_int, vp, vp, vp], St),
         "slp_query": ([vp, ctypes.POINTER(slp_info)], St),
         "slp_query_points": ([vp, ctypes.POINTER(ctypes.c_double)], St),
         "slp_check": ([vp], St),
@@ -250,6 +251,12 @@ def slp_plan(vertices, triangles, quadrature: int, tolerance: float, opts: slp_p
 
 def slp_eval(plan, input_kind: int, d_in, d_phi, stream=None):
     _check(load().slp_eval(plan, int(input_kind), _ptr(d_in), _ptr(d_phi), _stream(stream)), "slp_eval")
+
+
+def slp_eval_states(plan, input_kind: int, n_states: int, d_in, d_phi, stream=None):
+    """n_states evaluations of one plan (inputs back to back, outputs [n_states][N])."""
+    _check(load().slp_eval_states(plan, int(input_kind), int(n_states), _ptr(d_in), _ptr(d_phi), _stream(stream)),
+           "slp_eval_states")
 
 
 def slp_eval_host(plan, input_kind: int, h_in, h_phi, stream=None):

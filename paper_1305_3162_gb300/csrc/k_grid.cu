@@ -749,6 +749,39 @@ cudaError_t launch_nodal_prep(const DevPlan &p, const void *d_in, cudaStream_t s
     return cudaGetLastError();
 }
 
+// K states: block row y = state
+template <typename T>
+__global__ void __launch_bounds__(256) k_nodal_prep_states(DevPlan p, StatePtrs sp) {
+    typedef typename VecT<T>::T4 T4;
+    pdl_wait();
+    pdl_trigger();
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= p.N) return;
+    const T *in = (const T *)sp.in[blockIdx.y];
+    const int64_t v = p.tgt_perm[u];
+    T4 o;
+    o.x = in[3 * v];
+    o.y = in[3 * v + 1];
+    o.z = in[3 * v + 2];
+    o.w = T(0);
+    ((T4 *)p.m4)[(int64_t)blockIdx.y * p.N + u] = o;
+}
+
+cudaError_t launch_nodal_prep_states(const DevPlan &p, const StatePtrs &in, int K, cudaStream_t s) {
+    if (p.N == 0 || K <= 0) return cudaSuccess;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((p.N + 255) / 256), (unsigned)K);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (p.prec == 64) return cudaLaunchKernelEx(&cfg, k_nodal_prep_states<double>, p, in);
+    return cudaLaunchKernelEx(&cfg, k_nodal_prep_states<float>, p, in);
+}
+
 cudaError_t launch_charges(const DevPlan &p, int kind, const void *d_in, cudaStream_t s) {
     if (p.Q == 0) return cudaSuccess;
     const int nb = (int)((p.Q + 255) / 256);

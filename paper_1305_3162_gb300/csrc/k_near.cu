@@ -295,6 +295,73 @@ __global__ void __launch_bounds__(128) k_near_matrix(DevPlan p) {
     if (lane == 0) ((T *)p.phi_part)[t] = acc;
 }
 
+// K states with one pass over the operator: each entry is streamed once and
+// applied to the K sorted magnetisations (phi_part[k][t]); the per-state sums
+// run in the same order as in k_near_matrix.
+template <typename T, int K>
+__global__ void __launch_bounds__(128) k_near_matrix_states(DevPlan p) {
+    pdl_wait();
+    pdl_trigger();
+    typedef typename VecT<T>::T4 T4;
+    constexpr int U = 8;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t t = (int64_t)blockIdx.x * 4 + warp;
+    if (t >= p.N) return;
+    const T4 *val = (const T4 *)p.nm_val;
+    const T4 *m4 = (const T4 *)p.m4;
+    const int64_t e0 = p.nm_rowptr[t], e1 = p.nm_rowptr[t + 1];
+    T acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = T(0);
+    for (int64_t e = e0 + lane; e < e1; e += 32 * U) {
+        T4 w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = e + 32 * u;
+            if (i < e1) {
+                w[u] = ld_stream(val + i);
+            } else {
+                w[u].x = w[u].y = w[u].z = T(0);
+                w[u].w = pack_id(w[u].w, 0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t col = packed_cell(w[u].w);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const T4 mv = m4[k * p.N + col];
+                acc[k] += w[u].x * mv.x + w[u].y * mv.y + w[u].z * mv.z;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const T a = warp_sum(acc[k]);
+        if (lane == 0) ((T *)p.phi_part)[k * p.N + t] = a;
+    }
+}
+
+template <typename T> static cudaError_t near_states_t(const DevPlan &p, int K, cudaStream_t s) {
+    const unsigned nb = (unsigned)((p.N + 3) / 4);
+    switch (K) {
+        case 1: return launch_k(k_near_matrix_states<T, 1>, nb, 128, 0, s, p);
+        case 2: return launch_k(k_near_matrix_states<T, 2>, nb, 128, 0, s, p);
+        case 3: return launch_k(k_near_matrix_states<T, 3>, nb, 128, 0, s, p);
+        case 4: return launch_k(k_near_matrix_states<T, 4>, nb, 128, 0, s, p);
+        case 5: return launch_k(k_near_matrix_states<T, 5>, nb, 128, 0, s, p);
+        case 6: return launch_k(k_near_matrix_states<T, 6>, nb, 128, 0, s, p);
+        case 7: return launch_k(k_near_matrix_states<T, 7>, nb, 128, 0, s, p);
+        case 8: return launch_k(k_near_matrix_states<T, 8>, nb, 128, 0, s, p);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_near_matrix_states(const DevPlan &p, int K, cudaStream_t s) {
+    if (p.N == 0 || K <= 0) return cudaSuccess;
+    return p.prec == 64 ? near_states_t<double>(p, K, s) : near_states_t<float>(p, K, s);
+}
+
 cudaError_t launch_near_matrix(const DevPlan &p, const void *, cudaStream_t s) {
     if (p.N == 0) return cudaSuccess;
     const unsigned nb = (unsigned)((p.N + 3) / 4);

@@ -145,12 +145,16 @@ slp_status slp_batch_create(int n_plans, const slp_plan_t *plans, int n_items, c
         cudaStream_t s = b->streams[l + 1];
         cudaStreamWaitEvent(s, fork, 0);
         slp_plan_s &p = *plans[lanes[l].plan];
+        // the lane's items (all of one plan) share passes over the near-field operator
+        std::vector<const void *> ins;
+        std::vector<void *> outs;
         for (int it : lanes[l].items) {
-            st = slp_run_pipeline(p, lanes[l].view, input_kind, d_in[it], d_phi[it], s, SLP_STAGE_NEAR, nullptr,
-                                  &b->execs[l]);
-            if (st != SLP_OK) break;
-            b->launches += p.launches_per_eval;
+            ins.push_back(d_in[it]);
+            outs.push_back(d_phi[it]);
         }
+        int nl = 0;
+        st = slp_run_states(p, lanes[l].view, input_kind, ins.data(), outs.data(), (int)ins.size(), s, &b->execs[l], &nl);
+        b->launches += nl;
         cudaEventRecord(b->events[l], s);
         cudaStreamWaitEvent(s0, b->events[l], 0);
     }

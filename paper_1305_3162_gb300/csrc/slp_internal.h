@@ -22,6 +22,14 @@ struct TileItem {
 constexpr int SPREAD_GMAX = 16;
 constexpr int SPREAD_WARPS = 8;
 
+// Magnetisation states whose near-field products share one pass over the
+// precomputed operator (scratch for sorted m and near-field parts holds this
+// many states).
+constexpr int NEAR_STATES = 8;
+struct StatePtrs {
+    const void *in[NEAR_STATES];
+};
+
 // Targets per gather item (the plan splits target tiles into items of at
 // most this many; the gather kernel stages one item per block).
 constexpr int GATHER_CHUNK = 64;
@@ -67,13 +75,13 @@ struct DevPlan {
 
     // scratch (written during evaluation)
     void *qbuf;    // T [Q] weighted charges, sorted order
-    void *m4;      // T4 [N] nodal magnetisation in sorted target order (NODAL_MAG input)
+    void *m4;      // T4 [NEAR_STATES][N] nodal magnetisation in sorted target order (NODAL_MAG input)
     void *gridA;   // T [Lz][Ly][Lx] spread grid (kept zero between evaluations)
     void *gridB;   // T [Lz][Ly][Lx] interpolation grid
     void *S1;      // T2 [Lz][Ly][Kx]
     void *S2;      // T2 [Lz][n_y][Kx]
     void *phi_near; // T [32 * n_near] near-field partials per work item (deterministic mode)
-    void *phi_part; // T [N] near-field correction per sorted target, added by the gather
+    void *phi_part; // T [NEAR_STATES][N] near-field correction per sorted target, added by the gather
     const void *Dtab;   // T [n_z/2][n_y/2][Kx] kernel multiplier by |l_z|, |l_y|, l_x
     const void *tw[3];  // T2 [L_q] forward twiddles exp(-2 pi i t / L_q)
 
@@ -158,6 +166,10 @@ cudaError_t launch_nm_build(const NMBuild &b, int pass, int prec, int64_t *count
                             const int64_t *rowptr, void *val, cudaStream_t s);
 // phi_part = W m (overwrites)
 cudaError_t launch_near_matrix(const DevPlan &p, const void *d_m, cudaStream_t s);
+// K <= NEAR_STATES states at once: m4[k][.] from in[k] (sorted), then
+// phi_part[k][.] = W m_k with one pass over W
+cudaError_t launch_nodal_prep_states(const DevPlan &p, const StatePtrs &in, int K, cudaStream_t s);
+cudaError_t launch_near_matrix_states(const DevPlan &p, int K, cudaStream_t s);
 
 // Set the thread-local text returned by slp_last_error().
 void set_last_error(const char *msg);

@@ -949,8 +949,8 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     const int64_t G = (int64_t)p.L[0] * p.L[1] * p.L[2];
     const int Kx = p.n[0] / 2;
     TRY(dalloc(p, &d.qbuf, sizeof(T) * p.Q));
-    TRY(dalloc(p, &d.m4, 4 * sizeof(T) * p.N));
-    TRY(dalloc(p, &d.phi_part, sizeof(T) * p.N));
+    TRY(dalloc(p, &d.m4, 4 * sizeof(T) * p.N * slp::NEAR_STATES));
+    TRY(dalloc(p, &d.phi_part, sizeof(T) * p.N * slp::NEAR_STATES));
     TRY(dalloc(p, &d.gridA, sizeof(T) * G));
     TRY(dalloc(p, &d.gridB, sizeof(T) * G));
     TRY(dalloc(p, &d.S1, sizeof(T2) * (size_t)p.L[2] * p.L[1] * Kx));
@@ -1396,6 +1396,63 @@ slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, 
     return run_pipeline(p, p.dp, kind, d_in, d_phi, s, last, ev, ev ? nullptr : &p.exec);
 }
 
+// S states of nodal input with the precomputed near field, in chunks of up
+// to NEAR_STATES: per chunk, one sorting prep and one pass over the near-field
+// operator for all of the chunk's states run on ex->aux, while ex->main runs
+// each state's spread, FFT passes and gather (the gather of state k reads
+// near-field part k).  Each chunk's branch starts after the previous chunk's
+// gathers (they read the same scratch).  Other inputs or near modes run the
+// single-state pipeline per state.
+slp_status run_states(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *const *ins, void *const *outs,
+                      int S, cudaStream_t s, SlpExec *ex, int *launches) {
+    const bool use_matrix = kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
+    if (!use_matrix || !ex) {
+        for (int k = 0; k < S; ++k) {
+            TRY(run_pipeline(p, d, kind, ins[k], outs[k], s, SLP_STAGE_NEAR, nullptr, ex));
+            if (launches) *launches += p.launches_per_eval;
+        }
+        return SLP_OK;
+    }
+    const size_t es = p.prec == 64 ? 8 : 4;
+    cudaStream_t m = ex->main;
+    TRY(cuda_status(cudaEventRecord(ex->fork, s), "fork"));
+    TRY(cuda_status(cudaStreamWaitEvent(m, ex->fork, 0), "fork wait"));
+    for (int c0 = 0; c0 < S; c0 += slp::NEAR_STATES) {
+        const int K = std::min(slp::NEAR_STATES, S - c0);
+        slp::StatePtrs sp = {};
+        for (int k = 0; k < K; ++k) sp.in[k] = ins[c0 + k];
+        TRY(cuda_status(cudaEventRecord(ex->fork, m), "fork"));
+        TRY(cuda_status(cudaStreamWaitEvent(ex->aux, ex->fork, 0), "fork wait"));
+        TRY(cuda_status(slp::launch_nodal_prep_states(d, sp, K, ex->aux), "nodal prep"));
+        TRY(cuda_status(slp::launch_near_matrix_states(d, K, ex->aux), "near-field matrix"));
+        TRY(cuda_status(cudaEventRecord(ex->join, ex->aux), "join"));
+        for (int k = 0; k < K; ++k) {
+            TRY(cuda_status(slp::launch_spread(d, kind, ins[c0 + k], m), "spread"));
+            if (d.fuse_pb > 0) {
+                TRY(cuda_status(slp::launch_fft_forward_xy(d, m), "fft xy"));
+            } else {
+                TRY(cuda_status(slp::launch_fft_forward_x(d, m), "fft x"));
+                TRY(cuda_status(slp::launch_fft_forward_y(d, m), "fft y"));
+            }
+            TRY(cuda_status(slp::launch_fft_z_multiply(d, m), "fft z"));
+            if (d.fuse_pb > 0) {
+                TRY(cuda_status(slp::launch_fft_inverse_yx(d, m), "ifft yx"));
+            } else {
+                TRY(cuda_status(slp::launch_fft_inverse_y(d, m), "ifft y"));
+                TRY(cuda_status(slp::launch_fft_inverse_x(d, m), "ifft x"));
+            }
+            if (k == 0) TRY(cuda_status(cudaStreamWaitEvent(m, ex->join, 0), "join wait"));
+            slp::DevPlan dk = d;
+            dk.phi_part = (char *)d.phi_part + es * (size_t)p.N * k;
+            TRY(cuda_status(slp::launch_gather(dk, outs[c0 + k], m), "gather"));
+        }
+        if (launches) *launches += 2 + K * (p.launches_per_eval - 2);
+    }
+    TRY(cuda_status(cudaEventRecord(ex->done, m), "done"));
+    TRY(cuda_status(cudaStreamWaitEvent(s, ex->done, 0), "done wait"));
+    return SLP_OK;
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int dev) {
@@ -1428,6 +1485,11 @@ slp_status slp_run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, cons
     return run_pipeline(p, d, kind, d_in, d_phi, s, last, ev, ex);
 }
 
+slp_status slp_run_states(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *const *ins, void *const *outs,
+                          int n, cudaStream_t s, SlpExec *ex, int *launches) {
+    return run_states(p, d, kind, ins, outs, n, s, ex, launches);
+}
+
 cudaError_t slp_exec_create(SlpExec &e) {
     int least = 0, greatest = 0;
     cudaError_t r = cudaDeviceGetStreamPriorityRange(&least, &greatest);
@@ -1452,7 +1514,8 @@ int64_t slp_scratch_bytes(const slp_plan_s &p) {
     const int64_t es = p.prec == 64 ? 8 : 4;
     const int64_t G = (int64_t)p.L[0] * p.L[1] * p.L[2];
     const int64_t Kx = p.n[0] / 2;
-    int64_t b = es * p.Q + 5 * es * p.N + 2 * es * G + 2 * es * p.L[2] * p.L[1] * Kx + 2 * es * p.L[2] * p.n[1] * Kx;
+    int64_t b = es * p.Q + 5 * es * p.N * slp::NEAR_STATES + 2 * es * G + 2 * es * p.L[2] * p.L[1] * Kx +
+                2 * es * p.L[2] * p.n[1] * Kx;
     if (p.opts.deterministic) b += es * 32 * (int64_t)std::max<size_t>(1, p.near_items.size());
     return b;
 }
@@ -1466,8 +1529,8 @@ slp_status slp_alloc_scratch(slp_plan_s &p, slp::DevPlan &out, std::vector<void 
         void **dst;
         int64_t n;
     } reqs[] = {{&out.qbuf, es * p.Q},
-                {&out.m4, 4 * es * p.N},
-                {&out.phi_part, es * p.N},
+                {&out.m4, 4 * es * p.N * slp::NEAR_STATES},
+                {&out.phi_part, es * p.N * slp::NEAR_STATES},
                 {&out.gridA, es * G},
                 {&out.gridB, es * G},
                 {&out.S1, 2 * es * p.L[2] * p.L[1] * Kx},
@@ -1600,6 +1663,24 @@ slp_status slp_eval(slp_plan_t p, int kind, const void *d_in, void *d_phi, void 
     if (!d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "input or output pointer is NULL");
     DeviceGuard g(p->device);
     return run_pipeline(*p, kind, d_in, d_phi, (cudaStream_t)stream, SLP_STAGE_NEAR);
+}
+
+slp_status slp_eval_states(slp_plan_t p, int kind, int n_states, const void *d_in, void *d_phi, void *stream) {
+    if (!p) return fail(SLP_ERR_INVALID_ARG, "plan is NULL");
+    if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan cannot evaluate");
+    if (kind < 0 || kind > 2) return fail(SLP_ERR_INVALID_ARG, "unknown input kind %d", kind);
+    if (n_states < 1) return fail(SLP_ERR_INVALID_ARG, "n_states must be positive");
+    if (!d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "input or output pointer is NULL");
+    DeviceGuard g(p->device);
+    const size_t es = p->prec == 64 ? 8 : 4;
+    const size_t in_elems = kind == SLP_INPUT_SIGMA ? (size_t)p->Q : (kind == SLP_INPUT_MAG ? 3 * (size_t)p->Q : 3 * (size_t)p->N);
+    std::vector<const void *> ins(n_states);
+    std::vector<void *> outs(n_states);
+    for (int k = 0; k < n_states; ++k) {
+        ins[k] = (const char *)d_in + es * in_elems * k;
+        outs[k] = (char *)d_phi + es * (size_t)p->N * k;
+    }
+    return run_states(*p, p->dp, kind, ins.data(), outs.data(), n_states, (cudaStream_t)stream, &p->exec, nullptr);
 }
 
 slp_status slp_eval_host(slp_plan_t p, int kind, const void *h_in, void *h_phi, void *stream) {

@@ -97,6 +97,13 @@ constexpr int SLP_PROFILE_SLOTS = 10;
 slp_status slp_run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *d_in, void *d_phi,
                             cudaStream_t s, int last, cudaEvent_t *ev, SlpExec *ex);
 
+// Enqueue n evaluations of `p` on the device view `d` (states ins[k] ->
+// outs[k]); nodal input with the precomputed near field shares one pass over
+// the near-field operator among up to NEAR_STATES states.  Adds the kernels
+// launched to *launches when given.
+slp_status slp_run_states(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *const *ins, void *const *outs,
+                          int n, cudaStream_t s, SlpExec *ex, int *launches);
+
 // Allocate a second scratch set (charges, sorted m, grids, spectra, partials)
 // for `p` and return a device view that uses it; the pointers are appended to
 // `allocs` (released by the caller with cudaFree).  Grids and spectra are

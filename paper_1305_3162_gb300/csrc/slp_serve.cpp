@@ -170,11 +170,16 @@ slp_status launch_request(slp_server_s &S, Request &r, Slot &sl) {
     cudaError_t e = cudaMemcpy2DAsync(din, (size_t)ib, r.h_in, (size_t)ihb, (size_t)ihb, (size_t)r.n_states,
                                       cudaMemcpyHostToDevice, sl.stream);
     if (e != cudaSuccess) return slp_fail(SLP_ERR_CUDA, "request %lld: copy in: %s", (long long)r.id, cudaGetErrorString(e));
+    // the request's states share passes over the near-field operator
+    std::vector<const void *> ins(r.n_states);
+    std::vector<void *> outs(r.n_states);
     for (int k = 0; k < r.n_states; ++k) {
-        const slp_status st = slp_run_pipeline(p, sl.view, S.kind, din + k * ib, dout + k * ob, sl.stream,
-                                               SLP_STAGE_NEAR, nullptr, &sl.exec);
-        if (st != SLP_OK) return st;
+        ins[k] = din + k * ib;
+        outs[k] = dout + k * ob;
     }
+    const slp_status st = slp_run_states(p, sl.view, S.kind, ins.data(), outs.data(), r.n_states, sl.stream, &sl.exec,
+                                         nullptr);
+    if (st != SLP_OK) return st;
     e = cudaMemcpy2DAsync(r.h_out, (size_t)ohb, dout, (size_t)ob, (size_t)ohb, (size_t)r.n_states,
                           cudaMemcpyDeviceToHost, sl.stream);
     if (e != cudaSuccess) return slp_fail(SLP_ERR_CUDA, "request %lld: copy out: %s", (long long)r.id, cudaGetErrorString(e));

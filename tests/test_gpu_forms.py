@@ -77,3 +77,37 @@ def test_autotuner_picks_a_feasible_fast_grid():
         assert rel_l2(phi, oracle.slp_nodal(V, T, 7, m)) <= 1e-5
     finally:
         slp.slp_destroy(plan)
+
+
+def test_eval_states_matches_single_evaluations():
+    """slp_eval_states: 11 nodal states (a chunk of 8 sharing one pass over the
+    near-field operator, then 3) give the results of 11 slp_eval calls; a
+    sigma input (no shared pass) as well."""
+    slp = lib()
+    torch = torch_cuda()
+    V, T = meshes.icosphere(3)
+    plan = _plan(slp, V, T, 7, 1e-5, 32, (64, 64, 64))
+    try:
+        assert slp.slp_query(plan)["near_mode"] == slp.SLP_NEAR_PRECOMPUTED
+        S = 11
+        ms = np.stack([fields.smooth_random(V, 300 + k) for k in range(S)])
+        d_in = torch.as_tensor(ms.reshape(-1), dtype=torch.float32, device="cuda")
+        d_out = torch.full((S * V.shape[0],), float("nan"), dtype=torch.float32, device="cuda")
+        slp.slp_eval_states(plan, slp.SLP_INPUT_NODAL_MAG, S, d_in, d_out)
+        torch.cuda.synchronize()
+        got = d_out.double().cpu().numpy().reshape(S, -1)
+        for k in range(S):
+            ref = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, ms[k], 32)
+            assert rel_l2(got[k], ref) < 1e-6, k
+        assert rel_l2(got[9], oracle.slp_nodal(V, T, 7, ms[9])) <= 1e-5
+        Q = T.shape[0] * 7
+        sig = np.stack([fields.random_sigma(Q, 400 + k) for k in range(2)])
+        d_sig = torch.as_tensor(sig.reshape(-1), dtype=torch.float32, device="cuda")
+        d_out2 = torch.empty(2 * V.shape[0], dtype=torch.float32, device="cuda")
+        slp.slp_eval_states(plan, slp.SLP_INPUT_SIGMA, 2, d_sig, d_out2)
+        torch.cuda.synchronize()
+        got2 = d_out2.double().cpu().numpy().reshape(2, -1)
+        for k in range(2):
+            assert rel_l2(got2[k], run(slp, plan, slp.SLP_INPUT_SIGMA, sig[k], 32)) < 1e-6
+    finally:
+        slp.slp_destroy(plan)
