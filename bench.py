@@ -617,7 +617,7 @@ def run_served(args):
     rings = [[torch.empty(32 * V.shape[0], dtype=torch.float32).pin_memory() for _ in range(8)]
              for name, (V, T), q, grid in pool]
     so = slp.slp_server_default_opts()
-    so.slots_per_plan = 2
+    so.slots_per_plan = args.slots
     so.hbm_budget_bytes = int(args.budget_gb * 2 ** 30)
     server = slp.slp_server_create(plans, slp.SLP_INPUT_NODAL_MAG, so)
     # probes: one private request per mesh, before the stream, for parity
@@ -673,7 +673,7 @@ def run_served(args):
     line = {"metric": METRIC + " (served form)", "value": targets / wall, "unit": UNIT, "mode": "served",
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded meshes and magnetisations)",
             "config": {"workload": "Poisson arrivals over 8 resident meshes", "rate_req_per_s": args.rate,
-                       "requests": n_req, "states_per_request": "uniform 1..32", "slots_per_plan": 2,
+                       "requests": n_req, "states_per_request": "uniform 1..32", "slots_per_plan": args.slots,
                        "hbm_budget_gb": args.budget_gb, "plans_s": round(t_plan, 1), "meshes": info},
             "latency_p50_ms": stats["latency_p50_ms"], "latency_p99_ms": stats["latency_p99_ms"],
             "queue_wait_p50_ms": stats["queue_wait_p50_ms"], "queue_wait_p99_ms": stats["queue_wait_p99_ms"],
@@ -698,7 +698,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", choices=["plain", "batched", "served"], default="plain",
                     help="plain: the headline single evaluation; batched/served: the other forms")
-    ap.add_argument("--lanes", type=int, default=4, help="batched form: concurrent scratch sets per plan")
+    ap.add_argument("--lanes", type=int, default=1,
+                    help="batched form: concurrent scratch sets per plan (a lane batches its states itself)")
+    ap.add_argument("--slots", type=int, default=1, help="served form: concurrent request slots per plan")
     ap.add_argument("--rate", type=float, default=2000.0, help="served form: mean arrivals per second")
     ap.add_argument("--requests", type=int, default=400, help="served form: requests in the arrival stream")
     ap.add_argument("--budget-gb", type=float, default=48.0, help="served form: HBM budget of the server")

@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
     pdl_trigger();
     const int npairs = p.n_row_pairs;
     const int pr0 = blockIdx.x * PB;
-    T *A = (T *)p.gridA;
+    T *A = (T *)p.gridA + blockIdx.y * p.st_grid;
     // rows y0 and y0+1 of each pair, VW elements per vector load; all loads are
     // issued before the zeroing stores so they overlap
     typedef typename VecW<T>::V V;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256) k_fx(DevPlan p, int PB) {
         ((V *)(A + r0 + Lx))[xv] = VecW<T>::zero();
     }
     const C *res = fft_columns<C, false>(b0, b1, Lx, ld, PB, stw);
-    C *S1 = (C *)p.S1;
+    C *S1 = (C *)p.S1 + blockIdx.y * p.st_s1;
     for (int i = threadIdx.x; i < PB * Kx; i += blockDim.x) {
         const int b = i >> lgKx, k = i & (Kx - 1);
         if (pr0 + b >= npairs) continue;
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
     const int z = (p.z0 + zi) & (p.L[2] - 1);
     const int kx0 = (blockIdx.x - zi * ntile) * B;
     const int2 iv = p.plane_iv[z];  // active rows y0 .. y0 + rows - 1 (mod Ly)
-    const C *S1 = (const C *)p.S1 + (int64_t)z * Ly * Kx + kx0;
+    const C *S1 = (const C *)p.S1 + blockIdx.y * p.st_s1 + (int64_t)z * Ly * Kx + kx0;
     pipelined_copy<C>(
         Ly * B,
         [&](int i) {
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(256) k_fy(DevPlan p, int B) {
     __syncthreads();
     fft_columns_inplace<C, false>(buf, lgLy, ld, lgB, stw);
     const RadixPlan rp = radix_plan(lgLy);
-    C *S2 = (C *)p.S2 + (int64_t)z * ny * Kx + kx0;
+    C *S2 = (C *)p.S2 + blockIdx.y * p.st_s2 + (int64_t)z * ny * Kx + kx0;
     for (int i = threadIdx.x; i < ny * B; i += blockDim.x) {
         const int kp = i >> lgB, b = i & (B - 1);
         C v = cmk(T(0), T(0));
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(256) k_fz(DevPlan p, int B) {
     const int ntile = Kx / B;
     const int kp = blockIdx.x / ntile;
     const int kx0 = (blockIdx.x - kp * ntile) * B;
-    C *S2 = (C *)p.S2 + (int64_t)kp * Kx + kx0;
+    C *S2 = (C *)p.S2 + blockIdx.y * p.st_s2 + (int64_t)kp * Kx + kx0;
     const int64_t zs = (int64_t)ny * Kx;
     const int z0 = p.z0, nza = p.nz_act;
     if (kp == ny / 2) {  // Nyquist row in y: dropped
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
     const int z = (p.z0 + zi) & (p.L[2] - 1);
     const int kx0 = (blockIdx.x - zi * ntile) * B;
     const int2 iv = p.plane_iv[z];
-    const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx + kx0;
+    const C *S2 = (const C *)p.S2 + blockIdx.y * p.st_s2 + (int64_t)z * ny * Kx + kx0;
     // position q holds frequency k = fft_freq(q): mode k (k < ny/2) or mode
     // k - Ly (k > Ly - ny/2), zero elsewhere
     const RadixPlan rp = radix_plan(lgLy);
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(256) k_iy(DevPlan p, int B) {
         [&](int i, C v) { buf[(i >> lgB) * ld + (i & (B - 1))] = v; });
     __syncthreads();
     fft_columns_inplace<C, true>(buf, lgLy, ld, lgB, stw);
-    C *S1 = (C *)p.S1 + (int64_t)z * Ly * Kx + kx0;
+    C *S1 = (C *)p.S1 + blockIdx.y * p.st_s1 + (int64_t)z * Ly * Kx + kx0;
     for (int i = threadIdx.x; i < iv.y * B; i += blockDim.x) {
         const int y = (iv.x + (i >> lgB)) & (Ly - 1), b = i & (B - 1);
         S1[(int64_t)y * Kx + b] = buf[y * ld + b];
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
     pdl_wait();
     pdl_trigger();
     __syncthreads();
-    const C *S1 = (const C *)p.S1;
+    const C *S1 = (const C *)p.S1 + blockIdx.y * p.st_s1;
     typedef typename VecT<T>::T4 T4;  // (xa, xb) of one mode, loaded together
     pipelined_copy<T4>(
         PB * Kx,
@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(256) k_ix(DevPlan p, int PB) {
         });
     __syncthreads();
     const C *res = fft_columns<C, true>(b0, b1, Lx, ld, PB, stw);
-    T *G = (T *)p.gridB;
+    T *G = (T *)p.gridB + blockIdx.y * p.st_grid;
     typedef typename VecW<T>::V V;
     constexpr int VW = VecW<T>::W;
     constexpr int lgVW = VW == 4 ? 2 : 1;
@@ -670,7 +670,7 @@ __device__ __forceinline__ void k_fy_c_body(const DevPlan &p) {
     pdl_wait();
     pdl_trigger();
     const int2 iv = p.plane_iv[z];
-    const C *S1 = (const C *)p.S1 + (int64_t)z * Sh::L * Kx + kx0 + b;
+    const C *S1 = (const C *)p.S1 + blockIdx.y * p.st_s1 + (int64_t)z * Sh::L * Kx + kx0 + b;
     C v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -680,7 +680,7 @@ __device__ __forceinline__ void k_fy_c_body(const DevPlan &p) {
     __syncthreads();  // twiddles
     col_stage<C, LG, 0, false>(v, t, tw);
     col_forward_from<C, LG, 1>(buf, v, t, b, tw);
-    C *S2 = (C *)p.S2 + (int64_t)z * ny * Kx + kx0 + b;
+    C *S2 = (C *)p.S2 + blockIdx.y * p.st_s2 + (int64_t)z * ny * Kx + kx0 + b;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int k = col_freq<LG>(col_idx<LG, Sh::NS - 1>(t, r));
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(1 << LG, (1024 >> LG) > 0 ? (1024 >> LG) : 1) 
     const int64_t zs = (int64_t)ny * Kx;
     pdl_wait();
     pdl_trigger();
-    C *S2 = (C *)p.S2 + (int64_t)kp * Kx + kx0 + b;
+    C *S2 = (C *)p.S2 + blockIdx.y * p.st_s2 + (int64_t)kp * Kx + kx0 + b;
     if (kp == ny / 2) {  // Nyquist row in y: dropped
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
@@ -776,7 +776,7 @@ __device__ __forceinline__ void k_iy_c_body(const DevPlan &p) {
     pdl_wait();
     pdl_trigger();
     const int2 iv = p.plane_iv[z];
-    const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx + kx0 + b;
+    const C *S2 = (const C *)p.S2 + blockIdx.y * p.st_s2 + (int64_t)z * ny * Kx + kx0 + b;
     C v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -791,7 +791,7 @@ __device__ __forceinline__ void k_iy_c_body(const DevPlan &p) {
     __syncthreads();  // twiddles
     col_stage<C, LG, Sh::NS - 1, true>(v, t, tw);
     col_inverse_from<C, LG, Sh::NS - 2>(buf, v, t, b, tw);
-    C *S1 = (C *)p.S1 + (int64_t)z * Sh::L * Kx + kx0 + b;
+    C *S1 = (C *)p.S1 + blockIdx.y * p.st_s1 + (int64_t)z * Sh::L * Kx + kx0 + b;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int y = col_idx<LG, 0>(t, r);
@@ -886,7 +886,7 @@ __global__ void __launch_bounds__(1 << LG) k_ix_s(DevPlan p) {
     }
     // stage 0 reads frequencies t + r L / 8 of the pair's complex spectrum
     // Y(k) = xa(k) + i xb(k), Y(L - k) = conj(xa(k)) + i conj(xb(k))
-    const C *S1 = (const C *)p.S1 + r0 / Sh::L * Kx;
+    const C *S1 = (const C *)p.S1 + blockIdx.y * p.st_s1 + r0 / Sh::L * Kx;
     C v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -910,7 +910,7 @@ __global__ void __launch_bounds__(1 << LG) k_ix_s(DevPlan p) {
     __syncthreads();
     stk_from<C, LG, 1, true>(buf, t, b, tw);
     if (!on) return;
-    T *G = (T *)p.gridB + r0;
+    T *G = (T *)p.gridB + blockIdx.y * p.st_grid + r0;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int x = t + r * TPB;
@@ -958,7 +958,7 @@ __global__ void __launch_bounds__(256) k_fxy(DevPlan p, int PB) {
     const int npr = iv.y >> 1;
     const int j0 = c * PBc;
     const int nj = npr - j0 < 0 ? 0 : (npr - j0 > PBc ? PBc : npr - j0);
-    T *A = (T *)p.gridA + (int64_t)z * Ly * Lx;
+    T *A = (T *)p.gridA + blockIdx.y * p.st_grid + (int64_t)z * Ly * Lx;
     typedef typename VecW<T>::V V;
     constexpr int VW = VecW<T>::W;
     const int nv = Lx / VW, lgnv = __ffs(nv) - 1;
@@ -1000,7 +1000,7 @@ __global__ void __launch_bounds__(256) k_fxy(DevPlan p, int PB) {
     cluster.sync();
     fft_columns_inplace<C, false>(P, lgLy, ldp, lgKC, twy);
     const RadixPlan rp = radix_plan(lgLy);
-    C *S2 = (C *)p.S2 + (int64_t)z * ny * Kx + c * KC;
+    C *S2 = (C *)p.S2 + blockIdx.y * p.st_s2 + (int64_t)z * ny * Kx + c * KC;
     for (int i = threadIdx.x; i < ny * KC; i += blockDim.x) {
         const int kp = i >> lgKC, b = i & (KC - 1);
         C v = cmk(T(0), T(0));
@@ -1042,7 +1042,7 @@ __global__ void __launch_bounds__(256) k_iyx(DevPlan p, int PB) {
     // in-place inverse: position q holds mode k = fft_freq(q) (k < ny/2), or
     // k - Ly (k > Ly - ny/2), zero elsewhere
     const RadixPlan rp = radix_plan(lgLy);
-    const C *S2 = (const C *)p.S2 + (int64_t)z * ny * Kx + c * KC;
+    const C *S2 = (const C *)p.S2 + blockIdx.y * p.st_s2 + (int64_t)z * ny * Kx + c * KC;
     pipelined_copy<C>(
         Ly * KC,
         [&](int i) {
@@ -1077,7 +1077,7 @@ __global__ void __launch_bounds__(256) k_iyx(DevPlan p, int PB) {
     // all frequencies of this CTA's pairs have arrived
     cluster.sync();
     const C *res = fft_columns<C, true>(X0, X1, Lx, ldx, PBc, twx);
-    T *G = (T *)p.gridB + (int64_t)z * Ly * Lx;
+    T *G = (T *)p.gridB + blockIdx.y * p.st_grid + (int64_t)z * Ly * Lx;
     typedef typename VecW<T>::V V;
     constexpr int VW = VecW<T>::W;
     const int nv = Lx / VW, lgnv = __ffs(nv) - 1;
@@ -1162,7 +1162,7 @@ template <typename T> static cudaError_t fx_t(const DevPlan &p, cudaStream_t s) 
     cudaError_t e = prep(k_fx<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.n_row_pairs == 0) return cudaSuccess;
-    { const cudaError_t le = launch_k(k_fx<T>, (p.n_row_pairs + PB - 1) / PB, 256, sm, s, p, PB); if (le != cudaSuccess) return le; }
+    { const cudaError_t le = launch_k(k_fx<T>, dim3((p.n_row_pairs + PB - 1) / PB, p.ks), 256, sm, s, p, PB); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) {
@@ -1171,7 +1171,7 @@ template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) 
     if (col_engine_ok(p, p.L[0]) && p.L[0] >= 512) {
         if (p.n_row_pairs == 0) return cudaSuccess;
         const size_t sm = ((size_t)p.L[0] * (CB + 1) + p.L[0]) * 2 * sizeof(T);
-        const unsigned nb = (unsigned)((p.n_row_pairs + CB - 1) / CB);
+        const dim3 nb((unsigned)((p.n_row_pairs + CB - 1) / CB), (unsigned)p.ks);
         SLP_COL_DISPATCH(k_ix_s, T, __builtin_ctz(p.L[0]), nb, sm, s)
     }
     const size_t ce = 2 * sizeof(T);
@@ -1180,14 +1180,14 @@ template <typename T> static cudaError_t ix_t(const DevPlan &p, cudaStream_t s) 
     cudaError_t e = prep(k_ix<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.n_row_pairs == 0) return cudaSuccess;
-    { const cudaError_t le = launch_k(k_ix<T>, (p.n_row_pairs + PB - 1) / PB, 256, sm, s, p, PB); if (le != cudaSuccess) return le; }
+    { const cudaError_t le = launch_k(k_ix<T>, dim3((p.n_row_pairs + PB - 1) / PB, p.ks), 256, sm, s, p, PB); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) {
     if (col_engine_ok(p, p.L[1])) {
         if (p.nz_act == 0) return cudaSuccess;
         const size_t sm = ((size_t)p.L[1] * (CB + 1) + p.L[1]) * 2 * sizeof(T);
-        const unsigned nb = (unsigned)(p.nz_act * (p.Kx / CB));
+        const dim3 nb((unsigned)(p.nz_act * (p.Kx / CB)), (unsigned)p.ks);
         SLP_COL_DISPATCH2(k_fy_c, k_fy_c_long, T, __builtin_ctz(p.L[1]), nb, sm, s)
     }
     const size_t ce = 2 * sizeof(T);
@@ -1196,14 +1196,14 @@ template <typename T> static cudaError_t fy_t(const DevPlan &p, cudaStream_t s) 
     cudaError_t e = prep(k_fy<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
-    { const cudaError_t le = launch_k(k_fy<T>, p.nz_act * (p.Kx / B), 256, sm, s, p, B); if (le != cudaSuccess) return le; }
+    { const cudaError_t le = launch_k(k_fy<T>, dim3(p.nz_act * (p.Kx / B), p.ks), 256, sm, s, p, B); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) {
     if (col_engine_ok(p, p.L[1])) {
         if (p.nz_act == 0) return cudaSuccess;
         const size_t sm = ((size_t)p.L[1] * (CB + 1) + p.L[1]) * 2 * sizeof(T);
-        const unsigned nb = (unsigned)(p.nz_act * (p.Kx / CB));
+        const dim3 nb((unsigned)(p.nz_act * (p.Kx / CB)), (unsigned)p.ks);
         SLP_COL_DISPATCH2(k_iy_c, k_iy_c_long, T, __builtin_ctz(p.L[1]), nb, sm, s)
     }
     const size_t ce = 2 * sizeof(T);
@@ -1212,14 +1212,14 @@ template <typename T> static cudaError_t iy_t(const DevPlan &p, cudaStream_t s) 
     cudaError_t e = prep(k_iy<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
-    { const cudaError_t le = launch_k(k_iy<T>, p.nz_act * (p.Kx / B), 256, sm, s, p, B); if (le != cudaSuccess) return le; }
+    { const cudaError_t le = launch_k(k_iy<T>, dim3(p.nz_act * (p.Kx / B), p.ks), 256, sm, s, p, B); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 template <typename T> static cudaError_t fz_t(const DevPlan &p, cudaStream_t s) {
     if (col_engine_ok(p, p.L[2])) {
         if (p.nz_act == 0) return cudaSuccess;
         const size_t sm = ((size_t)p.L[2] * (CB + 1) + p.L[2]) * 2 * sizeof(T);
-        const unsigned nb = (unsigned)(p.n[1] * (p.Kx / CB));
+        const dim3 nb((unsigned)(p.n[1] * (p.Kx / CB)), (unsigned)p.ks);
         SLP_COL_DISPATCH(k_fz_c, T, __builtin_ctz(p.L[2]), nb, sm, s)
     }
     const size_t ce = 2 * sizeof(T);
@@ -1228,7 +1228,7 @@ template <typename T> static cudaError_t fz_t(const DevPlan &p, cudaStream_t s) 
     cudaError_t e = prep(k_fz<T>, sm);
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
-    { const cudaError_t le = launch_k(k_fz<T>, p.n[1] * (p.Kx / B), 256, sm, s, p, B); if (le != cudaSuccess) return le; }
+    { const cudaError_t le = launch_k(k_fz<T>, dim3(p.n[1] * (p.Kx / B), p.ks), 256, sm, s, p, B); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -1243,7 +1243,7 @@ template <typename K> static cudaError_t launch_cluster(K kern, const DevPlan &p
     if (e != cudaSuccess) return e;
     if (p.nz_act == 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(p.nz_act * FUSE_CL);
+    cfg.gridDim = dim3(p.nz_act * FUSE_CL, p.ks);
     cfg.blockDim = dim3(256);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;

@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(256) k_spread(DevPlan p, int fused_kind, const
 
     const TileItem it = p.spread_items[blockIdx.x];
     const int nsrc = it.end - it.begin;
+    if (p.ks > 1) in = (const T *)p.in_st[blockIdx.y];  // state of a batched launch
     {
         // charges either from the charge kernel (qbuf) or computed here from
         // the input (fused_kind >= 0)
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(256) k_spread(DevPlan p, int fused_kind, const
 
     const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
     const int gxs = it.c0x - M + 1 - XO, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
-    T *grid = (T *)p.gridA;
+    T *grid = (T *)p.gridA + blockIdx.y * p.st_grid;
     // 16-byte vector atomics need an aligned row start inside the grid (TS a
     // multiple of 4 makes gxs a multiple of 4 by construction of XO)
     const bool xin = gxs >= 0 && gxs + XE <= Lx && (gxs & 3) == 0;
@@ -325,6 +326,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spr
 
     const TileItem it = p.spread_items[blockIdx.x];
     const int nsrc = it.end - it.begin;
+    if (p.ks > 1) in = (const T *)p.in_st[blockIdx.y];  // state of a batched launch
     {
         // the tile copies (and the padding up to the window values), 16 bytes per store
         const int n4 = (int)(SM::wv(nwarps) * sizeof(T) / 16);
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spr
     constexpr int TE = G::TE, XE = G::XE;
     const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
     const int gxs = it.c0x - M + 1 - XO, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
-    T *grid = (T *)p.gridA;
+    T *grid = (T *)p.gridA + blockIdx.y * p.st_grid;
     const bool xin = gxs >= 0 && gxs + XE <= Lx && (gxs & 3) == 0;
     if (sizeof(T) == 4 && TS % 4 == 0 && xin) {
         constexpr int NV = XE / 4;
@@ -537,7 +539,8 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
     }
     const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
     const int gx0 = it.c0x - M + 1, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
-    const T *grid = (const T *)p.gridB;
+    const T *grid = (const T *)p.gridB + blockIdx.y * p.st_grid;
+    if (p.ks > 1) phi = (T *)p.out_st[blockIdx.y];  // state of a batched launch
     if (threadIdx.x < nt) {
         const int t = it.begin + threadIdx.x;
         const T4 g = ((const T4 *)p.tgt_grid)[t];
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
         sf[2 * GATHER_CHUNK + threadIdx.x] = g.z;
         sidx[threadIdx.x] = packed_cell(g.w);
         sidx[GATHER_CHUNK + threadIdx.x] = p.tgt_perm[t];
-        sphi[threadIdx.x] = ((const T *)p.phi_part)[t];
+        sphi[threadIdx.x] = ((const T *)p.phi_part)[blockIdx.y * p.N + t];
     }
     constexpr int XE = G::XE;
     const int gxs = gx0 - XO;  // a multiple of 4 when TS is
@@ -673,7 +676,7 @@ static cudaError_t spread_mt(const DevPlan &p, int fused_kind, const void *in, c
             if (e != cudaSuccess) return e;
         }
         if (p.n_spread > 0)
-            { const cudaError_t le = launch_k(k_spread_groups<T, M, TS>, p.n_spread, 32 * nw, sm, s, p, fused_kind, (const T *)in); if (le != cudaSuccess) return le; }
+            { const cudaError_t le = launch_k(k_spread_groups<T, M, TS>, dim3(p.n_spread, p.ks), 32 * nw, sm, s, p, fused_kind, (const T *)in); if (le != cudaSuccess) return le; }
         return cudaGetLastError();
     }
     int nw = 8;
@@ -683,7 +686,7 @@ static cudaError_t spread_mt(const DevPlan &p, int fused_kind, const void *in, c
         cudaError_t e = cudaFuncSetAttribute(k_spread<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    if (p.n_spread > 0) { const cudaError_t le = launch_k(k_spread<T, M, TS>, p.n_spread, 32 * nw, sm, s, p, fused_kind, (const T *)in); if (le != cudaSuccess) return le; }
+    if (p.n_spread > 0) { const cudaError_t le = launch_k(k_spread<T, M, TS>, dim3(p.n_spread, p.ks), 32 * nw, sm, s, p, fused_kind, (const T *)in); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 
@@ -695,7 +698,7 @@ template <typename T, int M, int TS> static cudaError_t gather_mt(const DevPlan 
         cudaError_t e = cudaFuncSetAttribute(k_gather<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    if (p.n_gather > 0) { const cudaError_t le = launch_k(k_gather<T, M, TS>, p.n_gather, 256, sm, s, p, (T *)phi); if (le != cudaSuccess) return le; }
+    if (p.n_gather > 0) { const cudaError_t le = launch_k(k_gather<T, M, TS>, dim3(p.n_gather, p.ks), 256, sm, s, p, (T *)phi); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
 }
 

@@ -113,6 +113,14 @@ struct DevPlan {
     const void *nm_val;        // T4 [nnz] (wx, wy, wz, unused)
     int64_t nm_nnz;
 
+    // state batch of one launch (grid.y): ks states, scratch of state y at
+    // gridA/gridB + y st_grid, S1 + y st_s1, S2 + y st_s2, phi_part + y N;
+    // with ks > 1 the spread reads in_st[y] and the gather writes out_st[y]
+    int ks;
+    int64_t st_grid, st_s1, st_s2;
+    const void *in_st[NEAR_STATES];
+    void *out_st[NEAR_STATES];
+
     int *err;  // device status word (sticky)
 };
 

@@ -951,15 +951,22 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     TRY(dalloc(p, &d.qbuf, sizeof(T) * p.Q));
     TRY(dalloc(p, &d.m4, 4 * sizeof(T) * p.N * slp::NEAR_STATES));
     TRY(dalloc(p, &d.phi_part, sizeof(T) * p.N * slp::NEAR_STATES));
-    TRY(dalloc(p, &d.gridA, sizeof(T) * G));
-    TRY(dalloc(p, &d.gridB, sizeof(T) * G));
-    TRY(dalloc(p, &d.S1, sizeof(T2) * (size_t)p.L[2] * p.L[1] * Kx));
-    TRY(dalloc(p, &d.S2, sizeof(T2) * (size_t)p.L[2] * p.n[1] * Kx));
+    // far-field scratch for a batch of kf states (slp_far_batch)
+    p.kf = slp_far_batch(p);
+    d.ks = 1;
+    d.st_grid = G;
+    d.st_s1 = (int64_t)p.L[2] * p.L[1] * Kx;
+    d.st_s2 = (int64_t)p.L[2] * p.n[1] * Kx;
+    TRY(dalloc(p, &d.gridA, sizeof(T) * G * p.kf));
+    TRY(dalloc(p, &d.gridB, sizeof(T) * G * p.kf));
+    TRY(dalloc(p, &d.S1, sizeof(T2) * d.st_s1 * p.kf));
+    TRY(dalloc(p, &d.S2, sizeof(T2) * d.st_s2 * p.kf));
     // grid A starts zero; rows outside the active region of S1, S2 and grid B
     // are never written, so they are cleared once here
-    if (cudaMemset(d.gridA, 0, sizeof(T) * G) != cudaSuccess || cudaMemset(d.gridB, 0, sizeof(T) * G) != cudaSuccess ||
-        cudaMemset(d.S1, 0, sizeof(T2) * (size_t)p.L[2] * p.L[1] * Kx) != cudaSuccess ||
-        cudaMemset(d.S2, 0, sizeof(T2) * (size_t)p.L[2] * p.n[1] * Kx) != cudaSuccess)
+    if (cudaMemset(d.gridA, 0, sizeof(T) * G * p.kf) != cudaSuccess ||
+        cudaMemset(d.gridB, 0, sizeof(T) * G * p.kf) != cudaSuccess ||
+        cudaMemset(d.S1, 0, sizeof(T2) * d.st_s1 * p.kf) != cudaSuccess ||
+        cudaMemset(d.S2, 0, sizeof(T2) * d.st_s2 * p.kf) != cudaSuccess)
         return fail(SLP_ERR_CUDA, "cudaMemset failed");
 
     std::vector<T> Dt(p.Dtab.begin(), p.Dtab.end());
@@ -1399,10 +1406,11 @@ slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, 
 // S states of nodal input with the precomputed near field, in chunks of up
 // to NEAR_STATES: per chunk, one sorting prep and one pass over the near-field
 // operator for all of the chunk's states run on ex->aux, while ex->main runs
-// each state's spread, FFT passes and gather (the gather of state k reads
-// near-field part k).  Each chunk's branch starts after the previous chunk's
-// gathers (they read the same scratch).  Other inputs or near modes run the
-// single-state pipeline per state.
+// the spread, FFT passes and gather for batches of kf states at a time (one
+// launch per kernel per batch; the gather of state k reads near-field part k).
+// Each chunk's branch starts after the previous chunk's gathers (they read the
+// same scratch).  Other inputs or near modes run the single-state pipeline per
+// state.
 slp_status run_states(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *const *ins, void *const *outs,
                       int S, cudaStream_t s, SlpExec *ex, int *launches) {
     const bool use_matrix = kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
@@ -1426,27 +1434,36 @@ slp_status run_states(slp_plan_s &p, const slp::DevPlan &d, int kind, const void
         TRY(cuda_status(slp::launch_nodal_prep_states(d, sp, K, ex->aux), "nodal prep"));
         TRY(cuda_status(slp::launch_near_matrix_states(d, K, ex->aux), "near-field matrix"));
         TRY(cuda_status(cudaEventRecord(ex->join, ex->aux), "join"));
-        for (int k = 0; k < K; ++k) {
-            TRY(cuda_status(slp::launch_spread(d, kind, ins[c0 + k], m), "spread"));
-            if (d.fuse_pb > 0) {
-                TRY(cuda_status(slp::launch_fft_forward_xy(d, m), "fft xy"));
-            } else {
-                TRY(cuda_status(slp::launch_fft_forward_x(d, m), "fft x"));
-                TRY(cuda_status(slp::launch_fft_forward_y(d, m), "fft y"));
-            }
-            TRY(cuda_status(slp::launch_fft_z_multiply(d, m), "fft z"));
-            if (d.fuse_pb > 0) {
-                TRY(cuda_status(slp::launch_fft_inverse_yx(d, m), "ifft yx"));
-            } else {
-                TRY(cuda_status(slp::launch_fft_inverse_y(d, m), "ifft y"));
-                TRY(cuda_status(slp::launch_fft_inverse_x(d, m), "ifft x"));
-            }
-            if (k == 0) TRY(cuda_status(cudaStreamWaitEvent(m, ex->join, 0), "join wait"));
+        // the far field in batches of kf states: one launch per kernel per batch
+        // (grid.y = state), state f at scratch copy f and near-field part f0 + f
+        int nbatch = 0;
+        for (int f0 = 0; f0 < K; f0 += p.kf, ++nbatch) {
+            const int kb = std::min(p.kf, K - f0);
             slp::DevPlan dk = d;
-            dk.phi_part = (char *)d.phi_part + es * (size_t)p.N * k;
-            TRY(cuda_status(slp::launch_gather(dk, outs[c0 + k], m), "gather"));
+            dk.ks = kb;
+            for (int f = 0; f < kb; ++f) {
+                dk.in_st[f] = ins[c0 + f0 + f];
+                dk.out_st[f] = outs[c0 + f0 + f];
+            }
+            dk.phi_part = (char *)d.phi_part + es * (size_t)p.N * f0;
+            TRY(cuda_status(slp::launch_spread(dk, kind, ins[c0 + f0], m), "spread"));
+            if (d.fuse_pb > 0) {
+                TRY(cuda_status(slp::launch_fft_forward_xy(dk, m), "fft xy"));
+            } else {
+                TRY(cuda_status(slp::launch_fft_forward_x(dk, m), "fft x"));
+                TRY(cuda_status(slp::launch_fft_forward_y(dk, m), "fft y"));
+            }
+            TRY(cuda_status(slp::launch_fft_z_multiply(dk, m), "fft z"));
+            if (d.fuse_pb > 0) {
+                TRY(cuda_status(slp::launch_fft_inverse_yx(dk, m), "ifft yx"));
+            } else {
+                TRY(cuda_status(slp::launch_fft_inverse_y(dk, m), "ifft y"));
+                TRY(cuda_status(slp::launch_fft_inverse_x(dk, m), "ifft x"));
+            }
+            if (f0 == 0) TRY(cuda_status(cudaStreamWaitEvent(m, ex->join, 0), "join wait"));
+            TRY(cuda_status(slp::launch_gather(dk, outs[c0 + f0], m), "gather"));
         }
-        if (launches) *launches += 2 + K * (p.launches_per_eval - 2);
+        if (launches) *launches += 2 + nbatch * (p.launches_per_eval - 2);
     }
     TRY(cuda_status(cudaEventRecord(ex->done, m), "done"));
     TRY(cuda_status(cudaStreamWaitEvent(s, ex->done, 0), "done wait"));
@@ -1510,12 +1527,23 @@ void slp_exec_destroy(SlpExec &e) {
     e = SlpExec();
 }
 
+int slp_far_batch(const slp_plan_s &p) {
+    const int64_t es = p.prec == 64 ? 8 : 4;
+    const int64_t G = (int64_t)p.L[0] * p.L[1] * p.L[2];
+    const int64_t Kx = p.n[0] / 2;
+    const int64_t per = es * (2 * G + 2 * (int64_t)p.L[2] * p.L[1] * Kx + 2 * (int64_t)p.L[2] * p.n[1] * Kx);
+    const int64_t budget = (int64_t)2 << 30;
+    int64_t k = per > 0 ? budget / per : 1;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(slp::NEAR_STATES, k));
+}
+
 int64_t slp_scratch_bytes(const slp_plan_s &p) {
     const int64_t es = p.prec == 64 ? 8 : 4;
     const int64_t G = (int64_t)p.L[0] * p.L[1] * p.L[2];
     const int64_t Kx = p.n[0] / 2;
-    int64_t b = es * p.Q + 5 * es * p.N * slp::NEAR_STATES + 2 * es * G + 2 * es * p.L[2] * p.L[1] * Kx +
-                2 * es * p.L[2] * p.n[1] * Kx;
+    const int64_t kf = slp_far_batch(p);
+    int64_t b = es * p.Q + 5 * es * p.N * slp::NEAR_STATES +
+                kf * (2 * es * G + 2 * es * p.L[2] * p.L[1] * Kx + 2 * es * p.L[2] * p.n[1] * Kx);
     if (p.opts.deterministic) b += es * 32 * (int64_t)std::max<size_t>(1, p.near_items.size());
     return b;
 }
@@ -1531,10 +1559,10 @@ slp_status slp_alloc_scratch(slp_plan_s &p, slp::DevPlan &out, std::vector<void 
     } reqs[] = {{&out.qbuf, es * p.Q},
                 {&out.m4, 4 * es * p.N * slp::NEAR_STATES},
                 {&out.phi_part, es * p.N * slp::NEAR_STATES},
-                {&out.gridA, es * G},
-                {&out.gridB, es * G},
-                {&out.S1, 2 * es * p.L[2] * p.L[1] * Kx},
-                {&out.S2, 2 * es * p.L[2] * p.n[1] * Kx},
+                {&out.gridA, es * G * p.kf},
+                {&out.gridB, es * G * p.kf},
+                {&out.S1, 2 * es * p.L[2] * p.L[1] * Kx * p.kf},
+                {&out.S2, 2 * es * p.L[2] * p.n[1] * Kx * p.kf},
                 {&out.phi_near, p.opts.deterministic ? es * 32 * (int64_t)std::max<size_t>(1, p.near_items.size()) : 0}};
     int64_t total = 0;
     for (auto &r : reqs) {
@@ -1551,9 +1579,9 @@ slp_status slp_alloc_scratch(slp_plan_s &p, slp::DevPlan &out, std::vector<void 
         *r.dst = ptr;
         total += (int64_t)nb;
     }
-    if (cudaMemset(out.gridA, 0, es * G) != cudaSuccess || cudaMemset(out.gridB, 0, es * G) != cudaSuccess ||
-        cudaMemset(out.S1, 0, 2 * es * p.L[2] * p.L[1] * Kx) != cudaSuccess ||
-        cudaMemset(out.S2, 0, 2 * es * p.L[2] * p.n[1] * Kx) != cudaSuccess)
+    if (cudaMemset(out.gridA, 0, es * G * p.kf) != cudaSuccess || cudaMemset(out.gridB, 0, es * G * p.kf) != cudaSuccess ||
+        cudaMemset(out.S1, 0, 2 * es * p.L[2] * p.L[1] * Kx * p.kf) != cudaSuccess ||
+        cudaMemset(out.S2, 0, 2 * es * p.L[2] * p.n[1] * Kx * p.kf) != cudaSuccess)
         return slp_fail(SLP_ERR_CUDA, "cudaMemset failed");
     if (bytes) *bytes = total;
     return SLP_OK;

@@ -49,6 +49,7 @@ struct slp_plan_s {
     // parameters
     int L[3] = {0, 0, 0}, n[3] = {0, 0, 0}, m = 0, TS = 8, TE = 0;
     int TSg = 8;  // target (gather) tile size in cells
+    int kf = 1;   // states of one far-field batch (scratch copies per scratch set)
     int kernel_mode = SLP_KERNEL_RADIAL, near_mode = SLP_NEAR_ON_THE_FLY;
     int grid_raised = 0;
     double ctr[3] = {0, 0, 0}, P[3] = {0, 0, 0}, D[3] = {0, 0, 0};
@@ -112,6 +113,10 @@ slp_status slp_alloc_scratch(slp_plan_s &p, slp::DevPlan &out, std::vector<void 
 
 // Bytes of one scratch set of `p`.
 int64_t slp_scratch_bytes(const slp_plan_s &p);
+
+// States of one far-field batch: the spread, FFT and gather scratch is held
+// this many times (at most NEAR_STATES, within 2 GB per scratch set).
+int slp_far_batch(const slp_plan_s &p);
 
 // Current device switched to `dev` for the guard's lifetime.
 struct SlpDeviceGuard {
