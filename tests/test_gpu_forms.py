@@ -111,3 +111,35 @@ def test_eval_states_matches_single_evaluations():
             assert rel_l2(got2[k], run(slp, plan, slp.SLP_INPUT_SIGMA, sig[k], 32)) < 1e-6
     finally:
         slp.slp_destroy(plan)
+
+
+@pytest.mark.parametrize("prec,tol,fuse", [(32, 1e-5, 1), (64, 1e-10, 0)], ids=["fp32-fused", "fp64"])
+def test_eval_states_fused_passes_and_fp64(prec, tol, fuse):
+    """State-batched far field through the fused plane passes (FP32) and in
+    FP64: 5 states against single evaluations and the oracle."""
+    slp = lib()
+    torch = torch_cuda()
+    V, T = meshes.icosphere(3)
+    o = slp.slp_default_opts()
+    o.precision = prec
+    for d in range(3):
+        o.grid[d] = 64
+    o.fuse_plane_passes = fuse
+    plan = slp.slp_plan(V, T, 7, tol, o)
+    try:
+        info = slp.slp_query(plan)
+        assert info["fused_plane_passes"] == fuse
+        S = 5
+        dt = torch.float64 if prec == 64 else torch.float32
+        ms = np.stack([fields.smooth_random(V, 500 + k) for k in range(S)])
+        d_in = torch.as_tensor(ms.reshape(-1), dtype=dt, device="cuda")
+        d_out = torch.empty(S * V.shape[0], dtype=dt, device="cuda")
+        slp.slp_eval_states(plan, slp.SLP_INPUT_NODAL_MAG, S, d_in, d_out)
+        torch.cuda.synchronize()
+        got = d_out.double().cpu().numpy().reshape(S, -1)
+        for k in range(S):
+            ref = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, ms[k], prec)
+            assert rel_l2(got[k], ref) < (1e-12 if prec == 64 else 1e-6), k
+        assert rel_l2(got[2], oracle.slp_nodal(V, T, 7, ms[2])) <= tol
+    finally:
+        slp.slp_destroy(plan)
