@@ -215,7 +215,10 @@ slp_status slp_eval_direct_static(const double *d_vertices, int64_t n_vertices, 
  * the batch: the caller refills d_in and reads d_phi between runs).
  * lanes_per_plan (1..64) scratch sets per plan run that plan's items
  * concurrently on separate streams (lane 0 is the plan's own scratch, the
- * others are allocated here); items are dealt round-robin to the lanes.
+ * others are allocated here); items are dealt round-robin to the lanes.  A
+ * lane evaluates its items as slp_eval_states does (shared near-field passes,
+ * state-batched far field), so one lane per plan is usually the fastest and
+ * needs no extra scratch.
  * slp_batch_create captures every item into one CUDA graph (fork/join over
  * the lanes); slp_batch_run launches it on `stream`.  All plans must share a
  * device.  A plan must not be evaluated elsewhere while a batch that uses it
