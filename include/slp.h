@@ -108,7 +108,13 @@ typedef struct {
     int fuse_plane_passes; /* x and y FFT passes fused per z plane (one block per plane, the plane
                               spectrum in shared memory): 0 off, 1 on where the plane fits,
                               -1 automatic (on when there are at least two active planes per SM) */
-    int reserved[6];
+    int fuse_column_passes; /* the y pass, the z pass with the kernel multiply and the inverse y pass
+                               fused, one cluster of four CTAs per stored x frequency holding that
+                               slab of the spectrum in distributed shared memory (needs equal y and
+                               z grids of 32..256 and unfused plane passes): 0 off, 1 on where it
+                               applies, -1 automatic (off: the separate passes, chained by
+                               programmatic dependent launch, measured faster) */
+    int reserved[5];
 } slp_plan_opts;
 
 typedef struct {
@@ -141,6 +147,7 @@ typedef struct {
                                     the window of some source or target, widened to row pairs */
     int active_planes;           /* z planes the FFT passes along y work on */
     int fused_plane_passes;      /* 1: the x and y passes run fused, one block per active plane */
+    int fused_column_passes;     /* 1: FY, FZ * D * IZ and IY run as one cluster launch */
 } slp_info;
 
 /* Fill opts with defaults: precision 32, automatic grid/m/kernel/near mode,

@@ -61,7 +61,8 @@ class slp_plan_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("grid", ctypes.c_int * 3), ("m", ctypes.c_int),
                 ("kernel_mode", ctypes.c_int), ("near_mode", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("device", ctypes.c_int), ("allow_grid_raise", ctypes.c_int), ("check_mesh", ctypes.c_int),
-                ("fuse_plane_passes", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("fuse_plane_passes", ctypes.c_int), ("fuse_column_passes", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 SLP_TUNE_MAX = 8
@@ -109,7 +110,8 @@ class slp_info(ctypes.Structure):
                 ("bytes_device", ctypes.c_int64), ("n_spread_items", ctypes.c_int64),
                 ("n_gather_items", ctypes.c_int64), ("n_near_items", ctypes.c_int64),
                 ("launches_per_eval", ctypes.c_int), ("active_rows", ctypes.c_int64),
-                ("active_planes", ctypes.c_int), ("fused_plane_passes", ctypes.c_int)]
+                ("active_planes", ctypes.c_int), ("fused_plane_passes", ctypes.c_int),
+                ("fused_column_passes", ctypes.c_int)]
 
     def to_dict(self):
         out = {}
@@ -457,7 +459,7 @@ class Plan:
 
     def __init__(self, vertices, triangles, quadrature=7, tolerance=1e-5, precision=32, grid=None, m=0,
                  kernel_mode=SLP_KERNEL_AUTO, near_mode=SLP_NEAR_AUTO, deterministic=False, device=0,
-                 allow_grid_raise=True, check_mesh=True, fuse_plane_passes=-1):
+                 allow_grid_raise=True, check_mesh=True, fuse_plane_passes=-1, fuse_column_passes=-1):
         o = slp_default_opts()
         o.precision = int(precision)
         if grid is not None:
@@ -471,6 +473,7 @@ class Plan:
         o.allow_grid_raise = int(bool(allow_grid_raise))
         o.check_mesh = int(bool(check_mesh))
         o.fuse_plane_passes = int(fuse_plane_passes)
+        o.fuse_column_passes = int(fuse_column_passes)
         self.handle = slp_plan(vertices, triangles, quadrature, tolerance, o)
         self.info = slp_query(self.handle)
         self.n_targets = self.info["n_targets"]

@@ -1096,6 +1096,144 @@ __global__ void __launch_bounds__(256) k_iyx(DevPlan p, int PB) {
     }
 }
 
+// ---------------------------------------------------------------- fused column passes
+// FY, FZ * D * IZ and IY of one stored x frequency kx run in a cluster of
+// YZY_CL CTAs; the kx slab of the spectrum, P[ky'][z] over the n_y kept
+// modes and the active z planes, never leaves distributed shared memory.
+// CTA c owns the active planes zi in [c ZC, (c+1) ZC) of the slab:
+//   1. FY of its planes (column engine, S1 rows in, kept modes into its P);
+//   2. after a cluster barrier, the z pencils of rows ky' in [c KC, (c+1) KC):
+//      each element is read from, and written back to, the P of the CTA that
+//      owns its plane (every element has one reader and one writer);
+//   3. after a second barrier, IY of its planes from its own P into S1.
+// A block of G L threads runs G groups of the column engine side by side
+// (group g transforms columns 8 g .. 8 g + 7 with its own exchange buffer).
+// No CTA touches another's shared memory after the second barrier, so CTAs
+// may exit in any order.  Needs L_y = L_z = L.
+
+template <typename T, int LG>
+__global__ void __launch_bounds__(512) k_yzy(DevPlan p, int ZC, int ZP) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    typedef typename VecT<T>::T2 C;
+    typedef ColShape<LG> Sh;
+    constexpr int L = Sh::L;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Kx = p.Kx, ny = p.n[1], nz = p.n[2];
+    const int KC = ny / YZY_CL;
+    const int c = (int)cluster.block_rank();
+    const int kx = (int)blockIdx.x / YZY_CL;
+    const int g = threadIdx.x >> LG, lt = threadIdx.x & (L - 1);
+    const int b = lt & (CB - 1), t = lt >> 3;
+    const int col = g * CB + b;
+    C *P = (C *)smem_raw;                 // [ny][ZP]
+    C *tw = P + (size_t)ny * ZP;          // [L]
+    C *buf = tw + L + (size_t)g * L * (CB + 1);  // this group's exchange buffer
+    for (int i = threadIdx.x; i < L; i += blockDim.x) tw[i] = ((const C *)p.tw[1])[i];
+    const int z0 = p.z0, nza = p.nz_act;
+
+    // step 1 / 3 column: active plane zi of this CTA
+    const int zi = c * ZC + col;
+    const bool on13 = col < ZC && zi < nza;
+    const int z = (z0 + zi) & (L - 1);
+    // step 2 column: row ky' (the Nyquist row ny / 2 is dropped)
+    const int kp = c * KC + col;
+    const bool on2 = col < KC && kp != ny / 2;
+    // multipliers of step 2 (plan data, loaded before the wait)
+    T dv[8];
+    {
+        const int aky = kp < ny / 2 ? kp : ny - kp;
+        const T *D = (const T *)p.Dtab + (int64_t)aky * Kx + kx;
+        const int64_t dz = (int64_t)(ny / 2) * Kx;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int kz = col_freq<LG>(col_idx<LG, Sh::NS - 1>(t, r));
+            const int akz = kz < L / 2 ? kz : L - kz;
+            dv[r] = (on2 && akz < nz / 2) ? D[akz * dz] : T(0);
+        }
+    }
+    const int2 iv = on13 ? p.plane_iv[z] : make_int2(0, 0);
+    pdl_wait();
+    pdl_trigger();
+    C *S1 = (C *)p.S1 + blockIdx.y * p.st_s1 + (int64_t)z * L * Kx + kx;
+
+    // 1. FY of plane z: active rows in, kept modes to P[ky'][col]
+    C v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int y = col_idx<LG, 0>(t, r);
+        v[r] = (on13 && ((y - iv.x) & (L - 1)) < iv.y) ? S1[(int64_t)y * Kx] : cmk(T(0), T(0));
+    }
+    __syncthreads();  // twiddles
+    col_stage<C, LG, 0, false>(v, t, tw);
+    col_forward_from<C, LG, 1>(buf, v, t, b, tw);
+    if (on13) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int k = col_freq<LG>(col_idx<LG, Sh::NS - 1>(t, r));
+            if (k < ny / 2)
+                P[k * ZP + col] = v[r];
+            else if (k > L - ny / 2)
+                P[(k - L + ny) * ZP + col] = v[r];
+        }
+    }
+    cluster.sync();
+
+    // 2. z pencil of row kp: element z lives in the P of CTA (z - z0) / ZC
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int zr = col_idx<LG, 0>(t, r);
+        const int zir = (zr - z0) & (L - 1);
+        C x = cmk(T(0), T(0));
+        if (on2 && zir < nza) {
+            const int q = zir / ZC;
+            x = *cluster.map_shared_rank(P + kp * ZP + (zir - q * ZC), q);
+        }
+        v[r] = x;
+    }
+    col_stage<C, LG, 0, false>(v, t, tw);
+    col_forward_from<C, LG, 1>(buf, v, t, b, tw);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = cscale(v[r], dv[r]);
+    col_stage<C, LG, Sh::NS - 1, true>(v, t, tw);
+    col_inverse_from<C, LG, Sh::NS - 2>(buf, v, t, b, tw);
+    if (on2) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int zr = col_idx<LG, 0>(t, r);
+            const int zir = (zr - z0) & (L - 1);
+            if (zir < nza) {
+                const int q = zir / ZC;
+                *cluster.map_shared_rank(P + kp * ZP + (zir - q * ZC), q) = v[r];
+            }
+        }
+    }
+    cluster.sync();
+
+    // 3. IY of plane z: kept modes from P (zero padded), active rows to S1
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int k = col_freq<LG>(col_idx<LG, Sh::NS - 1>(t, r));
+        C x = cmk(T(0), T(0));
+        if (on13) {
+            if (k < ny / 2)
+                x = P[k * ZP + col];
+            else if (k > L - ny / 2)
+                x = P[(k - L + ny) * ZP + col];
+        }
+        v[r] = x;
+    }
+    col_stage<C, LG, Sh::NS - 1, true>(v, t, tw);
+    col_inverse_from<C, LG, Sh::NS - 2>(buf, v, t, b, tw);
+    if (on13) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int y = col_idx<LG, 0>(t, r);
+            if (((y - iv.x) & (L - 1)) < iv.y) S1[(int64_t)y * Kx] = v[r];
+        }
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 // Batch sizes: at most 8 transforms per block (more blocks for the small
 // grids, where the passes are latency-bound), two buffers of (L x (B+1))
@@ -1264,6 +1402,48 @@ template <typename T> static cudaError_t fxy_t(const DevPlan &p, cudaStream_t s)
 template <typename T> static cudaError_t iyx_t(const DevPlan &p, cudaStream_t s) {
     return launch_cluster(k_iyx<T>, p, fused_cta_smem(p, p.fuse_pb, 2 * sizeof(T)), s);
 }
+
+// shared memory of one CTA of the fused column passes: P [ny][ZP], the
+// twiddles, G exchange buffers [L][CB + 1]
+static size_t yzy_cta_smem(const DevPlan &p, int G, int ZP, size_t ce) {
+    const size_t L = (size_t)p.L[1];
+    return ((size_t)p.n[1] * ZP + L + (size_t)G * L * (CB + 1)) * ce;
+}
+template <typename K> static cudaError_t launch_yzy_cluster(K kern, const DevPlan &p, size_t sm, cudaStream_t s) {
+    cudaError_t e = prep(kern, sm);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p.Kx * YZY_CL, p.ks);
+    cfg.blockDim = dim3(p.yzy_g * p.L[1]);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = YZY_CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    return cudaLaunchKernelEx(&cfg, kern, p, p.yzy_zc, p.yzy_zp);
+}
+template <typename T> static cudaError_t yzy_t(const DevPlan &p, cudaStream_t s) {
+    if (p.nz_act == 0) return cudaSuccess;
+    if (p.yzy_g < 1 || p.yzy_g * p.L[1] > 512 || p.L[1] != p.L[2]) return cudaErrorInvalidConfiguration;
+    const size_t sm = yzy_cta_smem(p, p.yzy_g, p.yzy_zp, 2 * sizeof(T));
+    switch (__builtin_ctz(p.L[1])) {
+        case 5: return launch_yzy_cluster(k_yzy<T, 5>, p, sm, s);
+        case 6: return launch_yzy_cluster(k_yzy<T, 6>, p, sm, s);
+        case 7: return launch_yzy_cluster(k_yzy<T, 7>, p, sm, s);
+        case 8: return launch_yzy_cluster(k_yzy<T, 8>, p, sm, s);
+    }
+    return cudaErrorInvalidConfiguration;
+}
+size_t fused_column_smem(const DevPlan &p, int G, int ZP) {
+    return yzy_cta_smem(p, G, ZP, 2 * (p.prec == 64 ? sizeof(double) : sizeof(float)));
+}
+cudaError_t launch_fft_yzy(const DevPlan &p, cudaStream_t s) { return p.prec == 64 ? yzy_t<double>(p, s) : yzy_t<float>(p, s); }
 
 size_t fused_plane_smem(const DevPlan &p, int PB) {
     if (PB < FUSE_CL || p.Kx < FUSE_CL) return (size_t)-1;  // not applicable

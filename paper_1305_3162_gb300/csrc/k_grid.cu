@@ -37,11 +37,21 @@ __global__ void __launch_bounds__(256) k_nodal_prep(DevPlan p, const T *__restri
 
 // w_k * sigma_k of sorted source k for the three input kinds (NODAL_MAG
 // interpolates the user-order nodal values of the triangle's vertices).
-template <typename T>
-__device__ __forceinline__ T source_charge(const DevPlan &p, int64_t k, int kind, const T *__restrict__ in) {
+// The plan part of a source's charge (its triangle's vertices and user index,
+// and w n), loaded apart from the input so that kernels can fetch it before
+// they wait for the previous kernel.
+template <typename T> struct ChargeRecipe {
+    int4 v;
+    typename VecT<T>::T4 wn;
+};
+template <typename T> __device__ __forceinline__ ChargeRecipe<T> charge_recipe(const DevPlan &p, int64_t k) {
     typedef typename VecT<T>::T4 T4;
-    const int4 v = p.src_tri[k];
-    const T4 wn = ((const T4 *)p.src_wn)[k];
+    return {p.src_tri[k], ((const T4 *)p.src_wn)[k]};
+}
+template <typename T>
+__device__ __forceinline__ T charge_apply(const DevPlan &p, const ChargeRecipe<T> &r, int kind, const T *__restrict__ in) {
+    const int4 v = r.v;
+    const auto wn = r.wn;
     const int u = v.w;
     if (kind == 0) return wn.w * in[u];
     T mx, my, mz;
@@ -59,6 +69,10 @@ __device__ __forceinline__ T source_charge(const DevPlan &p, int64_t k, int kind
         mz = l0 * a[2] + l1 * b[2] + l2 * c[2];
     }
     return mx * wn.x + my * wn.y + mz * wn.z;
+}
+template <typename T>
+__device__ __forceinline__ T source_charge(const DevPlan &p, int64_t k, int kind, const T *__restrict__ in) {
+    return charge_apply<T>(p, charge_recipe<T>(p, k), kind, in);
 }
 
 // qbuf[k] = w_k * sigma_k in sorted source order.
@@ -307,7 +321,7 @@ template <typename T, int M, int TS> struct SpreadSmem {
 };
 
 template <typename T, int M, int TS>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spread_groups(DevPlan p, int fused_kind, const T *__restrict__ in) {
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 4 : 1)) k_spread_groups(DevPlan p, int fused_kind, const T *__restrict__ in) {
     typedef typename VecT<T>::T4 T4;
     typedef TileGeomG<M, TS> G;
     typedef SpreadSmem<T, M, TS> SM;
@@ -345,27 +359,39 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spr
     }
     const T inv_m = T(1) / T(M);
     const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
+    // plan data, fetched before the wait: source positions, the charge recipe
+    // of the thread's first source, and the first 32 cell groups of the
+    // warp's first list (one per lane)
+    {
+        const T4 *src = (const T4 *)p.src_grid + it.begin;
+        for (int i = threadIdx.x; i < nsrc; i += blockDim.x) sg[i] = src[i];
+    }
+    ChargeRecipe<T> r0;
+    if (fused_kind >= 0 && (int)threadIdx.x < nsrc) r0 = charge_recipe<T>(p, it.begin + threadIdx.x);
+    // the plan's cell groups of this item, dealt to SPREAD_WARPS lists; a
+    // block with fewer warps takes lists w, w + nwarps, ...
+    const int *goff = p.sgroup_off + (int64_t)blockIdx.x * (SPREAD_WARPS + 1);
+    const int gl0 = goff[warp], gl1 = goff[warp + 1];
+    const int gpre = gl0 + lane < gl1 ? p.sgroups[gl0 + lane] : 0;
     // charges and grid A may be the previous kernel's output
     pdl_wait();
     pdl_trigger();
     {
-        const T4 *src = (const T4 *)p.src_grid + it.begin;
         const T *qb = (const T *)p.qbuf + it.begin;
         for (int i = threadIdx.x; i < nsrc; i += blockDim.x) {
-            sg[i] = src[i];
-            sq[i] = fused_kind >= 0 ? source_charge<T>(p, it.begin + i, fused_kind, in) : qb[i];
+            if (fused_kind >= 0)
+                sq[i] = charge_apply<T>(p, i == (int)threadIdx.x ? r0 : charge_recipe<T>(p, it.begin + i), fused_kind, in);
+            else
+                sq[i] = qb[i];
         }
     }
     __syncthreads();
 
     const int ix = lane % W, izs = lane / W;
     const bool lane_on = lane < W * ZL;
-    // the plan's cell groups of this item, dealt to SPREAD_WARPS lists; a
-    // block with fewer warps takes lists w, w + nwarps, ...
-    const int *goff = p.sgroup_off + (int64_t)blockIdx.x * (SPREAD_WARPS + 1);
     for (int wl = warp; wl < SPREAD_WARPS; wl += nwarps)
     for (int gi = goff[wl]; gi < goff[wl + 1]; ++gi) {
-        const int gd = p.sgroups[gi];
+        const int gd = (wl == warp && gi - gl0 < 32) ? __shfl_sync(0xffffffffu, gpre, gi - gl0) : p.sgroups[gi];
         const int g0 = gd & 0xffff, ng = gd >> 16;
         if (g0 + ng > nsrc || ng < 1 || ng > SPREAD_GMAX) {
             set_error(p.err, DEV_ERR_BAD_ITEM);
@@ -517,8 +543,6 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 5 : 1)) k_spr
 
 template <typename T, int M, int TS>
 __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) {
-    pdl_wait();
-    pdl_trigger();
     typedef typename VecT<T>::T4 T4;
     typedef TileGeom<M, TS> G;
     constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO;
@@ -541,6 +565,8 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
     const int gx0 = it.c0x - M + 1, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
     const T *grid = (const T *)p.gridB + blockIdx.y * p.st_grid;
     if (p.ks > 1) phi = (T *)p.out_st[blockIdx.y];  // state of a batched launch
+    // plan data first (target positions, permutation, window values): none of
+    // it depends on the previous kernel, so it overlaps that kernel's tail
     if (threadIdx.x < nt) {
         const int t = it.begin + threadIdx.x;
         const T4 g = ((const T4 *)p.tgt_grid)[t];
@@ -549,8 +575,45 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
         sf[2 * GATHER_CHUNK + threadIdx.x] = g.z;
         sidx[threadIdx.x] = packed_cell(g.w);
         sidx[GATHER_CHUNK + threadIdx.x] = p.tgt_perm[t];
-        sphi[threadIdx.x] = ((const T *)p.phi_part)[blockIdx.y * p.N + t];
     }
+    __syncthreads();
+
+    // window values of the warp's targets, wv[t * 3W + axis * W + i]: lane
+    // j = (wax, wi) evaluates point wi along axis wax (FP32: the interval
+    // polynomial, coefficients in registers), and point j + 32 where 3W > 32
+    {
+        const T inv_m = T(1) / T(M);
+        const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
+#pragma unroll
+        for (int j0 = 0; j0 < GW; j0 += 32) {
+            const int j = j0 + lane;
+            if (j < GW) {
+                const int wax = j / W, wi = j - wax * W;
+                T cf[WDEG + 1];
+                if (sizeof(T) == 4) {
+#pragma unroll
+                    for (int k = 0; k <= WDEG; ++k) cf[k] = ((const T *)p.wcoef)[wi * (WDEG + 1) + k];
+                }
+                for (int t = warp; t < nt; t += nwarps) {
+                    const T f = sf[wax * GATHER_CHUNK + t];
+                    T v;
+                    if (sizeof(T) == 4) {
+                        v = cf[WDEG];
+#pragma unroll
+                        for (int k = WDEG - 1; k >= 0; --k) v = v * f + cf[k];
+                    } else {
+                        v = kb_window(f + T(M - 1 - wi), inv_m, beta, isb);
+                    }
+                    wv[t * GW + j] = v;
+                }
+            }
+        }
+    }
+
+    // grid B and the near-field parts are the previous kernels' output
+    pdl_wait();
+    pdl_trigger();
+    if (threadIdx.x < nt) sphi[threadIdx.x] = ((const T *)p.phi_part)[blockIdx.y * p.N + it.begin + threadIdx.x];
     constexpr int XE = G::XE;
     const int gxs = gx0 - XO;  // a multiple of 4 when TS is
     if (sizeof(T) == 4 && TS % 4 == 0 && gxs >= 0 && gxs + XE <= Lx) {
@@ -588,37 +651,6 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
             });
     }
     __syncthreads();
-
-    // window values of the warp's targets, wv[t * 3W + axis * W + i]: lane
-    // j = (wax, wi) evaluates point wi along axis wax (FP32: the interval
-    // polynomial, coefficients in registers), and point j + 32 where 3W > 32
-    const T inv_m = T(1) / T(M);
-    const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
-#pragma unroll
-    for (int j0 = 0; j0 < GW; j0 += 32) {
-        const int j = j0 + lane;
-        if (j < GW) {
-            const int wax = j / W, wi = j - wax * W;
-            T cf[WDEG + 1];
-            if (sizeof(T) == 4) {
-#pragma unroll
-                for (int k = 0; k <= WDEG; ++k) cf[k] = ((const T *)p.wcoef)[wi * (WDEG + 1) + k];
-            }
-            for (int t = warp; t < nt; t += nwarps) {
-                const T f = sf[wax * GATHER_CHUNK + t];
-                T v;
-                if (sizeof(T) == 4) {
-                    v = cf[WDEG];
-#pragma unroll
-                    for (int k = WDEG - 1; k >= 0; --k) v = v * f + cf[k];
-                } else {
-                    v = kb_window(f + T(M - 1 - wi), inv_m, beta, isb);
-                }
-                wv[t * GW + j] = v;
-            }
-        }
-    }
-    __syncwarp();
 
     for (int t = warp; t < nt; t += nwarps) {
         int cx, cy, cz;

@@ -32,7 +32,7 @@ struct StatePtrs {
 
 // Targets per gather item (the plan splits target tiles into items of at
 // most this many; the gather kernel stages one item per block).
-constexpr int GATHER_CHUNK = 64;
+constexpr int GATHER_CHUNK = 32;
 
 // Work item of the near-field kernel: up to 32 sorted targets
 // [tbegin, tbegin + tcount) and a slice [rbegin, rend) of the range list,
@@ -93,6 +93,9 @@ struct DevPlan {
     const int *row_pairs;  // [n_row_pairs] z * (Ly / 2) + y / 2
     int n_row_pairs;
     int fuse_pb;           // > 0: fused plane passes with this many row pairs per plane (a power of two)
+    int yzy_g;             // > 0: fused column passes (FY, FZ * D * IZ, IY in one cluster launch),
+                           // G groups of the column engine per CTA
+    int yzy_zc, yzy_zp;    // active planes per CTA of a fused-column cluster, and P's row stride
 
     const TileItem *spread_items; int n_spread;
     int spread_chunk;             // most sources in one spread item
@@ -134,6 +137,11 @@ cudaError_t launch_fft_forward_y(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_z_multiply(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_inverse_y(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_inverse_x(const DevPlan &p, cudaStream_t s);
+// fused column passes (FY, FZ * D * IZ, IY of one stored x frequency per
+// cluster of YZY_CL CTAs; yzy_g > 0)
+constexpr int YZY_CL = 4;
+cudaError_t launch_fft_yzy(const DevPlan &p, cudaStream_t s);
+size_t fused_column_smem(const DevPlan &p, int G, int ZP);
 // fused plane passes (FX + FY, IY + IX; one block per active plane, fuse_pb > 0)
 cudaError_t launch_fft_forward_xy(const DevPlan &p, cudaStream_t s);
 cudaError_t launch_fft_inverse_yx(const DevPlan &p, cudaStream_t s);

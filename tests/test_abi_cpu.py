@@ -328,3 +328,29 @@ def test_empty_and_minimal_meshes(slp):
     info = slp.slp_query(p)
     assert info["n_targets"] == 4 and info["n_sources"] == 28
     slp.slp_destroy(p)
+
+
+@pytest.mark.parametrize("name", ["slp_mesh", "slp_plan_opts", "slp_info", "slp_tune_info", "slp_server_opts",
+                                  "slp_server_statistics"])
+def test_struct_layouts_match_the_header(slp, name, tmp_path):
+    """Every ctypes mirror of a public struct has the header's size and field
+    offsets (a C program compiled against include/slp.h prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    cls = getattr(slp, name)
+    fields = [f for f, _ in cls._fields_]
+    src = tmp_path / "layout.c"
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "slp.h"', "int main(void) {",
+             f'    printf("%zu\\n", sizeof({name}));']
+    lines += [f'    printf("%zu\\n", offsetof({name}, {f}));' for f in fields]
+    lines += ["    return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    assert got[0] == ctypes.sizeof(cls), (name, got[0], ctypes.sizeof(cls))
+    for f, off in zip(fields, got[1:]):
+        assert off == getattr(cls, f).offset, (name, f, off, getattr(cls, f).offset)

@@ -113,10 +113,12 @@ def test_eval_states_matches_single_evaluations():
         slp.slp_destroy(plan)
 
 
-@pytest.mark.parametrize("prec,tol,fuse", [(32, 1e-5, 1), (64, 1e-10, 0)], ids=["fp32-fused", "fp64"])
-def test_eval_states_fused_passes_and_fp64(prec, tol, fuse):
-    """State-batched far field through the fused plane passes (FP32) and in
-    FP64: 5 states against single evaluations and the oracle."""
+@pytest.mark.parametrize("prec,tol,fuse,fcol", [(32, 1e-5, 1, 0), (32, 1e-5, 0, 1), (64, 1e-10, 0, 1), (64, 1e-10, 0, 0)],
+                         ids=["fp32-fused-plane", "fp32-fused-column", "fp64-fused-column", "fp64"])
+def test_eval_states_fused_passes_and_fp64(prec, tol, fuse, fcol):
+    """State-batched far field through the fused plane passes (FP32), the
+    fused column passes (FP32, FP64) and the separate passes (FP64): 5
+    states against single evaluations and the oracle."""
     slp = lib()
     torch = torch_cuda()
     V, T = meshes.icosphere(3)
@@ -125,10 +127,12 @@ def test_eval_states_fused_passes_and_fp64(prec, tol, fuse):
     for d in range(3):
         o.grid[d] = 64
     o.fuse_plane_passes = fuse
+    o.fuse_column_passes = fcol
     plan = slp.slp_plan(V, T, 7, tol, o)
     try:
         info = slp.slp_query(plan)
         assert info["fused_plane_passes"] == fuse
+        assert info["fused_column_passes"] == fcol
         S = 5
         dt = torch.float64 if prec == 64 else torch.float32
         ms = np.stack([fields.smooth_random(V, 500 + k) for k in range(S)])

@@ -57,17 +57,20 @@ def test_input_kinds_sphere_L3(kind, prec, tol):
         slp.slp_destroy(plan)
 
 
-@pytest.mark.parametrize("fuse", [0, 1], ids=["separate", "fused"])
-def test_sphere_L5_workload(fuse):
+@pytest.mark.parametrize("fuse,fcol", [(0, 0), (1, 0), (0, 1)], ids=["separate", "fused-plane", "fused-column"])
+def test_sphere_L5_workload(fuse, fcol):
     """Sphere level 5 (20480 triangles), 7-point rule, grid 128^3, FP32, 1e-5,
-    with the x and y FFT passes separate and fused per plane."""
+    with the FFT passes separate, x and y fused per plane, and y, z, inverse
+    y fused per x frequency."""
     slp = lib()
     w = workloads.sphere()
-    plan = _plan(slp, w.V, w.T, w.quad, w.tolerance, w.precision, w.grid, fuse_plane_passes=fuse)
+    plan = _plan(slp, w.V, w.T, w.quad, w.tolerance, w.precision, w.grid, fuse_plane_passes=fuse,
+                 fuse_column_passes=fcol)
     try:
         info = slp.slp_query(plan)
         assert info["grid"] == [128, 128, 128] and not info["grid_raised"]
         assert info["fused_plane_passes"] == fuse
+        assert info["fused_column_passes"] == fcol
         phi = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, w.m_nodal, 32)
         ref = oracle.slp_nodal(w.V, w.T, w.quad, w.m_nodal)
         err = rel_l2(phi, ref)
@@ -77,6 +80,37 @@ def test_sphere_L5_workload(fuse):
         assert rel_t.max() < 1e-4
     finally:
         slp.slp_destroy(plan)
+
+
+@pytest.mark.parametrize("case", ["cube-L32-fp64", "sphere3-L64-fp32", "sphere3-L64-fp64", "sphere4-L128-fp32",
+                                  "sphere4-L256-fp32"])
+def test_fused_column_passes_match_separate(case):
+    """The fused column passes (FY, FZ * D * IZ, IY in one cluster launch)
+    give the separate passes' result at every length they compile for, in
+    both precisions; where they do not apply (256^3 here: too many modes per
+    CTA) the plan keeps the separate passes."""
+    slp = lib()
+    if case.startswith("cube"):
+        V, T = meshes.cube(8)
+        q, L = 3, 32
+    else:
+        V, T = meshes.icosphere(3 if "sphere3" in case else 4)
+        q, L = 7, int(case.split("-L")[1].split("-")[0])
+    prec = 64 if case.endswith("fp64") else 32
+    tol = 1e-10 if prec == 64 else 1e-5
+    m = fields.smooth_random(V, 77)
+    res = {}
+    for fcol in (0, 1):
+        plan = _plan(slp, V, T, q, tol, prec, (L, L, L), fuse_plane_passes=0, fuse_column_passes=fcol)
+        try:
+            info = slp.slp_query(plan)
+            res[fcol] = (info["fused_column_passes"], run(slp, plan, slp.SLP_INPUT_NODAL_MAG, m, prec))
+        finally:
+            slp.slp_destroy(plan)
+    assert res[0][0] == 0
+    assert res[1][0] == (0 if L == 256 else 1)
+    assert rel_l2(res[1][1], res[0][1]) < (1e-13 if prec == 64 else 2e-6)
+    assert rel_l2(res[1][1], oracle.slp_nodal(V, T, q, m)) <= tol
 
 
 def test_repeat_and_host_entry_point():
