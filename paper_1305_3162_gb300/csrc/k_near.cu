@@ -267,19 +267,31 @@ __global__ void __launch_bounds__(128) k_near_matrix(DevPlan p) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * 4 + warp;
     if (t >= p.N) return;
-    const T4 *val = (const T4 *)p.nm_val;
     const T4 *m4 = (const T4 *)p.m4;  // sorted nodal m (k_nodal_prep)
-    const int64_t e0 = p.nm_rowptr[t], e1 = p.nm_rowptr[t + 1];
+    const int64_t e0 = p.nm_rowptr[t];
+    const int n = (int)(p.nm_rowptr[t + 1] - e0);  // a row holds < 2^31 entries
+    const T4 *row = (const T4 *)p.nm_val + e0 + lane;
     T acc = T(0);
-    // batches of 32 U entries, predicated, so a row of ~500 entries takes two
-    // batches with U loads in flight per lane
-    for (int64_t e = e0 + lane; e < e1; e += 32 * U) {
+    // batches of 32 U entries (U 16-byte loads in flight per lane): the full
+    // batches without predicates, 32-bit offsets from the row start, then
+    // one predicated tail; lane l adds its entries l, l + 32, ... in order
+    int j = 0;
+    for (; j + 32 * U <= n; j += 32 * U) {
+        T4 w[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) w[u] = ld_stream(row + j + 32 * u);  // streamed once per evaluation
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const T4 mv = m4[packed_cell(w[u].w)];
+            acc += w[u].x * mv.x + w[u].y * mv.y + w[u].z * mv.z;
+        }
+    }
+    if (j < n) {
         T4 w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t i = e + 32 * u;
-            if (i < e1) {
-                w[u] = ld_stream(val + i);  // streamed once per evaluation
+            if (j + lane + 32 * u < n) {
+                w[u] = ld_stream(row + j + 32 * u);
             } else {
                 w[u].x = w[u].y = w[u].z = T(0);
                 w[u].w = pack_id(w[u].w, 0);
