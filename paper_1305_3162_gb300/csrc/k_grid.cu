@@ -320,8 +320,11 @@ template <typename T, int M, int TS> struct SpreadSmem {
     __host__ __device__ static size_t bytes(int nwarps, int chunk) { return head(nwarps) * sizeof(T) + (size_t)chunk * 5 * sizeof(T); }
 };
 
-template <typename T, int M, int TS>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 && M <= 4 ? 4 : 1)) k_spread_groups(DevPlan p, int fused_kind, const T *__restrict__ in) {
+// MINB: blocks per SM the register budget is set for.  Meshes with many
+// sources per cell group run best at 4 (64 registers, no spills); sparse
+// meshes, where the per-group overheads dominate, at 5 (48 registers).
+template <typename T, int M, int TS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_spread_groups(DevPlan p, int fused_kind, const T *__restrict__ in) {
     typedef typename VecT<T>::T4 T4;
     typedef TileGeomG<M, TS> G;
     typedef SpreadSmem<T, M, TS> SM;
@@ -549,15 +552,16 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
     constexpr int GW = 3 * W;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int GC = p.gather_chunk;
     T *tile = (T *)smem_raw;
-    T *wv = tile + ((G::SIZE + 3) & ~3);  // [GATHER_CHUNK][3W]
-    T *sf = wv + GATHER_CHUNK * GW;     // [3][GATHER_CHUNK] fractions
-    T *sphi = sf + 3 * GATHER_CHUNK;    // [GATHER_CHUNK] near-field parts
-    int *sidx = (int *)(sphi + GATHER_CHUNK);  // [2][GATHER_CHUNK] packed cell, output index
+    T *wv = tile + ((G::SIZE + 3) & ~3);  // [GC][3W]
+    T *sf = wv + GC * GW;               // [3][GC] fractions
+    T *sphi = sf + 3 * GC;              // [GC] near-field parts
+    int *sidx = (int *)(sphi + GC);     // [2][GC] packed cell, output index
 
     const TileItem it = p.gather_items[blockIdx.x];
     const int nt = it.end - it.begin;
-    if (nt > GATHER_CHUNK) {
+    if (nt > GC || GC > GATHER_CHUNK) {
         if (threadIdx.x == 0) set_error(p.err, DEV_ERR_BAD_ITEM);
         return;
     }
@@ -571,10 +575,10 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
         const int t = it.begin + threadIdx.x;
         const T4 g = ((const T4 *)p.tgt_grid)[t];
         sf[threadIdx.x] = g.x;
-        sf[GATHER_CHUNK + threadIdx.x] = g.y;
-        sf[2 * GATHER_CHUNK + threadIdx.x] = g.z;
+        sf[GC + threadIdx.x] = g.y;
+        sf[2 * GC + threadIdx.x] = g.z;
         sidx[threadIdx.x] = packed_cell(g.w);
-        sidx[GATHER_CHUNK + threadIdx.x] = p.tgt_perm[t];
+        sidx[GC + threadIdx.x] = p.tgt_perm[t];
     }
     __syncthreads();
 
@@ -595,7 +599,7 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
                     for (int k = 0; k <= WDEG; ++k) cf[k] = ((const T *)p.wcoef)[wi * (WDEG + 1) + k];
                 }
                 for (int t = warp; t < nt; t += nwarps) {
-                    const T f = sf[wax * GATHER_CHUNK + t];
+                    const T f = sf[wax * GC + t];
                     T v;
                     if (sizeof(T) == 4) {
                         v = cf[WDEG];
@@ -676,7 +680,7 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
             }
         }
         acc = warp_sum(acc);
-        if (lane == 0) phi[sidx[GATHER_CHUNK + t]] = acc + sphi[t];
+        if (lane == 0) phi[sidx[GC + t]] = acc + sphi[t];
     }
 }
 
@@ -702,14 +706,23 @@ static cudaError_t spread_mt(const DevPlan &p, int fused_kind, const void *in, c
         int nw = 8;
         while (nw > 1 && SpreadSmem<T, M, TS>::bytes(nw, p.spread_chunk) > 100 * 1024) nw >>= 1;
         const size_t sm = SpreadSmem<T, M, TS>::bytes(nw, p.spread_chunk);
-        if (sm > 48 * 1024) {
-            cudaError_t e =
-                cudaFuncSetAttribute(k_spread_groups<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
+        auto go = [&](auto kern) -> cudaError_t {
+            if (sm > 48 * 1024) {
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                if (e != cudaSuccess) return e;
+            }
+            if (p.n_spread > 0) {
+                const cudaError_t le = launch_k(kern, dim3(p.n_spread, p.ks), 32 * nw, sm, s, p, fused_kind, (const T *)in);
+                if (le != cudaSuccess) return le;
+            }
+            return cudaGetLastError();
+        };
+        if constexpr (sizeof(T) == 4 && M <= 4) {
+            if (p.spread_dense) return go(k_spread_groups<T, M, TS, 4>);
+            return go(k_spread_groups<T, M, TS, 5>);
+        } else {
+            return go(k_spread_groups<T, M, TS, 1>);
         }
-        if (p.n_spread > 0)
-            { const cudaError_t le = launch_k(k_spread_groups<T, M, TS>, dim3(p.n_spread, p.ks), 32 * nw, sm, s, p, fused_kind, (const T *)in); if (le != cudaSuccess) return le; }
-        return cudaGetLastError();
     }
     int nw = 8;
     while (nw > 1 && spread_smem<T, M, TS>(nw, p.wdeg, p.spread_chunk) > 100 * 1024) nw >>= 1;
@@ -724,8 +737,8 @@ static cudaError_t spread_mt(const DevPlan &p, int fused_kind, const void *in, c
 
 template <typename T, int M, int TS> static cudaError_t gather_mt(const DevPlan &p, void *phi, cudaStream_t s) {
     typedef TileGeom<M, TS> G;
-    const size_t sm = ((size_t)((G::SIZE + 3) & ~3) + GATHER_CHUNK * (3 * 2 * M + 4)) * sizeof(T) +
-                      2 * GATHER_CHUNK * sizeof(int);
+    const size_t GC = (size_t)p.gather_chunk;
+    const size_t sm = ((size_t)((G::SIZE + 3) & ~3) + GC * (3 * 2 * M + 4)) * sizeof(T) + 2 * GC * sizeof(int);
     if (sm > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_gather<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;

@@ -30,9 +30,10 @@ struct StatePtrs {
     const void *in[NEAR_STATES];
 };
 
-// Targets per gather item (the plan splits target tiles into items of at
-// most this many; the gather kernel stages one item per block).
-constexpr int GATHER_CHUNK = 32;
+// Targets per gather item, at most (the plan splits target tiles into items of
+// at most GATHER_CHUNK, or of half that when the full size leaves fewer than
+// two items per SM; the gather kernel stages one item per block).
+constexpr int GATHER_CHUNK = 64;
 
 // Work item of the near-field kernel: up to 32 sorted targets
 // [tbegin, tbegin + tcount) and a slice [rbegin, rend) of the range list,
@@ -99,6 +100,9 @@ struct DevPlan {
 
     const TileItem *spread_items; int n_spread;
     int spread_chunk;             // most sources in one spread item
+    int spread_dense;             // 1: at least 8 sources per cell group on average (FP32 M <= 4
+                                  // spread at 4 blocks per SM with 64 registers, else 5 with 48)
+    int gather_chunk;             // most targets in one gather item (<= GATHER_CHUNK)
     const int *sgroups;           // cell groups: first source (within the item) | count << 16
     const int *sgroup_off;        // [n_spread][SPREAD_WARPS + 1] group list bounds of each item
     const TileItem *gather_items; int n_gather;

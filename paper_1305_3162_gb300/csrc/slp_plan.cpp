@@ -1036,6 +1036,8 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     TRY(upload(p, &ptr, p.gather_items.data(), p.gather_items.size()));
     d.gather_items = (const slp::TileItem *)ptr;
     d.n_gather = (int)p.gather_items.size();
+    d.gather_chunk = p.gather_chunk;
+    d.spread_dense = p.sgroups.size() > 0 && (double)p.Q >= 8.0 * (double)p.sgroups.size() ? 1 : 0;
     TRY(upload(p, &ptr, p.near_items.data(), p.near_items.size()));
     d.near_items = (const slp::NearItem *)ptr;
     d.n_near = (int)p.near_items.size();
@@ -1679,7 +1681,14 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
         ch = std::max<int64_t>(128, std::min<int64_t>(1024, (ch + 31) / 32 * 32));
         tile_items(p->src_grid, skeys, p->Q, p->TS, (int)ch, p->spread_items);
     }
-    tile_items(p->tgt_grid, tkeys, p->N, p->TSg, slp::GATHER_CHUNK, p->gather_items);
+    // gather items of GATHER_CHUNK targets, or of half that when the full
+    // size leaves fewer than two items per SM (small, latency-bound gathers)
+    p->gather_chunk = slp::GATHER_CHUNK;
+    tile_items(p->tgt_grid, tkeys, p->N, p->TSg, p->gather_chunk, p->gather_items);
+    if (p->gather_items.size() < 2 * 152) {
+        p->gather_chunk = slp::GATHER_CHUNK / 2;
+        tile_items(p->tgt_grid, tkeys, p->N, p->TSg, p->gather_chunk, p->gather_items);
+    }
     // largest items first: blocks are dispatched in index order, so this
     // schedules the long items early and the short ones fill the tail
     auto by_size = [](const slp::TileItem &a, const slp::TileItem &b) { return a.end - a.begin > b.end - b.begin; };

@@ -49,6 +49,7 @@ struct slp_plan_s {
     // parameters
     int L[3] = {0, 0, 0}, n[3] = {0, 0, 0}, m = 0, TS = 8, TE = 0;
     int TSg = 8;  // target (gather) tile size in cells
+    int gather_chunk = 64;  // most targets in one gather item
     int kf = 1;   // states of one far-field batch (scratch copies per scratch set)
     int kernel_mode = SLP_KERNEL_RADIAL, near_mode = SLP_NEAR_ON_THE_FLY;
     int grid_raised = 0;
