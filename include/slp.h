@@ -148,6 +148,11 @@ typedef struct {
     int active_planes;           /* z planes the FFT passes along y work on */
     int fused_plane_passes;      /* 1: the x and y passes run fused, one block per active plane */
     int fused_column_passes;     /* 1: FY, FZ * D * IZ and IY run as one cluster launch */
+    int gather_item_targets;     /* most targets in one gather work item (64, or 32 when items of 64
+                                    would give fewer than four per SM) */
+    int spread_blocks_per_sm;    /* FP32 spread with m <= 4: the register budget's blocks per SM, 4
+                                    where cell groups hold >= 8 sources on average, else 5; 0 for
+                                    the other spread kernels */
 } slp_info;
 
 /* Fill opts with defaults: precision 32, automatic grid/m/kernel/near mode,

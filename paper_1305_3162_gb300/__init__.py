@@ -111,7 +111,8 @@ class slp_info(ctypes.Structure):
                 ("n_gather_items", ctypes.c_int64), ("n_near_items", ctypes.c_int64),
                 ("launches_per_eval", ctypes.c_int), ("active_rows", ctypes.c_int64),
                 ("active_planes", ctypes.c_int), ("fused_plane_passes", ctypes.c_int),
-                ("fused_column_passes", ctypes.c_int)]
+                ("fused_column_passes", ctypes.c_int), ("gather_item_targets", ctypes.c_int),
+                ("spread_blocks_per_sm", ctypes.c_int)]
 
     def to_dict(self):
         out = {}

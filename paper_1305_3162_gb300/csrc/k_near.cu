@@ -258,53 +258,70 @@ __device__ __forceinline__ double4 ld_stream(const double4 *p) {
     return make_double4(a.x, a.y, b.x, b.y);
 }
 
+// One batch of a near-field row: lane l takes entries j + l + 32 u (u < U),
+// 16-byte loads all issued before the gathered m; FULL batches need no
+// predicates, the tail batch reads zero weights past the row's end.  The K
+// sorted magnetisations are m4[k N + column]; lane l adds its entries in
+// order, so a row's sums do not depend on K.
+template <typename T, int K, int U, bool FULL>
+__device__ __forceinline__ void near_batch(const typename VecT<T>::T4 *__restrict__ row, int j, int n, int lane,
+                                           const typename VecT<T>::T4 *__restrict__ m4, int64_t N, T (&acc)[K]) {
+    typedef typename VecT<T>::T4 T4;
+    T4 w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        if (FULL || j + lane + 32 * u < n) {
+            w[u] = ld_stream(row + j + 32 * u);  // streamed once per evaluation
+        } else {
+            w[u].x = w[u].y = w[u].z = T(0);
+            w[u].w = pack_id(w[u].w, 0);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int col = packed_cell(w[u].w);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const T4 mv = m4[k * N + col];
+            acc[k] += w[u].x * mv.x + w[u].y * mv.y + w[u].z * mv.z;
+        }
+    }
+}
+
+// Row t of the operator applied to K states: batches of 32 U entries (U
+// loads in flight per lane), the full ones without predicates and at 32-bit
+// offsets from the row start, then one predicated tail.
+template <typename T, int K>
+__device__ __forceinline__ void near_row(const DevPlan &p, int64_t t, int lane) {
+    typedef typename VecT<T>::T4 T4;
+    constexpr int U = 8;
+    const T4 *m4 = (const T4 *)p.m4;  // sorted nodal m (k_nodal_prep), K copies
+    const int64_t e0 = p.nm_rowptr[t];
+    const int n = (int)(p.nm_rowptr[t + 1] - e0);  // a row holds < 2^31 entries
+    const T4 *row = (const T4 *)p.nm_val + e0 + lane;
+    T acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = T(0);
+    int j = 0;
+    for (; j + 32 * U <= n; j += 32 * U) near_batch<T, K, U, true>(row, j, n, lane, m4, p.N, acc);
+    if (j < n) near_batch<T, K, U, false>(row, j, n, lane, m4, p.N, acc);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const T a = warp_sum(acc[k]);
+        if (lane == 0) ((T *)p.phi_part)[k * p.N + t] = a;
+    }
+}
+
+// phi_part[t] = row t of the precomputed operator times the sorted nodal m:
+// one warp per row
 template <typename T>
 __global__ void __launch_bounds__(128) k_near_matrix(DevPlan p) {
     pdl_wait();
     pdl_trigger();
-    typedef typename VecT<T>::T4 T4;
-    constexpr int U = 8;  // independent 16-byte loads in flight per lane
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * 4 + warp;
     if (t >= p.N) return;
-    const T4 *m4 = (const T4 *)p.m4;  // sorted nodal m (k_nodal_prep)
-    const int64_t e0 = p.nm_rowptr[t];
-    const int n = (int)(p.nm_rowptr[t + 1] - e0);  // a row holds < 2^31 entries
-    const T4 *row = (const T4 *)p.nm_val + e0 + lane;
-    T acc = T(0);
-    // batches of 32 U entries (U 16-byte loads in flight per lane): the full
-    // batches without predicates, 32-bit offsets from the row start, then
-    // one predicated tail; lane l adds its entries l, l + 32, ... in order
-    int j = 0;
-    for (; j + 32 * U <= n; j += 32 * U) {
-        T4 w[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) w[u] = ld_stream(row + j + 32 * u);  // streamed once per evaluation
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const T4 mv = m4[packed_cell(w[u].w)];
-            acc += w[u].x * mv.x + w[u].y * mv.y + w[u].z * mv.z;
-        }
-    }
-    if (j < n) {
-        T4 w[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (j + lane + 32 * u < n) {
-                w[u] = ld_stream(row + j + 32 * u);
-            } else {
-                w[u].x = w[u].y = w[u].z = T(0);
-                w[u].w = pack_id(w[u].w, 0);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const T4 mv = m4[packed_cell(w[u].w)];
-            acc += w[u].x * mv.x + w[u].y * mv.y + w[u].z * mv.z;
-        }
-    }
-    acc = warp_sum(acc);
-    if (lane == 0) ((T *)p.phi_part)[t] = acc;
+    near_row<T, 1>(p, t, lane);
 }
 
 // K states with one pass over the operator: each entry is streamed once and
@@ -314,44 +331,10 @@ template <typename T, int K>
 __global__ void __launch_bounds__(128) k_near_matrix_states(DevPlan p) {
     pdl_wait();
     pdl_trigger();
-    typedef typename VecT<T>::T4 T4;
-    constexpr int U = 8;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t t = (int64_t)blockIdx.x * 4 + warp;
     if (t >= p.N) return;
-    const T4 *val = (const T4 *)p.nm_val;
-    const T4 *m4 = (const T4 *)p.m4;
-    const int64_t e0 = p.nm_rowptr[t], e1 = p.nm_rowptr[t + 1];
-    T acc[K];
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc[k] = T(0);
-    for (int64_t e = e0 + lane; e < e1; e += 32 * U) {
-        T4 w[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t i = e + 32 * u;
-            if (i < e1) {
-                w[u] = ld_stream(val + i);
-            } else {
-                w[u].x = w[u].y = w[u].z = T(0);
-                w[u].w = pack_id(w[u].w, 0);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t col = packed_cell(w[u].w);
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const T4 mv = m4[k * p.N + col];
-                acc[k] += w[u].x * mv.x + w[u].y * mv.y + w[u].z * mv.z;
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const T a = warp_sum(acc[k]);
-        if (lane == 0) ((T *)p.phi_part)[k * p.N + t] = a;
-    }
+    near_row<T, K>(p, t, lane);
 }
 
 template <typename T> static cudaError_t near_states_t(const DevPlan &p, int K, cudaStream_t s) {

@@ -32,7 +32,7 @@ struct StatePtrs {
 
 // Targets per gather item, at most (the plan splits target tiles into items of
 // at most GATHER_CHUNK, or of half that when the full size leaves fewer than
-// two items per SM; the gather kernel stages one item per block).
+// four items per SM; the gather kernel stages one item per block).
 constexpr int GATHER_CHUNK = 64;
 
 // Work item of the near-field kernel: up to 32 sorted targets

@@ -196,6 +196,12 @@ const double NFAC = 2.0;
 
 namespace {
 
+// many sources per spread cell group (at least 8 on average): the FP32 spread
+// for m <= 4 then runs at 4 blocks per SM with 64 registers, else at 5 with 48
+bool spread_dense(const slp_plan_s &p) {
+    return p.sgroups.size() > 0 && (double)p.Q >= 8.0 * (double)p.sgroups.size();
+}
+
 // ---------------------------------------------------------------- mesh
 slp_status validate_mesh(slp_plan_s &p) {
     const int64_t N = p.N, M = p.M;
@@ -1037,7 +1043,7 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     d.gather_items = (const slp::TileItem *)ptr;
     d.n_gather = (int)p.gather_items.size();
     d.gather_chunk = p.gather_chunk;
-    d.spread_dense = p.sgroups.size() > 0 && (double)p.Q >= 8.0 * (double)p.sgroups.size() ? 1 : 0;
+    d.spread_dense = spread_dense(p) ? 1 : 0;
     TRY(upload(p, &ptr, p.near_items.data(), p.near_items.size()));
     d.near_items = (const slp::NearItem *)ptr;
     d.n_near = (int)p.near_items.size();
@@ -1682,10 +1688,10 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
         tile_items(p->src_grid, skeys, p->Q, p->TS, (int)ch, p->spread_items);
     }
     // gather items of GATHER_CHUNK targets, or of half that when the full
-    // size leaves fewer than two items per SM (small, latency-bound gathers)
+    // size leaves fewer than four items per SM (small, latency-bound gathers)
     p->gather_chunk = slp::GATHER_CHUNK;
     tile_items(p->tgt_grid, tkeys, p->N, p->TSg, p->gather_chunk, p->gather_items);
-    if (p->gather_items.size() < 2 * 152) {
+    if (p->gather_items.size() < 4 * 152) {
         p->gather_chunk = slp::GATHER_CHUNK / 2;
         tile_items(p->tgt_grid, tkeys, p->N, p->TSg, p->gather_chunk, p->gather_items);
     }
@@ -1798,6 +1804,8 @@ slp_status slp_query(slp_plan_t p, slp_info *info) {
     info->active_planes = p->nz_act;
     info->fused_plane_passes = p->device >= 0 && p->dp.fuse_pb > 0 ? 1 : 0;
     info->fused_column_passes = p->device >= 0 && p->dp.yzy_g > 0 ? 1 : 0;
+    info->gather_item_targets = p->gather_chunk;
+    info->spread_blocks_per_sm = (p->prec == 32 && p->m <= 4) ? (spread_dense(*p) ? 4 : 5) : 0;
     return SLP_OK;
 }
 

@@ -354,3 +354,38 @@ def test_struct_layouts_match_the_header(slp, name, tmp_path):
     assert got[0] == ctypes.sizeof(cls), (name, got[0], ctypes.sizeof(cls))
     for f, off in zip(fields, got[1:]):
         assert off == getattr(cls, f).offset, (name, f, off, getattr(cls, f).offset)
+
+
+@pytest.mark.parametrize("case", ["sphere5-fp32", "cube100-fp32", "cube8-fp64"])
+def test_plan_chooses_spread_occupancy_and_gather_items(slp, case):
+    """The plan reads two launch choices off its own work lists: FP32 spread
+    blocks per SM (4 with >= 8 sources per cell group, else 5; 0 outside the
+    FP32 m <= 4 kernel) and the gather item size (64 targets, or 32 when
+    that leaves fewer than four items per SM); every item respects it."""
+    if case == "sphere5-fp32":
+        w = workloads.sphere()
+        V, T, q, tol, prec, grid = w.V, w.T, w.quad, w.tolerance, 32, w.grid
+        want = (32, 4)
+    elif case == "cube100-fp32":
+        V, T = meshes.cube(100)
+        q, tol, prec, grid = 3, 1e-5, 32, (512, 512, 512)
+        want = (64, 5)
+    else:
+        w = workloads.cube()
+        V, T, q, tol, prec, grid = w.V, w.T, w.quad, w.tolerance, 64, w.grid
+        want = (32, 0)
+    plan = _host_plan(slp, V, T, q, tol, prec, grid)
+    try:
+        info = slp.slp_query(plan)
+        assert (info["gather_item_targets"], info["spread_blocks_per_sm"]) == want
+        items = slp.slp_debug_host_array(plan, slp.SLP_HOST_GATHER_ITEMS).reshape(-1, 8)
+        assert len(items) == info["n_gather_items"]
+        sizes = items[:, 4] - items[:, 3]  # TileItem: c0x, c0y, c0z, begin, end, pad
+        assert sizes.min() >= 1 and sizes.max() <= info["gather_item_targets"]
+        assert int(sizes.sum()) == info["n_targets"]
+        groups = slp.slp_debug_host_array(plan, slp.SLP_HOST_SPREAD_GROUPS)
+        dense = info["n_sources"] >= 8 * len(groups)
+        if want[1]:
+            assert dense == (want[1] == 4)
+    finally:
+        slp.slp_destroy(plan)
