@@ -444,6 +444,9 @@ __global__ void __launch_bounds__(256, MINB) k_spread_groups(DevPlan p, int fuse
             for (int h = 0; h < H; ++h)
 #pragma unroll
                 for (int j = 0; j < W2; ++j) acc[h][j].x = acc[h][j].y = T(0);
+            // two sources per iteration where the 64-register budget holds
+            // them without spills (the 4-block build)
+#pragma unroll(MINB == 4 ? 2 : 1)
             for (int g = 0; g < ng; ++g) {
                 const T a = wv[g * WP + ix];
                 const T *wz = wv + 2 * AX + g * WP;
