@@ -365,7 +365,11 @@ def run_ours(args):
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "eps_near": info["eps_near"], "pairs_within_eps": pairs_within,
                        "near_pairs_visited": info["near_pairs"], "near_mode": ["auto", "on_the_fly", "precomputed"][info["near_mode"]],
-                       "near_matrix_nnz": info["near_matrix_nnz"]},
+                       "near_matrix_nnz": info["near_matrix_nnz"],
+                       "gather_item_targets": info.get("gather_item_targets"),
+                       "spread_blocks_per_sm": info.get("spread_blocks_per_sm"),
+                       "fft_passes": ("fused plane" if info.get("fused_plane_passes") else
+                                      "fused column" if info.get("fused_column_passes") else "separate")},
             "rel_l2": rel_l2, "parity_ok": parity_ok,
             "roofline": roofline, "per_kernel": per_kernel,
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
