@@ -437,10 +437,12 @@ slp_status choose_parameters(slp_plan_s &p) {
     for (int d = 0; d < 3; ++d)
         if (!(p.P[d] > p.D[d])) return fail(SLP_ERR_INVALID_ARG, "period does not contain the mesh");
 
-    // tile size: 4^3 cells, halved while a halo tile (padded layout of the
+    // tile size: 8^3 cells, halved while a halo tile (padded layout of the
     // spread/gather kernels) exceeds 40 KB, so several warps get a private copy
+    // (FP32 m <= 5 keeps 8: on sparse meshes the larger tiles flush less halo
+    // per source; FP64 and wider windows end at 4 or 2)
     const size_t esz = p.prec == 64 ? 8 : 4;
-    p.TS = 4;
+    p.TS = 8;
     while (p.TS > 2 && std::pow((double)(p.TS + 2 * p.m + 3), 3) * esz > 40 * 1024) p.TS /= 2;
     // targets: larger tiles (fewer gather items, each tile load shared by more targets)
     p.TSg = 8;
