@@ -1239,7 +1239,7 @@ __global__ void __launch_bounds__(512) k_yzy(DevPlan p, int ZC, int ZP) {
 // grids, where the passes are latency-bound), two buffers of (L x (B+1))
 // complex within ~64 KB.
 static int row_batch(int L, size_t celem) {
-    int pb = 8;
+    int pb = L <= 128 ? 4 : 8;  // short rows: more, smaller blocks (measured on the 128^3 sphere)
     while (pb > 1 && (2 * (size_t)L * (pb + 1) + L) * celem > 64 * 1024) pb >>= 1;
     return pb;
 }
