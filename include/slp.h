@@ -105,9 +105,10 @@ typedef struct {
                              slp_eval returns SLP_ERR_NO_DEVICE) */
     int allow_grid_raise; /* 1: raise a grid that cannot meet the tolerance (else error) */
     int check_mesh;       /* 1: require a closed, consistently and outward oriented surface */
-    int fuse_plane_passes; /* x and y FFT passes fused per z plane (one block per plane, the plane
-                              spectrum in shared memory): 0 off, 1 on where the plane fits,
-                              -1 automatic (on when there are at least two active planes per SM) */
+    int fuse_plane_passes; /* x and y FFT passes fused per z plane (a cluster of four CTAs per
+                              plane, the plane spectrum in distributed shared memory): 0 off, 1 on
+                              where the plane fits, -1 automatic (on when there are at least two
+                              active planes per SM) */
     int fuse_column_passes; /* the y pass, the z pass with the kernel multiply and the inverse y pass
                                fused, one cluster of four CTAs per stored x frequency holding that
                                slab of the spectrum in distributed shared memory (needs equal y and
@@ -146,7 +147,8 @@ typedef struct {
     int64_t active_rows;         /* grid rows (z, y) the FFT passes transform along x: those within
                                     the window of some source or target, widened to row pairs */
     int active_planes;           /* z planes the FFT passes along y work on */
-    int fused_plane_passes;      /* 1: the x and y passes run fused, one block per active plane */
+    int fused_plane_passes;      /* 1: the x and y passes run fused, one four-CTA cluster per active
+                                    plane */
     int fused_column_passes;     /* 1: FY, FZ * D * IZ and IY run as one cluster launch */
     int gather_item_targets;     /* most targets in one gather work item (64, or 32 when items of 64
                                     would give fewer than four per SM) */
