@@ -115,7 +115,11 @@ typedef struct {
                                z grids of 32..256 and unfused plane passes): 0 off, 1 on where it
                                applies, -1 automatic (off: the separate passes, chained by
                                programmatic dependent launch, measured faster) */
-    int reserved[5];
+    int check_finite;     /* 1: every evaluation checks its input and its result for NaN/Inf on the
+                             device, in kernels that read them anyway; a non-finite value sets the
+                             plan's status word, which slp_check then reports as SLP_ERR_NONFINITE
+                             (the evaluation still completes; nothing traps) */
+    int reserved[4];
 } slp_plan_opts;
 
 typedef struct {
@@ -198,10 +202,11 @@ slp_status slp_eval_states(slp_plan_t plan, int input_kind, int n_states, const 
  * Page-locked host memory gives asynchronous copies. */
 slp_status slp_eval_host(slp_plan_t plan, int input_kind, const void *h_in, void *h_phi, void *stream);
 
-/* Allocation-free evaluation for callers that cannot call cudaMalloc (code
- * running while a stream is captured into a CUDA graph, hosts inside another
- * framework's memory pool, loops that must not touch the allocator after
- * start-up).  The paper has no counterpart: this evaluates the same
+/* Allocation-free evaluation for callers that cannot call cudaMalloc where
+ * they need phi: host code running inside another framework's memory pool,
+ * which forbids raw device allocations, and solver loops that must not touch
+ * the allocator after start-up.  Such callers cannot build a plan (slp_plan
+ * allocates).  The paper has no counterpart: this evaluates the same
  * quantity as slp_eval, phi at the mesh vertices, by direct summation over
  * all (vertex, quadrature point) pairs, without a plan.
  * d_vertices:  device, [n_vertices][3] double;  d_triangles: device, [n_triangles][3]
@@ -218,7 +223,11 @@ slp_status slp_eval_host(slp_plan_t plan, int input_kind, const void *h_in, void
  * overlap on the GPU (other streams, other host threads) race: order them.
  * The first call on a device resolves the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Costs O(N Q): meant for small meshes. */
+ * before any stream capture.  Sums are compensated (Neumaier), so the FP32
+ * result stays within about 1e-6 relative of the exact quadrature sum up to
+ * the source limit.  A CUDA error pending from the caller's earlier work is
+ * reported (SLP_ERR_CUDA) and left in place, and nothing is launched.
+ * Costs O(N Q): meant for small meshes. */
 slp_status slp_eval_direct_static(const double *d_vertices, int64_t n_vertices, const int32_t *d_triangles,
                                   int64_t n_triangles, int quadrature, int precision, int input_kind,
                                   const void *d_in, void *d_phi, void *stream);
@@ -244,6 +253,24 @@ slp_status slp_batch_run(slp_batch_t batch, void *stream);
 slp_status slp_batch_query(slp_batch_t batch, int64_t *n_items, int64_t *n_lanes, int64_t *kernel_launches,
                            int64_t *extra_scratch_bytes);
 slp_status slp_batch_destroy(slp_batch_t batch);
+
+/* One-call batched evaluation (the batched form as a single entry point):
+ * plans[i] evaluates n_states_each[i] states, held back to back in d_in[i]
+ * (device, each state in the slp_eval layout of input_kind), into d_phi[i]
+ * (device, [n_states_each[i]][n_targets of plans[i]]).  A plan may appear in
+ * several entries.  Every state of every entry runs in one CUDA graph
+ * launched on `stream` (the states of one plan share the near-field passes
+ * and the state-batched far field, as in slp_eval_states; different plans
+ * overlap on the device).  The first call with a given argument set (plans,
+ * buffers, counts, input kind) captures that graph; later calls with the
+ * same set replay it, so buffers that are refilled in place between calls
+ * cost no capture.  The library keeps up to 8 such graphs (least recently
+ * used dropped first); slp_destroy releases those that use the plan.  The
+ * plans must not be evaluated on other streams while a call runs (the graph
+ * uses each plan's own scratch).  Stream-ordered.
+ * Errors: INVALID_ARG, NO_DEVICE, OOM, CUDA. */
+slp_status slp_eval_batched(int n, const slp_plan_t *plans, int input_kind, const void *const *d_in,
+                            void *const *d_phi, const int *n_states_each, void *stream);
 
 /* ---- Grid autotuner ----
  * Considers equal-spacing grids whose largest axis spans 32, 64, ..., 512
@@ -321,7 +348,9 @@ slp_status slp_query(slp_plan_t plan, slp_info *info);
 slp_status slp_query_points(slp_plan_t plan, double *points);
 
 /* Synchronise the plan's device and report (and clear) the sticky device
- * status word written by the kernels. */
+ * status word written by the kernels: SLP_ERR_NONFINITE when a checked
+ * evaluation (opts.check_finite) saw NaN/Inf in its input or result,
+ * SLP_ERR_CUDA for an inconsistent work item. */
 slp_status slp_check(slp_plan_t plan);
 
 /* Release the plan and all its device memory.  NULL is accepted. */

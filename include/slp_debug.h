@@ -83,10 +83,13 @@ slp_status slp_debug_host_array(slp_plan_t plan, int which, void *out, int64_t c
 slp_status slp_debug_timeline(slp_plan_t plan, int input_kind, const void *d_in, void *d_phi, void *stream,
                               float *ms);
 
-/* Run one full evaluation and time each kernel with CUDA events recorded on
- * `stream` between the launches; ms[i] receives kernel i's duration
- * (n >= 10 entries; the kernels in launch order are named by
- * slp_debug_stage_name).  Synchronises the stream. */
+/* Run one full evaluation in launch order on `stream` and time each kernel
+ * with a pair of CUDA events recorded around its launch; ms[i] receives the
+ * duration of kernel slot i, or -1 when that slot's kernel did not launch
+ * for this plan and input (n >= 15 entries; slots are named by
+ * slp_debug_stage_name: charges, spread, fft_x, fft_y, fft_z_mul, ifft_y,
+ * ifft_x, nodal_prep, near_zero, near, near_reduce, gather, fft_xy, ifft_yx,
+ * fft_yzy).  Synchronises the stream. */
 slp_status slp_debug_profile(slp_plan_t plan, int input_kind, const void *d_in, void *d_phi, void *stream,
                              float *ms, int n);
 const char *slp_debug_stage_name(int i);

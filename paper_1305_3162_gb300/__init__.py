@@ -62,7 +62,7 @@ class slp_plan_opts(ctypes.Structure):
                 ("kernel_mode", ctypes.c_int), ("near_mode", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("device", ctypes.c_int), ("allow_grid_raise", ctypes.c_int), ("check_mesh", ctypes.c_int),
                 ("fuse_plane_passes", ctypes.c_int), ("fuse_column_passes", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("check_finite", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 SLP_TUNE_MAX = 8
@@ -134,7 +134,7 @@ EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_states", "slp_
             "slp_debug_host_array", "slp_debug_window", "slp_debug_window_hat", "slp_debug_profile",
             "slp_debug_timeline",
             "slp_debug_stage_name", "slp_eval_direct_static", "slp_batch_create", "slp_batch_run",
-            "slp_batch_query", "slp_batch_destroy", "slp_plan_autotune", "slp_server_default_opts",
+            "slp_batch_query", "slp_batch_destroy", "slp_eval_batched", "slp_plan_autotune", "slp_server_default_opts",
             "slp_server_create", "slp_server_submit", "slp_server_status", "slp_server_wait", "slp_server_cancel",
             "slp_server_stats", "slp_server_destroy"]
 
@@ -184,6 +184,8 @@ def load():
         "slp_batch_run": ([vp, vp], St),
         "slp_batch_query": ([vp, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)], St),
         "slp_batch_destroy": ([vp], St),
+        "slp_eval_batched": ([ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                              ctypes.POINTER(ctypes.c_int), vp], St),
         "slp_plan_autotune": ([ctypes.POINTER(slp_mesh), ctypes.c_int, ctypes.c_double, ctypes.POINTER(slp_plan_opts),
                                ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(slp_tune_info)], St),
         "slp_server_default_opts": ([ctypes.POINTER(slp_server_opts)], St),
@@ -266,9 +268,41 @@ def slp_eval_host(plan, input_kind: int, h_in, h_phi, stream=None):
     _check(load().slp_eval_host(plan, int(input_kind), _ptr(h_in), _ptr(h_phi), _stream(stream)), "slp_eval_host")
 
 
+def _check_device_tensor(x, name, dtype_name, min_numel, where):
+    """Raise SlpError unless torch tensor x is a contiguous CUDA tensor on the
+    current device of the given dtype with at least min_numel elements (raw
+    integer addresses are passed through unchecked)."""
+    if isinstance(x, int) or not hasattr(x, "data_ptr"):
+        if isinstance(x, np.ndarray):
+            raise SlpError(SLP_ERR_INVALID_ARG, where, f"{name} is a host array; a device tensor is required")
+        return
+    import torch
+    if not x.is_cuda:
+        raise SlpError(SLP_ERR_INVALID_ARG, where, f"{name} is not a CUDA tensor")
+    if x.device.index != torch.cuda.current_device():
+        raise SlpError(SLP_ERR_INVALID_ARG, where, f"{name} is on {x.device}, not the current device")
+    if str(x.dtype) != "torch." + dtype_name:
+        raise SlpError(SLP_ERR_INVALID_ARG, where, f"{name} has dtype {x.dtype}, expected torch.{dtype_name}")
+    if not x.is_contiguous():
+        raise SlpError(SLP_ERR_INVALID_ARG, where, f"{name} is not contiguous")
+    if x.numel() < min_numel:
+        raise SlpError(SLP_ERR_INVALID_ARG, where, f"{name} holds {x.numel()} elements, needs {min_numel}")
+
+
 def slp_eval_direct_static(d_vertices, n_vertices, d_triangles, n_triangles, quadrature, precision, input_kind,
                            d_in, d_phi, stream=None):
-    """Allocation-free direct evaluation (see include/slp.h): device mesh, input and output."""
+    """Allocation-free direct evaluation (see include/slp.h): device mesh, input and output.
+
+    Torch tensors are checked (CUDA, current device, dtype, contiguity,
+    size) before their addresses reach the library."""
+    where = "slp_eval_direct_static"
+    nv, nt, q = int(n_vertices), int(n_triangles), int(quadrature)
+    fdt = "float64" if int(precision) == 64 else "float32"
+    need_in = {SLP_INPUT_SIGMA: q * nt, SLP_INPUT_MAG: 3 * q * nt, SLP_INPUT_NODAL_MAG: 3 * nv}.get(int(input_kind), 0)
+    _check_device_tensor(d_vertices, "d_vertices", "float64", 3 * nv, where)
+    _check_device_tensor(d_triangles, "d_triangles", "int32", 3 * nt, where)
+    _check_device_tensor(d_in, "d_in", fdt, need_in, where)
+    _check_device_tensor(d_phi, "d_phi", fdt, nv, where)
     _check(load().slp_eval_direct_static(_ptr(d_vertices), int(n_vertices), _ptr(d_triangles), int(n_triangles),
                                          int(quadrature), int(precision), int(input_kind), _ptr(d_in), _ptr(d_phi),
                                          _stream(stream)), "slp_eval_direct_static")
@@ -302,6 +336,17 @@ def slp_batch_query(batch) -> dict:
 def slp_batch_destroy(batch):
     if batch is not None:
         _check(load().slp_batch_destroy(batch), "slp_batch_destroy")
+
+
+def slp_eval_batched(plans, input_kind, d_in, d_phi, n_states_each, stream=None):
+    """Evaluate n_states_each[i] states of plans[i] (inputs back to back in
+    d_in[i], outputs [n][N_i] in d_phi[i]) in one cached CUDA graph."""
+    n = len(plans)
+    P = (ctypes.c_void_p * n)(*[p.value if isinstance(p, ctypes.c_void_p) else p for p in plans])
+    ins = (ctypes.c_void_p * n)(*[_ptr(x).value for x in d_in])
+    outs = (ctypes.c_void_p * n)(*[_ptr(x).value for x in d_phi])
+    cnt = (ctypes.c_int * n)(*[int(c) for c in n_states_each])
+    _check(load().slp_eval_batched(n, P, int(input_kind), ins, outs, cnt, _stream(stream)), "slp_eval_batched")
 
 
 def slp_plan_autotune(vertices, triangles, quadrature, tolerance, opts=None, reps=5):
@@ -438,12 +483,13 @@ def slp_debug_timeline(plan, input_kind, d_in, d_phi, stream=None):
 
 
 def slp_debug_profile(plan, input_kind, d_in, d_phi, stream=None) -> dict:
-    """Per-kernel durations (ms) of one evaluation, CUDA events on the launch stream."""
-    n = 10
+    """Per-kernel durations (ms) of one serial evaluation, CUDA events around
+    each launch on the launch stream; only the kernels that launched appear."""
+    n = 15
     ms = (ctypes.c_float * n)()
     _check(load().slp_debug_profile(plan, int(input_kind), _ptr(d_in), _ptr(d_phi), _stream(stream), ms, n),
            "slp_debug_profile")
-    return {load().slp_debug_stage_name(i).decode(): float(ms[i]) for i in range(n)}
+    return {load().slp_debug_stage_name(i).decode(): float(ms[i]) for i in range(n) if ms[i] >= 0.0}
 
 
 def slp_debug_window(m: int, d: float) -> float:

@@ -128,11 +128,13 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, unsigned block, s
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-// error codes written to the plan's status word
-enum { DEV_ERR_NONE = 0, DEV_ERR_BAD_ITEM = 1, DEV_ERR_BAD_INDEX = 2 };
-
 __device__ __forceinline__ void set_error(int *err, int code) {
     if (err) atomicCAS(err, 0, code);
+}
+
+// checked evaluation: record a NaN or Inf among the given values
+template <typename T> __device__ __forceinline__ void check_finite3(const DevPlan &p, T a, T b, T c) {
+    if (p.check_finite && !(isfinite(a) && isfinite(b) && isfinite(c))) set_error(p.err, DEV_ERR_NONFINITE);
 }
 
 }  // namespace slp

@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(256) k_nodal_prep(DevPlan p, const T *__restri
     o.y = in[3 * v + 1];
     o.z = in[3 * v + 2];
     o.w = T(0);
+    check_finite3(p, o.x, o.y, o.z);
     ((T4 *)p.m4)[u] = o;
 }
 
@@ -82,7 +83,9 @@ __global__ void __launch_bounds__(256) k_charges(DevPlan p, int kind, const T *_
     pdl_trigger();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= p.Q) return;
-    ((T *)p.qbuf)[k] = source_charge<T>(p, k, kind, in);
+    const T q = source_charge<T>(p, k, kind, in);
+    check_finite3(p, q, q, q);  // a NaN or Inf among the inputs this charge reads
+    ((T *)p.qbuf)[k] = q;
 }
 
 // ---------------------------------------------------------------- tile geometry
@@ -683,7 +686,11 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
             }
         }
         acc = warp_sum(acc);
-        if (lane == 0) phi[sidx[GC + t]] = acc + sphi[t];
+        if (lane == 0) {
+            const T v = acc + sphi[t];
+            check_finite3(p, v, v, v);
+            phi[sidx[GC + t]] = v;
+        }
     }
 }
 
@@ -815,6 +822,7 @@ __global__ void __launch_bounds__(256) k_nodal_prep_states(DevPlan p, StatePtrs 
     o.y = in[3 * v + 1];
     o.z = in[3 * v + 2];
     o.w = T(0);
+    check_finite3(p, o.x, o.y, o.z);
     ((T4 *)p.m4)[(int64_t)blockIdx.y * p.N + u] = o;
 }
 

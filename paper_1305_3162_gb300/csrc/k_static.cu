@@ -1,17 +1,18 @@
 // Allocation-free evaluation: slp_eval_direct_static.
 //
 // Some callers cannot call cudaMalloc at the point where they need the
-// potential: code that runs while a CUDA stream is being captured into a
-// graph, host code living inside another framework's memory pool that
+// potential: host code living inside another framework's memory pool that
 // forbids raw device allocations, or a solver loop that must not touch the
-// allocator after start-up.  They cannot build a plan (slp_plan allocates
-// the plan's device memory).  For small meshes this entry point evaluates
-// the same single layer potential by direct summation over all
-// (target, source) pairs and allocates nothing: the caller passes the mesh,
-// the input field and the output on the device, and the only scratch (the
-// quadrature points and weighted charges, one 4-vector per source) lives in
-// the file-scope array below, which every GPU that loads the library holds
-// until the process exits.
+// allocator after start-up (an allocation there can block on, or fail
+// against, memory that the surrounding application has already handed
+// out).  They cannot build a plan, because slp_plan allocates the plan's
+// device memory.  For small meshes this entry point evaluates the same
+// single layer potential by direct summation over all (target, source)
+// pairs and allocates nothing: the caller passes the mesh, the input field
+// and the output on the device, and the only scratch (the quadrature points
+// and weighted charges, one 4-vector per source) lives in the file-scope
+// array below, which every GPU that loads the library holds until the
+// process exits.
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -35,6 +36,12 @@ void *g_scratch_addr[MAX_DEVICES] = {nullptr};
 slp_status static_fail(slp_status s, const char *msg) {
     slp::set_last_error(msg);
     return s;
+}
+
+slp_status launch_fail(const char *what, cudaError_t e) {
+    char msg[256];
+    snprintf(msg, sizeof msg, "slp_eval_direct_static: launch of %s failed: %s", what, cudaGetErrorString(e));
+    return static_fail(SLP_ERR_CUDA, msg);
 }
 
 template <typename T> struct V4s;
@@ -97,7 +104,8 @@ __global__ void k_static_sources(const double *__restrict__ V, int64_t nv, const
 
 // phi_i = (1/4pi) sum_k q_k / |x_i - y_k| over all sources.  One block per 32
 // targets (lane = target); the 8 warps split the sources and their partial
-// sums are added in warp order, so the result is bitwise repeatable.
+// sums (each with its compensation term) are added in warp order, so the
+// result is bitwise repeatable.
 template <typename T>
 __global__ void __launch_bounds__(256) k_static_direct(const double *__restrict__ V, int64_t nv,
                                                        const typename V4s<T>::t *__restrict__ src, int64_t Q,
@@ -105,6 +113,7 @@ __global__ void __launch_bounds__(256) k_static_direct(const double *__restrict_
     typedef typename V4s<T>::t T4;
     __shared__ T4 stage[8][32];
     __shared__ T part[8][32];
+    __shared__ T cpart[8][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * 32 + lane;
     T tx = T(0), ty = T(0), tz = T(0);
@@ -115,7 +124,10 @@ __global__ void __launch_bounds__(256) k_static_direct(const double *__restrict_
     }
     const int64_t per = (Q + 7) / 8;
     const int64_t b = warp * per, e = min(Q, b + per);
-    T acc = T(0);
+    // Neumaier-compensated sum: a warp adds up to Q / 8 terms (262,144 at the
+    // FP32 scratch limit), so a plain FP32 running sum could lose digits; the
+    // compensation term keeps the error near one rounding of the total
+    T acc = T(0), comp = T(0);
     for (int64_t s0 = b; s0 < e; s0 += 32) {
         if (s0 + lane < e) stage[warp][lane] = src[s0 + lane];
         __syncwarp();
@@ -124,16 +136,27 @@ __global__ void __launch_bounds__(256) k_static_direct(const double *__restrict_
             const T4 y = stage[warp][jj];
             const T dx = tx - y.x, dy = ty - y.y, dz = tz - y.z;
             const T r2 = dx * dx + dy * dy + dz * dz;
-            if (r2 > T(0)) acc += y.w / sqrt(r2);
+            if (r2 > T(0)) {
+                const T term = y.w / sqrt(r2);
+                const T t = acc + term;
+                comp += fabs(acc) >= fabs(term) ? (acc - t) + term : (term - t) + acc;
+                acc = t;
+            }
         }
         __syncwarp();
     }
     part[warp][lane] = acc;
+    cpart[warp][lane] = comp;
     __syncthreads();
     if (warp == 0 && i < nv) {
-        T s = T(0);
-        for (int w = 0; w < 8; ++w) s += part[w][lane];
-        phi[i] = s * T(0.079577471545947667884);  // 1 / (4 pi)
+        T s = T(0), c = T(0);
+        for (int w = 0; w < 8; ++w) {
+            const T v = part[w][lane];
+            const T t = s + v;
+            c += (fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s) + cpart[w][lane];
+            s = t;
+        }
+        phi[i] = (s + c) * T(0.079577471545947667884);  // 1 / (4 pi)
     }
 }
 
@@ -179,9 +202,11 @@ slp_status launch_static(const double *V, int64_t nv, const int32_t *Tri, int64_
     const int64_t Q = nt * rp.q;
     k_static_sources<T><<<(unsigned)((Q + 255) / 256), 256, 0, s>>>(V, nv, Tri, nt, rp, kind, (const T *)in,
                                                                      (T4 *)scratch);
-    if (cudaGetLastError() != cudaSuccess) return static_fail(SLP_ERR_CUDA, "launch of the charge kernel failed");
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return launch_fail("the charge kernel", e);
     k_static_direct<T><<<(unsigned)((nv + 31) / 32), 256, 0, s>>>(V, nv, (const T4 *)scratch, Q, (T *)phi);
-    if (cudaGetLastError() != cudaSuccess) return static_fail(SLP_ERR_CUDA, "launch of the direct-sum kernel failed");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return launch_fail("the direct-sum kernel", e);
     return SLP_OK;
 }
 
@@ -211,6 +236,19 @@ extern "C" slp_status slp_eval_direct_static(const double *d_vertices, int64_t n
                  (long long)(n_triangles * quadrature), (long long)(n_triangles * quadrature * (int64_t)per),
                  STATIC_SCRATCH_BYTES, STATIC_SCRATCH_BYTES / per, precision);
         return static_fail(SLP_ERR_INVALID_ARG, msg);
+    }
+    {
+        // an error left by the caller's earlier work is reported as such, and
+        // left in place for the caller (the launch checks below would
+        // otherwise take it for their own and clear it)
+        const cudaError_t pending = cudaPeekAtLastError();
+        if (pending != cudaSuccess) {
+            char msg[256];
+            snprintf(msg, sizeof msg,
+                     "slp_eval_direct_static: a CUDA error from earlier work is pending (%s); nothing was launched",
+                     cudaGetErrorString(pending));
+            return static_fail(SLP_ERR_CUDA, msg);
+        }
     }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {

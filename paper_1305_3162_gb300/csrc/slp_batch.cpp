@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "slp_plan_internal.h"
@@ -195,6 +196,116 @@ slp_status slp_batch_query(slp_batch_t b, int64_t *n_items, int64_t *n_lanes, in
 slp_status slp_batch_destroy(slp_batch_t b) {
     release(b);
     return SLP_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ one-call batched evaluation
+// slp_eval_batched keeps the graphs it captures in a small cache keyed by the
+// full argument set (plans, buffers, state counts, input kind): the first call
+// with a given set captures the batch, later calls with the same set replay
+// it.  slp_destroy drops every cached graph that uses the destroyed plan.
+namespace {
+
+struct BatchKey {
+    std::vector<const void *> plans, ins;
+    std::vector<void *> outs;
+    std::vector<int> counts;
+    int kind = 0;
+    bool operator==(const BatchKey &o) const {
+        return kind == o.kind && plans == o.plans && ins == o.ins && outs == o.outs && counts == o.counts;
+    }
+};
+struct CachedBatch {
+    BatchKey key;
+    slp_batch_t batch = nullptr;
+    uint64_t last_use = 0;
+};
+constexpr size_t BATCH_CACHE_MAX = 8;
+std::mutex g_cache_mu;
+std::vector<CachedBatch> g_cache;
+uint64_t g_cache_tick = 0;
+
+}  // namespace
+
+void slp_batch_cache_drop(const slp_plan_s *plan) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (size_t i = 0; i < g_cache.size();) {
+        const auto &ps = g_cache[i].key.plans;
+        if (std::find(ps.begin(), ps.end(), (const void *)plan) != ps.end()) {
+            release(g_cache[i].batch);
+            g_cache.erase(g_cache.begin() + i);
+        } else {
+            ++i;
+        }
+    }
+}
+
+extern "C" {
+
+slp_status slp_eval_batched(int n, const slp_plan_t *plans, int input_kind, const void *const *d_in,
+                            void *const *d_phi, const int *n_states_each, void *stream) {
+    if (n < 1 || !plans || !d_in || !d_phi || !n_states_each)
+        return slp_fail(SLP_ERR_INVALID_ARG, "slp_eval_batched: empty batch or NULL array");
+    if (input_kind < SLP_INPUT_SIGMA || input_kind > SLP_INPUT_NODAL_MAG)
+        return slp_fail(SLP_ERR_INVALID_ARG, "slp_eval_batched: unknown input kind %d", input_kind);
+    BatchKey key;
+    key.kind = input_kind;
+    int64_t n_items = 0;
+    for (int i = 0; i < n; ++i) {
+        if (!plans[i]) return slp_fail(SLP_ERR_INVALID_ARG, "slp_eval_batched: plan %d is NULL", i);
+        if (n_states_each[i] < 0) return slp_fail(SLP_ERR_INVALID_ARG, "slp_eval_batched: entry %d has a negative state count", i);
+        if (n_states_each[i] > 0 && (!d_in[i] || !d_phi[i]))
+            return slp_fail(SLP_ERR_INVALID_ARG, "slp_eval_batched: entry %d has a NULL buffer", i);
+        key.plans.push_back(plans[i]);
+        key.ins.push_back(d_in[i]);
+        key.outs.push_back(d_phi[i]);
+        key.counts.push_back(n_states_each[i]);
+        n_items += n_states_each[i];
+    }
+    if (n_items == 0) return SLP_OK;
+    if (n_items > (1 << 20)) return slp_fail(SLP_ERR_INVALID_ARG, "slp_eval_batched: too many states");
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (CachedBatch &c : g_cache) {
+        if (c.key == key) {
+            c.last_use = ++g_cache_tick;
+            return slp_batch_run(c.batch, stream);
+        }
+    }
+    // a new argument set: one item per state, the plans listed once each
+    std::vector<slp_plan_t> uplans;
+    std::vector<int> plan_of;
+    std::vector<const void *> ins;
+    std::vector<void *> outs;
+    for (int i = 0; i < n; ++i) {
+        const slp_plan_s &p = *plans[i];
+        int u = (int)(std::find(uplans.begin(), uplans.end(), plans[i]) - uplans.begin());
+        if (u == (int)uplans.size()) uplans.push_back(plans[i]);
+        const size_t es = p.prec == 64 ? 8 : 4;
+        const size_t in_bytes = es * (size_t)(input_kind == SLP_INPUT_SIGMA ? p.Q
+                                            : input_kind == SLP_INPUT_MAG ? 3 * p.Q : 3 * p.N);
+        for (int k = 0; k < n_states_each[i]; ++k) {
+            plan_of.push_back(u);
+            ins.push_back((const char *)d_in[i] + in_bytes * k);
+            outs.push_back((char *)d_phi[i] + es * (size_t)p.N * k);
+        }
+    }
+    slp_batch_t b = nullptr;
+    const slp_status cst = slp_batch_create((int)uplans.size(), uplans.data(), (int)plan_of.size(), plan_of.data(),
+                                            input_kind, ins.data(), outs.data(), 1, &b);
+    if (cst != SLP_OK) return cst;
+    if (g_cache.size() >= BATCH_CACHE_MAX) {
+        auto lru = std::min_element(g_cache.begin(), g_cache.end(),
+                                    [](const CachedBatch &a, const CachedBatch &c) { return a.last_use < c.last_use; });
+        release(lru->batch);
+        g_cache.erase(lru);
+    }
+    CachedBatch c;
+    c.key = key;
+    c.batch = b;
+    c.last_use = ++g_cache_tick;
+    g_cache.push_back(c);
+    return slp_batch_run(b, stream);
 }
 
 // ------------------------------------------------------------------ autotuner

@@ -43,6 +43,9 @@ struct NearItem {
     int rbegin, rend;
 };
 
+// Error codes written to the plan's sticky status word (the first one stays).
+enum { DEV_ERR_NONE = 0, DEV_ERR_BAD_ITEM = 1, DEV_ERR_BAD_INDEX = 2, DEV_ERR_NONFINITE = 3 };
+
 // Device-side view of a plan.  Plain data, passed by value to launchers.
 struct DevPlan {
     int prec;           // 32 or 64
@@ -129,6 +132,7 @@ struct DevPlan {
     void *out_st[NEAR_STATES];
 
     int *err;  // device status word (sticky)
+    int check_finite;  // 1: inputs and results are checked for NaN/Inf (DEV_ERR_NONFINITE)
 };
 
 // Kernel launchers (return the launch error, if any).

@@ -882,6 +882,7 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     d.inv_s_sqrt2 = p.sigma_g > 0 ? 1.0 / (p.sigma_g * std::sqrt(2.0)) : 0.0;
     d.kernel_mode = p.kernel_mode;
     d.deterministic = p.opts.deterministic;
+    d.check_finite = p.opts.check_finite ? 1 : 0;
 
     // sources / targets in sorted order
     std::vector<T4> sg(p.Q), tg(p.N);
@@ -1312,57 +1313,65 @@ slp_status cuda_status(cudaError_t e, const char *what) {
     return fail(SLP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-// Kernels of one evaluation in serial order (names reported by the profiler entry point).
-const char *const STAGE_NAMES[] = {"charges", "spread", "fft_x", "fft_y", "fft_z_mul", "ifft_y", "ifft_x",
-                                   "near", "near_reduce", "gather"};
-const int N_STAGE_NAMES = 10;
+// Kernel slots of the profiler entry point (slp_debug_profile).  A serial
+// profiled evaluation brackets each kernel it launches with a pair of events
+// on the launch stream; slots whose kernel did not launch report -1.
+const char *const STAGE_NAMES[SLP_PROFILE_SLOTS] = {
+    "charges", "spread", "fft_x", "fft_y", "fft_z_mul", "ifft_y", "ifft_x", "nodal_prep",
+    "near_zero", "near", "near_reduce", "gather", "fft_xy", "ifft_yx", "fft_yzy"};
+enum {
+    SLOT_CHARGES, SLOT_SPREAD, SLOT_FFT_X, SLOT_FFT_Y, SLOT_FFT_Z, SLOT_IFFT_Y, SLOT_IFFT_X, SLOT_NODAL_PREP,
+    SLOT_NEAR_ZERO, SLOT_NEAR, SLOT_NEAR_REDUCE, SLOT_GATHER, SLOT_FFT_XY, SLOT_IFFT_YX, SLOT_FFT_YZY
+};
 
 // Enqueue the evaluation up to stage `last`.
-//   serial (ev != NULL, or ex == NULL): charges, spread, 5 FFT passes, near
-//     field into phi_part, gather (far field + phi_part) on s; with ev,
-//     ev[i] is recorded before kernel slot i and ev[i + 1] after it;
-//   concurrent (ex != NULL, no ev): the near field runs on ex->aux (lowest
+//   serial (prof != NULL, or ex == NULL): charges, spread, 5 FFT passes, near
+//     field into phi_part, gather (far field + phi_part) on s; with prof,
+//     every launched kernel is bracketed by its slot's two events;
+//   concurrent (ex != NULL, no prof): the near field runs on ex->aux (lowest
 //     priority) while the spread, FFT passes and gather run on ex->main
 //     (highest priority, so the latency-bound FFT blocks are dispatched ahead
 //     of pending near-field blocks); both fork from s, the gather waits for
 //     the near field, and s waits for the gather.
 slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *d_in, void *d_phi,
-                        cudaStream_t s, int last, cudaEvent_t *ev, SlpExec *ex) {
-    int k = 0;
-    auto rec = [&]() {
-        if (ev) cudaEventRecord(ev[k], s);
-        ++k;
+                        cudaStream_t s, int last, SlpProfile *prof, SlpExec *ex) {
+    // launch `fn` on stream t, bracketed by the slot's events when profiling
+    auto timed = [&](int slot, cudaStream_t t, auto fn, const char *what) -> slp_status {
+        if (prof) cudaEventRecord(prof->ev[2 * slot], t);
+        TRY(cuda_status(fn(), what));
+        if (prof) {
+            cudaEventRecord(prof->ev[2 * slot + 1], t);
+            prof->launched[slot] = true;
+        }
+        return SLP_OK;
     };
     // nodal input with the precomputed near field: the charges are only needed
     // by the spread, which computes them itself
     const bool use_matrix = kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
     const bool fuse = use_matrix && last > SLP_STAGE_CHARGES;
-    const bool concurrent = ex != nullptr && ev == nullptr && last >= SLP_STAGE_NEAR;
+    const bool concurrent = ex != nullptr && prof == nullptr && last >= SLP_STAGE_NEAR;
     const size_t es = p.prec == 64 ? 8 : 4;
+    const size_t part_bytes = (es * (size_t)p.N + 15) / 16 * 16;
     // near-field branch on stream t
     auto near_branch = [&](cudaStream_t t) -> slp_status {
         if (use_matrix) {
-            TRY(cuda_status(slp::launch_nodal_prep(d, d_in, t), "nodal prep"));
-            TRY(cuda_status(slp::launch_near_matrix(d, d_in, t), "near-field matrix"));
-            rec();
-            rec();
+            TRY(timed(SLOT_NODAL_PREP, t, [&] { return slp::launch_nodal_prep(d, d_in, t); }, "nodal prep"));
+            TRY(timed(SLOT_NEAR, t, [&] { return slp::launch_near_matrix(d, d_in, t); }, "near-field matrix"));
             return SLP_OK;
         }
         if (!p.opts.deterministic)
-            TRY(cuda_status(slp::launch_zero(d.phi_part, (es * (size_t)p.N + 15) / 16 * 16, t), "zero near field"));
-        TRY(cuda_status(slp::launch_near(d, t), "near field"));
-        rec();
+            TRY(timed(SLOT_NEAR_ZERO, t, [&] { return slp::launch_zero(d.phi_part, part_bytes, t); },
+                      "zero near field"));
+        TRY(timed(SLOT_NEAR, t, [&] { return slp::launch_near(d, t); }, "near field"));
         if (p.opts.deterministic)
-            TRY(cuda_status(slp::launch_near_reduce(d, p.d_blk_first, (int)p.near_blk_first.size() - 1, t),
-                            "near reduce"));
-        rec();
+            TRY(timed(SLOT_NEAR_REDUCE, t, [&] {
+                return slp::launch_near_reduce(d, p.d_blk_first, (int)p.near_blk_first.size() - 1, t);
+            }, "near reduce"));
         return SLP_OK;
     };
     cudaEvent_t *tl = concurrent ? ex->timeline : nullptr;
     if (tl) TRY(cuda_status(cudaEventRecord(tl[0], s), "timeline"));
-    rec();
-    if (!fuse) TRY(cuda_status(slp::launch_charges(d, kind, d_in, s), "charges"));
-    rec();
+    if (!fuse) TRY(timed(SLOT_CHARGES, s, [&] { return slp::launch_charges(d, kind, d_in, s); }, "charges"));
     if (last <= SLP_STAGE_CHARGES) return SLP_OK;
     cudaStream_t caller = s;
     if (concurrent) {
@@ -1374,42 +1383,32 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
         if (tl) TRY(cuda_status(cudaEventRecord(tl[3], ex->aux), "timeline"));
         TRY(cuda_status(cudaEventRecord(ex->join, ex->aux), "join"));
     }
-    TRY(cuda_status(slp::launch_spread(d, fuse ? kind : -1, d_in, s), "spread"));
+    TRY(timed(SLOT_SPREAD, s, [&] { return slp::launch_spread(d, fuse ? kind : -1, d_in, s); }, "spread"));
     if (tl) TRY(cuda_status(cudaEventRecord(tl[1], s), "timeline"));
-    rec();
     if (last <= SLP_STAGE_SPREAD) return SLP_OK;
     // fused plane passes (FX + FY, IY + IX) unless the run stops between them
     const bool fused = d.fuse_pb > 0;
     // fused column passes (FY, FZ, IY) unless the run stops between them
     const bool yzy = !fused && d.yzy_g > 0 && last >= SLP_STAGE_IFFT_Y;
     if (fused && last >= SLP_STAGE_FFT_Y) {
-        TRY(cuda_status(slp::launch_fft_forward_xy(d, s), "fft xy"));
-        rec();
-        rec();
+        TRY(timed(SLOT_FFT_XY, s, [&] { return slp::launch_fft_forward_xy(d, s); }, "fft xy"));
     } else {
-        TRY(cuda_status(slp::launch_fft_forward_x(d, s), "fft x"));
-        rec();
+        TRY(timed(SLOT_FFT_X, s, [&] { return slp::launch_fft_forward_x(d, s); }, "fft x"));
         if (last <= SLP_STAGE_FFT_X) return SLP_OK;
         if (yzy)
-            TRY(cuda_status(slp::launch_fft_yzy(d, s), "fft yzy"));
+            TRY(timed(SLOT_FFT_YZY, s, [&] { return slp::launch_fft_yzy(d, s); }, "fft yzy"));
         else
-            TRY(cuda_status(slp::launch_fft_forward_y(d, s), "fft y"));
-        rec();
+            TRY(timed(SLOT_FFT_Y, s, [&] { return slp::launch_fft_forward_y(d, s); }, "fft y"));
     }
     if (last <= SLP_STAGE_FFT_Y) return SLP_OK;
-    if (!yzy) TRY(cuda_status(slp::launch_fft_z_multiply(d, s), "fft z"));
-    rec();
+    if (!yzy) TRY(timed(SLOT_FFT_Z, s, [&] { return slp::launch_fft_z_multiply(d, s); }, "fft z"));
     if (last <= SLP_STAGE_FFT_Z) return SLP_OK;
     if (fused && last >= SLP_STAGE_IFFT_X) {
-        TRY(cuda_status(slp::launch_fft_inverse_yx(d, s), "ifft yx"));
-        rec();
-        rec();
+        TRY(timed(SLOT_IFFT_YX, s, [&] { return slp::launch_fft_inverse_yx(d, s); }, "ifft yx"));
     } else {
-        if (!yzy) TRY(cuda_status(slp::launch_fft_inverse_y(d, s), "ifft y"));
-        rec();
+        if (!yzy) TRY(timed(SLOT_IFFT_Y, s, [&] { return slp::launch_fft_inverse_y(d, s); }, "ifft y"));
         if (last <= SLP_STAGE_IFFT_Y) return SLP_OK;
-        TRY(cuda_status(slp::launch_fft_inverse_x(d, s), "ifft x"));
-        rec();
+        TRY(timed(SLOT_IFFT_X, s, [&] { return slp::launch_fft_inverse_x(d, s); }, "ifft x"));
     }
     if (last <= SLP_STAGE_IFFT_X) return SLP_OK;
     if (tl) TRY(cuda_status(cudaEventRecord(tl[2], s), "timeline"));
@@ -1419,13 +1418,10 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
         TRY(near_branch(s));
     } else {
         // far field only
-        TRY(cuda_status(slp::launch_zero(d.phi_part, (es * (size_t)p.N + 15) / 16 * 16, s), "zero near field"));
-        rec();
-        rec();
+        TRY(timed(SLOT_NEAR_ZERO, s, [&] { return slp::launch_zero(d.phi_part, part_bytes, s); }, "zero near field"));
     }
-    TRY(cuda_status(slp::launch_gather(d, d_phi, s), "gather"));
+    TRY(timed(SLOT_GATHER, s, [&] { return slp::launch_gather(d, d_phi, s); }, "gather"));
     if (tl) TRY(cuda_status(cudaEventRecord(tl[4], s), "timeline"));
-    rec();
     if (concurrent) {
         TRY(cuda_status(cudaEventRecord(ex->done, s), "done"));
         TRY(cuda_status(cudaStreamWaitEvent(caller, ex->done, 0), "done wait"));
@@ -1434,8 +1430,8 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
 }
 
 slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, cudaStream_t s, int last,
-                        cudaEvent_t *ev = nullptr) {
-    return run_pipeline(p, p.dp, kind, d_in, d_phi, s, last, ev, ev ? nullptr : &p.exec);
+                        SlpProfile *prof = nullptr) {
+    return run_pipeline(p, p.dp, kind, d_in, d_phi, s, last, prof, prof ? nullptr : &p.exec);
 }
 
 // S states of nodal input with the precomputed near field, in chunks of up
@@ -1535,8 +1531,8 @@ slp_status slp_fail(slp_status st, const char *fmt, ...) {
 }
 
 slp_status slp_run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *d_in, void *d_phi,
-                            cudaStream_t s, int last, cudaEvent_t *ev, SlpExec *ex) {
-    return run_pipeline(p, d, kind, d_in, d_phi, s, last, ev, ex);
+                            cudaStream_t s, int last, SlpProfile *prof, SlpExec *ex) {
+    return run_pipeline(p, d, kind, d_in, d_phi, s, last, prof, ex);
 }
 
 slp_status slp_run_states(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *const *ins, void *const *outs,
@@ -1826,6 +1822,8 @@ slp_status slp_check(slp_plan_t p) {
     TRY(cuda_status(cudaMemcpy(&code, p->dp.err, sizeof(int), cudaMemcpyDeviceToHost), "read status"));
     if (code != 0) {
         cudaMemset(p->dp.err, 0, sizeof(int));
+        if (code == slp::DEV_ERR_NONFINITE)
+            return fail(SLP_ERR_NONFINITE, "checked evaluation saw a NaN or Inf in its input or result");
         return fail(SLP_ERR_CUDA, "device status word %d (a kernel saw an inconsistent work item)", code);
     }
     return SLP_OK;
@@ -1833,6 +1831,7 @@ slp_status slp_check(slp_plan_t p) {
 
 slp_status slp_destroy(slp_plan_t p) {
     if (!p) return SLP_OK;
+    slp_batch_cache_drop(p);
     free_device(*p);
     delete p;
     return SLP_OK;
@@ -1973,20 +1972,21 @@ slp_status slp_debug_profile(slp_plan_t p, int kind, const void *d_in, void *d_p
                              int n) {
     if (!p || !ms) return fail(SLP_ERR_INVALID_ARG, "NULL argument");
     if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan");
-    if (n < N_STAGE_NAMES) return fail(SLP_ERR_INVALID_ARG, "need room for %d timings", N_STAGE_NAMES);
+    if (n < SLP_PROFILE_SLOTS) return fail(SLP_ERR_INVALID_ARG, "need room for %d timings", SLP_PROFILE_SLOTS);
     if (kind < 0 || kind > 2 || !d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "bad input");
     DeviceGuard g(p->device);
-    cudaEvent_t ev[N_STAGE_NAMES + 1];
-    for (int i = 0; i <= N_STAGE_NAMES; ++i)
-        if (cudaEventCreate(&ev[i]) != cudaSuccess) return fail(SLP_ERR_CUDA, "cudaEventCreate");
-    slp_status st = run_pipeline(*p, kind, d_in, d_phi, (cudaStream_t)stream, SLP_STAGE_NEAR, ev);
-    if (st == SLP_OK) st = cuda_status(cudaEventSynchronize(ev[N_STAGE_NAMES]), "event sync");
-    for (int i = 0; i < N_STAGE_NAMES && st == SLP_OK; ++i) {
-        float t = 0.f;
-        st = cuda_status(cudaEventElapsedTime(&t, ev[i], ev[i + 1]), "elapsed");
+    SlpProfile prof;
+    for (int i = 0; i < 2 * SLP_PROFILE_SLOTS; ++i)
+        if (cudaEventCreate(&prof.ev[i]) != cudaSuccess) return fail(SLP_ERR_CUDA, "cudaEventCreate");
+    for (int i = 0; i < SLP_PROFILE_SLOTS; ++i) prof.launched[i] = false;
+    slp_status st = run_pipeline(*p, kind, d_in, d_phi, (cudaStream_t)stream, SLP_STAGE_NEAR, &prof);
+    if (st == SLP_OK) st = cuda_status(cudaStreamSynchronize((cudaStream_t)stream), "stream sync");
+    for (int i = 0; i < SLP_PROFILE_SLOTS && st == SLP_OK; ++i) {
+        float t = -1.f;
+        if (prof.launched[i]) st = cuda_status(cudaEventElapsedTime(&t, prof.ev[2 * i], prof.ev[2 * i + 1]), "elapsed");
         ms[i] = t;
     }
-    for (int i = 0; i <= N_STAGE_NAMES; ++i) cudaEventDestroy(ev[i]);
+    for (int i = 0; i < 2 * SLP_PROFILE_SLOTS; ++i) cudaEventDestroy(prof.ev[i]);
     return st;
 }
 
@@ -2007,7 +2007,7 @@ slp_status slp_debug_timeline(slp_plan_t p, int kind, const void *d_in, void *d_
     return st;
 }
 
-const char *slp_debug_stage_name(int i) { return (i >= 0 && i < N_STAGE_NAMES) ? STAGE_NAMES[i] : ""; }
+const char *slp_debug_stage_name(int i) { return (i >= 0 && i < SLP_PROFILE_SLOTS) ? STAGE_NAMES[i] : ""; }
 
 double slp_debug_window(int m, double d) { return kb_window_host(m, d); }
 double slp_debug_window_hat(int m, int L, double l) { return kb_hat_host(m, L, l); }

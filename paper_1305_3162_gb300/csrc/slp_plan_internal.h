@@ -90,14 +90,20 @@ struct slp_plan_s {
 // Record a failure text for slp_last_error() and return the status.
 slp_status slp_fail(slp_status st, const char *fmt, ...);
 
+// Events of a profiled evaluation: kernel slot i is bracketed by ev[2i] and
+// ev[2i + 1] on its launch stream, and launched[i] is set when it ran.
+constexpr int SLP_PROFILE_SLOTS = 15;
+struct SlpProfile {
+    cudaEvent_t ev[2 * SLP_PROFILE_SLOTS];
+    bool launched[SLP_PROFILE_SLOTS];
+};
+
 // Enqueue one evaluation of `p` with the device view `d` (the plan's own
 // scratch or another scratch set) up to stage `last`.  With ex != NULL (and
-// no profiling events) the near-field branch runs concurrently on ex->aux;
-// with ev != NULL everything runs in order on s and events are recorded
-// around each kernel (SLP_PROFILE_SLOTS + 1 entries).
-constexpr int SLP_PROFILE_SLOTS = 10;
+// no profile) the near-field branch runs concurrently on ex->aux; with prof
+// != NULL everything runs in order on s and each launched kernel is timed.
 slp_status slp_run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *d_in, void *d_phi,
-                            cudaStream_t s, int last, cudaEvent_t *ev, SlpExec *ex);
+                            cudaStream_t s, int last, SlpProfile *prof, SlpExec *ex);
 
 // Enqueue n evaluations of `p` on the device view `d` (states ins[k] ->
 // outs[k]); nodal input with the precomputed near field shares one pass over
@@ -111,6 +117,10 @@ slp_status slp_run_states(slp_plan_s &p, const slp::DevPlan &d, int kind, const 
 // `allocs` (released by the caller with cudaFree).  Grids and spectra are
 // zeroed (rows outside the active region are never written afterwards).
 slp_status slp_alloc_scratch(slp_plan_s &p, slp::DevPlan &out, std::vector<void *> &allocs, int64_t *bytes);
+
+// Release the graphs slp_eval_batched cached for argument sets that use `plan`
+// (called by slp_destroy).
+void slp_batch_cache_drop(const slp_plan_s *plan);
 
 // Bytes of one scratch set of `p`.
 int64_t slp_scratch_bytes(const slp_plan_s &p);

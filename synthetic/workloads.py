@@ -13,6 +13,11 @@ precision and the relative L2 tolerance it is judged at.
   plate    2000 x 500 x 20 box, 5x5 squares (168000 triangles, 84002 nodes),
            3-point rule, smooth random m, grid 512x128x16 requested, FP32,
            tolerance 1e-5.  (Paper: thin film, Table 3.)
+  batched  64 smooth random states on the level-5 sphere, plus 16 meshes of
+           uneven size (cubes, spheres, plates; ~1.2k to ~200k triangles) with
+           4 states each (batched_items).
+  served   eight resident meshes (cube, sphere, plate, torus; ~2k to 1.92M
+           triangles) with their grids (served_pool).
 """
 from __future__ import annotations
 
@@ -87,3 +92,40 @@ def torus(R=2.0, r=0.5, nu=64, nv=32, grid=(128, 128, 64), precision=32, toleran
     seed = fields.workload_seed(index)
     m = fields.smooth_random(V, seed)
     return Workload(f"torus_{nu}x{nv}", V, T, 3, m, tuple(grid), precision, tolerance, seed)
+
+
+def batched_items():
+    """(name, V, T, q, grid or None for autotuned, [nodal m states]) of the
+    batched workload: 64 seeded smooth states on the level-5 sphere at 128^3,
+    plus 16 meshes of uneven size (cubes, spheres, plates; ~1.2k to ~200k
+    triangles) with 4 states each."""
+    items = []
+    V, T = meshes.icosphere(5)
+    items.append(("sphere_L5", V, T, 7, (128, 128, 128), [fields.smooth_random(V, 7000 + i) for i in range(64)]))
+    shapes = [("cube10", meshes.cube(10), 3), ("cube20", meshes.cube(20), 3), ("cube40", meshes.cube(40), 3),
+              ("cube70", meshes.cube(70), 3), ("cube100", meshes.cube(100), 3), ("cube128", meshes.cube(128), 3),
+              ("sphere_L3", meshes.icosphere(3), 7), ("sphere_L4", meshes.icosphere(4), 7),
+              ("sphere_L5b", meshes.icosphere(5, 2.0), 3), ("sphere_L6", meshes.icosphere(6), 3),
+              ("sphere_L4b", meshes.icosphere(4, 0.5), 3),
+              ("plate_a", meshes.box(400.0, 100.0, 4.0, 40, 10, 2), 3),
+              ("plate_b", meshes.box(1000.0, 250.0, 10.0, 100, 25, 2), 3),
+              ("plate_c", meshes.box(2000.0, 500.0, 20.0, 200, 50, 2), 3),
+              ("plate_d", meshes.box(1000.0, 1000.0, 20.0, 150, 150, 3), 3),
+              ("plate_e", meshes.box(2000.0, 500.0, 20.0, 300, 75, 3), 3)]
+    for k, (name, (V, T), q) in enumerate(shapes):
+        items.append((name, V, T, q, None, [fields.smooth_random(V, 8000 + 10 * k + i) for i in range(4)]))
+    return items
+
+
+def served_pool():
+    """(name, (V, T), q, grid) of the eight resident meshes of the served
+    workload: cube, sphere, plates and tori, ~2k to 1.92M triangles (the
+    largest a unit cube with 400 x 400 squares per face)."""
+    return [("cube13", meshes.cube(13), 3, (64, 64, 64)),
+            ("sphere_L5", meshes.icosphere(5), 7, (128, 128, 128)),
+            ("plate_2000x500x20_c10", meshes.box(2000.0, 500.0, 20.0, 200, 50, 2), 3, (512, 128, 128)),
+            ("torus_400x100", meshes.torus(2.0, 0.5, 400, 100), 3, (256, 256, 128)),
+            ("sphere_L6", meshes.icosphere(6), 3, (256, 256, 256)),
+            ("plate_2000x500x20_c5", meshes.box(2000.0, 500.0, 20.0, 400, 100, 4), 3, (512, 256, 256)),
+            ("torus_800x200", meshes.torus(2.0, 0.5, 800, 200), 3, (512, 512, 256)),
+            ("cube400", meshes.cube(400), 3, (1024, 1024, 1024))]

@@ -147,3 +147,139 @@ def test_eval_states_fused_passes_and_fp64(prec, tol, fuse, fcol):
         assert rel_l2(got[2], oracle.slp_nodal(V, T, 7, ms[2])) <= tol
     finally:
         slp.slp_destroy(plan)
+
+
+def test_eval_batched_one_call_matches_individual_evaluations():
+    """slp_eval_batched: every state of every entry equals slp_eval on it; a
+    second call with the same buffers (refilled in place) replays the cached
+    graph with the new inputs; a plan may appear in two entries."""
+    slp = lib()
+    torch = torch_cuda()
+    meshes_ = [(*meshes.icosphere(3), 7, (64, 64, 64)), (*meshes.cube(6), 3, (64, 64, 64))]
+    plans = [_plan(slp, V, T, q, 1e-5, 32, g) for V, T, q, g in meshes_]
+    try:
+        entries = [(0, 3), (1, 5), (0, 2)]  # (plan, states)
+        d_in, d_out = [], []
+        for pi, ns in entries:
+            V = meshes_[pi][0]
+            d_in.append(torch.empty(ns * 3 * V.shape[0], dtype=torch.float32, device="cuda"))
+            d_out.append(torch.empty(ns * V.shape[0], dtype=torch.float32, device="cuda"))
+        for rep in range(2):
+            states = []
+            for e, (pi, ns) in enumerate(entries):
+                V = meshes_[pi][0]
+                ms = [fields.smooth_random(V, 1000 * rep + 10 * e + k) for k in range(ns)]
+                states.append(ms)
+                d_in[e].copy_(torch.as_tensor(np.concatenate([m.ravel() for m in ms]), dtype=torch.float32))
+                d_out[e].fill_(float("nan"))
+            slp.slp_eval_batched([plans[pi] for pi, _ in entries], slp.SLP_INPUT_NODAL_MAG, d_in, d_out,
+                                 [ns for _, ns in entries], torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            for e, (pi, ns) in enumerate(entries):
+                N = meshes_[pi][0].shape[0]
+                got = d_out[e].double().cpu().numpy().reshape(ns, N)
+                assert np.all(np.isfinite(got))
+                for k in range(ns):
+                    ref = run(slp, plans[pi], slp.SLP_INPUT_NODAL_MAG, states[e][k], 32)
+                    assert rel_l2(got[k], ref) < 1e-6, (rep, e, k)
+        V, T, q, _ = meshes_[1]
+        ref = oracle.slp_nodal(V, T, q, states[1][4])
+        assert rel_l2(d_out[1].double().cpu().numpy().reshape(5, -1)[4], ref) <= 1e-5
+    finally:
+        for p in plans:
+            slp.slp_destroy(p)
+
+
+@pytest.mark.parametrize("kind", ["nodal", "sigma"])
+def test_checked_evaluation_reports_nonfinite_input(kind):
+    """opts.check_finite: a NaN placed in the host input (no GPU fault is
+    involved) is reported by slp_check as SLP_ERR_NONFINITE; the status is
+    cleared by the report; a clean input then passes; without the option the
+    same input is not reported."""
+    slp = lib()
+    torch = torch_cuda()
+    V, T = meshes.icosphere(2)
+    q = 7
+    if kind == "nodal":
+        k_in = slp.SLP_INPUT_NODAL_MAG
+        clean = fields.vortex(V, 5).ravel()
+    else:
+        k_in = slp.SLP_INPUT_SIGMA
+        clean = fields.random_sigma(T.shape[0] * q, 5)
+    bad = clean.copy()
+    bad[7] = np.nan
+    for check in (1, 0):
+        o = slp.slp_default_opts()
+        o.precision = 32
+        o.check_finite = check
+        for d in range(3):
+            o.grid[d] = 32
+        plan = slp.slp_plan(V, T, q, 1e-5, o)
+        try:
+            d_phi = torch.empty(V.shape[0], dtype=torch.float32, device="cuda")
+            d_bad = torch.as_tensor(bad, dtype=torch.float32, device="cuda")
+            slp.slp_eval(plan, k_in, d_bad, d_phi, torch.cuda.current_stream())
+            if check:
+                with pytest.raises(slp.SlpError) as e:
+                    slp.slp_check(plan)
+                assert e.value.status == slp.SLP_ERR_NONFINITE
+            else:
+                slp.slp_check(plan)
+            d_ok = torch.as_tensor(clean, dtype=torch.float32, device="cuda")
+            slp.slp_eval(plan, k_in, d_ok, d_phi, torch.cuda.current_stream())
+            slp.slp_check(plan)
+            assert np.all(np.isfinite(d_phi.cpu().numpy()))
+        finally:
+            slp.slp_destroy(plan)
+
+
+def test_batched_workload_full_item_list():
+    """The whole batched workload (64 sphere states plus 16 uneven meshes x 4
+    states, grids autotuned where the workload leaves them open) in one CUDA
+    graph: every item equals slp_eval on it, and one state per mesh is within
+    1e-5 of the FP64 oracle at up to 256 seeded targets."""
+    from synthetic import workloads
+    slp = lib()
+    torch = torch_cuda()
+    work = workloads.batched_items()
+    plans, plan_of, d_in, d_out, states = [], [], [], [], []
+    try:
+        for pi, (name, V, T, q, grid, sts) in enumerate(work):
+            o = slp.slp_default_opts()
+            o.precision = 32
+            if grid is not None:
+                for d in range(3):
+                    o.grid[d] = grid[d]
+                plans.append(slp.slp_plan(V, T, q, 1e-5, o))
+            else:
+                h, _ = slp.slp_plan_autotune(V, T, q, 1e-5, o, reps=2)
+                plans.append(h)
+            for m in sts:
+                plan_of.append(pi)
+                states.append((pi, m))
+                d_in.append(torch.as_tensor(m, dtype=torch.float32, device="cuda"))
+                d_out.append(torch.full((V.shape[0],), float("nan"), dtype=torch.float32, device="cuda"))
+        assert len(states) == 128
+        batch = slp.slp_batch_create(plans, plan_of, slp.SLP_INPUT_NODAL_MAG, d_in, d_out)
+        try:
+            slp.slp_batch_run(batch, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            seen = set()
+            for (pi, m), o in zip(states, d_out):
+                got = o.double().cpu().numpy()
+                assert np.all(np.isfinite(got))
+                ref = run(slp, plans[pi], slp.SLP_INPUT_NODAL_MAG, m, 32)
+                assert rel_l2(got, ref) < 1e-6, work[pi][0]
+                if pi not in seen:
+                    seen.add(pi)
+                    name, V, T, q, _, _ = work[pi]
+                    sel = np.sort(np.random.default_rng(pi).choice(V.shape[0], min(256, V.shape[0]), replace=False))
+                    y, _, _ = oracle.sources(V, T, q)
+                    qk = oracle.charges(V, T, q, oracle.KIND_NODAL_MAG, m)
+                    ref_o, _ = oracle.direct_subset(V, sel, y, qk)
+                    assert rel_l2(got[sel], ref_o) <= 1e-5, name
+        finally:
+            slp.slp_batch_destroy(batch)
+    finally:
+        for p in plans:
+            slp.slp_destroy(p)
