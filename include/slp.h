@@ -119,7 +119,12 @@ typedef struct {
                              device, in kernels that read them anyway; a non-finite value sets the
                              plan's status word, which slp_check then reports as SLP_ERR_NONFINITE
                              (the evaluation still completes; nothing traps) */
-    int reserved[4];
+    int spread_table;     /* FP32 spread with m <= 4: 1 reads each source's window values from a
+                             plan-time table (3 x 2m floats per source, 96 bytes at m = 4) instead of evaluating the window per group, 0 evaluates
+                             them, -1 automatic (the table from 2^18 sources: measured faster there,
+                             while on smaller meshes its extra traffic slows the concurrent
+                             near-field product more than it saves) */
+    int reserved[3];
 } slp_plan_opts;
 
 typedef struct {
@@ -159,6 +164,7 @@ typedef struct {
     int spread_blocks_per_sm;    /* FP32 spread with m <= 4: the register budget's blocks per SM, 4
                                     where cell groups hold >= 8 sources on average, else 5; 0 for
                                     the other spread kernels */
+    int spread_table;            /* 1: the spread reads plan-time window tables (opts.spread_table) */
 } slp_info;
 
 /* Fill opts with defaults: precision 32, automatic grid/m/kernel/near mode,

@@ -62,7 +62,7 @@ class slp_plan_opts(ctypes.Structure):
                 ("kernel_mode", ctypes.c_int), ("near_mode", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("device", ctypes.c_int), ("allow_grid_raise", ctypes.c_int), ("check_mesh", ctypes.c_int),
                 ("fuse_plane_passes", ctypes.c_int), ("fuse_column_passes", ctypes.c_int),
-                ("check_finite", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("check_finite", ctypes.c_int), ("spread_table", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 SLP_TUNE_MAX = 8
@@ -112,7 +112,7 @@ class slp_info(ctypes.Structure):
                 ("launches_per_eval", ctypes.c_int), ("active_rows", ctypes.c_int64),
                 ("active_planes", ctypes.c_int), ("fused_plane_passes", ctypes.c_int),
                 ("fused_column_passes", ctypes.c_int), ("gather_item_targets", ctypes.c_int),
-                ("spread_blocks_per_sm", ctypes.c_int)]
+                ("spread_blocks_per_sm", ctypes.c_int), ("spread_table", ctypes.c_int)]
 
     def to_dict(self):
         out = {}
@@ -506,7 +506,8 @@ class Plan:
 
     def __init__(self, vertices, triangles, quadrature=7, tolerance=1e-5, precision=32, grid=None, m=0,
                  kernel_mode=SLP_KERNEL_AUTO, near_mode=SLP_NEAR_AUTO, deterministic=False, device=0,
-                 allow_grid_raise=True, check_mesh=True, fuse_plane_passes=-1, fuse_column_passes=-1):
+                 allow_grid_raise=True, check_mesh=True, fuse_plane_passes=-1, fuse_column_passes=-1,
+                 spread_table=-1):
         o = slp_default_opts()
         o.precision = int(precision)
         if grid is not None:
@@ -521,6 +522,7 @@ class Plan:
         o.check_mesh = int(bool(check_mesh))
         o.fuse_plane_passes = int(fuse_plane_passes)
         o.fuse_column_passes = int(fuse_column_passes)
+        o.spread_table = int(spread_table)
         self.handle = slp_plan(vertices, triangles, quadrature, tolerance, o)
         self.info = slp_query(self.handle)
         self.n_targets = self.info["n_targets"]

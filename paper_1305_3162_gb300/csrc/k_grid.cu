@@ -61,7 +61,8 @@ __device__ __forceinline__ T charge_apply(const DevPlan &p, const ChargeRecipe<T
         my = in[3 * (int64_t)u + 1];
         mz = in[3 * (int64_t)u + 2];
     } else {
-        const int s = u - (u / p.q) * p.q;
+        // rule point of source u = j q + s (q is 1, 3 or 7: divisions by constants)
+        const int s = p.q == 7 ? u % 7 : (p.q == 3 ? u % 3 : 0);
         const T *lam = (const T *)p.lam + 3 * s;
         const T l0 = lam[0], l1 = lam[1], l2 = lam[2];
         const T *a = in + 3 * (int64_t)v.x, *b = in + 3 * (int64_t)v.y, *c = in + 3 * (int64_t)v.z;
@@ -543,6 +544,257 @@ __global__ void __launch_bounds__(256, MINB) k_spread_groups(DevPlan p, int fuse
     }
 }
 
+// ---------------------------------------------------------------- spread, window tables (FP32)
+// Variant for FP32 and 2M <= 8 that reads the window values of every source
+// from a plan-time table instead of evaluating the window: per sorted source
+// one row of 3 x WP floats (psi along x, y, z at the 2M points of its box,
+// each axis padded to WP = 2M rounded up to 4).  A warp walks its list of
+// cell groups; each group's table rows (contiguous) are copied into one of
+// two per-warp buffers with 16-byte asynchronous copies issued one group
+// ahead of use, so no registers are held for them while the current group
+// accumulates.  The group's box is accumulated in registers and added to the
+// block's shared tile.  Lane (ix, izs) holds the box column (ix, iz = izs +
+// ZL h, all iy) as H x W/2 pairs; the group's local cell comes with the group
+// list, so the tile address of every update is a per-lane constant plus
+// compile-time offsets.
+template <int M> struct TabGeom {
+    static constexpr int W = 2 * M;
+    static constexpr int WP = (W + 3) & ~3;
+    static constexpr int ROW = 3 * WP;          // floats per source row
+    static constexpr int PARTS = ROW / 4;       // float4 per source row
+    static constexpr int GF4 = SPREAD_GMAX * PARTS;  // float4 of one full group
+    static constexpr int LD = (GF4 + 31) / 32;  // copies per lane per group
+};
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// shared memory: tile, two table buffers per warp, charges and the item's
+// group descriptors and cells (at most one group per source)
+template <int M> __host__ __device__ constexpr size_t spread_tab_smem(int nwarps, int chunk, int size) {
+    return (((size_t)size + 3) & ~(size_t)3) * 4 + (size_t)nwarps * 2 * SPREAD_GMAX * TabGeom<M>::ROW * 4 +
+           (size_t)chunk * 4 * 3 + (SPREAD_WARPS + 1) * 4;
+}
+
+template <int M, int TS, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_spread_tab(DevPlan p, int fused_kind, const float *__restrict__ in) {
+    typedef TileGeomG<M, TS> G;
+    typedef TabGeom<M> TG;
+    constexpr int W = G::W, RS = G::RS, PS = G::PS, XO = G::XO, ZL = G::ZL, H = G::H;
+    constexpr int WP = TG::WP, ROW = TG::ROW, PARTS = TG::PARTS, LD = TG::LD;
+    constexpr int BUF = SPREAD_GMAX * ROW;  // floats of one warp buffer
+    static_assert(W <= 8, "2M <= 8");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    float *tile = (float *)smem_raw;
+    float *wbuf = tile + ((G::SIZE + 3) & ~3) + (size_t)warp * 2 * BUF;
+    float *sq = tile + ((G::SIZE + 3) & ~3) + (size_t)nwarps * 2 * BUF;
+
+    const TileItem it = p.spread_items[blockIdx.x];
+    const int nsrc = it.end - it.begin;
+    // the item's group lists: descriptors and cells staged in shared memory
+    int *sgd = (int *)(sq + p.spread_chunk);
+    int *sgc = sgd + p.spread_chunk;
+    int *soff = sgc + p.spread_chunk;
+    if (p.ks > 1) in = (const float *)p.in_st[blockIdx.y];  // state of a batched launch
+    {
+        const int n4 = ((G::SIZE + 3) & ~3) / 4;
+        for (int i = threadIdx.x; i < n4; i += blockDim.x) ((float4 *)tile)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float4 *wtab = (const float4 *)p.wtab + (int64_t)it.begin * PARTS;
+    {
+        // group lists of the item (plan data): offsets relative to the item's first group
+        const int *goff = p.sgroup_off + (int64_t)blockIdx.x * (SPREAD_WARPS + 1);
+        const int gfirst = goff[0], ng_item = min(goff[SPREAD_WARPS] - gfirst, p.spread_chunk);
+        if (threadIdx.x <= SPREAD_WARPS) soff[threadIdx.x] = min(max(goff[threadIdx.x] - gfirst, 0), ng_item);
+        for (int i = threadIdx.x; i < ng_item; i += blockDim.x) {
+            sgd[i] = p.sgroups[gfirst + i];
+            sgc[i] = p.sgroup_cell[gfirst + i];
+        }
+    }
+    __syncthreads();
+    // the warp's group lists (a block with fewer warps takes lists w, w + nwarps, ...)
+    const int *goff = soff;
+    int wl = warp, gi = goff[warp], gend = goff[warp + 1];
+    // advance (wl, gi) to the warp's next group, if any
+    auto next = [&]() -> bool {
+        while (gi >= gend) {
+            wl += nwarps;
+            if (wl >= SPREAD_WARPS) return false;
+            gi = goff[wl];
+            gend = goff[wl + 1];
+        }
+        return true;
+    };
+    // group gi's descriptor, and its table rows copied into buffer b
+    auto fetch = [&](int b, int &g0, int &ng, int &cell) {
+        const int gd = sgd[gi];
+        g0 = gd & 0xffff;
+        ng = gd >> 16;
+        cell = sgc[gi];
+        const int nf = (ng >= 1 && ng <= SPREAD_GMAX && g0 + ng <= nsrc) ? ng * PARTS : 0;
+        const float4 *src = wtab + (int64_t)g0 * PARTS;
+        float4 *dst = (float4 *)(wbuf + b * BUF);
+#pragma unroll
+        for (int u = 0; u < LD; ++u) {
+            const int f = lane + 32 * u;
+            if (f < nf) cp_async16(dst + f, src + f);
+        }
+        cp_async_commit();
+    };
+    // plan data before the wait: the charge recipe of the thread's first
+    // source and the table rows of the warp's first group
+    ChargeRecipe<float> r0;
+    if (fused_kind >= 0 && (int)threadIdx.x < nsrc) r0 = charge_recipe<float>(p, it.begin + threadIdx.x);
+    bool have = next();
+    int g0 = 0, ng = 0, cell = 0, cur = 0;
+    if (have) fetch(0, g0, ng, cell);
+    // charges may be the previous kernel's output (or computed here from the input)
+    pdl_wait();
+    pdl_trigger();
+    for (int i = threadIdx.x; i < nsrc; i += blockDim.x) {
+        if (fused_kind >= 0)
+            sq[i] = charge_apply<float>(p, i == (int)threadIdx.x ? r0 : charge_recipe<float>(p, it.begin + i),
+                                        fused_kind, in);
+        else
+            sq[i] = ((const float *)p.qbuf)[it.begin + i];
+    }
+    __syncthreads();
+
+    const int ix = lane % W, izs = lane / W;
+    const bool lane_on = lane < W * ZL;
+    // lane's fixed part of every tile update: column ix, first z offset izs
+    float *const lane_tile = tile + XO + ix + izs * PS;
+    while (have) {
+        const int c_g0 = g0, c_ng = ng, c_cell = cell;
+        ++gi;
+        have = next();
+        if (have) {
+            fetch(cur ^ 1, g0, ng, cell);  // the next group's rows copy while this one accumulates
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncwarp();
+        if (c_g0 + c_ng > nsrc || c_ng < 1 || c_ng > SPREAD_GMAX) {
+            set_error(p.err, DEV_ERR_BAD_ITEM);
+        } else if (lane_on) {
+            constexpr int W2 = (W + 1) / 2;
+            float2 acc[H][W2];
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+#pragma unroll
+                for (int j = 0; j < W2; ++j) acc[h][j] = make_float2(0.f, 0.f);
+            const float *r = wbuf + cur * BUF;
+            const float *qg = sq + c_g0;
+#pragma unroll 2
+            for (int g = 0; g < c_ng; ++g, r += ROW) {
+                const float a = r[ix] * qg[g];
+                float b[H];
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    const int iz = izs + ZL * h;
+                    b[h] = (ZL * H == W || iz < W) ? a * r[2 * WP + iz] : 0.f;
+                }
+                float wy[WP];
+                load_row<WP>(r + WP, wy);
+#pragma unroll
+                for (int j = 0; j < W2; ++j)
+#pragma unroll
+                    for (int h = 0; h < H; ++h)
+                        acc[h][j] = __ffma2_rn(make_float2(b[h], b[h]), make_float2(wy[2 * j], wy[2 * j + 1]), acc[h][j]);
+            }
+            float *base = lane_tile + (c_cell >> 16) * PS + ((c_cell >> 8) & 0xff) * RS + (c_cell & 0xff);
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                if (ZL * H == W || izs + ZL * h < W) {
+#pragma unroll
+                    for (int iy = 0; iy < W; ++iy)
+                        atomicAdd(base + ZL * h * PS + iy * RS, (iy & 1) ? acc[h][iy >> 1].y : acc[h][iy >> 1].x);
+                }
+            }
+        }
+        // every lane is done with buffer `cur` before the next copy into it
+        __syncwarp();
+        cur ^= 1;
+    }
+    __syncthreads();
+
+    constexpr int TE = G::TE, XE = G::XE;
+    const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
+    const int gxs = it.c0x - M + 1 - XO, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
+    float *grid = (float *)p.gridA + blockIdx.y * p.st_grid;
+    const bool xin = gxs >= 0 && gxs + XE <= Lx && (gxs & 3) == 0;
+    if (TS % 4 == 0 && xin && (256 % (XE / 4)) == 0 && blockDim.x == 256) {
+        // thread t adds vector v = t % NV of rows r = t / NV + (256 / NV) j
+        constexpr int NV = XE / 4, RSTEP = 256 / NV, NROW = TE * TE;
+        const int v = threadIdx.x % NV;
+        int r = threadIdx.x / NV;
+        int iy = r % TE, iz = r / TE;
+        for (; r < NROW; r += RSTEP) {
+            const float *t = tile + iz * PS + iy * RS + 4 * v;
+            float a[4];
+            if constexpr (PS % 4 == 0) {
+                const float4 f = *(const float4 *)t;
+                a[0] = f.x; a[1] = f.y; a[2] = f.z; a[3] = f.w;
+            } else if constexpr (PS % 2 == 0) {
+                const float2 f0 = *(const float2 *)t, f1 = *(const float2 *)(t + 2);
+                a[0] = f0.x; a[1] = f0.y; a[2] = f1.x; a[3] = f1.y;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) a[e] = t[e];
+            }
+            if (a[0] != 0.f || a[1] != 0.f || a[2] != 0.f || a[3] != 0.f) {
+                const int gy = (gy0 + iy) & (Ly - 1), gz = (gz0 + iz) & (Lz - 1);
+                float4 *dst = (float4 *)(grid + ((int64_t)gz * Ly + gy) * Lx + gxs) + v;
+                atomicAdd(dst, make_float4(a[0], a[1], a[2], a[3]));
+            }
+            // advance (iy, iz) by RSTEP rows
+            iy += RSTEP % TE;
+            iz += RSTEP / TE;
+            if (iy >= TE) {
+                iy -= TE;
+                ++iz;
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < TE * TE * XE; i += blockDim.x) {
+            const int x = i % XE, rr = i / XE;
+            const int iy = rr % TE, iz = rr / TE;
+            const float v = tile[iz * PS + iy * RS + x];
+            if (v == 0.f) continue;
+            const int gx = (gxs + x) & (Lx - 1);
+            const int gy = (gy0 + iy) & (Ly - 1), gz = (gz0 + iz) & (Lz - 1);
+            atomicAdd(grid + ((int64_t)gz * Ly + gy) * Lx + gx, v);
+        }
+    }
+}
+
+// Plan-time window table of the FP32 table spread: row k (sorted source k)
+// holds psi(f_q + M - 1 - i) for axis q and point i < 2M, evaluated in FP64
+// from the source's fractional grid coordinate, each axis padded with zeros
+// to WP values.
+template <int M>
+__global__ void k_wtab_build(const float4 *__restrict__ src_grid, int64_t Q, double beta, double isb,
+                             float *__restrict__ out) {
+    typedef TabGeom<M> TG;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Q) return;
+    const float4 g = src_grid[k];
+    const double f[3] = {(double)g.x, (double)g.y, (double)g.z};
+    float *row = out + k * TG::ROW;
+    for (int ax = 0; ax < 3; ++ax)
+        for (int i = 0; i < TG::WP; ++i)
+            row[ax * TG::WP + i] =
+                i < TG::W ? (float)kb_window(f[ax] + double(M - 1 - i), 1.0 / M, beta, isb) : 0.f;
+}
+
 // ---------------------------------------------------------------- gather
 // One block per work item (a tile and up to GATHER_CHUNK of its targets): the
 // tile plus halo of grid B is staged in shared memory (same padded layout as
@@ -728,6 +980,26 @@ static cudaError_t spread_mt(const DevPlan &p, int fused_kind, const void *in, c
             return cudaGetLastError();
         };
         if constexpr (sizeof(T) == 4 && M <= 4) {
+            if (p.wtab) {
+                typedef TileGeomG<M, TS> G;
+                const size_t smt = spread_tab_smem<M>(nw, p.spread_chunk, G::SIZE);
+                auto go_t = [&](auto kern) -> cudaError_t {
+                    if (smt > 48 * 1024) {
+                        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt);
+                        if (e != cudaSuccess) return e;
+                    }
+                    if (p.n_spread > 0) {
+                        const cudaError_t le = launch_k(kern, dim3(p.n_spread, p.ks), 32 * nw, smt, s, p, fused_kind,
+                                                        (const float *)in);
+                        if (le != cudaSuccess) return le;
+                    }
+                    return cudaGetLastError();
+                };
+                if (p.spread_dense) return go_t(k_spread_tab<M, TS, 4>);
+                return go_t(k_spread_tab<M, TS, 5>);
+            }
+        }
+        if constexpr (sizeof(T) == 4 && M <= 4) {
             if (p.spread_dense) return go(k_spread_groups<T, M, TS, 4>);
             return go(k_spread_groups<T, M, TS, 5>);
         } else {
@@ -790,6 +1062,25 @@ template <typename T, int M> static cudaError_t gather_t(const DevPlan &p, void 
 cudaError_t launch_spread(const DevPlan &p, int fused_kind, const void *in, cudaStream_t s) {
     if (p.prec == 64) { SLP_DISPATCH_M(spread_t, double, p, fused_kind, in, s) }
     SLP_DISPATCH_M(spread_t, float, p, fused_kind, in, s)
+}
+
+template <int M> static cudaError_t wtab_m(const DevPlan &p, float *out, cudaStream_t s) {
+    if (p.Q == 0) return cudaSuccess;
+    k_wtab_build<M><<<(unsigned)((p.Q + 255) / 256), 256, 0, s>>>((const float4 *)p.src_grid, p.Q, p.beta,
+                                                                  p.inv_sinh_beta, out);
+    return cudaGetLastError();
+}
+
+int spread_table_row(int m) { return 3 * ((2 * m + 3) & ~3); }
+
+cudaError_t launch_wtab_build(const DevPlan &p, float *out, cudaStream_t s) {
+    switch (p.m) {
+        case 2: return wtab_m<2>(p, out, s);
+        case 3: return wtab_m<3>(p, out, s);
+        case 4: return wtab_m<4>(p, out, s);
+        case 5: return wtab_m<5>(p, out, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_gather(const DevPlan &p, void *phi, cudaStream_t s) {

@@ -107,6 +107,9 @@ struct DevPlan {
                                   // spread at 4 blocks per SM with 64 registers, else 5 with 48)
     int gather_chunk;             // most targets in one gather item (<= GATHER_CHUNK)
     const int *sgroups;           // cell groups: first source (within the item) | count << 16
+    const int *sgroup_cell;       // local cell of each group in its item's tile: lx | ly << 8 | lz << 16
+    const void *wtab;             // FP32 table spread: [Q][3][WP] window values per sorted source (NULL: the
+                                  // spread evaluates the window)
     const int *sgroup_off;        // [n_spread][SPREAD_WARPS + 1] group list bounds of each item
     const TileItem *gather_items; int n_gather;
     const NearItem *near_items;   int n_near;
@@ -157,6 +160,10 @@ cudaError_t launch_fft_inverse_yx(const DevPlan &p, cudaStream_t s);
 size_t fused_plane_smem(const DevPlan &p, int PB);
 // phi[perm[t]] = far field at t + phi_part[t]
 cudaError_t launch_gather(const DevPlan &p, void *d_phi, cudaStream_t s);
+// FP32 table spread: floats per source row of the window table (3 x 2m padded
+// to a multiple of 4) and its plan-time build into `out` ([Q] rows)
+int spread_table_row(int m);
+cudaError_t launch_wtab_build(const DevPlan &p, float *out, cudaStream_t s);
 // near field into phi_part (atomics: phi_part must be zero; deterministic: per-item partials, then the reduction
 // overwrites phi_part)
 cudaError_t launch_near(const DevPlan &p, cudaStream_t s);

@@ -528,6 +528,7 @@ void tile_items(const std::vector<double> &grid, const std::vector<uint64_t> &ke
 // of a group ~ a fixed part for its tile update plus one part per source).
 void spread_groups(slp_plan_s &p) {
     p.sgroups.clear();
+    p.sgroup_cell.clear();
     p.sgroup_off.assign(p.spread_items.size() * (slp::SPREAD_WARPS + 1), 0);
     std::vector<std::pair<int, int>> g;  // (count, first)
     std::vector<std::vector<int>> lists(slp::SPREAD_WARPS);
@@ -555,6 +556,13 @@ void spread_groups(slp_plan_s &p) {
         for (int w = 0; w < slp::SPREAD_WARPS; ++w) {
             off[w] = (int32_t)p.sgroups.size();
             p.sgroups.insert(p.sgroups.end(), lists[w].begin(), lists[w].end());
+            // the group's cell relative to the tile's base cell
+            for (int gd : lists[w]) {
+                const uint32_t cell = (uint32_t)p.src_grid[4 * (int64_t)(it.begin + (gd & 0xffff)) + 3];
+                const int lx = (int)(cell & 1023) - it.c0x, ly = (int)((cell >> 10) & 1023) - it.c0y,
+                          lz = (int)((cell >> 20) & 1023) - it.c0z;
+                p.sgroup_cell.push_back(lx | (ly << 8) | (lz << 16));
+            }
         }
         off[slp::SPREAD_WARPS] = (int32_t)p.sgroups.size();
     }
@@ -813,6 +821,8 @@ void active_region(slp_plan_s &p) {
 }
 
 // ---------------------------------------------------------------- device upload
+slp_status cuda_status(cudaError_t e, const char *what);
+
 template <typename T> struct V4;
 template <> struct V4<float> { typedef float4 t; typedef float2 t2; };
 template <> struct V4<double> { typedef double4 t; typedef double2 t2; };
@@ -1042,6 +1052,18 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     d.sgroups = (const int *)ptr;
     TRY(upload(p, &ptr, p.sgroup_off.data(), p.sgroup_off.size()));
     d.sgroup_off = (const int *)ptr;
+    TRY(upload(p, &ptr, p.sgroup_cell.data(), p.sgroup_cell.size()));
+    d.sgroup_cell = (const int *)ptr;
+    d.wtab = nullptr;
+    if (sizeof(T) == 4 && p.m <= 4 && p.Q > 0 &&
+        (p.opts.spread_table > 0 || (p.opts.spread_table < 0 && p.Q >= (1 << 18)))) {
+        // FP32 table spread: window values of every sorted source, built once here
+        void *wt = nullptr;
+        TRY(dalloc(p, &wt, sizeof(float) * (size_t)p.Q * slp::spread_table_row(p.m)));
+        TRY(cuda_status(slp::launch_wtab_build(d, (float *)wt, 0), "window table"));
+        TRY(cuda_status(cudaDeviceSynchronize(), "window table"));
+        d.wtab = wt;
+    }
     TRY(upload(p, &ptr, p.gather_items.data(), p.gather_items.size()));
     d.gather_items = (const slp::TileItem *)ptr;
     d.n_gather = (int)p.gather_items.size();
@@ -1634,6 +1656,7 @@ slp_status slp_default_opts(slp_plan_opts *o) {
     o->check_mesh = 1;
     o->fuse_plane_passes = -1;
     o->fuse_column_passes = -1;
+    o->spread_table = -1;
     return SLP_OK;
 }
 
@@ -1804,6 +1827,7 @@ slp_status slp_query(slp_plan_t p, slp_info *info) {
     info->fused_column_passes = p->device >= 0 && p->dp.yzy_g > 0 ? 1 : 0;
     info->gather_item_targets = p->gather_chunk;
     info->spread_blocks_per_sm = (p->prec == 32 && p->m <= 4) ? (spread_dense(*p) ? 4 : 5) : 0;
+    info->spread_table = p->dp.wtab != nullptr ? 1 : 0;
     return SLP_OK;
 }
 

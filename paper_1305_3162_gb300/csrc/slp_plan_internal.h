@@ -63,6 +63,7 @@ struct slp_plan_s {
     std::vector<double> src_grid, tgt_grid;  // [.][4]
     std::vector<slp::TileItem> spread_items, gather_items;
     std::vector<int32_t> sgroups, sgroup_off;  // spread cell groups and per-item warp lists
+    std::vector<int32_t> sgroup_cell;          // local cell of each group (lx | ly << 8 | lz << 16)
     std::vector<slp::NearItem> near_items;
     std::vector<int2> near_ranges;
     std::vector<int> near_blk_first;  // CSR of items per target block

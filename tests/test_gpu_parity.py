@@ -57,20 +57,22 @@ def test_input_kinds_sphere_L3(kind, prec, tol):
         slp.slp_destroy(plan)
 
 
-@pytest.mark.parametrize("fuse,fcol", [(0, 0), (1, 0), (0, 1)], ids=["separate", "fused-plane", "fused-column"])
-def test_sphere_L5_workload(fuse, fcol):
+@pytest.mark.parametrize("fuse,fcol,table", [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1)],
+                         ids=["separate", "fused-plane", "fused-column", "spread-table"])
+def test_sphere_L5_workload(fuse, fcol, table):
     """Sphere level 5 (20480 triangles), 7-point rule, grid 128^3, FP32, 1e-5,
     with the FFT passes separate, x and y fused per plane, and y, z, inverse
-    y fused per x frequency."""
+    y fused per x frequency; and with the spread reading window tables."""
     slp = lib()
     w = workloads.sphere()
     plan = _plan(slp, w.V, w.T, w.quad, w.tolerance, w.precision, w.grid, fuse_plane_passes=fuse,
-                 fuse_column_passes=fcol)
+                 fuse_column_passes=fcol, spread_table=table)
     try:
         info = slp.slp_query(plan)
         assert info["grid"] == [128, 128, 128] and not info["grid_raised"]
         assert info["fused_plane_passes"] == fuse
         assert info["fused_column_passes"] == fcol
+        assert info["spread_table"] == table
         phi = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, w.m_nodal, 32)
         ref = oracle.slp_nodal(w.V, w.T, w.quad, w.m_nodal)
         err = rel_l2(phi, ref)

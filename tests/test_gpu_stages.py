@@ -10,13 +10,14 @@ from tests.gpu_util import lib, rel_l2, run
 pytestmark = pytest.mark.gpu
 
 
-def _plan(slp, V, T, q, tol, prec, grid, kernel_mode=0, fuse=-1):
+def _plan(slp, V, T, q, tol, prec, grid, kernel_mode=0, fuse=-1, table=-1):
     o = slp.slp_default_opts()
     o.precision = prec
     for d in range(3):
         o.grid[d] = grid[d]
     o.kernel_mode = kernel_mode
     o.fuse_plane_passes = fuse
+    o.spread_table = table
     return slp.slp_plan(V, T, q, tol, o)
 
 
@@ -25,6 +26,7 @@ CASES = [
     ("sphere_L3_fp64_radial", lambda: meshes.icosphere(3), 7, 1e-8, 64, (64, 64, 64), 1, 1e-11),
     ("sphere_L3_fp32_radial", lambda: meshes.icosphere(3), 7, 1e-5, 32, (64, 64, 64), 1, 2e-5),
     ("box_fp32_aniso", lambda: meshes.box(2.0, 1.0, 0.5, 12, 6, 3), 3, 1e-5, 32, (128, 64, 64), 1, 2e-5),
+    ("sphere_L3_fp32_table", lambda: meshes.icosphere(3), 7, 1e-5, 32, (64, 64, 64), 1, 2e-5),
     ("cube_fp64_separable", lambda: meshes.cube(8), 3, 1e-10, 64, (32, 32, 32), 2, 1e-11),
 ]
 
@@ -39,10 +41,12 @@ def test_stages(case, fuse):
     name, mk, q, tol, prec, grid, kmode, rtol = case
     slp = lib()
     V, T = mk()
-    plan = _plan(slp, V, T, q, tol, prec, grid, kmode, fuse)
+    table = 1 if name.endswith("_table") else 0
+    plan = _plan(slp, V, T, q, tol, prec, grid, kmode, fuse, table)
     try:
         info = slp.slp_query(plan)
         assert info["fused_plane_passes"] == fuse
+        assert info["spread_table"] == table
         L = info["grid"]
         n = info["modes"]
         m = info["m"]
