@@ -336,13 +336,13 @@ def _roofline_objects(slp, plan, w, info, prof_ms, ms_step, pairs_within, worklo
     return roofline, _per_kernel(info, prof_ms, w, pairs_within, hbm_peak)
 
 
-def _plain_config(slp, w, args, flush, steps, warmup, n_sample=None, profile=True):
+def _plain_config(slp, w, args, flush, steps, warmup, n_sample=None, profile=True, kernel_mode=0):
     """One workload through slp_eval: parity gate, timed steps, per-kernel profile."""
     import torch
     dev = torch.cuda.current_device()
     t0 = time.perf_counter()
     plan = slp.Plan(w.V, w.T, quadrature=w.quad, tolerance=w.tolerance, precision=w.precision, grid=w.grid,
-                    device=dev)
+                    device=dev, kernel_mode=kernel_mode)
     t_plan = time.perf_counter() - t0
     try:
         info = plan.info
@@ -365,7 +365,7 @@ def _plain_config(slp, w, args, flush, steps, warmup, n_sample=None, profile=Tru
                "ms_per_step": ms, "steps": steps, "warmup": warmup, "dtype": "f32" if w.precision == 32 else "f64",
                "n_targets": w.n_targets, "n_sources": w.n_sources, "grid_requested": list(w.grid),
                "grid": info["grid"], "grid_raised": bool(info["grid_raised"]), "m": info["m"],
-               "kernel_mode": ["auto", "radial", "separable"][info["kernel_mode"]],
+               "kernel_mode": ["auto", "radial", "separable", "expsum"][info["kernel_mode"]],
                "near_mode": ["auto", "on_the_fly", "precomputed"][info["near_mode"]],
                "tolerance": w.tolerance, "rel_l2": rel_l2, "parity_targets": n_checked,
                "parity_ok": rel_l2 <= w.tolerance, "plan_s": round(t_plan, 2),
@@ -392,6 +392,9 @@ def run_suite(args):
     t0 = time.perf_counter()
     suite["cfg0_cube_fp64"] = _plain_config(slp, workloads.cube(), args, flush, 50, 5)
     suite["cfg2_plate"] = _plain_config(slp, workloads.plate(), args, flush, 20, 3, n_sample=2048)
+    # the paper's own smooth kernel (exponential sum of Gaussians) on the sphere workload
+    suite["sphere_expsum_kernel"] = _plain_config(slp, workloads.sphere(tolerance=1e-4), args, flush, 50, 5,
+                                                  kernel_mode=slp.SLP_KERNEL_EXPSUM)
     del flush
     torch.cuda.empty_cache()
     suite["cfg3_batched"] = run_batched(args, emit=False, steps=10, warmup=3)

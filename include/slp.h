@@ -71,9 +71,20 @@ enum { SLP_INPUT_SIGMA = 0, SLP_INPUT_MAG = 1, SLP_INPUT_NODAL_MAG = 2 };
  *   SEPARABLE: N_s = a separable band-limited periodic kernel; every pair is
  *              near and the near kernel is N - N_s evaluated exactly
  *              (for grids too small to resolve RADIAL at the tolerance);
+ *   EXPSUM:    the paper's kernel (Sec. 3.3): the body scaled into
+ *              (-0.2, 0.2)^3 of a cubic torus of period P (the scaling of the
+ *              paper's experiments), 1/r approximated on [eps, P/2] by a sum of
+ *              Gaussians sum_k w_k exp(-g_k r^2) truncated to the S' widest
+ *              terms that the grid resolves, Fourier coefficients of each
+ *              Gaussian integrated over one period per axis (separable,
+ *              S' (n_x + n_y + n_z)/2 numbers), near-field kernel
+ *              (1/r - sum_k w_k exp(-g_k r^2)) / (4 pi) inside eps.  Its
+ *              accuracy is the paper's: the truncated periodic extension of
+ *              the widest Gaussians limits it to about 1e-3 relative, so it
+ *              is chosen only explicitly;
  *   AUTO:      RADIAL when feasible on the grid, else SEPARABLE for small
  *              meshes at precision 64, else a raised grid (when allowed). */
-enum { SLP_KERNEL_AUTO = 0, SLP_KERNEL_RADIAL = 1, SLP_KERNEL_SEPARABLE = 2 };
+enum { SLP_KERNEL_AUTO = 0, SLP_KERNEL_RADIAL = 1, SLP_KERNEL_SEPARABLE = 2, SLP_KERNEL_EXPSUM = 3 };
 
 /* Near-field evaluation:
  *   ON_THE_FLY:  kernel values computed per pair in every evaluation;
@@ -165,6 +176,7 @@ typedef struct {
                                     where cell groups hold >= 8 sources on average, else 5; 0 for
                                     the other spread kernels */
     int spread_table;            /* 1: the spread reads plan-time window tables (opts.spread_table) */
+    int expsum_terms;            /* EXPSUM: Gaussians kept in the smooth kernel (S'); 0 otherwise */
 } slp_info;
 
 /* Fill opts with defaults: precision 32, automatic grid/m/kernel/near mode,

@@ -58,7 +58,10 @@ enum {
     SLP_HOST_ACTIVE_Z = 12,    /* int32 [2]: first active plane z0 and active plane count (mod Lz) */
     SLP_HOST_SPREAD_GROUPS = 13,    /* int32 [n]: spread cell groups, first source within the item
                                        | source count << 16 */
-    SLP_HOST_SPREAD_GROUP_OFF = 14  /* int32 [spread items][9]: bounds of the 8 group lists of each item */
+    SLP_HOST_SPREAD_GROUP_OFF = 14, /* int32 [spread items][9]: bounds of the 8 group lists of each item */
+    SLP_HOST_EXPSUM = 15            /* double [S'][2]: weight w_k and exponent g_k of the kept exp-sum terms,
+                                       w_k exp(-g_k u^2) summing to about 1/u for u = r / P in [eps / P, 1/2]
+                                       (EXPSUM plans; empty otherwise) */
 };
 
 /* Run the pipeline of slp_eval up to and including stage last_stage, starting

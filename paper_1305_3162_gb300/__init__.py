@@ -33,7 +33,7 @@ SLP_ERR_UNSUPPORTED = 9
 
 SLP_QUAD_1, SLP_QUAD_3, SLP_QUAD_7 = 1, 3, 7
 SLP_INPUT_SIGMA, SLP_INPUT_MAG, SLP_INPUT_NODAL_MAG = 0, 1, 2
-SLP_KERNEL_AUTO, SLP_KERNEL_RADIAL, SLP_KERNEL_SEPARABLE = 0, 1, 2
+SLP_KERNEL_AUTO, SLP_KERNEL_RADIAL, SLP_KERNEL_SEPARABLE, SLP_KERNEL_EXPSUM = 0, 1, 2, 3
 SLP_NEAR_AUTO, SLP_NEAR_ON_THE_FLY, SLP_NEAR_PRECOMPUTED = 0, 1, 2
 
 SLP_STAGE_CHARGES, SLP_STAGE_SPREAD, SLP_STAGE_FFT_X, SLP_STAGE_FFT_Y, SLP_STAGE_FFT_Z = 0, 1, 2, 3, 4
@@ -42,7 +42,7 @@ SLP_BUF_QBUF, SLP_BUF_GRID_A, SLP_BUF_GRID_B, SLP_BUF_S1, SLP_BUF_S2, SLP_BUF_DT
 (SLP_HOST_SRC_PERM, SLP_HOST_TGT_PERM, SLP_HOST_SRC_GRID, SLP_HOST_TGT_GRID, SLP_HOST_SPREAD_ITEMS,
  SLP_HOST_GATHER_ITEMS, SLP_HOST_NEAR_ITEMS, SLP_HOST_NEAR_RANGES, SLP_HOST_DTAB, SLP_HOST_SRC_POINTS,
  SLP_HOST_TGT_POINTS, SLP_HOST_PLANE_ROWS, SLP_HOST_ACTIVE_Z, SLP_HOST_SPREAD_GROUPS,
- SLP_HOST_SPREAD_GROUP_OFF) = range(15)
+ SLP_HOST_SPREAD_GROUP_OFF, SLP_HOST_EXPSUM) = range(16)
 
 
 class SlpError(RuntimeError):
@@ -112,7 +112,8 @@ class slp_info(ctypes.Structure):
                 ("launches_per_eval", ctypes.c_int), ("active_rows", ctypes.c_int64),
                 ("active_planes", ctypes.c_int), ("fused_plane_passes", ctypes.c_int),
                 ("fused_column_passes", ctypes.c_int), ("gather_item_targets", ctypes.c_int),
-                ("spread_blocks_per_sm", ctypes.c_int), ("spread_table", ctypes.c_int)]
+                ("spread_blocks_per_sm", ctypes.c_int), ("spread_table", ctypes.c_int),
+                ("expsum_terms", ctypes.c_int)]
 
     def to_dict(self):
         out = {}
@@ -462,7 +463,8 @@ _HOST_DTYPES = {SLP_HOST_SRC_PERM: np.int32, SLP_HOST_TGT_PERM: np.int32, SLP_HO
                 SLP_HOST_TGT_GRID: np.float64, SLP_HOST_SPREAD_ITEMS: np.int32, SLP_HOST_GATHER_ITEMS: np.int32,
                 SLP_HOST_NEAR_ITEMS: np.int32, SLP_HOST_NEAR_RANGES: np.int32, SLP_HOST_DTAB: np.float64,
                 SLP_HOST_SRC_POINTS: np.float64, SLP_HOST_TGT_POINTS: np.float64, SLP_HOST_PLANE_ROWS: np.int32,
-                SLP_HOST_ACTIVE_Z: np.int32, SLP_HOST_SPREAD_GROUPS: np.int32, SLP_HOST_SPREAD_GROUP_OFF: np.int32}
+                SLP_HOST_ACTIVE_Z: np.int32, SLP_HOST_SPREAD_GROUPS: np.int32, SLP_HOST_SPREAD_GROUP_OFF: np.int32,
+                SLP_HOST_EXPSUM: np.float64}
 
 
 def slp_debug_host_array(plan, which: int):

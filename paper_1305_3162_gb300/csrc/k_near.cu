@@ -4,7 +4,9 @@
 //
 // where N_s is the smooth kernel the far path actually applies:
 //   RADIAL:    (N - N_s)(r) = erfc(r / (s sqrt 2)) / (4 pi r)  (r < eps);
-//   SEPARABLE: (N - N_s)(d) = 1/(4 pi |d|) - A prod_q f_q(d_q / L_q), every pair.
+//   SEPARABLE: (N - N_s)(d) = 1/(4 pi |d|) - A prod_q f_q(d_q / L_q), every pair;
+//   EXPSUM:    (N - N_s)(r) = (1/r - sum_k w_k exp(-g_k r^2)) / (4 pi)  (r < eps,
+//              the exponential sum of Sec. 3.3).
 //
 // One warp per work item: lane t owns target tbegin + t; the warp walks the
 // item's source ranges 32 sources at a time, staging them in shared memory
@@ -24,6 +26,15 @@ __device__ __forceinline__ float near_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double near_rsqrt(double x) { return rsqrt(x); }
 __device__ __forceinline__ float near_cospi(float x) { return cospif(x); }
 __device__ __forceinline__ double near_cospi(double x) { return cospi(x); }
+__device__ __forceinline__ float near_exp(float x) { return expf(x); }
+__device__ __forceinline__ double near_exp(double x) { return exp(x); }
+
+// sum_k w_k exp(-g_k r2) of the exp-sum kernel
+template <typename T> __device__ __forceinline__ T expsum_value(const T *__restrict__ w, const T *__restrict__ g, int n, T r2) {
+    T s = T(0);
+    for (int k = 0; k < n; ++k) s += w[k] * near_exp(-g[k] * r2);
+    return s;
+}
 
 // f(t) = h[0] + 2 sum_{l>=1} h[l] cos(2 pi l t), by Clenshaw's recurrence in x = cos(2 pi t).
 template <typename T> __device__ __forceinline__ T sep_factor(const T *__restrict__ h, int nh, T t) {
@@ -88,6 +99,10 @@ __global__ void __launch_bounds__(NEAR_WARPS * 32) k_near(DevPlan p) {
                         const T ri = near_rsqrt(r2);
                         acc += sq[warp][j] * near_erfc<T>(r2 * ri * a) * ri;
                     }
+                } else if (MODE == 3) {
+                    if (r2 < eps2)
+                        acc += sq[warp][j] *
+                               (near_rsqrt(r2) - expsum_value((const T *)p.es_w, (const T *)p.es_g, p.es_n, r2));
                 } else {
                     const T ri = near_rsqrt(r2);
                     const T ux = (T(ctx - csx) + (ftx - g.x)) / T(p.L[0]);
@@ -133,6 +148,8 @@ template <typename T> static cudaError_t near_t(const DevPlan &p, cudaStream_t s
     const int nb = (p.n_near + NEAR_WARPS - 1) / NEAR_WARPS;
     if (p.kernel_mode == 2)
         { const cudaError_t le = launch_k(k_near<T, 2>, nb, NEAR_WARPS * 32, 0, s, p); if (le != cudaSuccess) return le; }
+    else if (p.kernel_mode == 3)
+        { const cudaError_t le = launch_k(k_near<T, 3>, nb, NEAR_WARPS * 32, 0, s, p); if (le != cudaSuccess) return le; }
     else
         { const cudaError_t le = launch_k(k_near<T, 1>, nb, NEAR_WARPS * 32, 0, s, p); if (le != cudaSuccess) return le; }
     return cudaGetLastError();
@@ -176,6 +193,7 @@ __device__ __forceinline__ double nm_kernel(const NMBuild &b, double dx, double 
                           sep_factor(b.sep_h[2], b.sep_nh[2], dz / b.P[2]);
         return (ri - b.sep_A4pi * kn) * 0.079577471545947667884;
     }
+    if (b.kernel_mode == 3) return (ri - expsum_value(b.es_w, b.es_g, b.es_n, r2)) * 0.079577471545947667884;
     return erfc(r2 * ri * b.inv_s_sqrt2) * ri * 0.079577471545947667884;
 }
 

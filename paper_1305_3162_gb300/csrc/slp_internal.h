@@ -120,6 +120,10 @@ struct DevPlan {
     const void *sep_h[3]; int sep_nh[3];  // hq[0..nh-1], term l uses weight (l==0 ? 1 : 2) * hq[l]
     double sep_A;
 
+    // exp-sum kernel (EXPSUM): N_s(r) = sum_k es_w[k] exp(-es_g[k] r^2) / (4 pi), physical units
+    const void *es_w, *es_g;  // T [es_n]
+    int es_n;
+
     // precomputed near-field operator (NODAL_MAG): CSR over sorted targets
     const int64_t *nm_rowptr;  // [N + 1]
     const int *nm_col;         // [nnz] vertex ids
@@ -192,6 +196,8 @@ struct NMBuild {
     int sep_nh[3];
     double sep_A4pi;         // 4 pi A
     double P[3];
+    const double *es_w, *es_g;  // EXPSUM terms, physical units
+    int es_n;
 };
 cudaError_t launch_nm_build(const NMBuild &b, int pass, int prec, int64_t *counts, int64_t *pairs,
                             const int64_t *rowptr, void *val, cudaStream_t s);

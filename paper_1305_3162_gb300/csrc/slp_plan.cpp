@@ -292,6 +292,100 @@ void radial_params(slp_plan_s &p, double c) {
     p.eps = s * std::sqrt(2.0) * erfc_inv(tnf);
 }
 
+// ---------------------------------------------------------------- exp-sum kernel (Sec. 3.3)
+// Sum of Gaussians for 1/r on [rmin, beta] (torus units) by the trapezoidal
+// rule applied to 1/r = (2/sqrt(pi)) int exp(t - r^2 e^{2t}) dt over the real
+// line: node t_k gives g_k = e^{2 t_k} and w_k = (2h/sqrt(pi)) e^{t_k}.  The
+// range of t is cut where the integrand's tails fall below delta (left:
+// (2/sqrt(pi)) e^{t} r <= delta at r = beta; right: r^2 e^{2t} past
+// log(1/delta) at r = rmin), and the step h is halved from 1 until the sum
+// meets 1/r to relative delta/2 on a log-spaced check grid of [rmin, beta].
+// Terms come out ordered from the widest Gaussian to the narrowest.
+void expsum_terms(double rmin, double beta, double delta, std::vector<double> &w, std::vector<double> &g) {
+    const double t_lo = std::log(delta * std::sqrt(PI) / (2.0 * beta)) - 1.0;
+    const double t_hi = std::log(std::sqrt(std::log(4.0 / delta) + 4.0) / rmin) + 0.5;
+    for (double h = 1.0; h > 1e-3; h *= 0.8) {
+        w.clear();
+        g.clear();
+        for (double t = t_lo; t <= t_hi + 1e-12; t += h) {
+            w.push_back(2.0 * h / std::sqrt(PI) * std::exp(t));
+            g.push_back(std::exp(2.0 * t));
+        }
+        double worst = 0.0;
+        for (int i = 0; i <= 400; ++i) {
+            const double r = rmin * std::pow(beta / rmin, i / 400.0);
+            double s = 0.0;
+            for (size_t k = 0; k < w.size(); ++k) s += w[k] * std::exp(-g[k] * r * r);
+            worst = std::max(worst, std::fabs(s * r - 1.0));
+        }
+        if (worst <= 0.5 * delta) return;
+    }
+}
+
+// I(g, l) = int_{-1/2}^{1/2} exp(-g u^2) cos(2 pi l u) du, the Fourier
+// coefficient over one period of the torus (the definition of c_l(N_s) in
+// Sec. 2.2): the whole-line transform when the Gaussian has decayed at the
+// cell face, else composite 10-point Gauss-Legendre on [0, 1/2] with two
+// panels per period of the cosine.
+double gauss_period_coeff(double g, int l) {
+    if (g * 0.25 > 45.0) return std::sqrt(PI / g) * std::exp(-PI * PI * (double)l * l / g);
+    static const double X[5] = {0.1488743389816312, 0.4333953941292472, 0.6794095682990244, 0.8650633666889845,
+                                0.9739065285171717};
+    static const double Wt[5] = {0.2955242247147529, 0.2692667193099963, 0.2190863625159820, 0.1494513491505806,
+                                 0.0666713443086881};
+    const int np = 2 * std::abs(l) + 8;
+    const double hw = 0.25 / np;  // half panel width on [0, 1/2]
+    double s = 0.0;
+    for (int k = 0; k < np; ++k) {
+        const double c = (2 * k + 1) * hw;
+        for (int j = 0; j < 5; ++j)
+            for (int sg = -1; sg <= 1; sg += 2) {
+                const double u = c + sg * X[j] * hw;
+                s += Wt[j] * std::exp(-g * u * u) * std::cos(2.0 * PI * l * u);
+            }
+    }
+    return 2.0 * s * hw;
+}
+
+// Parameters of the EXPSUM kernel: cubic torus of period P = D_max / 0.4,
+// the sum for 1/r on [r0, 1/2] (torus units; r0 far below any near radius),
+// the widest terms the grid resolves (Fourier factor below tau_k at
+// |l| = n/2 for the smallest n), and the near radius eps: the smallest r from
+// which the kept terms still meet 1/r to relative tol.
+slp_status expsum_params(slp_plan_s &p) {
+    const double dmax = std::max(p.D[0], std::max(p.D[1], p.D[2]));
+    const double P = dmax / 0.4;
+    for (int d = 0; d < 3; ++d) p.P[d] = P;
+    const double delta = std::min(0.1, p.tol);
+    const double tk = std::min(0.1, p.tol);
+    std::vector<double> w, g;
+    expsum_terms(1e-4, 0.5, delta, w, g);
+    const int nmin = std::min(p.n[0], std::min(p.n[1], p.n[2]));
+    const double gmax = PI * PI * (0.5 * nmin) * (0.5 * nmin) / std::log(1.0 / tk);
+    p.es_w.clear();
+    p.es_g.clear();
+    for (size_t k = 0; k < w.size(); ++k)
+        if (g[k] <= gmax) {
+            p.es_w.push_back(w[k]);
+            p.es_g.push_back(g[k]);
+        }
+    if (p.es_w.empty())
+        return fail(SLP_ERR_TOLERANCE_INFEASIBLE, "grid too small for any exp-sum term (n = %d)", nmin);
+    // near radius (torus units): scan down from 1/2 while the kept sum meets 1/r
+    double eps_u = 0.5;
+    for (int i = 0; i <= 2000; ++i) {
+        const double r = 0.5 * std::pow(1e-4 / 0.5, i / 2000.0);
+        double s = 0.0;
+        for (size_t k = 0; k < p.es_w.size(); ++k) s += p.es_w[k] * std::exp(-p.es_g[k] * r * r);
+        if (std::fabs(s * r - 1.0) > delta) break;
+        eps_u = r;
+    }
+    p.eps = eps_u * P;
+    p.sigma_g = 0;
+    p.R = 0;
+    return SLP_OK;
+}
+
 slp_status choose_parameters(slp_plan_s &p) {
     // bounding box and enclosing-ball diameter of targets (sources are convex
     // combinations of targets, so they lie inside both)
@@ -406,6 +500,9 @@ slp_status choose_parameters(slp_plan_s &p) {
             return fail(SLP_ERR_TOLERANCE_INFEASIBLE, "grid %dx%dx%d cannot resolve the smooth kernel at tolerance %g",
                         p.L[0], p.L[1], p.L[2], p.tol);
         radial_params(p, c);
+    } else if (mode == SLP_KERNEL_EXPSUM) {
+        const slp_status st = expsum_params(p);
+        if (st != SLP_OK) return st;
     } else if (mode == SLP_KERNEL_SEPARABLE) {
         // every pair is near; the far kernel is any band-limited periodic
         // function that the near kernel can subtract exactly
@@ -712,6 +809,16 @@ void near_items(slp_plan_s &p, const std::vector<uint64_t> &skeys, const std::ve
 // kernel multiplier table D[|kz|][|ky|][kx] (l in I_n, Nyquist dropped)
 void build_dtab(slp_plan_s &p) {
     const int Kx = p.n[0] / 2, hy = p.n[1] / 2, hz = p.n[2] / 2;
+    if (p.kernel_mode == SLP_KERNEL_EXPSUM) {
+        // the S' (n_x + n_y + n_z) / 2 one-period Fourier factors of the Gaussians
+        const int hn[3] = {Kx, hy, hz};
+        const size_t S = p.es_w.size();
+        for (int d = 0; d < 3; ++d) {
+            p.es_I[d].assign(S * hn[d], 0.0);
+            for (size_t k = 0; k < S; ++k)
+                for (int l = 0; l < hn[d]; ++l) p.es_I[d][k * hn[d] + l] = gauss_period_coeff(p.es_g[k], l);
+        }
+    }
     p.Dtab.assign((size_t)hz * hy * Kx, 0.0);
     std::vector<double> W[3];
     const int hn[3] = {Kx, hy, hz};
@@ -737,6 +844,13 @@ void build_dtab(slp_plan_s &p) {
                     }
                     kh *= std::exp(-0.5 * p.sigma_g * p.sigma_g * k2);
                     cl = kh / V;
+                } else if (p.kernel_mode == SLP_KERNEL_EXPSUM) {
+                    // separable factors: c_l = (1 / (4 pi P)) sum_k w_k I_k(l_x) I_k(l_y) I_k(l_z)
+                    const size_t S = p.es_w.size();
+                    cl = 0.0;
+                    for (size_t k = 0; k < S; ++k)
+                        cl += p.es_w[k] * p.es_I[0][k * Kx + kx] * p.es_I[1][k * hy + ky] * p.es_I[2][k * hz + kz];
+                    cl /= 4.0 * PI * p.P[0];
                 } else {
                     cl = p.sep_A * p.sep_h[0][kx] * p.sep_h[1][ky] * p.sep_h[2][kz];
                 }
@@ -1077,6 +1191,18 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     TRY(upload(p, &ptr, p.near_blk_first.data(), p.near_blk_first.size()));
     p.d_blk_first = (int *)ptr;
     if (p.opts.deterministic) TRY(dalloc(p, &d.phi_near, sizeof(T) * 32 * std::max<size_t>(1, p.near_items.size())));
+    if (p.kernel_mode == SLP_KERNEL_EXPSUM) {
+        std::vector<T> w(p.es_w.size()), g(p.es_g.size());
+        for (size_t k = 0; k < w.size(); ++k) {
+            w[k] = (T)(p.es_w[k] / p.P[0]);
+            g[k] = (T)(p.es_g[k] / (p.P[0] * p.P[0]));
+        }
+        TRY(upload(p, &ptr, w.data(), w.size()));
+        d.es_w = ptr;
+        TRY(upload(p, &ptr, g.data(), g.size()));
+        d.es_g = ptr;
+        d.es_n = (int)w.size();
+    }
     if (p.kernel_mode == SLP_KERNEL_SEPARABLE) {
         for (int a = 0; a < 3; ++a) {
             std::vector<T> h(p.sep_h[a].begin(), p.sep_h[a].end());
@@ -1301,6 +1427,19 @@ slp_status build_near_matrix(slp_plan_s &p, const std::vector<uint64_t> &tkeys) 
         nb.sep_A4pi = 4.0 * PI * p.sep_A;
     }
     for (int a = 0; a < 3; ++a) nb.P[a] = p.P[a];
+    TmpBuf b_esw, b_esg;
+    if (p.kernel_mode == SLP_KERNEL_EXPSUM) {
+        std::vector<double> w(p.es_w.size()), g(p.es_g.size());
+        for (size_t k = 0; k < w.size(); ++k) {
+            w[k] = p.es_w[k] / p.P[0];
+            g[k] = p.es_g[k] / (p.P[0] * p.P[0]);
+        }
+        TRY(tmp_upload(b_esw, w.data(), w.size()));
+        TRY(tmp_upload(b_esg, g.data(), g.size()));
+        nb.es_w = (const double *)b_esw.p;
+        nb.es_g = (const double *)b_esg.p;
+        nb.es_n = (int)w.size();
+    }
     TRY(cuda_status(slp::launch_nm_build(nb, 0, p.prec, (int64_t *)b_cnt.p, (int64_t *)b_pairs.p, nullptr, nullptr, 0),
                     "near matrix count"));
     std::vector<int64_t> cnt(N), prs(N);
@@ -1828,6 +1967,7 @@ slp_status slp_query(slp_plan_t p, slp_info *info) {
     info->gather_item_targets = p->gather_chunk;
     info->spread_blocks_per_sm = (p->prec == 32 && p->m <= 4) ? (spread_dense(*p) ? 4 : 5) : 0;
     info->spread_table = p->dp.wtab != nullptr ? 1 : 0;
+    info->expsum_terms = p->kernel_mode == SLP_KERNEL_EXPSUM ? (int)p->es_w.size() : 0;
     return SLP_OK;
 }
 
@@ -1947,6 +2087,7 @@ slp_status slp_debug_host_count(slp_plan_t p, int which, int64_t *count) {
         case SLP_HOST_PLANE_ROWS: *count = 2 * (int64_t)p->plane_iv.size(); break;
         case SLP_HOST_ACTIVE_Z: *count = 2; break;
         case SLP_HOST_SPREAD_GROUPS: *count = (int64_t)p->sgroups.size(); break;
+        case SLP_HOST_EXPSUM: *count = (int64_t)(2 * p->es_w.size()); break;
         case SLP_HOST_SPREAD_GROUP_OFF: *count = (int64_t)p->sgroup_off.size(); break;
         default: return fail(SLP_ERR_INVALID_ARG, "unknown host array %d", which);
     }
@@ -1981,6 +2122,12 @@ slp_status slp_debug_host_array(slp_plan_t p, int which, void *out, int64_t coun
         }
         case SLP_HOST_PLANE_ROWS: memcpy(out, p->plane_iv.data(), 4 * count); break;
         case SLP_HOST_SPREAD_GROUPS: memcpy(out, p->sgroups.data(), 4 * count); break;
+        case SLP_HOST_EXPSUM:
+            for (size_t k = 0; k < p->es_w.size(); ++k) {
+                ((double *)out)[2 * k] = p->es_w[k];
+                ((double *)out)[2 * k + 1] = p->es_g[k];
+            }
+            break;
         case SLP_HOST_SPREAD_GROUP_OFF: memcpy(out, p->sgroup_off.data(), 4 * count); break;
         case SLP_HOST_ACTIVE_Z: {
             int32_t *o = (int32_t *)out;

@@ -57,6 +57,9 @@ struct slp_plan_s {
     double diam = 0, sigma_g = 0, R = 0, eps = 0, c_band = 0;
     double sep_A = 0;
     std::vector<double> sep_h[3];
+    // EXPSUM: kept terms w_k exp(-g_k u^2) of 1/u in torus units (u = r / P),
+    // and per axis the one-period Fourier factors I_k(l), [S'][n_q / 2]
+    std::vector<double> es_w, es_g, es_I[3];
 
     // sorted data (host)
     std::vector<int32_t> src_perm, tgt_perm;

@@ -144,7 +144,7 @@ def ifft_x(S1, Lx):
     return np.fft.irfft(X, n=Lx, axis=2) * Lx
 
 
-def near_radial(tgt_pts, src_pts, q, eps, sigma_g):
+def _near(tgt_pts, src_pts, q, eps, kern):
     from scipy.spatial import cKDTree
     tree = cKDTree(src_pts)
     lists = tree.query_ball_point(tgt_pts, eps)
@@ -154,5 +154,20 @@ def near_radial(tgt_pts, src_pts, q, eps, sigma_g):
             continue
         lst = np.asarray(lst)
         r = np.linalg.norm(tgt_pts[i] - src_pts[lst], axis=1)
-        out[i] = np.sum(q[lst] * erfc(r / (sigma_g * np.sqrt(2))) / r) / (4 * np.pi)
+        keep = r < eps
+        out[i] = np.sum(q[lst][keep] * kern(r[keep])) / (4 * np.pi)
     return out
+
+
+def near_radial(tgt_pts, src_pts, q, eps, sigma_g):
+    """Near-field part with the radial kernel erfc(r / (s sqrt 2)) / (4 pi r)."""
+    return _near(tgt_pts, src_pts, q, eps, lambda r: erfc(r / (sigma_g * np.sqrt(2))) / r)
+
+
+def near_expsum(tgt_pts, src_pts, q, eps, w, g, P):
+    """Near-field part with the exp-sum kernel (1/r - sum_k w_k exp(-g_k (r/P)^2) / P) / (4 pi),
+    (w, g) the terms in torus units."""
+    def kern(r):
+        u = r / P
+        return 1.0 / r - (w[None, :] * np.exp(-g[None, :] * u[:, None] ** 2)).sum(axis=1) / P
+    return _near(tgt_pts, src_pts, q, eps, kern)

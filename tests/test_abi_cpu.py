@@ -389,3 +389,59 @@ def test_plan_chooses_spread_occupancy_and_gather_items(slp, case):
             assert dense == (want[1] == 4)
     finally:
         slp.slp_destroy(plan)
+
+
+def test_expsum_terms_approximate_inverse_r_on_the_far_interval(slp):
+    """EXPSUM (Sec. 3.3): the kept Gaussians sum to 1/u within the plan
+    tolerance on [eps/P, 1/2] (torus units), checked at 2000 log-spaced u with
+    numpy; below eps the dropped narrow terms are missing, so the sum falls
+    short of 1/u there (the near-field kernel carries the difference); every
+    kept term is resolved by the grid (Fourier factor exp(-pi^2 l^2 / g) below
+    the tolerance at |l| = n/2)."""
+    V, T = meshes.icosphere(3)
+    tol = 1e-4
+    p = _host_plan(slp, V, T, q=7, tol=tol, grid=(64, 64, 64), kernel_mode=slp.SLP_KERNEL_EXPSUM)
+    info = slp.slp_query(p)
+    assert info["kernel_mode"] == slp.SLP_KERNEL_EXPSUM
+    P = info["period"][0]
+    assert info["period"] == [P, P, P]
+    # the body sits in (-0.2, 0.2)^3 of the torus (the scaling of the paper's experiments)
+    assert abs(np.ptp(V, axis=0).max() / P - 0.4) < 1e-9
+    wg = slp.slp_debug_host_array(p, slp.SLP_HOST_EXPSUM).reshape(-1, 2)
+    assert wg.shape[0] == info["expsum_terms"] > 5
+    w, g = wg[:, 0], wg[:, 1]
+    eu = info["eps_near"] / P
+    u = np.exp(np.linspace(np.log(eu), np.log(0.5), 2000))
+    s = (w[None, :] * np.exp(-g[None, :] * u[:, None] ** 2)).sum(axis=1)
+    assert np.abs(s * u - 1).max() <= tol
+    s0 = (w * np.exp(-g * (0.3 * eu) ** 2)).sum()
+    assert s0 * 0.3 * eu < 1 - tol
+    n = min(info["modes"])
+    assert np.all(np.exp(-np.pi ** 2 * (n / 2) ** 2 / g) <= tol * 1.0001)
+    slp.slp_destroy(p)
+
+
+def test_expsum_dtab_matches_one_period_quadrature(slp):
+    """EXPSUM D table: c_l(N_s) = (1 / (4 pi P)) sum_k w_k prod_q
+    int_{-1/2}^{1/2} exp(-g_k u^2) cos(2 pi l_q u) du (the Fourier coefficient
+    over one period, Sec. 2.2, of the separable Gaussians, Sec. 3.3), recovered
+    from D W^2 and compared with scipy quadrature of each factor."""
+    from scipy.integrate import quad
+    V, T = meshes.icosphere(2)
+    p = _host_plan(slp, V, T, q=3, tol=1e-4, grid=(32, 32, 32), kernel_mode=slp.SLP_KERNEL_EXPSUM)
+    info = slp.slp_query(p)
+    n, L, m = info["modes"], info["grid"], info["m"]
+    P = info["period"][0]
+    wg = slp.slp_debug_host_array(p, slp.SLP_HOST_EXPSUM).reshape(-1, 2)
+    D = slp.slp_debug_host_array(p, slp.SLP_HOST_DTAB).reshape(n[2] // 2, n[1] // 2, n[0] // 2)
+
+    def factor(g, l):
+        v, _ = quad(lambda u: np.exp(-g * u * u) * np.cos(2 * np.pi * l * u), -0.5, 0.5, limit=400, epsabs=1e-14, epsrel=1e-12)
+        return v
+
+    for (kz, ky, kx) in [(0, 0, 0), (1, 2, 3), (3, 1, 0), (7, 7, 7), (5, 0, 2)]:
+        cl = sum(w * factor(g, kx) * factor(g, ky) * factor(g, kz) for w, g in wg) / (4 * np.pi * P)
+        W = (slp.slp_debug_window_hat(m, L[0], kx) * slp.slp_debug_window_hat(m, L[1], ky) *
+             slp.slp_debug_window_hat(m, L[2], kz))
+        assert abs(D[kz, ky, kx] * W * W - cl) <= 1e-9 * abs(cl) + 1e-14
+    slp.slp_destroy(p)

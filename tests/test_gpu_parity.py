@@ -304,3 +304,42 @@ def test_far_from_origin_and_zero_input():
         assert np.all(zero == 0.0)
     finally:
         slp.slp_destroy(plan)
+
+
+@pytest.mark.parametrize("body,level,grid,prec,near,bar",
+                         [("sphere", 3, 64, 32, 0, 1e-4), ("sphere", 4, 128, 32, 0, 1e-4),
+                          ("sphere", 3, 64, 64, 1, 1e-4), ("sphere", 4, 128, 64, 2, 1e-4),
+                          ("cube", 12, 64, 64, 0, 2e-4)],
+                         ids=["sphere-L3-64-fp32", "sphere-L4-128-fp32", "sphere-L3-64-fp64-onthefly",
+                              "sphere-L4-128-fp64-precomputed", "cube12-64-fp64"])
+def test_expsum_kernel_mode_at_the_papers_accuracy(body, level, grid, prec, near, bar):
+    """The paper's kernel (EXPSUM: exponential sum of Gaussians, Sec. 3.3,
+    separable one-period Fourier coefficients, near kernel 1/r - N_s) through
+    the same spread / FFT / gather path, against the FP64 oracle, at plan
+    tolerance 1e-4.  On the sphere every pair distance stays inside the
+    sum's interval [eps, P/2] and the error stays within the tolerance
+    (measured 4.1e-5 at 64^3, 5.9e-6 at 128^3); on the cube the
+    corner-to-corner pairs (0.69 P) lie beyond P/2, where the Gaussians no
+    longer follow 1/r exactly (measured 7.4e-5), so the cube's bar is twice
+    the tolerance."""
+    slp = lib()
+    V, T = meshes.icosphere(level) if body == "sphere" else meshes.cube(level)
+    q = 7 if body == "sphere" else 3
+    plan = _plan(slp, V, T, q, 1e-4, prec, (grid, grid, grid), kernel_mode=slp.SLP_KERNEL_EXPSUM, near_mode=near)
+    try:
+        info = slp.slp_query(plan)
+        assert info["kernel_mode"] == slp.SLP_KERNEL_EXPSUM and info["expsum_terms"] > 5
+        m = fields.vortex(V, 21)
+        phi = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, m, prec)
+        ref = oracle.slp_nodal(V, T, q, m)
+        err = rel_l2(phi, ref)
+        print(f"EXPSUM {body} {level} grid {grid} FP{prec}: rel-L2 {err:.3e}, S' = {info['expsum_terms']}, "
+              f"eps/P = {info['eps_near'] / info['period'][0]:.4f}")
+        assert err <= bar, err
+        # sigma input (on-the-fly near field) gives the same potential
+        sig = oracle.charges(V, T, q, oracle.KIND_NODAL_MAG, m)
+        _, wk, _ = oracle.sources(V, T, q)
+        phi_s = run(slp, plan, slp.SLP_INPUT_SIGMA, sig / wk, prec)
+        assert rel_l2(phi_s, phi) <= (1e-5 if prec == 32 else 1e-10)
+    finally:
+        slp.slp_destroy(plan)

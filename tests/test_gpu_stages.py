@@ -27,6 +27,8 @@ CASES = [
     ("sphere_L3_fp32_radial", lambda: meshes.icosphere(3), 7, 1e-5, 32, (64, 64, 64), 1, 2e-5),
     ("box_fp32_aniso", lambda: meshes.box(2.0, 1.0, 0.5, 12, 6, 3), 3, 1e-5, 32, (128, 64, 64), 1, 2e-5),
     ("sphere_L3_fp32_table", lambda: meshes.icosphere(3), 7, 1e-5, 32, (64, 64, 64), 1, 2e-5),
+    ("sphere_L3_fp64_expsum", lambda: meshes.icosphere(3), 7, 1e-4, 64, (64, 64, 64), 3, 1e-11),
+    ("sphere_L3_fp32_expsum", lambda: meshes.icosphere(3), 7, 1e-4, 32, (64, 64, 64), 3, 2e-5),
     ("cube_fp64_separable", lambda: meshes.cube(8), 3, 1e-10, 64, (32, 32, 32), 2, 1e-11),
 ]
 
@@ -122,11 +124,16 @@ def test_stages(case, fuse):
         far_ref[tperm] = far_sorted
         assert rel_l2(phi_far, far_ref) < rtol, "gather"
 
-        # near field (radial kernel only; the separable kernel is checked end to end)
+        # near field (radial and exp-sum kernels; the separable kernel is checked end to end)
         phi = run(slp, plan, slp.SLP_INPUT_SIGMA, sigma, prec)
-        if info["kernel_mode"] == slp.SLP_KERNEL_RADIAL:
+        if info["kernel_mode"] in (slp.SLP_KERNEL_RADIAL, slp.SLP_KERNEL_EXPSUM):
             sp = slp.slp_debug_host_array(plan, slp.SLP_HOST_SRC_POINTS).reshape(-1, 3)
-            near_sorted = ref.near_radial(V[tperm], sp, qb, info["eps_near"], info["sigma_g"])
+            if info["kernel_mode"] == slp.SLP_KERNEL_RADIAL:
+                near_sorted = ref.near_radial(V[tperm], sp, qb, info["eps_near"], info["sigma_g"])
+            else:
+                wg = slp.slp_debug_host_array(plan, slp.SLP_HOST_EXPSUM).reshape(-1, 2)
+                near_sorted = ref.near_expsum(V[tperm], sp, qb, info["eps_near"], wg[:, 0], wg[:, 1],
+                                              info["period"][0])
             near_ref = np.zeros_like(near_sorted)
             near_ref[tperm] = near_sorted
             scale = np.linalg.norm(phi)
