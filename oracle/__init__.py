@@ -10,7 +10,9 @@ arrays.  See that file's header for the definition and the citations.
 
 Parity status: every function here is pinned by tests/test_oracle_pins.py
 (quadrature exactness, closed-form sphere potentials, the analytic triangle
-integral, invariances).
+integral against a Duffy-transformed Gauss-Legendre rule, invariances; the
+triangle-integrated definition by the same sphere closed forms, converging
+faster than the point rules).
 """
 from __future__ import annotations
 
@@ -58,7 +60,12 @@ def _load():
             lib.slpo_charges.argtypes = [ctypes.c_int, d, I64, i32, I64, ctypes.c_int, d, d]
             lib.slpo_direct.argtypes = [d, I64, d, d, I64, d, ctypes.c_int]
             lib.slpo_direct_subset.argtypes = [d, i64p, I64, d, d, I64, d, ctypes.c_int]
-            for f in (lib.slpo_rule, lib.slpo_sources, lib.slpo_charges, lib.slpo_direct, lib.slpo_direct_subset):
+            lib.slpo_triangle_integral.argtypes = [d, d, d, d]
+            lib.slpo_triangle_integral.restype = ctypes.c_double
+            lib.slpo_element_charges.argtypes = [d, I64, i32, I64, d, d]
+            lib.slpo_direct_p0.argtypes = [d, i64p, I64, d, I64, i32, I64, d, d, ctypes.c_int]
+            for f in (lib.slpo_rule, lib.slpo_sources, lib.slpo_charges, lib.slpo_direct, lib.slpo_direct_subset,
+                      lib.slpo_element_charges, lib.slpo_direct_p0):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -145,3 +152,39 @@ def slp(V, T, q: int, kind: int, data, nthreads: int = 0):
 def slp_nodal(V, T, q: int, m_nodal, nthreads: int = 0):
     """Convenience: nodal magnetisation input (P1 interpolation, sigma = m.n)."""
     return slp(V, T, q, KIND_NODAL_MAG, m_nodal, nthreads)
+
+
+# ---------------------------------------------------------------- triangle-integrated (P0) definition
+def triangle_integral(v0, v1, v2, x):
+    """int over the flat triangle (v0, v1, v2) of 1/|x - y| dA(y) (closed form)."""
+    a = [_f64(np.asarray(p, dtype=np.float64).reshape(3)) for p in (v0, v1, v2, x)]
+    return float(_load().slpo_triangle_integral(*[_p(v) for v in a]))
+
+
+def element_charges(V, T, m_nodal):
+    """g_j: integral mean of m . n_j over triangle j for P1 nodal m."""
+    V = _f64(V)
+    T = _i32(T)
+    m = _f64(m_nodal)
+    g = np.zeros(T.shape[0])
+    rc = _load().slpo_element_charges(_p(V), V.shape[0], _p(T, ctypes.c_int32), T.shape[0], _p(m), _p(g))
+    if rc != 0:
+        raise ValueError(f"slpo_element_charges failed ({rc})")
+    return g
+
+
+def slp_p0(V, T, g, sel=None, nthreads: int = 0):
+    """phi_i = (1/4pi) sum_j g_j int_{S_j} 1/|x_i - y| dA(y) at the vertices
+    (or at V[sel]), every triangle integrated exactly.  Returns phi."""
+    V = _f64(V)
+    T = _i32(T)
+    g = _f64(g)
+    if sel is None:
+        ns, sp = V.shape[0], None
+    else:
+        sel = np.ascontiguousarray(sel, dtype=np.int64)
+        ns, sp = sel.shape[0], _p(sel, ctypes.c_int64)
+    phi = np.zeros(ns)
+    _load().slpo_direct_p0(_p(V), sp, ns, _p(V), V.shape[0], _p(T, ctypes.c_int32), T.shape[0], _p(g), _p(phi),
+                           int(nthreads))
+    return phi

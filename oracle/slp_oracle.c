@@ -23,6 +23,16 @@
  * Neumaier-compensated accumulation per target and OpenMP over targets.
  * No blocking, no splitting of the kernel, no approximation.
  *
+ * A second definition, for the triangle-integrated discretisation (paper
+ * Sec. 2.2, Eq. (slayer3) itself, no quadrature): element-wise constant
+ * charges g_j (the L2 projection of m . n onto constants per triangle,
+ * i.e. its integral mean) and exact triangle integrals,
+ *
+ *     phi_i = (1 / 4 pi) * sum_j g_j * int_{S_j} 1 / |x_i - y| dA(y),
+ *
+ * each integral by the edge-sum closed form for a uniformly charged flat
+ * polygon (Wilton et al. 1984; Graglia 1993), again over every pair.
+ *
  * Quadrature rules (the point order is part of the library contract: the
  * source index is k = j * q + s):
  *   q = 3: degree-2 rule with interior points, barycentric (2/3, 1/6, 1/6)
@@ -207,6 +217,118 @@ int slpo_direct_subset(const double *x, const int64_t *sel, int64_t ns, const do
         for (int64_t k = 0; k < nq; ++k) {
             const double d0 = xi0 - y[3 * k], d1 = xi1 - y[3 * k + 1], d2 = xi2 - y[3 * k + 2];
             const double v = qk[k] / sqrt(d0 * d0 + d1 * d1 + d2 * d2);
+            const double tt = sum + v;
+            if (fabs(sum) >= fabs(v))
+                comp += (sum - tt) + v;
+            else
+                comp += (v - tt) + sum;
+            sum = tt;
+        }
+        phi[t] = (sum + comp) / (4.0 * ORACLE_PI);
+    }
+    return used;
+}
+
+/* ---------------------------------------------------------------- triangle integrals
+ * int_{S} 1/|x - y| dA(y) over the flat triangle S = (v0, v1, v2).  With n the
+ * unit normal of the winding, h = (x - v0) . n the signed height of x over
+ * the plane and rho = x - h n its projection, and for each edge e from p- to
+ * p+ (counter-clockwise about n): l the unit edge direction, u = l x n the
+ * in-plane outward normal, l-/l+ = (p-/+ - rho) . l, P0 = (p- - rho) . u,
+ * R-/R+ = |x - p-/+| and R0^2 = P0^2 + h^2:
+ *
+ *   I = sum_e P0 ln((R+ + l+) / (R- + l-))
+ *       - |h| sum_e [atan(P0 l+ / (R0^2 + |h| R+)) - atan(P0 l- / (R0^2 + |h| R-))].
+ *
+ * An edge whose line passes through rho (P0 = 0) contributes nothing: its log
+ * term vanishes with P0, and so do its atan terms. */
+static void sub3(const double *a, const double *b, double *o) { o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2]; }
+static double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+static void cross3(const double *a, const double *b, double *o)
+{
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+double slpo_triangle_integral(const double *v0, const double *v1, const double *v2, const double *x)
+{
+    const double *v[3] = {v0, v1, v2};
+    double e1[3], e2[3], n[3], d[3];
+    sub3(v1, v0, e1);
+    sub3(v2, v0, e2);
+    cross3(e1, e2, n);
+    const double nn = sqrt(dot3(n, n));
+    if (!(nn > 0.0)) return 0.0;
+    n[0] /= nn; n[1] /= nn; n[2] /= nn;
+    sub3(x, v0, d);
+    const double h = dot3(d, n), ah = fabs(h);
+    const double rho[3] = {x[0] - h * n[0], x[1] - h * n[1], x[2] - h * n[2]};
+    double total = 0.0;
+    for (int e = 0; e < 3; ++e) {
+        const double *pm = v[e], *pp = v[(e + 1) % 3];
+        double L[3], l[3], u[3], am[3], ap[3], xm[3], xp[3];
+        sub3(pp, pm, L);
+        const double len = sqrt(dot3(L, L));
+        l[0] = L[0] / len; l[1] = L[1] / len; l[2] = L[2] / len;
+        cross3(l, n, u);
+        sub3(pm, rho, am);
+        sub3(pp, rho, ap);
+        const double lm = dot3(am, l), lp = dot3(ap, l), P0 = dot3(am, u);
+        sub3(x, pm, xm);
+        sub3(x, pp, xp);
+        const double Rm = sqrt(dot3(xm, xm)), Rp = sqrt(dot3(xp, xp));
+        const double R02 = P0 * P0 + h * h;
+        if (fabs(P0) > 1e-14 * len) total += P0 * log((Rp + lp) / (Rm + lm));
+        if (ah > 0.0) total -= ah * (atan(P0 * lp / (R02 + ah * Rp)) - atan(P0 * lm / (R02 + ah * Rm)));
+    }
+    return total;
+}
+
+/* Element charges: g_j = (1/|S_j|) int_{S_j} m . n_j dA for the nodal m
+ * interpolated linearly (P1) on the triangle, which is n_j . (m_a + m_b + m_c) / 3
+ * (the integral mean of a linear function is its value at the centroid). */
+int slpo_element_charges(const double *V, int64_t nv, const int32_t *T, int64_t nt, const double *m, double *g)
+{
+    for (int64_t j = 0; j < nt; ++j) {
+        const int32_t a = T[3 * j], b = T[3 * j + 1], c = T[3 * j + 2];
+        if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv) return 1;
+        double e1[3], e2[3], n[3];
+        sub3(V + 3 * (int64_t)b, V + 3 * (int64_t)a, e1);
+        sub3(V + 3 * (int64_t)c, V + 3 * (int64_t)a, e2);
+        cross3(e1, e2, n);
+        const double nn = sqrt(dot3(n, n));
+        if (!(nn > 0.0)) return 2;
+        double mc[3];
+        for (int k = 0; k < 3; ++k) mc[k] = (m[3 * (int64_t)a + k] + m[3 * (int64_t)b + k] + m[3 * (int64_t)c + k]) / 3.0;
+        g[j] = dot3(mc, n) / nn;
+    }
+    return 0;
+}
+
+/* phi_t = (1/4pi) sum_j g_j int_{S_j} 1/|x_{sel[t]} - y| dA(y) over every
+ * triangle, Neumaier summation, OpenMP over targets; sel == NULL takes every
+ * target (ns = nx).  Returns the thread count used. */
+int slpo_direct_p0(const double *x, const int64_t *sel, int64_t ns, const double *V, int64_t nv,
+                   const int32_t *T, int64_t nt, const double *g, double *phi, int nthreads)
+{
+    int used = 1;
+    (void)nv;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel
+    {
+#pragma omp single
+        used = omp_get_num_threads();
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int64_t t = 0; t < ns; ++t) {
+        const int64_t i = sel ? sel[t] : t;
+        double sum = 0.0, comp = 0.0;
+        for (int64_t j = 0; j < nt; ++j) {
+            const double v = g[j] * slpo_triangle_integral(V + 3 * (int64_t)T[3 * j], V + 3 * (int64_t)T[3 * j + 1],
+                                                           V + 3 * (int64_t)T[3 * j + 2], x + 3 * i);
             const double tt = sum + v;
             if (fabs(sum) >= fabs(v))
                 comp += (sum - tt) + v;

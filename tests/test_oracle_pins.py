@@ -303,3 +303,82 @@ def test_mesh_generators_closed_and_outward():
         rkey = e[:, 1] * (nv + 1) + e[:, 0]
         assert np.unique(key).size == key.size
         assert np.array_equal(np.sort(key), np.sort(rkey))
+
+
+# ---------------------------------------------------------------- triangle-integrated (P0) definition
+@pytest.mark.parametrize("x", [(0.2, 0.3, 0.5), (0.2, 0.3, 0.0), (1.5, -0.4, 0.05), (0.0, 0.0, 0.0),
+                               (0.5, 0.5, 0.0), (-3.0, 2.0, 1.0), (0.1, 0.1, -1e-6)])
+def test_oracle_triangle_integral_matches_duffy_and_python_closed_form(oracle_lib, x):
+    """The C closed form against the Duffy-transformed Gauss-Legendre rule
+    about the projection of x (Sec. 3.4), including x on the plane, at a
+    vertex and on an edge, and against the closed form written in Python."""
+    rng = np.random.default_rng(5)
+    for _ in range(4):
+        v0 = rng.normal(size=3) * 0.1
+        v1 = v0 + np.array([1.0, 0.1, 0.0]) + rng.normal(size=3) * 0.05
+        v2 = v0 + np.array([0.2, 0.9, 0.0]) + rng.normal(size=3) * 0.05
+        for xx in (np.asarray(x, float), v0, 0.5 * (v0 + v1)):
+            c = oracle_lib.triangle_integral(v0, v1, v2, xx)
+            assert abs(c - triangle_potential_closed_form(v0, v1, v2, xx)) <= 1e-13 * max(1.0, abs(c))
+            assert abs(c - triangle_potential_duffy(v0, v1, v2, xx, 200)) <= 1e-12 * max(1.0, abs(c))
+
+
+def test_oracle_triangle_integral_far_field_limit(oracle_lib):
+    """Far from the triangle, the integral tends to |S| / |x - c| (c the
+    centroid) with a relative correction of order (size / distance)^2."""
+    v0, v1, v2 = np.array([0.0, 0, 0]), np.array([1.0, 0, 0]), np.array([0.0, 1, 0])
+    area, c = 0.5, (v0 + v1 + v2) / 3
+    prev = None
+    for dist in (10.0, 20.0, 40.0, 80.0):
+        x = c + dist * np.array([0.3, 0.5, 0.81]) / np.linalg.norm([0.3, 0.5, 0.81])
+        err = abs(oracle_lib.triangle_integral(v0, v1, v2, x) * dist / area - 1.0)
+        assert err < 1.0 / dist ** 2
+        if prev is not None:
+            assert err < prev / 3.0
+        prev = err
+
+
+def test_oracle_element_charges_are_integral_means(oracle_lib):
+    """For a linear field m(x) = A x, the P1 interpolant is exact and the
+    integral mean of m . n over a triangle is n . A c (c the centroid)."""
+    V, T = meshes.icosphere(2)
+    A = np.array([[0.3, -1.0, 0.2], [0.5, 0.1, 0.7], [-0.4, 0.2, 1.1]])
+    g = oracle_lib.element_charges(V, T, V @ A.T)
+    c = V[T].mean(axis=1)
+    n = np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]])
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    assert np.abs(g - np.einsum("ij,ij->i", c @ A.T, n)).max() < 1e-14
+
+
+def test_oracle_p0_sphere_closed_forms_converge_at_second_order(oracle_lib):
+    """Exact triangle integrals of element-wise constant charges on the
+    icosphere: sigma = 1 gives phi = R and the uniformly magnetised sphere
+    (g_j = n_j . e_z) gives phi = z/3 (Sec. 4), up to the flat-facet
+    geometry error, which falls by about 4x per refinement (second order;
+    the point rules above converge at first order)."""
+    prev = None
+    for level in (2, 3, 4):
+        V, T = meshes.icosphere(level)
+        sel = np.arange(0, V.shape[0], max(1, V.shape[0] // 300))
+        e1 = np.abs(oracle_lib.slp_p0(V, T, np.ones(T.shape[0]), sel=sel) - 1.0).max()
+        gz = oracle_lib.element_charges(V, T, np.tile([0.0, 0.0, 1.0], (V.shape[0], 1)))
+        e2 = np.abs(oracle_lib.slp_p0(V, T, gz, sel=sel) - V[sel, 2] / 3).max()
+        assert e1 < 0.06 / 4 ** level and e2 < 0.03 / 4 ** level, (level, e1, e2)
+        if prev is not None:
+            assert e1 < prev[0] / 3.5 and e2 < prev[1] / 3.5
+        prev = (e1, e2)
+
+
+def test_oracle_p0_invariances_and_subset(oracle_lib):
+    """Linearity in g, translation invariance, phi(sX) = s phi(X) for the
+    same g, and the subset form equal to the full one."""
+    V, T = meshes.cube(4)
+    rng = np.random.default_rng(3)
+    g1, g2 = rng.uniform(-1, 1, T.shape[0]), rng.uniform(-1, 1, T.shape[0])
+    p1, p2 = oracle_lib.slp_p0(V, T, g1), oracle_lib.slp_p0(V, T, g2)
+    p12 = oracle_lib.slp_p0(V, T, 2.0 * g1 - 0.5 * g2)
+    assert _rel_l2(p12, 2.0 * p1 - 0.5 * p2) < 1e-13
+    assert _rel_l2(oracle_lib.slp_p0(V + np.array([3.0, -2.0, 7.0]), T, g1), p1) < 1e-12
+    assert _rel_l2(oracle_lib.slp_p0(2.5 * V, T, g1), 2.5 * p1) < 1e-13
+    sel = np.array([0, 5, 17, V.shape[0] - 1])
+    assert np.array_equal(oracle_lib.slp_p0(V, T, g1, sel=sel), p1[sel])
