@@ -62,8 +62,15 @@ enum { SLP_QUAD_1 = 1, SLP_QUAD_3 = 3, SLP_QUAD_7 = 7 };
  *   SIGMA:     sigma at the quadrature points, [Q] (Q = q * n_triangles);
  *   MAG:       m at the quadrature points, [Q][3]; sigma = m . n_j;
  *   NODAL_MAG: m at the mesh vertices, [N][3]; interpolated linearly on each
- *              triangle (P1, Sec. 2.1) to the points; sigma = m(y) . n_j. */
-enum { SLP_INPUT_SIGMA = 0, SLP_INPUT_MAG = 1, SLP_INPUT_NODAL_MAG = 2 };
+ *              triangle (P1, Sec. 2.1) to the points; sigma = m(y) . n_j;
+ *              in plans with opts.integration = 1 it is projected onto
+ *              element-wise constants instead: g_j = (1/|S_j|) int_{S_j} m . n_j
+ *              (the L2 projection of Sec. 2.2);
+ *   ELEMENT:   element-wise constant charge g_j per triangle, [n_triangles]
+ *              (plans with opts.integration = 1 only; SIGMA and MAG need the
+ *              quadrature points and are refused there with
+ *              SLP_ERR_UNSUPPORTED). */
+enum { SLP_INPUT_SIGMA = 0, SLP_INPUT_MAG = 1, SLP_INPUT_NODAL_MAG = 2, SLP_INPUT_ELEMENT = 3 };
 
 /* Smooth-kernel choice (the splitting N = (N - N_s) + N_s of Sec. 2.2):
  *   RADIAL:    N_s = (N truncated at radius R) convolved with an isotropic
@@ -130,12 +137,21 @@ typedef struct {
                              device, in kernels that read them anyway; a non-finite value sets the
                              plan's status word, which slp_check then reports as SLP_ERR_NONFINITE
                              (the evaluation still completes; nothing traps) */
+    int integration;      /* 0: point quadrature (the quadrature form of Sec. 3: sources at the rule's
+                             points, the oracle's definition); 1: triangle integrals (Sec. 2.2,
+                             Eq. (slayer3) with element-wise constant charges g_j): the gridding
+                             matrix A_rj = int_{S_j} Psi(r - y) dA of Sec. 3.1 assembled once per plan
+                             (8 x 8 Duffy-Gauss rule per triangle) and applied as a sparse product,
+                             and the near-field integrals of Sec. 3.4 computed exactly (closed form of
+                             the 1/r part, which covers the weakly singular case) and applied as a
+                             second sparse product.  Grids of at most 2^27 points and triangles up to
+                             24 - 2m grid cells across; otherwise SLP_ERR_UNSUPPORTED */
     int spread_table;     /* FP32 spread with m <= 4: 1 reads each source's window values from a
                              plan-time table (3 x 2m floats per source, 96 bytes at m = 4) instead of evaluating the window per group, 0 evaluates
                              them, -1 automatic (the table from 2^18 sources: measured faster there,
                              while on smaller meshes its extra traffic slows the concurrent
                              near-field product more than it saves) */
-    int reserved[3];
+    int reserved[2];
 } slp_plan_opts;
 
 typedef struct {
@@ -177,6 +193,9 @@ typedef struct {
                                     the other spread kernels */
     int spread_table;            /* 1: the spread reads plan-time window tables (opts.spread_table) */
     int expsum_terms;            /* EXPSUM: Gaussians kept in the smooth kernel (S'); 0 otherwise */
+    int integration;             /* opts.integration of the plan */
+    int64_t grid_matrix_nnz;     /* integration = 1: entries of the gridding matrix A */
+    int64_t near_tri_nnz;        /* integration = 1: (target, triangle) entries of the near-field matrix */
 } slp_info;
 
 /* Fill opts with defaults: precision 32, automatic grid/m/kernel/near mode,

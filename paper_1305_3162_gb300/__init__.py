@@ -32,7 +32,7 @@ SLP_ERR_NO_DEVICE = 8
 SLP_ERR_UNSUPPORTED = 9
 
 SLP_QUAD_1, SLP_QUAD_3, SLP_QUAD_7 = 1, 3, 7
-SLP_INPUT_SIGMA, SLP_INPUT_MAG, SLP_INPUT_NODAL_MAG = 0, 1, 2
+SLP_INPUT_SIGMA, SLP_INPUT_MAG, SLP_INPUT_NODAL_MAG, SLP_INPUT_ELEMENT = 0, 1, 2, 3
 SLP_KERNEL_AUTO, SLP_KERNEL_RADIAL, SLP_KERNEL_SEPARABLE, SLP_KERNEL_EXPSUM = 0, 1, 2, 3
 SLP_NEAR_AUTO, SLP_NEAR_ON_THE_FLY, SLP_NEAR_PRECOMPUTED = 0, 1, 2
 
@@ -62,7 +62,8 @@ class slp_plan_opts(ctypes.Structure):
                 ("kernel_mode", ctypes.c_int), ("near_mode", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("device", ctypes.c_int), ("allow_grid_raise", ctypes.c_int), ("check_mesh", ctypes.c_int),
                 ("fuse_plane_passes", ctypes.c_int), ("fuse_column_passes", ctypes.c_int),
-                ("check_finite", ctypes.c_int), ("spread_table", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("check_finite", ctypes.c_int), ("integration", ctypes.c_int), ("spread_table", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 SLP_TUNE_MAX = 8
@@ -113,7 +114,8 @@ class slp_info(ctypes.Structure):
                 ("active_planes", ctypes.c_int), ("fused_plane_passes", ctypes.c_int),
                 ("fused_column_passes", ctypes.c_int), ("gather_item_targets", ctypes.c_int),
                 ("spread_blocks_per_sm", ctypes.c_int), ("spread_table", ctypes.c_int),
-                ("expsum_terms", ctypes.c_int)]
+                ("expsum_terms", ctypes.c_int), ("integration", ctypes.c_int), ("grid_matrix_nnz", ctypes.c_int64),
+                ("near_tri_nnz", ctypes.c_int64)]
 
     def to_dict(self):
         out = {}
@@ -509,7 +511,7 @@ class Plan:
     def __init__(self, vertices, triangles, quadrature=7, tolerance=1e-5, precision=32, grid=None, m=0,
                  kernel_mode=SLP_KERNEL_AUTO, near_mode=SLP_NEAR_AUTO, deterministic=False, device=0,
                  allow_grid_raise=True, check_mesh=True, fuse_plane_passes=-1, fuse_column_passes=-1,
-                 spread_table=-1):
+                 spread_table=-1, integration=0):
         o = slp_default_opts()
         o.precision = int(precision)
         if grid is not None:
@@ -525,6 +527,7 @@ class Plan:
         o.fuse_plane_passes = int(fuse_plane_passes)
         o.fuse_column_passes = int(fuse_column_passes)
         o.spread_table = int(spread_table)
+        o.integration = int(integration)
         self.handle = slp_plan(vertices, triangles, quadrature, tolerance, o)
         self.info = slp_query(self.handle)
         self.n_targets = self.info["n_targets"]

@@ -55,7 +55,7 @@ slp_status slp_batch_create(int n_plans, const slp_plan_t *plans, int n_items, c
     *out = nullptr;
     if (n_plans < 1 || !plans || n_items < 1 || !plan_of || !d_in || !d_phi)
         return slp_fail(SLP_ERR_INVALID_ARG, "empty batch or NULL array");
-    if (input_kind < SLP_INPUT_SIGMA || input_kind > SLP_INPUT_NODAL_MAG)
+    if (input_kind < SLP_INPUT_SIGMA || input_kind > SLP_INPUT_ELEMENT)
         return slp_fail(SLP_ERR_INVALID_ARG, "unknown input kind %d", input_kind);
     if (lanes_per_plan < 1 || lanes_per_plan > 64) return slp_fail(SLP_ERR_INVALID_ARG, "lanes_per_plan must be 1..64");
     const int dev = plans[0] ? plans[0]->device : -1;
@@ -63,6 +63,8 @@ slp_status slp_batch_create(int n_plans, const slp_plan_t *plans, int n_items, c
         if (!plans[i]) return slp_fail(SLP_ERR_INVALID_ARG, "plan %d is NULL", i);
         if (plans[i]->device < 0) return slp_fail(SLP_ERR_NO_DEVICE, "plan %d is host-only", i);
         if (plans[i]->device != dev) return slp_fail(SLP_ERR_INVALID_ARG, "all plans of a batch must share a device");
+        const slp_status ks = slp_check_kind(*plans[i], input_kind);
+        if (ks != SLP_OK) return ks;
     }
     std::vector<std::vector<int>> items_of(n_plans);
     for (int i = 0; i < n_items; ++i) {
@@ -247,7 +249,7 @@ slp_status slp_eval_batched(int n, const slp_plan_t *plans, int input_kind, cons
                             void *const *d_phi, const int *n_states_each, void *stream) {
     if (n < 1 || !plans || !d_in || !d_phi || !n_states_each)
         return slp_fail(SLP_ERR_INVALID_ARG, "slp_eval_batched: empty batch or NULL array");
-    if (input_kind < SLP_INPUT_SIGMA || input_kind > SLP_INPUT_NODAL_MAG)
+    if (input_kind < SLP_INPUT_SIGMA || input_kind > SLP_INPUT_ELEMENT)
         return slp_fail(SLP_ERR_INVALID_ARG, "slp_eval_batched: unknown input kind %d", input_kind);
     BatchKey key;
     key.kind = input_kind;
@@ -282,8 +284,7 @@ slp_status slp_eval_batched(int n, const slp_plan_t *plans, int input_kind, cons
         int u = (int)(std::find(uplans.begin(), uplans.end(), plans[i]) - uplans.begin());
         if (u == (int)uplans.size()) uplans.push_back(plans[i]);
         const size_t es = p.prec == 64 ? 8 : 4;
-        const size_t in_bytes = es * (size_t)(input_kind == SLP_INPUT_SIGMA ? p.Q
-                                            : input_kind == SLP_INPUT_MAG ? 3 * p.Q : 3 * p.N);
+        const size_t in_bytes = es * (size_t)slp_input_count(p, input_kind);
         for (int k = 0; k < n_states_each[i]; ++k) {
             plan_of.push_back(u);
             ins.push_back((const char *)d_in[i] + in_bytes * k);

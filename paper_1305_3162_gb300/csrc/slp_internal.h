@@ -140,7 +140,76 @@ struct DevPlan {
 
     int *err;  // device status word (sticky)
     int check_finite;  // 1: inputs and results are checked for NaN/Inf (DEV_ERR_NONFINITE)
+
+    // triangle-integrated discretisation (integration = 1)
+    int integration;
+    const int4 *tri_v;      // [M] user vertex ids of each triangle
+    const void *tri_n3;     // T4 [M] outward unit normal / 3
+    void *gbuf;             // T [M] element charges of the current input (scratch)
+    // gridding matrix A, CSR over the grid points the triangles' boxes reach
+    int64_t am_rows;
+    const int64_t *am_rowptr, *am_row;  // [am_rows + 1], [am_rows] grid linear index
+    const int *am_col;                  // triangle of each entry
+    const void *am_val;                 // T
+    // near-field matrix over triangles, CSR over sorted targets
+    const int64_t *nt_rowptr;
+    const int *nt_col;
+    const void *nt_val;
 };
+
+// Duffy-Gauss rule of the triangle-integrated plans (8 x 8 points) and the
+// largest box of grid points per axis a triangle's window may reach.
+constexpr int TRI_RULE = 64;
+constexpr int TRI_BOX = 24;
+
+// Plan-time inputs of the gridding-matrix assembly (FP64).
+struct TriBuildA {
+    const double3 *ugrid;   // [NV] vertex grid coordinates (cells, 0..L)
+    const double3 *xphys;   // [NV] vertex physical coordinates (relative to the torus centre)
+    const int4 *tri;        // [M] vertex ids
+    int64_t M, NV;
+    int m, L[3];
+    double beta, isb;
+    const double *ra, *rb, *rw;  // rule on the reference triangle {0 <= b <= a <= 1}, weights summing to 1/2
+    int np;
+    int *err;
+};
+// Plan-time inputs of the near-field matrix over triangles (FP64).
+struct TriBuildN {
+    const double3 *tgt;      // [N] sorted targets, physical, relative to the centre
+    const int *tgt_perm;     // [N] sorted -> user vertex
+    const int *tgt_block;    // [N] target block of each sorted target
+    const int *blk_r0;       // [nblk + 1]
+    const int2 *ranges;      // candidate vertex ranges (sorted target order)
+    const int *vt_ptr, *vt_ent;  // vertex -> adjacent (triangle * 4 + corner)
+    const int *tri_min_sorted;   // [M] smallest sorted index among the triangle's vertices
+    const double3 *xphys;    // [NV] vertex physical coordinates (relative to the centre)
+    const int4 *tri;         // [M]
+    int64_t N;
+    double eps;
+    int kernel_mode;
+    double inv_s_sqrt2;
+    const double *es_w, *es_g;
+    int es_n;
+    const double *sep_h[3];
+    int sep_nh[3];
+    double sep_A4pi;
+    double P[3];
+    const double *ra, *rb, *rw;
+    int np;
+    int *err;
+};
+cudaError_t launch_amat_count(const TriBuildA &b, int *cnt, cudaStream_t s);
+cudaError_t launch_amat_fill(const TriBuildA &b, int prec, const int *slot_of, const int64_t *rowptr, int *cursor,
+                             int *col, void *val, cudaStream_t s);
+cudaError_t launch_csr_sort(int64_t nrows, int prec, const int64_t *rowptr, int *col, void *val, cudaStream_t s);
+cudaError_t launch_nmt_build(const TriBuildN &b, int pass, int prec, int64_t *counts, const int64_t *rowptr,
+                             int *col, void *val, cudaStream_t s);
+// element charges of NODAL_MAG input into gbuf
+cudaError_t launch_p0_charges(const DevPlan &p, const void *d_in, cudaStream_t s);
+// y[row_idx ? row_idx[i] : i] = sum over CSR row i of val * x[col]
+cudaError_t launch_csr_apply(int prec, int lanes_per_row, int64_t nrows, const int64_t *rowptr, const int64_t *row_idx,
+                             const int *col, const void *val, const void *x, void *y, cudaStream_t s);
 
 // Kernel launchers (return the launch error, if any).
 cudaError_t launch_nodal_prep(const DevPlan &p, const void *d_in, cudaStream_t s);

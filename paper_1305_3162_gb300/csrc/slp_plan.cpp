@@ -904,6 +904,23 @@ void active_region(slp_plan_s &p) {
     };
     mark(p.src_grid, p.Q);
     mark(p.tgt_grid, p.N);
+    if (p.opts.integration) {
+        // triangle integrals reach every cell of each triangle's bounding box
+        for (int64_t j = 0; j < p.M; ++j) {
+            int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+            for (int a = 0; a < 3; ++a) {
+                double g[4];
+                int c[3];
+                grid_coords(p, &p.V[3 * (int64_t)p.T[3 * j + a]], g, c[0], c[1], c[2]);
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = std::min(lo[d], c[d]);
+                    hi[d] = std::max(hi[d], c[d]);
+                }
+            }
+            for (int z = lo[2]; z <= hi[2]; ++z)
+                for (int y = lo[1]; y <= hi[1]; ++y) col[(size_t)(((z % Lz) + Lz) % Lz) * Ly + (((y % Ly) + Ly) % Ly)] = 1;
+        }
+    }
     for (int z = 0; z < Lz; ++z)
         for (int y = 0; y < Ly; ++y)
             if (col[(size_t)z * Ly + y])
@@ -1191,6 +1208,24 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     TRY(upload(p, &ptr, p.near_blk_first.data(), p.near_blk_first.size()));
     p.d_blk_first = (int *)ptr;
     if (p.opts.deterministic) TRY(dalloc(p, &d.phi_near, sizeof(T) * 32 * std::max<size_t>(1, p.near_items.size())));
+    d.integration = p.opts.integration ? 1 : 0;
+    if (d.integration) {
+        // triangles: vertex ids and n_j / 3 for the element charges of nodal input
+        std::vector<int4> tv(p.M);
+        std::vector<T4> n3(p.M);
+        for (int64_t j = 0; j < p.M; ++j) {
+            tv[j] = make_int4(p.T[3 * j], p.T[3 * j + 1], p.T[3 * j + 2], 0);
+            n3[j].x = (T)(p.nrm[3 * j] / 3.0);
+            n3[j].y = (T)(p.nrm[3 * j + 1] / 3.0);
+            n3[j].z = (T)(p.nrm[3 * j + 2] / 3.0);
+            n3[j].w = T(0);
+        }
+        TRY(upload(p, &ptr, tv.data(), tv.size()));
+        d.tri_v = (const int4 *)ptr;
+        TRY(upload(p, &ptr, n3.data(), n3.size()));
+        d.tri_n3 = ptr;
+        TRY(dalloc(p, &d.gbuf, sizeof(T) * (size_t)std::max<int64_t>(p.M, 1)));
+    }
     if (p.kernel_mode == SLP_KERNEL_EXPSUM) {
         std::vector<T> w(p.es_w.size()), g(p.es_g.size());
         for (size_t k = 0; k < w.size(); ++k) {
@@ -1267,10 +1302,25 @@ template <typename S> slp_status tmp_upload(TmpBuf &b, const S *src, size_t n) {
 // block, r_adj being the largest distance from a vertex to a quadrature point
 // of an adjacent triangle.  Returns SLP_OK without building when the matrix
 // would exceed the memory budget (near_mode stays ON_THE_FLY).
-slp_status build_near_matrix(slp_plan_s &p, const std::vector<uint64_t> &tkeys) {
-    const int64_t N = p.N, M = p.M, q = p.q;
+// Candidates of the near-field operators: for every target block of the
+// near-field work list, the ranges of sorted vertices (2x2x2-cell bins,
+// contiguous in the sort) whose bounding boxes lie within rad of the block's
+// bounding box (all vertices when all_pairs), plus the vertex -> (triangle,
+// corner) adjacency and the sorted targets' positions relative to the centre.
+struct NearCandidates {
+    std::vector<int> vt_ptr, vt_ent;
+    std::vector<double4> tgt;
+    std::vector<int> tgt_block, blk_r0;
+    std::vector<int2> ranges;
+};
+
+void near_candidates(const slp_plan_s &p, const std::vector<uint64_t> &tkeys, double rad, bool all_pairs,
+                     NearCandidates &c) {
+    const int64_t N = p.N, M = p.M;
     // vertex -> adjacent (triangle, local vertex)
-    std::vector<int> vt_ptr(N + 1, 0), vt_ent(3 * M);
+    std::vector<int> &vt_ptr = c.vt_ptr, &vt_ent = c.vt_ent;
+    vt_ptr.assign(N + 1, 0);
+    vt_ent.assign(3 * M, 0);
     for (int64_t j = 0; j < M; ++j)
         for (int a = 0; a < 3; ++a) vt_ptr[p.T[3 * j + a] + 1]++;
     for (int64_t i = 0; i < N; ++i) vt_ptr[i + 1] += vt_ptr[i];
@@ -1279,30 +1329,20 @@ slp_status build_near_matrix(slp_plan_s &p, const std::vector<uint64_t> &tkeys) 
         for (int64_t j = 0; j < M; ++j)
             for (int a = 0; a < 3; ++a) vt_ent[fillc[p.T[3 * j + a]]++] = (int)(j * 4 + a);
     }
-    double r_adj = 0.0;
-    for (int64_t j = 0; j < M; ++j)
-        for (int a = 0; a < 3; ++a) {
-            const double *v = &p.V[3 * p.T[3 * j + a]];
-            for (int s2 = 0; s2 < q; ++s2) {
-                const double *y = &p.y[3 * (j * q + s2)];
-                const double d = std::sqrt((v[0] - y[0]) * (v[0] - y[0]) + (v[1] - y[1]) * (v[1] - y[1]) +
-                                           (v[2] - y[2]) * (v[2] - y[2]));
-                r_adj = std::max(r_adj, d);
-            }
-        }
-    const bool all_pairs = p.kernel_mode == SLP_KERNEL_SEPARABLE || !(p.eps < p.diam);
-    const double rad = all_pairs ? INFINITY : p.eps + r_adj * (1.0 + 1e-9) + 1e-12 * p.diam;
-
     // target physical positions (sorted, relative to the centre)
-    std::vector<double4> tgt(N);
+    std::vector<double4> &tgt = c.tgt;
+    tgt.resize(N);
     for (int64_t i = 0; i < N; ++i) {
         const double *v = &p.V[3 * (int64_t)p.tgt_perm[i]];
         tgt[i] = make_double4(v[0] - p.ctr[0], v[1] - p.ctr[1], v[2] - p.ctr[2], 0.0);
     }
     // target blocks (as in the near-field work list)
     const int nblk = (int)p.near_blk_first.size() - 1;
-    std::vector<int> tgt_block(N, 0), blk_r0(nblk + 1, 0);
-    std::vector<int2> ranges;
+    std::vector<int> &tgt_block = c.tgt_block, &blk_r0 = c.blk_r0;
+    tgt_block.assign(N, 0);
+    blk_r0.assign(nblk + 1, 0);
+    std::vector<int2> &ranges = c.ranges;
+    ranges.clear();
     struct Bin {
         int b, e;
         double lo[3], hi[3];
@@ -1382,6 +1422,29 @@ slp_status build_near_matrix(slp_plan_s &p, const std::vector<uint64_t> &tkeys) 
         }
     }
     blk_r0[nblk] = (int)ranges.size();
+
+}
+
+slp_status build_near_matrix(slp_plan_s &p, const std::vector<uint64_t> &tkeys) {
+    const int64_t N = p.N, M = p.M, q = p.q;
+    double r_adj = 0.0;
+    for (int64_t j = 0; j < M; ++j)
+        for (int a = 0; a < 3; ++a) {
+            const double *v = &p.V[3 * p.T[3 * j + a]];
+            for (int s2 = 0; s2 < q; ++s2) {
+                const double *y = &p.y[3 * (j * q + s2)];
+                const double d = std::sqrt((v[0] - y[0]) * (v[0] - y[0]) + (v[1] - y[1]) * (v[1] - y[1]) +
+                                           (v[2] - y[2]) * (v[2] - y[2]));
+                r_adj = std::max(r_adj, d);
+            }
+        }
+    const bool all_pairs = p.kernel_mode == SLP_KERNEL_SEPARABLE || !(p.eps < p.diam);
+    const double rad = all_pairs ? INFINITY : p.eps + r_adj * (1.0 + 1e-9) + 1e-12 * p.diam;
+    NearCandidates cand;
+    near_candidates(p, tkeys, rad, all_pairs, cand);
+    std::vector<int> &vt_ptr = cand.vt_ptr, &vt_ent = cand.vt_ent, &tgt_block = cand.tgt_block, &blk_r0 = cand.blk_r0;
+    std::vector<double4> &tgt = cand.tgt;
+    std::vector<int2> &ranges = cand.ranges;
 
     // device inputs
     std::vector<double4> src(p.Q), nrm(M);
@@ -1469,6 +1532,227 @@ slp_status build_near_matrix(slp_plan_s &p, const std::vector<uint64_t> &tkeys) 
     return SLP_OK;
 }
 
+// Duffy-Gauss rule of the triangle-integrated plans on the reference triangle
+// {0 <= b <= a <= 1} (area 1/2): a = s, b = s t for Gauss-Legendre nodes s, t
+// on [0, 1] and weight w_s w_t s (the Jacobian of (s, t) -> (s, s t)).  The
+// Gauss-Legendre nodes are roots of P_n found by Newton's method from
+// cos(pi (i + 3/4) / (n + 1/2)), with weights 2 / ((1 - x^2) P_n'(x)^2).
+void tri_rule(int n, std::vector<double> &ra, std::vector<double> &rb, std::vector<double> &rw) {
+    std::vector<double> x(n), w(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = 0.5 * (1.0 - z);  // [0, 1]
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);  // half of the [-1, 1] weight
+    }
+    ra.clear();
+    rb.clear();
+    rw.clear();
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            ra.push_back(x[i]);
+            rb.push_back(x[i] * x[k]);
+            rw.push_back(w[i] * w[k] * x[i]);
+        }
+}
+
+// Triangle-integrated plans: the gridding matrix A (CSR over grid points) and
+// the near-field matrix over triangles (CSR over sorted targets), both
+// assembled on the device in FP64 and stored at the plan precision.
+template <typename T> slp_status build_tri_matrices(slp_plan_s &p, const std::vector<uint64_t> &tkeys) {
+    const int64_t N = p.N, M = p.M;
+    const int64_t G = (int64_t)p.L[0] * p.L[1] * p.L[2];
+    if (G > ((int64_t)1 << 27)) return fail(SLP_ERR_UNSUPPORTED, "triangle integrals need a grid of at most 2^27 points");
+    std::vector<double3> ug(N), xp(N);
+    for (int64_t i = 0; i < N; ++i) {
+        const double *v = &p.V[3 * i];
+        xp[i] = make_double3(v[0] - p.ctr[0], v[1] - p.ctr[1], v[2] - p.ctr[2]);
+        ug[i] = make_double3((v[0] - p.ctr[0]) / p.P[0] * p.L[0] + 0.5 * p.L[0],
+                             (v[1] - p.ctr[1]) / p.P[1] * p.L[1] + 0.5 * p.L[1],
+                             (v[2] - p.ctr[2]) / p.P[2] * p.L[2] + 0.5 * p.L[2]);
+    }
+    std::vector<int4> tri(M);
+    for (int64_t j = 0; j < M; ++j) tri[j] = make_int4(p.T[3 * j], p.T[3 * j + 1], p.T[3 * j + 2], 0);
+    std::vector<double> ra, rb, rw;
+    tri_rule(8, ra, rb, rw);
+    TmpBuf b_ug, b_xp, b_tri, b_ra, b_rb, b_rw, b_cnt;
+    TRY(tmp_upload(b_ug, ug.data(), ug.size()));
+    TRY(tmp_upload(b_xp, xp.data(), xp.size()));
+    TRY(tmp_upload(b_tri, tri.data(), tri.size()));
+    TRY(tmp_upload(b_ra, ra.data(), ra.size()));
+    TRY(tmp_upload(b_rb, rb.data(), rb.size()));
+    TRY(tmp_upload(b_rw, rw.data(), rw.size()));
+    slp::TriBuildA ba;
+    memset(&ba, 0, sizeof ba);
+    ba.ugrid = (const double3 *)b_ug.p;
+    ba.xphys = (const double3 *)b_xp.p;
+    ba.tri = (const int4 *)b_tri.p;
+    ba.M = M;
+    ba.NV = N;
+    ba.m = p.m;
+    for (int d = 0; d < 3; ++d) ba.L[d] = p.L[d];
+    ba.beta = KB_B * p.m;
+    ba.isb = 1.0 / std::sinh(ba.beta);
+    ba.ra = (const double *)b_ra.p;
+    ba.rb = (const double *)b_rb.p;
+    ba.rw = (const double *)b_rw.p;
+    ba.np = (int)ra.size();
+    ba.err = p.dp.err;
+    // the status word of the plan is clear here; the assembly kernels report into it
+    auto status = [&](const char *what) -> slp_status {
+        int code = 0;
+        TRY(cuda_status(cudaDeviceSynchronize(), what));
+        TRY(cuda_status(cudaMemcpy(&code, p.dp.err, sizeof(int), cudaMemcpyDeviceToHost), what));
+        if (code == slp::DEV_ERR_BAD_ITEM)
+            return fail(SLP_ERR_UNSUPPORTED, "%s: a triangle spans more than %d grid cells", what, slp::TRI_BOX - 2 * p.m);
+        if (code != 0) return fail(SLP_ERR_CUDA, "%s: device status word %d", what, code);
+        return SLP_OK;
+    };
+    {
+        std::vector<int> zeros(G, 0);
+        TRY(tmp_upload(b_cnt, zeros.data(), zeros.size()));
+    }
+    TRY(cuda_status(slp::launch_amat_count(ba, (int *)b_cnt.p, 0), "gridding matrix count"));
+    TRY(status("gridding matrix count"));
+    std::vector<int> cnt(G), slot_of(G, -1);
+    TRY(cuda_status(cudaMemcpy(cnt.data(), b_cnt.p, sizeof(int) * G, cudaMemcpyDeviceToHost), "count copy"));
+    std::vector<int64_t> rowptr(1, 0), rowidx;
+    for (int64_t g = 0; g < G; ++g)
+        if (cnt[g] > 0) {
+            slot_of[g] = (int)rowidx.size();
+            rowidx.push_back(g);
+            rowptr.push_back(rowptr.back() + cnt[g]);
+        }
+    const int64_t nrows = (int64_t)rowidx.size(), annz = rowptr.back();
+    void *ptr = nullptr;
+    TRY(upload(p, &ptr, rowptr.data(), rowptr.size()));
+    p.dp.am_rowptr = (const int64_t *)ptr;
+    TRY(upload(p, &ptr, rowidx.data(), rowidx.size()));
+    p.dp.am_row = (const int64_t *)ptr;
+    TRY(dalloc(p, &ptr, sizeof(int) * (size_t)std::max<int64_t>(annz, 1)));
+    p.dp.am_col = (const int *)ptr;
+    TRY(dalloc(p, &ptr, sizeof(T) * (size_t)std::max<int64_t>(annz, 1)));
+    p.dp.am_val = ptr;
+    p.dp.am_rows = nrows;
+    {
+        TmpBuf b_slot, b_cur;
+        TRY(tmp_upload(b_slot, slot_of.data(), slot_of.size()));
+        std::vector<int> z(std::max<int64_t>(nrows, 1), 0);
+        TRY(tmp_upload(b_cur, z.data(), z.size()));
+        TRY(cuda_status(slp::launch_amat_fill(ba, p.prec, (const int *)b_slot.p, p.dp.am_rowptr, (int *)b_cur.p,
+                                              (int *)p.dp.am_col, (void *)p.dp.am_val, 0), "gridding matrix fill"));
+        TRY(cuda_status(slp::launch_csr_sort(nrows, p.prec, p.dp.am_rowptr, (int *)p.dp.am_col, (void *)p.dp.am_val, 0),
+                        "gridding matrix order"));
+        TRY(status("gridding matrix fill"));
+    }
+    p.am_nnz = annz;
+
+    // near-field matrix: every triangle within eps of the target (point-triangle distance)
+    double emax = 0.0;
+    for (int64_t j = 0; j < M; ++j)
+        for (int a = 0; a < 3; ++a) {
+            const double *u = &p.V[3 * (int64_t)p.T[3 * j + a]], *v = &p.V[3 * (int64_t)p.T[3 * j + (a + 1) % 3]];
+            emax = std::max(emax, std::sqrt((u[0] - v[0]) * (u[0] - v[0]) + (u[1] - v[1]) * (u[1] - v[1]) +
+                                            (u[2] - v[2]) * (u[2] - v[2])));
+        }
+    const bool all_pairs = p.kernel_mode == SLP_KERNEL_SEPARABLE || !(p.eps < p.diam);
+    const double rad = all_pairs ? INFINITY : p.eps + emax * (1.0 + 1e-9) + 1e-12 * p.diam;
+    NearCandidates cand;
+    near_candidates(p, tkeys, rad, all_pairs, cand);
+    std::vector<int> inv(N), tmin(M);
+    for (int64_t i = 0; i < N; ++i) inv[p.tgt_perm[i]] = (int)i;
+    for (int64_t j = 0; j < M; ++j)
+        tmin[j] = std::min(inv[p.T[3 * j]], std::min(inv[p.T[3 * j + 1]], inv[p.T[3 * j + 2]]));
+    std::vector<double3> tg(N);
+    for (int64_t i = 0; i < N; ++i) tg[i] = make_double3(cand.tgt[i].x, cand.tgt[i].y, cand.tgt[i].z);
+    TmpBuf b_tg, b_blk, b_r0, b_rng, b_vtp, b_vte, b_tmin, b_h[3], b_esw, b_esg, b_ncnt;
+    TRY(tmp_upload(b_tg, tg.data(), tg.size()));
+    TRY(tmp_upload(b_blk, cand.tgt_block.data(), cand.tgt_block.size()));
+    TRY(tmp_upload(b_r0, cand.blk_r0.data(), cand.blk_r0.size()));
+    TRY(tmp_upload(b_rng, cand.ranges.data(), std::max<size_t>(cand.ranges.size(), 1)));
+    TRY(tmp_upload(b_vtp, cand.vt_ptr.data(), cand.vt_ptr.size()));
+    TRY(tmp_upload(b_vte, cand.vt_ent.data(), cand.vt_ent.size()));
+    TRY(tmp_upload(b_tmin, tmin.data(), tmin.size()));
+    slp::TriBuildN bn;
+    memset(&bn, 0, sizeof bn);
+    bn.tgt = (const double3 *)b_tg.p;
+    bn.tgt_perm = p.dp.tgt_perm;
+    bn.tgt_block = (const int *)b_blk.p;
+    bn.blk_r0 = (const int *)b_r0.p;
+    bn.ranges = (const int2 *)b_rng.p;
+    bn.vt_ptr = (const int *)b_vtp.p;
+    bn.vt_ent = (const int *)b_vte.p;
+    bn.tri_min_sorted = (const int *)b_tmin.p;
+    bn.xphys = (const double3 *)b_xp.p;
+    bn.tri = (const int4 *)b_tri.p;
+    bn.N = N;
+    bn.eps = std::isfinite(p.eps) ? p.eps : 1e300;
+    bn.kernel_mode = p.kernel_mode;
+    bn.inv_s_sqrt2 = p.sigma_g > 0 ? 1.0 / (p.sigma_g * std::sqrt(2.0)) : 0.0;
+    if (p.kernel_mode == SLP_KERNEL_EXPSUM) {
+        std::vector<double> w(p.es_w.size()), g(p.es_g.size());
+        for (size_t k = 0; k < w.size(); ++k) {
+            w[k] = p.es_w[k] / p.P[0];
+            g[k] = p.es_g[k] / (p.P[0] * p.P[0]);
+        }
+        TRY(tmp_upload(b_esw, w.data(), w.size()));
+        TRY(tmp_upload(b_esg, g.data(), g.size()));
+        bn.es_w = (const double *)b_esw.p;
+        bn.es_g = (const double *)b_esg.p;
+        bn.es_n = (int)w.size();
+    }
+    if (p.kernel_mode == SLP_KERNEL_SEPARABLE) {
+        for (int a = 0; a < 3; ++a) {
+            TRY(tmp_upload(b_h[a], p.sep_h[a].data(), p.sep_h[a].size()));
+            bn.sep_h[a] = (const double *)b_h[a].p;
+            bn.sep_nh[a] = (int)p.sep_h[a].size();
+        }
+        bn.sep_A4pi = 4.0 * PI * p.sep_A;
+    }
+    for (int a = 0; a < 3; ++a) bn.P[a] = p.P[a];
+    bn.ra = (const double *)b_ra.p;
+    bn.rb = (const double *)b_rb.p;
+    bn.rw = (const double *)b_rw.p;
+    bn.np = (int)ra.size();
+    bn.err = p.dp.err;
+    {
+        std::vector<int64_t> z(N + 1, 0);
+        TRY(tmp_upload(b_ncnt, z.data(), z.size()));
+    }
+    TRY(cuda_status(slp::launch_nmt_build(bn, 0, p.prec, (int64_t *)b_ncnt.p, nullptr, nullptr, nullptr, 0),
+                    "near-field matrix count"));
+    TRY(status("near-field matrix count"));
+    std::vector<int64_t> ncnt(N), nrp(N + 1, 0);
+    TRY(cuda_status(cudaMemcpy(ncnt.data(), b_ncnt.p, sizeof(int64_t) * N, cudaMemcpyDeviceToHost), "count copy"));
+    for (int64_t i = 0; i < N; ++i) nrp[i + 1] = nrp[i] + ncnt[i];
+    const int64_t nnnz = nrp[N];
+    TRY(upload(p, &ptr, nrp.data(), nrp.size()));
+    p.dp.nt_rowptr = (const int64_t *)ptr;
+    TRY(dalloc(p, &ptr, sizeof(int) * (size_t)std::max<int64_t>(nnnz, 1)));
+    p.dp.nt_col = (const int *)ptr;
+    TRY(dalloc(p, &ptr, sizeof(T) * (size_t)std::max<int64_t>(nnnz, 1)));
+    p.dp.nt_val = ptr;
+    TRY(cuda_status(slp::launch_nmt_build(bn, 1, p.prec, nullptr, p.dp.nt_rowptr, (int *)p.dp.nt_col,
+                                          (void *)p.dp.nt_val, 0), "near-field matrix fill"));
+    TRY(status("near-field matrix fill"));
+    p.nt_nnz = nnnz;
+    p.near_mode = SLP_NEAR_PRECOMPUTED;
+    // element charges (nodal input), gridding product, 5 FFT passes, near-field product, gather
+    p.launches_per_eval = 9;
+    return SLP_OK;
+}
+
 slp_status cuda_status(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return SLP_OK;
     return fail(SLP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -1506,15 +1790,26 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
         }
         return SLP_OK;
     };
+    // triangle integrals: element charges, then two sparse products (gridding
+    // matrix into grid A, near-field matrix into phi_part)
+    const bool tri = p.opts.integration != 0;
+    const void *gch = kind == SLP_INPUT_ELEMENT ? d_in : d.gbuf;
     // nodal input with the precomputed near field: the charges are only needed
     // by the spread, which computes them itself
-    const bool use_matrix = kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
+    const bool use_matrix = !tri && kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
     const bool fuse = use_matrix && last > SLP_STAGE_CHARGES;
     const bool concurrent = ex != nullptr && prof == nullptr && last >= SLP_STAGE_NEAR;
     const size_t es = p.prec == 64 ? 8 : 4;
     const size_t part_bytes = (es * (size_t)p.N + 15) / 16 * 16;
     // near-field branch on stream t
     auto near_branch = [&](cudaStream_t t) -> slp_status {
+        if (tri) {
+            TRY(timed(SLOT_NEAR, t, [&] {
+                return slp::launch_csr_apply(p.prec, 32, p.N, d.nt_rowptr, nullptr, d.nt_col, d.nt_val, gch,
+                                             d.phi_part, t);
+            }, "near-field matrix"));
+            return SLP_OK;
+        }
         if (use_matrix) {
             TRY(timed(SLOT_NODAL_PREP, t, [&] { return slp::launch_nodal_prep(d, d_in, t); }, "nodal prep"));
             TRY(timed(SLOT_NEAR, t, [&] { return slp::launch_near_matrix(d, d_in, t); }, "near-field matrix"));
@@ -1532,7 +1827,12 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
     };
     cudaEvent_t *tl = concurrent ? ex->timeline : nullptr;
     if (tl) TRY(cuda_status(cudaEventRecord(tl[0], s), "timeline"));
-    if (!fuse) TRY(timed(SLOT_CHARGES, s, [&] { return slp::launch_charges(d, kind, d_in, s); }, "charges"));
+    if (tri) {
+        if (kind == SLP_INPUT_NODAL_MAG)
+            TRY(timed(SLOT_CHARGES, s, [&] { return slp::launch_p0_charges(d, d_in, s); }, "element charges"));
+    } else if (!fuse) {
+        TRY(timed(SLOT_CHARGES, s, [&] { return slp::launch_charges(d, kind, d_in, s); }, "charges"));
+    }
     if (last <= SLP_STAGE_CHARGES) return SLP_OK;
     cudaStream_t caller = s;
     if (concurrent) {
@@ -1544,7 +1844,13 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
         if (tl) TRY(cuda_status(cudaEventRecord(tl[3], ex->aux), "timeline"));
         TRY(cuda_status(cudaEventRecord(ex->join, ex->aux), "join"));
     }
-    TRY(timed(SLOT_SPREAD, s, [&] { return slp::launch_spread(d, fuse ? kind : -1, d_in, s); }, "spread"));
+    if (tri)
+        TRY(timed(SLOT_SPREAD, s, [&] {
+            return slp::launch_csr_apply(p.prec, 8, d.am_rows, d.am_rowptr, d.am_row, d.am_col, d.am_val, gch,
+                                         d.gridA, s);
+        }, "gridding matrix"));
+    else
+        TRY(timed(SLOT_SPREAD, s, [&] { return slp::launch_spread(d, fuse ? kind : -1, d_in, s); }, "spread"));
     if (tl) TRY(cuda_status(cudaEventRecord(tl[1], s), "timeline"));
     if (last <= SLP_STAGE_SPREAD) return SLP_OK;
     // fused plane passes (FX + FY, IY + IX) unless the run stops between them
@@ -1605,7 +1911,8 @@ slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, 
 // state.
 slp_status run_states(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *const *ins, void *const *outs,
                       int S, cudaStream_t s, SlpExec *ex, int *launches) {
-    const bool use_matrix = kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
+    const bool use_matrix =
+        !p.opts.integration && kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
     if (!use_matrix || !ex) {
         for (int k = 0; k < S; ++k) {
             TRY(run_pipeline(p, d, kind, ins[k], outs[k], s, SLP_STAGE_NEAR, nullptr, ex));
@@ -1680,6 +1987,15 @@ struct DeviceGuard {
 }  // namespace
 
 void slp::set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+
+slp_status slp_check_kind(const slp_plan_s &p, int kind) {
+    if (kind < SLP_INPUT_SIGMA || kind > SLP_INPUT_ELEMENT) return slp_fail(SLP_ERR_INVALID_ARG, "unknown input kind %d", kind);
+    if (p.opts.integration && (kind == SLP_INPUT_SIGMA || kind == SLP_INPUT_MAG))
+        return slp_fail(SLP_ERR_UNSUPPORTED, "plans with triangle integrals take element charges or nodal m");
+    if (!p.opts.integration && kind == SLP_INPUT_ELEMENT)
+        return slp_fail(SLP_ERR_UNSUPPORTED, "element charges need a plan with opts.integration = 1");
+    return SLP_OK;
+}
 
 slp_status slp_fail(slp_status st, const char *fmt, ...) {
     char buf[512];
@@ -1757,7 +2073,8 @@ slp_status slp_alloc_scratch(slp_plan_s &p, slp::DevPlan &out, std::vector<void 
                 {&out.gridB, es * G * p.kf},
                 {&out.S1, 2 * es * p.L[2] * p.L[1] * Kx * p.kf},
                 {&out.S2, 2 * es * p.L[2] * p.n[1] * Kx * p.kf},
-                {&out.phi_near, p.opts.deterministic ? es * 32 * (int64_t)std::max<size_t>(1, p.near_items.size()) : 0}};
+                {&out.phi_near, p.opts.deterministic ? es * 32 * (int64_t)std::max<size_t>(1, p.near_items.size()) : 0},
+                {&out.gbuf, p.opts.integration ? es * p.M : 0}};
     int64_t total = 0;
     for (auto &r : reqs) {
         if (r.n == 0) continue;
@@ -1875,7 +2192,10 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
         }
         DeviceGuard g(p->device);
         st = p->prec == 64 ? upload_all<double>(*p) : upload_all<float>(*p);
-        if (st == SLP_OK && o.near_mode != SLP_NEAR_ON_THE_FLY) st = build_near_matrix(*p, tkeys);
+        if (st == SLP_OK && o.integration)
+            st = p->prec == 64 ? build_tri_matrices<double>(*p, tkeys) : build_tri_matrices<float>(*p, tkeys);
+        else if (st == SLP_OK && o.near_mode != SLP_NEAR_ON_THE_FLY)
+            st = build_near_matrix(*p, tkeys);
         if (st == SLP_OK && slp_exec_create(p->exec) != cudaSuccess) st = fail(SLP_ERR_CUDA, "stream creation failed");
         if (st != SLP_OK) {
             free_device(*p);
@@ -1890,7 +2210,7 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
 slp_status slp_eval(slp_plan_t p, int kind, const void *d_in, void *d_phi, void *stream) {
     if (!p) return fail(SLP_ERR_INVALID_ARG, "plan is NULL");
     if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan cannot evaluate");
-    if (kind < 0 || kind > 2) return fail(SLP_ERR_INVALID_ARG, "unknown input kind %d", kind);
+    TRY(slp_check_kind(*p, kind));
     if (!d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "input or output pointer is NULL");
     DeviceGuard g(p->device);
     return run_pipeline(*p, kind, d_in, d_phi, (cudaStream_t)stream, SLP_STAGE_NEAR);
@@ -1899,7 +2219,7 @@ slp_status slp_eval(slp_plan_t p, int kind, const void *d_in, void *d_phi, void 
 slp_status slp_eval_states(slp_plan_t p, int kind, int n_states, const void *d_in, void *d_phi, void *stream) {
     if (!p) return fail(SLP_ERR_INVALID_ARG, "plan is NULL");
     if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan cannot evaluate");
-    if (kind < 0 || kind > 2) return fail(SLP_ERR_INVALID_ARG, "unknown input kind %d", kind);
+    TRY(slp_check_kind(*p, kind));
     if (n_states < 1) return fail(SLP_ERR_INVALID_ARG, "n_states must be positive");
     if (!d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "input or output pointer is NULL");
     DeviceGuard g(p->device);
@@ -1917,11 +2237,11 @@ slp_status slp_eval_states(slp_plan_t p, int kind, int n_states, const void *d_i
 slp_status slp_eval_host(slp_plan_t p, int kind, const void *h_in, void *h_phi, void *stream) {
     if (!p) return fail(SLP_ERR_INVALID_ARG, "plan is NULL");
     if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan cannot evaluate");
-    if (kind < 0 || kind > 2) return fail(SLP_ERR_INVALID_ARG, "unknown input kind %d", kind);
+    TRY(slp_check_kind(*p, kind));
     if (!h_in || !h_phi) return fail(SLP_ERR_INVALID_ARG, "input or output pointer is NULL");
     DeviceGuard g(p->device);
     const size_t es = p->prec == 64 ? 8 : 4;
-    const size_t nin = kind == SLP_INPUT_SIGMA ? (size_t)p->Q : (kind == SLP_INPUT_MAG ? 3 * (size_t)p->Q : 3 * (size_t)p->N);
+    const size_t nin = (size_t)slp_input_count(*p, kind);
     cudaStream_t s = (cudaStream_t)stream;
     TRY(cuda_status(cudaMemcpyAsync(p->d_stage_in, h_in, nin * es, cudaMemcpyHostToDevice, s), "copy in"));
     TRY(run_pipeline(*p, kind, p->d_stage_in, p->d_stage_phi, s, SLP_STAGE_NEAR));
@@ -1968,6 +2288,9 @@ slp_status slp_query(slp_plan_t p, slp_info *info) {
     info->spread_blocks_per_sm = (p->prec == 32 && p->m <= 4) ? (spread_dense(*p) ? 4 : 5) : 0;
     info->spread_table = p->dp.wtab != nullptr ? 1 : 0;
     info->expsum_terms = p->kernel_mode == SLP_KERNEL_EXPSUM ? (int)p->es_w.size() : 0;
+    info->integration = p->opts.integration ? 1 : 0;
+    info->grid_matrix_nnz = p->am_nnz;
+    info->near_tri_nnz = p->nt_nnz;
     return SLP_OK;
 }
 
@@ -2023,7 +2346,8 @@ const char *slp_last_error(void) { return g_last_error.c_str(); }
 slp_status slp_debug_run(slp_plan_t p, int kind, const void *d_in, void *d_phi, void *stream, int last) {
     if (!p) return fail(SLP_ERR_INVALID_ARG, "plan is NULL");
     if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan");
-    if (kind < 0 || kind > 2 || !d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "bad input");
+    if (!d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "bad input");
+    TRY(slp_check_kind(*p, kind));
     DeviceGuard g(p->device);
     // a partial run may have left a spread grid behind: start from zero
     const size_t es = p->prec == 64 ? 8 : 4;
@@ -2144,7 +2468,8 @@ slp_status slp_debug_profile(slp_plan_t p, int kind, const void *d_in, void *d_p
     if (!p || !ms) return fail(SLP_ERR_INVALID_ARG, "NULL argument");
     if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan");
     if (n < SLP_PROFILE_SLOTS) return fail(SLP_ERR_INVALID_ARG, "need room for %d timings", SLP_PROFILE_SLOTS);
-    if (kind < 0 || kind > 2 || !d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "bad input");
+    if (!d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "bad input");
+    TRY(slp_check_kind(*p, kind));
     DeviceGuard g(p->device);
     SlpProfile prof;
     for (int i = 0; i < 2 * SLP_PROFILE_SLOTS; ++i)
@@ -2164,7 +2489,8 @@ slp_status slp_debug_profile(slp_plan_t p, int kind, const void *d_in, void *d_p
 slp_status slp_debug_timeline(slp_plan_t p, int kind, const void *d_in, void *d_phi, void *stream, float *ms) {
     if (!p || !ms) return fail(SLP_ERR_INVALID_ARG, "NULL argument");
     if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan");
-    if (kind < 0 || kind > 2 || !d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "bad input");
+    if (!d_in || !d_phi) return fail(SLP_ERR_INVALID_ARG, "bad input");
+    TRY(slp_check_kind(*p, kind));
     DeviceGuard g(p->device);
     cudaEvent_t tl[5];
     for (int i = 0; i < 5; ++i)

@@ -60,6 +60,8 @@ struct slp_plan_s {
     // EXPSUM: kept terms w_k exp(-g_k u^2) of 1/u in torus units (u = r / P),
     // and per axis the one-period Fourier factors I_k(l), [S'][n_q / 2]
     std::vector<double> es_w, es_g, es_I[3];
+    // triangle-integrated plans: entries of the gridding and near-field matrices
+    int64_t am_nnz = 0, nt_nnz = 0;
 
     // sorted data (host)
     std::vector<int32_t> src_perm, tgt_perm;
@@ -93,6 +95,20 @@ struct slp_plan_s {
 
 // Record a failure text for slp_last_error() and return the status.
 slp_status slp_fail(slp_status st, const char *fmt, ...);
+
+// Values of one input of the given kind (SLP_INPUT_*).
+inline int64_t slp_input_count(const slp_plan_s &p, int kind) {
+    switch (kind) {
+        case SLP_INPUT_SIGMA: return p.Q;
+        case SLP_INPUT_MAG: return 3 * p.Q;
+        case SLP_INPUT_NODAL_MAG: return 3 * p.N;
+        case SLP_INPUT_ELEMENT: return p.M;
+    }
+    return 0;
+}
+
+// SLP_OK when the plan evaluates inputs of this kind.
+slp_status slp_check_kind(const slp_plan_s &p, int kind);
 
 // Events of a profiled evaluation: kernel slot i is bracketed by ev[2i] and
 // ev[2i + 1] on its launch stream, and launched[i] is set when it ran.

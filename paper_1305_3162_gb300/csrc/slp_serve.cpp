@@ -317,7 +317,7 @@ slp_status slp_server_create(int n_plans, const slp_plan_t *plans, int input_kin
     if (!out) return slp_fail(SLP_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n_plans < 1 || !plans) return slp_fail(SLP_ERR_INVALID_ARG, "no plans");
-    if (input_kind < SLP_INPUT_SIGMA || input_kind > SLP_INPUT_NODAL_MAG)
+    if (input_kind < SLP_INPUT_SIGMA || input_kind > SLP_INPUT_ELEMENT)
         return slp_fail(SLP_ERR_INVALID_ARG, "unknown input kind %d", input_kind);
     slp_server_opts o;
     if (opts)
@@ -330,6 +330,8 @@ slp_status slp_server_create(int n_plans, const slp_plan_t *plans, int input_kin
         if (!plans[i]) return slp_fail(SLP_ERR_INVALID_ARG, "plan %d is NULL", i);
         if (plans[i]->device < 0) return slp_fail(SLP_ERR_NO_DEVICE, "plan %d is host-only", i);
         if (plans[i]->device != dev) return slp_fail(SLP_ERR_INVALID_ARG, "all plans of a server must share a device");
+        const slp_status ks = slp_check_kind(*plans[i], input_kind);
+        if (ks != SLP_OK) return ks;
     }
     SlpDeviceGuard g(dev);
     slp_server_s *S = new slp_server_s();
@@ -350,7 +352,7 @@ slp_status slp_server_create(int n_plans, const slp_plan_t *plans, int input_kin
         slp_plan_s &p = *plans[i];
         S->plans.push_back(plans[i]);
         const int64_t es = p.prec == 64 ? 8 : 4;
-        const int64_t per_in = input_kind == SLP_INPUT_SIGMA ? p.Q : (input_kind == SLP_INPUT_MAG ? 3 * p.Q : 3 * p.N);
+        const int64_t per_in = slp_input_count(p, input_kind);
         S->in_bytes_per_state.push_back(((es * per_in + 255) / 256) * 256);
         S->out_bytes_per_state.push_back(((es * p.N + 255) / 256) * 256);
         S->in_host_bytes.push_back(es * per_in);
