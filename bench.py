@@ -189,6 +189,17 @@ def _algorithmic(info, stage, w, pairs_within):
     s1 = 2 * es * R * Kx              # active rows of S1 (complex [Lz][Ly][Kx])
     s2 = 2 * es * Za * n[1] * Kx      # active planes of S2 (complex [Lz][ny][Kx])
     dtab = es * n[2] * n[1] * Kx // 4
+    if info.get("integration"):
+        # triangle integrals: element charges, and two sparse products (entry: value + 4-byte column)
+        A = info["grid_matrix_nnz"]
+        rows = info["grid_matrix_rows"]
+        W = info["near_tri_nnz"]
+        tri = {"charges": ("hbm", 3 * es * N + 16 * M + es * M),
+               # entries, row pointers and grid indices read, element charges read, grid points written
+               "spread": ("hbm", (es + 4) * A + 16 * rows + 8 + es * M + es * rows),
+               "near": ("hbm", (es + 4) * W + 8 * (N + 1) + es * M + es * N)}
+        if stage in tri:
+            return tri[stage]
     table = {
         "charges": ("hbm", 3 * es * N + 3 * es * Q + 4 * Q + 32 * M),
         # the spread's floor is arithmetic: one multiply-add per (source, window point)
@@ -259,9 +270,11 @@ def _pairs_within(slp, plan, w, eps):
     return int(np.sum(cnt))
 
 
-def _parity(slp, plan, w, kind, d_states, states, d_phi, stream, idx, n_sample=None):
+def _parity(slp, plan, w, kind, d_states, states, d_phi, stream, idx, n_sample=None, triangles=False):
     """Max rel-L2 over the states `idx` against the FP64 oracle: all targets,
-    or n_sample seeded targets (oracle direct sum at those targets only)."""
+    or n_sample seeded targets (oracle direct sum at those targets only);
+    triangles: the oracle's triangle-integrated definition (element charges,
+    exact integrals)."""
     import torch
 
     import oracle
@@ -276,7 +289,11 @@ def _parity(slp, plan, w, kind, d_states, states, d_phi, stream, idx, n_sample=N
         torch.cuda.synchronize()
         slp.slp_check(plan.handle)
         phi = d_phi.double().cpu().numpy()
-        if sel is None:
+        if triangles:
+            ref = oracle.slp_p0(w.V, w.T, oracle.element_charges(w.V, w.T, states[i]), sel=sel)
+            if sel is not None:
+                phi = phi[sel]
+        elif sel is None:
             ref = oracle.slp_nodal(w.V, w.T, w.quad, states[i])
         else:
             qk = oracle.charges(w.V, w.T, w.quad, oracle.KIND_NODAL_MAG, states[i])
@@ -336,13 +353,13 @@ def _roofline_objects(slp, plan, w, info, prof_ms, ms_step, pairs_within, worklo
     return roofline, _per_kernel(info, prof_ms, w, pairs_within, hbm_peak)
 
 
-def _plain_config(slp, w, args, flush, steps, warmup, n_sample=None, profile=True, kernel_mode=0):
+def _plain_config(slp, w, args, flush, steps, warmup, n_sample=None, profile=True, kernel_mode=0, integration=0):
     """One workload through slp_eval: parity gate, timed steps, per-kernel profile."""
     import torch
     dev = torch.cuda.current_device()
     t0 = time.perf_counter()
     plan = slp.Plan(w.V, w.T, quadrature=w.quad, tolerance=w.tolerance, precision=w.precision, grid=w.grid,
-                    device=dev, kernel_mode=kernel_mode)
+                    device=dev, kernel_mode=kernel_mode, integration=integration)
     t_plan = time.perf_counter() - t0
     try:
         info = plan.info
@@ -353,7 +370,7 @@ def _plain_config(slp, w, args, flush, steps, warmup, n_sample=None, profile=Tru
         stream = torch.cuda.current_stream()
         kind = slp.SLP_INPUT_NODAL_MAG
         rel_l2, n_checked = _parity(slp, plan, w, kind, d_states, states, d_phi, stream, (0, N_STATES - 1),
-                                    n_sample)
+                                    n_sample, triangles=bool(integration))
         for i in range(warmup):
             flush.fill_(float(i))
             plan.eval(kind, d_states[i % N_STATES], d_phi, stream)
@@ -368,6 +385,8 @@ def _plain_config(slp, w, args, flush, steps, warmup, n_sample=None, profile=Tru
                "kernel_mode": ["auto", "radial", "separable", "expsum"][info["kernel_mode"]],
                "near_mode": ["auto", "on_the_fly", "precomputed"][info["near_mode"]],
                "tolerance": w.tolerance, "rel_l2": rel_l2, "parity_targets": n_checked,
+               "discretisation": "triangle integrals, element charges" if integration else
+                                 f"{w.quad}-point quadrature",
                "parity_ok": rel_l2 <= w.tolerance, "plan_s": round(t_plan, 2),
                "gpu_launches": info["launches_per_eval"] * steps}
         if profile:
@@ -395,6 +414,8 @@ def run_suite(args):
     # the paper's own smooth kernel (exponential sum of Gaussians) on the sphere workload
     suite["sphere_expsum_kernel"] = _plain_config(slp, workloads.sphere(tolerance=1e-4), args, flush, 50, 5,
                                                   kernel_mode=slp.SLP_KERNEL_EXPSUM)
+    # the paper's discretisation: element charges, triangle-integrated gridding matrix, exact near field
+    suite["sphere_triangle_integrals"] = _plain_config(slp, workloads.sphere(), args, flush, 50, 5, integration=1)
     del flush
     torch.cuda.empty_cache()
     suite["cfg3_batched"] = run_batched(args, emit=False, steps=10, warmup=3)
@@ -626,8 +647,8 @@ def run_batched(args, emit=True, steps=None, warmup=None):
             h, rec = slp.slp_plan_autotune(V, T, q, 1e-5, o, reps=3)
             plans.append(h)
             c = rec["candidates"][rec["chosen"]]
-            tune.append({"mesh": name, "grid": c["grid"], "ms": round(c["ms"], 4), "autotuned": True,
-                         "kernel_mode": c["kernel_mode"], "candidates": len(rec["candidates"])})
+            tune.append({"mesh": name, "autotuned": True, "candidates": len(rec["candidates"]),
+                         **{k: (round(v, 4) if k == "ms" else v) for k, v in c.items()}})
         for m in sts:
             plan_of.append(pi)
             d_in.append(torch.as_tensor(m, dtype=torch.float32, device="cuda"))

@@ -147,11 +147,16 @@ typedef struct {
                              second sparse product.  Grids of at most 2^27 points and triangles up to
                              24 - 2m grid cells across; otherwise SLP_ERR_UNSUPPORTED */
     int spread_table;     /* FP32 spread with m <= 4: 1 reads each source's window values from a
-                             plan-time table (3 x 2m floats per source, 96 bytes at m = 4) instead of evaluating the window per group, 0 evaluates
-                             them, -1 automatic (the table from 2^18 sources: measured faster there,
-                             while on smaller meshes its extra traffic slows the concurrent
-                             near-field product more than it saves) */
-    int reserved[2];
+                             plan-time table (3 x 2m floats per source, 96 bytes at m = 4) instead
+                             of evaluating the window per group; 0 or -1 (automatic) evaluates them.
+                             Alone the table spread is 7-13 % faster, but its streamed table loads
+                             wait behind a concurrent near-field product that saturates HBM (the
+                             2000 x 500 x 20 plate: 1.28 against 0.91 ms per evaluation), so only
+                             the autotuner, which times both, turns it on */
+    int gather_item_targets;  /* most targets per gather work item: 32 or 64; 0 automatic (64, or 32 when
+                                 items of 64 would give fewer than four per SM) */
+    int spread_blocks;        /* FP32 spread with m <= 4: register budget for 4 or 5 blocks per SM; 0
+                                 automatic (4 where cell groups hold >= 8 sources on average, else 5) */
 } slp_plan_opts;
 
 typedef struct {
@@ -195,6 +200,7 @@ typedef struct {
     int expsum_terms;            /* EXPSUM: Gaussians kept in the smooth kernel (S'); 0 otherwise */
     int integration;             /* opts.integration of the plan */
     int64_t grid_matrix_nnz;     /* integration = 1: entries of the gridding matrix A */
+    int64_t grid_matrix_rows;    /* integration = 1: grid points A reaches (its rows) */
     int64_t near_tri_nnz;        /* integration = 1: (target, triangle) entries of the near-field matrix */
 } slp_info;
 
@@ -309,22 +315,33 @@ slp_status slp_batch_destroy(slp_batch_t batch);
 slp_status slp_eval_batched(int n, const slp_plan_t *plans, int input_kind, const void *const *d_in,
                             void *const *d_phi, const int *n_states_each, void *stream);
 
-/* ---- Grid autotuner ----
- * Considers equal-spacing grids whose largest axis spans 32, 64, ..., 512
- * cells (powers of two per axis), drops grids that cannot meet the tolerance
- * (allow_grid_raise is forced off), ranks the rest by a cost model from
- * host-only plans (grid points, near-field pairs, sources), builds the two
- * cheapest on the opts' device, times `reps` evaluations of each with nodal
- * input, and returns the faster plan in *out.  info (may be NULL) receives every candidate's grid
- * and mean milliseconds and the index chosen.  The remaining opts apply to
- * every candidate. */
-#define SLP_TUNE_MAX 8
+/* ---- Autotuner ----
+ * Grid: considers equal-spacing grids whose largest axis spans 32, 64, ...,
+ * 512 cells (powers of two per axis), drops grids that cannot meet the
+ * tolerance (allow_grid_raise is forced off), ranks the rest by a cost model
+ * from host-only plans (grid points, near-field pairs, sources), builds the
+ * two cheapest on the opts' device and times `reps` evaluations of each with
+ * nodal input.  Then, from the faster one, one knob at a time (coordinate
+ * descent): the spread's window source (table or evaluated) and register
+ * budget (4 or 5 blocks per SM), the gather item size (32 or 64 targets) and
+ * the FFT pass arrangement (separate, fused plane passes, fused column
+ * passes), each alternative built and timed, and kept when faster than the
+ * incumbent by more than 1 %.  Knobs the plan does not use (FP64, wide
+ * windows) are skipped.  Returns the fastest plan in *out; info (may be NULL)
+ * receives every timed candidate's settings and mean milliseconds and the
+ * index chosen.  Options other than the tuned ones apply to every
+ * candidate. */
+#define SLP_TUNE_MAX 16
 typedef struct {
     int n_candidates;
     int chosen;
     int grid[SLP_TUNE_MAX][3];
     double ms[SLP_TUNE_MAX];
     int kernel_mode[SLP_TUNE_MAX];
+    int spread_table[SLP_TUNE_MAX];         /* 1: window tables */
+    int spread_blocks[SLP_TUNE_MAX];        /* 4 or 5; 0 when the spread has no such build */
+    int gather_item_targets[SLP_TUNE_MAX];
+    int fft_passes[SLP_TUNE_MAX];           /* 0 separate, 1 fused plane passes, 2 fused column passes */
 } slp_tune_info;
 slp_status slp_plan_autotune(const slp_mesh *mesh, int quadrature, double tolerance, const slp_plan_opts *opts,
                              int reps, slp_plan_t *out, slp_tune_info *info);

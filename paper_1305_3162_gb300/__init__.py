@@ -63,21 +63,26 @@ class slp_plan_opts(ctypes.Structure):
                 ("device", ctypes.c_int), ("allow_grid_raise", ctypes.c_int), ("check_mesh", ctypes.c_int),
                 ("fuse_plane_passes", ctypes.c_int), ("fuse_column_passes", ctypes.c_int),
                 ("check_finite", ctypes.c_int), ("integration", ctypes.c_int), ("spread_table", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("gather_item_targets", ctypes.c_int), ("spread_blocks", ctypes.c_int)]
 
 
-SLP_TUNE_MAX = 8
+SLP_TUNE_MAX = 16
 
 
 class slp_tune_info(ctypes.Structure):
     _fields_ = [("n_candidates", ctypes.c_int), ("chosen", ctypes.c_int),
                 ("grid", (ctypes.c_int * 3) * SLP_TUNE_MAX), ("ms", ctypes.c_double * SLP_TUNE_MAX),
-                ("kernel_mode", ctypes.c_int * SLP_TUNE_MAX)]
+                ("kernel_mode", ctypes.c_int * SLP_TUNE_MAX), ("spread_table", ctypes.c_int * SLP_TUNE_MAX),
+                ("spread_blocks", ctypes.c_int * SLP_TUNE_MAX), ("gather_item_targets", ctypes.c_int * SLP_TUNE_MAX),
+                ("fft_passes", ctypes.c_int * SLP_TUNE_MAX)]
 
     def to_dict(self):
         n = self.n_candidates
         return {"chosen": self.chosen,
-                "candidates": [{"grid": list(self.grid[i]), "ms": self.ms[i], "kernel_mode": self.kernel_mode[i]}
+                "candidates": [{"grid": list(self.grid[i]), "ms": self.ms[i], "kernel_mode": self.kernel_mode[i],
+                                "spread_table": self.spread_table[i], "spread_blocks": self.spread_blocks[i],
+                                "gather_item_targets": self.gather_item_targets[i],
+                                "fft_passes": ["separate", "fused plane", "fused column"][self.fft_passes[i]]}
                                for i in range(n)]}
 
 
@@ -115,7 +120,7 @@ class slp_info(ctypes.Structure):
                 ("fused_column_passes", ctypes.c_int), ("gather_item_targets", ctypes.c_int),
                 ("spread_blocks_per_sm", ctypes.c_int), ("spread_table", ctypes.c_int),
                 ("expsum_terms", ctypes.c_int), ("integration", ctypes.c_int), ("grid_matrix_nnz", ctypes.c_int64),
-                ("near_tri_nnz", ctypes.c_int64)]
+                ("grid_matrix_rows", ctypes.c_int64), ("near_tri_nnz", ctypes.c_int64)]
 
     def to_dict(self):
         out = {}

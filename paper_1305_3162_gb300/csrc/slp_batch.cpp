@@ -368,9 +368,59 @@ slp_status slp_plan_autotune(const slp_mesh *mesh, int quadrature, double tolera
     cudaEventCreate(&e1);
     slp_plan_t best = nullptr;
     double best_ms = 1e300;
+    slp_plan_opts best_o = o;
     int ntried = 0;
     slp_tune_info ti;
     memset(&ti, 0, sizeof ti);
+    // build the plan of `oc`, time reps evaluations after one warm-up, record
+    // it, and keep it when faster than the incumbent by more than `margin`
+    auto trial = [&](const slp_plan_opts &oc, double margin) -> bool {
+        if (ntried >= SLP_TUNE_MAX) return false;
+        slp_plan_opts o2 = oc;
+        slp_plan_t pl = nullptr;
+        if (slp_plan(mesh, quadrature, tolerance, &o2, &pl) != SLP_OK) return false;
+        slp_info inf;
+        slp_query(pl, &inf);
+        if (best) {
+            // an option the plan cannot use resolves to the incumbent's settings: nothing to time
+            slp_info bi;
+            slp_query(best, &bi);
+            const bool same = inf.grid[0] == bi.grid[0] && inf.grid[1] == bi.grid[1] && inf.grid[2] == bi.grid[2] &&
+                              inf.spread_table == bi.spread_table && inf.spread_blocks_per_sm == bi.spread_blocks_per_sm &&
+                              inf.gather_item_targets == bi.gather_item_targets &&
+                              inf.fused_plane_passes == bi.fused_plane_passes &&
+                              inf.fused_column_passes == bi.fused_column_passes;
+            if (same) {
+                slp_destroy(pl);
+                return false;
+            }
+        }
+        slp_status st = slp_eval(pl, SLP_INPUT_NODAL_MAG, d_in, d_out, s);
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < reps && st == SLP_OK; ++r) st = slp_eval(pl, SLP_INPUT_NODAL_MAG, d_in, d_out, s);
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (st == SLP_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        const int k = ntried++;
+        for (int d = 0; d < 3; ++d) ti.grid[k][d] = inf.grid[d];
+        ti.ms[k] = st == SLP_OK ? ms : -1.0;
+        ti.kernel_mode[k] = inf.kernel_mode;
+        ti.spread_table[k] = inf.spread_table;
+        ti.spread_blocks[k] = inf.spread_blocks_per_sm;
+        ti.gather_item_targets[k] = inf.gather_item_targets;
+        ti.fft_passes[k] = inf.fused_plane_passes ? 1 : (inf.fused_column_passes ? 2 : 0);
+        if (st == SLP_OK && ms < best_ms * (1.0 - margin)) {
+            if (best) slp_destroy(best);
+            best = pl;
+            best_ms = ms;
+            best_o = oc;
+            ti.chosen = k;
+            return true;
+        }
+        slp_destroy(pl);
+        return false;
+    };
     // candidates, ranked by a cost model evaluated on host-only plans:
     // t ~ 2.5e-11 s per grid point (five FFT passes) + 2.5e-13 s per near pair
     // visited + 2.4e-10 s per source (spread), fitted on GB300 measurements;
@@ -401,32 +451,45 @@ slp_status slp_plan_autotune(const slp_mesh *mesh, int quadrature, double tolera
     }
     std::sort(cands.begin(), cands.end(), [](const Cand &a, const Cand &b2) { return a.model < b2.model; });
     if (cands.size() > 2) cands.resize(2);
-    for (const Cand &cand : cands) {
-        if (ntried >= SLP_TUNE_MAX) break;
-        slp_plan_opts oc = cand.o;
-        slp_plan_t p = nullptr;
-        if (slp_plan(mesh, quadrature, tolerance, &oc, &p) != SLP_OK) continue;
-        // time reps evaluations (after one warm-up)
-        slp_status st = slp_eval(p, SLP_INPUT_NODAL_MAG, d_in, d_out, s);
-        cudaEventRecord(e0, s);
-        for (int r = 0; r < reps && st == SLP_OK; ++r) st = slp_eval(p, SLP_INPUT_NODAL_MAG, d_in, d_out, s);
-        cudaEventRecord(e1, s);
-        float ms = 0.f;
-        if (st == SLP_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-        ms /= reps;
-        slp_info inf;
-        slp_query(p, &inf);
-        for (int d = 0; d < 3; ++d) ti.grid[ntried][d] = inf.grid[d];
-        ti.ms[ntried] = st == SLP_OK ? ms : -1.0;
-        ti.kernel_mode[ntried] = inf.kernel_mode;
-        ++ntried;
-        if (st == SLP_OK && ms < best_ms) {
-            if (best) slp_destroy(best);
-            best = p;
-            best_ms = ms;
-            ti.chosen = ntried - 1;
-        } else {
-            slp_destroy(p);
+    for (const Cand &cand : cands) trial(cand.o, 0.0);
+    if (best) {
+        // one knob at a time from the best grid, with the resolved settings as
+        // the starting point
+        slp_info bi;
+        slp_query(best, &bi);
+        slp_plan_opts cur = best_o;
+        cur.spread_table = bi.spread_table;
+        cur.gather_item_targets = bi.gather_item_targets;
+        cur.spread_blocks = bi.spread_blocks_per_sm;
+        cur.fuse_plane_passes = bi.fused_plane_passes;
+        cur.fuse_column_passes = bi.fused_column_passes;
+        best_o = cur;
+        const bool fp32_groups = bi.precision == 32 && bi.m <= 4;
+        if (fp32_groups) {
+            slp_plan_opts t = best_o;
+            t.spread_table = 1 - best_o.spread_table;
+            trial(t, 0.01);
+            t = best_o;
+            t.spread_blocks = best_o.spread_blocks == 4 ? 5 : 4;
+            trial(t, 0.01);
+        }
+        {
+            slp_plan_opts t = best_o;
+            t.gather_item_targets = best_o.gather_item_targets == 64 ? 32 : 64;
+            trial(t, 0.01);
+        }
+        {
+            // the FFT pass arrangements other than the current one (a fused form the
+            // plan cannot use falls back to separate passes and is not tried)
+            const int cur_form = best_o.fuse_plane_passes ? 1 : (best_o.fuse_column_passes ? 2 : 0);
+            const slp_plan_opts base = best_o;
+            for (int form = 0; form < 3; ++form) {
+                if (form == cur_form) continue;
+                slp_plan_opts t = base;
+                t.fuse_plane_passes = form == 1;
+                t.fuse_column_passes = form == 2;
+                trial(t, 0.01);
+            }
         }
     }
     ti.n_candidates = ntried;

@@ -199,6 +199,7 @@ namespace {
 // many sources per spread cell group (at least 8 on average): the FP32 spread
 // for m <= 4 then runs at 4 blocks per SM with 64 registers, else at 5 with 48
 bool spread_dense(const slp_plan_s &p) {
+    if (p.opts.spread_blocks) return p.opts.spread_blocks == 4;
     return p.sgroups.size() > 0 && (double)p.Q >= 8.0 * (double)p.sgroups.size();
 }
 
@@ -1186,8 +1187,7 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     TRY(upload(p, &ptr, p.sgroup_cell.data(), p.sgroup_cell.size()));
     d.sgroup_cell = (const int *)ptr;
     d.wtab = nullptr;
-    if (sizeof(T) == 4 && p.m <= 4 && p.Q > 0 &&
-        (p.opts.spread_table > 0 || (p.opts.spread_table < 0 && p.Q >= (1 << 18)))) {
+    if (sizeof(T) == 4 && p.m <= 4 && p.Q > 0 && p.opts.spread_table > 0) {
         // FP32 table spread: window values of every sorted source, built once here
         void *wt = nullptr;
         TRY(dalloc(p, &wt, sizeof(float) * (size_t)p.Q * slp::spread_table_row(p.m)));
@@ -2166,9 +2166,17 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
     }
     // gather items of GATHER_CHUNK targets, or of half that when the full
     // size leaves fewer than four items per SM (small, latency-bound gathers)
-    p->gather_chunk = slp::GATHER_CHUNK;
+    if (o.gather_item_targets != 0 && o.gather_item_targets != 32 && o.gather_item_targets != 64) {
+        delete p;
+        return fail(SLP_ERR_INVALID_ARG, "gather_item_targets must be 0, 32 or 64");
+    }
+    if (o.spread_blocks != 0 && o.spread_blocks != 4 && o.spread_blocks != 5) {
+        delete p;
+        return fail(SLP_ERR_INVALID_ARG, "spread_blocks must be 0, 4 or 5");
+    }
+    p->gather_chunk = o.gather_item_targets ? o.gather_item_targets : slp::GATHER_CHUNK;
     tile_items(p->tgt_grid, tkeys, p->N, p->TSg, p->gather_chunk, p->gather_items);
-    if (p->gather_items.size() < 4 * 152) {
+    if (o.gather_item_targets == 0 && p->gather_items.size() < 4 * 152) {
         p->gather_chunk = slp::GATHER_CHUNK / 2;
         tile_items(p->tgt_grid, tkeys, p->N, p->TSg, p->gather_chunk, p->gather_items);
     }
@@ -2290,6 +2298,7 @@ slp_status slp_query(slp_plan_t p, slp_info *info) {
     info->expsum_terms = p->kernel_mode == SLP_KERNEL_EXPSUM ? (int)p->es_w.size() : 0;
     info->integration = p->opts.integration ? 1 : 0;
     info->grid_matrix_nnz = p->am_nnz;
+    info->grid_matrix_rows = p->dp.am_rows;
     info->near_tri_nnz = p->nt_nnz;
     return SLP_OK;
 }
