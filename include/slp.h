@@ -117,8 +117,15 @@ typedef struct {
     int m;                /* Kaiser-Bessel half-width in grid cells; 0 = from the tolerance */
     int kernel_mode;      /* SLP_KERNEL_* */
     int near_mode;        /* SLP_NEAR_* */
-    int deterministic;    /* 1: near-field sums in a fixed order (the spread still adds tiles with
-                             atomics, so results repeat to rounding level, not bitwise) */
+    int deterministic;    /* 1: every sum in a fixed order, so an evaluation repeats bitwise whatever
+                             runs beside it: the near field per work item in item order, and the spread
+                             as a product with a precomputed point gridding matrix (entry (r, k) the
+                             window product of source k at grid point r, 8 bytes per entry, (2m)^3
+                             entries per source, rows in ascending source order) in place of the
+                             tiled spread's atomics; the matrix is built when it needs at most 24 GiB
+                             and half of the free memory (slp_info.deterministic_spread), else the
+                             spread keeps its atomics and results repeat to rounding level.  Plans
+                             with opts.integration are deterministic in either setting */
     int device;           /* CUDA device ordinal; -1 builds a host-only plan (slp_query works,
                              slp_eval returns SLP_ERR_NO_DEVICE) */
     int allow_grid_raise; /* 1: raise a grid that cannot meet the tolerance (else error) */
@@ -202,6 +209,8 @@ typedef struct {
     int64_t grid_matrix_nnz;     /* integration = 1: entries of the gridding matrix A */
     int64_t grid_matrix_rows;    /* integration = 1: grid points A reaches (its rows) */
     int64_t near_tri_nnz;        /* integration = 1: (target, triangle) entries of the near-field matrix */
+    int deterministic_spread;    /* 1: deterministic point plan whose spread is the precomputed point gridding
+                                    matrix (then grid_matrix_nnz/rows describe that matrix) */
 } slp_info;
 
 /* Fill opts with defaults: precision 32, automatic grid/m/kernel/near mode,

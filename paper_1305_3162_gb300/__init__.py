@@ -120,7 +120,8 @@ class slp_info(ctypes.Structure):
                 ("fused_column_passes", ctypes.c_int), ("gather_item_targets", ctypes.c_int),
                 ("spread_blocks_per_sm", ctypes.c_int), ("spread_table", ctypes.c_int),
                 ("expsum_terms", ctypes.c_int), ("integration", ctypes.c_int), ("grid_matrix_nnz", ctypes.c_int64),
-                ("grid_matrix_rows", ctypes.c_int64), ("near_tri_nnz", ctypes.c_int64)]
+                ("grid_matrix_rows", ctypes.c_int64), ("near_tri_nnz", ctypes.c_int64),
+                ("deterministic_spread", ctypes.c_int)]
 
     def to_dict(self):
         out = {}

@@ -336,6 +336,90 @@ __global__ void __launch_bounds__(256) k_nmt_build(TriBuildN b, int pass, int64_
     if (pass == 0 && lane == 0) counts[t] = cnt;
 }
 
+// ---------------------------------------------------------------- point gridding matrix (deterministic mode)
+// For plans with opts.deterministic the spread of the point sources is also a
+// precomputed sparse product: entry (r, k) = prod_q psi(r_q - u_{k,q}) over
+// the 2m^3 box of sorted source k, stored by grid point with the sources of a
+// row in ascending order, applied to the charges w_k sigma_k.  Every grid
+// point is then written once with a sum in a fixed order, where the tiled
+// spread adds tiles with atomics in whatever order the blocks finish.
+__device__ __forceinline__ void point_box(const PointBuild &b, int64_t k, int &cx, int &cy, int &cz, double3 &f) {
+    const double4 g = b.src[k];
+    const int c = (int)g.w;
+    cx = c & 1023;
+    cy = (c >> 10) & 1023;
+    cz = (c >> 20) & 1023;
+    f = make_double3(g.x, g.y, g.z);
+}
+
+__global__ void k_pmat_count(PointBuild b, int *__restrict__ cnt) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= b.Q) return;
+    int cx, cy, cz;
+    double3 f;
+    point_box(b, k, cx, cy, cz, f);
+    const int W = 2 * b.m;
+    for (int iz = 0; iz < W; ++iz)
+        for (int iy = 0; iy < W; ++iy)
+            for (int ix = 0; ix < W; ++ix) {
+                const int x = (((cx - b.m + 1 + ix) % b.L[0]) + b.L[0]) % b.L[0];
+                const int y = (((cy - b.m + 1 + iy) % b.L[1]) + b.L[1]) % b.L[1];
+                const int z = (((cz - b.m + 1 + iz) % b.L[2]) + b.L[2]) % b.L[2];
+                atomicAdd(cnt + ((int64_t)z * b.L[1] + y) * b.L[0] + x, 1);
+            }
+}
+
+template <typename T>
+__global__ void k_pmat_fill(PointBuild b, const int *__restrict__ slot_of, const int64_t *__restrict__ rowptr,
+                            int *__restrict__ cursor, int *__restrict__ col, T *__restrict__ val) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= b.Q) return;
+    int cx, cy, cz;
+    double3 f;
+    point_box(b, k, cx, cy, cz, f);
+    const int W = 2 * b.m;
+    double w[3][16];
+    const double fr[3] = {f.x, f.y, f.z};
+    for (int q = 0; q < 3; ++q)
+        for (int i = 0; i < W; ++i) w[q][i] = kb_window(fr[q] + double(b.m - 1 - i), 1.0 / b.m, b.beta, b.isb);
+    for (int iz = 0; iz < W; ++iz)
+        for (int iy = 0; iy < W; ++iy)
+            for (int ix = 0; ix < W; ++ix) {
+                const int x = (((cx - b.m + 1 + ix) % b.L[0]) + b.L[0]) % b.L[0];
+                const int y = (((cy - b.m + 1 + iy) % b.L[1]) + b.L[1]) % b.L[1];
+                const int z = (((cz - b.m + 1 + iz) % b.L[2]) + b.L[2]) % b.L[2];
+                const int slot = slot_of[((int64_t)z * b.L[1] + y) * b.L[0] + x];
+                if (slot < 0) {
+                    set_error(b.err, DEV_ERR_BAD_INDEX);
+                    continue;
+                }
+                const int64_t pos = rowptr[slot] + atomicAdd(cursor + slot, 1);
+                if (pos >= rowptr[slot + 1]) {
+                    set_error(b.err, DEV_ERR_BAD_INDEX);
+                    continue;
+                }
+                col[pos] = (int)k;
+                val[pos] = (T)(w[0][ix] * w[1][iy] * w[2][iz]);
+            }
+}
+
+cudaError_t launch_pmat_count(const PointBuild &b, int *cnt, cudaStream_t s) {
+    if (b.Q == 0) return cudaSuccess;
+    k_pmat_count<<<(unsigned)((b.Q + 255) / 256), 256, 0, s>>>(b, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pmat_fill(const PointBuild &b, int prec, const int *slot_of, const int64_t *rowptr, int *cursor,
+                             int *col, void *val, cudaStream_t s) {
+    if (b.Q == 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((b.Q + 127) / 128);
+    if (prec == 64)
+        k_pmat_fill<double><<<nb, 128, 0, s>>>(b, slot_of, rowptr, cursor, col, (double *)val);
+    else
+        k_pmat_fill<float><<<nb, 128, 0, s>>>(b, slot_of, rowptr, cursor, col, (float *)val);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- evaluation
 // g_j = (n_j / 3) . (m_a + m_b + m_c): the integral mean of m . n_j for P1 m
 template <typename T>

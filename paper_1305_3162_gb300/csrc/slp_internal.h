@@ -147,6 +147,8 @@ struct DevPlan {
     const void *tri_n3;     // T4 [M] outward unit normal / 3
     void *gbuf;             // T [M] element charges of the current input (scratch)
     // gridding matrix A, CSR over the grid points the triangles' boxes reach
+    // (deterministic point plans: the point gridding matrix, columns = sorted sources)
+    int det_spread;         // 1: the point spread is the sparse product with am_* applied to qbuf
     int64_t am_rows;
     const int64_t *am_rowptr, *am_row;  // [am_rows + 1], [am_rows] grid linear index
     const int *am_col;                  // triangle of each entry
@@ -199,6 +201,17 @@ struct TriBuildN {
     int np;
     int *err;
 };
+// Plan-time inputs of the point gridding matrix of deterministic plans (FP64).
+struct PointBuild {
+    const double4 *src;  // [Q] sorted sources: fractional grid coordinate (x, y, z) and packed cell (w)
+    int64_t Q;
+    int m, L[3];
+    double beta, isb;
+    int *err;
+};
+cudaError_t launch_pmat_count(const PointBuild &b, int *cnt, cudaStream_t s);
+cudaError_t launch_pmat_fill(const PointBuild &b, int prec, const int *slot_of, const int64_t *rowptr, int *cursor,
+                             int *col, void *val, cudaStream_t s);
 cudaError_t launch_amat_count(const TriBuildA &b, int *cnt, cudaStream_t s);
 cudaError_t launch_amat_fill(const TriBuildA &b, int prec, const int *slot_of, const int64_t *rowptr, int *cursor,
                              int *col, void *val, cudaStream_t s);

@@ -1567,6 +1567,77 @@ void tri_rule(int n, std::vector<double> &ra, std::vector<double> &rb, std::vect
         }
 }
 
+// Deterministic point plans: the gridding matrix of the sorted point sources,
+// CSR over grid points, the entries of a row in ascending source order (the
+// spread then writes every grid point once, with a fixed summation order).
+// Kept when it needs at most 24 GiB and half of the free device memory;
+// otherwise the plan keeps the tiled spread (results repeat to rounding level).
+template <typename T> slp_status build_point_matrix(slp_plan_s &p) {
+    const int64_t G = (int64_t)p.L[0] * p.L[1] * p.L[2];
+    const int64_t W = 2 * p.m;
+    const size_t need = (size_t)p.Q * W * W * W * (sizeof(T) + sizeof(int));
+    size_t freeb = 0, totb = 0;
+    cudaMemGetInfo(&freeb, &totb);
+    if (G > ((int64_t)1 << 28) || need > ((size_t)24 << 30) || need > freeb / 2) return SLP_OK;
+    std::vector<double4> src(p.Q);
+    for (int64_t k = 0; k < p.Q; ++k)
+        src[k] = make_double4(p.src_grid[4 * k], p.src_grid[4 * k + 1], p.src_grid[4 * k + 2], p.src_grid[4 * k + 3]);
+    TmpBuf b_src, b_cnt;
+    TRY(tmp_upload(b_src, src.data(), src.size()));
+    {
+        std::vector<int> zeros(G, 0);
+        TRY(tmp_upload(b_cnt, zeros.data(), zeros.size()));
+    }
+    slp::PointBuild pb;
+    memset(&pb, 0, sizeof pb);
+    pb.src = (const double4 *)b_src.p;
+    pb.Q = p.Q;
+    pb.m = p.m;
+    for (int d = 0; d < 3; ++d) pb.L[d] = p.L[d];
+    pb.beta = KB_B * p.m;
+    pb.isb = 1.0 / std::sinh(pb.beta);
+    pb.err = p.dp.err;
+    TRY(cuda_status(slp::launch_pmat_count(pb, (int *)b_cnt.p, 0), "point gridding matrix count"));
+    TRY(cuda_status(cudaDeviceSynchronize(), "point gridding matrix count"));
+    std::vector<int> cnt(G), slot_of(G, -1);
+    TRY(cuda_status(cudaMemcpy(cnt.data(), b_cnt.p, sizeof(int) * G, cudaMemcpyDeviceToHost), "count copy"));
+    std::vector<int64_t> rowptr(1, 0), rowidx;
+    for (int64_t g = 0; g < G; ++g)
+        if (cnt[g] > 0) {
+            slot_of[g] = (int)rowidx.size();
+            rowidx.push_back(g);
+            rowptr.push_back(rowptr.back() + cnt[g]);
+        }
+    const int64_t nrows = (int64_t)rowidx.size(), nnz = rowptr.back();
+    void *ptr = nullptr;
+    TRY(upload(p, &ptr, rowptr.data(), rowptr.size()));
+    p.dp.am_rowptr = (const int64_t *)ptr;
+    TRY(upload(p, &ptr, rowidx.data(), rowidx.size()));
+    p.dp.am_row = (const int64_t *)ptr;
+    TRY(dalloc(p, &ptr, sizeof(int) * (size_t)std::max<int64_t>(nnz, 1)));
+    p.dp.am_col = (const int *)ptr;
+    TRY(dalloc(p, &ptr, sizeof(T) * (size_t)std::max<int64_t>(nnz, 1)));
+    p.dp.am_val = ptr;
+    p.dp.am_rows = nrows;
+    TmpBuf b_slot, b_cur;
+    TRY(tmp_upload(b_slot, slot_of.data(), slot_of.size()));
+    {
+        std::vector<int> z(std::max<int64_t>(nrows, 1), 0);
+        TRY(tmp_upload(b_cur, z.data(), z.size()));
+    }
+    TRY(cuda_status(slp::launch_pmat_fill(pb, p.prec, (const int *)b_slot.p, p.dp.am_rowptr, (int *)b_cur.p,
+                                          (int *)p.dp.am_col, (void *)p.dp.am_val, 0), "point gridding matrix fill"));
+    TRY(cuda_status(slp::launch_csr_sort(nrows, p.prec, p.dp.am_rowptr, (int *)p.dp.am_col, (void *)p.dp.am_val, 0),
+                    "point gridding matrix order"));
+    TRY(cuda_status(cudaDeviceSynchronize(), "point gridding matrix fill"));
+    int code = 0;
+    TRY(cuda_status(cudaMemcpy(&code, p.dp.err, sizeof(int), cudaMemcpyDeviceToHost), "status"));
+    if (code != 0) return fail(SLP_ERR_CUDA, "point gridding matrix: device status word %d", code);
+    p.am_nnz = nnz;
+    p.dp.det_spread = 1;
+    return SLP_OK;
+}
+
 // Triangle-integrated plans: the gridding matrix A (CSR over grid points) and
 // the near-field matrix over triangles (CSR over sorted targets), both
 // assembled on the device in FP64 and stored at the plan precision.
@@ -1797,7 +1868,10 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
     // nodal input with the precomputed near field: the charges are only needed
     // by the spread, which computes them itself
     const bool use_matrix = !tri && kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
-    const bool fuse = use_matrix && last > SLP_STAGE_CHARGES;
+    // deterministic point plans: the spread is the sparse product with the
+    // point gridding matrix, which reads the charges from qbuf
+    const bool det = !tri && d.det_spread;
+    const bool fuse = use_matrix && !det && last > SLP_STAGE_CHARGES;
     const bool concurrent = ex != nullptr && prof == nullptr && last >= SLP_STAGE_NEAR;
     const size_t es = p.prec == 64 ? 8 : 4;
     const size_t part_bytes = (es * (size_t)p.N + 15) / 16 * 16;
@@ -1844,10 +1918,10 @@ slp_status run_pipeline(slp_plan_s &p, const slp::DevPlan &d, int kind, const vo
         if (tl) TRY(cuda_status(cudaEventRecord(tl[3], ex->aux), "timeline"));
         TRY(cuda_status(cudaEventRecord(ex->join, ex->aux), "join"));
     }
-    if (tri)
+    if (tri || det)
         TRY(timed(SLOT_SPREAD, s, [&] {
-            return slp::launch_csr_apply(p.prec, 8, d.am_rows, d.am_rowptr, d.am_row, d.am_col, d.am_val, gch,
-                                         d.gridA, s);
+            return slp::launch_csr_apply(p.prec, 8, d.am_rows, d.am_rowptr, d.am_row, d.am_col, d.am_val,
+                                         tri ? gch : d.qbuf, d.gridA, s);
         }, "gridding matrix"));
     else
         TRY(timed(SLOT_SPREAD, s, [&] { return slp::launch_spread(d, fuse ? kind : -1, d_in, s); }, "spread"));
@@ -1911,8 +1985,10 @@ slp_status run_pipeline(slp_plan_s &p, int kind, const void *d_in, void *d_phi, 
 // state.
 slp_status run_states(slp_plan_s &p, const slp::DevPlan &d, int kind, const void *const *ins, void *const *outs,
                       int S, cudaStream_t s, SlpExec *ex, int *launches) {
-    const bool use_matrix =
-        !p.opts.integration && kind == SLP_INPUT_NODAL_MAG && p.near_mode == SLP_NEAR_PRECOMPUTED;
+    // the state-batched far field uses the tiled spread; deterministic point
+    // plans evaluate their states one by one
+    const bool use_matrix = !p.opts.integration && !d.det_spread && kind == SLP_INPUT_NODAL_MAG &&
+                            p.near_mode == SLP_NEAR_PRECOMPUTED;
     if (!use_matrix || !ex) {
         for (int k = 0; k < S; ++k) {
             TRY(run_pipeline(p, d, kind, ins[k], outs[k], s, SLP_STAGE_NEAR, nullptr, ex));
@@ -2204,6 +2280,8 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
             st = p->prec == 64 ? build_tri_matrices<double>(*p, tkeys) : build_tri_matrices<float>(*p, tkeys);
         else if (st == SLP_OK && o.near_mode != SLP_NEAR_ON_THE_FLY)
             st = build_near_matrix(*p, tkeys);
+        if (st == SLP_OK && o.deterministic && !o.integration)
+            st = p->prec == 64 ? build_point_matrix<double>(*p) : build_point_matrix<float>(*p);
         if (st == SLP_OK && slp_exec_create(p->exec) != cudaSuccess) st = fail(SLP_ERR_CUDA, "stream creation failed");
         if (st != SLP_OK) {
             free_device(*p);
@@ -2299,6 +2377,7 @@ slp_status slp_query(slp_plan_t p, slp_info *info) {
     info->integration = p->opts.integration ? 1 : 0;
     info->grid_matrix_nnz = p->am_nnz;
     info->grid_matrix_rows = p->dp.am_rows;
+    info->deterministic_spread = p->dp.det_spread;
     info->near_tri_nnz = p->nt_nnz;
     return SLP_OK;
 }

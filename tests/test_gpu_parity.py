@@ -134,19 +134,28 @@ def test_repeat_and_host_entry_point():
         slp.slp_destroy(plan)
 
 
-def test_deterministic_mode_bitwise():
+@pytest.mark.parametrize("prec,tol", [(32, 1e-5), (64, 1e-10)])
+def test_deterministic_mode_bitwise(prec, tol):
+    """deterministic = 1: the spread is the product with the point gridding
+    matrix and the near field sums in item order, so the same input gives
+    the same bits on every evaluation, with other evaluations (another state,
+    sigma input) run in between, for nodal and sigma inputs."""
     slp = lib()
     V, T = meshes.icosphere(3)
     m = fields.vortex(V, 6)
-    plan = _plan(slp, V, T, 7, 1e-5, 32, (64, 64, 64), deterministic=1)
+    sigma = fields.random_sigma(T.shape[0] * 7, 8)
+    plan = _plan(slp, V, T, 7, tol, prec, (64, 64, 64), deterministic=1)
     try:
-        a = run(slp, plan, 2, m, 32)
-        ref = oracle.slp_nodal(V, T, 7, m)
-        assert rel_l2(a, ref) <= 1e-5
-        # near field is bitwise repeatable; the spread still uses atomics, so
-        # compare at rounding level
-        b = run(slp, plan, 2, m, 32)
-        assert rel_l2(a, b) < 1e-6
+        info = slp.slp_query(plan)
+        assert info["deterministic_spread"] == 1 and info["grid_matrix_nnz"] == T.shape[0] * 7 * (2 * info["m"]) ** 3
+        a = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, m, prec)
+        assert rel_l2(a, oracle.slp_nodal(V, T, 7, m)) <= tol
+        s1 = run(slp, plan, slp.SLP_INPUT_SIGMA, sigma, prec)
+        assert rel_l2(s1, oracle.slp(V, T, 7, oracle.KIND_SIGMA, sigma)) <= tol
+        run(slp, plan, slp.SLP_INPUT_NODAL_MAG, fields.vortex(V, 7), prec)
+        b = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, m, prec)
+        s2 = run(slp, plan, slp.SLP_INPUT_SIGMA, sigma, prec)
+        assert np.array_equal(a, b) and np.array_equal(s1, s2)
     finally:
         slp.slp_destroy(plan)
 

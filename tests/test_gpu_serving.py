@@ -11,13 +11,14 @@ from tests.gpu_util import lib, rel_l2, torch_cuda
 pytestmark = pytest.mark.gpu
 
 
-def _plans(slp):
+def _plans(slp, deterministic=0):
     specs = [(*meshes.icosphere(3), 7, (64, 64, 64)), (*meshes.cube(10), 3, (64, 64, 64)),
              (*meshes.torus(2.0, 0.5, 48, 16), 3, (64, 64, 32))]
     plans = []
     for V, T, q, g in specs:
         o = slp.slp_default_opts()
         o.precision = 32
+        o.deterministic = deterministic
         for d in range(3):
             o.grid[d] = g[d]
         plans.append(slp.slp_plan(V, T, q, 1e-5, o))
@@ -30,10 +31,14 @@ def _pinned(a):
     return t
 
 
-def test_result_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("deterministic", [0, 1], ids=["default", "deterministic"])
+def test_result_same_alone_and_in_the_mix(deterministic):
+    """The probe request alone and inside a mix of 40 concurrent requests:
+    within 1e-6 by default (the tiled spread adds with atomics), bitwise
+    equal with deterministic plans."""
     slp = lib()
     torch = torch_cuda()
-    specs, plans = _plans(slp)
+    specs, plans = _plans(slp, deterministic)
     o = slp.slp_server_default_opts()
     o.slots_per_plan = 2
     o.hbm_budget_bytes = 1 << 30
@@ -68,6 +73,8 @@ def test_result_same_alone_and_in_the_mix():
             assert slp.slp_server_wait(server, rid2, 120.0) == slp.SLP_REQ_DONE
         mix = h_mix.numpy().astype(np.float64)
         assert rel_l2(mix, alone) <= 1e-6
+        if deterministic:
+            assert np.array_equal(mix, alone)
         st = slp.slp_server_stats(server)
         assert st["completed"] == 41 and st["rejected"] == 0
         assert st["max_inflight"] >= 2  # requests overlapped on the device
