@@ -254,6 +254,21 @@ slp_status slp_eval_states(slp_plan_t plan, int input_kind, int n_states, const 
  * Page-locked host memory gives asynchronous copies. */
 slp_status slp_eval_host(slp_plan_t plan, int input_kind, const void *h_in, void *h_phi, void *stream);
 
+/* Pipelined host-buffer evaluation: enqueues, without waiting, the copy of
+ * h_in into one of the plan's two staging slots (on an internal copy-in
+ * stream), the evaluation (on `stream`) and the copy of phi into h_phi (on
+ * an internal copy-out stream), alternating slots, so that the copy-in of the
+ * next call and the copy-out of the previous one overlap this evaluation.
+ * h_in must stay unchanged and h_phi unread until slp_eval_host_wait returns;
+ * page-locked memory keeps the copies asynchronous.  Calls on one plan come
+ * from one host thread; the staging slots are allocated with the plan.
+ * Errors: INVALID_ARG, NO_DEVICE, UNSUPPORTED, CUDA. */
+slp_status slp_eval_host_async(slp_plan_t plan, int input_kind, const void *h_in, void *h_phi, void *stream);
+
+/* Blocks until the results of every earlier slp_eval_host_async call on the
+ * plan are in host memory. */
+slp_status slp_eval_host_wait(slp_plan_t plan);
+
 /* Allocation-free evaluation for callers that cannot call cudaMalloc where
  * they need phi: host code running inside another framework's memory pool,
  * which forbids raw device allocations, and solver loops that must not touch

@@ -137,7 +137,8 @@ class slp_info(ctypes.Structure):
 _lib = None
 
 #: C entry points the binding requires (the declarations of include/slp.h and include/slp_debug.h)
-EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_states", "slp_eval_host", "slp_query", "slp_query_points",
+EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_states", "slp_eval_host", "slp_eval_host_async",
+            "slp_eval_host_wait", "slp_query", "slp_query_points",
             "slp_check", "slp_destroy", "slp_status_string", "slp_last_error",
             "slp_debug_run", "slp_debug_copy", "slp_debug_buffer_bytes", "slp_debug_host_count",
             "slp_debug_host_array", "slp_debug_window", "slp_debug_window_hat", "slp_debug_profile",
@@ -170,6 +171,8 @@ def load():
                       ctypes.POINTER(vp)], St),
         "slp_eval": ([vp, ctypes.c_int, vp, vp, vp], St),
         "slp_eval_host": ([vp, ctypes.c_int, vp, vp, vp], St),
+        "slp_eval_host_async": ([vp, ctypes.c_int, vp, vp, vp], St),
+        "slp_eval_host_wait": ([vp], St),
         "slp_eval_states": ([vp, ctypes.c_int, ctypes.c_int, vp, vp, vp], St),
         "slp_query": ([vp, ctypes.POINTER(slp_info)], St),
         "slp_query_points": ([vp, ctypes.POINTER(ctypes.c_double)], St),
@@ -296,6 +299,16 @@ def _check_device_tensor(x, name, dtype_name, min_numel, where):
         raise SlpError(SLP_ERR_INVALID_ARG, where, f"{name} is not contiguous")
     if x.numel() < min_numel:
         raise SlpError(SLP_ERR_INVALID_ARG, where, f"{name} holds {x.numel()} elements, needs {min_numel}")
+
+
+def slp_eval_host_async(plan, input_kind: int, h_in, h_phi, stream=None):
+    """Pipelined host-buffer evaluation (results valid after slp_eval_host_wait)."""
+    _check(load().slp_eval_host_async(plan, int(input_kind), _ptr(h_in), _ptr(h_phi), _stream(stream)),
+           "slp_eval_host_async")
+
+
+def slp_eval_host_wait(plan):
+    _check(load().slp_eval_host_wait(plan), "slp_eval_host_wait")
 
 
 def slp_eval_direct_static(d_vertices, n_vertices, d_triangles, n_triangles, quadrature, precision, input_kind,

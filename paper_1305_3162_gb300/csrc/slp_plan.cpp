@@ -1254,6 +1254,10 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
     // staging buffers for slp_eval_host
     TRY(dalloc(p, &p.d_stage_in, sizeof(T) * 3 * std::max(p.Q, p.N)));
     TRY(dalloc(p, &p.d_stage_phi, sizeof(T) * p.N));
+    for (int k = 0; k < 2; ++k) {
+        TRY(dalloc(p, &p.d_astage_in[k], sizeof(T) * 3 * std::max(p.Q, p.N)));
+        TRY(dalloc(p, &p.d_astage_phi[k], sizeof(T) * p.N));
+    }
     // on-the-fly near field: charges, spread, 5 FFT passes (3 when the plane
     // passes are fused), gather, and either zeroing + atomic near field or
     // near field + ordered reduction
@@ -1267,6 +1271,13 @@ void free_device(slp_plan_s &p) {
     cudaGetDevice(&prev);
     cudaSetDevice(p.device);
     slp_exec_destroy(p.exec);
+    for (int k = 0; k < 2; ++k) {
+        if (p.ev_in[k]) cudaEventDestroy(p.ev_in[k]);
+        if (p.ev_eval[k]) cudaEventDestroy(p.ev_eval[k]);
+        if (p.ev_out[k]) cudaEventDestroy(p.ev_out[k]);
+    }
+    if (p.cs_in) cudaStreamDestroy(p.cs_in);
+    if (p.cs_out) cudaStreamDestroy(p.cs_out);
     for (void *a : p.allocs) cudaFree(a);
     p.allocs.clear();
     cudaSetDevice(prev);
@@ -2283,6 +2294,15 @@ slp_status slp_plan(const slp_mesh *mesh, int quadrature, double tolerance, cons
         if (st == SLP_OK && o.deterministic && !o.integration)
             st = p->prec == 64 ? build_point_matrix<double>(*p) : build_point_matrix<float>(*p);
         if (st == SLP_OK && slp_exec_create(p->exec) != cudaSuccess) st = fail(SLP_ERR_CUDA, "stream creation failed");
+        if (st == SLP_OK) {
+            bool ok = cudaStreamCreateWithFlags(&p->cs_in, cudaStreamNonBlocking) == cudaSuccess &&
+                      cudaStreamCreateWithFlags(&p->cs_out, cudaStreamNonBlocking) == cudaSuccess;
+            for (int k = 0; k < 2 && ok; ++k)
+                ok = cudaEventCreateWithFlags(&p->ev_in[k], cudaEventDisableTiming) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&p->ev_eval[k], cudaEventDisableTiming) == cudaSuccess &&
+                     cudaEventCreateWithFlags(&p->ev_out[k], cudaEventDisableTiming) == cudaSuccess;
+            if (!ok) st = fail(SLP_ERR_CUDA, "copy stream creation failed");
+        }
         if (st != SLP_OK) {
             free_device(*p);
             delete p;
@@ -2334,6 +2354,41 @@ slp_status slp_eval_host(slp_plan_t p, int kind, const void *h_in, void *h_phi, 
     TRY(cuda_status(cudaMemcpyAsync(h_phi, p->d_stage_phi, (size_t)p->N * es, cudaMemcpyDeviceToHost, s), "copy out"));
     TRY(cuda_status(cudaStreamSynchronize(s), "synchronize"));
     return SLP_OK;
+}
+
+slp_status slp_eval_host_async(slp_plan_t p, int kind, const void *h_in, void *h_phi, void *stream) {
+    if (!p) return fail(SLP_ERR_INVALID_ARG, "plan is NULL");
+    if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan cannot evaluate");
+    TRY(slp_check_kind(*p, kind));
+    if (!h_in || !h_phi) return fail(SLP_ERR_INVALID_ARG, "input or output pointer is NULL");
+    DeviceGuard g(p->device);
+    const size_t es = p->prec == 64 ? 8 : 4;
+    const size_t nin = (size_t)slp_input_count(*p, kind);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int k = p->aslot;
+    p->aslot ^= 1;
+    // copy-in: after the evaluation that last read this slot
+    TRY(cuda_status(cudaStreamWaitEvent(p->cs_in, p->ev_eval[k], 0), "copy-in wait"));
+    TRY(cuda_status(cudaMemcpyAsync(p->d_astage_in[k], h_in, nin * es, cudaMemcpyHostToDevice, p->cs_in), "copy in"));
+    TRY(cuda_status(cudaEventRecord(p->ev_in[k], p->cs_in), "copy-in event"));
+    // evaluation: after its input arrived and the copy-out that last read this slot's phi
+    TRY(cuda_status(cudaStreamWaitEvent(s, p->ev_in[k], 0), "evaluation wait"));
+    TRY(cuda_status(cudaStreamWaitEvent(s, p->ev_out[k], 0), "evaluation wait"));
+    TRY(run_pipeline(*p, kind, p->d_astage_in[k], p->d_astage_phi[k], s, SLP_STAGE_NEAR));
+    TRY(cuda_status(cudaEventRecord(p->ev_eval[k], s), "evaluation event"));
+    // copy-out
+    TRY(cuda_status(cudaStreamWaitEvent(p->cs_out, p->ev_eval[k], 0), "copy-out wait"));
+    TRY(cuda_status(cudaMemcpyAsync(h_phi, p->d_astage_phi[k], (size_t)p->N * es, cudaMemcpyDeviceToHost, p->cs_out),
+                    "copy out"));
+    TRY(cuda_status(cudaEventRecord(p->ev_out[k], p->cs_out), "copy-out event"));
+    return SLP_OK;
+}
+
+slp_status slp_eval_host_wait(slp_plan_t p) {
+    if (!p) return fail(SLP_ERR_INVALID_ARG, "plan is NULL");
+    if (p->device < 0) return SLP_OK;
+    DeviceGuard g(p->device);
+    return cuda_status(cudaStreamSynchronize(p->cs_out), "synchronize copy-out");
 }
 
 slp_status slp_query(slp_plan_t p, slp_info *info) {

@@ -85,6 +85,12 @@ struct slp_plan_s {
     std::vector<void *> allocs;
     int64_t bytes_device = 0;
     void *d_stage_in = nullptr, *d_stage_phi = nullptr;
+    // pipelined host-buffer evaluations: two staging slots, copy streams and
+    // the events that order them (copy-in k -> evaluation k -> copy-out k)
+    void *d_astage_in[2] = {nullptr, nullptr}, *d_astage_phi[2] = {nullptr, nullptr};
+    cudaStream_t cs_in = nullptr, cs_out = nullptr;
+    cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_eval[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+    int aslot = 0;
     int *d_blk_first = nullptr;
     int launches_per_eval = 0;
     int64_t near_pairs_within = -1;

@@ -10,7 +10,7 @@ import pytest
 
 import oracle
 from synthetic import fields, meshes, workloads
-from tests.gpu_util import lib, rel_l2, run
+from tests.gpu_util import lib, rel_l2, run, torch_cuda
 
 pytestmark = pytest.mark.gpu
 
@@ -350,5 +350,28 @@ def test_expsum_kernel_mode_at_the_papers_accuracy(body, level, grid, prec, near
         _, wk, _ = oracle.sources(V, T, q)
         phi_s = run(slp, plan, slp.SLP_INPUT_SIGMA, sig / wk, prec)
         assert rel_l2(phi_s, phi) <= (1e-5 if prec == 32 else 1e-10)
+    finally:
+        slp.slp_destroy(plan)
+
+
+def test_pipelined_host_evaluation_matches_device_evaluation():
+    """slp_eval_host_async: six states through the two staging slots (copy-in,
+    evaluation and copy-out on separate streams, each call's output in its own
+    page-locked buffer) give the results of slp_eval on the same states."""
+    slp = lib()
+    torch = torch_cuda()
+    V, T = meshes.icosphere(3)
+    plan = _plan(slp, V, T, 7, 1e-5, 32, (64, 64, 64))
+    try:
+        states = [fields.vortex(V, 40 + i) for i in range(6)]
+        h_in = [torch.as_tensor(m.ravel(), dtype=torch.float32).pin_memory() for m in states]
+        h_out = [torch.full((V.shape[0],), float("nan"), dtype=torch.float32).pin_memory() for _ in states]
+        stream = torch.cuda.current_stream()
+        for a, b in zip(h_in, h_out):
+            slp.slp_eval_host_async(plan, slp.SLP_INPUT_NODAL_MAG, a, b, stream)
+        slp.slp_eval_host_wait(plan)
+        for m, b in zip(states, h_out):
+            ref = run(slp, plan, slp.SLP_INPUT_NODAL_MAG, m, 32)
+            assert rel_l2(b.numpy().astype(np.float64), ref) < 1e-6
     finally:
         slp.slp_destroy(plan)
