@@ -254,6 +254,35 @@ slp_status slp_eval_states(slp_plan_t plan, int input_kind, int n_states, const 
  * Page-locked host memory gives asynchronous copies. */
 slp_status slp_eval_host(slp_plan_t plan, int input_kind, const void *h_in, void *h_phi, void *stream);
 
+/* ---- Evaluation at other points (probes) ----
+ * The paper evaluates phi_2 at every finite-element node, the interior ones
+ * included (Sec. 2.1, Alg. 1).  A probe set attaches such points to a plan:
+ * they are sorted into the plan's grid cells and get their own gather work
+ * list and rows of the near-field operator (the vertex operator of a plan
+ * with the precomputed near field, or the triangle operator of a plan with
+ * opts.integration = 1).  points: host [n][3], read during the call.  Each
+ * point must lie in the mesh's bounding box (the period isolates that box
+ * from its images) and in the ball about the box centre through the
+ * farthest vertex (within it every source is nearer than the smooth
+ * kernel's truncation radius), else SLP_ERR_INVALID_ARG; and its window
+ * must fall on grid rows the pruned transforms compute (rows that some
+ * vertex or source window reaches; the interior of a closed mesh always
+ * does), else SLP_ERR_UNSUPPORTED.
+ * slp_eval_probe runs slp_eval on the mesh vertices (d_phi, [n_targets])
+ * and then, on the same stream, the probes' near-field product and window
+ * interpolation from the same interpolation grid (d_phi_points, [n]).  It
+ * takes NODAL_MAG input, or ELEMENT in plans with triangle integrals.
+ * Errors: INVALID_ARG, NO_DEVICE, UNSUPPORTED (a point plan without the
+ * precomputed near field, or a point off the computed rows), OOM, CUDA. */
+typedef struct slp_probe_s *slp_probe_t;
+slp_status slp_probe_create(slp_plan_t plan, const double *points, int64_t n_points, slp_probe_t *out);
+slp_status slp_eval_probe(slp_plan_t plan, slp_probe_t probe, int input_kind, const void *d_in, void *d_phi,
+                          void *d_phi_points, void *stream);
+/* Points and near-field operator entries of the probe set. */
+slp_status slp_probe_query(slp_probe_t probe, int64_t *n_points, int64_t *near_nnz);
+/* Release a probe set (before its plan).  NULL is accepted. */
+slp_status slp_probe_destroy(slp_probe_t probe);
+
 /* Pipelined host-buffer evaluation: enqueues, without waiting, the copy of
  * h_in into one of the plan's two staging slots (on an internal copy-in
  * stream), the evaluation (on `stream`) and the copy of phi into h_phi (on

@@ -173,18 +173,20 @@ def element_charges(V, T, m_nodal):
     return g
 
 
-def slp_p0(V, T, g, sel=None, nthreads: int = 0):
+def slp_p0(V, T, g, sel=None, nthreads: int = 0, x=None):
     """phi_i = (1/4pi) sum_j g_j int_{S_j} 1/|x_i - y| dA(y) at the vertices
-    (or at V[sel]), every triangle integrated exactly.  Returns phi."""
+    (or at V[sel], or at the points x [n][3] when given), every triangle
+    integrated exactly.  Returns phi."""
     V = _f64(V)
     T = _i32(T)
     g = _f64(g)
+    X = V if x is None else _f64(np.asarray(x, dtype=np.float64).reshape(-1, 3))
     if sel is None:
-        ns, sp = V.shape[0], None
+        ns, sp = X.shape[0], None
     else:
         sel = np.ascontiguousarray(sel, dtype=np.int64)
         ns, sp = sel.shape[0], _p(sel, ctypes.c_int64)
     phi = np.zeros(ns)
-    _load().slpo_direct_p0(_p(V), sp, ns, _p(V), V.shape[0], _p(T, ctypes.c_int32), T.shape[0], _p(g), _p(phi),
+    _load().slpo_direct_p0(_p(X), sp, ns, _p(V), V.shape[0], _p(T, ctypes.c_int32), T.shape[0], _p(g), _p(phi),
                            int(nthreads))
     return phi

@@ -138,7 +138,8 @@ _lib = None
 
 #: C entry points the binding requires (the declarations of include/slp.h and include/slp_debug.h)
 EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_states", "slp_eval_host", "slp_eval_host_async",
-            "slp_eval_host_wait", "slp_query", "slp_query_points",
+            "slp_eval_host_wait", "slp_probe_create", "slp_eval_probe", "slp_probe_query", "slp_probe_destroy",
+            "slp_query", "slp_query_points",
             "slp_check", "slp_destroy", "slp_status_string", "slp_last_error",
             "slp_debug_run", "slp_debug_copy", "slp_debug_buffer_bytes", "slp_debug_host_count",
             "slp_debug_host_array", "slp_debug_window", "slp_debug_window_hat", "slp_debug_profile",
@@ -173,6 +174,10 @@ def load():
         "slp_eval_host": ([vp, ctypes.c_int, vp, vp, vp], St),
         "slp_eval_host_async": ([vp, ctypes.c_int, vp, vp, vp], St),
         "slp_eval_host_wait": ([vp], St),
+        "slp_probe_create": ([vp, ctypes.POINTER(ctypes.c_double), I64, ctypes.POINTER(vp)], St),
+        "slp_eval_probe": ([vp, vp, ctypes.c_int, vp, vp, vp, vp], St),
+        "slp_probe_query": ([vp, ctypes.POINTER(I64), ctypes.POINTER(I64)], St),
+        "slp_probe_destroy": ([vp], St),
         "slp_eval_states": ([vp, ctypes.c_int, ctypes.c_int, vp, vp, vp], St),
         "slp_query": ([vp, ctypes.POINTER(slp_info)], St),
         "slp_query_points": ([vp, ctypes.POINTER(ctypes.c_double)], St),
@@ -305,6 +310,32 @@ def slp_eval_host_async(plan, input_kind: int, h_in, h_phi, stream=None):
     """Pipelined host-buffer evaluation (results valid after slp_eval_host_wait)."""
     _check(load().slp_eval_host_async(plan, int(input_kind), _ptr(h_in), _ptr(h_phi), _stream(stream)),
            "slp_eval_host_async")
+
+
+def slp_probe_create(plan, points):
+    """Attach evaluation points (host [n][3]) to a plan; returns the probe handle."""
+    pts = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    out = ctypes.c_void_p()
+    _check(load().slp_probe_create(plan, pts.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), pts.shape[0],
+                                   ctypes.byref(out)), "slp_probe_create")
+    return out
+
+
+def slp_eval_probe(plan, probe, input_kind, d_in, d_phi, d_phi_points, stream=None):
+    """slp_eval at the mesh vertices plus the probe points from the same evaluation."""
+    _check(load().slp_eval_probe(plan, probe, int(input_kind), _ptr(d_in), _ptr(d_phi), _ptr(d_phi_points),
+                                 _stream(stream)), "slp_eval_probe")
+
+
+def slp_probe_query(probe) -> dict:
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().slp_probe_query(probe, ctypes.byref(a), ctypes.byref(b)), "slp_probe_query")
+    return {"n_points": a.value, "near_nnz": b.value}
+
+
+def slp_probe_destroy(probe):
+    if probe is not None:
+        _check(load().slp_probe_destroy(probe), "slp_probe_destroy")
 
 
 def slp_eval_host_wait(plan):

@@ -1325,6 +1325,82 @@ struct NearCandidates {
     std::vector<int2> ranges;
 };
 
+// Bins of the sorted targets (vertices): runs of one aligned 2x2x2-cell block,
+// contiguous in the sort, with their bounding boxes.
+struct TargetBins {
+    struct Bin {
+        int b, e;
+        double lo[3], hi[3];
+    };
+    std::vector<Bin> bins;
+    std::unordered_map<uint64_t, int> bin_of;
+};
+
+void target_bins(const slp_plan_s &p, const std::vector<uint64_t> &tkeys, const std::vector<double4> &tgt,
+                 TargetBins &tb) {
+    const int64_t N = p.N;
+    tb.bins.clear();
+    tb.bin_of.clear();
+    for (int64_t i = 0; i < N;) {
+        int64_t j = i;
+        const uint64_t bk = tkeys[i] >> 3;
+        while (j < N && (tkeys[j] >> 3) == bk) ++j;
+        TargetBins::Bin bn;
+        bn.b = (int)i;
+        bn.e = (int)j;
+        for (int d = 0; d < 3; ++d) {
+            bn.lo[d] = 1e300;
+            bn.hi[d] = -1e300;
+        }
+        for (int64_t k = i; k < j; ++k) {
+            const double x[3] = {tgt[k].x, tgt[k].y, tgt[k].z};
+            for (int d = 0; d < 3; ++d) {
+                bn.lo[d] = std::min(bn.lo[d], x[d]);
+                bn.hi[d] = std::max(bn.hi[d], x[d]);
+            }
+        }
+        const uint32_t packed = (uint32_t)p.tgt_grid[4 * i + 3];
+        const uint64_t bx = (packed & 1023) / 2, by = ((packed >> 10) & 1023) / 2, bz = ((packed >> 20) & 1023) / 2;
+        tb.bin_of[(bz << 40) | (by << 20) | bx] = (int)tb.bins.size();
+        tb.bins.push_back(bn);
+        i = j;
+    }
+}
+
+// Append to `ranges` the runs of sorted vertices in bins within rad of the box [lo, hi].
+void bins_within(const slp_plan_s &p, const TargetBins &tb, const double *lo, const double *hi, double rad,
+                 std::vector<int2> &ranges) {
+    const size_t first = ranges.size();
+    int b0[3], b1[3];
+    for (int d = 0; d < 3; ++d) {
+        const double h = p.P[d] / p.L[d];
+        const double u0 = (lo[d] - rad) / h + 0.5 * p.L[d], u1 = (hi[d] + rad) / h + 0.5 * p.L[d];
+        b0[d] = std::max(0, (int)std::floor(u0) - 1) / 2;
+        b1[d] = std::min(p.L[d] - 1, (int)std::floor(u1) + 1) / 2;
+    }
+    std::vector<int> found;
+    for (int bz = b0[2]; bz <= b1[2]; ++bz)
+        for (int by = b0[1]; by <= b1[1]; ++by)
+            for (int bx = b0[0]; bx <= b1[0]; ++bx) {
+                auto itb = tb.bin_of.find(((uint64_t)bz << 40) | ((uint64_t)by << 20) | (uint64_t)bx);
+                if (itb == tb.bin_of.end()) continue;
+                const TargetBins::Bin &bn = tb.bins[itb->second];
+                double d2 = 0;
+                for (int d = 0; d < 3; ++d) {
+                    const double g = std::max(0.0, std::max(bn.lo[d] - hi[d], lo[d] - bn.hi[d]));
+                    d2 += g * g;
+                }
+                if (d2 <= rad * rad) found.push_back(itb->second);
+            }
+    std::sort(found.begin(), found.end(), [&](int a2, int b2) { return tb.bins[a2].b < tb.bins[b2].b; });
+    for (int f : found) {
+        if (ranges.size() > first && ranges.back().y == tb.bins[f].b)
+            ranges.back().y = tb.bins[f].e;
+        else
+            ranges.push_back(make_int2(tb.bins[f].b, tb.bins[f].e));
+    }
+}
+
 void near_candidates(const slp_plan_s &p, const std::vector<uint64_t> &tkeys, double rad, bool all_pairs,
                      NearCandidates &c) {
     const int64_t N = p.N, M = p.M;
@@ -1354,39 +1430,8 @@ void near_candidates(const slp_plan_s &p, const std::vector<uint64_t> &tkeys, do
     blk_r0.assign(nblk + 1, 0);
     std::vector<int2> &ranges = c.ranges;
     ranges.clear();
-    struct Bin {
-        int b, e;
-        double lo[3], hi[3];
-    };
-    std::vector<Bin> bins;
-    std::unordered_map<uint64_t, int> bin_of;
-    if (!all_pairs) {
-        for (int64_t i = 0; i < N;) {
-            int64_t j = i;
-            const uint64_t bk = tkeys[i] >> 3;
-            while (j < N && (tkeys[j] >> 3) == bk) ++j;
-            Bin bn;
-            bn.b = (int)i;
-            bn.e = (int)j;
-            for (int d = 0; d < 3; ++d) {
-                bn.lo[d] = 1e300;
-                bn.hi[d] = -1e300;
-            }
-            for (int64_t k = i; k < j; ++k) {
-                const double x[3] = {tgt[k].x, tgt[k].y, tgt[k].z};
-                for (int d = 0; d < 3; ++d) {
-                    bn.lo[d] = std::min(bn.lo[d], x[d]);
-                    bn.hi[d] = std::max(bn.hi[d], x[d]);
-                }
-            }
-            const uint32_t packed = (uint32_t)p.tgt_grid[4 * i + 3];
-            const uint64_t bx = (packed & 1023) / 2, by = ((packed >> 10) & 1023) / 2, bz = ((packed >> 20) & 1023) / 2;
-            bin_of[(bz << 40) | (by << 20) | bx] = (int)bins.size();
-            bins.push_back(bn);
-            i = j;
-        }
-    }
-    std::vector<int> found;
+    TargetBins tb;
+    if (!all_pairs) target_bins(p, tkeys, tgt, tb);
     for (int b = 0; b < nblk; ++b) {
         const slp::NearItem &it = p.near_items[p.near_blk_first[b]];
         for (int t = it.tbegin; t < it.tbegin + it.tcount; ++t) tgt_block[t] = b;
@@ -1403,37 +1448,9 @@ void near_candidates(const slp_plan_s &p, const std::vector<uint64_t> &tkeys, do
                 hi[d] = std::max(hi[d], x[d]);
             }
         }
-        int b0[3], b1[3];
-        for (int d = 0; d < 3; ++d) {
-            const double h = p.P[d] / p.L[d];
-            const double u0 = (lo[d] - rad) / h + 0.5 * p.L[d], u1 = (hi[d] + rad) / h + 0.5 * p.L[d];
-            b0[d] = std::max(0, (int)std::floor(u0) - 1) / 2;
-            b1[d] = std::min(p.L[d] - 1, (int)std::floor(u1) + 1) / 2;
-        }
-        found.clear();
-        for (int bz = b0[2]; bz <= b1[2]; ++bz)
-            for (int by = b0[1]; by <= b1[1]; ++by)
-                for (int bx = b0[0]; bx <= b1[0]; ++bx) {
-                    auto itb = bin_of.find(((uint64_t)bz << 40) | ((uint64_t)by << 20) | (uint64_t)bx);
-                    if (itb == bin_of.end()) continue;
-                    const Bin &bn = bins[itb->second];
-                    double d2 = 0;
-                    for (int d = 0; d < 3; ++d) {
-                        const double g = std::max(0.0, std::max(bn.lo[d] - hi[d], lo[d] - bn.hi[d]));
-                        d2 += g * g;
-                    }
-                    if (d2 <= rad * rad) found.push_back(itb->second);
-                }
-        std::sort(found.begin(), found.end(), [&](int a2, int b2) { return bins[a2].b < bins[b2].b; });
-        for (int f : found) {
-            if ((int)ranges.size() > blk_r0[b] && ranges.back().y == bins[f].b)
-                ranges.back().y = bins[f].e;
-            else
-                ranges.push_back(make_int2(bins[f].b, bins[f].e));
-        }
+        bins_within(p, tb, lo, hi, rad, ranges);
     }
     blk_r0[nblk] = (int)ranges.size();
-
 }
 
 slp_status build_near_matrix(slp_plan_s &p, const std::vector<uint64_t> &tkeys) {
@@ -1832,6 +1849,297 @@ template <typename T> slp_status build_tri_matrices(slp_plan_s &p, const std::ve
     p.near_mode = SLP_NEAR_PRECOMPUTED;
     // element charges (nodal input), gridding product, 5 FFT passes, near-field product, gather
     p.launches_per_eval = 9;
+    return SLP_OK;
+}
+
+}  // namespace
+
+// A probe set: extra evaluation points of a plan (see slp_probe_create).
+struct slp_probe_s {
+    slp_plan_s *plan = nullptr;
+    int device = 0;
+    int64_t n = 0;
+    int64_t near_nnz = 0;
+    slp::DevPlan view;            // the plan's view with the probes as targets
+    std::vector<void *> allocs;
+};
+
+namespace {
+
+template <typename T> slp_status probe_build(slp_plan_s &p, const double *pts, int64_t n, slp_probe_s &pr) {
+    typedef typename V4<T>::t T4;
+    const bool tri = p.opts.integration != 0;
+    // sorted probes in the plan's cells, their gather items
+    std::vector<int32_t> perm;
+    std::vector<double> grid;
+    std::vector<uint64_t> keys;
+    sort_points(p, pts, n, p.TSg, perm, grid, keys);
+    // every probe's window rows must lie in the region the transforms compute
+    {
+        const int Ly = p.L[1], Lz = p.L[2], m = p.m;
+        auto in_iv = [](int v, int start, int len, int L) { return ((v - start) % L + L) % L < len; };
+        for (int64_t i = 0; i < n; ++i) {
+            const uint32_t pk = (uint32_t)grid[4 * i + 3];
+            const int cy = (pk >> 10) & 1023, cz = (pk >> 20) & 1023;
+            for (int oz = -m + 1; oz <= m; ++oz) {
+                const int z = ((cz + oz) % Lz + Lz) % Lz;
+                bool ok = in_iv(z, p.z0, p.nz_act, Lz);
+                for (int oy = -m + 1; ok && oy <= m; ++oy)
+                    ok = in_iv(((cy + oy) % Ly + Ly) % Ly, p.plane_iv[z].x, p.plane_iv[z].y, Ly);
+                if (!ok)
+                    return fail(SLP_ERR_UNSUPPORTED, "point %lld lies outside the grid rows this plan transforms",
+                                (long long)perm[i]);
+            }
+        }
+    }
+    std::vector<slp::TileItem> items;
+    tile_items(grid, keys, n, p.TSg, p.gather_chunk, items);
+    std::stable_sort(items.begin(), items.end(),
+                     [](const slp::TileItem &a, const slp::TileItem &b) { return a.end - a.begin > b.end - b.begin; });
+    auto alloc_up = [&](void **dst, const void *src, size_t bytes) -> slp_status {
+        const cudaError_t e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? SLP_ERR_OOM : SLP_ERR_CUDA, "probe allocation: %s",
+                        cudaGetErrorString(e));
+        }
+        pr.allocs.push_back(*dst);
+        if (src && bytes) TRY(cuda_status(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice), "probe upload"));
+        return SLP_OK;
+    };
+    slp::DevPlan v = p.dp;
+    v.N = n;
+    v.ks = 1;
+    std::vector<T4> tg(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const double *g = &grid[4 * i];
+        tg[i].x = (T)g[0];
+        tg[i].y = (T)g[1];
+        tg[i].z = (T)g[2];
+        uint32_t pk = (uint32_t)g[3];
+        if (sizeof(T) == 4) {
+            float f;
+            memcpy(&f, &pk, 4);
+            tg[i].w = (T)f;
+        } else {
+            tg[i].w = (T)pk;
+        }
+        if (tg[i].x >= T(1)) tg[i].x = std::nextafter(T(1), T(0));
+        if (tg[i].y >= T(1)) tg[i].y = std::nextafter(T(1), T(0));
+        if (tg[i].z >= T(1)) tg[i].z = std::nextafter(T(1), T(0));
+    }
+    void *ptr = nullptr;
+    TRY(alloc_up(&ptr, tg.data(), sizeof(T4) * n));
+    v.tgt_grid = ptr;
+    TRY(alloc_up(&ptr, perm.data(), sizeof(int32_t) * n));
+    v.tgt_perm = (const int *)ptr;
+    TRY(alloc_up(&ptr, items.data(), sizeof(slp::TileItem) * items.size()));
+    v.gather_items = (const slp::TileItem *)ptr;
+    v.n_gather = (int)items.size();
+    TRY(alloc_up(&ptr, nullptr, sizeof(T) * ((n + 3) / 4 * 4)));
+    v.phi_part = ptr;
+
+    // near-field candidates: blocks of 32 consecutive sorted probes, the plan's
+    // vertex bins within eps plus the largest triangle (or quadrature point) reach
+    std::vector<double4> ptg(n);
+    for (int64_t i = 0; i < n; ++i) {
+        const double *x = &pts[3 * (int64_t)perm[i]];
+        ptg[i] = make_double4(x[0] - p.ctr[0], x[1] - p.ctr[1], x[2] - p.ctr[2], 0.0);
+    }
+    double reach = 0.0;
+    for (int64_t j = 0; j < p.M; ++j)
+        for (int a = 0; a < 3; ++a) {
+            const double *u = &p.V[3 * (int64_t)p.T[3 * j + a]], *w = &p.V[3 * (int64_t)p.T[3 * j + (a + 1) % 3]];
+            reach = std::max(reach, std::sqrt((u[0] - w[0]) * (u[0] - w[0]) + (u[1] - w[1]) * (u[1] - w[1]) +
+                                              (u[2] - w[2]) * (u[2] - w[2])));
+        }
+    const bool all_pairs = p.kernel_mode == SLP_KERNEL_SEPARABLE || !(p.eps < p.diam);
+    const double rad = all_pairs ? INFINITY : p.eps + reach * (1.0 + 1e-9) + 1e-12 * p.diam;
+    NearCandidates cand;
+    {
+        std::vector<uint64_t> tkeys;
+        std::vector<int32_t> tperm;
+        std::vector<double> tgrid;
+        sort_points(p, p.V.data(), p.N, p.TSg, tperm, tgrid, tkeys);
+        near_candidates(p, tkeys, rad, all_pairs, cand);  // vertex adjacency and bins of the plan's targets
+        TargetBins tb;
+        if (!all_pairs) target_bins(p, tkeys, cand.tgt, tb);
+        const int64_t nblk = (n + 31) / 32;
+        cand.tgt_block.assign(n, 0);
+        cand.blk_r0.assign(nblk + 1, 0);
+        cand.ranges.clear();
+        for (int64_t b = 0; b < nblk; ++b) {
+            cand.blk_r0[b] = (int)cand.ranges.size();
+            double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+            for (int64_t t = 32 * b; t < std::min(n, 32 * b + 32); ++t) {
+                cand.tgt_block[t] = (int)b;
+                const double x[3] = {ptg[t].x, ptg[t].y, ptg[t].z};
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = std::min(lo[d], x[d]);
+                    hi[d] = std::max(hi[d], x[d]);
+                }
+            }
+            if (all_pairs)
+                cand.ranges.push_back(make_int2(0, (int)p.N));
+            else
+                bins_within(p, tb, lo, hi, rad, cand.ranges);
+        }
+        cand.blk_r0[nblk] = (int)cand.ranges.size();
+    }
+    TmpBuf b_blk, b_r0, b_rng, b_vtp, b_vte, b_cnt, b_pairs;
+    TRY(tmp_upload(b_blk, cand.tgt_block.data(), cand.tgt_block.size()));
+    TRY(tmp_upload(b_r0, cand.blk_r0.data(), cand.blk_r0.size()));
+    TRY(tmp_upload(b_rng, cand.ranges.data(), std::max<size_t>(cand.ranges.size(), 1)));
+    TRY(tmp_upload(b_vtp, cand.vt_ptr.data(), cand.vt_ptr.size()));
+    TRY(tmp_upload(b_vte, cand.vt_ent.data(), cand.vt_ent.size()));
+    {
+        std::vector<int64_t> z(n + 1, 0);
+        TRY(tmp_upload(b_cnt, z.data(), z.size()));
+        TRY(tmp_upload(b_pairs, z.data(), z.size()));
+    }
+    std::vector<int64_t> cnt(n), rowptr(n + 1, 0);
+    if (tri) {
+        // rows of the triangle operator (the plan's assembly, probes as targets)
+        std::vector<double3> tg3(n), xp(p.N);
+        for (int64_t i = 0; i < n; ++i) tg3[i] = make_double3(ptg[i].x, ptg[i].y, ptg[i].z);
+        for (int64_t i = 0; i < p.N; ++i)
+            xp[i] = make_double3(p.V[3 * i] - p.ctr[0], p.V[3 * i + 1] - p.ctr[1], p.V[3 * i + 2] - p.ctr[2]);
+        std::vector<int4> trv(p.M);
+        std::vector<int> inv(p.N), tmin(p.M);
+        for (int64_t j = 0; j < p.M; ++j) trv[j] = make_int4(p.T[3 * j], p.T[3 * j + 1], p.T[3 * j + 2], 0);
+        for (int64_t i = 0; i < p.N; ++i) inv[p.tgt_perm[i]] = (int)i;
+        for (int64_t j = 0; j < p.M; ++j)
+            tmin[j] = std::min(inv[p.T[3 * j]], std::min(inv[p.T[3 * j + 1]], inv[p.T[3 * j + 2]]));
+        std::vector<double> ra, rb, rw;
+        tri_rule(8, ra, rb, rw);
+        TmpBuf b_tg, b_xp, b_tri, b_tmin, b_ra, b_rb, b_rw, b_esw, b_esg, b_h[3];
+        TRY(tmp_upload(b_tg, tg3.data(), tg3.size()));
+        TRY(tmp_upload(b_xp, xp.data(), xp.size()));
+        TRY(tmp_upload(b_tri, trv.data(), trv.size()));
+        TRY(tmp_upload(b_tmin, tmin.data(), tmin.size()));
+        TRY(tmp_upload(b_ra, ra.data(), ra.size()));
+        TRY(tmp_upload(b_rb, rb.data(), rb.size()));
+        TRY(tmp_upload(b_rw, rw.data(), rw.size()));
+        slp::TriBuildN bn;
+        memset(&bn, 0, sizeof bn);
+        bn.tgt = (const double3 *)b_tg.p;
+        bn.tgt_perm = p.dp.tgt_perm;
+        bn.tgt_block = (const int *)b_blk.p;
+        bn.blk_r0 = (const int *)b_r0.p;
+        bn.ranges = (const int2 *)b_rng.p;
+        bn.vt_ptr = (const int *)b_vtp.p;
+        bn.vt_ent = (const int *)b_vte.p;
+        bn.tri_min_sorted = (const int *)b_tmin.p;
+        bn.xphys = (const double3 *)b_xp.p;
+        bn.tri = (const int4 *)b_tri.p;
+        bn.N = n;
+        bn.eps = std::isfinite(p.eps) ? p.eps : 1e300;
+        bn.kernel_mode = p.kernel_mode;
+        bn.inv_s_sqrt2 = p.sigma_g > 0 ? 1.0 / (p.sigma_g * std::sqrt(2.0)) : 0.0;
+        if (p.kernel_mode == SLP_KERNEL_EXPSUM) {
+            std::vector<double> w(p.es_w.size()), g(p.es_g.size());
+            for (size_t k = 0; k < w.size(); ++k) {
+                w[k] = p.es_w[k] / p.P[0];
+                g[k] = p.es_g[k] / (p.P[0] * p.P[0]);
+            }
+            TRY(tmp_upload(b_esw, w.data(), w.size()));
+            TRY(tmp_upload(b_esg, g.data(), g.size()));
+            bn.es_w = (const double *)b_esw.p;
+            bn.es_g = (const double *)b_esg.p;
+            bn.es_n = (int)w.size();
+        }
+        if (p.kernel_mode == SLP_KERNEL_SEPARABLE) {
+            for (int a = 0; a < 3; ++a) {
+                TRY(tmp_upload(b_h[a], p.sep_h[a].data(), p.sep_h[a].size()));
+                bn.sep_h[a] = (const double *)b_h[a].p;
+                bn.sep_nh[a] = (int)p.sep_h[a].size();
+            }
+            bn.sep_A4pi = 4.0 * PI * p.sep_A;
+        }
+        for (int a = 0; a < 3; ++a) bn.P[a] = p.P[a];
+        bn.ra = (const double *)b_ra.p;
+        bn.rb = (const double *)b_rb.p;
+        bn.rw = (const double *)b_rw.p;
+        bn.np = (int)ra.size();
+        bn.err = p.dp.err;
+        TRY(cuda_status(slp::launch_nmt_build(bn, 0, p.prec, (int64_t *)b_cnt.p, nullptr, nullptr, nullptr, 0),
+                        "probe near count"));
+        TRY(cuda_status(cudaMemcpy(cnt.data(), b_cnt.p, sizeof(int64_t) * n, cudaMemcpyDeviceToHost), "count copy"));
+        for (int64_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + cnt[i];
+        TRY(alloc_up(&ptr, rowptr.data(), sizeof(int64_t) * (n + 1)));
+        v.nt_rowptr = (const int64_t *)ptr;
+        TRY(alloc_up(&ptr, nullptr, sizeof(int) * (size_t)std::max<int64_t>(rowptr[n], 1)));
+        v.nt_col = (const int *)ptr;
+        TRY(alloc_up(&ptr, nullptr, sizeof(T) * (size_t)std::max<int64_t>(rowptr[n], 1)));
+        v.nt_val = ptr;
+        TRY(cuda_status(slp::launch_nmt_build(bn, 1, p.prec, nullptr, v.nt_rowptr, (int *)v.nt_col, (void *)v.nt_val, 0),
+                        "probe near fill"));
+    } else {
+        // rows of the vertex operator (the plan's assembly, probes as targets)
+        std::vector<double4> src(p.Q), nrm(p.M);
+        for (int64_t k = 0; k < p.Q; ++k)
+            src[k] = make_double4(p.y[3 * k] - p.ctr[0], p.y[3 * k + 1] - p.ctr[1], p.y[3 * k + 2] - p.ctr[2], p.wk[k]);
+        for (int64_t j = 0; j < p.M; ++j) nrm[j] = make_double4(p.nrm[3 * j], p.nrm[3 * j + 1], p.nrm[3 * j + 2], 0.0);
+        TmpBuf b_tg, b_src, b_nrm, b_lam, b_h[3];
+        TRY(tmp_upload(b_tg, ptg.data(), ptg.size()));
+        TRY(tmp_upload(b_src, src.data(), src.size()));
+        TRY(tmp_upload(b_nrm, nrm.data(), nrm.size()));
+        TRY(tmp_upload(b_lam, p.lam.data(), p.lam.size()));
+        slp::NMBuild nb;
+        memset(&nb, 0, sizeof nb);
+        nb.tgt = (const double4 *)b_tg.p;
+        nb.tgt_perm = p.dp.tgt_perm;
+        nb.tgt_block = (const int *)b_blk.p;
+        nb.blk_r0 = (const int *)b_r0.p;
+        nb.ranges = (const int2 *)b_rng.p;
+        nb.vt_ptr = (const int *)b_vtp.p;
+        nb.vt_ent = (const int *)b_vte.p;
+        nb.src = (const double4 *)b_src.p;
+        nb.nrm = (const double4 *)b_nrm.p;
+        nb.lam = (const double *)b_lam.p;
+        nb.q = p.q;
+        nb.N = n;
+        nb.eps2 = std::isfinite(p.eps) ? p.eps * p.eps : 1e300;
+        nb.inv_s_sqrt2 = p.sigma_g > 0 ? 1.0 / (p.sigma_g * std::sqrt(2.0)) : 0.0;
+        nb.kernel_mode = p.kernel_mode;
+        TmpBuf b_esw, b_esg;
+        if (p.kernel_mode == SLP_KERNEL_SEPARABLE) {
+            for (int a = 0; a < 3; ++a) {
+                TRY(tmp_upload(b_h[a], p.sep_h[a].data(), p.sep_h[a].size()));
+                nb.sep_h[a] = (const double *)b_h[a].p;
+                nb.sep_nh[a] = (int)p.sep_h[a].size();
+            }
+            nb.sep_A4pi = 4.0 * PI * p.sep_A;
+        }
+        if (p.kernel_mode == SLP_KERNEL_EXPSUM) {
+            std::vector<double> w(p.es_w.size()), g(p.es_g.size());
+            for (size_t k = 0; k < w.size(); ++k) {
+                w[k] = p.es_w[k] / p.P[0];
+                g[k] = p.es_g[k] / (p.P[0] * p.P[0]);
+            }
+            TRY(tmp_upload(b_esw, w.data(), w.size()));
+            TRY(tmp_upload(b_esg, g.data(), g.size()));
+            nb.es_w = (const double *)b_esw.p;
+            nb.es_g = (const double *)b_esg.p;
+            nb.es_n = (int)w.size();
+        }
+        for (int a = 0; a < 3; ++a) nb.P[a] = p.P[a];
+        TRY(cuda_status(slp::launch_nm_build(nb, 0, p.prec, (int64_t *)b_cnt.p, (int64_t *)b_pairs.p, nullptr, nullptr, 0),
+                        "probe near count"));
+        TRY(cuda_status(cudaMemcpy(cnt.data(), b_cnt.p, sizeof(int64_t) * n, cudaMemcpyDeviceToHost), "count copy"));
+        for (int64_t i = 0; i < n; ++i) rowptr[i + 1] = rowptr[i] + cnt[i];
+        TRY(alloc_up(&ptr, rowptr.data(), sizeof(int64_t) * (n + 1)));
+        v.nm_rowptr = (const int64_t *)ptr;
+        TRY(alloc_up(&ptr, nullptr, sizeof(T4) * (size_t)std::max<int64_t>(rowptr[n], 1)));
+        v.nm_val = ptr;
+        TRY(cuda_status(slp::launch_nm_build(nb, 1, p.prec, nullptr, nullptr, v.nm_rowptr, ptr, 0), "probe near fill"));
+    }
+    TRY(cuda_status(cudaDeviceSynchronize(), "probe near build"));
+    int code = 0;
+    TRY(cuda_status(cudaMemcpy(&code, p.dp.err, sizeof(int), cudaMemcpyDeviceToHost), "status"));
+    if (code != 0) return fail(SLP_ERR_CUDA, "probe near build: device status word %d", code);
+    pr.near_nnz = rowptr[n];
+    pr.view = v;
     return SLP_OK;
 }
 
@@ -2381,6 +2689,85 @@ slp_status slp_eval_host_async(slp_plan_t p, int kind, const void *h_in, void *h
     TRY(cuda_status(cudaMemcpyAsync(h_phi, p->d_astage_phi[k], (size_t)p->N * es, cudaMemcpyDeviceToHost, p->cs_out),
                     "copy out"));
     TRY(cuda_status(cudaEventRecord(p->ev_out[k], p->cs_out), "copy-out event"));
+    return SLP_OK;
+}
+
+slp_status slp_probe_create(slp_plan_t p, const double *points, int64_t n, slp_probe_t *out) {
+    if (!out) return fail(SLP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p || !points || n < 1) return fail(SLP_ERR_INVALID_ARG, "plan, points or count missing");
+    if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan");
+    if (n > (1LL << 30)) return fail(SLP_ERR_INVALID_ARG, "too many points");
+    if (!p->opts.integration && p->near_mode != SLP_NEAR_PRECOMPUTED)
+        return fail(SLP_ERR_UNSUPPORTED, "probes need the precomputed near field or triangle integrals");
+    // the bounding box keeps the pairs clear of periodic images; the ball of
+    // diameter diam about its centre keeps every source within the distance
+    // where the truncated smooth kernel is still the smoothed 1/r
+    for (int64_t i = 0; i < n; ++i) {
+        double r2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const double x = points[3 * i + d];
+            if (!std::isfinite(x) || std::fabs(x - p->ctr[d]) > 0.5 * p->D[d] * (1.0 + 1e-9) + 1e-12 * p->diam)
+                return fail(SLP_ERR_INVALID_ARG, "point %lld lies outside the mesh's bounding box", (long long)i);
+            r2 += (x - p->ctr[d]) * (x - p->ctr[d]);
+        }
+        if (std::sqrt(r2) > 0.5 * p->diam)
+            return fail(SLP_ERR_INVALID_ARG, "point %lld lies outside the mesh's enclosing ball", (long long)i);
+    }
+    DeviceGuard g(p->device);
+    slp_probe_s *pr = new slp_probe_s();
+    pr->plan = p;
+    pr->device = p->device;
+    pr->n = n;
+    const slp_status st = p->prec == 64 ? probe_build<double>(*p, points, n, *pr) : probe_build<float>(*p, points, n, *pr);
+    if (st != SLP_OK) {
+        for (void *a : pr->allocs) cudaFree(a);
+        delete pr;
+        return st;
+    }
+    *out = pr;
+    return SLP_OK;
+}
+
+slp_status slp_eval_probe(slp_plan_t p, slp_probe_t pr, int kind, const void *d_in, void *d_phi, void *d_phi_points,
+                          void *stream) {
+    if (!p || !pr || pr->plan != p) return fail(SLP_ERR_INVALID_ARG, "plan and probe set do not belong together");
+    if (p->device < 0) return fail(SLP_ERR_NO_DEVICE, "host-only plan cannot evaluate");
+    TRY(slp_check_kind(*p, kind));
+    if (kind != SLP_INPUT_NODAL_MAG && kind != SLP_INPUT_ELEMENT)
+        return fail(SLP_ERR_UNSUPPORTED, "probes take nodal or element input");
+    if (!d_in || !d_phi || !d_phi_points) return fail(SLP_ERR_INVALID_ARG, "input or output pointer is NULL");
+    DeviceGuard g(p->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    TRY(run_pipeline(*p, kind, d_in, d_phi, s, SLP_STAGE_NEAR));
+    // the probes' near-field part, then their interpolation from the same grid B
+    const slp::DevPlan &v = pr->view;
+    if (p->opts.integration) {
+        const void *gch = kind == SLP_INPUT_ELEMENT ? d_in : p->dp.gbuf;
+        TRY(cuda_status(slp::launch_csr_apply(p->prec, 32, pr->n, v.nt_rowptr, nullptr, v.nt_col, v.nt_val, gch,
+                                              v.phi_part, s), "probe near field"));
+    } else {
+        TRY(cuda_status(slp::launch_near_matrix(v, nullptr, s), "probe near field"));
+    }
+    TRY(cuda_status(slp::launch_gather(v, d_phi_points, s), "probe gather"));
+    return SLP_OK;
+}
+
+slp_status slp_probe_query(slp_probe_t pr, int64_t *n_points, int64_t *near_nnz) {
+    if (!pr) return fail(SLP_ERR_INVALID_ARG, "probe is NULL");
+    if (n_points) *n_points = pr->n;
+    if (near_nnz) *near_nnz = pr->near_nnz;
+    return SLP_OK;
+}
+
+slp_status slp_probe_destroy(slp_probe_t pr) {
+    if (!pr) return SLP_OK;
+    {
+        DeviceGuard g(pr->device);
+        cudaDeviceSynchronize();
+        for (void *a : pr->allocs) cudaFree(a);
+    }
+    delete pr;
     return SLP_OK;
 }
 

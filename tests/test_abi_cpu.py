@@ -445,3 +445,24 @@ def test_expsum_dtab_matches_one_period_quadrature(slp):
              slp.slp_debug_window_hat(m, L[2], kz))
         assert abs(D[kz, ky, kx] * W * W - cl) <= 1e-9 * abs(cl) + 1e-14
     slp.slp_destroy(p)
+
+
+def test_probe_sets_refuse_host_only_plans_and_bad_arguments(slp):
+    V, T = meshes.cube(3)
+    p = _host_plan(slp, V, T)
+    try:
+        with pytest.raises(slp.SlpError) as e:
+            slp.slp_probe_create(p, np.zeros((4, 3)))
+        assert e.value.status == slp.SLP_ERR_NO_DEVICE
+        with pytest.raises(slp.SlpError) as e:
+            slp.slp_probe_create(p, np.zeros((0, 3)))
+        assert e.value.status == slp.SLP_ERR_INVALID_ARG
+        with pytest.raises(slp.SlpError) as e:
+            slp.slp_eval_probe(p, None, slp.SLP_INPUT_NODAL_MAG, 0, 0, 0)
+        assert e.value.status == slp.SLP_ERR_INVALID_ARG
+        with pytest.raises(slp.SlpError) as e:
+            slp.slp_probe_query(None)
+        assert e.value.status == slp.SLP_ERR_INVALID_ARG
+        slp.slp_probe_destroy(None)
+    finally:
+        slp.slp_destroy(p)

@@ -382,3 +382,28 @@ def test_oracle_p0_invariances_and_subset(oracle_lib):
     assert _rel_l2(oracle_lib.slp_p0(2.5 * V, T, g1), 2.5 * p1) < 1e-13
     sel = np.array([0, 5, 17, V.shape[0] - 1])
     assert np.array_equal(oracle_lib.slp_p0(V, T, g1, sel=sel), p1[sel])
+
+
+def test_oracle_p0_off_surface_points_match_the_sphere_potentials(oracle_lib):
+    """At points off the surface: sigma = 1 on the sphere of radius 1 gives
+    phi = 1 inside and 1/|x| outside; the uniformly magnetised sphere gives
+    z/3 inside and z/(3|x|^3) outside (Sec. 4).  The flat-facet error falls
+    at second order, as on the surface."""
+    rng = np.random.default_rng(8)
+    d = rng.normal(size=(60, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    r = np.concatenate([rng.uniform(0.0, 0.7, 30), rng.uniform(1.3, 2.0, 30)])
+    x = d * r[:, None]
+    inside = r < 1
+    ref1 = np.where(inside, 1.0, 1.0 / r)
+    refz = np.where(inside, x[:, 2] / 3, x[:, 2] / (3 * r ** 3))
+    prev = None
+    for level in (2, 3, 4):
+        V, T = meshes.icosphere(level)
+        e1 = np.abs(oracle_lib.slp_p0(V, T, np.ones(T.shape[0]), x=x) - ref1).max()
+        gz = oracle_lib.element_charges(V, T, np.tile([0.0, 0.0, 1.0], (V.shape[0], 1)))
+        e2 = np.abs(oracle_lib.slp_p0(V, T, gz, x=x) - refz).max()
+        assert e1 < 0.5 / 4 ** level and e2 < 0.2 / 4 ** level, (level, e1, e2)
+        if prev is not None:
+            assert e1 < prev[0] / 3.5 and e2 < prev[1] / 3.5, (level, e1, e2, prev)
+        prev = (e1, e2)
