@@ -10,10 +10,13 @@ Shapes (Sec. 4 of the paper uses a cube, a sphere and a thin film):
   * ``cube``      the unit cube as a ``box``;
   * ``icosphere`` an icosahedron subdivided ``level`` times, vertices
                   projected onto the sphere;
-  * ``torus``     a parametric torus with major radius R and minor radius r.
+  * ``torus``     a parametric torus with major radius R and minor radius r;
+  * ``ball_tets`` a tetrahedral volume mesh of a ball (the finite element
+                  mesh of the paper's sphere tests, Sec. 2.1 and Sec. 4).
 
-All meshes are closed, 2-manifold and oriented with outward normals
-(counter-clockwise winding seen from outside).
+All surface meshes are closed, 2-manifold and oriented with outward normals
+(counter-clockwise winding seen from outside); volume meshes list each
+tetrahedron with positive orientation.
 """
 from __future__ import annotations
 
@@ -138,3 +141,89 @@ def mesh_stats(V, T):
     P = V[T]
     vol = np.einsum("ij,ij->i", P[:, 0], np.cross(P[:, 1], P[:, 2])).sum() / 6.0
     return {"n_vertices": int(V.shape[0]), "n_triangles": int(T.shape[0]), "signed_volume": float(vol)}
+
+
+_KUHN = []
+for _order in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+    _bits, _path = 0, [0]
+    for _a in _order:
+        _bits |= 4 >> _a
+        _path.append(_bits)
+    _KUHN.append(_path)  # corners (bit 2: first index, bit 0: third) on the path 000 -> 111
+
+
+def ball_tets(n: int, radius: float = 1.0, layers: int | None = None, core: float = 0.5):
+    """Tetrahedral mesh of the ball of the given radius about the origin.
+
+    A cubed sphere: an inner cube [-c, c]^3 (c = core * radius) of n^3
+    cells, and a shell of ``layers`` (default n/2) hexahedral layers
+    between the cube's surface and the sphere, six patches of n x n columns;
+    a shell node over the cube-surface point q at layer k sits at
+    (1 - t) q + t radius q/|q| with t = k/layers.  Every hexahedron, in its
+    index coordinates (each patch indexed along increasing global axes and
+    outward), is cut into the six tetrahedra along its main diagonal, so
+    that neighbouring cells cut their shared faces alike (a conforming
+    mesh), and no tetrahedron has all four nodes on the sphere.  n even.
+    Returns (nodes [N][3] float64, tets [K][4] int32), every tet positively
+    oriented.
+    """
+    if n < 2 or n % 2:
+        raise ValueError("n must be even and at least 2")
+    nr = max(1, n // 2) if layers is None else int(layers)
+    H = n // 2
+    W = n + 1
+
+    def key(q, k):
+        return (((q[:, 0] + H) * W + (q[:, 1] + H)) * W + (q[:, 2] + H)) * (nr + 1) + k
+
+    def corner_offsets(b):
+        return b >> 2 & 1, b >> 1 & 1, b & 1
+
+    g = np.arange(-H, H + 1)
+    Q = np.stack([x.ravel() for x in np.meshgrid(g, g, g, indexing="ij")], 1)
+    keys = [key(Q, 0)]
+    pos = [Q * (core * radius / H)]
+    tet_keys = []
+    c = np.arange(-H, H)
+    base = np.stack([x.ravel() for x in np.meshgrid(c, c, c, indexing="ij")], 1)
+    for path in _KUHN:
+        tet_keys.append(np.stack([key(base + np.array(corner_offsets(b)), 0) for b in path], 1))
+    for ax in range(3):
+        o = [d for d in range(3) if d != ax]
+        for side in (-1, 1):
+            u, v = (x.ravel() for x in np.meshgrid(g, g, indexing="ij"))
+            q = np.zeros((u.size, 3), dtype=np.int64)
+            q[:, ax] = side * H
+            q[:, o[0]], q[:, o[1]] = u, v
+            qp = q * (core * radius / H)
+            for k in range(1, nr + 1):
+                t = k / nr
+                keys.append(key(q, k))
+                pos.append((1 - t) * qp + t * radius * qp / np.linalg.norm(qp, axis=1, keepdims=True))
+            uu, vv, kk = (x.ravel() for x in np.meshgrid(c, c, np.arange(nr), indexing="ij"))
+            for path in _KUHN:
+                cols = []
+                for b in path:
+                    du, dv, dk = corner_offsets(b)
+                    qq = np.zeros((uu.size, 3), dtype=np.int64)
+                    qq[:, ax] = side * H
+                    qq[:, o[0]], qq[:, o[1]] = uu + du, vv + dv
+                    cols.append(key(qq, kk + dk))
+                tet_keys.append(np.stack(cols, 1))
+    keys = np.concatenate(keys)
+    pos = np.concatenate(pos)
+    uk, first = np.unique(keys, return_index=True)
+    nodes = pos[first]
+    allk = np.concatenate(tet_keys)
+    tets = np.searchsorted(uk, allk)
+    a, b, cc, d = (nodes[tets[:, q]] for q in range(4))
+    vol = np.einsum("ij,ij->i", b - a, np.cross(cc - a, d - a))
+    flip = vol < 0
+    tets[flip, 2], tets[flip, 3] = tets[flip, 3].copy(), tets[flip, 2].copy()
+    return nodes, tets.astype(np.int32)
+
+
+def tet_volumes(nodes, tets):
+    """Signed volumes of the tetrahedra (positive when positively oriented)."""
+    a, b, c, d = (nodes[tets[:, q]] for q in range(4))
+    return np.einsum("ij,ij->i", b - a, np.cross(c - a, d - a)) / 6.0

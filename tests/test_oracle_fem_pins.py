@@ -1,0 +1,115 @@
+"""Pins of the scalar-potential oracle (oracle/fem.py, Alg. 1 and Sec. 2.1)
+against closed forms and exact integrals, independent of the oracle's own
+formulas: the uniformly magnetised sphere (phi_1 = 0, phi = m . x / 3), the
+hedgehog m = x/|x| of Sec. 4 (phi = |x| - R, phi_2 = 0), a linear m with
+div m = 3 (phi_1 = (|x|^2 - R^2)/2), and the P1 forms on linear functions."""
+import numpy as np
+import pytest
+
+from oracle import fem
+from synthetic import meshes
+
+R = 0.2
+
+
+def _hedgehog(X):
+    r = np.linalg.norm(X, axis=1)
+    return np.divide(X, r[:, None], out=np.zeros_like(X), where=r[:, None] > 0), r
+
+
+def test_ball_mesh_is_a_closed_conforming_volume_mesh():
+    """Positive volumes; the boundary faces (each face of one tet only,
+    wound outward) enclose exactly the tets' volume; the volume converges to
+    4/3 pi R^3 at second order (flat facets)."""
+    prev = None
+    for n in (4, 8, 16):
+        X, K = meshes.ball_tets(n, R)
+        v = meshes.tet_volumes(X, K)
+        assert v.min() > 0.1 * v.mean()
+        faces, owner, opp = fem.boundary_faces(X, K)
+        enclosed = meshes.mesh_stats(X, faces)["signed_volume"]
+        assert abs(enclosed - v.sum()) < 1e-14
+        assert np.allclose(np.linalg.norm(X[faces], axis=2), R)  # boundary nodes on the sphere
+        err = 4 / 3 * np.pi * R ** 3 - v.sum()
+        assert err > 0
+        if prev is not None:
+            assert err < prev / 3.5
+        prev = err
+        # every face of a tet is a boundary face or shared by exactly two tets
+        allf = np.sort(np.concatenate([K[:, [1, 2, 3]], K[:, [0, 2, 3]], K[:, [0, 1, 3]], K[:, [0, 1, 2]]]), axis=1)
+        _, cnt = np.unique(allf, axis=0, return_counts=True)
+        assert set(cnt.tolist()) == {1, 2} and (cnt == 1).sum() == faces.shape[0]
+
+
+def test_p1_forms_on_linear_functions():
+    """S 1 = 0; e^T S e = |a|^2 |Omega_h| and e^T M e = int f^2 for f = a . x
+    + c (the latter by a degree-2 four-point rule on every tet)."""
+    X, K = meshes.ball_tets(4, R)
+    S, M = fem.stiffness(X, K), fem.mass(X, K)
+    vol = meshes.tet_volumes(X, K)
+    assert np.abs(S @ np.ones(X.shape[0])).max() < 1e-14
+    a, c = np.array([0.3, -1.2, 0.7]), 0.4
+    e = X @ a + c
+    assert abs(e @ (S @ e) - (a @ a) * vol.sum()) < 1e-13
+    alpha, beta = 0.5854101966249685, 0.1381966011250105  # (5 + 3 sqrt5)/20, (5 - sqrt5)/20
+    P = X[K]
+    ref = 0.0
+    for i in range(4):
+        lam = np.full(4, beta)
+        lam[i] = alpha
+        pt = np.einsum("a,tad->td", lam, P)
+        ref += (vol / 4 * (pt @ a + c) ** 2).sum()
+    assert abs(e @ (M @ e) - ref) < 1e-14
+
+
+def test_phi1_closed_forms():
+    """Uniform m: b = 0 at free nodes, so phi_1 = 0.  m = x (div m = 3):
+    phi_1 = (|x|^2 - R^2)/2; m = x/|x|: phi_1 = |x| - R (away from the centre,
+    where the nodal m is 0 and the field is singular); both converge at
+    second order in the nodal max norm."""
+    prev = None
+    for n in (4, 8, 16):
+        X, K = meshes.ball_tets(n, R)
+        assert np.abs(fem.phi1(X, K, np.tile([0.2, -0.5, 1.0], (X.shape[0], 1)))).max() < 1e-15
+        r = np.linalg.norm(X, axis=1)
+        e1 = np.abs(fem.phi1(X, K, X) - (r ** 2 - R ** 2) / 2).max()
+        m, _ = _hedgehog(X)
+        e2 = np.abs(fem.phi1(X, K, m) - (r - R))[r > 0.3 * R].max()
+        assert e1 < 0.06 * R ** 2 and e2 < 0.06 * R, (n, e1, e2)
+        if prev is not None:
+            assert e1 < prev[0] / 2.5 and e2 < prev[1] / 2.5, (n, e1, e2, prev)
+        prev = (e1, e2)
+
+
+def test_uniformly_magnetised_ball():
+    """m = e: phi_1 = 0 and phi = e . x / 3 at every node (Sec. 4), the
+    error falling at second order."""
+    prev = None
+    e = np.array([0.0, 0.6, 0.8])
+    for n in (4, 8, 16):
+        X, K = meshes.ball_tets(n, R)
+        phi, p1, g = fem.potential(X, K, np.tile(e, (X.shape[0], 1)))
+        assert np.abs(p1).max() < 1e-15
+        err = np.abs(phi - X @ e / 3).max()
+        assert err < 0.02 * R
+        if prev is not None:
+            assert err < prev / 3.0, (n, err, prev)
+        prev = err
+
+
+def test_hedgehog_reproduces_the_closed_form_of_sec4():
+    """m = x/|x|: phi = |x| - R inside, g -> 0 on the boundary.  L2 and H1
+    seminorm errors of the nodal interpolants (as in Sec. 4) fall at second
+    and first order; at 1536 tets the L2 error is below the 1.0e-3 printed
+    for the paper's coarsest mesh (3058 elements, Table 2)."""
+    prev = None
+    for n in (4, 8, 16):
+        X, K = meshes.ball_tets(n, R)
+        m, r = _hedgehog(X)
+        phi, p1, g = fem.potential(X, K, m)
+        l2, h1 = fem.p1_errors(X, K, phi - (r - R))
+        if n == 4:
+            assert K.shape[0] == 1536 and l2 < 1.0e-3 and h1 < 2.5e-2, (l2, h1)
+        if prev is not None:
+            assert l2 < prev[0] / 3.0 and h1 < prev[1] / 1.7 and np.abs(g).max() < prev[2], (n, l2, h1, prev)
+        prev = (l2, h1, np.abs(g).max())
