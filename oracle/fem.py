@@ -13,14 +13,17 @@ The split of Sec. 2.1, written out step by step on a P1 tetrahedral mesh:
   and the load b_k = sum_T int_T m . grad eta_k with m the P1 interpolant of
   the nodal values; only the free (non-boundary) rows and columns are solved
   (the subsystem of Sec. 2.1 with zero Dirichlet data), here by a sparse
-  direct solve (scipy's SuperLU), where the paper uses ILU-preconditioned CG.
+  direct solve (scipy's SuperLU), where the paper uses ILU-preconditioned CG;
+  for meshes too large for the direct solve, scipy's conjugate gradients
+  with a Jacobi preconditioner to a relative residual of 1e-13
+  (``phi1_iterative``, pinned to the direct solve).
 * g: on every boundary triangle S_j the integral mean of m . n_j (the L2
   projection of Sec. 2.2) minus the normal derivative of phi_1 from the
   tetrahedron that owns the triangle (grad phi_1 is constant there).
 * phi_2: the single layer potential of g, element-wise constant, integrated
   exactly over every boundary triangle (``oracle.slp_p0``), at every node.
 
-Pinned by tests/test_oracle_pins.py: the closed forms of Sec. 4 (uniform
+Pinned by tests/test_oracle_fem_pins.py: the closed forms of Sec. 4 (uniform
 magnetisation: phi_1 = 0 and phi = m . x / 3; the hedgehog m = x/|x|:
 phi = |x| - R), converging under refinement, and the P1 mass and stiffness
 forms on polynomials they integrate exactly.
@@ -122,6 +125,44 @@ def phi1(nodes, tets, m):
     if free.size:
         out[free] = spla.spsolve(S[free][:, free].tocsc(), b[free])
     return out
+
+
+def phi1_iterative(nodes, tets, m, rtol: float = 1e-13):
+    """phi_1 as in ``phi1``, the free subsystem solved by scipy's conjugate
+    gradients (Jacobi preconditioner) to |r| <= rtol |b|."""
+    faces, _, _ = boundary_faces(nodes, tets)
+    bnd = np.zeros(nodes.shape[0], dtype=bool)
+    bnd[faces.ravel()] = True
+    free = np.nonzero(~bnd)[0]
+    S = stiffness(nodes, tets)[free][:, free].tocsr()
+    b = load(nodes, tets, np.asarray(m, dtype=np.float64))[free]
+    out = np.zeros(nodes.shape[0])
+    if free.size:
+        dinv = 1.0 / S.diagonal()
+        M = spla.LinearOperator(S.shape, matvec=lambda v: dinv * v)
+        try:
+            x, info = spla.cg(S, b, rtol=rtol, atol=0.0, maxiter=100000, M=M)
+        except TypeError:  # scipy before 1.12 names it tol
+            x, info = spla.cg(S, b, tol=rtol, atol=0.0, maxiter=100000, M=M)
+        if info != 0:
+            raise RuntimeError(f"conjugate gradients did not converge ({info})")
+        out[free] = x
+    return out
+
+
+def potential_at(nodes, tets, m, sel, phi_1=None, nthreads: int = 0):
+    """phi = phi_1 + phi_2 at the nodes sel only (phi_1 everywhere, by the
+    iterative solve unless given): for meshes whose all-node sum is too long.
+    Returns (phi[sel], phi_1)."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    p1 = phi1_iterative(nodes, tets, m) if phi_1 is None else phi_1
+    faces, g = charges(nodes, tets, m, p1)
+    used = np.unique(faces.ravel())
+    ren = -np.ones(nodes.shape[0], dtype=np.int64)
+    ren[used] = np.arange(used.size)
+    p2 = slp_p0(nodes[used], ren[faces].astype(np.int32), g, nthreads=nthreads, x=nodes[sel])
+    return p1[sel] + p2, p1
 
 
 def charges(nodes, tets, m, phi_1):

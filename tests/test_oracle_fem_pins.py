@@ -113,3 +113,18 @@ def test_hedgehog_reproduces_the_closed_form_of_sec4():
         if prev is not None:
             assert l2 < prev[0] / 3.0 and h1 < prev[1] / 1.7 and np.abs(g).max() < prev[2], (n, l2, h1, prev)
         prev = (l2, h1, np.abs(g).max())
+
+
+def test_iterative_phi1_and_sampled_potential_equal_the_direct_forms():
+    """phi1_iterative equals the direct solve within 1e-11 relative, and
+    potential_at equals potential at the sampled nodes."""
+    from synthetic import fields
+    for n in (4, 8):
+        X, K = meshes.ball_tets(n, R)
+        m = fields.smooth_random(X, 5)
+        a, b = fem.phi1(X, K, m), fem.phi1_iterative(X, K, m)
+        assert np.linalg.norm(a - b) <= 1e-11 * np.linalg.norm(a)
+    phi, _, _ = fem.potential(X, K, m)
+    sel = np.arange(0, X.shape[0], 7)
+    got, _ = fem.potential_at(X, K, m, sel)
+    assert np.linalg.norm(got - phi[sel]) <= 1e-11 * np.linalg.norm(phi[sel])
