@@ -29,10 +29,15 @@ workloads, each behind its own oracle parity gate:
                    graph, against the same items one at a time;
   cfg4_served      Poisson arrivals over 8 resident meshes at 2000 req/s and at
                    half the measured saturated throughput, p50/p99, against the
-                   same requests one at a time.
+                   same requests one at a time;
+  sphere_expsum_kernel       the sphere with the paper's exponential-sum kernel;
+  sphere_triangle_integrals  the sphere with element charges, the gridding
+                   matrix of triangle integrals and exact near-field integrals;
+  ball_scalar_potential      phi = phi_1 + phi_2 of Alg. 1 on a tetrahedral
+                   ball (786k tets, 134k nodes) for the hedgehog m = x/|x|.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--no-suite] [--workload ...] [--mode plain|batched|served]
+                  [--no-suite] [--workload ...] [--mode plain|batched|served|potential]
 
 `--impl reference` times the FP64 oracle (plain C direct sum, OpenMP) on the
 host cores instead, on a bounded sample of the same workload.
@@ -400,6 +405,93 @@ def _plain_config(slp, w, args, flush, steps, warmup, n_sample=None, profile=Tru
         plan.close()
 
 
+def _potential_config(slp, args, flush, n, steps, warmup, prec=32, tol=1e-5, n_sample=2048):
+    """The scalar potential of Alg. 1 on a tetrahedral ball of radius 0.2
+    (n^3 core cells, 12 n^2 boundary triangles) for the hedgehog m = x/|x| of
+    Sec. 4: parity against the FP64 oracle (phi_1 everywhere, phi at sampled
+    nodes), the closed form phi = |x| - R, timed evaluations and the inner
+    step's byte roofline."""
+    import torch
+
+    from oracle import fem
+    from synthetic import meshes
+    dev = torch.cuda.current_device()
+    R = 0.2
+    X, K = meshes.ball_tets(n, R)
+    r = np.linalg.norm(X, axis=1)
+    m = np.divide(X, r[:, None], out=np.zeros_like(X), where=r[:, None] > 0)
+    o = slp.slp_default_opts()
+    o.precision = prec
+    o.device = dev
+    t0 = time.perf_counter()
+    pot = slp.slp_potential_create(X, K, tol, o)
+    t_setup = time.perf_counter() - t0
+    try:
+        dt = torch.float32 if prec == 32 else torch.float64
+        d_m = torch.as_tensor(m, dtype=dt, device="cuda")
+        d_phi = torch.empty(X.shape[0], dtype=dt, device="cuda")
+        d_phi1 = torch.empty(X.shape[0], dtype=dt, device="cuda")
+        stream = torch.cuda.current_stream()
+        slp.slp_potential_eval(pot, d_m, d_phi, d_phi1, stream)
+        torch.cuda.synchronize()
+        phi, phi1 = d_phi.double().cpu().numpy(), d_phi1.double().cpu().numpy()
+        rng = np.random.default_rng(31)
+        sel = np.sort(rng.choice(X.shape[0], size=min(n_sample, X.shape[0]), replace=False))
+        ref, ref1 = fem.potential_at(X, K, m, sel)
+        rel = float(np.linalg.norm(phi[sel] - ref) / np.linalg.norm(ref))
+        rel1 = float(np.linalg.norm(phi1 - ref1) / np.linalg.norm(ref1))
+        l2, h1 = fem.p1_errors(X, K, phi - (r - R))
+        for i in range(warmup):
+            flush.fill_(float(i))
+            slp.slp_potential_eval(pot, d_m, d_phi, None, stream)
+        torch.cuda.synchronize()
+        ms, ms1, ms2 = [], [], []
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            slp.slp_potential_eval(pot, d_m, d_phi, None, stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            q = slp.slp_potential_query(pot)
+            ms1.append(q["ms_phi1"])
+            ms2.append(q["ms_phi2"])
+        q = slp.slp_potential_query(pot)
+        t = sum(ms) / steps
+        t1, t2 = sum(ms1) / steps, sum(ms2) / steps
+        it, nf, nnz = q["cg_iterations"], q["n_free"], q["stiffness_nnz"]
+        # one FP32 inner step: S (4-byte value, 4-byte column per entry), row
+        # pointers, D^-1, and r, w, s, p, x_c read once and r, w, s, p, x_c
+        # written once per row
+        it_bytes = 8 * nnz + 8 * (nf + 1) + 4 * nf + 40 * nf
+        # each FP64 correction: S (8 + 4 bytes per entry), x, b read, x written,
+        # the inner start written (r, x_c, p, s)
+        corr_bytes = 12 * nnz + 8 * (nf + 1) + 24 * nf + 16 * nf
+        load_bytes = (48 if prec == 64 else 24) * q["load_nnz"] + 8 * (nf + 1) + 40 * nf
+        alg = it * it_bytes + q["cg_corrections"] * corr_bytes + load_bytes
+        achieved = alg / (t1 / 1e3) / 1e9
+        peaks, peak_src = _peaks()
+        ok = rel <= tol and rel1 <= tol
+        return {"workload": f"ball_R0.2_n{n}_tets{K.shape[0]}_fp{prec}",
+                "value": X.shape[0] / (t / 1e3) if ok else 0.0, "unit": "nodes/s",
+                "ms_per_step": t, "steps": steps, "warmup": warmup, "dtype": "f32" if prec == 32 else "f64",
+                "n_nodes": int(X.shape[0]), "n_tets": int(K.shape[0]), "n_free": nf,
+                "n_boundary": q["n_boundary"], "n_faces": q["n_faces"], "stiffness_nnz": nnz,
+                "cg_iterations": it, "cg_corrections": q["cg_corrections"], "cg_residual": q["cg_residual"],
+                "cg_tolerance": q["cg_tolerance"], "ms_phi1": t1, "ms_phi2": t2, "us_per_inner_step": 1e3 * t1 / max(it, 1),
+                "tolerance": tol, "rel_l2": rel, "rel_l2_phi1": rel1,
+                "parity_nodes": int(sel.size), "parity_ok": ok,
+                "hedgehog_l2": l2, "hedgehog_h1_semi": h1, "setup_s": round(t_setup, 2),
+                "roofline": {"kernel": "phi_1 solve (k_cg_step, k_fem_residual, k_fem_load)",
+                             "bound": "hbm", "achieved": achieved, "peak": float(peaks["hbm_gbs"]),
+                             "unit": "GB/s", "frac": achieved / float(peaks["hbm_gbs"]), "traffic": None,
+                             "bytes_per_inner_step": it_bytes, "peak_source": peak_src,
+                             "note": "working set L2-resident at this size"}}
+    finally:
+        slp.slp_potential_destroy(pot)
+
+
 def run_suite(args):
     """The other workloads, each behind its own parity gate (N = 1 only)."""
     import torch
@@ -416,6 +508,8 @@ def run_suite(args):
                                                   kernel_mode=slp.SLP_KERNEL_EXPSUM)
     # the paper's discretisation: element charges, triangle-integrated gridding matrix, exact near field
     suite["sphere_triangle_integrals"] = _plain_config(slp, workloads.sphere(), args, flush, 50, 5, integration=1)
+    # the full scalar potential of Alg. 1 (P1 Dirichlet solve, boundary charges, phi_2 at every node)
+    suite["ball_scalar_potential"] = _potential_config(slp, args, flush, 32, 10, 3)
     del flush
     torch.cuda.empty_cache()
     suite["cfg3_batched"] = run_batched(args, emit=False, steps=10, warmup=3)
@@ -935,8 +1029,10 @@ def main():
     ap.add_argument("--no-suite", action="store_true",
                     help="headline only: skip the other workloads carried under \"configs\"")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--mode", choices=["plain", "batched", "served"], default="plain",
-                    help="plain: the headline single evaluation; batched/served: the other forms")
+    ap.add_argument("--mode", choices=["plain", "batched", "served", "potential"], default="plain",
+                    help="plain: the headline single evaluation; batched/served: the other forms; "
+                         "potential: the scalar potential of a tetrahedral ball alone")
+    ap.add_argument("--ball-n", type=int, default=32, help="potential mode: core cells per axis of the ball")
     ap.add_argument("--lanes", type=int, default=1,
                     help="batched form: concurrent scratch sets per plan (a lane batches its states itself)")
     ap.add_argument("--slots", type=int, default=1, help="served form: concurrent request slots per plan")
@@ -952,6 +1048,14 @@ def main():
         run_batched(args)
     elif args.mode == "served":
         run_served(args)
+    elif args.mode == "potential":
+        import torch
+
+        import paper_1305_3162_gb300 as slp
+        from paper_1305_3162_gb300 import _build
+        _build.build()
+        flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps(_potential_config(slp, args, flush, args.ball_n, args.steps, args.warmup)))
     else:
         run_ours(args)
 

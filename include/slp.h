@@ -283,6 +283,67 @@ slp_status slp_probe_query(slp_probe_t probe, int64_t *n_points, int64_t *near_n
 /* Release a probe set (before its plan).  NULL is accepted. */
 slp_status slp_probe_destroy(slp_probe_t probe);
 
+/* ---- The scalar potential phi = phi_1 + phi_2 on a tetrahedral mesh (Alg. 1) ----
+ * The split of Sec. 2.1: phi_1 solves the Dirichlet problem of Sec. 2.1
+ * (P1 elements, zero on the boundary, only the free (non-boundary) nodes are
+ * unknowns) and phi_2 is the single layer potential of
+ * g = m.n - d phi_1/dn on the boundary, at every node.
+ * Setup (slp_potential_create): the boundary (faces of one tetrahedron only,
+ * wound away from its fourth node), the free-node stiffness matrix and the
+ * load operator b = B m of Sec. 2.1 (host FP64), the boundary's
+ * triangle-integrated plan (opts.integration is set; Sec. 3) and a probe set
+ * of the free nodes.
+ * Computation (slp_potential_eval): b = B m (in the plan's precision);
+ * phi_1 by iterative refinement on the device: Jacobi-preconditioned
+ * conjugate gradients in FP32 cut the residual of the current correction
+ * equation by 1e-4, the correction joins the FP64 solution and the residual
+ * b - S x is recomputed in FP64, until |b - S x| <= cg_tolerance |b|;
+ * g_j = (mean of m over boundary triangle j) . n_j + phi_1(o) / h_j, o the
+ * owning tetrahedron's fourth node and h_j its height over the triangle
+ * (d phi_1/dn = -phi_1(o)/h_j, phi_1 being zero on the triangle); phi_2 at
+ * the boundary nodes (the plan's targets) and the free nodes (its probes);
+ * phi = phi_1 + phi_2.
+ * nodes: host [n_nodes][3]; tets: host [n_tets][4], either orientation, read
+ * during the call; every node in some tetrahedron, every face in at most two,
+ * the boundary one closed surface as slp_plan requires.  tolerance, opts: as
+ * for slp_plan (opts->device must be a device).  cg_tolerance: 0 picks
+ * tolerance / 100 (at least 1e-14); cg_max_iterations (FP32 steps in all):
+ * 0 picks 10000.
+ * Errors: INVALID_ARG, MESH, TOLERANCE_INFEASIBLE, OOM, CUDA, NO_DEVICE. */
+typedef struct slp_potential_s *slp_potential_t;
+typedef struct {
+    int64_t n_nodes, n_tets;
+    int64_t n_free;            /* unknowns of phi_1 */
+    int64_t n_boundary;        /* boundary nodes: the plan's targets */
+    int64_t n_faces;           /* boundary triangles */
+    int64_t stiffness_nnz;     /* entries of S(free, free) */
+    int64_t load_nnz;          /* entries of the load operator */
+    int64_t cg_iterations;     /* FP32 steps of the last evaluation (-1 before the first) */
+    int64_t cg_corrections;    /* its FP64 residual corrections */
+    int64_t cg_max_iterations;
+    double cg_residual;        /* |b - S x| / |b| after the last evaluation */
+    double cg_tolerance;
+    double ms_phi1;            /* device time of the last evaluation's load and solve (-1: not finished) */
+    double ms_phi2;            /* ... of its charges, single layer potential and sum */
+    slp_plan_t surface_plan;   /* the boundary's plan, owned by the potential (query only) */
+} slp_potential_info;
+slp_status slp_potential_create(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                                double tolerance, const slp_plan_opts *opts, double cg_tolerance,
+                                int cg_max_iterations, slp_potential_t *out);
+/* d_m: device [n_nodes][3] (plan precision), the nodal magnetisation;
+ * d_phi: device [n_nodes], overwritten with phi; d_phi_1: NULL or device
+ * [n_nodes], overwritten with phi_1.  Enqueued on `stream`; the call returns
+ * once the solve has converged on the device (the host reads the solver's
+ * state after every 16 steps while the next 16 are already queued), so it
+ * cannot be captured into a CUDA graph; phi_2 and the sum are then enqueued
+ * behind it.  Errors: INVALID_ARG, CUDA, NONFINITE (the iteration met
+ * NaN/Inf), TOLERANCE_INFEASIBLE (cg_max_iterations reached: phi is still
+ * written, from the last iterate). */
+slp_status slp_potential_eval(slp_potential_t pot, const void *d_m, void *d_phi, void *d_phi_1, void *stream);
+slp_status slp_potential_query(slp_potential_t pot, slp_potential_info *info);
+/* Release the potential with its plan and probe set.  NULL is accepted. */
+slp_status slp_potential_destroy(slp_potential_t pot);
+
 /* Pipelined host-buffer evaluation: enqueues, without waiting, the copy of
  * h_in into one of the plan's two staging slots (on an internal copy-in
  * stream), the evaluation (on `stream`) and the copy of phi into h_phi (on

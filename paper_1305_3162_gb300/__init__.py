@@ -105,6 +105,15 @@ class slp_server_statistics(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class slp_potential_info(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_tets", ctypes.c_int64), ("n_free", ctypes.c_int64),
+                ("n_boundary", ctypes.c_int64), ("n_faces", ctypes.c_int64), ("stiffness_nnz", ctypes.c_int64),
+                ("load_nnz", ctypes.c_int64), ("cg_iterations", ctypes.c_int64), ("cg_corrections", ctypes.c_int64),
+                ("cg_max_iterations", ctypes.c_int64), ("cg_residual", ctypes.c_double),
+                ("cg_tolerance", ctypes.c_double), ("ms_phi1", ctypes.c_double), ("ms_phi2", ctypes.c_double),
+                ("surface_plan", ctypes.c_void_p)]
+
+
 class slp_info(ctypes.Structure):
     _fields_ = [("n_targets", ctypes.c_int64), ("n_sources", ctypes.c_int64), ("n_triangles", ctypes.c_int64),
                 ("quadrature", ctypes.c_int), ("precision", ctypes.c_int), ("grid", ctypes.c_int * 3),
@@ -139,6 +148,7 @@ _lib = None
 #: C entry points the binding requires (the declarations of include/slp.h and include/slp_debug.h)
 EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_states", "slp_eval_host", "slp_eval_host_async",
             "slp_eval_host_wait", "slp_probe_create", "slp_eval_probe", "slp_probe_query", "slp_probe_destroy",
+            "slp_potential_create", "slp_potential_eval", "slp_potential_query", "slp_potential_destroy",
             "slp_query", "slp_query_points",
             "slp_check", "slp_destroy", "slp_status_string", "slp_last_error",
             "slp_debug_run", "slp_debug_copy", "slp_debug_buffer_bytes", "slp_debug_host_count",
@@ -178,6 +188,12 @@ def load():
         "slp_eval_probe": ([vp, vp, ctypes.c_int, vp, vp, vp, vp], St),
         "slp_probe_query": ([vp, ctypes.POINTER(I64), ctypes.POINTER(I64)], St),
         "slp_probe_destroy": ([vp], St),
+        "slp_potential_create": ([ctypes.POINTER(ctypes.c_double), I64, ctypes.POINTER(ctypes.c_int32), I64,
+                                  ctypes.c_double, ctypes.POINTER(slp_plan_opts), ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(vp)], St),
+        "slp_potential_eval": ([vp, vp, vp, vp, vp], St),
+        "slp_potential_query": ([vp, ctypes.POINTER(slp_potential_info)], St),
+        "slp_potential_destroy": ([vp], St),
         "slp_eval_states": ([vp, ctypes.c_int, ctypes.c_int, vp, vp, vp], St),
         "slp_query": ([vp, ctypes.POINTER(slp_info)], St),
         "slp_query_points": ([vp, ctypes.POINTER(ctypes.c_double)], St),
@@ -336,6 +352,38 @@ def slp_probe_query(probe) -> dict:
 def slp_probe_destroy(probe):
     if probe is not None:
         _check(load().slp_probe_destroy(probe), "slp_probe_destroy")
+
+
+def slp_potential_create(nodes, tets, tolerance: float, opts: slp_plan_opts | None = None,
+                         cg_tolerance: float = 0.0, cg_max_iterations: int = 0):
+    """The scalar potential of a tetrahedral mesh (nodes [N][3], tets [K][4]);
+    returns the handle (release with slp_potential_destroy)."""
+    X = np.ascontiguousarray(nodes, dtype=np.float64)
+    K = np.ascontiguousarray(tets, dtype=np.int32)
+    out = ctypes.c_void_p()
+    o = opts if opts is not None else slp_default_opts()
+    _check(load().slp_potential_create(X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), X.shape[0],
+                                       K.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), K.shape[0],
+                                       float(tolerance), ctypes.byref(o), float(cg_tolerance), int(cg_max_iterations),
+                                       ctypes.byref(out)), "slp_potential_create")
+    return out
+
+
+def slp_potential_eval(pot, d_m, d_phi, d_phi_1=None, stream=None):
+    """phi = phi_1 + phi_2 at every node from the nodal m (and phi_1 when asked)."""
+    _check(load().slp_potential_eval(pot, _ptr(d_m), _ptr(d_phi), _ptr(d_phi_1), _stream(stream)),
+           "slp_potential_eval")
+
+
+def slp_potential_query(pot) -> dict:
+    info = slp_potential_info()
+    _check(load().slp_potential_query(pot, ctypes.byref(info)), "slp_potential_query")
+    return {name: getattr(info, name) for name, _ in info._fields_}
+
+
+def slp_potential_destroy(pot):
+    if pot is not None:
+        _check(load().slp_potential_destroy(pot), "slp_potential_destroy")
 
 
 def slp_eval_host_wait(plan):

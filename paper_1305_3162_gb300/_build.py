@@ -19,8 +19,8 @@ LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libslp_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-CU_SOURCES = ["k_grid.cu", "k_fft.cu", "k_near.cu", "k_static.cu", "k_tri.cu"]
-CPP_SOURCES = ["slp_plan.cpp", "slp_batch.cpp", "slp_serve.cpp"]
+CU_SOURCES = ["k_grid.cu", "k_fft.cu", "k_near.cu", "k_static.cu", "k_tri.cu", "k_fem.cu"]
+CPP_SOURCES = ["slp_plan.cpp", "slp_batch.cpp", "slp_serve.cpp", "slp_fem.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,94 @@
+// Device data and launchers of the scalar potential phi = phi_1 + phi_2 on a
+// tetrahedral mesh (Alg. 1, Sec. 2.1): the P1 load operator, the conjugate
+// gradients for the Dirichlet problem of phi_1 (FP32 iterations refined by
+// FP64 residuals), the boundary charges g = m.n - dphi_1/dn and the final sum.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace slp {
+
+// Scalars of the solve.  Each is written only by the last block of a launch
+// (after every other block of that launch has read what it needs) and read
+// by the following launches.
+struct CgState {
+    float gamma;        // r . D^-1 r of the inner residual
+    float alpha;        // step length of the next inner step
+    float beta;         // direction update of the next inner step
+    float rr;           // r . r of the inner residual after the last step
+    float rr0;          // r . r of the inner residual at the inner start
+    double bb;          // b . b
+    double rr_hi;       // |b - S x|^2 (FP64 residual) after the last correction
+    double scale;       // the inner problem's right-hand side is rho / scale
+    double inv_scale;
+    long long iter;     // inner steps, all corrections together
+    long long outer;    // corrections (FP64 residuals) done
+    int done;           // the inner iteration has stopped: later inner launches return at once
+    int outer_done;     // |b - S x| <= tol |b|, out of iterations, or non-finite
+    int bad;            // a non-finite scalar was seen
+    unsigned count[5];  // arrival counters of the load, scale, start, residual and step launches
+};
+
+struct FemDev {
+    int64_t nf = 0;    // free nodes: the unknowns of the free subsystem
+    int nblk_max = 1;  // most blocks of a launch, hence the row length of the partial sums
+    // S(fn, fn): CSR over free rows and columns with FP64 values (the
+    // residual), and the same matrix in FP32 in slices of 32 rows for the
+    // inner steps (one thread per row: entry k of the slice's lane l at
+    // sl_ptr[slice] + 32 k + l, sl_w[slice] entries per row, short rows
+    // padded with zero entries at their own column); 1 / diagonal in FP32
+    const int64_t *s_ptr = nullptr;
+    const int *s_col = nullptr;
+    const double *s_val = nullptr;
+    const int64_t *sl_ptr = nullptr;
+    const int *sl_w = nullptr;
+    const int *sl_col = nullptr;
+    const float *sl_val = nullptr;
+    const float *dinv = nullptr;
+    // load operator b(fn) = B m, CSR over free rows, columns are the other
+    // nodes of the row's tetrahedra, entries |T|/4 grad eta_row summed over
+    // them, applied to the differences m_col - m_row (every free row of B sums
+    // to zero, so the row's own column drops out); float4 in FP32 plans,
+    // double4 in FP64 plans
+    const int *fnode = nullptr;  // node of each free row
+    const int64_t *b_ptr = nullptr;
+    const int *b_col = nullptr;
+    const void *b_val = nullptr;
+    double *b = nullptr, *x = nullptr, *rho = nullptr;  // FP64 load, solution and residual
+    // the inner iteration (FP32): correction and direction, and residual r,
+    // w = S D^-1 r and s = S p in buffers of even and odd steps
+    float *xc = nullptr, *p = nullptr;
+    float *r[2] = {nullptr, nullptr}, *w[2] = {nullptr, nullptr}, *s[2] = {nullptr, nullptr};
+    double *part = nullptr;   // [3][nblk_max] block partial sums, FP64 (load, residual)
+    float *part32 = nullptr;  // [3][nblk_max] block partial sums, FP32 (inner steps)
+    CgState *st = nullptr;
+    double tol2 = 0.0;    // outer stop: |b - S x|^2 <= tol2 |b|^2
+    float inner2 = 0.f;   // inner stop: r.r <= inner2 r0.r0
+    long long max_iter = 0;
+    // boundary triangles: nodes (a, b, c) wound outward and the free index of the
+    // owning tetrahedron's fourth node (-1 when it lies on the boundary); unit
+    // normal and 1/h, h the tetrahedron's height over the triangle
+    int64_t nfaces = 0;
+    const int4 *face = nullptr;
+    const double4 *face_n = nullptr;
+    // per node: free index (>= 0) or -1 - boundary index
+    int64_t nnodes = 0;
+    const int *slot = nullptr;
+};
+
+constexpr int FEM_THREADS = 256;
+constexpr int FEM_CHUNK = 16;       // inner steps per captured graph (even: parities repeat)
+constexpr double FEM_INNER = 1e-4;  // each correction's inner steps cut its residual by this factor
+
+// b = B m and x = 0; the first inner iteration set up from r = b / scale
+cudaError_t launch_fem_load(const FemDev &d, int prec, const void *m, cudaStream_t s);
+// one inner step (parity: the step's index mod 2)
+cudaError_t launch_cg_iteration(const FemDev &d, int parity, cudaStream_t s);
+// x += scale * correction, the FP64 residual, the next inner iteration set up from it
+cudaError_t launch_fem_correct(const FemDev &d, cudaStream_t s);
+cudaError_t launch_fem_charges(const FemDev &d, int prec, const void *m, void *g, cudaStream_t s);
+cudaError_t launch_fem_combine(const FemDev &d, int prec, const void *phi2_b, const void *phi2_f, void *phi,
+                               void *phi1, cudaStream_t s);
+
+}  // namespace slp

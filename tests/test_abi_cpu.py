@@ -331,7 +331,7 @@ def test_empty_and_minimal_meshes(slp):
 
 
 @pytest.mark.parametrize("name", ["slp_mesh", "slp_plan_opts", "slp_info", "slp_tune_info", "slp_server_opts",
-                                  "slp_server_statistics"])
+                                  "slp_server_statistics", "slp_potential_info"])
 def test_struct_layouts_match_the_header(slp, name, tmp_path):
     """Every ctypes mirror of a public struct has the header's size and field
     offsets (a C program compiled against include/slp.h prints them)."""
@@ -466,3 +466,20 @@ def test_probe_sets_refuse_host_only_plans_and_bad_arguments(slp):
         slp.slp_probe_destroy(None)
     finally:
         slp.slp_destroy(p)
+
+
+def test_potential_refuses_host_only_plans_and_bad_meshes(slp):
+    """The scalar potential needs a device; argument and mesh checks come first."""
+    X, K = meshes.ball_tets(2, 1.0)
+    o = slp.slp_default_opts()
+    o.device = -1
+    with pytest.raises(slp.SlpError) as e:
+        slp.slp_potential_create(X, K, 1e-5, o)
+    assert e.value.status == slp.SLP_ERR_NO_DEVICE
+    with pytest.raises(slp.SlpError) as e:
+        slp.slp_potential_create(X, K[:0], 1e-5)
+    assert e.value.status == slp.SLP_ERR_INVALID_ARG
+    with pytest.raises(slp.SlpError) as e:
+        slp.slp_potential_create(X, K, 1e-5, cg_max_iterations=-1)
+    assert e.value.status == slp.SLP_ERR_INVALID_ARG
+    slp.slp_potential_destroy(None)

@@ -1,0 +1,124 @@
+"""The scalar potential phi = phi_1 + phi_2 on a tetrahedral ball (Alg. 1,
+Sec. 2.1): the device path (P1 load operator, the refined conjugate-gradient
+solve for phi_1, boundary charges, the triangle-integrated single layer
+potential at the boundary nodes and, through probes, at the free nodes)
+against the FP64 oracle (sparse direct solve and exact triangle integrals),
+and the closed forms of Sec. 4."""
+import numpy as np
+import pytest
+
+from oracle import fem
+from synthetic import fields, meshes
+from tests.gpu_util import lib, rel_l2, to_dev, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+R = 0.2
+
+
+def _opts(slp, prec, grid):
+    o = slp.slp_default_opts()
+    o.precision = prec
+    for d in range(3):
+        o.grid[d] = grid
+    return o
+
+
+def _eval(slp, pot, m, prec, with_phi1=True):
+    torch = torch_cuda()
+    dt = torch.float64 if prec == 64 else torch.float32
+    n = m.shape[0]
+    d_phi = torch.zeros(n, dtype=dt, device="cuda")
+    d_phi1 = torch.zeros(n, dtype=dt, device="cuda") if with_phi1 else None
+    slp.slp_potential_eval(pot, to_dev(m, prec), d_phi, d_phi1, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return d_phi.double().cpu().numpy(), (d_phi1.double().cpu().numpy() if with_phi1 else None)
+
+
+def _hedgehog(X):
+    r = np.linalg.norm(X, axis=1)
+    return np.divide(X, r[:, None], out=np.zeros_like(X), where=r[:, None] > 0), r
+
+
+CASES = [
+    # (name, n, prec, tol, grid, field, bar)
+    ("n4_fp64_random", 4, 64, 1e-10, 32, "random", 1e-9),
+    ("n8_fp64_hedgehog", 8, 64, 1e-10, 64, "hedgehog", 1e-9),
+    ("n4_fp32_random", 4, 32, 1e-5, 32, "random", 1e-5),
+    ("n8_fp32_random", 8, 32, 1e-5, 64, "random", 1e-5),
+    ("n8_fp32_hedgehog", 8, 32, 1e-5, 64, "hedgehog", 1e-5),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_potential_matches_the_oracle(case):
+    """phi and phi_1 at every node equal the oracle's within the bar (FP64:
+    the solve stops at |b - S x| <= 1e-12 |b|; FP32: the plan tolerance)."""
+    name, n, prec, tol, grid, field, bar = case
+    slp = lib()
+    X, K = meshes.ball_tets(n, R)
+    m = fields.smooth_random(X, 17) if field == "random" else _hedgehog(X)[0]
+    pot = slp.slp_potential_create(X, K, tol, _opts(slp, prec, grid))
+    try:
+        phi, phi1 = _eval(slp, pot, m, prec)
+        info = slp.slp_potential_query(pot)
+        ref, ref1, _ = fem.potential(X, K, m)
+        e, e1 = rel_l2(phi, ref), rel_l2(phi1, ref1)
+        print(f"{name}: rel-L2 phi {e:.3e} phi_1 {e1:.3e}; {info['cg_iterations']} FP32 steps, "
+              f"{info['cg_corrections']} corrections, residual {info['cg_residual']:.2e}; "
+              f"{info['n_free']} free, {info['n_boundary']} boundary nodes")
+        assert info["n_free"] + info["n_boundary"] == X.shape[0] and info["n_faces"] == 12 * n * n
+        assert info["cg_residual"] <= info["cg_tolerance"]
+        assert e <= bar and e1 <= bar, (e, e1)
+    finally:
+        slp.slp_potential_destroy(pot)
+
+
+def test_hedgehog_closed_form_and_repeatability():
+    """m = x/|x| (Sec. 4): the device potential's L2 and H1-seminorm errors
+    against |x| - R equal the oracle's to three digits and fall below the
+    paper's Table 2 values at comparable element counts; two evaluations
+    agree bitwise."""
+    slp = lib()
+    errs = []
+    for n in (4, 8):
+        X, K = meshes.ball_tets(n, R)
+        m, r = _hedgehog(X)
+        pot = slp.slp_potential_create(X, K, 1e-10, _opts(slp, 64, 32 * n // 4))
+        try:
+            phi, _ = _eval(slp, pot, m, 64)
+            again, _ = _eval(slp, pot, m, 64, with_phi1=False)
+            assert np.array_equal(phi, again)
+        finally:
+            slp.slp_potential_destroy(pot)
+        l2, h1 = fem.p1_errors(X, K, phi - (r - R))
+        ref, _, _ = fem.potential(X, K, m)
+        l2o, h1o = fem.p1_errors(X, K, ref - (r - R))
+        assert abs(l2 - l2o) <= 1e-3 * l2o and abs(h1 - h1o) <= 1e-3 * h1o, (l2, l2o, h1, h1o)
+        errs.append((K.shape[0], l2, h1))
+    print("hedgehog (tets, L2, H1 semi):", errs)
+    # Table 2: 3058 elements 1.0e-3 / 9.9e-3; 14169 elements 7.2e-4 / 3.0e-3
+    assert errs[0][1] < 1.0e-3 and errs[1][1] < 7.2e-4 and errs[1][2] < 9.9e-3
+
+
+def test_uniform_magnetisation_and_iteration_limit():
+    """m = e_z: phi_1 = 0 and phi = z/3 up to the flat-facet error; with
+    cg_max_iterations = 2 the hedgehog stops early and reports
+    TOLERANCE_INFEASIBLE."""
+    slp = lib()
+    X, K = meshes.ball_tets(8, R)
+    pot = slp.slp_potential_create(X, K, 1e-10, _opts(slp, 64, 64))
+    try:
+        phi, phi1 = _eval(slp, pot, np.tile([0.0, 0.0, 1.0], (X.shape[0], 1)), 64)
+        assert np.abs(phi1).max() < 1e-14
+        assert np.abs(phi - X[:, 2] / 3).max() < 5e-3 * R  # the oracle: 7.9e-4 = 3.9e-3 R
+    finally:
+        slp.slp_potential_destroy(pot)
+    pot = slp.slp_potential_create(X, K, 1e-10, _opts(slp, 64, 64), cg_max_iterations=2)
+    try:
+        with pytest.raises(slp.SlpError) as e:
+            _eval(slp, pot, _hedgehog(X)[0], 64)
+        assert e.value.status == slp.SLP_ERR_TOLERANCE_INFEASIBLE
+        assert slp.slp_potential_query(pot)["cg_iterations"] == 2
+    finally:
+        slp.slp_potential_destroy(pot)
