@@ -334,9 +334,12 @@ __global__ void __launch_bounds__(NT) k_cg_step(FemDev d, int par) {
         s.alpha = alpha_n;
         s.rr = t[2];
         s.iter += 1;
-        const bool bad = !(isfinite(alpha_n) && isfinite(beta_n) && isfinite(t[2]));
+        // a residual that reached the stopping test (exactly zero included,
+        // where the next step's coefficients are 0/0) ends the inner iteration
+        const bool conv = t[2] <= d.inner2 * s.rr0;
+        const bool bad = !isfinite(t[2]) || (!conv && !(isfinite(alpha_n) && isfinite(beta_n)));
         s.bad = s.bad || bad;
-        s.done = bad || t[2] <= d.inner2 * s.rr0 || s.iter >= d.max_iter;
+        s.done = bad || conv || s.iter >= d.max_iter;
     }
 }
 

@@ -12,7 +12,9 @@ Shapes (Sec. 4 of the paper uses a cube, a sphere and a thin film):
                   projected onto the sphere;
   * ``torus``     a parametric torus with major radius R and minor radius r;
   * ``ball_tets`` a tetrahedral volume mesh of a ball (the finite element
-                  mesh of the paper's sphere tests, Sec. 2.1 and Sec. 4).
+                  mesh of the paper's sphere tests, Sec. 2.1 and Sec. 4);
+  * ``cube_tets`` a tetrahedral volume mesh of a cube (six tetrahedra per
+                  cell of a structured grid).
 
 All surface meshes are closed, 2-manifold and oriented with outward normals
 (counter-clockwise winding seen from outside); volume meshes list each
@@ -216,6 +218,33 @@ def ball_tets(n: int, radius: float = 1.0, layers: int | None = None, core: floa
     nodes = pos[first]
     allk = np.concatenate(tet_keys)
     tets = np.searchsorted(uk, allk)
+    a, b, cc, d = (nodes[tets[:, q]] for q in range(4))
+    vol = np.einsum("ij,ij->i", b - a, np.cross(cc - a, d - a))
+    flip = vol < 0
+    tets[flip, 2], tets[flip, 3] = tets[flip, 3].copy(), tets[flip, 2].copy()
+    return nodes, tets.astype(np.int32)
+
+
+def cube_tets(n: int, side: float = 1.0, nz: int | None = None):
+    """Tetrahedral mesh of the cube [-side/2, side/2]^3 (or, with nz cells
+    along z, of the slab of cubic cells side/n on a side and nz thick): n x n
+    x nz cells, each cut into the six tetrahedra along its main diagonal
+    (the cut _KUHN lists, conforming between cells).  Tetrahedra at the
+    edges have all four nodes on the surface; with nz = 1 every node is.
+    Returns (nodes [N][3], tets [K][4] int32), positively oriented."""
+    nz = n if nz is None else int(nz)
+    if n < 1 or nz < 1:
+        raise ValueError("n and nz must be at least 1")
+    g = np.linspace(-0.5 * side, 0.5 * side, n + 1)
+    gz = (np.arange(nz + 1) - 0.5 * nz) * (side / n)
+    nodes = np.stack([x.ravel() for x in np.meshgrid(g, g, gz, indexing="ij")], 1)
+
+    def idx(i, j, k):
+        return (i * (n + 1) + j) * (nz + 1) + k
+
+    i, j, k = (x.ravel() for x in np.meshgrid(np.arange(n), np.arange(n), np.arange(nz), indexing="ij"))
+    tets = np.concatenate([np.stack([idx(i + (b >> 2 & 1), j + (b >> 1 & 1), k + (b & 1)) for b in path], 1)
+                           for path in _KUHN])
     a, b, cc, d = (nodes[tets[:, q]] for q in range(4))
     vol = np.einsum("ij,ij->i", b - a, np.cross(cc - a, d - a))
     flip = vol < 0

@@ -19,8 +19,9 @@ R = 0.2
 def _opts(slp, prec, grid):
     o = slp.slp_default_opts()
     o.precision = prec
+    g = grid if isinstance(grid, tuple) else (grid, grid, grid)
     for d in range(3):
-        o.grid[d] = grid
+        o.grid[d] = g[d]
     return o
 
 
@@ -120,5 +121,33 @@ def test_uniform_magnetisation_and_iteration_limit():
             _eval(slp, pot, _hedgehog(X)[0], 64)
         assert e.value.status == slp.SLP_ERR_TOLERANCE_INFEASIBLE
         assert slp.slp_potential_query(pot)["cg_iterations"] == 2
+    finally:
+        slp.slp_potential_destroy(pot)
+
+
+@pytest.mark.parametrize("n, nz, grid", [(4, 1, (16, 16, 8)), (2, 2, 16), (6, 6, 16)],
+                         ids=["no_free_node", "one_free_node", "n6"])
+def test_cube_meshes_with_boundary_only_tetrahedra(n, nz, grid):
+    """Structured cubes and slabs: tetrahedra at the edges have all four
+    nodes on the surface (their triangles get no dphi_1/dn term); a slab one
+    cell thick has no free node at all (phi_1 = 0, phi_2 only at the
+    boundary) and the 2^3 cube a single one; phi and phi_1 equal the
+    oracle's in FP64.  (Coarse grids: a triangle of a triangle-integrated
+    plan may span at most 10 cells.)"""
+    slp = lib()
+    X, K = meshes.cube_tets(n, 0.4, nz)
+    m = fields.smooth_random(X, 3)
+    pot = slp.slp_potential_create(X, K, 1e-10, _opts(slp, 64, grid))
+    try:
+        phi, phi1 = _eval(slp, pot, m, 64)
+        info = slp.slp_potential_query(pot)
+        ref, ref1, _ = fem.potential(X, K, m)
+        e = rel_l2(phi, ref)
+        print(f"cube n={n} nz={nz}: {info['n_free']} free nodes, rel-L2 phi {e:.3e}")
+        assert e <= 1e-9, e
+        if info["n_free"]:
+            assert rel_l2(phi1, ref1) <= 1e-9
+        else:
+            assert not phi1.any() and info["cg_iterations"] == 0
     finally:
         slp.slp_potential_destroy(pot)
