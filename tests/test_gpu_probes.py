@@ -181,3 +181,22 @@ def test_probe_refusals():
         slp.slp_probe_destroy(probe)
         for p in (fly, pre, other):
             slp.slp_destroy(p)
+
+
+@pytest.mark.parametrize("integration", [0, 1], ids=["points", "triangles"])
+def test_probes_at_the_vertices_equal_the_boundary_result(integration):
+    """Probes placed on the mesh vertices themselves get the same near-field
+    rows and window weights as the plan's targets, so phi at those probes
+    equals phi at the vertices (FP64, to rounding of the summation order)."""
+    slp = lib()
+    V, T = meshes.icosphere(3)
+    plan = _plan(slp, V, T, 1e-10, 64, (64, 64, 64), integration, 0,
+                 None if integration else slp.SLP_NEAR_PRECOMPUTED)
+    probe = slp.slp_probe_create(plan, V)
+    try:
+        m = fields.smooth_random(V, 9)
+        phi_v, phi_x = _eval(slp, plan, probe, slp.SLP_INPUT_NODAL_MAG, m, V.shape[0], 64)
+        assert np.abs(phi_x - phi_v).max() <= 1e-13 * np.abs(phi_v).max(), np.abs(phi_x - phi_v).max()
+    finally:
+        slp.slp_probe_destroy(probe)
+        slp.slp_destroy(plan)
