@@ -196,7 +196,12 @@ __global__ void __launch_bounds__(256) k_spread(DevPlan p, int fused_kind, const
             set_error(p.err, DEV_ERR_BAD_ITEM);
             continue;
         }
-        window_values<M>(wv, g.x, g.y, g.z, coef, p.wdeg, inv_m, beta, isb);
+        if (sizeof(T) == 8 && p.wtab64_src) {
+            const double *tab = p.wtab64_src + (int64_t)(it.begin + k) * 3 * W;
+            for (int j = lane; j < 3 * W; j += 32) wv[j] = (T)tab[j];
+        } else {
+            window_values<M>(wv, g.x, g.y, g.z, coef, p.wdeg, inv_m, beta, isb);
+        }
         __syncwarp();
         T wx[W];
 #pragma unroll
@@ -430,9 +435,10 @@ __global__ void __launch_bounds__(256, MINB) k_spread_groups(DevPlan p, int fuse
                     if (g + 1 < ng) dst[(g + 1) * WP] = v.y;
                 }
             } else {
+                const double *tab = p.wtab64_src ? p.wtab64_src + (int64_t)(it.begin + g0) * 3 * W + wax * W + wi : nullptr;
                 for (int g = 0; g < ng; ++g) {
                     const T f = ((const T *)(sg + g0 + g))[wax];
-                    T v = kb_window(f + T(M - 1 - wi), inv_m, beta, isb);
+                    T v = tab ? (T)tab[g * 3 * W] : kb_window(f + T(M - 1 - wi), inv_m, beta, isb);
                     if (wax == 0) v *= sq[g0 + g];
                     dst[g * WP] = v;
                 }
@@ -863,6 +869,8 @@ __global__ void __launch_bounds__(256) k_gather(DevPlan p, T *__restrict__ phi) 
                         v = cf[WDEG];
 #pragma unroll
                         for (int k = WDEG - 1; k >= 0; --k) v = v * f + cf[k];
+                    } else if (p.wtab64_tgt) {
+                        v = (T)p.wtab64_tgt[(int64_t)(it.begin + t) * GW + j];
                     } else {
                         v = kb_window(f + T(M - 1 - wi), inv_m, beta, isb);
                     }
@@ -1072,6 +1080,44 @@ template <int M> static cudaError_t wtab_m(const DevPlan &p, float *out, cudaStr
 }
 
 int spread_table_row(int m) { return 3 * ((2 * m + 3) & ~3); }
+
+// FP64 window values, one thread per (point, axis, window point): the same
+// expression the spread and gather kernels evaluate (inv_m = 1/M), so a
+// table entry is bitwise the value the kernel would compute.
+template <int M>
+__global__ void __launch_bounds__(256) k_wtab64_build(const double4 *__restrict__ pts, int64_t n, double beta,
+                                                      double isb, double *__restrict__ out) {
+    constexpr int W = 2 * M;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * 3 * W) return;
+    const int64_t pt = idx / (3 * W);
+    const int j = (int)(idx - pt * 3 * W), ax = j / W, i = j - ax * W;
+    const double4 g = pts[pt];
+    const double f = ax == 0 ? g.x : (ax == 1 ? g.y : g.z);
+    const double inv_m = 1.0 / double(M);
+    out[idx] = kb_window(f + double(M - 1 - i), inv_m, beta, isb);
+}
+
+template <int M> static cudaError_t wtab64_m(const void *pts, int64_t n, double beta, double isb, double *out,
+                                             cudaStream_t s) {
+    const int64_t total = n * 3 * 2 * M;
+    if (total == 0) return cudaSuccess;
+    k_wtab64_build<M><<<(unsigned)((total + 255) / 256), 256, 0, s>>>((const double4 *)pts, n, beta, isb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wtab64_build(const DevPlan &p, const void *pts, int64_t n, double *out, cudaStream_t s) {
+    switch (p.m) {
+        case 2: return wtab64_m<2>(pts, n, p.beta, p.inv_sinh_beta, out, s);
+        case 3: return wtab64_m<3>(pts, n, p.beta, p.inv_sinh_beta, out, s);
+        case 4: return wtab64_m<4>(pts, n, p.beta, p.inv_sinh_beta, out, s);
+        case 5: return wtab64_m<5>(pts, n, p.beta, p.inv_sinh_beta, out, s);
+        case 6: return wtab64_m<6>(pts, n, p.beta, p.inv_sinh_beta, out, s);
+        case 7: return wtab64_m<7>(pts, n, p.beta, p.inv_sinh_beta, out, s);
+        case 8: return wtab64_m<8>(pts, n, p.beta, p.inv_sinh_beta, out, s);
+    }
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_wtab_build(const DevPlan &p, float *out, cudaStream_t s) {
     switch (p.m) {

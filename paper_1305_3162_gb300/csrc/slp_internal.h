@@ -108,6 +108,10 @@ struct DevPlan {
     int gather_chunk;             // most targets in one gather item (<= GATHER_CHUNK)
     const int *sgroups;           // cell groups: first source (within the item) | count << 16
     const int *sgroup_cell;       // local cell of each group in its item's tile: lx | ly << 8 | lz << 16
+    // FP64 plans: window values of every sorted source and target, [count][3][2m]
+    // (axis-major per point), computed once at plan time by the same device
+    // function the kernels would call (NULL: the kernels evaluate the window)
+    const double *wtab64_src, *wtab64_tgt;
     const void *wtab;             // FP32 table spread: [Q][3][WP] window values per sorted source (NULL: the
                                   // spread evaluates the window)
     const int *sgroup_off;        // [n_spread][SPREAD_WARPS + 1] group list bounds of each item
@@ -250,6 +254,9 @@ cudaError_t launch_gather(const DevPlan &p, void *d_phi, cudaStream_t s);
 // to a multiple of 4) and its plan-time build into `out` ([Q] rows)
 int spread_table_row(int m);
 cudaError_t launch_wtab_build(const DevPlan &p, float *out, cudaStream_t s);
+// FP64 window values of n sorted points (sources or targets, grid coordinates
+// in pts) into out ([n][3][2m])
+cudaError_t launch_wtab64_build(const DevPlan &p, const void *pts, int64_t n, double *out, cudaStream_t s);
 // near field into phi_part (atomics: phi_part must be zero; deterministic: per-item partials, then the reduction
 // overwrites phi_part)
 cudaError_t launch_near(const DevPlan &p, cudaStream_t s);

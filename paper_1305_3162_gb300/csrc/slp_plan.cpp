@@ -1195,6 +1195,26 @@ template <typename T> slp_status upload_all(slp_plan_s &p) {
         TRY(cuda_status(cudaDeviceSynchronize(), "window table"));
         d.wtab = wt;
     }
+    d.wtab64_src = d.wtab64_tgt = nullptr;
+    if (sizeof(T) == 8) {
+        // FP64: the window values of every sorted source and target, built once
+        // here (this GPU's FP64 rate makes the window's sqrt and sinh the
+        // largest cost of the FP64 spread and gather); at most 2 GB
+        const size_t per = sizeof(double) * 3 * 2 * (size_t)p.m;
+        const size_t nsrc = p.opts.integration ? 0 : (size_t)p.Q;
+        if (per * (nsrc + (size_t)p.N) <= ((size_t)2 << 30)) {
+            void *ws = nullptr, *wt = nullptr;
+            if (nsrc > 0) {
+                TRY(dalloc(p, &ws, per * nsrc));
+                TRY(cuda_status(slp::launch_wtab64_build(d, d.src_grid, (int64_t)nsrc, (double *)ws, 0), "window table"));
+            }
+            TRY(dalloc(p, &wt, std::max<size_t>(per * (size_t)p.N, 16)));
+            TRY(cuda_status(slp::launch_wtab64_build(d, d.tgt_grid, p.N, (double *)wt, 0), "window table"));
+            TRY(cuda_status(cudaDeviceSynchronize(), "window table"));
+            d.wtab64_src = (const double *)ws;
+            d.wtab64_tgt = (const double *)wt;
+        }
+    }
     TRY(upload(p, &ptr, p.gather_items.data(), p.gather_items.size()));
     d.gather_items = (const slp::TileItem *)ptr;
     d.n_gather = (int)p.gather_items.size();
@@ -1910,6 +1930,7 @@ template <typename T> slp_status probe_build(slp_plan_s &p, const double *pts, i
     slp::DevPlan v = p.dp;
     v.N = n;
     v.ks = 1;
+    v.wtab64_tgt = nullptr;  // the plan's target window table does not cover the probes
     std::vector<T4> tg(n);
     for (int64_t i = 0; i < n; ++i) {
         const double *g = &grid[4 * i];
