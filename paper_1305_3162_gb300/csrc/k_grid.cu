@@ -107,160 +107,10 @@ template <int M, int TS> struct TileGeom {
 };
 
 // Window values w[axis][i] = psi(f_axis + M - 1 - i) for the 3 x 2M window
-// points of one source or target, computed by the lanes of one warp.
-// FP32: per-interval polynomial in the fraction f (coefficients fitted on the
-// host, max error ~1e-10 of psi(0)); FP64: the closed form.
+// points of a source or target.  FP32: per-interval polynomial in the
+// fraction f (coefficients fitted on the host, max error ~1e-10 of psi(0));
+// FP64: the closed form (or the plan's FP64 window tables).
 constexpr int WDEG = 9;  // degree of the FP32 window polynomials (set by the plan)
-
-template <int M>
-__device__ __forceinline__ void window_values(float *wv, float fx, float fy, float fz, const float *__restrict__ coef,
-                                              int, float, float, float) {
-    constexpr int W = 2 * M;
-    const int lane = threadIdx.x & 31;
-    for (int j = lane; j < 3 * W; j += 32) {
-        const int ax = j / W, i = j - ax * W;
-        const float f = ax == 0 ? fx : (ax == 1 ? fy : fz);
-        const float *c = coef + i * (WDEG + 1);
-        float v = c[WDEG];
-#pragma unroll
-        for (int k = WDEG - 1; k >= 0; --k) v = fmaf(v, f, c[k]);
-        wv[j] = v;
-    }
-}
-template <int M>
-__device__ __forceinline__ void window_values(double *wv, double fx, double fy, double fz, const double *, int,
-                                              double inv_m, double beta, double isb) {
-    constexpr int W = 2 * M;
-    const int lane = threadIdx.x & 31;
-    for (int j = lane; j < 3 * W; j += 32) {
-        const int ax = j / W, i = j - ax * W;
-        const double f = ax == 0 ? fx : (ax == 1 ? fy : fz);
-        wv[j] = kb_window(f + double(M - 1 - i), inv_m, beta, isb);
-    }
-}
-
-// ---------------------------------------------------------------- spread
-// Each warp accumulates into its own copy of the halo tile, so the updates
-// are plain read-modify-writes: within one warp instruction every lane owns a
-// different (y, z) row of the source's window box, and consecutive sources of
-// a warp are ordered by __syncwarp.  The warp copies are summed in a fixed
-// order and the tile is added to the global grid, 16 bytes per atomic where
-// the row does not wrap around the periodic grid.
-template <typename T, int M, int TS>
-__global__ void __launch_bounds__(256) k_spread(DevPlan p, int fused_kind, const T *__restrict__ in) {
-    pdl_wait();
-    pdl_trigger();
-    typedef typename VecT<T>::T4 T4;
-    typedef TileGeom<M, TS> G;
-    constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO, XE = G::XE;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    T *tiles = (T *)smem_raw;
-    T *coef = tiles + nwarps * G::SIZE;
-    const int ncoef = W * (p.wdeg + 1);
-    T *wv = coef + ((ncoef + 3) & ~3) + warp * (3 * W);
-    T *my = tiles + warp * G::SIZE;
-
-    // the item's sources (positions and charges), staged once per block
-    const size_t head = ((size_t)nwarps * G::SIZE + ((ncoef + 3) & ~3) + (size_t)nwarps * 3 * W + 3) & ~(size_t)3;
-    T4 *sg = (T4 *)(tiles + head);
-    T *sq = (T *)(sg + p.spread_chunk);
-
-    const TileItem it = p.spread_items[blockIdx.x];
-    const int nsrc = it.end - it.begin;
-    if (p.ks > 1) in = (const T *)p.in_st[blockIdx.y];  // state of a batched launch
-    {
-        // charges either from the charge kernel (qbuf) or computed here from
-        // the input (fused_kind >= 0)
-        const T4 *src = (const T4 *)p.src_grid + it.begin;
-        const T *qb = (const T *)p.qbuf + it.begin;
-        for (int i = threadIdx.x; i < nsrc; i += blockDim.x) {
-            sg[i] = src[i];
-            sq[i] = fused_kind >= 0 ? source_charge<T>(p, it.begin + i, fused_kind, in) : qb[i];
-        }
-    }
-    for (int i = threadIdx.x; i < nwarps * G::SIZE; i += blockDim.x) tiles[i] = T(0);
-    if (sizeof(T) == 4)
-        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) coef[i] = ((const T *)p.wcoef)[i];
-    __syncthreads();
-
-    const T inv_m = T(1) / T(M);
-    const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
-    for (int k = warp; k < nsrc; k += nwarps) {
-        const T4 g = sg[k];
-        const T qk = sq[k];
-        int cx, cy, cz;
-        unpack_cell(packed_cell(g.w), cx, cy, cz);
-        const int lx = cx - it.c0x, ly = cy - it.c0y, lz = cz - it.c0z;
-        if ((unsigned)lx >= (unsigned)TS || (unsigned)ly >= (unsigned)TS || (unsigned)lz >= (unsigned)TS) {
-            set_error(p.err, DEV_ERR_BAD_ITEM);
-            continue;
-        }
-        if (sizeof(T) == 8 && p.wtab64_src) {
-            const double *tab = p.wtab64_src + (int64_t)(it.begin + k) * 3 * W;
-            for (int j = lane; j < 3 * W; j += 32) wv[j] = (T)tab[j];
-        } else {
-            window_values<M>(wv, g.x, g.y, g.z, coef, p.wdeg, inv_m, beta, isb);
-        }
-        __syncwarp();
-        T wx[W];
-#pragma unroll
-        for (int ix = 0; ix < W; ++ix) wx[ix] = wv[ix];
-        T *base = my + lz * PS + ly * RS + lx + XO;
-#pragma unroll
-        for (int rep = 0; rep < (W * W + 31) / 32; ++rep) {
-            const int pi = lane + 32 * rep;
-            if (pi < W * W) {
-                const int iy = pi % W, iz = pi / W;
-                const T wyz = qk * wv[2 * W + iz] * wv[W + iy];
-                T *row = base + iz * PS + iy * RS;
-                T r[W];
-#pragma unroll
-                for (int ix = 0; ix < W; ++ix) r[ix] = row[ix];
-#pragma unroll
-                for (int ix = 0; ix < W; ++ix) row[ix] = r[ix] + wyz * wx[ix];
-            }
-        }
-        __syncwarp();
-    }
-    __syncthreads();
-
-    const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
-    const int gxs = it.c0x - M + 1 - XO, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
-    T *grid = (T *)p.gridA + blockIdx.y * p.st_grid;
-    // 16-byte vector atomics need an aligned row start inside the grid (TS a
-    // multiple of 4 makes gxs a multiple of 4 by construction of XO)
-    const bool xin = gxs >= 0 && gxs + XE <= Lx && (gxs & 3) == 0;
-    if (sizeof(T) == 4 && TS % 4 == 0 && xin) {
-        // 4-wide: rows of XE/4 aligned vectors
-        constexpr int NV = XE / 4;
-        for (int i = threadIdx.x; i < TE * TE * NV; i += blockDim.x) {
-            const int v = i % NV, r = i / NV;
-            const int iy = r % TE, iz = r / TE;
-            float a[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int w = 0; w < nwarps; ++w) {
-                const T *t = tiles + w * G::SIZE + iz * PS + iy * RS + 4 * v;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) a[e] += (float)t[e];
-            }
-            if (a[0] == 0.f && a[1] == 0.f && a[2] == 0.f && a[3] == 0.f) continue;
-            const int gy = (gy0 + iy) & (Ly - 1), gz = (gz0 + iz) & (Lz - 1);
-            float4 *dst = (float4 *)((float *)grid + ((int64_t)gz * Ly + gy) * Lx + gxs) + v;
-            atomicAdd(dst, make_float4(a[0], a[1], a[2], a[3]));
-        }
-    } else {
-        for (int i = threadIdx.x; i < TE * TE * XE; i += blockDim.x) {
-            const int x = i % XE, r = i / XE;
-            const int iy = r % TE, iz = r / TE;
-            T v = T(0);
-            for (int w = 0; w < nwarps; ++w) v += tiles[w * G::SIZE + iz * PS + iy * RS + x];
-            if (v == T(0)) continue;
-            const int gx = (gxs + x) & (Lx - 1);
-            const int gy = (gy0 + iy) & (Ly - 1), gz = (gz0 + iz) & (Lz - 1);
-            atomicAdd(grid + ((int64_t)gz * Ly + gy) * Lx + gx, v);
-        }
-    }
-}
 
 // ---------------------------------------------------------------- spread, cell groups
 // Variant for 2M <= 10: runs of consecutive sources that share a grid cell
@@ -963,11 +813,119 @@ __global__ void k_zero4(float4 *p, int64_t n4) {
 }
 
 // ---------------------------------------------------------------- launchers
-template <typename T, int M, int TS> static size_t spread_smem(int nwarps, int wdeg, int chunk) {
+// Spread of wide windows (2m > 10): one tile per block, no per-warp copies.
+// The block stages the window values of SB sources at a time in shared
+// memory (from the FP64 window table or evaluated), the x values times the
+// charge; then warp w adds, source after source, the box points of the
+// tile's z planes z = w, w + nwarps, ... (lanes over the (x, y) points of a
+// plane), so every tile element is updated by one warp in source order: no
+// atomics, and one tile holds many sources, so the flush of the halo tile
+// into the grid (global atomics) is shared by all of them.
+template <typename T, int M, int TS> struct PlaneSmem {
     typedef TileGeom<M, TS> G;
-    const int ncoef = 2 * M * (wdeg + 1);
-    const size_t head = (((size_t)nwarps * G::SIZE + ((ncoef + 3) & ~3) + (size_t)nwarps * 3 * 2 * M) + 3) & ~(size_t)3;
-    return head * sizeof(T) + (size_t)chunk * (4 * sizeof(T) + sizeof(T));
+    static constexpr int SB = 32;  // sources per staged batch
+    __host__ __device__ static size_t coef_off() { return ((size_t)G::SIZE + 3) & ~(size_t)3; }
+    __host__ __device__ static size_t wv_off(int wdeg) {
+        return coef_off() + (((size_t)2 * M * (wdeg + 1) + 3) & ~(size_t)3);
+    }
+    __host__ __device__ static size_t bytes(int wdeg) {
+        return (wv_off(wdeg) + (size_t)SB * 3 * 2 * M) * sizeof(T) + (size_t)SB * sizeof(int);
+    }
+};
+
+template <typename T, int M, int TS>
+__global__ void __launch_bounds__(256) k_spread_planes(DevPlan p, int fused_kind, const T *__restrict__ in) {
+    pdl_wait();
+    pdl_trigger();
+    typedef typename VecT<T>::T4 T4;
+    typedef TileGeom<M, TS> G;
+    typedef PlaneSmem<T, M, TS> SM;
+    constexpr int W = G::W, TE = G::TE, RS = G::RS, PS = G::PS, XO = G::XO, XE = G::XE, SB = SM::SB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    T *tile = (T *)smem_raw;
+    T *coef = tile + SM::coef_off();
+    T *wv = tile + SM::wv_off(p.wdeg);  // [SB][3W]
+    int *cell = (int *)(wv + SB * 3 * W);
+    const int ncoef = W * (p.wdeg + 1);
+
+    const TileItem it = p.spread_items[blockIdx.x];
+    const int nsrc = it.end - it.begin;
+    if (p.ks > 1) in = (const T *)p.in_st[blockIdx.y];  // state of a batched launch
+    for (int i = threadIdx.x; i < G::SIZE; i += blockDim.x) tile[i] = T(0);
+    if (sizeof(T) == 4)
+        for (int i = threadIdx.x; i < ncoef; i += blockDim.x) coef[i] = ((const T *)p.wcoef)[i];
+    const T inv_m = T(1) / T(M);
+    const T beta = (T)p.beta, isb = (T)p.inv_sinh_beta;
+    const T4 *src = (const T4 *)p.src_grid;
+    for (int b0 = 0; b0 < nsrc; b0 += SB) {
+        const int nb = min(SB, nsrc - b0);
+        __syncthreads();  // the previous batch's values are no longer read; the tile and coef are set
+        for (int idx = threadIdx.x; idx < nb * 3 * W; idx += blockDim.x) {
+            const int sidx = idx / (3 * W), j = idx - sidx * 3 * W, ax = j / W, i = j - ax * W;
+            const int k = it.begin + b0 + sidx;
+            T v;
+            if (sizeof(T) == 8 && p.wtab64_src) {
+                v = (T)p.wtab64_src[(int64_t)k * 3 * W + j];
+            } else {
+                const T4 g = src[k];
+                const T f = ax == 0 ? g.x : (ax == 1 ? g.y : g.z);
+                if (sizeof(T) == 4) {
+                    const T *c = coef + i * (WDEG + 1);
+                    v = c[WDEG];
+#pragma unroll
+                    for (int e = WDEG - 1; e >= 0; --e) v = v * f + c[e];
+                } else {
+                    v = kb_window(f + T(M - 1 - i), inv_m, beta, isb);
+                }
+            }
+            if (ax == 0)
+                v *= fused_kind >= 0 ? source_charge<T>(p, k, fused_kind, in) : ((const T *)p.qbuf)[k];
+            wv[sidx * 3 * W + j] = v;
+        }
+        for (int sidx = threadIdx.x; sidx < nb; sidx += blockDim.x) {
+            int cx, cy, cz;
+            unpack_cell(packed_cell(src[it.begin + b0 + sidx].w), cx, cy, cz);
+            const int lx = cx - it.c0x, ly = cy - it.c0y, lz = cz - it.c0z;
+            if ((unsigned)lx >= (unsigned)TS || (unsigned)ly >= (unsigned)TS || (unsigned)lz >= (unsigned)TS) {
+                set_error(p.err, DEV_ERR_BAD_ITEM);
+                cell[sidx] = -1;
+            } else {
+                cell[sidx] = lx | (ly << 8) | (lz << 16);
+            }
+        }
+        __syncthreads();
+        for (int sidx = 0; sidx < nb; ++sidx) {
+            const int c = cell[sidx];
+            if (c < 0) continue;
+            const int lx = c & 255, ly = (c >> 8) & 255, lz = c >> 16;
+            const T *w = wv + sidx * 3 * W;
+            // the first of the warp's planes at or after lz
+            int iz = ((warp - lz) % nwarps + nwarps) % nwarps;
+            for (; iz < W; iz += nwarps) {
+                const T wz = w[2 * W + iz];
+                T *plane = tile + (lz + iz) * PS + ly * RS + lx + XO;
+                for (int pi = lane; pi < W * W; pi += 32) {
+                    const int iy = pi / W, ix = pi - iy * W;
+                    plane[iy * RS + ix] += w[ix] * (w[W + iy] * wz);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    const int Lx = p.L[0], Ly = p.L[1], Lz = p.L[2];
+    const int gxs = it.c0x - M + 1 - XO, gy0 = it.c0y - M + 1, gz0 = it.c0z - M + 1;
+    T *grid = (T *)p.gridA + blockIdx.y * p.st_grid;
+    for (int i = threadIdx.x; i < TE * TE * XE; i += blockDim.x) {
+        const int x = i % XE, r = i / XE;
+        const int iy = r % TE, iz = r / TE;
+        const T v = tile[iz * PS + iy * RS + x];
+        if (v == T(0)) continue;
+        const int gx = (gxs + x) & (Lx - 1);
+        const int gy = (gy0 + iy) & (Ly - 1), gz = (gz0 + iz) & (Lz - 1);
+        atomicAdd(grid + ((int64_t)gz * Ly + gy) * Lx + gx, v);
+    }
 }
 
 template <typename T, int M, int TS>
@@ -1014,14 +972,16 @@ static cudaError_t spread_mt(const DevPlan &p, int fused_kind, const void *in, c
             return go(k_spread_groups<T, M, TS, 1>);
         }
     }
-    int nw = 8;
-    while (nw > 1 && spread_smem<T, M, TS>(nw, p.wdeg, p.spread_chunk) > 100 * 1024) nw >>= 1;
-    const size_t sm = spread_smem<T, M, TS>(nw, p.wdeg, p.spread_chunk);
+    const size_t sm = PlaneSmem<T, M, TS>::bytes(p.wdeg);
     if (sm > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_spread<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaError_t e = cudaFuncSetAttribute(k_spread_planes<T, M, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
-    if (p.n_spread > 0) { const cudaError_t le = launch_k(k_spread<T, M, TS>, dim3(p.n_spread, p.ks), 32 * nw, sm, s, p, fused_kind, (const T *)in); if (le != cudaSuccess) return le; }
+    if (p.n_spread > 0) {
+        const cudaError_t le = launch_k(k_spread_planes<T, M, TS>, dim3(p.n_spread, p.ks), 256, sm, s, p, fused_kind,
+                                        (const T *)in);
+        if (le != cudaSuccess) return le;
+    }
     return cudaGetLastError();
 }
 

@@ -538,10 +538,21 @@ slp_status choose_parameters(slp_plan_s &p) {
     // tile size: 8^3 cells, halved while a halo tile (padded layout of the
     // spread/gather kernels) exceeds 40 KB, so several warps get a private copy
     // (FP32 m <= 5 keeps 8: on sparse meshes the larger tiles flush less halo
-    // per source; FP64 and wider windows end at 4 or 2)
+    // per source; FP64 ends at 4 or 2).  Windows wider than 10 points are
+    // spread into one tile per block (no private copies): halved while that
+    // tile exceeds 96 KB.
     const size_t esz = p.prec == 64 ? 8 : 4;
     p.TS = 8;
-    while (p.TS > 2 && std::pow((double)(p.TS + 2 * p.m + 3), 3) * esz > 40 * 1024) p.TS /= 2;
+    if (p.m > 5) {
+        auto tile_bytes = [&](int ts) {  // TileGeom's padded layout
+            const int te = ts + 2 * p.m - 1, xo = (4 - ((p.m - 1) % 4)) % 4, xe = (xo + te + 3) / 4 * 4;
+            const int rs = xe % 8 == 4 ? xe : xe + 4, ps = (te * rs + 31) / 32 * 32 + 1;
+            return (size_t)te * ps * esz;
+        };
+        while (p.TS > 2 && tile_bytes(p.TS) > 96 * 1024) p.TS /= 2;
+    } else {
+        while (p.TS > 2 && std::pow((double)(p.TS + 2 * p.m + 3), 3) * esz > 40 * 1024) p.TS /= 2;
+    }
     // targets: larger tiles (fewer gather items, each tile load shared by more targets)
     p.TSg = 8;
     while (p.TSg > 2 && std::pow((double)(p.TSg + 2 * p.m + 3), 3) * esz > 40 * 1024) p.TSg /= 2;
