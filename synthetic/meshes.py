@@ -14,7 +14,9 @@ Shapes (Sec. 4 of the paper uses a cube, a sphere and a thin film):
   * ``ball_tets`` a tetrahedral volume mesh of a ball (the finite element
                   mesh of the paper's sphere tests, Sec. 2.1 and Sec. 4);
   * ``cube_tets`` a tetrahedral volume mesh of a cube (six tetrahedra per
-                  cell of a structured grid).
+                  cell of a structured grid);
+  * ``shell_tets`` a tetrahedral mesh of a spherical shell (two boundary
+                  spheres: the outer one and the surface of the cavity).
 
 All surface meshes are closed, 2-manifold and oriented with outward normals
 (counter-clockwise winding seen from outside); volume meshes list each
@@ -245,6 +247,59 @@ def cube_tets(n: int, side: float = 1.0, nz: int | None = None):
     i, j, k = (x.ravel() for x in np.meshgrid(np.arange(n), np.arange(n), np.arange(nz), indexing="ij"))
     tets = np.concatenate([np.stack([idx(i + (b >> 2 & 1), j + (b >> 1 & 1), k + (b & 1)) for b in path], 1)
                            for path in _KUHN])
+    a, b, cc, d = (nodes[tets[:, q]] for q in range(4))
+    vol = np.einsum("ij,ij->i", b - a, np.cross(cc - a, d - a))
+    flip = vol < 0
+    tets[flip, 2], tets[flip, 3] = tets[flip, 3].copy(), tets[flip, 2].copy()
+    return nodes, tets.astype(np.int32)
+
+
+def shell_tets(n: int, r_in: float, radius: float, layers: int | None = None):
+    """Tetrahedral mesh of the spherical shell r_in <= |x| <= radius: the
+    cubed-sphere patches of ``ball_tets`` (n x n columns over each face of
+    the cube) with ``layers`` (default n/2) hexahedral layers from the inner
+    sphere to the outer one, node k of a column at radius
+    r_in + (radius - r_in) k / layers, every hexahedron cut into six
+    tetrahedra along its diagonal as in ``ball_tets``.  n even.  Returns
+    (nodes [N][3], tets [K][4] int32), positively oriented."""
+    if n < 2 or n % 2 or not (0.0 < r_in < radius):
+        raise ValueError("n must be even and 0 < r_in < radius")
+    nr = max(1, n // 2) if layers is None else int(layers)
+    H = n // 2
+    W = n + 1
+
+    def key(q, k):
+        return (((q[:, 0] + H) * W + (q[:, 1] + H)) * W + (q[:, 2] + H)) * (nr + 1) + k
+
+    g = np.arange(-H, H + 1)
+    c = np.arange(-H, H)
+    keys, pos, tet_keys = [], [], []
+    for ax in range(3):
+        o = [d for d in range(3) if d != ax]
+        for side in (-1, 1):
+            u, v = (x.ravel() for x in np.meshgrid(g, g, indexing="ij"))
+            q = np.zeros((u.size, 3), dtype=np.int64)
+            q[:, ax] = side * H
+            q[:, o[0]], q[:, o[1]] = u, v
+            dirs = q / np.linalg.norm(q, axis=1, keepdims=True)
+            for k in range(nr + 1):
+                keys.append(key(q, k))
+                pos.append(dirs * (r_in + (radius - r_in) * k / nr))
+            uu, vv, kk = (x.ravel() for x in np.meshgrid(c, c, np.arange(nr), indexing="ij"))
+            for path in _KUHN:
+                cols = []
+                for b in path:
+                    du, dv, dk = b >> 2 & 1, b >> 1 & 1, b & 1
+                    qq = np.zeros((uu.size, 3), dtype=np.int64)
+                    qq[:, ax] = side * H
+                    qq[:, o[0]], qq[:, o[1]] = uu + du, vv + dv
+                    cols.append(key(qq, kk + dk))
+                tet_keys.append(np.stack(cols, 1))
+    keys = np.concatenate(keys)
+    pos = np.concatenate(pos)
+    uk, first = np.unique(keys, return_index=True)
+    nodes = pos[first]
+    tets = np.searchsorted(uk, np.concatenate(tet_keys))
     a, b, cc, d = (nodes[tets[:, q]] for q in range(4))
     vol = np.einsum("ij,ij->i", b - a, np.cross(cc - a, d - a))
     flip = vol < 0

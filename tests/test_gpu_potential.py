@@ -151,3 +151,37 @@ def test_cube_meshes_with_boundary_only_tetrahedra(n, nz, grid):
             assert not phi1.any() and info["cg_iterations"] == 0
     finally:
         slp.slp_potential_destroy(pot)
+
+
+@pytest.mark.parametrize("n, prec, tol, grid, bar", [(4, 64, 1e-10, 32, 1e-9), (8, 32, 1e-5, 64, 1e-5)],
+                         ids=["n4_fp64", "n8_fp32"])
+def test_shell_with_a_cavity(n, prec, tol, grid, bar):
+    """A spherical shell 0.1 <= |x| <= 0.2: two boundary components, the
+    cavity's faces wound toward the centre, no node inside the cavity.
+    phi and phi_1 equal the oracle's for a random field and the hedgehog;
+    the uniform field gives phi_1 = 0 and, up to the flat-facet error the
+    oracle also makes, phi = z (1 - a^3/|x|^3)/3."""
+    slp = lib()
+    a, b = 0.1, 0.2
+    X, K = meshes.shell_tets(n, a, b)
+    r = np.linalg.norm(X, axis=1)
+    pot = slp.slp_potential_create(X, K, tol, _opts(slp, prec, grid))
+    try:
+        info = slp.slp_potential_query(pot)
+        assert info["n_faces"] == 24 * n * n and info["n_free"] + info["n_boundary"] == X.shape[0]
+        for field in ("random", "hedgehog", "uniform"):
+            m = {"random": lambda: fields.smooth_random(X, 29), "hedgehog": lambda: X / r[:, None],
+                 "uniform": lambda: np.tile([0.0, 0.0, 1.0], (X.shape[0], 1))}[field]()
+            phi, phi1 = _eval(slp, pot, m, prec)
+            ref, ref1, _ = fem.potential(X, K, m)
+            e = rel_l2(phi, ref)
+            print(f"shell n={n} {field}: rel-L2 phi {e:.3e}, {slp.slp_potential_query(pot)['cg_iterations']} steps")
+            assert e <= bar, (field, e)
+            if field == "uniform":
+                assert np.abs(phi1).max() < 1e-14
+                exact = X[:, 2] * (1 - a ** 3 / r ** 3) / 3
+                assert np.abs(phi - exact).max() <= np.abs(ref - exact).max() + bar * np.abs(ref).max()
+            else:
+                assert rel_l2(phi1, ref1) <= bar
+    finally:
+        slp.slp_potential_destroy(pot)

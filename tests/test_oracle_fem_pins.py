@@ -2,7 +2,10 @@
 against closed forms and exact integrals, independent of the oracle's own
 formulas: the uniformly magnetised sphere (phi_1 = 0, phi = m . x / 3), the
 hedgehog m = x/|x| of Sec. 4 (phi = |x| - R, phi_2 = 0), a linear m with
-div m = 3 (phi_1 = (|x|^2 - R^2)/2), and the P1 forms on linear functions."""
+div m = 3 (phi_1 = (|x|^2 - R^2)/2), the P1 forms on linear functions, and a
+spherical shell a <= |x| <= b, whose boundary has two components (uniform m:
+phi = m . x (1 - a^3/|x|^3)/3; hedgehog: phi = |x| - b,
+phi_1 = |x| - (a + b) + ab/|x|)."""
 import numpy as np
 import pytest
 
@@ -128,3 +131,69 @@ def test_iterative_phi1_and_sampled_potential_equal_the_direct_forms():
     sel = np.arange(0, X.shape[0], 7)
     got, _ = fem.potential_at(X, K, m, sel)
     assert np.linalg.norm(got - phi[sel]) <= 1e-11 * np.linalg.norm(phi[sel])
+
+
+A, B = 0.1, 0.2  # the shell's inner and outer radii
+
+
+def test_shell_mesh_has_two_boundary_components_wound_away_from_the_domain():
+    """The shell's boundary faces lie on the two spheres (24 n^2 of them),
+    every face's normal points out of the volume (toward the centre on the
+    cavity), and the outer surface's enclosed volume minus the cavity's
+    equals the tets' volume."""
+    for n in (4, 8):
+        X, K = meshes.shell_tets(n, A, B)
+        v = meshes.tet_volumes(X, K)
+        assert v.min() > 0.1 * v.mean()
+        faces, _, _ = fem.boundary_faces(X, K)
+        assert faces.shape[0] == 24 * n * n
+        rad = np.linalg.norm(X[faces], axis=2)
+        inner = np.all(np.abs(rad - A) < 1e-15, axis=1)
+        outer = np.all(np.abs(rad - B) < 1e-15, axis=1)
+        assert (inner ^ outer).all() and inner.sum() == outer.sum()
+        cen = X[faces].mean(axis=1)
+        nrm = np.cross(X[faces[:, 1]] - X[faces[:, 0]], X[faces[:, 2]] - X[faces[:, 0]])
+        out = np.einsum("ij,ij->i", nrm, cen)
+        assert (out[outer] > 0).all() and (out[inner] < 0).all()
+        vo = meshes.mesh_stats(X, faces[outer])["signed_volume"]
+        vi = meshes.mesh_stats(X, faces[inner])["signed_volume"]
+        assert vo > 0 and vi < 0 and abs(vo + vi - v.sum()) < 1e-14
+
+
+def test_uniformly_magnetised_shell():
+    """m = e: b = 0, so phi_1 = 0; phi is the uniformly magnetised ball of
+    radius b minus that of radius a, e . x (1 - a^3/|x|^3)/3 in the shell,
+    the nodal error falling at second order (flat facets on both spheres)."""
+    e = np.array([0.0, 0.6, 0.8])
+    prev = None
+    for n in (4, 8, 16):
+        X, K = meshes.shell_tets(n, A, B)
+        r = np.linalg.norm(X, axis=1)
+        phi, p1, _ = fem.potential(X, K, np.tile(e, (X.shape[0], 1)))
+        assert np.abs(p1).max() < 1e-15
+        err = np.abs(phi - X @ e * (1 - A ** 3 / r ** 3) / 3).max()
+        assert err < 0.015 * B, (n, err)
+        if prev is not None:
+            assert err < prev / 3.5, (n, err, prev)
+        prev = err
+
+
+def test_hedgehog_in_a_shell():
+    """m = x/|x| in the shell: the charge -div m = -2/|x| and the surface
+    charges +1 (outer) and -1 (cavity) add to zero, so phi = |x| - b in the
+    shell.  phi_1 = |x| - (a + b) + ab/|x| (zero on both spheres) converges
+    at second order in L2; g takes dphi_1/dn from a one-sided P1 gradient,
+    and as phi_1 is curved along the radius (unlike the ball's |x| - R) phi
+    converges at first order in the radial spacing.  A cavity charge of the
+    wrong sign would leave an error of order a that does not fall."""
+    prev = None
+    for n in (4, 8, 16):
+        X, K = meshes.shell_tets(n, A, B)
+        m, r = _hedgehog(X)
+        phi, p1, _ = fem.potential(X, K, m)
+        l2, _ = fem.p1_errors(X, K, phi - (r - B))
+        l21, _ = fem.p1_errors(X, K, p1 - (r - (A + B) + A * B / r))
+        if prev is not None:
+            assert l2 < prev[0] / 1.7 and l21 < prev[1] / 2.8, (n, l2, l21, prev)
+        prev = (l2, l21)
+    assert l2 < 0.25 * A * np.sqrt(4 / 3 * np.pi * (B ** 3 - A ** 3)), l2  # n = 16: 0.22
