@@ -20,18 +20,26 @@
 //   alpha_{k+1} = gamma_{k+1} / (delta_{k+1} - beta_{k+1} gamma_{k+1} / alpha_k),
 // which needs both dot products at one point of the step.  One launch does
 // a step: every vector update is per row, and u_{k+1} at the columns the
-// product gathers is formed there from r_k, w_k and s_{k-1} (the step reads
-// the buffers of one parity and writes those of the other).  The launch's
-// block partial sums are combined by its last block (the one whose arrival
-// completes the grid; no block waits), in one fixed order, so the solve
-// repeats bitwise.  The inner steps give each row one thread over the
-// matrix in slices of 32 rows (every lane busy with its own row's update,
-// coalesced reads of the entries); the load uses groups of 8 lanes per row
-// over CSR.  Steps launched after the inner stop return at once, so a host
-// that queues steps ahead of the stopping test wastes only empty launches.
+// product gathers is formed there from r_k, w_k and s_{k-1}, which a row
+// keeps together with its 1 / diagonal in one 16-byte record (the step
+// reads the records of one parity and writes those of the other).  A launch
+// leaves its blocks' partial sums of gamma_{k+1}, delta_{k+1} and r.r; every
+// block of the next launch adds them itself, in one fixed order, and derives
+// alpha_{k+1} and beta_{k+1}, so all blocks hold the same scalars, no launch
+// ends in a one-block tail, and the solve repeats bitwise.  An inner
+// iteration starts with a set-up launch (the same kernel with alpha = beta =
+// 0), which forms w_0 = S u_0 and the first partial sums.  The launches are
+// chained by programmatic dependent launch: before its dependency wait a warp
+// loads the first column indices and entries of its slice (plan data).  The
+// inner steps give each row one thread over the matrix in slices of 32 rows
+// (every lane busy with its own row's update, coalesced reads of the
+// entries); the load uses groups of 8 lanes per row over CSR.  Steps
+// launched after the inner stop return at once, so a host that queues steps
+// ahead of the stopping test wastes only empty launches.
 #include <algorithm>
 #include <cmath>
 
+#include "dev_common.cuh"
 #include "slp_fem.h"
 
 namespace slp {
@@ -73,7 +81,6 @@ __device__ bool block_flag(const int *flag) {
 }
 
 __device__ __forceinline__ double *partials(const FemDev &d, double) { return d.part; }
-__device__ __forceinline__ float *partials(const FemDev &d, float) { return d.part32; }
 
 // Store this block's K partial sums (held by thread 0); returns true in the
 // block that arrives last, after which that block may read every block's
@@ -200,7 +207,7 @@ __global__ void __launch_bounds__(NT) k_fem_residual(FemDev d) {
         hh += rho * rho;
     }
     const double v[1] = {block_sum(hh, sh)};
-    if (!arrive(d, v, &d.st->count[3])) return;
+    if (!arrive(d, v, &d.st->count[1])) return;
     double t[1];
     sum_partials(d, gridDim.x, t, sh);
     if (threadIdx.x == 0) {
@@ -210,136 +217,188 @@ __global__ void __launch_bounds__(NT) k_fem_residual(FemDev d) {
     }
 }
 
-// Start of an inner iteration: r_0 = rho / scale in FP32 (parity 0), the
-// correction, direction and s zero; gamma_0 = r_0 . D^-1 r_0 and r_0 . r_0.
+// Start of an inner iteration (per row): the parity-0 records
+// {r_0 = rho / scale, w = 0, s = 0, 1 / diagonal}, correction and direction
+// zero; the inner record 0 set for the set-up launch.
 __global__ void __launch_bounds__(NT) k_cg_scale(FemDev d) {
-    __shared__ float sh[NT / 32];
     if (block_flag(&d.st->done)) return;
     const double inv = d.st->inv_scale;
-    float rz = 0.f, rr = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x; i < d.nf; i += (int64_t)gridDim.x * NT) {
-        const float r = (float)(d.rho[i] * inv);
         d.xc[i] = 0.f;
         d.p[i] = 0.f;
-        d.s[0][i] = 0.f;
-        d.r[0][i] = r;
-        rz += r * (d.dinv[i] * r);
-        rr += r * r;
+        d.v[0][i] = make_float4((float)(d.rho[i] * inv), 0.f, 0.f, d.dinv[i]);
     }
-    const float v[2] = {block_sum(rz, sh), block_sum(rr, sh)};
-    if (!arrive(d, v, &d.st->count[1])) return;
-    float t[2];
-    sum_partials(d, gridDim.x, t, sh);
-    if (threadIdx.x == 0) {
-        CgState &s = *d.st;
-        s.gamma = t[0];
-        s.rr = s.rr0 = t[1];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        CgInner &o = d.st->in[0];
+        o.gamma = o.alpha = o.rr0 = 0.f;
+        o.mode = 0;
+        o.iter = d.st->iter;
     }
 }
 
-// Slices of 32 rows handled by the calling warp, one per lane (the loop
-// is warp-uniform).
-#define FOR_SLICES(t)                                                                            \
-    for (int64_t t = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5, nsl_ = (d.nf + 31) >> 5; t < nsl_; \
-         t += ((int64_t)gridDim.x * NT) >> 5)
-
-// w_0 = S u_0 (u_0 = D^-1 r_0) and delta_0 = w_0 . u_0; alpha_0 = gamma_0 / delta_0, beta_0 = 0
-__global__ void __launch_bounds__(NT) k_cg_init(FemDev d) {
-    __shared__ float sh[NT / 32];
-    if (block_flag(&d.st->done)) return;
-    const int lane = threadIdx.x & 31;
-    const float *__restrict__ r0 = d.r[0];
-    float dl = 0.f;
-    FOR_SLICES(t) {
-        const int64_t i = 32 * t + lane;
-        const int64_t base = d.sl_ptr[t] + lane;
-        const int width = d.sl_w[t];
-        float w = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < width; ++k) {
-            const int c = d.sl_col[base + 32 * k];
-            w += d.sl_val[base + 32 * k] * (d.dinv[c] * r0[c]);
-        }
-        if (i < d.nf) {
-            d.w[0][i] = w;
-            dl += w * (d.dinv[i] * r0[i]);
-        }
-    }
-    const float v[1] = {block_sum(dl, sh)};
-    if (!arrive(d, v, &d.st->count[2])) return;
-    float t[1];
-    sum_partials(d, gridDim.x, t, sh);
-    if (threadIdx.x == 0) {
-        CgState &s = *d.st;
-        s.alpha = s.gamma / t[0];
-        s.beta = 0.f;
-        const bool bad = !isfinite(s.alpha);
-        s.bad = s.bad || bad;
-        if (bad) s.done = 1;
+// Sums over the block of K values, the same in every thread (a fixed order:
+// shuffles down to lane 0, then the warps' sums in warp order).
+template <int K> __device__ void block_sum_all(float (&v)[K], float (*sh)[NT / 32]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[k][warp] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) t += sh[k][w];
+        v[k] = t;
     }
 }
 
-// One step of the single-reduction recurrence: buffers of parity par are
-// read, those of parity par ^ 1 written.
-__global__ void __launch_bounds__(NT) k_cg_step(FemDev d, int par) {
-    __shared__ float sh[NT / 32];
-    if (block_flag(&d.st->done)) return;
-    const float alpha = d.st->alpha, beta = d.st->beta;
-    const float *__restrict__ r0 = d.r[par];
-    const float *__restrict__ w0 = d.w[par];
-    const float *__restrict__ s0 = d.s[par];
-    float *__restrict__ r1 = d.r[par ^ 1];
-    float *__restrict__ w1 = d.w[par ^ 1];
-    float *__restrict__ s1 = d.s[par ^ 1];
+constexpr int CH = 8;  // matrix entries of a row loaded, and columns gathered, at once
+
+// One inner launch of parity q (records and partial sums of parity q read,
+// those of parity q ^ 1 written): the set-up launch (mode 0) or a step.
+__global__ void __launch_bounds__(NT, 4) k_cg_step(FemDev d, int q) {
+    __shared__ float sh_in[3][NT / 32], sh_out[3][NT / 32];
     const int lane = threadIdx.x & 31;
+    const int64_t nsl = (d.nf + 31) >> 5, tstep = ((int64_t)gridDim.x * NT) >> 5;
+    int64_t t = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
+    int64_t base = 0;
+    int width = 0, c[CH];
+    float a[CH];
+    // plan data of the warp's first slice, before the dependency wait
+    auto load_chunk = [&](int k0) {
+        const int64_t self = min(32 * t + lane, d.nf - 1);
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const bool ok = k0 + j < width;
+            c[j] = ok ? d.sl_col[base + 32 * (k0 + j)] : (int)self;
+            a[j] = ok ? d.sl_val[base + 32 * (k0 + j)] : 0.f;
+        }
+    };
+    if (t < nsl) {
+        base = d.sl_ptr[t] + lane;
+        width = d.sl_w[t];
+        load_chunk(0);
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (block_flag(&d.st->done)) return;
+    const CgInner in = d.st->in[q];
+    float alpha = 0.f, beta = 0.f;
+    if (in.mode > 0) {
+        // the previous launch's partial sums: gamma, delta and r.r of its result
+        const float *part = d.part32 + (size_t)q * 3 * d.nblk_max;
+        const int n = (int)gridDim.x;
+        float v[3] = {0.f, 0.f, 0.f};
+        for (int i0 = 0; i0 < n; i0 += 4 * NT) {
+            float b[3][4];
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = i0 + j * NT + threadIdx.x;
+                    b[k][j] = i < n ? __ldcg(part + k * d.nblk_max + i) : 0.f;
+                }
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) v[k] += b[k][j];
+        }
+        block_sum_all(v, sh_in);
+        const float gm = v[0], dl = v[1], rr = v[2];
+        float rr0 = in.rr0;
+        if (in.mode == 1) {
+            beta = 0.f;
+            alpha = gm / dl;
+            rr0 = rr;
+        } else {
+            beta = gm / in.gamma;
+            alpha = gm / (dl - beta * gm / in.alpha);
+        }
+        // a residual that reached the stopping test (exactly zero included,
+        // where the coefficients are 0/0) ends the inner iteration
+        const bool conv = rr <= d.inner2 * rr0;
+        const bool bad = !isfinite(rr) || (!conv && !(isfinite(alpha) && isfinite(beta)));
+        const bool stop = bad || conv || in.iter >= d.max_iter;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            CgState &s = *d.st;
+            s.gamma = gm;
+            s.rr = rr;
+            s.iter = stop ? in.iter : in.iter + 1;
+            if (stop) {
+                s.bad = s.bad || bad;
+                s.done = 1;
+            } else {
+                CgInner &o = s.in[q ^ 1];
+                o.gamma = gm;
+                o.alpha = alpha;
+                o.rr0 = rr0;
+                o.mode = 2;
+                o.iter = in.iter + 1;
+            }
+        }
+        if (stop) return;  // the same decision in every block
+    } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+        CgInner &o = d.st->in[q ^ 1];
+        o.gamma = o.alpha = o.rr0 = 0.f;
+        o.mode = 1;
+        o.iter = in.iter;
+    }
+    const float4 *__restrict__ v0 = d.v[q];
+    float4 *__restrict__ v1 = d.v[q ^ 1];
     float gm = 0.f, dl = 0.f, rr = 0.f;
-    FOR_SLICES(t) {
+    while (t < nsl) {
         const int64_t i = 32 * t + lane;
-        const int64_t base = d.sl_ptr[t] + lane;
-        const int width = d.sl_w[t];
-        float w = 0.f;
-#pragma unroll 4
-        for (int k = 0; k < width; ++k) {
-            const int c = d.sl_col[base + 32 * k];
-            // u_{k+1} at column c from r_k, w_k and s_{k-1}
-            const float rc = r0[c] - alpha * (w0[c] + beta * s0[c]);
-            w += d.sl_val[base + 32 * k] * (d.dinv[c] * rc);
+        const bool row = i < d.nf;
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        float pold = 0.f, xold = 0.f;
+        if (row) {
+            o = v0[i];
+            pold = d.p[i];
+            xold = d.xc[i];
         }
-        if (i < d.nf) {
-            const float di = d.dinv[i];
-            const float p = di * r0[i] + beta * d.p[i];
-            const float sn = w0[i] + beta * s0[i];
+        float w = 0.f;
+        for (int k0 = 0; k0 < width; k0 += CH) {
+            if (k0 > 0) load_chunk(k0);
+            float4 g[CH];
+#pragma unroll
+            for (int j = 0; j < CH; ++j) g[j] = v0[c[j]];
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+                // u_{k+1} at column c_j from r_k, w_k and s_{k-1}
+                const float rc = g[j].x - alpha * (g[j].y + beta * g[j].z);
+                w += a[j] * (g[j].w * rc);
+            }
+        }
+        if (row) {
+            const float p = o.w * o.x + beta * pold;
+            const float sn = o.y + beta * o.z;
             d.p[i] = p;
-            d.xc[i] += alpha * p;
-            const float rn = r0[i] - alpha * sn;
-            s1[i] = sn;
-            r1[i] = rn;
-            w1[i] = w;
-            const float un = di * rn;
+            d.xc[i] = xold + alpha * p;
+            const float rn = o.x - alpha * sn;
+            v1[i] = make_float4(rn, w, sn, o.w);
+            const float un = o.w * rn;
             gm += rn * un;
             dl += w * un;
             rr += rn * rn;
         }
+        t += tstep;
+        if (t < nsl) {
+            base = d.sl_ptr[t] + lane;
+            width = d.sl_w[t];
+            load_chunk(0);
+        }
     }
-    const float v[3] = {block_sum(gm, sh), block_sum(dl, sh), block_sum(rr, sh)};
-    if (!arrive(d, v, &d.st->count[4])) return;
-    float t[3];
-    sum_partials(d, gridDim.x, t, sh);
+    float v[3] = {gm, dl, rr};
+    block_sum_all(v, sh_out);
     if (threadIdx.x == 0) {
-        CgState &s = *d.st;
-        const float beta_n = t[0] / s.gamma;
-        const float alpha_n = t[0] / (t[1] - beta_n * t[0] / s.alpha);
-        s.gamma = t[0];
-        s.beta = beta_n;
-        s.alpha = alpha_n;
-        s.rr = t[2];
-        s.iter += 1;
-        // a residual that reached the stopping test (exactly zero included,
-        // where the next step's coefficients are 0/0) ends the inner iteration
-        const bool conv = t[2] <= d.inner2 * s.rr0;
-        const bool bad = !isfinite(t[2]) || (!conv && !(isfinite(alpha_n) && isfinite(beta_n)));
-        s.bad = s.bad || bad;
-        s.done = bad || conv || s.iter >= d.max_iter;
+        float *out = d.part32 + (size_t)(q ^ 1) * 3 * d.nblk_max;
+        out[blockIdx.x] = v[0];
+        out[d.nblk_max + blockIdx.x] = v[1];
+        out[2 * d.nblk_max + blockIdx.x] = v[2];
     }
 }
 
@@ -409,20 +468,17 @@ cudaError_t launch_fem_load(const FemDev &d, int prec, const void *m, cudaStream
     else
         k_fem_load<float><<<row_blocks(d), NT, 0, s>>>(d, (const float *)m);
     k_cg_scale<<<elem_blocks(d), NT, 0, s>>>(d);
-    k_cg_init<<<elem_blocks(d), NT, 0, s>>>(d);
     return cudaGetLastError();
 }
 
 cudaError_t launch_cg_iteration(const FemDev &d, int parity, cudaStream_t s) {
-    k_cg_step<<<elem_blocks(d), NT, 0, s>>>(d, parity);
-    return cudaGetLastError();
+    return launch_k(k_cg_step, dim3(elem_blocks(d)), NT, 0, s, d, parity);
 }
 
 cudaError_t launch_fem_correct(const FemDev &d, cudaStream_t s) {
     k_fem_correct<<<elem_blocks(d), NT, 0, s>>>(d);
     k_fem_residual<<<elem_blocks(d), NT, 0, s>>>(d);
     k_cg_scale<<<elem_blocks(d), NT, 0, s>>>(d);
-    k_cg_init<<<elem_blocks(d), NT, 0, s>>>(d);
     return cudaGetLastError();
 }
 

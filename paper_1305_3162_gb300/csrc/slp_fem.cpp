@@ -357,15 +357,14 @@ slp_status build(slp_potential_s &P, const double *X, int64_t N, const int32_t *
     d.rho = vec + 2 * stride;
     d.part = vec + 3 * stride;
     float *v32 = nullptr;
-    FTRY(upload(P, &v32, (const float *)nullptr, (size_t)stride * 8 + 3 * d.nblk_max));
-    d.part32 = v32 + 8 * stride;
+    FTRY(upload(P, &v32, (const float *)nullptr, (size_t)stride * 2 + 6 * d.nblk_max));
     d.xc = v32;
     d.p = v32 + stride;
-    for (int k = 0; k < 2; ++k) {
-        d.r[k] = v32 + (2 + k) * stride;
-        d.w[k] = v32 + (4 + k) * stride;
-        d.s[k] = v32 + (6 + k) * stride;
-    }
+    d.part32 = v32 + 2 * stride;
+    float4 *v4 = nullptr;
+    FTRY(upload(P, &v4, (const float4 *)nullptr, (size_t)stride * 2));
+    d.v[0] = v4;
+    d.v[1] = v4 + stride;
     FTRY(upload(P, &d.st, (const slp::CgState *)nullptr, 1));
     FTRY(cu(cudaMemset(d.st, 0, sizeof(slp::CgState)), "state"));
     FTRY(cu(cudaMemset(d.x, 0, sizeof(double) * stride), "phi_1"));

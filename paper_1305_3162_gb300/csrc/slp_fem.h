@@ -9,15 +9,24 @@
 
 namespace slp {
 
-// Scalars of the solve.  Each is written only by the last block of a launch
-// (after every other block of that launch has read what it needs) and read
-// by the following launches.
+// Scalars an inner step carries to the next one.  A step of parity q reads
+// record q and block 0 writes record q ^ 1, so no block reads what another
+// block of the same launch writes.
+struct CgInner {
+    float gamma;     // gamma_k = r_k . D^-1 r_k of the step that wrote the record
+    float alpha;     // alpha_k of that step
+    float rr0;       // r . r at the start of the inner iteration
+    int mode;        // 0: set-up launch (alpha = beta = 0), 1: first step, 2: later steps
+    long long iter;  // inner steps so far, all corrections together
+};
+
+// Scalars of the solve.  The FP64 fields are written by the last block of the
+// load and residual launches; the inner steps write `in` (above) and, from
+// block 0, the copies the host reads (gamma, rr, iter, done, bad).
 struct CgState {
+    CgInner in[2];
     float gamma;        // r . D^-1 r of the inner residual
-    float alpha;        // step length of the next inner step
-    float beta;         // direction update of the next inner step
-    float rr;           // r . r of the inner residual after the last step
-    float rr0;          // r . r of the inner residual at the inner start
+    float rr;           // r . r of the inner residual at the last stopping test
     double bb;          // b . b
     double rr_hi;       // |b - S x|^2 (FP64 residual) after the last correction
     double scale;       // the inner problem's right-hand side is rho / scale
@@ -27,7 +36,7 @@ struct CgState {
     int done;           // the inner iteration has stopped: later inner launches return at once
     int outer_done;     // |b - S x| <= tol |b|, out of iterations, or non-finite
     int bad;            // a non-finite scalar was seen
-    unsigned count[5];  // arrival counters of the load, scale, start, residual and step launches
+    unsigned count[2];  // arrival counters of the load and residual launches
 };
 
 struct FemDev {
@@ -56,12 +65,13 @@ struct FemDev {
     const int *b_col = nullptr;
     const void *b_val = nullptr;
     double *b = nullptr, *x = nullptr, *rho = nullptr;  // FP64 load, solution and residual
-    // the inner iteration (FP32): correction and direction, and residual r,
-    // w = S D^-1 r and s = S p in buffers of even and odd steps
+    // the inner iteration (FP32): correction and direction, and per row
+    // {r, w = S D^-1 r, s = S p, 1 / diagonal} in buffers of even and odd
+    // steps (one 16-byte load gives a column everything the product needs)
     float *xc = nullptr, *p = nullptr;
-    float *r[2] = {nullptr, nullptr}, *w[2] = {nullptr, nullptr}, *s[2] = {nullptr, nullptr};
-    double *part = nullptr;   // [3][nblk_max] block partial sums, FP64 (load, residual)
-    float *part32 = nullptr;  // [3][nblk_max] block partial sums, FP32 (inner steps)
+    float4 *v[2] = {nullptr, nullptr};
+    double *part = nullptr;   // [nblk_max] block partial sums, FP64 (load, residual)
+    float *part32 = nullptr;  // [2][3][nblk_max] block partial sums of the inner steps, by parity
     CgState *st = nullptr;
     double tol2 = 0.0;    // outer stop: |b - S x|^2 <= tol2 |b|^2
     float inner2 = 0.f;   // inner stop: r.r <= inner2 r0.r0
@@ -83,7 +93,8 @@ constexpr double FEM_INNER = 1e-4;  // each correction's inner steps cut its res
 
 // b = B m and x = 0; the first inner iteration set up from r = b / scale
 cudaError_t launch_fem_load(const FemDev &d, int prec, const void *m, cudaStream_t s);
-// one inner step (parity: the step's index mod 2)
+// one inner launch (parity: the launch's index mod 2; each inner iteration
+// starts at parity 0 with a set-up launch, then one step per launch)
 cudaError_t launch_cg_iteration(const FemDev &d, int parity, cudaStream_t s);
 // x += scale * correction, the FP64 residual, the next inner iteration set up from it
 cudaError_t launch_fem_correct(const FemDev &d, cudaStream_t s);
