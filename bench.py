@@ -458,6 +458,7 @@ def _potential_config(slp, args, flush, n, steps, warmup, prec=32, tol=1e-5, n_s
             ms1.append(q["ms_phi1"])
             ms2.append(q["ms_phi2"])
         q = slp.slp_potential_query(pot)
+        grid = [int(g) for g in slp.slp_query(q["surface_plan"])["grid"]]
         t = sum(ms) / steps
         t1, t2 = sum(ms1) / steps, sum(ms2) / steps
         it, nf, nnz = q["cg_iterations"], q["n_free"], q["stiffness_nnz"]
@@ -482,6 +483,7 @@ def _potential_config(slp, args, flush, n, steps, warmup, prec=32, tol=1e-5, n_s
                 "ms_per_step": t, "steps": steps, "warmup": warmup, "dtype": "f32" if prec == 32 else "f64",
                 "n_nodes": int(X.shape[0]), "n_tets": int(K.shape[0]), "n_free": nf,
                 "n_boundary": q["n_boundary"], "n_faces": q["n_faces"], "stiffness_nnz": nnz,
+                "grid": grid,
                 "cg_iterations": it, "cg_corrections": q["cg_corrections"], "cg_residual": q["cg_residual"],
                 "cg_tolerance": q["cg_tolerance"], "ms_phi1": t1, "ms_phi2": t2, "us_per_inner_step": 1e3 * t1 / max(it, 1),
                 "tolerance": tol, "rel_l2": rel, "rel_l2_phi1": rel1,

@@ -305,8 +305,15 @@ slp_status slp_probe_destroy(slp_probe_t probe);
  * phi = phi_1 + phi_2.
  * nodes: host [n_nodes][3]; tets: host [n_tets][4], either orientation, read
  * during the call; every node in some tetrahedron, every face in at most two,
- * the boundary one closed surface as slp_plan requires.  tolerance, opts: as
- * for slp_plan (opts->device must be a device).  cg_tolerance: 0 picks
+ * the boundary closed as slp_plan requires (it may have several components,
+ * as a shell's two spheres).  tolerance, opts: as for slp_plan
+ * (opts->device must be a device), except that an automatic grid (all three
+ * entries 0) is sized for the boundary and free nodes together: per axis the
+ * power of two nearest 3.7 ((n_boundary + n_free) F)^(1/5) times the axis'
+ * share of the period, F the boundary triangles (for L cells per axis the
+ * grid work grows as L^3 and the exact near field as
+ * (n_boundary + n_free) F / L^2), halved while a triangle spans more cells
+ * than the plan's triangle integrals allow.  cg_tolerance: 0 picks
  * tolerance / 100 (at least 1e-14); cg_max_iterations (FP32 steps in all):
  * 0 picks 10000.
  * Errors: INVALID_ARG, MESH, TOLERANCE_INFEASIBLE, OOM, CUDA, NO_DEVICE. */

@@ -185,3 +185,23 @@ def test_shell_with_a_cavity(n, prec, tol, grid, bar):
                 assert rel_l2(phi1, ref1) <= bar
     finally:
         slp.slp_potential_destroy(pot)
+
+
+def test_automatic_grid_follows_the_cost_rule():
+    """With the grid left automatic, the plan's grid is the power of two
+    nearest 3.7 ((n_boundary + n_free) F)^(1/5) per axis (128 for the n = 16
+    ball: 17217 nodes, 3072 triangles), and phi still equals the oracle's."""
+    slp = lib()
+    X, K = meshes.ball_tets(16, R)
+    o = slp.slp_default_opts()
+    pot = slp.slp_potential_create(X, K, 1e-5, o)
+    try:
+        info = slp.slp_potential_query(pot)
+        grid = list(slp.slp_query(info["surface_plan"])["grid"])
+        assert info["n_faces"] == 3072 and grid == [128, 128, 128], grid
+        m = fields.smooth_random(X, 41)
+        phi, phi1 = _eval(slp, pot, m, 32)
+        ref, ref1, _ = fem.potential(X, K, m)
+        assert rel_l2(phi, ref) <= 1e-5 and rel_l2(phi1, ref1) <= 1e-5
+    finally:
+        slp.slp_potential_destroy(pot)
