@@ -335,7 +335,10 @@ def _roofline_objects(slp, plan, w, info, prof_ms, ms_step, pairs_within, worklo
     else:
         achieved = work / dom_s / 1e12
         mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x clock
+        # FMA lanes per SM and clock: 128 in FP32, 2 in FP64 (the nominal 1.25
+        # TFLOP/s FP64 rate at 2070 MHz), times 2 flops, times the clock
+        lanes = 2 if info["precision"] == 64 else 128
+        peak = 152 * lanes * 2 * mhz * 1e6 / 1e12
         unit = "TFLOP/s"
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", f"dram_traffic_{w.name}_fp{w.precision}.txt")
@@ -350,7 +353,8 @@ def _roofline_objects(slp, plan, w, info, prof_ms, ms_step, pairs_within, worklo
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
                 "traffic": traffic, "kernel": dom, "kernel_ms": prof_ms[dom],
                 "kernel_bytes_or_flops": work,
-                "peak_source": ("sm_max_mhz of " if bound == "alu" else "") + peak_src,
+                "peak_source": (("FP64 " if info["precision"] == 64 else "FP32 ") + "FMA lanes x sm_max_mhz of "
+                                if bound == "alu" else "") + peak_src,
                 # whole evaluation: stage-separated bytes model, and with the near-field operator
                 "eval_bytes_model": model, "eval_bytes_near_operator": near,
                 "eval_frac": (model + near) / t / 1e9 / hbm_peak,
