@@ -339,11 +339,11 @@ slp_status slp_potential_create(const double *nodes, int64_t n_nodes, const int3
                                 int cg_max_iterations, slp_potential_t *out);
 /* d_m: device [n_nodes][3] (plan precision), the nodal magnetisation;
  * d_phi: device [n_nodes], overwritten with phi; d_phi_1: NULL or device
- * [n_nodes], overwritten with phi_1.  Enqueued on `stream`; the call returns
- * once the solve has converged on the device (the host reads the solver's
- * state after every 16 steps while the next 16 are already queued), so it
- * cannot be captured into a CUDA graph; phi_2 and the sum are then enqueued
- * behind it.  Errors: INVALID_ARG, CUDA, NONFINITE (the iteration met
+ * [n_nodes], overwritten with phi_1.  Enqueued on `stream`: the load, the
+ * solve (one graph whose loops over corrections and inner steps run on the
+ * device until the solve stops), phi_2 and the sum.  The call then waits
+ * for the solve, not for phi_2, to return its status, so it cannot be
+ * captured into a CUDA graph.  Errors: INVALID_ARG, CUDA, NONFINITE (the iteration met
  * NaN/Inf), TOLERANCE_INFEASIBLE (cg_max_iterations reached: phi is still
  * written, from the last iterate). */
 slp_status slp_potential_eval(slp_potential_t pot, const void *d_m, void *d_phi, void *d_phi_1, void *stream);

@@ -411,6 +411,39 @@ __global__ void __launch_bounds__(NT) k_fem_correct(FemDev d) {
         d.x[i] += scale * (double)d.xc[i];
 }
 
+// Loop control of the solve graph: WHILE (corrections) { WHILE (inner) {
+// FEM_CHUNK inner launches }, correction, residual, next inner start }.  One
+// thread sets the handle (the only caller while the kernel runs).  Each loop
+// also counts its passes on the device and ends at its bound whatever the
+// state says, so both loops end: the corrections at FEM_MAX_OUTER, the inner
+// passes (which end by themselves once max_iter steps are done) at a bound
+// above that, where the solve is marked bad.
+__global__ void k_loop_outer_start(FemDev d, cudaGraphConditionalHandle h) {
+    d.st->loops_outer = 0;
+    cudaGraphSetConditional(h, d.st->outer_done ? 0u : 1u);
+}
+
+__global__ void k_loop_outer_next(FemDev d, cudaGraphConditionalHandle h, int bound) {
+    CgState &s = *d.st;
+    const int n = ++s.loops_outer;
+    cudaGraphSetConditional(h, (!s.outer_done && n < bound) ? 1u : 0u);
+}
+
+__global__ void k_loop_inner_start(FemDev d, cudaGraphConditionalHandle h) {
+    d.st->loops_inner = 0;
+    cudaGraphSetConditional(h, d.st->done ? 0u : 1u);
+}
+
+__global__ void k_loop_inner_next(FemDev d, cudaGraphConditionalHandle h, int bound) {
+    CgState &s = *d.st;
+    const int n = ++s.loops_inner;
+    if (!s.done && n >= bound) {
+        s.bad = 1;
+        s.done = 1;
+    }
+    cudaGraphSetConditional(h, s.done ? 0u : 1u);
+}
+
 // g_j = (mean of the nodal m over the triangle) . n_j + phi_1(opposite node) / h_j
 // (dphi_1/dn = -phi_1(o)/h_j: the other three nodes are boundary nodes, phi_1 = 0)
 template <typename T>
@@ -479,6 +512,16 @@ cudaError_t launch_fem_correct(const FemDev &d, cudaStream_t s) {
     k_fem_correct<<<elem_blocks(d), NT, 0, s>>>(d);
     k_fem_residual<<<elem_blocks(d), NT, 0, s>>>(d);
     k_cg_scale<<<elem_blocks(d), NT, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fem_loop(FemLoop which, const FemDev &d, cudaGraphConditionalHandle h, int bound, cudaStream_t s) {
+    switch (which) {
+        case LOOP_OUTER_START: k_loop_outer_start<<<1, 1, 0, s>>>(d, h); break;
+        case LOOP_OUTER_NEXT: k_loop_outer_next<<<1, 1, 0, s>>>(d, h, bound); break;
+        case LOOP_INNER_START: k_loop_inner_start<<<1, 1, 0, s>>>(d, h); break;
+        case LOOP_INNER_NEXT: k_loop_inner_next<<<1, 1, 0, s>>>(d, h, bound); break;
+    }
     return cudaGetLastError();
 }
 

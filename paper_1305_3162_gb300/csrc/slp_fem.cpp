@@ -11,11 +11,13 @@
 //     the mean of the four nodal values (m is P1);
 //   * the boundary's triangle-integrated plan (opts.integration = 1) and a
 //     probe set of the free nodes, so that phi_2 reaches every node;
-//   * one CUDA graph of FEM_CHUNK inner conjugate-gradient steps.
-// Evaluation (slp_potential_eval): b = B m; the refined solve on the device
-// (FP32 inner steps, FP64 corrections), the host testing the device's state
-// once per graph launch while the next one is already queued; the charges g;
-// phi_2 through the plan and its probes; phi = phi_1 + phi_2.
+//   * the solve as one CUDA graph: WHILE nodes over the corrections and,
+//     inside each, over passes of FEM_CHUNK inner conjugate-gradient
+//     launches, their handles set on the device from the solver's state.
+// Evaluation (slp_potential_eval): b = B m; the solve graph (FP32 inner
+// steps, FP64 corrections, no host round trip); the charges g; phi_2 through
+// the plan and its probes; phi = phi_1 + phi_2.  The host waits for the
+// solve's state only, to return its status.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -37,7 +39,7 @@ struct slp_potential_s {
     slp_probe_t probe = nullptr;
     slp::FemDev d;
     void *g = nullptr, *phi2_b = nullptr, *phi2_f = nullptr;  // plan precision
-    slp::CgState *h_st = nullptr;                               // page-locked, [2]
+    slp::CgState *h_st = nullptr;                               // page-locked
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -66,6 +68,83 @@ template <typename X> slp_status upload(slp_potential_s &p, X **dst, const X *sr
     if (src && n) FTRY(cu(cudaMemcpy(ptr, src, n * sizeof(X), cudaMemcpyHostToDevice), "potential upload"));
     *dst = (X *)ptr;
     return SLP_OK;
+}
+
+// Captures the launches of `launch` into graph g after the nodes dep[0..ndep);
+// *last is the node the captured work ends in.
+template <typename F>
+cudaError_t capture_into(cudaGraph_t g, cudaStream_t s, const cudaGraphNode_t *dep, size_t ndep, F launch,
+                         cudaGraphNode_t *last) {
+    cudaError_t e = cudaStreamBeginCaptureToGraph(s, g, dep, nullptr, ndep, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t le = launch();
+    cudaStreamCaptureStatus cs;
+    const cudaGraphNode_t *tail = nullptr;
+    size_t ntail = 0;
+    cudaError_t ie = cudaStreamGetCaptureInfo(s, &cs, nullptr, nullptr, &tail, nullptr, &ntail);
+    if (ie == cudaSuccess && ntail == 1)
+        *last = tail[0];
+    else if (ie == cudaSuccess)
+        ie = cudaErrorInvalidValue;  // the captured work must end in one node
+    cudaGraph_t out = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &out);
+    return le != cudaSuccess ? le : ie != cudaSuccess ? ie : ce;
+}
+
+// A WHILE node on `handle` after node dep; *body is the graph it repeats.
+cudaError_t add_while(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle handle, cudaGraphNode_t *node,
+                      cudaGraph_t *body) {
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    const cudaError_t e = cudaGraphAddNode(node, g, &dep, nullptr, 1, &cp);
+    if (e == cudaSuccess) *body = cp.conditional.phGraph_out[0];
+    return e;
+}
+
+// The solve: [outer start] -> WHILE (corrections) { [inner start] -> WHILE
+// (inner) { FEM_CHUNK inner launches -> [inner next] } -> correction,
+// residual, next inner start -> [outer next] }.  The handles start at 0 and
+// only the loop-control kernels set them.
+cudaError_t build_solve_graph(slp_potential_s &P) {
+    const slp::FemDev &d = P.d;
+    cudaStream_t s = P.cap;
+    const int inner_bound = (int)std::min<long long>((d.max_iter + slp::FEM_CHUNK - 1) / slp::FEM_CHUNK + 3, 1 << 30);
+    cudaError_t e = cudaGraphCreate(&P.graph, 0);
+    cudaGraphConditionalHandle ho = 0, hi = 0;
+    cudaGraphNode_t start = nullptr, outer = nullptr, istart = nullptr, inner = nullptr, last = nullptr;
+    cudaGraph_t obody = nullptr, ibody = nullptr;
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&ho, P.graph, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess)
+        e = capture_into(P.graph, s, nullptr, 0, [&] { return slp::launch_fem_loop(slp::LOOP_OUTER_START, d, ho, 0, s); },
+                         &start);
+    if (e == cudaSuccess) e = add_while(P.graph, start, ho, &outer, &obody);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hi, obody, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess)
+        e = capture_into(obody, s, nullptr, 0, [&] { return slp::launch_fem_loop(slp::LOOP_INNER_START, d, hi, 0, s); },
+                         &istart);
+    if (e == cudaSuccess) e = add_while(obody, istart, hi, &inner, &ibody);
+    if (e == cudaSuccess)
+        e = capture_into(ibody, s, nullptr, 0,
+                         [&] {
+                             cudaError_t le = cudaSuccess;
+                             for (int k = 0; k < slp::FEM_CHUNK && le == cudaSuccess; ++k)
+                                 le = slp::launch_cg_iteration(d, k & 1, s);
+                             if (le != cudaSuccess) return le;
+                             return slp::launch_fem_loop(slp::LOOP_INNER_NEXT, d, hi, inner_bound, s);
+                         },
+                         &last);
+    if (e == cudaSuccess)
+        e = capture_into(obody, s, &inner, 1,
+                         [&] {
+                             const cudaError_t le = slp::launch_fem_correct(d, s);
+                             if (le != cudaSuccess) return le;
+                             return slp::launch_fem_loop(slp::LOOP_OUTER_NEXT, d, ho, slp::FEM_MAX_OUTER, s);
+                         },
+                         &last);
+    return e;
 }
 
 void release(slp_potential_s *p) {
@@ -425,20 +504,15 @@ slp_status build(slp_potential_s &P, const double *X, int64_t N, const int32_t *
     P.g = tb;
     P.phi2_b = tb + es * ((F + 7) / 8 * 8);
     P.phi2_f = (unsigned char *)P.phi2_b + es * ((nb + 7) / 8 * 8);
-    FTRY(cu(cudaHostAlloc((void **)&P.h_st, 2 * sizeof(slp::CgState), cudaHostAllocDefault), "host state"));
+    FTRY(cu(cudaHostAlloc((void **)&P.h_st, sizeof(slp::CgState), cudaHostAllocDefault), "host state"));
     for (auto &e : P.ev) FTRY(cu(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event"));
     for (auto &e : P.tev) FTRY(cu(cudaEventCreate(&e), "event"));
 
-    // one graph of FEM_CHUNK inner steps (even, so the parities repeat per launch)
+    // the solve graph
     if (nf > 0) {
         FTRY(cu(cudaStreamCreateWithFlags(&P.cap, cudaStreamNonBlocking), "stream"));
-        FTRY(cu(cudaStreamBeginCapture(P.cap, cudaStreamCaptureModeThreadLocal), "capture"));
-        cudaError_t le = cudaSuccess;
-        for (int k = 0; k < slp::FEM_CHUNK && le == cudaSuccess; ++k) le = slp::launch_cg_iteration(d, k & 1, P.cap);
-        const cudaError_t ce = cudaStreamEndCapture(P.cap, &P.graph);
-        FTRY(cu(le, "iteration capture"));
-        FTRY(cu(ce, "iteration capture"));
-        FTRY(cu(cudaGraphInstantiate(&P.exec, P.graph, 0), "iteration graph"));
+        FTRY(cu(build_solve_graph(P), "solve graph"));
+        FTRY(cu(cudaGraphInstantiate(&P.exec, P.graph, 0), "solve graph"));
     }
     return cu(cudaDeviceSynchronize(), "potential setup");
 }
@@ -484,52 +558,13 @@ slp_status slp_potential_eval(slp_potential_t P, const void *d_m, void *d_phi, v
     bool bad = false, converged = true;
     FTRY(cu(cudaEventRecord(P->tev[0], s), "event"));
     if (P->nf > 0) {
+        // the load, then the solve graph (its loops end on the device: the
+        // inner steps at max_iter in all, the corrections at FEM_MAX_OUTER);
+        // the state is copied behind it for the status
         FTRY(cu(slp::launch_fem_load(d, P->prec, d_m, s), "load"));
-        // Each correction: inner chunks, two graph launches in flight (the
-        // older one's state is read while the newer one runs; inner launches
-        // after the inner stop return at once), then the FP64 correction and
-        // residual, whose state decides whether another correction follows.
-        // Every loop is bounded: the device ends the inner steps at max_iter
-        // steps in all, and the corrections at MAX_OUTER.
-        constexpr int MAX_OUTER = 64;
-        int64_t slot = 0;
-        auto post = [&](bool graph) -> slp_status {
-            if (graph)
-                FTRY(cu(cudaGraphLaunch(P->exec, s), "iteration graph"));
-            else
-                FTRY(cu(slp::launch_fem_correct(d, s), "correction"));
-            FTRY(cu(cudaMemcpyAsync(&P->h_st[slot & 1], d.st, sizeof(slp::CgState), cudaMemcpyDeviceToHost, s),
-                    "state copy"));
-            FTRY(cu(cudaEventRecord(P->ev[slot & 1], s), "event"));
-            ++slot;
-            return SLP_OK;
-        };
-        auto wait = [&](int64_t k) -> slp_status { return cu(cudaEventSynchronize(P->ev[k & 1]), "iteration wait"); };
-        const int64_t max_chunks = (d.max_iter + slp::FEM_CHUNK - 1) / slp::FEM_CHUNK + 2;
-        bool finished = false;
-        for (int o = 0; o < MAX_OUTER && !finished; ++o) {
-            // inner steps until the device says the inner iteration stopped
-            const int64_t first = slot;
-            FTRY(post(true));
-            for (int64_t c = 0; c < max_chunks; ++c) {
-                FTRY(post(true));
-                FTRY(wait(first + c));
-                if (P->h_st[(first + c) & 1].done) break;
-            }
-            // the chunk still in flight returns at once; the correction follows it
-            FTRY(post(false));
-            FTRY(wait(slot - 1));
-            const slp::CgState &h = P->h_st[(slot - 1) & 1];
-            iters = h.iter;
-            outer = h.outer;
-            res = h.bb > 0 ? std::sqrt(std::max(h.rr_hi, 0.0) / h.bb) : 0.0;
-            if (h.outer_done) {
-                finished = true;
-                bad = h.bad != 0;
-                converged = !bad && (h.bb == 0.0 || h.rr_hi <= d.tol2 * h.bb);
-            }
-        }
-        if (!finished) converged = false;
+        FTRY(cu(cudaGraphLaunch(P->exec, s), "solve graph"));
+        FTRY(cu(cudaMemcpyAsync(P->h_st, d.st, sizeof(slp::CgState), cudaMemcpyDeviceToHost, s), "state copy"));
+        FTRY(cu(cudaEventRecord(P->ev[0], s), "event"));
     }
     FTRY(cu(cudaEventRecord(P->tev[1], s), "event"));
     FTRY(cu(slp::launch_fem_charges(d, P->prec, d_m, P->g, s), "charges"));
@@ -539,6 +574,15 @@ slp_status slp_potential_eval(slp_potential_t P, const void *d_m, void *d_phi, v
         FTRY(slp_eval(P->plan, SLP_INPUT_ELEMENT, P->g, P->phi2_b, s));
     FTRY(cu(slp::launch_fem_combine(d, P->prec, P->phi2_b, P->phi2_f, d_phi, d_phi_1, s), "sum"));
     FTRY(cu(cudaEventRecord(P->tev[2], s), "event"));
+    if (P->nf > 0) {
+        FTRY(cu(cudaEventSynchronize(P->ev[0]), "solve wait"));
+        const slp::CgState &h = *P->h_st;
+        iters = h.iter;
+        outer = h.outer;
+        res = h.bb > 0 ? std::sqrt(std::max(h.rr_hi, 0.0) / h.bb) : 0.0;
+        bad = h.bad != 0;
+        converged = h.outer_done && !bad && (h.bb == 0.0 || h.rr_hi <= d.tol2 * h.bb);
+    }
     P->timed = true;
     P->last_iter = iters;
     P->last_outer = outer;

@@ -37,6 +37,8 @@ struct CgState {
     int outer_done;     // |b - S x| <= tol |b|, out of iterations, or non-finite
     int bad;            // a non-finite scalar was seen
     unsigned count[2];  // arrival counters of the load and residual launches
+    int loops_outer;    // passes of the solve graph's correction loop
+    int loops_inner;    // passes of its inner loop in the current correction
 };
 
 struct FemDev {
@@ -88,8 +90,13 @@ struct FemDev {
 };
 
 constexpr int FEM_THREADS = 256;
-constexpr int FEM_CHUNK = 16;       // inner steps per captured graph (even: parities repeat)
+constexpr int FEM_CHUNK = 16;       // inner launches per pass of the inner loop (even: parities repeat)
 constexpr double FEM_INNER = 1e-4;  // each correction's inner steps cut its residual by this factor
+constexpr int FEM_MAX_OUTER = 64;   // corrections at most
+
+// Loop control of the solve graph (one thread each): the value of a WHILE
+// node's handle, from the state.
+enum FemLoop { LOOP_OUTER_START, LOOP_OUTER_NEXT, LOOP_INNER_START, LOOP_INNER_NEXT };
 
 // b = B m and x = 0; the first inner iteration set up from r = b / scale
 cudaError_t launch_fem_load(const FemDev &d, int prec, const void *m, cudaStream_t s);
@@ -98,6 +105,8 @@ cudaError_t launch_fem_load(const FemDev &d, int prec, const void *m, cudaStream
 cudaError_t launch_cg_iteration(const FemDev &d, int parity, cudaStream_t s);
 // x += scale * correction, the FP64 residual, the next inner iteration set up from it
 cudaError_t launch_fem_correct(const FemDev &d, cudaStream_t s);
+// bound: LOOP_OUTER_NEXT the most corrections, LOOP_INNER_NEXT the most inner passes per correction
+cudaError_t launch_fem_loop(FemLoop which, const FemDev &d, cudaGraphConditionalHandle h, int bound, cudaStream_t s);
 cudaError_t launch_fem_charges(const FemDev &d, int prec, const void *m, void *g, cudaStream_t s);
 cudaError_t launch_fem_combine(const FemDev &d, int prec, const void *phi2_b, const void *phi2_f, void *phi,
                                void *phi1, cudaStream_t s);
