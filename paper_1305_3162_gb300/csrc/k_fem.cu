@@ -258,56 +258,102 @@ template <int K> __device__ void block_sum_all(float (&v)[K], float (*sh)[NT / 3
 
 constexpr int CH = 8;  // matrix entries of a row loaded, and columns gathered, at once
 
+// w += (S u)(row) over the row's entries [k0, width) of its slice (base: the
+// lane's first entry), u at each column from its record, CH entries at a
+// time; entries past the row's width read the row's own record with weight 0.
+__device__ __forceinline__ void row_product(const FemDev &d, const float4 *__restrict__ v0, int64_t base, int width,
+                                            int k0, int self, float alpha, float beta, float &w) {
+    for (; k0 < width; k0 += CH) {
+        int c[CH];
+        float a[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            const bool ok = k0 + j < width;
+            c[j] = ok ? d.sl_col[base + 32 * (k0 + j)] : self;
+            a[j] = ok ? d.sl_val[base + 32 * (k0 + j)] : 0.f;
+        }
+        float4 g[CH];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) g[j] = v0[c[j]];
+#pragma unroll
+        for (int j = 0; j < CH; ++j) w += a[j] * (g[j].w * (g[j].x - alpha * (g[j].y + beta * g[j].z)));
+    }
+}
+
 // One inner launch of parity q (records and partial sums of parity q read,
 // those of parity q ^ 1 written): the set-up launch (mode 0) or a step.
+// Before the dependency wait a thread takes its row's first 2 CH entries
+// (plan data): CH into registers, CH into shared memory.  After it, the
+// loads that do not depend on the step's scalars go out together: the stop
+// flag, the inner record, the previous launch's partial sums, the first CH
+// gathered columns (their addresses are plan data) and the row's own record;
+// alpha and beta are formed while they are in flight.
 __global__ void __launch_bounds__(NT, 4) k_cg_step(FemDev d, int q) {
     __shared__ float sh_in[3][NT / 32], sh_out[3][NT / 32];
+    __shared__ int s_col[CH][NT];
+    __shared__ float s_val[CH][NT];
+    __shared__ int s_done;
     const int lane = threadIdx.x & 31;
     const int64_t nsl = (d.nf + 31) >> 5, tstep = ((int64_t)gridDim.x * NT) >> 5;
     int64_t t = ((int64_t)blockIdx.x * NT + threadIdx.x) >> 5;
     int64_t base = 0;
-    int width = 0, c[CH];
-    float a[CH];
-    // plan data of the warp's first slice, before the dependency wait
-    auto load_chunk = [&](int k0) {
-        const int64_t self = min(32 * t + lane, d.nf - 1);
-#pragma unroll
-        for (int j = 0; j < CH; ++j) {
-            const bool ok = k0 + j < width;
-            c[j] = ok ? d.sl_col[base + 32 * (k0 + j)] : (int)self;
-            a[j] = ok ? d.sl_val[base + 32 * (k0 + j)] : 0.f;
-        }
-    };
+    int width = 0;
+    int self = 0;
     if (t < nsl) {
         base = d.sl_ptr[t] + lane;
         width = d.sl_w[t];
-        load_chunk(0);
+        self = (int)min(32 * t + lane, d.nf - 1);
+    }
+    int c[CH];
+    float a[CH];
+#pragma unroll
+    for (int j = 0; j < 2 * CH; ++j) {
+        const bool ok = j < width;
+        const int cj = ok ? d.sl_col[base + 32 * j] : self;
+        const float aj = ok ? d.sl_val[base + 32 * j] : 0.f;
+        if (j < CH) {
+            c[j] = cj;
+            a[j] = aj;
+        } else {
+            s_col[j - CH][threadIdx.x] = cj;
+            s_val[j - CH][threadIdx.x] = aj;
+        }
     }
     pdl_wait();
     pdl_trigger();
-    if (block_flag(&d.st->done)) return;
+    int flag = 0;
+    if (threadIdx.x == 0) flag = *(volatile const int *)&d.st->done;
     const CgInner in = d.st->in[q];
-    float alpha = 0.f, beta = 0.f;
-    if (in.mode > 0) {
-        // the previous launch's partial sums: gamma, delta and r.r of its result
+    const float4 *__restrict__ v0 = d.v[q];
+    float4 g[CH];
+#pragma unroll
+    for (int j = 0; j < CH; ++j) g[j] = v0[c[j]];
+    // the previous launch's partial sums: gamma, delta and r.r of its result
+    // (read whatever the mode; used only after a step)
+    float v[3] = {0.f, 0.f, 0.f};
+    {
         const float *part = d.part32 + (size_t)q * 3 * d.nblk_max;
         const int n = (int)gridDim.x;
-        float v[3] = {0.f, 0.f, 0.f};
-        for (int i0 = 0; i0 < n; i0 += 4 * NT) {
-            float b[3][4];
+        for (int i0 = 0; i0 < n; i0 += 2 * NT) {
+            float b[3][2];
 #pragma unroll
             for (int k = 0; k < 3; ++k)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int i = i0 + j * NT + threadIdx.x;
-                    b[k][j] = i < n ? __ldcg(part + k * d.nblk_max + i) : 0.f;
+                for (int j = 0; j < 2; ++j) {
+                    const int ii = i0 + j * NT + threadIdx.x;
+                    b[k][j] = ii < n ? __ldcg(part + k * d.nblk_max + ii) : 0.f;
                 }
 #pragma unroll
             for (int k = 0; k < 3; ++k)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) v[k] += b[k][j];
+                for (int j = 0; j < 2; ++j) v[k] += b[k][j];
         }
-        block_sum_all(v, sh_in);
+    }
+    if (threadIdx.x == 0) s_done = flag;
+    block_sum_all(v, sh_in);  // its barrier also publishes s_done
+    if (s_done) return;       // the same in every thread of the block
+    float alpha = 0.f, beta = 0.f;
+    if (in.mode > 0) {
         const float gm = v[0], dl = v[1], rr = v[2];
         float rr0 = in.rr0;
         if (in.mode == 1) {
@@ -332,26 +378,40 @@ __global__ void __launch_bounds__(NT, 4) k_cg_step(FemDev d, int q) {
                 s.bad = s.bad || bad;
                 s.done = 1;
             } else {
-                CgInner &o = s.in[q ^ 1];
-                o.gamma = gm;
-                o.alpha = alpha;
-                o.rr0 = rr0;
-                o.mode = 2;
-                o.iter = in.iter + 1;
+                CgInner &on = s.in[q ^ 1];
+                on.gamma = gm;
+                on.alpha = alpha;
+                on.rr0 = rr0;
+                on.mode = 2;
+                on.iter = in.iter + 1;
             }
         }
         if (stop) return;  // the same decision in every block
     } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-        CgInner &o = d.st->in[q ^ 1];
-        o.gamma = o.alpha = o.rr0 = 0.f;
-        o.mode = 1;
-        o.iter = in.iter;
+        CgInner &on = d.st->in[q ^ 1];
+        on.gamma = on.alpha = on.rr0 = 0.f;
+        on.mode = 1;
+        on.iter = in.iter;
     }
-    const float4 *__restrict__ v0 = d.v[q];
     float4 *__restrict__ v1 = d.v[q ^ 1];
     float gm = 0.f, dl = 0.f, rr = 0.f;
-    while (t < nsl) {
-        const int64_t i = 32 * t + lane;
+    // the row update from its own record and the product w of its row
+    auto update = [&](int64_t r, float w, float4 rec, float p_old, float x_old) {
+        const float p = rec.w * rec.x + beta * p_old;
+        const float sn = rec.y + beta * rec.z;
+        d.p[r] = p;
+        d.xc[r] = x_old + alpha * p;
+        const float rn = rec.x - alpha * sn;
+        v1[r] = make_float4(rn, w, sn, rec.w);
+        const float un = rec.w * rn;
+        gm += rn * un;
+        dl += w * un;
+        rr += rn * rn;
+    };
+    int64_t i = 32 * t + lane;
+    if (t < nsl) {
+        // the row's own record and the second chunk's columns, in flight
+        // while the first chunk is added
         const bool row = i < d.nf;
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         float pold = 0.f, xold = 0.f;
@@ -360,45 +420,40 @@ __global__ void __launch_bounds__(NT, 4) k_cg_step(FemDev d, int q) {
             pold = d.p[i];
             xold = d.xc[i];
         }
+        float4 h[CH];
+        if (width > CH) {
+#pragma unroll
+            for (int j = 0; j < CH; ++j) h[j] = v0[s_col[j][threadIdx.x]];
+        }
+        // u_{k+1} at column c from r_k, w_k and s_{k-1}
         float w = 0.f;
-        for (int k0 = 0; k0 < width; k0 += CH) {
-            if (k0 > 0) load_chunk(k0);
-            float4 g[CH];
 #pragma unroll
-            for (int j = 0; j < CH; ++j) g[j] = v0[c[j]];
+        for (int j = 0; j < CH; ++j) w += a[j] * (g[j].w * (g[j].x - alpha * (g[j].y + beta * g[j].z)));
+        if (width > CH) {
 #pragma unroll
-            for (int j = 0; j < CH; ++j) {
-                // u_{k+1} at column c_j from r_k, w_k and s_{k-1}
-                const float rc = g[j].x - alpha * (g[j].y + beta * g[j].z);
-                w += a[j] * (g[j].w * rc);
-            }
+            for (int j = 0; j < CH; ++j)
+                w += s_val[j][threadIdx.x] * (h[j].w * (h[j].x - alpha * (h[j].y + beta * h[j].z)));
         }
-        if (row) {
-            const float p = o.w * o.x + beta * pold;
-            const float sn = o.y + beta * o.z;
-            d.p[i] = p;
-            d.xc[i] = xold + alpha * p;
-            const float rn = o.x - alpha * sn;
-            v1[i] = make_float4(rn, w, sn, o.w);
-            const float un = o.w * rn;
-            gm += rn * un;
-            dl += w * un;
-            rr += rn * rn;
-        }
-        t += tstep;
-        if (t < nsl) {
-            base = d.sl_ptr[t] + lane;
-            width = d.sl_w[t];
-            load_chunk(0);
-        }
+        if (width > 2 * CH) row_product(d, v0, base, width, 2 * CH, self, alpha, beta, w);
+        if (row) update(i, w, o, pold, xold);
     }
-    float v[3] = {gm, dl, rr};
-    block_sum_all(v, sh_out);
+    // further slices of the warp (meshes with more rows than one thread each)
+    for (t += tstep; t < nsl; t += tstep) {
+        base = d.sl_ptr[t] + lane;
+        width = d.sl_w[t];
+        i = 32 * t + lane;
+        self = (int)min(i, d.nf - 1);
+        float w = 0.f;
+        row_product(d, v0, base, width, 0, self, alpha, beta, w);
+        if (i < d.nf) update(i, w, v0[i], d.p[i], d.xc[i]);
+    }
+    float vo[3] = {gm, dl, rr};
+    block_sum_all(vo, sh_out);
     if (threadIdx.x == 0) {
         float *out = d.part32 + (size_t)(q ^ 1) * 3 * d.nblk_max;
-        out[blockIdx.x] = v[0];
-        out[d.nblk_max + blockIdx.x] = v[1];
-        out[2 * d.nblk_max + blockIdx.x] = v[2];
+        out[blockIdx.x] = vo[0];
+        out[d.nblk_max + blockIdx.x] = vo[1];
+        out[2 * d.nblk_max + blockIdx.x] = vo[2];
     }
 }
 
