@@ -8,7 +8,8 @@
 // FP64 solution, and the residual b - S x is recomputed in FP64 (the FP64
 // pipe of this GPU is a small fraction of its FP32 rate, while each
 // correction needs only a few digits).  Per-thread FP64 work is confined to
-// the FP64 residual, the correction and the last block's scalars.
+// the load, the FP64 residual and the correction; the load and the residual
+// form their scalars in their last block.
 //
 // The inner iteration is the conjugate-gradient recurrence with a single
 // reduction per step (Chronopoulos and Gear): with u = D^-1 r and w = S u,
@@ -29,13 +30,13 @@
 // ends in a one-block tail, and the solve repeats bitwise.  An inner
 // iteration starts with a set-up launch (the same kernel with alpha = beta =
 // 0), which forms w_0 = S u_0 and the first partial sums.  The launches are
-// chained by programmatic dependent launch: before its dependency wait a warp
-// loads the first column indices and entries of its slice (plan data).  The
+// chained by programmatic dependent launch: before its dependency wait a
+// thread loads its row's first column indices and entries (plan data).  The
 // inner steps give each row one thread over the matrix in slices of 32 rows
 // (every lane busy with its own row's update, coalesced reads of the
-// entries); the load uses groups of 8 lanes per row over CSR.  Steps
-// launched after the inner stop return at once, so a host that queues steps
-// ahead of the stopping test wastes only empty launches.
+// entries); the load uses groups of 8 lanes per row over CSR.  Launches
+// after the inner stop return at once, so the rest of a pass of the solve
+// graph's inner loop costs only empty launches.
 #include <algorithm>
 #include <cmath>
 

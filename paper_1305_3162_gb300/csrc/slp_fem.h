@@ -22,7 +22,8 @@ struct CgInner {
 
 // Scalars of the solve.  The FP64 fields are written by the last block of the
 // load and residual launches; the inner steps write `in` (above) and, from
-// block 0, the copies the host reads (gamma, rr, iter, done, bad).
+// block 0, the fields the host reads (gamma, rr, iter, done, bad); the solve
+// graph's loop-control kernels keep the loop counters.
 struct CgState {
     CgInner in[2];
     float gamma;        // r . D^-1 r of the inner residual
