@@ -322,15 +322,20 @@ def _timed_steps(plan, kind, d_states, d_phi, stream, flush, steps):
     return [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
 
 
+def _dominant_kernel(prof_ms, bound_of, tie=0.03):
+    """The kernel with the longest median duration.  Kernels within `tie` of
+    it are a tie at timing noise, which goes to an HBM-bound kernel (on the
+    sphere the spread and the near-field product differ by about 1 %), then
+    to the longer one."""
+    top = max(v for v in prof_ms.values() if v > 0)
+    tied = [k for k, v in prof_ms.items() if v >= (1.0 - tie) * top]
+    return max(tied, key=lambda k: (bound_of(k) == "hbm", prof_ms[k]))
+
+
 def _roofline_objects(slp, plan, w, info, prof_ms, ms_step, pairs_within, workload_key):
     peaks, peak_src = _peaks()
     hbm_peak = float(peaks["hbm_gbs"])
-    # the dominant kernel: the longest median; kernels within 3 % of it are a
-    # tie at timing noise, which goes to an HBM-bound kernel (on the sphere the
-    # spread and the near-field product differ by about 1 %)
-    top = max(prof_ms[k] for k in prof_ms if prof_ms[k] > 0)
-    tied = [k for k in prof_ms if prof_ms[k] >= 0.97 * top]
-    dom = max(tied, key=lambda k: (_algorithmic(info, k, w, pairs_within)[0] == "hbm", prof_ms[k]))
+    dom = _dominant_kernel(prof_ms, lambda k: _algorithmic(info, k, w, pairs_within)[0])
     bound, work = _algorithmic(info, dom, w, pairs_within)
     dom_s = prof_ms[dom] / 1e3
     if bound == "hbm":

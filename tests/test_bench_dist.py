@@ -51,6 +51,20 @@ def test_max_over_ranks_and_whole_job_throughput():
         assert v == pytest.approx(1000 * 10 * ws / 1.5)
 
 
+def test_dominant_kernel_breaks_noise_ties_toward_hbm():
+    """The roofline's kernel: the longest median, except that kernels within
+    3 % of it count as a tie, which goes to an HBM-bound kernel; a clear
+    winner is kept whatever its bound."""
+    import bench
+    bound = {"spread": "alu", "near": "hbm", "gather": "hbm", "fft_x": "hbm"}.get
+    sphere = {"spread": 0.02458, "near": 0.02445, "gather": 0.0101, "fft_x": 0.0093}
+    assert bench._dominant_kernel(sphere, bound) == "near"
+    assert bench._dominant_kernel({**sphere, "near": 0.02470}, bound) == "near"
+    cube_fp64 = {"spread": 0.0506, "near": 0.0120, "gather": 0.0101}
+    assert bench._dominant_kernel(cube_fp64, bound) == "spread"
+    assert bench._dominant_kernel({"gather": 0.010, "near": 0.0099, "spread": 0.0}, bound) == "gather"
+
+
 def test_single_process_is_unchanged():
     import bench
     assert bench._max_over_ranks(None, 0.25) == 0.25
