@@ -309,7 +309,7 @@ slp_status slp_probe_destroy(slp_probe_t probe);
  * as a shell's two spheres).  tolerance, opts: as for slp_plan
  * (opts->device must be a device), except that an automatic grid (all three
  * entries 0) is sized for the boundary and free nodes together: per axis the
- * power of two nearest 3.7 ((n_boundary + n_free) F)^(1/5) times the axis'
+ * power of two nearest 3.0 ((n_boundary + n_free) F)^(1/5) times the axis'
  * share of the period, F the boundary triangles (for L cells per axis the
  * grid work grows as L^3 and the exact near field as
  * (n_boundary + n_free) F / L^2), halved while a triangle spans more cells

@@ -206,8 +206,9 @@ struct Face {
 // as L^3 per axis length L, and its exact near field (boundary nodes and free
 // nodes within the truncation radius of a triangle, a radius that shrinks as
 // 1/L) as n_points F / L^2, so the cheapest grid grows as (n_points F)^(1/5).
-// The factor 3.7 is the one measured best (within a factor of two either way)
-// on tetrahedral balls of 17k and 134k nodes; each axis gets its share of the
+// The factor 3.0 lies inside the range that picks the grid measured best on
+// tetrahedral balls of 17k, 134k and 449k nodes (128, 256 and 256 cells per
+// axis; any factor from 2.6 to 3.46 does); each axis gets its share of the
 // period as in the plan's own automatic grid, rounded to the nearest power of
 // two.
 void potential_grid(const std::vector<double> &V, int64_t n_points, int64_t F, int grid[3]) {
@@ -229,7 +230,7 @@ void potential_grid(const std::vector<double> &V, int64_t n_points, int64_t F, i
         r2 = std::max(r2, s);
     }
     const double diam = 2.0 * std::sqrt(r2);
-    const double cells = 3.7 * std::pow((double)std::max<int64_t>(n_points, 1) * (double)std::max<int64_t>(F, 1), 0.2);
+    const double cells = 3.0 * std::pow((double)std::max<int64_t>(n_points, 1) * (double)std::max<int64_t>(F, 1), 0.2);
     for (int d = 0; d < 3; ++d) {
         const double want = cells * (D[d] + diam) / (dmax + diam);
         int v = 16;

@@ -189,7 +189,7 @@ def test_shell_with_a_cavity(n, prec, tol, grid, bar):
 
 def test_automatic_grid_follows_the_cost_rule():
     """With the grid left automatic, the plan's grid is the power of two
-    nearest 3.7 ((n_boundary + n_free) F)^(1/5) per axis (128 for the n = 16
+    nearest 3.0 ((n_boundary + n_free) F)^(1/5) per axis (128 for the n = 16
     ball: 17217 nodes, 3072 triangles), and phi still equals the oracle's."""
     slp = lib()
     X, K = meshes.ball_tets(16, R)
