@@ -205,3 +205,29 @@ def test_automatic_grid_follows_the_cost_rule():
         assert rel_l2(phi, ref) <= 1e-5 and rel_l2(phi1, ref1) <= 1e-5
     finally:
         slp.slp_potential_destroy(pot)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_zero_field_and_non_finite_input(prec):
+    """m = 0: b = 0, the solve stops before any inner step and phi = phi_1 =
+    0 exactly.  A NaN in m: the load's sums are not finite, the solve ends at
+    once and the call reports NONFINITE; the next call with a finite m
+    succeeds again."""
+    slp = lib()
+    X, K = meshes.ball_tets(4, R)
+    pot = slp.slp_potential_create(X, K, 1e-5 if prec == 32 else 1e-10, _opts(slp, prec, 32))
+    try:
+        phi, phi1 = _eval(slp, pot, np.zeros_like(X), prec)
+        assert not phi.any() and not phi1.any()
+        assert slp.slp_potential_query(pot)["cg_iterations"] == 0
+        bad = fields.smooth_random(X, 5)
+        bad[7, 1] = np.nan
+        with pytest.raises(slp.SlpError) as e:
+            _eval(slp, pot, bad, prec)
+        assert e.value.status == slp.SLP_ERR_NONFINITE
+        m = fields.smooth_random(X, 5)
+        phi, _ = _eval(slp, pot, m, prec)
+        ref, _, _ = fem.potential(X, K, m)
+        assert rel_l2(phi, ref) <= (1e-5 if prec == 32 else 1e-9)
+    finally:
+        slp.slp_potential_destroy(pot)
