@@ -103,6 +103,33 @@ const char *slp_debug_stage_name(int i);
 double slp_debug_window(int m, double d);
 double slp_debug_window_hat(int m, int L, double l);
 
+/* The host set-up of the scalar potential (slp_potential_create without a
+ * device; Sec. 2.1 and Alg. 1): the node classes, the boundary triangles,
+ * the free-node stiffness matrix and the load operator, in FP64.
+ * nodes, tets: as for slp_potential_create.  counts[5] receives n_free,
+ * n_boundary, n_faces, the stiffness entries s_nnz and the load entries
+ * b_nnz.  Each array that is not NULL receives (a first call with NULL arrays
+ * gives the sizes):
+ *   node_slot [n_nodes] int32: free index (>= 0) or -1 - boundary index;
+ *   faces [n_faces][4] int32: nodes a, b, c wound so that (b - a) x (c - a)
+ *     points out of the volume, and the free index of the owning
+ *     tetrahedron's fourth node (-1 when it is a boundary node);
+ *   face_geom [n_faces][4] double: the unit outward normal and 1/h, h the
+ *     owning tetrahedron's height over the triangle;
+ *   s_ptr [n_free + 1] int64, s_col [s_nnz] int32, s_val [s_nnz] double:
+ *     S(free, free) in CSR over free indices, columns ascending,
+ *     S_ab = sum over tetrahedra T of |T| grad eta_a . grad eta_b;
+ *   b_ptr [n_free + 1] int64, b_col [b_nnz] int32, b_val [b_nnz][3] double:
+ *     the load operator in CSR over free rows, columns node indices
+ *     ascending (the row's own node left out): b_a = sum over the row's
+ *     entries of b_val . (m_col - m_a), = sum over T of |T| grad eta_a .
+ *     mean_T(m) for nodal m.
+ * Errors: INVALID_ARG, MESH (as slp_potential_create). */
+slp_status slp_debug_fem_assemble(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                                  int64_t counts[5], int32_t *node_slot, int32_t *faces, double *face_geom,
+                                  int64_t *s_ptr, int32_t *s_col, double *s_val, int64_t *b_ptr, int32_t *b_col,
+                                  double *b_val);
+
 #ifdef __cplusplus
 }
 #endif

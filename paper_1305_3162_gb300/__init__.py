@@ -153,7 +153,7 @@ EXPORTED = ["slp_default_opts", "slp_plan", "slp_eval", "slp_eval_states", "slp_
             "slp_check", "slp_destroy", "slp_status_string", "slp_last_error",
             "slp_debug_run", "slp_debug_copy", "slp_debug_buffer_bytes", "slp_debug_host_count",
             "slp_debug_host_array", "slp_debug_window", "slp_debug_window_hat", "slp_debug_profile",
-            "slp_debug_timeline",
+            "slp_debug_timeline", "slp_debug_fem_assemble",
             "slp_debug_stage_name", "slp_eval_direct_static", "slp_batch_create", "slp_batch_run",
             "slp_batch_query", "slp_batch_destroy", "slp_eval_batched", "slp_plan_autotune", "slp_server_default_opts",
             "slp_server_create", "slp_server_submit", "slp_server_status", "slp_server_wait", "slp_server_cancel",
@@ -211,6 +211,8 @@ def load():
         "slp_debug_profile": ([vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int], St),
         "slp_debug_timeline": ([vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(ctypes.c_float)], St),
         "slp_debug_stage_name": ([ctypes.c_int], ctypes.c_char_p),
+        "slp_debug_fem_assemble": ([ctypes.POINTER(ctypes.c_double), I64, ctypes.POINTER(ctypes.c_int32), I64,
+                                    ctypes.POINTER(I64), vp, vp, vp, vp, vp, vp, vp, vp, vp], St),
         "slp_eval_direct_static": ([vp, I64, vp, I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp], St),
         "slp_batch_create": ([ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                               ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)], St),
@@ -366,6 +368,28 @@ def slp_potential_create(nodes, tets, tolerance: float, opts: slp_plan_opts | No
                                        K.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), K.shape[0],
                                        float(tolerance), ctypes.byref(o), float(cg_tolerance), int(cg_max_iterations),
                                        ctypes.byref(out)), "slp_potential_create")
+    return out
+
+
+def slp_debug_fem_assemble(nodes, tets) -> dict:
+    """The host set-up of the scalar potential (include/slp_debug.h): node
+    classes, outward boundary faces with normals and 1/h, S(free, free) and
+    the load operator as numpy arrays."""
+    X = np.ascontiguousarray(nodes, dtype=np.float64)
+    K = np.ascontiguousarray(tets, dtype=np.int32)
+    args = (X.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), X.shape[0],
+            K.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), K.shape[0])
+    counts = (ctypes.c_int64 * 5)()
+    _check(load().slp_debug_fem_assemble(*args, counts, *([None] * 9)), "slp_debug_fem_assemble")
+    nf, nb, nfc, snz, bnz = (int(c) for c in counts)
+    out = {"n_free": nf, "n_boundary": nb,
+           "node_slot": np.zeros(X.shape[0], np.int32), "faces": np.zeros((nfc, 4), np.int32),
+           "face_geom": np.zeros((nfc, 4)), "s_ptr": np.zeros(nf + 1, np.int64), "s_col": np.zeros(snz, np.int32),
+           "s_val": np.zeros(snz), "b_ptr": np.zeros(nf + 1, np.int64), "b_col": np.zeros(bnz, np.int32),
+           "b_val": np.zeros((bnz, 3))}
+    keys = ("node_slot", "faces", "face_geom", "s_ptr", "s_col", "s_val", "b_ptr", "b_col", "b_val")
+    _check(load().slp_debug_fem_assemble(*args, counts, *[out[k].ctypes.data_as(ctypes.c_void_p) for k in keys]),
+           "slp_debug_fem_assemble")
     return out
 
 

@@ -23,6 +23,7 @@
 #include <cstring>
 #include <vector>
 
+#include "../../include/slp_debug.h"
 #include "slp_fem.h"
 #include "slp_plan_internal.h"
 
@@ -239,8 +240,24 @@ void potential_grid(const std::vector<double> &V, int64_t n_points, int64_t F, i
     }
 }
 
-slp_status build(slp_potential_s &P, const double *X, int64_t N, const int32_t *tets, int64_t K, double tolerance,
-                 const slp_plan_opts *opts) {
+// The set-up on the host (FP64): node classes and numbering, the boundary
+// triangles wound outward with their normals and 1/h, S(free, free) in CSR
+// and the load operator in CSR over free rows.
+struct FemHost {
+    int64_t nf = 0, nb = 0, F = 0;
+    std::vector<int> slot;  // per node: free index (>= 0) or -1 - boundary index
+    std::vector<int64_t> free_nodes, bnd_nodes;
+    std::vector<int32_t> Ts;       // [F][3] boundary triangles in boundary-node indices, wound outward
+    std::vector<int4> face;        // nodes a, b, c (outward) and the free index of the fourth node, or -1
+    std::vector<double4> face_n;   // unit outward normal and 1/h
+    std::vector<int64_t> s_ptr, b_ptr;
+    std::vector<int> s_col, b_col;  // free indices (S), node indices (B)
+    std::vector<double> s_val, dinv;
+    std::vector<float> s_val32;
+    std::vector<double4> b_val;    // (x, y, z, 0)
+};
+
+slp_status assemble(const double *X, int64_t N, const int32_t *tets, int64_t K, FemHost &H) {
     // hat-function gradients of every tetrahedron
     std::vector<double> grads((size_t)K * 12), vols(K);
     for (int64_t t = 0; t < K; ++t) {
@@ -283,8 +300,9 @@ slp_status build(slp_potential_s &P, const double *X, int64_t N, const int32_t *
         if (!used[i]) return slp_fail(SLP_ERR_MESH, "node %lld belongs to no tetrahedron", (long long)i);
     for (const Face &f : bfaces)
         for (int a = 0; a < 3; ++a) bnd[f.k[a]] = 1;
-    std::vector<int> slot(N);
-    std::vector<int64_t> free_nodes, bnd_nodes;
+    std::vector<int> &slot = H.slot;
+    std::vector<int64_t> &free_nodes = H.free_nodes, &bnd_nodes = H.bnd_nodes;
+    slot.assign(N, 0);
     for (int64_t i = 0; i < N; ++i) {
         if (bnd[i]) {
             slot[i] = -1 - (int)bnd_nodes.size();
@@ -295,13 +313,16 @@ slp_status build(slp_potential_s &P, const double *X, int64_t N, const int32_t *
         }
     }
     const int64_t nf = (int64_t)free_nodes.size(), nb = (int64_t)bnd_nodes.size(), F = (int64_t)bfaces.size();
-    P.nf = nf;
-    P.nb = nb;
-    P.nfaces = F;
+    H.nf = nf;
+    H.nb = nb;
+    H.F = F;
     // boundary triangles wound outward, their normals and 1/h
-    std::vector<int32_t> Ts((size_t)F * 3);
-    std::vector<int4> face(F);
-    std::vector<double4> face_n(F);
+    std::vector<int32_t> &Ts = H.Ts;
+    std::vector<int4> &face = H.face;
+    std::vector<double4> &face_n = H.face_n;
+    Ts.assign((size_t)F * 3, 0);
+    face.assign(F, int4{});
+    face_n.assign(F, double4{});
     for (int64_t j = 0; j < F; ++j) {
         const Face &f = bfaces[j];
         const int32_t o = tets[4 * f.tet + f.local];
@@ -359,11 +380,19 @@ slp_status build(slp_potential_s &P, const double *X, int64_t N, const int32_t *
     };
     merge(se);
     merge(be);
-    std::vector<int64_t> s_ptr(nf + 1, 0), b_ptr(nf + 1, 0);
-    std::vector<int> s_col(se.size()), b_col(be.size());
-    std::vector<double> s_val(se.size()), dinv(nf, 0.0);
-    std::vector<float> s_val32(se.size());
-    std::vector<double4> b_val(be.size());
+    std::vector<int64_t> &s_ptr = H.s_ptr, &b_ptr = H.b_ptr;
+    std::vector<int> &s_col = H.s_col, &b_col = H.b_col;
+    std::vector<double> &s_val = H.s_val, &dinv = H.dinv;
+    std::vector<float> &s_val32 = H.s_val32;
+    std::vector<double4> &b_val = H.b_val;
+    s_ptr.assign(nf + 1, 0);
+    b_ptr.assign(nf + 1, 0);
+    s_col.assign(se.size(), 0);
+    b_col.assign(be.size(), 0);
+    s_val.assign(se.size(), 0.0);
+    dinv.assign(nf, 0.0);
+    s_val32.assign(se.size(), 0.f);
+    b_val.assign(be.size(), double4{});
     for (size_t i = 0; i < se.size(); ++i) {
         const int64_t r = se[i].key / nf, c = se[i].key % nf;
         ++s_ptr[r + 1];
@@ -384,12 +413,34 @@ slp_status build(slp_potential_s &P, const double *X, int64_t N, const int32_t *
         if (!(dinv[i] > 0) || !std::isfinite(dinv[i]))
             return slp_fail(SLP_ERR_MESH, "free node %lld has no positive stiffness diagonal", (long long)free_nodes[i]);
     }
-    P.s_nnz = (int64_t)se.size();
-    P.b_nnz = (int64_t)be.size();
     se.clear();
     se.shrink_to_fit();
     be.clear();
     be.shrink_to_fit();
+
+    return SLP_OK;
+}
+
+slp_status build(slp_potential_s &P, const double *X, int64_t N, const int32_t *tets, int64_t K, double tolerance,
+                 const slp_plan_opts *opts) {
+    FemHost H;
+    FTRY(assemble(X, N, tets, K, H));
+    const int64_t nf = H.nf, nb = H.nb, F = H.F;
+    P.nf = nf;
+    P.nb = nb;
+    P.nfaces = F;
+    P.s_nnz = (int64_t)H.s_col.size();
+    P.b_nnz = (int64_t)H.b_col.size();
+    const std::vector<int> &slot = H.slot;
+    const std::vector<int64_t> &free_nodes = H.free_nodes, &bnd_nodes = H.bnd_nodes;
+    const std::vector<int32_t> &Ts = H.Ts;
+    const std::vector<int4> &face = H.face;
+    const std::vector<double4> &face_n = H.face_n;
+    const std::vector<int64_t> &s_ptr = H.s_ptr, &b_ptr = H.b_ptr;
+    const std::vector<int> &s_col = H.s_col, &b_col = H.b_col;
+    const std::vector<double> &s_val = H.s_val, &dinv = H.dinv;
+    const std::vector<float> &s_val32 = H.s_val32;
+    const std::vector<double4> &b_val = H.b_val;
 
     // the boundary's plan and the free nodes as its probes
     std::vector<double> Vs((size_t)nb * 3), Xf((size_t)nf * 3);
@@ -629,6 +680,53 @@ slp_status slp_potential_query(slp_potential_t P, slp_potential_info *info) {
 
 slp_status slp_potential_destroy(slp_potential_t P) {
     release(P);
+    return SLP_OK;
+}
+
+slp_status slp_debug_fem_assemble(const double *nodes, int64_t n_nodes, const int32_t *tets, int64_t n_tets,
+                                  int64_t counts[5], int32_t *node_slot, int32_t *faces, double *face_geom,
+                                  int64_t *s_ptr, int32_t *s_col, double *s_val, int64_t *b_ptr, int32_t *b_col,
+                                  double *b_val) {
+    if (!counts) return slp_fail(SLP_ERR_INVALID_ARG, "counts is NULL");
+    if (!nodes || !tets || n_nodes < 4 || n_tets < 1)
+        return slp_fail(SLP_ERR_INVALID_ARG, "nodes or tetrahedra missing");
+    if (n_nodes >= (1LL << 31) || n_tets >= (1LL << 31)) return slp_fail(SLP_ERR_INVALID_ARG, "mesh too large");
+    for (int64_t i = 0; i < 3 * n_nodes; ++i)
+        if (!std::isfinite(nodes[i])) return slp_fail(SLP_ERR_INVALID_ARG, "node coordinates must be finite");
+    FemHost H;
+    FTRY(assemble(nodes, n_nodes, tets, n_tets, H));
+    counts[0] = H.nf;
+    counts[1] = H.nb;
+    counts[2] = H.F;
+    counts[3] = (int64_t)H.s_col.size();
+    counts[4] = (int64_t)H.b_col.size();
+    if (node_slot)
+        for (int64_t i = 0; i < n_nodes; ++i) node_slot[i] = H.slot[i];
+    for (int64_t j = 0; j < H.F; ++j) {
+        if (faces) {
+            faces[4 * j] = H.face[j].x;
+            faces[4 * j + 1] = H.face[j].y;
+            faces[4 * j + 2] = H.face[j].z;
+            faces[4 * j + 3] = H.face[j].w;
+        }
+        if (face_geom) {
+            face_geom[4 * j] = H.face_n[j].x;
+            face_geom[4 * j + 1] = H.face_n[j].y;
+            face_geom[4 * j + 2] = H.face_n[j].z;
+            face_geom[4 * j + 3] = H.face_n[j].w;
+        }
+    }
+    if (s_ptr) std::copy(H.s_ptr.begin(), H.s_ptr.end(), s_ptr);
+    if (s_col) std::copy(H.s_col.begin(), H.s_col.end(), s_col);
+    if (s_val) std::copy(H.s_val.begin(), H.s_val.end(), s_val);
+    if (b_ptr) std::copy(H.b_ptr.begin(), H.b_ptr.end(), b_ptr);
+    if (b_col) std::copy(H.b_col.begin(), H.b_col.end(), b_col);
+    if (b_val)
+        for (size_t e = 0; e < H.b_val.size(); ++e) {
+            b_val[3 * e] = H.b_val[e].x;
+            b_val[3 * e + 1] = H.b_val[e].y;
+            b_val[3 * e + 2] = H.b_val[e].z;
+        }
     return SLP_OK;
 }
 
